@@ -1,0 +1,402 @@
+"""Pins of the oracle against the paper and the mathematics (CPU only).
+
+Each oracle function is checked against something other than itself: hand-derived values,
+published known-answer outputs, a high-precision textbook recurrence, SciPy's barycentric
+interpolation, dense eigendecompositions, closed-form log-determinants and finite differences.
+"""
+from __future__ import annotations
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import divdiff, leja, logdet, rng
+from synth import (csr_from_dense, diagonal, laplacian_2d, laplacian_3d, matern_2d,
+                   matern_2d_derivatives, random_spd)
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------------------------ Léja points
+
+def test_leja_prefix_hand_derived():
+    want = [float(r[0]) for r in _golden_rows("leja_prefix.txt")]
+    got = leja.fast_leja_points(len(want))
+    assert got.tolist() == want
+
+
+def test_leja_matches_exact_rational_construction():
+    """Fast Léja points by exact rational arithmetic (no rounding anywhere; ties -> smaller x)
+    agree with the FP64 construction on a 60-point prefix."""
+    count = 60
+    pts = [Fraction(2), Fraction(-2)]
+    while len(pts) < count:
+        srt = sorted(pts)
+        best, best_x = None, None
+        for a, b in zip(srt[:-1], srt[1:]):
+            x = (a + b) / 2
+            s = Fraction(1)
+            for p in pts:
+                s *= abs(x - p)
+            if best is None or s > best:
+                best, best_x = s, x
+        pts.append(best_x)
+    got = leja.fast_leja_points(count)
+    assert got.tolist() == [float(p) for p in pts]
+
+
+def test_leja_greedy_property_against_grid():
+    """Each fast Léja point nearly maximises prod |x - xi_k| over a fine grid of [-2, 2]
+    (the continuous definition, Eq. Léja5): within a factor 0.5, and the points are distinct."""
+    xi = leja.fast_leja_points(80)
+    assert len(set(xi.tolist())) == 80
+    assert np.all(np.abs(xi) <= 2.0)
+    grid = np.linspace(-2, 2, 200001)
+    logs = np.zeros_like(grid)
+    for j in range(1, 80):
+        logs += np.log(np.abs(grid - xi[j - 1]) + 1e-300)
+        val = np.sum(np.log(np.abs(xi[j] - xi[:j])))
+        assert val >= logs.max() + math.log(0.5)
+
+
+# ------------------------------------------------------------------------ divided differences
+
+@pytest.mark.parametrize("lmin,lmax,m", [
+    (0.1, 8.1, 39),          # 2-D Laplacian + 0.1 I, before sigma-normalisation
+    (1.0, 81.0, 39),         # the same interval after sigma-normalisation
+    (1.0, 241.0, 60),        # 3-D Laplacian + 0.05 I
+    (1.0, 241.0, 120),
+    (1.0, 8080.0, 80),       # Matérn tau (kappa^2 I + L)^2 with kappa = 0.3
+    (2.0, 3.0, 10),
+])
+def test_divided_differences_vs_high_precision_recurrence(lmin, lmax, m):
+    xi = leja.fast_leja_points(m + 1)
+    c, g = (lmin + lmax) / 2, (lmax - lmin) / 4
+    d, p = divdiff.divided_differences(xi, c, g)
+    ref = pins.hp_scaled_divided_differences(lmin, lmax, xi)
+    assert np.max(np.abs(d - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_divided_differences_two_point_closed_form():
+    lmin, lmax = 0.3, 7.0
+    xi = leja.fast_leja_points(2)          # z_0 = lmax, z_1 = lmin
+    c, g = (lmin + lmax) / 2, (lmax - lmin) / 4
+    d, _ = divdiff.divided_differences(xi, c, g)
+    assert d[0] == pytest.approx(math.log(lmax), rel=1e-15)
+    assert d[1] == pytest.approx(g * (math.log(lmin) - math.log(lmax)) / (lmin - lmax), rel=1e-13)
+
+
+def test_divided_differences_interpolate_log_at_nodes():
+    lmin, lmax, m = 0.05, 12.05, 60
+    xi = leja.fast_leja_points(m + 1)
+    c, g = (lmin + lmax) / 2, (lmax - lmin) / 4
+    d, _ = divdiff.divided_differences(xi, c, g)
+    for i in range(0, m + 1, 7):
+        z = c + g * xi[i]
+        assert pins.newton_value_hp(d, xi, lmin, lmax, z) == pytest.approx(math.log(z), rel=1e-12, abs=1e-12)
+
+
+def test_divided_differences_independent_of_s():
+    """log(Q_m) e_1 does not depend on s_val (only the series' convergence does): a dropped
+    log(s) term or a wrong Taylor sign would make the two disagree."""
+    lmin, lmax, m = 1.0, 50.0, 40
+    xi = leja.fast_leja_points(m + 1)
+    c, g = (lmin + lmax) / 2, (lmax - lmin) / 4
+    d1, _ = divdiff.divided_differences(xi, c, g, s=c)
+    d2, _ = divdiff.divided_differences(xi, c, g, s=0.7 * lmax)
+    assert np.max(np.abs(d1 - d2)) <= 1e-12 * np.max(np.abs(d1))
+
+
+def test_divided_differences_sigma_invariance():
+    """Scaling the interval by 1/sigma leaves d_j (j >= 1) unchanged and shifts d_0 by -log sigma."""
+    lmin, lmax, m = 0.1, 8.1, 39
+    sigma = logdet.sigma_of(lmin)
+    _, _, _, d1, _ = logdet.newton_leja_setup(lmin, lmax, m)
+    _, _, _, d2, _ = logdet.newton_leja_setup(lmin / sigma, lmax / sigma, m)
+    assert d2[0] == pytest.approx(d1[0] - math.log(sigma), rel=1e-13)
+    assert np.max(np.abs(d1[1:] - d2[1:])) <= 1e-12 * np.max(np.abs(d1))
+
+
+def test_divided_differences_nonconvergence_is_an_error():
+    xi = leja.fast_leja_points(21)
+    with pytest.raises(divdiff.DividedDifferenceError):
+        divdiff.divided_differences(xi, 5.0, 2.4, s=5.0, max_terms=50)
+
+
+def test_taylor_term_counts_match_survey_checks():
+    # s = c gives |z/s - 1| <= (k-1)/(k+1); the term counts grow with the condition number
+    _, _, _, _, p1 = logdet.newton_leja_setup(1.0, 81.0, 39)
+    _, _, _, _, p3 = logdet.newton_leja_setup(1.0, 8080.0, 80)
+    assert 500 < p1 < 5000
+    assert 20000 < p3 < 500000
+
+
+# --------------------------------------------------------------------------------------- probes
+
+def test_splitmix64_known_answers():
+    golden = 0x9E3779B97F4A7C15
+    for seed, idx, val in _golden_rows("splitmix64_kat.txt"):
+        state = (int(seed) + (int(idx) - 1) * golden) % 2 ** 64
+        got = int(rng.mix(np.array([state], dtype=np.uint64))[0])
+        assert got == int(val, 16)
+
+
+def test_probe_counter_layout():
+    # x[row, col] for stream s is mix(seed ^ mix(s<<56 | col<<32 | row))
+    x = rng.raw_bits(7, 1, 5, 3)
+    for r in range(5):
+        for c in range(3):
+            ctr = (1 << 56) | (c << 32) | r
+            inner = int(rng.mix(np.array([ctr], dtype=np.uint64))[0])
+            assert int(x[r, c]) == int(rng.mix(np.array([7 ^ inner], dtype=np.uint64))[0])
+
+
+def test_rademacher_statistics():
+    S = rng.rademacher(0, 0, 200000, 4)
+    assert set(np.unique(S).tolist()) == {-1.0, 1.0}
+    assert np.all(np.abs(S.mean(axis=0)) < 5 / math.sqrt(200000))
+    # different columns / streams / seeds are uncorrelated
+    G = rng.rademacher(0, 1, 200000, 4)
+    assert abs(np.mean(S[:, 0] * S[:, 1])) < 5 / math.sqrt(200000)
+    assert abs(np.mean(S[:, 0] * G[:, 0])) < 5 / math.sqrt(200000)
+    assert abs(np.mean(S[:, 0] * rng.rademacher(1, 0, 200000, 1)[:, 0])) < 5 / math.sqrt(200000)
+
+
+def test_gaussian_statistics():
+    g = rng.gaussian(3, 0, 400000, 1)[:, 0]
+    assert abs(g.mean()) < 5 / math.sqrt(400000)
+    assert abs(g.var() - 1.0) < 0.02
+    assert abs(np.mean(g ** 4) - 3.0) < 0.1        # Gaussian kurtosis
+    assert np.all(np.isfinite(g))
+
+
+# ------------------------------------------------------------------------------ p(A)V (Alg. 2)
+
+def test_apply_poly_diagonal_matrix_equals_scalar_interpolant():
+    n, lmin, lmax, m = 300, 0.2, 9.0, 45
+    dvals = np.linspace(lmin, lmax, n) ** 1.0
+    A = diagonal(dvals)
+    V = rng.rademacher(1, 0, n, 3)
+    P = logdet.apply_poly(A, V, lmin, lmax, m)
+    p = pins.interpolant(lmin, lmax, leja.fast_leja_points(m + 1))
+    ref = p(dvals)[:, None] * V
+    assert np.max(np.abs(P - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_apply_poly_dense_eigendecomposition(seed):
+    A = random_spd(150, nnz_per_row=6, seed=seed, empty_rows=3, dense_row=(seed == 1))
+    Ad = A.to_scipy().toarray()
+    lam = np.linalg.eigvalsh(Ad)
+    lmin, lmax = 0.9 * lam[0], 1.1 * lam[-1]
+    m = 50
+    V = np.random.default_rng(seed).standard_normal((A.n, 4))
+    P = logdet.apply_poly(A, V, lmin, lmax, m)
+    p = pins.interpolant(lmin, lmax, leja.fast_leja_points(m + 1))
+    ref = pins.dense_matrix_function(Ad, p) @ V
+    assert np.max(np.abs(P - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_apply_poly_converges_to_log():
+    """Proposition 3.1: the error of p_m(A)v against log(A)v decays geometrically."""
+    A = laplacian_2d(12, 0.5)
+    Ad = A.to_scipy().toarray()
+    lmin, lmax = logdet.gershgorin(A)
+    V = rng.rademacher(0, 0, A.n, 1)
+    ref = pins.dense_matrix_function(Ad, np.log) @ V
+    errs = [np.max(np.abs(logdet.apply_poly(A, V, lmin, lmax, m) - ref)) for m in (10, 20, 40, 80)]
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    kappa = lmax / lmin
+    rho = (math.sqrt(kappa) + 1) / (math.sqrt(kappa) - 1)
+    assert errs[3] < 50 * rho ** -80 * np.max(np.abs(ref)) + 1e-12
+
+
+def test_apply_poly_fp32_mode_stays_close():
+    A = laplacian_2d(20, 0.1)
+    V = rng.rademacher(0, 0, A.n, 2)
+    P64 = logdet.apply_poly(A, V, 0.1, 8.1, 39)
+    P32 = logdet.apply_poly(A, V, 0.1, 8.1, 39, f32=True)
+    err = np.max(np.abs(P64 - P32)) / np.max(np.abs(P64))
+    assert 1e-9 < err < 2e-5
+
+
+# --------------------------------------------------------------------------- bounds and sigma
+
+def test_gershgorin_laplacian_closed_form():
+    lo, hi = logdet.gershgorin(laplacian_2d(30, 0.25))
+    assert lo == pytest.approx(0.25, abs=1e-14) and hi == pytest.approx(8.25, rel=1e-15)
+    lo, hi = logdet.gershgorin(laplacian_3d(9, 0.05))
+    assert lo == pytest.approx(0.05, abs=1e-14) and hi == pytest.approx(12.05, rel=1e-15)
+
+
+def test_gershgorin_contains_spectrum():
+    for seed in range(3):
+        A = random_spd(120, seed=seed, dense_row=True)
+        lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+        lo, hi = logdet.gershgorin(A)
+        assert lo <= lam[0] + 1e-12 and lam[-1] <= hi + 1e-12
+    # hand-made 2x2: [[2, -3], [-3, 5]] -> rows give [-1, 5] and [2, 8]
+    lo, hi = logdet.gershgorin(csr_from_dense(np.array([[2.0, -3.0], [-3.0, 5.0]])))
+    assert (lo, hi) == (-1.0, 8.0)
+
+
+def test_power_iteration_bounds_lmax():
+    A = random_spd(200, seed=4)
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    lp = logdet.power_iteration_lmax(A, iters=20, seed=3)
+    assert lp <= lam[-1] * (1 + 1e-12)
+    assert lp >= 0.8 * lam[-1]
+
+
+def test_sigma_rule():
+    assert logdet.sigma_of(0.1) == 0.1
+    assert logdet.sigma_of(2.0) == 1.0
+    with pytest.raises(ValueError):
+        logdet.sigma_of(0.0)
+    with pytest.raises(ValueError):
+        logdet.sigma_of(-1.0)
+
+
+def test_degree_from_bounds():
+    assert logdet.degree_from_bounds(1.0, 9.0) == math.ceil(math.log(1e6) / math.log(2.0))
+    assert logdet.degree_from_bounds(1.0, 1e9) == 250
+    assert logdet.degree_from_bounds(1.0, 1.0 + 1e-9) == 10
+    assert logdet.degree_from_bounds(1.0, 1.5) == 10
+
+
+# ---------------------------------------------------------------------------- Hutch++ (Alg. 3)
+
+def test_hutchpp_with_k_ge_n_is_the_exact_polynomial_trace():
+    """With as many sketch columns as rows, Q spans R^n, the residual part vanishes and the
+    estimate is n log sigma + tr p(A / sigma) = sum_i p(lambda_i) exactly."""
+    A = random_spd(40, seed=5)
+    Ad = A.to_scipy().toarray()
+    lam = np.linalg.eigvalsh(Ad)
+    lmin, lmax = 0.9 * lam[0], 1.1 * lam[-1]
+    m = 30
+    S, G = logdet.make_probes(A.n, 40, seed=2)
+    r = logdet.hutchpp_logdet(A, lmin, lmax, m, S, G)
+    sigma = logdet.sigma_of(lmin)
+    p = pins.interpolant(lmin / sigma, lmax / sigma, leja.fast_leja_points(m + 1))
+    ref = A.n * math.log(sigma) + float(np.sum(p(lam / sigma)))
+    assert r["estimate"] == pytest.approx(ref, rel=1e-11)
+    assert abs(r["trace_res"]) < 1e-10
+
+
+@pytest.mark.parametrize("lscale", [0.02, 3.0])   # sigma < 1 and sigma = 1
+def test_hutchpp_matches_dense_route(lscale):
+    """Algorithm 3 evaluated through a dense F = p(A/sigma) and an SVD-based orthonormal basis
+    (scipy.linalg.orth) instead of the recurrence and Householder QR."""
+    from scipy.linalg import orth
+    A0 = random_spd(90, seed=6)
+    A = csr_from_dense(A0.to_scipy().toarray() * lscale)
+    Ad = A.to_scipy().toarray()
+    lam = np.linalg.eigvalsh(Ad)
+    lmin, lmax = 0.9 * lam[0], 1.1 * lam[-1]
+    m, k = 35, 8
+    S, G = logdet.make_probes(A.n, k, seed=11)
+    r = logdet.hutchpp_logdet(A, lmin, lmax, m, S, G)
+    sigma = logdet.sigma_of(lmin)
+    p = pins.interpolant(lmin / sigma, lmax / sigma, leja.fast_leja_points(m + 1))
+    F = pins.dense_matrix_function(Ad / sigma, p)
+    Q = orth(F @ S)
+    Gp = G - Q @ (Q.T @ G)
+    ref = A.n * math.log(sigma) + np.trace(Q.T @ F @ Q) + np.trace(Gp.T @ F @ Gp) / k
+    assert r["estimate"] == pytest.approx(ref, rel=1e-10)
+
+
+def test_hutchpp_config1_against_closed_form():
+    """2-D Laplacian + 0.1 I on 100 x 100, bounds [0.1, 8.1], 40 Léja points, 30 Rademacher
+    probes from seed 0: the estimate is close to the closed-form log-determinant."""
+    A = laplacian_2d(100, 0.1)
+    exact = pins.logdet_laplacian_2d(100, 0.1)
+    assert exact == pytest.approx(12232.673634578276, rel=1e-14)
+    r = logdet.logdet_leja(A, 0.1, 8.1, 39, 30, 0)
+    assert abs(r["estimate"] - exact) / exact < 5e-3
+
+
+def test_polynomial_bias_config1():
+    """The degree-39 interpolant's exact trace differs from the log-determinant by ~4e-7."""
+    N, shift, m = 100, 0.1, 39
+    mu = pins.lap_eigs_1d(N)
+    lam = (mu[:, None] + mu[None, :] + shift).ravel()
+    sigma = logdet.sigma_of(0.1)
+    p = pins.interpolant(0.1 / sigma, 8.1 / sigma, leja.fast_leja_points(m + 1))
+    tr = N * N * math.log(sigma) + math.fsum(p(lam / sigma))
+    exact = pins.logdet_laplacian_2d(N, shift)
+    assert 1e-8 < abs(tr - exact) / exact < 1e-5
+
+
+def test_matern_closed_form_matches_dense():
+    A = matern_2d(8, 0.3, 1.7)
+    sign, ld = np.linalg.slogdet(A.to_scipy().toarray())
+    assert sign > 0 and ld == pytest.approx(pins.logdet_matern_2d(8, 0.3, 1.7), rel=1e-12)
+    A3 = laplacian_3d(6, 0.05)
+    sign, ld = np.linalg.slogdet(A3.to_scipy().toarray())
+    assert ld == pytest.approx(pins.logdet_laplacian_3d(6, 0.05), rel=1e-12)
+
+
+# ----------------------------------------------------------------------------------- gradients
+
+def _fd_check(A, lmin, lmax, m, k, seed, entries, h=1e-6):
+    S, G = logdet.make_probes(A.n, k, seed)
+    r = logdet.hutchpp_logdet(A, lmin, lmax, m, S, G)
+    g = logdet.hutchpp_grad_values(A, lmin, lmax, m, r["Q"], r["Gp"])
+    for e in entries:
+        vp = A.values.copy(); vp[e] += h
+        vm = A.values.copy(); vm[e] -= h
+        fd = (logdet.frozen_estimate(A, vp, lmin, lmax, m, r["Q"], r["Gp"])
+              - logdet.frozen_estimate(A, vm, lmin, lmax, m, r["Q"], r["Gp"])) / (2 * h)
+        assert g[e] == pytest.approx(fd, rel=2e-5, abs=1e-7)
+    return g
+
+
+def test_grad_values_finite_differences_symmetric():
+    A = random_spd(60, seed=8)
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    _fd_check(A, 0.9 * lam[0], 1.1 * lam[-1], 25, 5, 3, entries=[0, 7, 33, A.nnz // 2, A.nnz - 1])
+
+
+def test_grad_values_finite_differences_nonsymmetric():
+    """The adjoint uses (B - xi I)^T; a non-symmetric matrix catches a transposed operand."""
+    rs = np.random.default_rng(9)
+    n = 30
+    M = np.diag(rs.uniform(4, 6, n)) + (rs.random((n, n)) < 0.15) * rs.uniform(-0.3, 0.5, (n, n))
+    A = csr_from_dense(M)
+    ev = np.linalg.eigvals(M).real
+    _fd_check(A, 0.8 * ev.min(), 1.2 * ev.max(), 20, 4, 4, entries=[1, 5, 17, A.nnz - 3])
+
+
+def test_grad_theta_matches_exact_trace_matern():
+    """With k >= n the frozen estimator is the exact polynomial trace, so
+    sum_e g_e da_e/dtheta = tr(p'(A) dA/dtheta) ~ tr(A^-1 dA/dtheta): n/tau for tau and
+    4 kappa sum 1/(kappa^2 + mu) for kappa."""
+    N, kappa, tau = 6, 0.3, 1.3
+    A = matern_2d(N, kappa, tau)
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    lmin, lmax = 0.95 * lam[0], 1.05 * lam[-1]
+    m = 200
+    S, G = logdet.make_probes(A.n, A.n, seed=1)
+    r = logdet.hutchpp_logdet(A, lmin, lmax, m, S, G)
+    g = logdet.hutchpp_grad_values(A, lmin, lmax, m, r["Q"], r["Gp"])
+    dk, dt = matern_2d_derivatives(N, kappa, tau)
+    ex_k, ex_t = pins.dlogdet_matern_2d(N, kappa, tau)
+    assert float(g @ dt) == pytest.approx(ex_t, rel=1e-5)
+    assert float(g @ dk) == pytest.approx(ex_k, rel=1e-5)
+    # the gradient of a symmetric matrix's estimator is symmetric
+    Gm = __import__("scipy.sparse", fromlist=["csr_matrix"]).csr_matrix((g, A.colind, A.rowptr), shape=(A.n, A.n))
+    assert abs(Gm - Gm.T).max() <= 1e-10 * abs(Gm).max()
