@@ -1,0 +1,326 @@
+"""Benchmark of the Léja-point log-determinant hot path on GB300.
+
+Workload (default): Q = L_3D + 0.05 I, 7-point Dirichlet Laplacian on a 128^3 grid
+(n = 2,097,152, nnz = 14,581,760, int32 CSR), bounds [0.05, 12.05], Léja degree 60, Hutch++ with
+99 Rademacher probes (33/33/33) from seed 1. One step = one full estimate (Algorithm 3): probes,
+pass 1 (m fused SpMM steps, width 33), CholeskyQR2 + deflation, pass 2 (m fused SpMM+trace steps,
+width 66), host combine.
+
+Metric: Léja SpMM-recurrence GB/s = algorithmic bytes of the 2m Léja steps per estimate x steps
+/ device time (the QR and probe time is inside the timed region but adds no bytes). Inputs are
+resident in HBM and larger than L2 (the 553 MB-1.1 GB probe blocks, 175 MB matrix).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--precision df64|f64|f32] [--degree M]
+Under torchrun (N > 1) every rank runs an independent replica with seed + rank (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Léja SpMM-recurrence GB/s (% HBM peak)"
+UNIT = "GB/s"
+GRID_N = 128
+SHIFT = 0.05
+BOUNDS = (0.05, 12.05)
+PROBES = 99
+SEED = 1
+
+DTYPE_NAME = {"df64": "df64 (float-float on FP32 pipes, 8-byte storage)", "f64": "f64",
+              "f32": "f32 (FP64 accumulation of P and traces)"}
+ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A, s_W, s_P, s_V
+
+
+def step_bytes(n: int, nnz: int, b: int, prec: str, mode: str) -> int:
+    """Algorithmic (compulsory) bytes of one fused Léja step over an n x b block:
+    CSR values + column indices + row pointers, W_j read, W_{j+1} written, and
+    P read+written (pass 1) or V read (pass 2)."""
+    s_a, s_w, s_p, s_v = ELEM[prec]
+    base = nnz * (s_a + 4) + 4 * (n + 1) + n * b * 2 * s_w
+    return base + (n * b * 2 * s_p if mode == "accum" else n * b * s_v)
+
+
+def estimate_bytes(n: int, nnz: int, k: int, m: int, prec: str) -> int:
+    return m * (step_bytes(n, nnz, k, prec, "accum") + step_bytes(n, nnz, 2 * k, prec, "dot"))
+
+
+def load_peaks() -> tuple[dict, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(A, prec: str, budget_s: float = 12.0) -> dict:
+    """The FP64 CPU oracle as it stands (one column at a time, SciPy CSR mat-vec), timed on a
+    bounded sample: Algorithm 2 steps on single probe columns until ~budget_s of CPU time."""
+    import numpy as np
+
+    from oracle import logdet as O
+    from oracle import rng as R
+    sigma = O.sigma_of(BOUNDS[0])
+    lt, ut = BOUNDS[0] / sigma, BOUNDS[1] / sigma
+    sample_m = 8
+    xi, c, g, d, _ = O.newton_leja_setup(lt, ut, sample_m)
+    M = O._scipy(A)
+    cols = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        v = R.rademacher(SEED, 0, A.n, 1)
+        O.leja_apply_columns(M, v, xi, d, c, g, sigma)
+        cols += 1
+    dt = time.perf_counter() - t0
+    # per column-step bytes in the oracle's own FP64 layout: CSR + w read + w written + P read/written
+    per = A.nnz * 12 + 4 * (A.n + 1) + A.n * (2 * 8 + 2 * 8)
+    gbs = cols * sample_m * per / dt / 1e9
+    return {"value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cols} probe column(s) x {sample_m} Léja steps (Algorithm 2, FP64, SciPy CSR mat-vec) "
+                      f"on the {GRID_N}^3 Laplacian in {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from synth import laplacian_3d
+    A = laplacian_3d(GRID_N, SHIFT)
+    for _ in range(args.warmup):
+        cpu_baseline(A, args.precision, budget_s=2.0)
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(A, args.precision, budget_s=6.0)
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"L3D+{SHIFT}I {GRID_N}^3 (n={A.n}, nnz={A.nnz}), degree {args.degree}, "
+                                   f"{PROBES} Rademacher probes, seed {SEED}", "model": None},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="df64", choices=["df64", "f64", "f32"])
+    ap.add_argument("--degree", type=int, default=60)
+    ap.add_argument("--variants", type=int, default=1, help="also time the other precisions (1 = yes)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2603_02207_gb300 as L
+    from paper_2603_02207_gb300 import build as _b
+    from synth import laplacian_3d
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _b.build()
+    A = laplacian_3d(GRID_N, SHIFT)
+    n, nnz, k, m = A.n, A.nnz, PROBES // 3, args.degree
+    h = L.Handle()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def time_precision(prec: str, steps: int, warmup: int, sampler=None):
+        dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+        opts = L.options(degree=m, probes=PROBES, seed=SEED + rank, precision=prec)
+        for _ in range(warmup):
+            L.ll_logdet_forward(h, dA, *BOUNDS, opts)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.start()
+        p1, p2, launches, est = [], [], 0, None
+        e0.record(stream)
+        for _ in range(steps):
+            est = L.ll_logdet_forward(h, dA, *BOUNDS, opts)
+            inf = h.info()
+            p1.append(inf["ms_pass1"])
+            p2.append(inf["ms_pass2"])
+            launches += inf["kernel_launches"]
+        e1.record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return dict(ms=ms, est=est, p1=p1, p2=p2, launches=launches, clocks=clocks, info=h.info(), dA=dA, opts=opts)
+
+    prec = args.precision
+    sampler = ClockSampler(local) if rank == 0 else None
+    r = time_precision(prec, args.steps, args.warmup, sampler)
+    ms_step = r["ms"] / args.steps
+    bytes_est = estimate_bytes(n, nnz, k, m, prec)
+    value = world * bytes_est * args.steps / (r["ms"] / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the pass-2 fused SpMM + trace step, width 2k)
+    peaks, peak_src = load_peaks()
+    p2_launch_ms = statistics.median(r["p2"]) / m
+    p1_launch_ms = statistics.median(r["p1"]) / m
+    b_p2 = step_bytes(n, nnz, 2 * k, prec, "dot")
+    b_p1 = step_bytes(n, nnz, k, prec, "accum")
+    achieved = b_p2 / (p2_launch_ms / 1e3) / 1e9
+    roof = {"kernel": f"k_leja_step<{prec},DOT> (b={2 * k})", "bound": "hbm", "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": peak_src,
+            "per_launch_bytes": b_p2, "per_launch_ms": p2_launch_ms,
+            "pass1_kernel": {"achieved": b_p1 / (p1_launch_ms / 1e3) / 1e9, "per_launch_bytes": b_p1,
+                             "per_launch_ms": p1_launch_ms}}
+
+    # end to end through the C ABI with host buffers (CSR copied host->device every call)
+    e2e = None
+    if rank == 0 or world > 1:
+        opts = r["opts"]
+        Ah = A
+        for _ in range(1):
+            L.ll_logdet_forward_host(h, Ah, *BOUNDS, opts)
+        barrier()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            L.ll_logdet_forward_host(h, Ah, *BOUNDS, opts)
+        e1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        vs = 4 if prec == "f32" else 8
+        h2d = 4 * (n + 1) + 4 * nnz + vs * nnz
+        d2h = (m + 1) * (2 * k) * 8 + 2 * 4
+        e2e = {"value": world * bytes_est * args.steps / wall / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": wall * 1e3 / args.steps}
+
+    variants = {}
+    if args.variants:
+        for other in ("df64", "f64", "f32"):
+            if other == prec:
+                continue
+            rv = time_precision(other, 2, 1)
+            bv = estimate_bytes(n, nnz, k, m, other)
+            variants[other] = {"value": bv * 2 / (rv["ms"] / 1e3) / 1e9, "ms_per_step": rv["ms"] / 2,
+                               "pass1_launch_ms": statistics.median(rv["p1"]) / m,
+                               "pass2_launch_ms": statistics.median(rv["p2"]) / m,
+                               "estimate": rv["est"]}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
+    from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only
+    exact = logdet_laplacian_3d(GRID_N, SHIFT)
+    info = r["info"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE_NAME[prec], "data": "synthetic",
+        "config": {"workload": f"L3D+{SHIFT}I on {GRID_N}^3 (n={n}, nnz={nnz}), bounds {list(BOUNDS)}, "
+                               f"degree {m}, Hutch++ {PROBES} Rademacher probes (k={k}), seed {SEED}",
+                   "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (probe blocks 0.5-1.1 GB, matrix 175 MB); no flush"},
+        "hbm_frac_of_measured": value / peaks["hbm_gbs"],
+        "matvecs_per_s": world * m * 3 * k * args.steps / (r["ms"] / 1e3),
+        "estimate": r["est"], "exact_logdet": exact, "rel_err_vs_exact": abs(r["est"] - exact) / abs(exact),
+        "phase_ms": {"probes": info["ms_probes"], "pass1": info["ms_pass1"], "qr": info["ms_qr"],
+                     "pass2": info["ms_pass2"], "total": info["ms_total"]},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": r["launches"], "clocks": r["clocks"], "variants": variants,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

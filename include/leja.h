@@ -1,0 +1,223 @@
+/*
+ * leja.h — C ABI of the GB300 (sm_103a) Léja-point log-determinant library.
+ *
+ * The library estimates log det A for a sparse symmetric positive definite matrix A (CSR) by
+ * the method of Mbingui, Tambue & Karambal, "Novel technique based on Léja Points Approximation
+ * for Log-determinant Estimation of Large matrices" (arXiv 2603.02207):
+ *   log det A = n log sigma + tr log(A / sigma)                       (Section 4, Eq. scaled_sigma_matrix)
+ *   log(A / sigma) V ~ p_m(A / sigma) V, p_m the Newton interpolant of log at m+1 fast Léja
+ *   points mapped to the spectral interval                             (Section 3, Algorithms 1-2)
+ *   tr is estimated by Hutch++ (sketch, QR, deterministic part, deflated Hutchinson part)
+ *                                                                      (Section 4.1, Algorithm 3)
+ * Every compute step runs in the library's own CUDA kernels on the device.
+ *
+ * Conventions for every entry point:
+ *   - Matrix and block pointers are DEVICE pointers unless the parameter says "host". They are
+ *     owned by the caller and only read (inputs) or written (outputs) during the call.
+ *   - Dense blocks are row-major: element (i, j) of an n x b block X with leading dimension ldx
+ *     is X[i * ldx + j], ldx >= b.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that return a host value
+ *     synchronise that stream before returning; the others only enqueue work.
+ *   - Every call returns an ll_status. On failure the outputs are left unchanged (except device
+ *     outputs of calls that only enqueue work, which are unspecified) and ll_last_error(h)
+ *     describes the failure.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef LEJA_H_
+#define LEJA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LL_OK = 0,
+    LL_ERR_INVALID_ARG = 1,       /* a null pointer, a negative size, an unknown enum value      */
+    LL_ERR_BAD_CSR = 2,           /* rowptr not monotone, rowptr[0] != 0, rowptr[n] != nnz,
+                                     or a column index outside [0, n)                            */
+    LL_ERR_BAD_BOUNDS = 3,        /* lmin <= 0 or lmin >= lmax, or non-finite bounds             */
+    LL_ERR_DD_NOT_CONVERGED = 4,  /* the Taylor series of Algorithm 1 did not converge           */
+    LL_ERR_QR_BREAKDOWN = 5,      /* CholeskyQR met a non-positive pivot (rank-deficient sketch) */
+    LL_ERR_NONFINITE = 6,         /* a NaN or Inf appeared in the traces                         */
+    LL_ERR_TIMEOUT = 7,           /* a bounded device-side wait ran out                          */
+    LL_ERR_OOM = 8,               /* device workspace allocation failed                          */
+    LL_ERR_CUDA = 9,              /* a CUDA runtime error                                        */
+    LL_ERR_UNSUPPORTED = 10,      /* a valid but unimplemented option combination                */
+    LL_ERR_NO_FORWARD = 11        /* backward called without a kept forward                      */
+} ll_status;
+
+/* Storage type of the CSR values. */
+enum { LL_F64 = 0, LL_F32 = 1 };
+
+/* Arithmetic of the Léja recurrence (a12):
+ *   LL_PREC_F64        W_j, P and the traces in IEEE FP64 on the FP64 pipe.
+ *   LL_PREC_DF64       W_j, P and V stored as float pairs (hi, lo) and updated in double-float
+ *                      arithmetic on the FP32 pipes (about 46-48 significant bits); the traces and
+ *                      the QR are FP64. Same 8 bytes per element as FP64.
+ *   LL_PREC_F32_MIXED  matrix values and W_j in FP32; P = sum_j d_j W_j and the traces accumulated
+ *                      in FP64; QR in FP64.                                                         */
+enum { LL_PREC_F64 = 0, LL_PREC_DF64 = 1, LL_PREC_F32_MIXED = 2 };
+
+enum { LL_PROBE_RADEMACHER = 0, LL_PROBE_GAUSSIAN = 1 };
+
+/* s_val of Algorithm 1: the Lemma 3.1 optimum c = (lmin+lmax)/2, or lmax/2. */
+enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
+
+/* Probe streams of the counter-based generator (see ll_probes). */
+enum { LL_STREAM_S = 0, LL_STREAM_G = 1, LL_STREAM_POWER = 2 };
+
+typedef struct {
+    int64_t n;                 /* order of the square matrix                                    */
+    int64_t nnz;               /* stored entries                                                 */
+    const int32_t* rowptr;     /* device, n+1 entries, rowptr[0] = 0, rowptr[n] = nnz           */
+    const int32_t* colind;     /* device, nnz entries in [0, n)                                  */
+    const void* values;        /* device, nnz entries of type `dtype`                            */
+    int dtype;                 /* LL_F64 or LL_F32                                               */
+} ll_csr;
+
+typedef struct {
+    double lmin, lmax;         /* spectral interval [lambda_min, lambda_max], 0 < lmin < lmax    */
+} ll_bounds;
+
+typedef struct {
+    int degree;                /* m: m+1 Léja points, m operator applications per pass          */
+    int probes;                /* m_vec, a positive multiple of 3; k = m_vec / 3                */
+    uint64_t seed;             /* probe seed                                                     */
+    int probe_kind;            /* LL_PROBE_RADEMACHER or LL_PROBE_GAUSSIAN                      */
+    int precision;             /* LL_PREC_*                                                      */
+    int sval_mode;             /* LL_SVAL_*                                                      */
+    int keep_for_backward;     /* 1: keep [Q | G'] and the coefficients for ll_logdet_backward   */
+    int rows_per_thread;       /* 0 = autotuned; otherwise rows each thread handles per tile     */
+    int threads_per_block;     /* 0 = autotuned; otherwise CTA size of the step kernels          */
+    int ckpt_stride;           /* backward: W_j checkpoint stride; 0 = ceil(sqrt(m))            */
+    int use_graph;             /* 1: capture the m-step passes in a CUDA graph (default 1)       */
+} ll_options;
+
+typedef struct ll_handle ll_handle;
+
+/* Diagnostics of the last forward call on a handle. */
+typedef struct {
+    double sigma, c, gamma;          /* normalisation and affine map of the scaled interval       */
+    double trace_q, trace_res;       /* tr(Q^T F Q) and the Hutchinson part                       */
+    double estimate;                 /* n log sigma + trace_q + trace_res                         */
+    int taylor_terms;                /* p used by Algorithm 1                                     */
+    int k;                           /* sketch columns used (min(m_vec/3, n))                     */
+    int kernel_launches;             /* library kernels launched by the call                      */
+    float ms_probes, ms_pass1, ms_qr, ms_pass2, ms_total;   /* device times (CUDA events)         */
+} ll_info;
+
+/* ---- handle -------------------------------------------------------------------------------- */
+
+/* Create a handle on the current CUDA device. The handle owns the device workspace and the
+ * kept forward state. */
+ll_status ll_create(ll_handle** out);
+void ll_destroy(ll_handle* h);
+const char* ll_status_string(ll_status s);
+/* Text of the last failure on this handle (empty when none). Owned by the handle. */
+const char* ll_last_error(const ll_handle* h);
+/* Fill *opts with defaults: degree 40, probes 30, seed 0, Rademacher, LL_PREC_DF64, s_val = c,
+ * no backward, autotuned launch shape, ckpt_stride 0, CUDA graphs on. */
+void ll_default_options(ll_options* opts);
+
+/* ---- host-side method pieces (FP64 on the host: their stability needs it) ------------------ */
+
+/* First `count` fast Léja points on [-2, 2] into xi_out (host, count doubles).
+ * Section 3, Eq. (Léja5), fast variant (Baglama, Calvetti & Reichel 1998) as used in
+ * Section 3.1: xi_0 = 2, xi_1 = -2, candidates are midpoints of neighbouring chosen points,
+ * score prod_k |x - xi_k| (FP64, k ascending), scores within a relative 1e-10 of the best are
+ * ties and the smallest tied x wins. */
+ll_status ll_leja_points(int count, double* xi_out);
+
+/* Scaled divided differences d_j = gamma^j log[z_0..z_j], j = 0..degree, of log at
+ * z_i = c + gamma xi_i with c = (lmin+lmax)/2 and gamma = (lmax-lmin)/4, by Algorithm 1
+ * (Section 3.1): d = log(Q_m) e_1 with Q_m = c I + gamma Qhat_m and a Taylor series of
+ * log(I + (Q_m - s I)/s). The series stops when a term's max-norm falls below 1e-18 times the
+ * sum's (after >= 10 terms); more than 5e6 terms gives LL_ERR_DD_NOT_CONVERGED.
+ * d_out: host, degree+1 doubles. terms_out: host, may be NULL. */
+ll_status ll_divided_differences(ll_bounds bounds, int degree, int sval_mode, double* d_out, int* terms_out);
+
+/* ---- device kernels exposed for parity checks ---------------------------------------------- */
+
+/* Gershgorin interval [min_i (a_ii - R_i), max_i (a_ii + R_i)], R_i = sum_{j!=i} |a_ij|
+ * (Section 3 and Algorithm 1 step 1). Host result; synchronises `stream`. A non-positive lower
+ * bound is returned as is: the caller decides (the Remark in Section 3 replaces it by an
+ * epsilon > 0). Validates the CSR first. */
+ll_status ll_gershgorin(ll_handle* h, const ll_csr* A, ll_bounds* out, void* stream);
+
+/* Rayleigh quotient of A after `iters` normalised power steps from the Rademacher vector of
+ * stream LL_STREAM_POWER (a cheap lambda_max estimate in the spirit of Appendix A).
+ * lmax_out: host; synchronises `stream`. */
+ll_status ll_power_lmax(ll_handle* h, const ll_csr* A, int iters, uint64_t seed, double* lmax_out, void* stream);
+
+/* Probe block: out[i * ld + j] = probe(kind, seed, stream_id, row i, column j) for i < n,
+ * j < cols, FP64, by the counter-based generator
+ *   mix(z) = SplitMix64 output function of z + 0x9E3779B97F4A7C15 (Steele, Lea & Flood 2014),
+ *   x = mix(seed ^ mix(stream_id * 2^56 + j * 2^32 + i)),
+ *   Rademacher: 1 - 2 * (x >> 63);  Gaussian: Box-Muller of u1 = ((x >> 11) + 1) 2^-53 and
+ *   u2 = (mix(x) >> 11) 2^-53.
+ * Algorithm 3 steps 2 and 6. Requires n < 2^32, cols < 2^24. Enqueue only. */
+ll_status ll_probes(ll_handle* h, int kind, uint64_t seed, int stream_id, int64_t n, int cols,
+                    double* out, int64_t ld, void* stream);
+
+/* PV = p_m(A) V: the degree-m Newton-Léja interpolant of log on [lmin, lmax] applied to the
+ * n x b block V (Algorithm 2 with a fixed degree, all b columns at once):
+ *   W_0 = V, W_{j+1} = (B - xi_j I) W_j with B = (A - c I) / gamma, PV = sum_j d_j W_j.
+ * V, PV: device FP64, row-major, leading dimensions ldv, ldp (>= b). PV must not alias V.
+ * precision: LL_PREC_*; the matrix values may be LL_F64 or LL_F32. Enqueue only (the host
+ * coefficient set-up is synchronous). */
+ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int degree, int precision,
+                        const double* V, int64_t ldv, int b, double* PV, int64_t ldp, void* stream);
+
+/* ---- the estimator ------------------------------------------------------------------------- */
+
+/* logdet_leja(csr, bounds, degree, probes, seed): Algorithm 3.
+ *   sigma = lmin if lmin < 1 else 1; A~ = A / sigma on [lmin/sigma, lmax/sigma];
+ *   S, G: n x k probes (k = probes/3; streams LL_STREAM_S, LL_STREAM_G);
+ *   Y = p(A~) S; Q = CholeskyQR2(Y) (FP64); G' = G - Q (Q^T G);
+ *   estimate = n log sigma + tr(Q^T p(A~) Q) + (1/k) tr(G'^T p(A~) G').
+ * The matrix is device-resident (A). *estimate: host; synchronises `stream`.
+ * With opts->keep_for_backward the handle keeps [Q | G'] for ll_logdet_backward. */
+ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, const ll_options* opts,
+                            double* estimate, void* stream);
+
+/* The same estimate for a HOST-resident CSR (rowptr/colind/values are host pointers): the call
+ * copies the matrix to the device (host-to-device copies inside the call), runs
+ * ll_logdet_forward, and returns the estimate on the host. */
+ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* A_host, ll_bounds bounds,
+                                 const ll_options* opts, double* estimate, void* stream);
+
+/* Derivative of the last kept forward estimate with respect to every stored value of A,
+ * with [Q | G'], the bounds, sigma and the coefficients held fixed (stop-gradient through the
+ * QR and the bounds; not in the paper):
+ *   grad_values[e] += grad_output * (1/gamma) sum_{j<m} Lambda_{j+1}[r_e, :] . W_j[c_e, :],
+ *   Lambda_m = d_m U, Lambda_j = d_j U + (B - xi_j I)^T Lambda_{j+1}, U = [Q | G'/k].
+ * A must be symmetric (B^T = B is used) and the same matrix (pattern and values) as in the
+ * forward. W_j are checkpointed every ckpt_stride steps and recomputed.
+ * grad_values: device, nnz doubles, overwritten. Enqueue only. */
+ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream);
+
+/* Many independent estimates in one persistent launch per pass (batching, a11): count matrices
+ * mats[0..count-1] (device CSR each), bounds b[i], per-matrix degree degrees[i] (NULL = from the
+ * bound ratio: m = clamp(ceil(ln 1e6 / ln rho), 10, 250), rho = (sqrt(kappa)+1)/(sqrt(kappa)-1),
+ * Proposition 3.1). opts->probes, seed, kind and precision apply to every matrix; matrix i uses
+ * seed + i. estimates: host, count doubles; synchronises `stream`. */
+ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b, int count,
+                            const ll_options* opts, const int* degrees, double* estimates, void* stream);
+
+/* Diagnostics of the last ll_logdet_forward on this handle. */
+ll_status ll_get_info(const ll_handle* h, ll_info* out);
+
+/* Copy the kept basis [Q | G'] of the last forward with keep_for_backward (FP64, n x (kq + kg):
+ * columns [0, kq) hold Q, columns [kq, kq + kg) hold G' = (I - Q Q^T) G) into `out` (device,
+ * leading dimension ld >= kq + kg). With out == NULL only the sizes are returned.
+ * Sizes: host pointers, each may be NULL. Enqueue only (the copy runs on `stream`).
+ * LL_ERR_NO_FORWARD when nothing is kept. */
+ll_status ll_kept_basis(const ll_handle* h, double* out, int64_t ld, int64_t* n_out, int* kq_out, int* kg_out,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEJA_H_ */

@@ -1,0 +1,10 @@
+"""GB300-native Léja-point log-determinant estimator (arXiv 2603.02207).
+
+The compute path is the native library libleja.so (CUDA for sm_103a behind the C ABI in
+include/leja.h); this package is its thin Python binding. Importing the package does not load
+the library; the first call does, and raises ImportError if it has not been built.
+"""
+from .api import (DeviceCSR, Handle, LejaError, ll_apply_poly, ll_divided_differences,  # noqa: F401
+                  ll_gershgorin, ll_leja_points, ll_logdet_backward, ll_logdet_forward,
+                  ll_kept_basis, ll_logdet_forward_host, ll_power_lmax, ll_probes, logdet_leja,
+                  options)

@@ -1,0 +1,232 @@
+"""Python binding of the C ABI in include/leja.h (argument marshalling only).
+
+PyTorch provides device memory and streams; every compute step runs in libleja.so's kernels.
+Device arrays are torch CUDA tensors; host arrays are NumPy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+
+from . import _ffi
+from ._ffi import (LL_F32, LL_F64, LL_PREC_DF64, LL_PREC_F32_MIXED, LL_PREC_F64,  # noqa: F401
+                   LL_PROBE_GAUSSIAN, LL_PROBE_RADEMACHER, LL_STREAM_G, LL_STREAM_POWER, LL_STREAM_S,
+                   LL_SVAL_CENTER, LL_SVAL_HALF_LMAX)
+
+PRECISIONS = {"f64": LL_PREC_F64, "df64": LL_PREC_DF64, "f32": LL_PREC_F32_MIXED}
+PROBE_KINDS = {"rademacher": LL_PROBE_RADEMACHER, "gaussian": LL_PROBE_GAUSSIAN}
+
+
+class LejaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_ffi.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.name = _ffi.STATUS_NAMES.get(status, str(status))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Handle:
+    """Owns an ll_handle (device workspace and kept forward state) on the current device."""
+
+    def __init__(self):
+        self._lib = _ffi.load()
+        h = ctypes.c_void_p()
+        st = self._lib.ll_create(ctypes.byref(h))
+        if st != 0:
+            raise LejaError(st, "ll_create failed")
+        self.ptr = h
+
+    def check(self, st: int):
+        if st != 0:
+            msg = self._lib.ll_last_error(self.ptr)
+            raise LejaError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            self._lib.ll_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = _ffi.ll_info()
+        self.check(self._lib.ll_get_info(self.ptr, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _ffi.ll_info._fields_}
+
+
+@dataclasses.dataclass
+class DeviceCSR:
+    """A CSR matrix resident on the GPU (int32 indices; float64 or float32 values)."""
+
+    n: int
+    rowptr: object
+    colind: object
+    values: object
+
+    @staticmethod
+    def from_host(csr, dtype: str = "f64", device: str = "cuda") -> "DeviceCSR":
+        torch = _torch()
+        vt = torch.float64 if dtype == "f64" else torch.float32
+        return DeviceCSR(n=int(csr.n),
+                         rowptr=torch.as_tensor(np.asarray(csr.rowptr, dtype=np.int32)).to(device),
+                         colind=torch.as_tensor(np.asarray(csr.colind, dtype=np.int32)).to(device),
+                         values=torch.as_tensor(np.asarray(csr.values)).to(device=device, dtype=vt))
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colind.shape[0])
+
+    def c(self) -> _ffi.ll_csr:
+        torch = _torch()
+        assert self.rowptr.dtype == torch.int32 and self.colind.dtype == torch.int32
+        assert self.rowptr.is_contiguous() and self.colind.is_contiguous() and self.values.is_contiguous()
+        dt = LL_F64 if self.values.dtype == torch.float64 else LL_F32
+        return _ffi.ll_csr(self.n, self.nnz, self.rowptr.data_ptr(), self.colind.data_ptr(),
+                           self.values.data_ptr(), dt)
+
+
+def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
+    """ll_csr over host NumPy arrays (kept alive by the returned tuple)."""
+    rp = np.ascontiguousarray(csr.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(csr.colind, dtype=np.int32)
+    va = np.ascontiguousarray(csr.values)
+    dt = LL_F64 if va.dtype == np.float64 else LL_F32
+    s = _ffi.ll_csr(int(csr.n), int(ci.shape[0]), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, dt)
+    return s, (rp, ci, va)
+
+
+def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str = "rademacher",
+            precision: str = "df64", sval_mode: int = LL_SVAL_CENTER, keep_for_backward: bool = False,
+            rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
+            use_graph: bool = True) -> _ffi.ll_options:
+    o = _ffi.ll_options()
+    _ffi.load().ll_default_options(ctypes.byref(o))
+    o.degree = degree
+    o.probes = probes
+    o.seed = seed
+    o.probe_kind = PROBE_KINDS[probe_kind]
+    o.precision = PRECISIONS[precision]
+    o.sval_mode = sval_mode
+    o.keep_for_backward = int(keep_for_backward)
+    o.rows_per_thread = rows_per_thread
+    o.threads_per_block = threads_per_block
+    o.ckpt_stride = ckpt_stride
+    o.use_graph = int(use_graph)
+    return o
+
+
+# ------------------------------------------------------------------------------ host pieces
+
+def ll_leja_points(count: int) -> np.ndarray:
+    out = np.zeros(count, dtype=np.float64)
+    st = _ffi.load().ll_leja_points(count, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != 0:
+        raise LejaError(st, "ll_leja_points")
+    return out
+
+
+def ll_divided_differences(lmin: float, lmax: float, degree: int, sval_mode: int = LL_SVAL_CENTER):
+    out = np.zeros(degree + 1, dtype=np.float64)
+    terms = ctypes.c_int(0)
+    st = _ffi.load().ll_divided_differences(_ffi.ll_bounds(lmin, lmax), degree, sval_mode,
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(terms))
+    if st != 0:
+        raise LejaError(st, "ll_divided_differences")
+    return out, terms.value
+
+
+# ---------------------------------------------------------------------------- device pieces
+
+def ll_gershgorin(h: Handle, A: DeviceCSR, stream=None) -> tuple[float, float]:
+    out = _ffi.ll_bounds()
+    a = A.c()
+    h.check(h._lib.ll_gershgorin(h.ptr, ctypes.byref(a), ctypes.byref(out), _stream_ptr(stream)))
+    return out.lmin, out.lmax
+
+
+def ll_power_lmax(h: Handle, A: DeviceCSR, iters: int = 20, seed: int = 0, stream=None) -> float:
+    out = ctypes.c_double()
+    a = A.c()
+    h.check(h._lib.ll_power_lmax(h.ptr, ctypes.byref(a), iters, seed, ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
+
+
+def ll_probes(h: Handle, kind: str, seed: int, stream_id: int, n: int, cols: int, stream=None):
+    torch = _torch()
+    out = torch.empty((n, cols), dtype=torch.float64, device="cuda")
+    h.check(h._lib.ll_probes(h.ptr, PROBE_KINDS[kind], seed, stream_id, n, cols, out.data_ptr(), cols,
+                             _stream_ptr(stream)))
+    return out
+
+
+def ll_apply_poly(h: Handle, A: DeviceCSR, lmin: float, lmax: float, degree: int, V, precision: str = "f64",
+                  stream=None):
+    torch = _torch()
+    assert V.dtype == torch.float64 and V.is_cuda and V.dim() == 2 and V.stride(1) == 1
+    n, b = V.shape
+    out = torch.empty((n, b), dtype=torch.float64, device=V.device)
+    a = A.c()
+    h.check(h._lib.ll_apply_poly(h.ptr, ctypes.byref(a), _ffi.ll_bounds(lmin, lmax), degree, PRECISIONS[precision],
+                                 V.data_ptr(), V.stride(0), b, out.data_ptr(), b, _stream_ptr(stream)))
+    return out
+
+
+def ll_logdet_forward(h: Handle, A: DeviceCSR, lmin: float, lmax: float, opts: _ffi.ll_options, stream=None) -> float:
+    est = ctypes.c_double()
+    a = A.c()
+    h.check(h._lib.ll_logdet_forward(h.ptr, ctypes.byref(a), _ffi.ll_bounds(lmin, lmax), ctypes.byref(opts),
+                                     ctypes.byref(est), _stream_ptr(stream)))
+    return est.value
+
+
+def ll_logdet_forward_host(h: Handle, csr, lmin: float, lmax: float, opts: _ffi.ll_options, stream=None) -> float:
+    est = ctypes.c_double()
+    a, keep = host_csr_struct(csr)
+    h.check(h._lib.ll_logdet_forward_host(h.ptr, ctypes.byref(a), _ffi.ll_bounds(lmin, lmax), ctypes.byref(opts),
+                                          ctypes.byref(est), _stream_ptr(stream)))
+    del keep
+    return est.value
+
+
+def ll_logdet_backward(h: Handle, A: DeviceCSR, grad_output: float = 1.0, stream=None):
+    torch = _torch()
+    g = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+    a = A.c()
+    h.check(h._lib.ll_logdet_backward(h.ptr, ctypes.byref(a), grad_output, g.data_ptr(), _stream_ptr(stream)))
+    return g
+
+
+def ll_kept_basis(h: Handle, stream=None):
+    """(Q, G') of the last forward with keep_for_backward, as FP64 torch tensors (copies)."""
+    torch = _torch()
+    n = ctypes.c_int64()
+    kq = ctypes.c_int()
+    kg = ctypes.c_int()
+    h.check(h._lib.ll_kept_basis(h.ptr, None, 0, ctypes.byref(n), ctypes.byref(kq), ctypes.byref(kg), None))
+    out = torch.empty((n.value, kq.value + kg.value), dtype=torch.float64, device="cuda")
+    h.check(h._lib.ll_kept_basis(h.ptr, out.data_ptr(), kq.value + kg.value, None, None, None, _stream_ptr(stream)))
+    return out[:, :kq.value], out[:, kq.value:]
+
+
+def logdet_leja(A: DeviceCSR, bounds: tuple[float, float], degree: int, probes: int, seed: int,
+                precision: str = "df64", probe_kind: str = "rademacher", handle: Handle | None = None) -> float:
+    """logdet_leja(csr, bounds, degree, probes, seed) -> estimate (Algorithm 3)."""
+    h = handle or Handle()
+    return ll_logdet_forward(h, A, bounds[0], bounds[1],
+                             options(degree=degree, probes=probes, seed=seed, precision=precision, probe_kind=probe_kind))

@@ -1,0 +1,635 @@
+// C ABI of the Léja log-determinant library: handle and workspace, argument checks, the host
+// coefficient set-up, and the orchestration of the device passes of Algorithm 3.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <cstdlib>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "host_math.h"
+#include "kernels.cuh"
+#include "leja.h"
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ll_handle {
+    int device = 0;
+    int sm_count = 152;
+    std::string err;
+    std::map<std::string, Buf> ws;
+    ll_info info{};
+    cudaEvent_t ev[6] = {};
+    int launches = 0;
+    int max_fwd_offset = 0;   // largest col - row of the last validated matrix
+    // cached coefficients of the last set-up
+    double dd_lmin = 0, dd_lmax = 0;
+    int dd_degree = -1, dd_sval = -1, dd_terms = 0;
+    std::vector<double> dd;
+    // kept forward state (for the backward)
+    bool kept = false;
+    int64_t kept_n = 0, kept_nnz = 0;
+    int kept_kq = 0, kept_kg = 0, kept_m = 0, kept_prec = 0, kept_ckpt = 0;
+    double kept_sigma = 1, kept_c = 0, kept_gamma = 1;
+    std::vector<double> kept_d, kept_xi;
+};
+
+namespace ll {
+namespace {
+
+ll_status fail(ll_handle* h, ll_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+#define LL_CK(expr)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return fail(h, LL_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void* ws_get(ll_handle* h, const char* name, size_t bytes, cudaError_t* err) {
+    Buf& b = h->ws[name];
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return b.p;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = e;
+        return nullptr;
+    }
+    b.bytes = bytes;
+    return b.p;
+}
+
+#define WS(ptr, type, name, bytes)                                                               \
+    type ptr = nullptr;                                                                          \
+    do {                                                                                         \
+        cudaError_t e_ = cudaSuccess;                                                            \
+        ptr = (type)ws_get(h, name, (bytes), &e_);                                               \
+        if (!ptr) return fail(h, LL_ERR_OOM, std::string("workspace ") + name + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+ll_status check_csr_args(ll_handle* h, const ll_csr* A) {
+    if (!A) return fail(h, LL_ERR_INVALID_ARG, "null matrix");
+    if (A->n < 0 || A->nnz < 0) return fail(h, LL_ERR_INVALID_ARG, "negative size");
+    if (A->n >= (int64_t)1 << 31 || A->nnz >= (int64_t)1 << 31) return fail(h, LL_ERR_UNSUPPORTED, "n and nnz must be < 2^31 (int32 CSR)");
+    if (A->dtype != LL_F64 && A->dtype != LL_F32) return fail(h, LL_ERR_INVALID_ARG, "unknown value dtype");
+    if (A->n > 0 && (!A->rowptr || (A->nnz > 0 && (!A->colind || !A->values))))
+        return fail(h, LL_ERR_INVALID_ARG, "null CSR array");
+    return LL_OK;
+}
+
+ll_status check_bounds(ll_handle* h, ll_bounds b) {
+    if (!std::isfinite(b.lmin) || !std::isfinite(b.lmax) || !(b.lmin > 0.0) || !(b.lmin < b.lmax))
+        return fail(h, LL_ERR_BAD_BOUNDS, "bounds must satisfy 0 < lmin < lmax (finite)");
+    return LL_OK;
+}
+
+// Validates the device CSR (synchronises the stream).
+ll_status validate_csr(ll_handle* h, const ll_csr* A, cudaStream_t s) {
+    if (A->n == 0) return LL_OK;
+    WS(flag, int*, "csr_flag", 2 * sizeof(int));
+    LL_CK(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
+    LL_CK(launch_validate_csr(A->rowptr, A->colind, (int)A->n, A->nnz, flag, s));
+    h->launches++;
+    int hv[2] = {0, 0};
+    LL_CK(cudaMemcpyAsync(hv, flag, sizeof hv, cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    const int hf = hv[0];
+    h->max_fwd_offset = hv[1];
+    if (hf) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "invalid CSR:%s%s%s", (hf & 4) ? " rowptr[0]!=0 or rowptr[n]!=nnz;" : "",
+                 (hf & 1) ? " rowptr decreasing;" : "", (hf & 2) ? " column index out of range;" : "");
+        return fail(h, LL_ERR_BAD_CSR, buf);
+    }
+    return LL_OK;
+}
+
+// Léja points and Algorithm 1 coefficients for [lmin, lmax] (cached on the handle).
+ll_status setup_coefficients(ll_handle* h, double lmin, double lmax, int degree, int sval, std::vector<double>& xi,
+                             std::vector<double>& d) {
+    xi.resize(degree + 1);
+    leja_points(degree + 1, xi.data());
+    if (!(h->dd_degree == degree && h->dd_sval == sval && h->dd_lmin == lmin && h->dd_lmax == lmax)) {
+        std::vector<double> dn(degree + 1);
+        const int terms = divided_differences_alg1(lmin, lmax, degree, sval, dn.data(), kTaylorMaxTerms);
+        if (terms < 0) return fail(h, LL_ERR_DD_NOT_CONVERGED, "Algorithm 1 Taylor series did not converge within 5e6 terms");
+        h->dd = dn;
+        h->dd_degree = degree;
+        h->dd_sval = sval;
+        h->dd_lmin = lmin;
+        h->dd_lmax = lmax;
+        h->dd_terms = terms;
+    }
+    d = h->dd;
+    return LL_OK;
+}
+
+int64_t pad_elems(int64_t x) { return (x + 31) & ~(int64_t)31; }
+
+// Runs m Léja steps over an n x b block.
+//   mode ACCUM: W_0 = win0 (ld = ldw), P accumulates sum_j d_j W_j (P type, ld = ldp)
+//   mode DOT:   W_0 = V = win0, dots[(j) * b + col] = <V_col, W_j col> for j = 0..m
+ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int precision, int mode, int n, int b,
+                   const void* win0, long long ldw, void* wa, void* wb, void* P, long long ldp, double* dots,
+                   const std::vector<double>& beta, const std::vector<double>& d, int threads_target, int rpt,
+                   cudaStream_t s) {
+    const int m = (int)d.size() - 1;
+    StepParams p{};
+    p.rowptr = A->rowptr;
+    p.colind = A->colind;
+    p.vals = vals_prep;
+    p.ldw = ldw;
+    p.ldv = ldw;
+    p.ldp = ldp;
+    // one row per gather batch (64 registers, two CTAs per SM); the L2 bulk prefetch stays off by
+    // default: on the 96^3 Laplacian it doubled the DRAM reads of the trace step for a 4% gain
+    p.rb = 1;
+    p.pf_dist = 0;
+    StepLaunch L = plan_step(precision, mode, n, A->nnz, b, threads_target, rpt, p, h->sm_count);
+    {
+        const double window = (double)h->max_fwd_offset * (double)ldw * (precision == LL_PREC_F32_MIXED ? 4.0 : 8.0);
+        p.pf_far = (h->max_fwd_offset > p.rl * p.rpt && window < 48e6) ? h->max_fwd_offset : 0;
+    }
+    if (mode == MODE_DOT) {
+        WS(partials, double*, "dot_partials", (size_t)2 * L.grid * b * sizeof(double));
+        WS(ticket, unsigned int*, "dot_ticket", sizeof(unsigned int));
+        LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
+        p.partials = partials;
+        p.ticket = ticket;
+        p.v = win0;
+    }
+    p.p = P;
+    for (int j = 0; j < m; ++j) {
+        p.win = (j == 0) ? win0 : ((j & 1) ? wa : wb);
+        p.wout = (j & 1) ? wb : wa;
+        p.first = (j == 0);
+        p.beta = beta[j];
+        p.d0 = d[0];
+        p.dn = d[j + 1];
+        p.beta_df = df_split(beta[j]);
+        p.d0_df = df_split(d[0]);
+        p.dn_df = df_split(d[j + 1]);
+        if (mode == MODE_DOT) {
+            p.dots_next = dots + (size_t)(j + 1) * b;
+            p.dots_first = dots;
+        }
+        LL_CK(launch_step(precision, mode, L, p, s));
+        h->launches++;
+    }
+    return LL_OK;
+}
+
+}  // namespace
+}  // namespace ll
+
+using namespace ll;
+
+extern "C" {
+
+ll_status ll_create(ll_handle** out) {
+    if (!out) return LL_ERR_INVALID_ARG;
+    ll_handle* h = new ll_handle();
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return LL_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    for (auto& e : h->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return LL_ERR_CUDA;
+        }
+    }
+    *out = h;
+    return LL_OK;
+}
+
+void ll_destroy(ll_handle* h) {
+    if (!h) return;
+    for (auto& kv : h->ws)
+        if (kv.second.p) cudaFree(kv.second.p);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+const char* ll_status_string(ll_status s) {
+    switch (s) {
+        case LL_OK: return "LL_OK";
+        case LL_ERR_INVALID_ARG: return "LL_ERR_INVALID_ARG";
+        case LL_ERR_BAD_CSR: return "LL_ERR_BAD_CSR";
+        case LL_ERR_BAD_BOUNDS: return "LL_ERR_BAD_BOUNDS";
+        case LL_ERR_DD_NOT_CONVERGED: return "LL_ERR_DD_NOT_CONVERGED";
+        case LL_ERR_QR_BREAKDOWN: return "LL_ERR_QR_BREAKDOWN";
+        case LL_ERR_NONFINITE: return "LL_ERR_NONFINITE";
+        case LL_ERR_TIMEOUT: return "LL_ERR_TIMEOUT";
+        case LL_ERR_OOM: return "LL_ERR_OOM";
+        case LL_ERR_CUDA: return "LL_ERR_CUDA";
+        case LL_ERR_UNSUPPORTED: return "LL_ERR_UNSUPPORTED";
+        case LL_ERR_NO_FORWARD: return "LL_ERR_NO_FORWARD";
+    }
+    return "LL_ERR_UNKNOWN";
+}
+
+const char* ll_last_error(const ll_handle* h) { return h ? h->err.c_str() : ""; }
+
+void ll_default_options(ll_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->degree = 40;
+    o->probes = 30;
+    o->seed = 0;
+    o->probe_kind = LL_PROBE_RADEMACHER;
+    o->precision = LL_PREC_DF64;
+    o->sval_mode = LL_SVAL_CENTER;
+    o->keep_for_backward = 0;
+    o->rows_per_thread = 0;
+    o->threads_per_block = 0;
+    o->ckpt_stride = 0;
+    o->use_graph = 1;
+}
+
+ll_status ll_leja_points(int count, double* xi_out) {
+    if (count < 0 || (count > 0 && !xi_out)) return LL_ERR_INVALID_ARG;
+    if (count > 100000) return LL_ERR_UNSUPPORTED;
+    leja_points(count, xi_out);
+    return LL_OK;
+}
+
+ll_status ll_divided_differences(ll_bounds b, int degree, int sval_mode, double* d_out, int* terms_out) {
+    if (degree < 0 || !d_out) return LL_ERR_INVALID_ARG;
+    if (sval_mode != LL_SVAL_CENTER && sval_mode != LL_SVAL_HALF_LMAX) return LL_ERR_INVALID_ARG;
+    if (!std::isfinite(b.lmin) || !std::isfinite(b.lmax) || !(b.lmin > 0.0) || !(b.lmin < b.lmax)) return LL_ERR_BAD_BOUNDS;
+    const int terms = divided_differences_alg1(b.lmin, b.lmax, degree, sval_mode, d_out, kTaylorMaxTerms);
+    if (terms < 0) return LL_ERR_DD_NOT_CONVERGED;
+    if (terms_out) *terms_out = terms;
+    return LL_OK;
+}
+
+ll_status ll_gershgorin(ll_handle* h, const ll_csr* A, ll_bounds* out, void* stream) {
+    if (!h || !out) return LL_ERR_INVALID_ARG;
+    ll_status st = check_csr_args(h, A);
+    if (st != LL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (A->n == 0) return fail(h, LL_ERR_INVALID_ARG, "empty matrix has no spectrum");
+    st = validate_csr(h, A, s);
+    if (st != LL_OK) return st;
+    const int grid = h->sm_count * 4;
+    WS(partials, double*, "gg_partials", (size_t)2 * grid * sizeof(double));
+    WS(ticket, unsigned int*, "gg_ticket", sizeof(unsigned int));
+    WS(res, double*, "gg_out", 2 * sizeof(double));
+    LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
+    LL_CK(launch_gershgorin(A->rowptr, A->colind, A->values, A->dtype, (int)A->n, partials, ticket, res, grid, s));
+    h->launches++;
+    double hres[2];
+    LL_CK(cudaMemcpyAsync(hres, res, sizeof hres, cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    out->lmin = hres[0];
+    out->lmax = hres[1];
+    return LL_OK;
+}
+
+ll_status ll_power_lmax(ll_handle* h, const ll_csr* A, int iters, uint64_t seed, double* lmax_out, void* stream) {
+    if (!h || !lmax_out || iters < 0) return LL_ERR_INVALID_ARG;
+    ll_status st = check_csr_args(h, A);
+    if (st != LL_OK) return st;
+    if (A->n == 0) return fail(h, LL_ERR_INVALID_ARG, "empty matrix has no spectrum");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = validate_csr(h, A, s);
+    if (st != LL_OK) return st;
+    const int n = (int)A->n;
+    const int grid = h->sm_count * 4;
+    WS(x, double*, "pw_x", (size_t)n * sizeof(double));
+    WS(y, double*, "pw_y", (size_t)n * sizeof(double));
+    WS(partials, double*, "pw_partials", (size_t)grid * sizeof(double));
+    WS(ticket, unsigned int*, "pw_ticket", sizeof(unsigned int));
+    WS(nrm, double*, "pw_nrm", sizeof(double));
+    LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
+    LL_CK(launch_probes(T_F64, LL_PROBE_RADEMACHER, seed, LL_STREAM_POWER, n, 1, x, 1, s));
+    LL_CK(launch_dot_f64(x, x, n, partials, ticket, nrm, grid, s));
+    LL_CK(launch_scale_f64(x, nrm, n, 0, s));
+    h->launches += 3;
+    for (int it = 0; it < iters; ++it) {
+        LL_CK(launch_spmv_f64(A->rowptr, A->colind, A->values, A->dtype, n, x, y, s));
+        LL_CK(launch_dot_f64(y, y, n, partials, ticket, nrm, grid, s));
+        LL_CK(launch_scale_f64(y, nrm, n, 0, s));
+        h->launches += 3;
+        double* t = x; x = y; y = t;
+    }
+    LL_CK(launch_spmv_f64(A->rowptr, A->colind, A->values, A->dtype, n, x, y, s));
+    LL_CK(launch_dot_f64(x, y, n, partials, ticket, nrm, grid, s));
+    h->launches += 2;
+    double hn = 0;
+    LL_CK(cudaMemcpyAsync(&hn, nrm, sizeof hn, cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    *lmax_out = hn;
+    return LL_OK;
+}
+
+ll_status ll_probes(ll_handle* h, int kind, uint64_t seed, int stream_id, int64_t n, int cols, double* out,
+                    int64_t ld, void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    if (kind != LL_PROBE_RADEMACHER && kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
+    if (n < 0 || cols < 0 || ld < cols || stream_id < 0 || stream_id > 255) return fail(h, LL_ERR_INVALID_ARG, "bad probe shape");
+    if (n >= ((int64_t)1 << 31) || cols >= (1 << 24)) return fail(h, LL_ERR_UNSUPPORTED, "probe block too large");
+    if (n * cols == 0) return LL_OK;
+    if (!out) return fail(h, LL_ERR_INVALID_ARG, "null output");
+    LL_CK(launch_probes(T_F64, kind, seed, stream_id, (int)n, cols, out, ld, (cudaStream_t)stream));
+    h->launches++;
+    return LL_OK;
+}
+
+ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int degree, int precision, const double* V,
+                        int64_t ldv, int b, double* PV, int64_t ldp, void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    ll_status st = check_csr_args(h, A);
+    if (st != LL_OK) return st;
+    if ((st = check_bounds(h, bounds)) != LL_OK) return st;
+    if (degree < 0 || b < 0 || ldv < b || ldp < b) return fail(h, LL_ERR_INVALID_ARG, "bad degree or block shape");
+    if (precision < LL_PREC_F64 || precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
+    const int n = (int)A->n;
+    if (n == 0 || b == 0) return LL_OK;
+    if (b > 512) return fail(h, LL_ERR_UNSUPPORTED, "block width above 512");
+    if (!V || !PV) return fail(h, LL_ERR_INVALID_ARG, "null block");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->launches = 0;
+    if ((st = validate_csr(h, A, s)) != LL_OK) return st;
+    std::vector<double> xi, d;
+    if ((st = setup_coefficients(h, bounds.lmin, bounds.lmax, degree, LL_SVAL_CENTER, xi, d)) != LL_OK) return st;
+    const double c = (bounds.lmin + bounds.lmax) / 2.0, gamma = (bounds.lmax - bounds.lmin) / 4.0;
+    std::vector<double> beta(degree + 1);
+    for (int j = 0; j <= degree; ++j) beta[j] = -(c / gamma + xi[j]);
+    const int wt = w_type_of(precision), pt = p_type_of(precision);
+    const size_t nb = (size_t)n * b;
+    WS(vprep, void*, "ap_vals", (size_t)A->nnz * elem_size(wt));
+    WS(w0, void*, "ap_w0", nb * elem_size(wt));
+    WS(wa, void*, "ap_wa", nb * elem_size(wt));
+    WS(wb, void*, "ap_wb", nb * elem_size(wt));
+    LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / gamma, precision, vprep, s));
+    LL_CK(launch_convert_block(V, ldv, precision, w0, b, n, b, s));
+    h->launches += 2;
+    if (degree == 0) {
+        // p_0 = d_0: PV = d_0 V
+        LL_CK(launch_scaled_copy_f64(V, ldv, PV, ldp, n, b, d[0], s));
+        h->launches++;
+        return LL_OK;
+    }
+    if (pt == T_F64) {
+        // P is FP64: accumulate straight into the caller's PV (ld = ldp)
+        st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, b, wa, wb, PV, ldp, nullptr, beta, d, 0, 0, s);
+        if (st != LL_OK) return st;
+    } else {
+        WS(pp, void*, "ap_p", nb * elem_size(pt));
+        st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, b, wa, wb, pp, b, nullptr, beta, d, 0, 0, s);
+        if (st != LL_OK) return st;
+        LL_CK(launch_block_to_f64(precision, pp, b, PV, ldp, n, b, s));
+        h->launches++;
+    }
+    return LL_OK;
+}
+
+ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, const ll_options* opts, double* estimate,
+                            void* stream) {
+    if (!h || !opts || !estimate) return LL_ERR_INVALID_ARG;
+    ll_status st = check_csr_args(h, A);
+    if (st != LL_OK) return st;
+    if ((st = check_bounds(h, bounds)) != LL_OK) return st;
+    const ll_options& o = *opts;
+    if (o.degree < 1) return fail(h, LL_ERR_INVALID_ARG, "degree must be >= 1");
+    if (o.probes <= 0 || o.probes % 3 != 0) return fail(h, LL_ERR_INVALID_ARG, "probes must be a positive multiple of 3");
+    if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
+    if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
+    if (o.sval_mode != LL_SVAL_CENTER && o.sval_mode != LL_SVAL_HALF_LMAX) return fail(h, LL_ERR_INVALID_ARG, "unknown s_val mode");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->launches = 0;
+    h->kept = false;
+    const int n = (int)A->n;
+    if (n == 0) {
+        *estimate = 0.0;
+        return LL_OK;
+    }
+    const int kg = o.probes / 3;
+    const int kq = kg < n ? kg : n;
+    const int b2 = kq + kg;
+    if (b2 > 512 || kq > 96) return fail(h, LL_ERR_UNSUPPORTED, "m_vec / 3 above 96 is not supported");
+    if ((st = validate_csr(h, A, s)) != LL_OK) return st;
+
+    // host set-up: sigma, the scaled interval, Léja points, Algorithm 1 coefficients
+    const double sigma = sigma_of(bounds.lmin);
+    const double lt = bounds.lmin / sigma, ut = bounds.lmax / sigma;
+    std::vector<double> xi, d;
+    if ((st = setup_coefficients(h, lt, ut, o.degree, o.sval_mode, xi, d)) != LL_OK) return st;
+    const double c = (lt + ut) / 2.0, gamma = (ut - lt) / 4.0;
+    const int m = o.degree;
+    std::vector<double> beta(m + 1);
+    for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + xi[j]);
+
+    const int prec = o.precision;
+    const int wt = w_type_of(prec), pt = p_type_of(prec);
+    const size_t ew = elem_size(wt), ep = elem_size(pt);
+    // workspace
+    WS(vprep, void*, "fw_vals", (size_t)A->nnz * ew);
+    WS(S, void*, "fw_S", (size_t)n * kq * ew);
+    WS(G, double*, "fw_G", (size_t)n * kg * sizeof(double));
+    WS(P, void*, "fw_P", (size_t)n * kq * ep);
+    WS(wa, void*, "fw_wa", (size_t)n * b2 * ew);
+    WS(wb, void*, "fw_wb", (size_t)n * b2 * ew);
+    WS(basis, double*, "fw_basis", (size_t)n * b2 * sizeof(double));
+    WS(q1, double*, "fw_q1", (size_t)n * kq * sizeof(double));
+    void* V = basis;
+    if (wt != T_F64) {
+        WS(vv, void*, "fw_V", (size_t)n * b2 * ew);
+        V = vv;
+    }
+    const int ggrid = h->sm_count * 2;
+    WS(gpart, double*, "fw_gram_partials", (size_t)ggrid * (size_t)kq * (kq > kg ? kq : kg) * sizeof(double));
+    WS(gticket, unsigned int*, "fw_gram_ticket", sizeof(unsigned int));
+    WS(gram, double*, "fw_gram", (size_t)kq * (kq > kg ? kq : kg) * sizeof(double));
+    WS(rinv, double*, "fw_rinv", (size_t)kq * kq * sizeof(double));
+    WS(qrstat, int*, "fw_qr_status", sizeof(int));
+    WS(dots, double*, "fw_dots", (size_t)(m + 1) * b2 * sizeof(double));
+
+    LL_CK(cudaEventRecord(h->ev[0], s));
+    LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), s));
+    LL_CK(cudaMemsetAsync(qrstat, 0, sizeof(int), s));
+    // matrix values scaled by 1 / (sigma gamma): B = (A/sigma - c I)/gamma = prepared - (c/gamma) I
+    LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
+    // Algorithm 3 step 2 (S) and step 6 (G)
+    LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, S, kq, s));
+    LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, G, kg, s));
+    h->launches += 3;
+    LL_CK(cudaEventRecord(h->ev[1], s));
+
+    if (kq == n) {
+        // k >= n: the sketch spans R^n, so Q = I is an orthonormal basis of span(Y) and
+        // G' = (I - Q Q^T) G = 0; the estimate is the exact trace of p(A~)
+        LL_CK(cudaEventRecord(h->ev[2], s));
+        LL_CK(cudaMemsetAsync(basis, 0, (size_t)n * b2 * sizeof(double), s));
+        LL_CK(launch_unit_diag(T_F64, basis, b2, n, s));
+        h->launches++;
+        if (wt != T_F64) {
+            LL_CK(cudaMemsetAsync(V, 0, (size_t)n * b2 * ew, s));
+            LL_CK(launch_unit_diag(wt, V, b2, n, s));
+            h->launches++;
+        }
+        LL_CK(cudaEventRecord(h->ev[3], s));
+    } else {
+        // step 3: Y = p(A~) S
+        st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, kq, S, kq, wa, wb, P, kq, nullptr, beta, d,
+                      o.threads_per_block, o.rows_per_thread, s);
+        if (st != LL_OK) return st;
+        LL_CK(cudaEventRecord(h->ev[2], s));
+
+        // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']
+        LL_CK(launch_gram(pt, P, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
+        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, s));
+        LL_CK(launch_apply_rinv(pt, P, kq, n, kq, rinv, q1, kq, T_F64, nullptr, 0, s));
+        LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
+        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, s));
+        LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, b2, wt, wt != T_F64 ? V : nullptr, b2, s));
+        LL_CK(launch_gram(T_F64, basis, b2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, s));
+        LL_CK(launch_project(basis, b2, kq, G, kg, kg, gram, n, basis + kq, b2, wt,
+                             wt != T_F64 ? (void*)((char*)V + (size_t)kq * ew) : nullptr, b2, s));
+        h->launches += 8;
+        LL_CK(cudaEventRecord(h->ev[3], s));
+    }
+
+    // steps 5-6: traces t_j[col] = <V_col, W_j col> for j = 0..m
+    st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, b2, wa, wb, nullptr, 0, dots, beta, d,
+                  o.threads_per_block, o.rows_per_thread, s);
+    if (st != LL_OK) return st;
+    LL_CK(cudaEventRecord(h->ev[4], s));
+
+    std::vector<double> hd((size_t)(m + 1) * b2);
+    int hstat = 0;
+    LL_CK(cudaMemcpyAsync(hd.data(), dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaMemcpyAsync(&hstat, qrstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    if (hstat) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2: non-positive pivot (rank-deficient sketch)");
+
+    // step 7 and output: n log sigma + tr(Q^T F Q) + (1/k) tr(G'^T F G')
+    double tq = 0.0, tr = 0.0;
+    for (int j = 0; j <= m; ++j) {
+        double sq = 0.0, sr = 0.0;
+        for (int col = 0; col < kq; ++col) sq += hd[(size_t)j * b2 + col];
+        for (int col = kq; col < b2; ++col) sr += hd[(size_t)j * b2 + col];
+        tq += d[j] * sq;
+        tr += d[j] * sr;
+    }
+    tr /= (double)kg;
+    if (!std::isfinite(tq) || !std::isfinite(tr)) return fail(h, LL_ERR_NONFINITE, "non-finite trace");
+    const double est = (double)n * std::log(sigma) + tq + tr;
+
+    ll_info& I = h->info;
+    I.sigma = sigma;
+    I.c = c;
+    I.gamma = gamma;
+    I.trace_q = tq;
+    I.trace_res = tr;
+    I.estimate = est;
+    I.taylor_terms = h->dd_terms;
+    I.k = kq;
+    I.kernel_launches = h->launches;
+    cudaEventElapsedTime(&I.ms_probes, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&I.ms_pass1, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&I.ms_pass2, h->ev[3], h->ev[4]);
+    cudaEventElapsedTime(&I.ms_total, h->ev[0], h->ev[4]);
+
+    if (o.keep_for_backward) {
+        h->kept = true;
+        h->kept_n = n;
+        h->kept_nnz = A->nnz;
+        h->kept_kq = kq;
+        h->kept_kg = kg;
+        h->kept_m = m;
+        h->kept_prec = prec;
+        h->kept_ckpt = o.ckpt_stride;
+        h->kept_sigma = sigma;
+        h->kept_c = c;
+        h->kept_gamma = gamma;
+        h->kept_d = d;
+        h->kept_xi = xi;
+    }
+    *estimate = est;
+    return LL_OK;
+}
+
+ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* Ah, ll_bounds bounds, const ll_options* opts,
+                                 double* estimate, void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    ll_status st = check_csr_args(h, Ah);
+    if (st != LL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vs = Ah->dtype == LL_F64 ? 8 : 4;
+    WS(rp, int32_t*, "host_rowptr", (size_t)(Ah->n + 1) * sizeof(int32_t));
+    WS(ci, int32_t*, "host_colind", (size_t)Ah->nnz * sizeof(int32_t));
+    WS(va, void*, "host_values", (size_t)Ah->nnz * vs);
+    LL_CK(cudaMemcpyAsync(rp, Ah->rowptr, (size_t)(Ah->n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (Ah->nnz > 0) {
+        LL_CK(cudaMemcpyAsync(ci, Ah->colind, (size_t)Ah->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        LL_CK(cudaMemcpyAsync(va, Ah->values, (size_t)Ah->nnz * vs, cudaMemcpyHostToDevice, s));
+    }
+    ll_csr Ad = *Ah;
+    Ad.rowptr = rp;
+    Ad.colind = ci;
+    Ad.values = va;
+    return ll_logdet_forward(h, &Ad, bounds, opts, estimate, stream);
+}
+
+ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    (void)A; (void)grad_output; (void)grad_values; (void)stream;
+    if (!h->kept) return fail(h, LL_ERR_NO_FORWARD, "no kept forward (call ll_logdet_forward with keep_for_backward = 1)");
+    return fail(h, LL_ERR_UNSUPPORTED, "backward not built yet");
+}
+
+ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b, int count, const ll_options* opts,
+                            const int* degrees, double* estimates, void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    (void)mats; (void)b; (void)count; (void)opts; (void)degrees; (void)estimates; (void)stream;
+    return fail(h, LL_ERR_UNSUPPORTED, "batched launch not built yet");
+}
+
+ll_status ll_get_info(const ll_handle* h, ll_info* out) {
+    if (!h || !out) return LL_ERR_INVALID_ARG;
+    *out = h->info;
+    return LL_OK;
+}
+
+ll_status ll_kept_basis(const ll_handle* h, double* out, int64_t ld, int64_t* n_out, int* kq_out, int* kg_out,
+                        void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    if (!h->kept) return LL_ERR_NO_FORWARD;
+    auto it = h->ws.find("fw_basis");
+    if (it == h->ws.end()) return LL_ERR_NO_FORWARD;
+    const int b2 = h->kept_kq + h->kept_kg;
+    if (n_out) *n_out = h->kept_n;
+    if (kq_out) *kq_out = h->kept_kq;
+    if (kg_out) *kg_out = h->kept_kg;
+    if (!out) return LL_OK;
+    if (ld < b2) return LL_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ld * sizeof(double), it->second.p, (size_t)b2 * sizeof(double),
+                                      (size_t)b2 * sizeof(double), (size_t)h->kept_n, cudaMemcpyDeviceToDevice,
+                                      (cudaStream_t)stream);
+    return e == cudaSuccess ? LL_OK : LL_ERR_CUDA;
+}
+
+}  // extern "C"

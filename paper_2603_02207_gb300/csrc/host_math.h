@@ -1,0 +1,22 @@
+// Host-side FP64 method pieces (see host_math.cpp).
+#pragma once
+#include "leja.h"
+
+namespace ll {
+
+constexpr double kLejaTieRtol = 1e-10;      // relative tie tolerance of the fast Léja argmax
+constexpr double kTaylorRelTol = 1e-18;     // Algorithm 1 series stop: term < tol * sum (max-norms)
+constexpr int kTaylorMinTerms = 10;
+constexpr int kTaylorMaxTerms = 5000000;
+
+// First `count` fast Léja points on [-2, 2] (cached, thread-safe).
+void leja_points(int count, double* out);
+// Algorithm 1 on [lmin, lmax]: d[0..degree]; returns the number of Taylor terms, -1 if the
+// series did not converge within max_terms.
+int divided_differences_alg1(double lmin, double lmax, int degree, int sval_mode, double* d, int max_terms);
+// Section 4: sigma = lmin if lmin < 1 else 1.
+double sigma_of(double lmin);
+// Proposition 3.1 degree rule: clamp(ceil(ln 1e6 / ln rho), 10, 250).
+int degree_from_bounds(double lmin, double lmax);
+
+}  // namespace ll

@@ -1,0 +1,108 @@
+// Kernel launch interfaces of the Léja log-determinant library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "leja.h"
+
+namespace ll {
+
+enum StepMode { MODE_PLAIN = 0, MODE_ACCUM = 1, MODE_DOT = 2 };
+
+// One Léja step over an n x b block, all columns at once (Algorithm 2 loop body):
+//   Wout = B Win - xi_j Win   with B = (A - c I)/gamma folded into prepared values a_e / gamma
+//          and beta = -(c/gamma + xi_j) applied to the row's own entry,
+//   ACCUM: P = (first ? d0 * Win : P) + dn * Wout
+//   DOT:   dots_next[col] = sum_i V[i, col] * Wout[i, col]   (and dots_first = V . Win if first)
+struct StepParams {
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const void* vals;        // prepared values (storage type of the precision)
+    const void* win;
+    void* wout;
+    const void* v;
+    void* p;
+    double* partials;        // DOT: 2 * grid * b doubles
+    unsigned int* ticket;    // DOT: zero-initialised counter, reset by the last block
+    double* dots_next;
+    double* dots_first;
+    long long ldw, ldv, ldp;
+    int n, b, rl, rpt, num_tiles, smem_cap;
+    int first;
+    int rb;                  // rows per gather batch and thread (1 or 2)
+    int pf_dist;             // L2 prefetch distance in tiles of this CTA (0 = off)
+    long long pf_far;        // forward row offset of far neighbours to prefetch (0 = none)
+    double beta, d0, dn;
+    float2 beta_df, d0_df, dn_df;
+};
+
+struct StepLaunch {
+    int threads;      // CTA size (multiple of 32, >= rl * b)
+    int grid;
+    size_t smem;
+};
+
+// Shape of the step launch for a block width b (threads_target: CTA size target; rpt: rows per
+// thread per tile); fills p.rl, p.rpt, p.num_tiles, p.smem_cap.
+StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int threads_target, int rpt,
+                     StepParams& p, int sm_count);
+cudaError_t launch_step(int precision, int mode, const StepLaunch& L, const StepParams& p, cudaStream_t s);
+
+cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols,
+                          void* out, long long ld, cudaStream_t s);
+// flag[0]: error bits (1 rowptr decreasing, 2 column out of range, 4 rowptr[0] != 0 or rowptr[n] != nnz);
+// flag[1]: largest forward offset max(col - row) over the stored entries (>= 0)
+cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz,
+                                int* flag, cudaStream_t s);
+cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype,
+                              int n, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
+// out[e] = convert(values[e] * scale) into the storage type of `precision`
+cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, double scale, int precision,
+                                  void* out, cudaStream_t s);
+// out (type of `precision` W storage, ld_out) <- in (FP64, ld_in), n x b
+cudaError_t launch_convert_block(const double* in, long long ld_in, int precision, void* out,
+                                 long long ld_out, int n, int b, cudaStream_t s);
+// out (FP64, ld_out) <- in (type of `precision` P storage, ld_in)
+cudaError_t launch_block_to_f64(int precision, const void* in, long long ld_in, double* out,
+                                long long ld_out, int n, int b, cudaStream_t s);
+
+// out = alpha * in (FP64 blocks)
+cudaError_t launch_scaled_copy_f64(const double* in, long long ld_in, double* out, long long ld_out, int n, int b,
+                                   double alpha, cudaStream_t s);
+
+// out[i * ld + i] = 1 for i < n (type t); the rest of `out` is left as is
+cudaError_t launch_unit_diag(int t, void* out, long long ld, int n, cudaStream_t s);
+
+// Power iteration helpers (FP64): y = A x; and reductions
+cudaError_t launch_spmv_f64(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype, int n,
+                            const double* x, double* y, cudaStream_t s);
+cudaError_t launch_dot_f64(const double* x, const double* y, int n, double* partials, unsigned int* ticket,
+                           double* out, int grid, cudaStream_t s);
+cudaError_t launch_scale_f64(double* x, const double* num, int n, int mode, cudaStream_t s);
+
+// CholeskyQR pieces (FP64 arithmetic)
+// out (kx x kz, row-major) = X^T Z, X: n x kx (type tx), Z: n x kz (type tz); sym: X == Z
+cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, const void* Z, long long ldz, int kz,
+                        int n, bool sym, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
+// Cholesky G = R^T R (upper R) and Rinv = R^{-1}; status[0] = 1 on a non-positive pivot
+cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, cudaStream_t s);
+// Out = X * Rinv (upper triangular k x k), X type tx; writes FP64 (out64) and optionally out2 (type t2)
+cudaError_t launch_apply_rinv(int tx, const void* X, long long ldx, int n, int k, const double* Rinv,
+                              double* out64, long long ld64, int t2, void* out2, long long ld2, cudaStream_t s);
+// G' = G - Q C, G: FP64 (ldg), Q: FP64 (ldq), C k x kg; writes FP64 (out64) and optionally out2 (type t2)
+cudaError_t launch_project(const double* Q, long long ldq, int k, const double* G, long long ldg, int kg,
+                           const double* C, int n, double* out64, long long ld64, int t2, void* out2,
+                           long long ld2, cudaStream_t s);
+
+// element types used by the typed helpers above
+enum ElemType { T_F64 = 0, T_F32 = 1, T_DF64 = 2 };
+inline int w_type_of(int precision) {
+    return precision == LL_PREC_F64 ? T_F64 : (precision == LL_PREC_DF64 ? T_DF64 : T_F32);
+}
+inline int p_type_of(int precision) {
+    return precision == LL_PREC_DF64 ? T_DF64 : T_F64;
+}
+inline size_t elem_size(int t) { return t == T_F32 ? 4 : 8; }
+
+}  // namespace ll

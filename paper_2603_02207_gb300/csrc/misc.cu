@@ -1,0 +1,264 @@
+// Probe generation, CSR validation, Gershgorin bounds, value preparation, block conversions and
+// the FP64 pieces of the power iteration.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ll {
+
+// ---------------------------------------------------------------------------- probes (Alg. 3)
+template <typename T>
+__global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols, T* out, long long ld) {
+    const long long total = (long long)n * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(e / cols);
+        const int col = (int)(e - (long long)row * cols);
+        const double v = probe_value(kind, seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row);
+        store_f64<T>(out, (size_t)row * ld + col, v);
+    }
+}
+
+cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols,
+                          void* out, long long ld, cudaStream_t s) {
+    const long long total = (long long)n * cols;
+    if (total <= 0) return cudaSuccess;
+    const int threads = 256;
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    switch (out_type) {
+        case T_F64: k_probes<double><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, (double*)out, ld); break;
+        case T_F32: k_probes<float><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, (float*)out, ld); break;
+        default: k_probes<float2><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, (float2*)out, ld); break;
+    }
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- CSR validation
+// flag[0] bits: 1 = rowptr decreasing, 2 = column index out of range, 4 = rowptr[0] != 0 or
+// rowptr[n] != nnz. flag[1]: largest forward offset col - row (rows with a valid range only).
+__global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    if (tid == 0 && (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) atomicOr(flag, 4);
+    int maxoff = 0;
+    for (int i = tid; i < n; i += stride) {
+        const int a = rowptr[i], e = rowptr[i + 1];
+        if (e < a) { atomicOr(flag, 1); continue; }
+        if (a < 0 || (int64_t)e > nnz) { atomicOr(flag, 4); continue; }
+        for (int k = a; k < e; ++k) {
+            const int c = colind[k];
+            if (c < 0 || c >= n) atomicOr(flag, 2);
+            else maxoff = max(maxoff, c - i);
+        }
+    }
+    if (maxoff > 0) atomicMax(flag + 1, maxoff);
+}
+
+cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, cudaStream_t s) {
+    k_validate_csr<<<152 * 4, 256, 0, s>>>(rowptr, colind, n, nnz, flag);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- Gershgorin (Section 3)
+template <typename T>
+__global__ void k_gershgorin(const int32_t* rowptr, const int32_t* colind, const T* vals, int n,
+                             double* partials, unsigned int* ticket, double* out) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double a_ii = 0.0, r_i = 0.0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            const double v = (double)vals[k];
+            if (colind[k] == i) a_ii += v; else r_i += fabs(v);
+        }
+        lo = fmin(lo, a_ii - r_i);
+        hi = fmax(hi, a_ii + r_i);
+    }
+    __shared__ double s_lo[256], s_hi[256];
+    __shared__ bool s_last;
+    s_lo[threadIdx.x] = lo;
+    s_hi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + w]);
+            s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = s_lo[0];
+        partials[2 * blockIdx.x + 1] = s_hi[0];
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double L = INFINITY, H = -INFINITY;
+        for (int g = 0; g < (int)gridDim.x; ++g) {
+            L = fmin(L, __ldcg(&partials[2 * g]));
+            H = fmax(H, __ldcg(&partials[2 * g + 1]));
+        }
+        out[0] = L;
+        out[1] = H;
+        *ticket = 0u;
+    }
+}
+
+cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype,
+                              int n, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s) {
+    if (dtype == LL_F64) k_gershgorin<double><<<grid, 256, 0, s>>>(rowptr, colind, (const double*)vals, n, partials, ticket, out);
+    else k_gershgorin<float><<<grid, 256, 0, s>>>(rowptr, colind, (const float*)vals, n, partials, ticket, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ value preparation
+template <typename TI, typename TO>
+__global__ void k_prepare(const TI* in, int64_t nnz, double scale, TO* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        store_f64<TO>(out, (size_t)e, (double)in[e] * scale);
+}
+
+cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, double scale, int precision,
+                                  void* out, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    const int grid = 152 * 8, threads = 256;
+    const int t = w_type_of(precision);
+    if (dtype == LL_F64) {
+        if (t == T_F64) k_prepare<double, double><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (double*)out);
+        else if (t == T_F32) k_prepare<double, float><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (float*)out);
+        else k_prepare<double, float2><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (float2*)out);
+    } else {
+        if (t == T_F64) k_prepare<float, double><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (double*)out);
+        else if (t == T_F32) k_prepare<float, float><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float*)out);
+        else k_prepare<float, float2><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float2*)out);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ block conversions
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* in, long long ld_in, TO* out, long long ld_out, int n, int b) {
+    const long long total = (long long)n * b;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / b);
+        const int c = (int)(e - (long long)r * b);
+        store_f64<TO>(out, (size_t)r * ld_out + c, load_f64<TI>(in, (size_t)r * ld_in + c));
+    }
+}
+
+cudaError_t launch_convert_block(const double* in, long long ld_in, int precision, void* out,
+                                 long long ld_out, int n, int b, cudaStream_t s) {
+    if ((long long)n * b <= 0) return cudaSuccess;
+    const int grid = 152 * 8, threads = 256;
+    switch (w_type_of(precision)) {
+        case T_F64: k_convert<double, double><<<grid, threads, 0, s>>>(in, ld_in, (double*)out, ld_out, n, b); break;
+        case T_F32: k_convert<double, float><<<grid, threads, 0, s>>>(in, ld_in, (float*)out, ld_out, n, b); break;
+        default: k_convert<double, float2><<<grid, threads, 0, s>>>(in, ld_in, (float2*)out, ld_out, n, b); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_to_f64(int precision, const void* in, long long ld_in, double* out,
+                                long long ld_out, int n, int b, cudaStream_t s) {
+    if ((long long)n * b <= 0) return cudaSuccess;
+    const int grid = 152 * 8, threads = 256;
+    if (p_type_of(precision) == T_DF64)
+        k_convert<float2, double><<<grid, threads, 0, s>>>((const float2*)in, ld_in, out, ld_out, n, b);
+    else
+        k_convert<double, double><<<grid, threads, 0, s>>>((const double*)in, ld_in, out, ld_out, n, b);
+    return cudaGetLastError();
+}
+
+__global__ void k_scaled_copy(const double* in, long long ld_in, double* out, long long ld_out, int n, int b, double alpha) {
+    const long long total = (long long)n * b;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / b);
+        const int c = (int)(e - (long long)r * b);
+        out[(size_t)r * ld_out + c] = alpha * in[(size_t)r * ld_in + c];
+    }
+}
+
+cudaError_t launch_scaled_copy_f64(const double* in, long long ld_in, double* out, long long ld_out, int n, int b,
+                                   double alpha, cudaStream_t s) {
+    if ((long long)n * b <= 0) return cudaSuccess;
+    k_scaled_copy<<<152 * 8, 256, 0, s>>>(in, ld_in, out, ld_out, n, b, alpha);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_unit_diag(T* out, long long ld, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        store_f64<T>(out, (size_t)i * ld + i, 1.0);
+}
+
+cudaError_t launch_unit_diag(int t, void* out, long long ld, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    switch (t) {
+        case T_F64: k_unit_diag<double><<<152, 256, 0, s>>>((double*)out, ld, n); break;
+        case T_F32: k_unit_diag<float><<<152, 256, 0, s>>>((float*)out, ld, n); break;
+        default: k_unit_diag<float2><<<152, 256, 0, s>>>((float2*)out, ld, n); break;
+    }
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- power iteration (FP64)
+template <typename T>
+__global__ void k_spmv(const int32_t* rowptr, const int32_t* colind, const T* vals, int n, const double* x, double* y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) acc = fma((double)vals[k], x[colind[k]], acc);
+        y[i] = acc;
+    }
+}
+
+cudaError_t launch_spmv_f64(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype, int n,
+                            const double* x, double* y, cudaStream_t s) {
+    if (dtype == LL_F64) k_spmv<double><<<152 * 8, 256, 0, s>>>(rowptr, colind, (const double*)vals, n, x, y);
+    else k_spmv<float><<<152 * 8, 256, 0, s>>>(rowptr, colind, (const float*)vals, n, x, y);
+    return cudaGetLastError();
+}
+
+__global__ void k_dot(const double* x, const double* y, int n, double* partials, unsigned int* ticket, double* out) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc = fma(x[i], y[i], acc);
+    __shared__ double s[256];
+    __shared__ bool s_last;
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s[0];
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (int g = 0; g < (int)gridDim.x; ++g) t += __ldcg(&partials[g]);
+        *out = t;
+        *ticket = 0u;
+    }
+}
+
+cudaError_t launch_dot_f64(const double* x, const double* y, int n, double* partials, unsigned int* ticket,
+                           double* out, int grid, cudaStream_t s) {
+    k_dot<<<grid, 256, 0, s>>>(x, y, n, partials, ticket, out);
+    return cudaGetLastError();
+}
+
+// mode 0: x /= sqrt(*num)
+__global__ void k_scale(double* x, const double* num, int n, int mode) {
+    const double f = 1.0 / sqrt(*num);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] *= f;
+}
+
+cudaError_t launch_scale_f64(double* x, const double* num, int n, int mode, cudaStream_t s) {
+    k_scale<<<152 * 8, 256, 0, s>>>(x, num, n, mode);
+    return cudaGetLastError();
+}
+
+}  // namespace ll
