@@ -151,6 +151,24 @@ ll_status ll_gershgorin(ll_handle* h, const ll_csr* A, ll_bounds* out, void* str
  * lmax_out: host; synchronises `stream`. */
 ll_status ll_power_lmax(ll_handle* h, const ll_csr* A, int iters, uint64_t seed, double* lmax_out, void* stream);
 
+/* Largest matrix order accepted by ll_power_lmax_noalloc. */
+#define LL_NOALLOC_MAX_ROWS (1 << 18)
+
+/* The same estimate as ll_power_lmax (identical kernels and reduction order, so identical
+ * results), for callers that cannot allocate device memory: code running inside an application
+ * whose device memory belongs to another allocator (a framework's caching pool or a fixed arena
+ * that forbids raw cudaMalloc), or latency-sensitive code that cannot accept the implicit device
+ * synchronisation of cudaMalloc/cudaFree. No handle is needed and nothing is allocated: the
+ * working vectors and reduction scratch live in one device array of about 4.2 MB that the library
+ * reserves on every GPU that loads it, until the process exits. The paper has no counterpart.
+ *   - A: device CSR with at most LL_NOALLOC_MAX_ROWS (262,144) rows; larger -> LL_ERR_UNSUPPORTED.
+ *   - lmax_out: host; the call synchronises `stream`.
+ *   - The first call on a device looks up the array's address with that device current; make
+ *     that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (the call clears what must
+ *     start at zero). Calls that overlap on the GPU race with each other: serialise them. */
+ll_status ll_power_lmax_noalloc(const ll_csr* A, int iters, uint64_t seed, double* lmax_out, void* stream);
+
 /* Probe block: out[i * ld + j] = probe(kind, seed, stream_id, row i, column j) for i < n,
  * j < cols, FP64, by the counter-based generator
  *   mix(z) = SplitMix64 output function of z + 0x9E3779B97F4A7C15 (Steele, Lea & Flood 2014),

@@ -23,6 +23,7 @@ LL_PREC_F64, LL_PREC_DF64, LL_PREC_F32_MIXED = 0, 1, 2
 LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
+LL_NOALLOC_MAX_ROWS = 1 << 18
 
 
 class ll_csr(ctypes.Structure):
@@ -67,6 +68,7 @@ SIGNATURES = {
     "ll_divided_differences": (_I, [ll_bounds, _I, _I, _PD, ctypes.POINTER(_I)]),
     "ll_gershgorin": (_I, [_P, ctypes.POINTER(ll_csr), ctypes.POINTER(ll_bounds), _P]),
     "ll_power_lmax": (_I, [_P, ctypes.POINTER(ll_csr), _I, _U64, _PD, _P]),
+    "ll_power_lmax_noalloc": (_I, [ctypes.POINTER(ll_csr), _I, _U64, _PD, _P]),
     "ll_probes": (_I, [_P, _I, _U64, _I, _I64, _I, _P, _I64, _P]),
     "ll_apply_poly": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, _I, _I, _P, _I64, _I, _P, _I64, _P]),
     "ll_logdet_forward": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, ctypes.POINTER(ll_options), _PD, _P]),

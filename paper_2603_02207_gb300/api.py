@@ -167,6 +167,19 @@ def ll_power_lmax(h: Handle, A: DeviceCSR, iters: int = 20, seed: int = 0, strea
     return out.value
 
 
+def ll_power_lmax_noalloc(A: DeviceCSR, iters: int = 20, seed: int = 0, stream=None) -> float:
+    """ll_power_lmax without any device allocation and without a handle, for callers that
+    cannot allocate device memory (their memory belongs to another allocator, or they cannot
+    afford cudaMalloc's implicit synchronisation). At most 262,144 rows; calls share one
+    library-owned scratch array, so calls that overlap on the GPU must be serialised."""
+    out = ctypes.c_double()
+    a = A.c()
+    st = _ffi.load().ll_power_lmax_noalloc(ctypes.byref(a), iters, seed, ctypes.byref(out), _stream_ptr(stream))
+    if st != 0:
+        raise LejaError(st, "ll_power_lmax_noalloc")
+    return out.value
+
+
 def ll_probes(h: Handle, kind: str, seed: int, stream_id: int, n: int, cols: int, stream=None):
     torch = _torch()
     out = torch.empty((n, cols), dtype=torch.float64, device="cuda")
