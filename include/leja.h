@@ -54,10 +54,12 @@ enum { LL_F64 = 0, LL_F32 = 1 };
 /* Arithmetic of the Léja recurrence (a12):
  *   LL_PREC_F64        W_j, P and the traces in IEEE FP64 on the FP64 pipe.
  *   LL_PREC_DF64       W_j, P and V stored as float pairs (hi, lo) and updated in double-float
- *                      arithmetic on the FP32 pipes (about 46-48 significant bits); the traces and
- *                      the QR are FP64. Same 8 bytes per element as FP64.
+ *                      arithmetic on the FP32 pipes (about 46-48 significant bits); trace sums
+ *                      are finished in FP64; the QR products run in double-float with FP64
+ *                      accumulation and an FP64 Cholesky. Same 8 bytes per element as FP64.
  *   LL_PREC_F32_MIXED  matrix values and W_j in FP32; P = sum_j d_j W_j and the traces accumulated
- *                      in FP64; QR in FP64.                                                         */
+ *                      in double-float (exact FP32 products, TwoSum accumulation: FP64-class);
+ *                      QR as in LL_PREC_DF64.                                                       */
 enum { LL_PREC_F64 = 0, LL_PREC_DF64 = 1, LL_PREC_F32_MIXED = 2 };
 
 enum { LL_PROBE_RADEMACHER = 0, LL_PROBE_GAUSSIAN = 1 };

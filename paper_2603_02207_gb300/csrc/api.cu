@@ -459,7 +459,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         V = vv;
     }
     const int ggrid = h->sm_count * 2;
-    WS(gpart, double*, "fw_gram_partials", (size_t)ggrid * (size_t)kq * (kq > kg ? kq : kg) * sizeof(double));
+    const size_t gp1 = gram_partials_doubles(kq, kq, true, ggrid), gp2 = gram_partials_doubles(kq, kg, false, ggrid);
+    WS(gpart, double*, "fw_gram_partials", (gp1 > gp2 ? gp1 : gp2) * sizeof(double));
     WS(gticket, unsigned int*, "fw_gram_ticket", sizeof(unsigned int));
     WS(gram, double*, "fw_gram", (size_t)kq * (kq > kg ? kq : kg) * sizeof(double));
     WS(rinv, double*, "fw_rinv", (size_t)kq * kq * sizeof(double));

@@ -81,7 +81,9 @@ cudaError_t launch_dot_f64(const double* x, const double* y, int n, double* part
                            double* out, int grid, cudaStream_t s);
 cudaError_t launch_scale_f64(double* x, const double* num, int n, int mode, cudaStream_t s);
 
-// CholeskyQR pieces (FP64 arithmetic)
+// CholeskyQR pieces
+// doubles of Gram partials needed for a launch with `grid` CTAs
+size_t gram_partials_doubles(int kx, int kz, bool sym, int grid);
 // out (kx x kz, row-major) = X^T Z, X: n x kx (type tx), Z: n x kz (type tz); sym: X == Z
 cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, const void* Z, long long ldz, int kz,
                         int n, bool sym, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
@@ -101,7 +103,7 @@ inline int w_type_of(int precision) {
     return precision == LL_PREC_F64 ? T_F64 : (precision == LL_PREC_DF64 ? T_DF64 : T_F32);
 }
 inline int p_type_of(int precision) {
-    return precision == LL_PREC_DF64 ? T_DF64 : T_F64;
+    return precision == LL_PREC_F64 ? T_F64 : T_DF64;
 }
 inline size_t elem_size(int t) { return t == T_F32 ? 4 : 8; }
 

@@ -1,111 +1,197 @@
 // Tall-skinny QR of the Hutch++ sketch by CholeskyQR2, and the deflation of the residual probes
-// (Algorithm 3 steps 4 and 6: Q = orth(Y), G' = G - Q (Q^T G)). FP64 arithmetic throughout.
+// (Algorithm 3 steps 4 and 6: Q = orth(Y), G' = G - Q (Q^T G)).
 //   Gram:   X^T Z over n rows, per-CTA partials reduced by the last CTA in a fixed order;
-//   chol:   G = R^T R (upper R) and R^{-1} in one CTA, with a breakdown flag;
+//   chol:   G = R^T R (upper R) and R^{-1} in one CTA (FP64, k <= 96), with a breakdown flag;
 //   apply:  X R^{-1} row by row (R^{-1} in shared memory);
 //   project: G - Q C row by row (C in shared memory).
+// The O(n k^2) products run in double-float arithmetic on the FP32 pipes (about 46-48 bits per
+// product, FP64 accumulation across row blocks); the k x k Cholesky stays in FP64.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace ll {
 
-constexpr int GRAM_THREADS = 256;
-constexpr int GRAM_E = 8;       // entries per thread per CTA
-constexpr int GRAM_TR = 16;     // rows per shared tile
+constexpr int QR_THREADS = 256;
+constexpr int QR_TR = 32;       // rows per shared-memory tile of the Gram kernel
+constexpr int QR_FLUSH = 8;     // tiles summed in double-float before an FP64 flush
 
+// Element (i) of a block as an unevaluated float pair hi + lo.
+__device__ __forceinline__ void ld_split(const double* p, size_t i, float& h, float& l) {
+    const double x = p[i];
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+}
+__device__ __forceinline__ void ld_split(const float2* p, size_t i, float& h, float& l) {
+    const float2 v = p[i];
+    h = v.x;
+    l = v.y;
+}
+__device__ __forceinline__ void ld_split(const float* p, size_t i, float& h, float& l) {
+    h = p[i];
+    l = 0.f;
+}
+
+// X^T Z over n rows in double-float arithmetic on the FP32 pipes (GB300's FP64 pipe runs at 1/62
+// of FP32). Each thread owns a 4x4 register tile of the output and a group of rows; per-thread
+// double-float sums cover QR_FLUSH * QR_TR rows at most before they are added into FP64
+// accumulators, so the error stays near FP64's. Per-CTA partials are reduced by the last CTA in
+// a fixed order. sym: Z == X and only the upper-triangular 4x4 tiles are computed.
 template <typename TX, typename TZ>
-__global__ void __launch_bounds__(GRAM_THREADS) k_gram(const TX* X, long long ldx, int kx, const TZ* Z, long long ldz, int kz,
-                                                       int n, int sym, double* partials, unsigned int* ticket, double* out) {
-    extern __shared__ __align__(16) double sg[];
-    double* xs = sg;                       // GRAM_TR x kx
-    double* zs = sg + GRAM_TR * kx;        // GRAM_TR x kz
+__global__ void __launch_bounds__(QR_THREADS) k_gram(const TX* X, long long ldx, int kx, const TZ* Z, long long ldz, int kz,
+                                                     int n, int sym, double* partials, unsigned int* ticket, double* out) {
+    extern __shared__ __align__(16) float sgf[];
     __shared__ bool s_last;
-    const int count = sym ? kx * (kx + 1) / 2 : kx * kz;
-    const int chunk0 = blockIdx.y * GRAM_THREADS * GRAM_E;
-    int ea[GRAM_E], ec[GRAM_E];
-    double acc[GRAM_E];
-#pragma unroll
-    for (int q = 0; q < GRAM_E; ++q) {
-        const int e = chunk0 + q * GRAM_THREADS + threadIdx.x;
-        acc[q] = 0.0;
-        ea[q] = -1; ec[q] = 0;
-        if (e < count) {
-            if (sym) {
-                int a = 0, rem = e;
-                while (rem >= kx - a) { rem -= kx - a; ++a; }
-                ea[q] = a; ec[q] = a + rem;
-            } else {
-                ea[q] = e / kz; ec[q] = e - (e / kz) * kz;
-            }
+    const int kxp = (kx + 3) & ~3;
+    const int kzp = sym ? kxp : ((kz + 3) & ~3);
+    float* xh = sgf;
+    float* xl = xh + QR_TR * kxp;
+    float* zh = sym ? xh : xl + QR_TR * kxp;
+    float* zl = sym ? xl : zh + QR_TR * kzp;
+    const int ta = kxp / 4, tc = kzp / 4;
+    const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
+    const int otc = min(OT, QR_THREADS);
+    const int G = QR_THREADS / otc;
+    const int t = threadIdx.x;
+    const int g = t / otc;
+    const int ot = blockIdx.y * otc + (t - g * otc);
+    const bool act = (g < G) && (ot < OT) && (t - g * otc < otc);
+    int ia = 0, ic = 0;
+    if (act) {
+        if (sym) {
+            int rem = ot;
+            while (rem >= ta - ia) { rem -= ta - ia; ++ia; }
+            ic = ia + rem;
+        } else {
+            ia = ot / tc;
+            ic = ot - ia * tc;
         }
     }
-    const int ntiles = (n + GRAM_TR - 1) / GRAM_TR;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int r0 = t * GRAM_TR;
-        const int rows = min(GRAM_TR, n - r0);
-        for (int i = threadIdx.x; i < GRAM_TR * kx; i += blockDim.x) {
-            const int rr = i / kx, c = i - rr * kx;
-            xs[i] = rr < rows ? load_f64<TX>(X, (size_t)(r0 + rr) * ldx + c) : 0.0;
+    float h[16], l[16];
+    double a64[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) { h[e] = 0.f; l[e] = 0.f; a64[e] = 0.0; }
+    const int ntiles = (n + QR_TR - 1) / QR_TR;
+    int cnt = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int i = t; i < QR_TR * kxp; i += QR_THREADS) {
+            const int r = i / kxp, a = i - r * kxp;
+            const int row = tile * QR_TR + r;
+            float hh = 0.f, ll = 0.f;
+            if (row < n && a < kx) ld_split(X, (size_t)row * ldx + a, hh, ll);
+            xh[i] = hh;
+            xl[i] = ll;
         }
         if (!sym) {
-            for (int i = threadIdx.x; i < GRAM_TR * kz; i += blockDim.x) {
-                const int rr = i / kz, c = i - rr * kz;
-                zs[i] = rr < rows ? load_f64<TZ>(Z, (size_t)(r0 + rr) * ldz + c) : 0.0;
+            for (int i = t; i < QR_TR * kzp; i += QR_THREADS) {
+                const int r = i / kzp, c = i - r * kzp;
+                const int row = tile * QR_TR + r;
+                float hh = 0.f, ll = 0.f;
+                if (row < n && c < kz) ld_split(Z, (size_t)row * ldz + c, hh, ll);
+                zh[i] = hh;
+                zl[i] = ll;
             }
         }
         __syncthreads();
-        const double* zsrc = sym ? xs : zs;
-        const int ldzs = sym ? kx : kz;
+        if (act) {
+            for (int rr = g; rr < QR_TR; rr += G) {
+                const float4 a4h = *reinterpret_cast<const float4*>(&xh[rr * kxp + ia * 4]);
+                const float4 a4l = *reinterpret_cast<const float4*>(&xl[rr * kxp + ia * 4]);
+                const float4 c4h = *reinterpret_cast<const float4*>(&zh[rr * kzp + ic * 4]);
+                const float4 c4l = *reinterpret_cast<const float4*>(&zl[rr * kzp + ic * 4]);
+                const float ah[4] = {a4h.x, a4h.y, a4h.z, a4h.w}, al[4] = {a4l.x, a4l.y, a4l.z, a4l.w};
+                const float ch[4] = {c4h.x, c4h.y, c4h.z, c4h.w}, cl[4] = {c4l.x, c4l.y, c4l.z, c4l.w};
 #pragma unroll
-        for (int q = 0; q < GRAM_E; ++q) {
-            if (ea[q] >= 0) {
-                double s = acc[q];
-                for (int rr = 0; rr < GRAM_TR; ++rr) s = fma(xs[rr * kx + ea[q]], zsrc[rr * ldzs + ec[q]], s);
-                acc[q] = s;
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) df_mac(h[i * 4 + j], l[i * 4 + j], ah[i], al[i], ch[j], cl[j]);
             }
         }
         __syncthreads();
+        if (++cnt == QR_FLUSH) {
+            cnt = 0;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) { a64[e] += (double)h[e] + (double)l[e]; h[e] = 0.f; l[e] = 0.f; }
+        }
     }
-    const int nblk = gridDim.x * gridDim.y;
-    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
-    for (int q = 0; q < GRAM_E; ++q) {
-        const int e = chunk0 + q * GRAM_THREADS + threadIdx.x;
-        if (e < count) partials[(size_t)blockIdx.x * count + e] = acc[q];
+    for (int e = 0; e < 16; ++e) a64[e] += (double)h[e] + (double)l[e];
+    // reduce the row groups (fixed order) and write this CTA's partial
+    double* red = reinterpret_cast<double*>(sgf);
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) red[((size_t)g * otc + (t - g * otc)) * 16 + e] = a64[e];
+    }
+    __syncthreads();
+    if (t < otc && blockIdx.y * otc + t < OT) {
+        const int o = blockIdx.y * otc + t;
+        for (int e = 0; e < 16; ++e) {
+            double sacc = 0.0;
+            for (int gg = 0; gg < G; ++gg) sacc += red[((size_t)gg * otc + t) * 16 + e];
+            partials[((size_t)blockIdx.x * OT + o) * 16 + e] = sacc;
+        }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)nblk - 1);
+    if (t == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
     __syncthreads();
     if (s_last) {
         __threadfence();
-        for (int e = threadIdx.x; e < count; e += blockDim.x) {
-            double s = 0.0;
-            for (int g = 0; g < (int)gridDim.x; ++g) s += __ldcg(&partials[(size_t)g * count + e]);
+        for (int q = t; q < OT * 16; q += QR_THREADS) {
+            const int o = q / 16, e = q - o * 16;
+            double sacc = 0.0;
+            for (int bx = 0; bx < (int)gridDim.x; ++bx) sacc += __ldcg(&partials[((size_t)bx * OT + o) * 16 + e]);
+            int oa, oc;
             if (sym) {
-                int a = 0, rem = e;
-                while (rem >= kx - a) { rem -= kx - a; ++a; }
-                const int c = a + rem;
-                out[a * kx + c] = s;
-                out[c * kx + a] = s;
+                int rem = o;
+                oa = 0;
+                while (rem >= ta - oa) { rem -= ta - oa; ++oa; }
+                oc = oa + rem;
             } else {
-                out[e] = s;
+                oa = o / tc;
+                oc = o - oa * tc;
+            }
+            const int a = oa * 4 + e / 4, c = oc * 4 + e % 4;
+            if (a < kx && c < kz) {
+                if (sym) {
+                    if (a <= c) { out[a * kx + c] = sacc; out[c * kx + a] = sacc; }
+                } else {
+                    out[a * kz + c] = sacc;
+                }
             }
         }
-        if (threadIdx.x == 0) *ticket = 0u;
+        if (t == 0) *ticket = 0u;
     }
-    (void)bid;
 }
 
 template <typename TX, typename TZ>
 static cudaError_t gram_typed(const void* X, long long ldx, int kx, const void* Z, long long ldz, int kz, int n, bool sym,
                               double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s) {
-    const int count = sym ? kx * (kx + 1) / 2 : kx * kz;
-    const int chunks = (count + GRAM_THREADS * GRAM_E - 1) / (GRAM_THREADS * GRAM_E);
-    const size_t smem = (size_t)GRAM_TR * (kx + (sym ? 0 : kz)) * sizeof(double);
-    dim3 g(grid, chunks);
-    k_gram<TX, TZ><<<g, GRAM_THREADS, smem, s>>>((const TX*)X, ldx, kx, (const TZ*)Z, ldz, kz, n, sym ? 1 : 0, partials, ticket, out);
+    const int kxp = (kx + 3) & ~3, kzp = sym ? kxp : ((kz + 3) & ~3);
+    const int ta = kxp / 4, tc = kzp / 4;
+    const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
+    const int chunks = (OT + QR_THREADS - 1) / QR_THREADS;
+    size_t smem = (size_t)QR_TR * (kxp + (sym ? 0 : kzp)) * 2 * sizeof(float);
+    const size_t red = (size_t)QR_THREADS * 16 * sizeof(double);
+    if (smem < red) smem = red;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gram<TX, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int gx = grid / chunks;
+    if (gx < 1) gx = 1;
+    dim3 gd(gx, chunks);
+    k_gram<TX, TZ><<<gd, QR_THREADS, smem, s>>>((const TX*)X, ldx, kx, (const TZ*)Z, ldz, kz, n, sym ? 1 : 0, partials, ticket, out);
     return cudaGetLastError();
+}
+
+size_t gram_partials_doubles(int kx, int kz, bool sym, int grid) {
+    const int kxp = (kx + 3) & ~3, kzp = sym ? kxp : ((kz + 3) & ~3);
+    const int ta = kxp / 4, tc = kzp / 4;
+    const size_t OT = sym ? (size_t)ta * (ta + 1) / 2 : (size_t)ta * tc;
+    return (size_t)grid * OT * 16;
 }
 
 cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, const void* Z, long long ldz, int kz,
@@ -178,50 +264,99 @@ cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, 
 }
 
 // ------------------------------------------------------------------- row-wise small products
-// mode 0: out[r, col] = sum_{a <= col} X[r, a] M[a, col]           (X R^{-1}, M upper triangular)
-// mode 1: out[r, col] = G[r, col] - sum_{a < kx} X[r, a] M[a, col]  (G - Q C)
+// mode 0: out[r, c] = sum_{a <= c} X[r, a] M[a, c]           (X R^{-1}, M upper triangular)
+// mode 1: out[r, c] = G[r, c] - sum_{a < kx} X[r, a] M[a, c]  (G - Q C)
+// Double-float products on the FP32 pipes; each thread computes 4 consecutive columns of a row.
+__device__ __forceinline__ void st_out2(double* p, size_t i, float h, float l) { p[i] = (double)h + (double)l; }
+__device__ __forceinline__ void st_out2(float* p, size_t i, float h, float l) { p[i] = h + l; }
+__device__ __forceinline__ void st_out2(float2* p, size_t i, float h, float l) { p[i] = df_norm(h, l); }
+
 template <typename TX, typename T2, int MODE>
-__global__ void k_rowprod(const TX* X, long long ldx, int kx, const double* M, int kc, const double* G, long long ldg,
-                          int n, int rl, double* out64, long long ld64, T2* out2, long long ld2) {
-    extern __shared__ __align__(16) double sm[];   // kx x kc
-    for (int i = threadIdx.x; i < kx * kc; i += blockDim.x) sm[i] = M[i];
-    __syncthreads();
-    const int rlane = threadIdx.x / kc;
-    const int col = threadIdx.x - rlane * kc;
-    if (rlane >= rl) return;
-    for (int r = blockIdx.x * rl + rlane; r < n; r += gridDim.x * rl) {
-        const size_t xo = (size_t)r * ldx;
-        double s = 0.0;
-        const int amax = (MODE == 0) ? col + 1 : kx;
-        for (int a = 0; a < amax; ++a) s = fma(load_f64<TX>(X, xo + a), sm[a * kc + col], s);
-        const double v = (MODE == 0) ? s : G[(size_t)r * ldg + col] - s;
-        out64[(size_t)r * ld64 + col] = v;
-        if (out2) store_f64<T2>(out2, (size_t)r * ld2 + col, v);
+__global__ void __launch_bounds__(QR_THREADS) k_rowprod(const TX* X, long long ldx, int kx, const double* M, int kc,
+                                                        const double* G, long long ldg, int n, double* out64, long long ld64,
+                                                        T2* out2, long long ld2) {
+    extern __shared__ __align__(16) float srp[];
+    const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
+    const int CG = kcp / 4;
+    const int RG = QR_THREADS / CG;
+    float* mh = srp;                    // kx x kcp
+    float* ml = mh + (size_t)kx * kcp;
+    float* xh = ml + (size_t)kx * kcp;  // RG x kxp
+    float* xl = xh + (size_t)RG * kxp;
+    for (int i = threadIdx.x; i < kx * kcp; i += blockDim.x) {
+        const int a = i / kcp, c = i - a * kcp;
+        float hh = 0.f, ll = 0.f;
+        if (c < kc) ld_split(M, (size_t)a * kc + c, hh, ll);
+        mh[i] = hh;
+        ml[i] = ll;
+    }
+    const int cg = threadIdx.x % CG;
+    const int rr = threadIdx.x / CG;
+    const bool act = rr < RG;
+    const int ntiles = (n + RG - 1) / RG;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < RG * kxp; i += blockDim.x) {
+            const int r = i / kxp, a = i - r * kxp;
+            const int row = tile * RG + r;
+            float hh = 0.f, ll = 0.f;
+            if (row < n && a < kx) ld_split(X, (size_t)row * ldx + a, hh, ll);
+            xh[i] = hh;
+            xl[i] = ll;
+        }
+        __syncthreads();
+        const int row = tile * RG + rr;
+        if (!act || row >= n) continue;
+        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        const int amax = (MODE == 0) ? min(kx, cg * 4 + 4) : kx;
+        for (int a = 0; a < amax; ++a) {
+            const float x_h = xh[rr * kxp + a], x_l = xl[rr * kxp + a];
+            const float4 m4h = *reinterpret_cast<const float4*>(&mh[(size_t)a * kcp + cg * 4]);
+            const float4 m4l = *reinterpret_cast<const float4*>(&ml[(size_t)a * kcp + cg * 4]);
+            df_mac(h[0], l[0], x_h, x_l, m4h.x, m4l.x);
+            df_mac(h[1], l[1], x_h, x_l, m4h.y, m4l.y);
+            df_mac(h[2], l[2], x_h, x_l, m4h.z, m4l.z);
+            df_mac(h[3], l[3], x_h, x_l, m4h.w, m4l.w);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = cg * 4 + j;
+            if (c >= kc) break;
+            if (MODE == 0) {
+                out64[(size_t)row * ld64 + c] = (double)h[j] + (double)l[j];
+                if (out2) st_out2(out2, (size_t)row * ld2 + c, h[j], l[j]);
+            } else {
+                const double v = G[(size_t)row * ldg + c] - ((double)h[j] + (double)l[j]);
+                out64[(size_t)row * ld64 + c] = v;
+                if (out2) store_f64<T2>(out2, (size_t)row * ld2 + c, v);
+            }
+        }
     }
 }
 
 template <typename TX, int MODE>
 static cudaError_t rowprod_dispatch(int t2, const TX* X, long long ldx, int kx, const double* M, int kc, const double* G,
                                     long long ldg, int n, double* out64, long long ld64, void* out2, long long ld2, cudaStream_t s) {
-    int rl = 256 / kc;
-    if (rl < 1) rl = 1;
-    const int threads = ((rl * kc + 31) / 32) * 32;
-    int blocks = (n + rl - 1) / rl;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
+    const int CG = kcp / 4;
+    const int RG = QR_THREADS / CG;
+    if (RG < 1) return cudaErrorInvalidValue;
+    int blocks = (n + RG - 1) / RG;
+    if (blocks > 152 * 4) blocks = 152 * 4;
     if (blocks < 1) return cudaSuccess;
-    const size_t smem = (size_t)kx * kc * sizeof(double);
+    const size_t smem = ((size_t)2 * kx * kcp + (size_t)2 * RG * kxp) * sizeof(float);
     switch (t2) {
         case T_F32:
             cudaFuncSetAttribute(k_rowprod<TX, float, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, float, MODE><<<blocks, threads, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, rl, out64, ld64, (float*)out2, ld2);
+            k_rowprod<TX, float, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (float*)out2, ld2);
             break;
         case T_DF64:
             cudaFuncSetAttribute(k_rowprod<TX, float2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, float2, MODE><<<blocks, threads, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, rl, out64, ld64, (float2*)out2, ld2);
+            k_rowprod<TX, float2, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (float2*)out2, ld2);
             break;
         default:
             cudaFuncSetAttribute(k_rowprod<TX, double, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, double, MODE><<<blocks, threads, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, rl, out64, ld64, (double*)out2, ld2);
+            k_rowprod<TX, double, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (double*)out2, ld2);
             break;
     }
     return cudaGetLastError();

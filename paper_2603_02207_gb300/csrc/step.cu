@@ -20,7 +20,7 @@ namespace ll {
 template <int PREC> struct Storage;
 template <> struct Storage<LL_PREC_F64> { using W = double; using V = double; using P = double; };
 template <> struct Storage<LL_PREC_DF64> { using W = float2; using V = float2; using P = float2; };
-template <> struct Storage<LL_PREC_F32_MIXED> { using W = float; using V = float; using P = double; };
+template <> struct Storage<LL_PREC_F32_MIXED> { using W = float; using V = float; using P = float2; };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
     };
 
     // per-thread trace partials (one column per thread)
-    Acc<PREC> tq{}, t0q{};
+    Acc<LL_PREC_DF64> tq{}, t0q{};   // double-float trace partials (F32 and DF64 modes)
     double t_acc = 0.0, t0_acc = 0.0;
 
     int tile = blockIdx.x;
@@ -241,12 +241,21 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
                         const float wn = fmaf((float)p.beta, wr[q], acc[q].v);
                         wout[own] = wn;
                         if constexpr (MODE == MODE_ACCUM) {
-                            const double base = p.first ? p.d0 * (double)wr[q] : po[q];
-                            pblk[rq * p.ldp + col] = fma(p.dn, (double)wn, base);
+                            // P (double-float) += d_{j+1} W_{j+1}, all on the FP32 pipes
+                            float ph, pl;
+                            if (p.first) {
+                                ph = 0.f; pl = 0.f;
+                                df_mac(ph, pl, p.d0_df.x, p.d0_df.y, wr[q], 0.f);
+                            } else {
+                                ph = po[q].x; pl = po[q].y;
+                            }
+                            df_mac(ph, pl, p.dn_df.x, p.dn_df.y, wn, 0.f);
+                            pblk[rq * p.ldp + col] = df_norm(ph, pl);
                         }
                         if constexpr (MODE == MODE_DOT) {
-                            t_acc = fma((double)vr[q], (double)wn, t_acc);
-                            if (p.first) t0_acc = fma((double)vr[q], (double)wr[q], t0_acc);
+                            // exact FP32 products accumulated in double-float
+                            df_mac(tq.h, tq.l, vr[q], 0.f, wn, 0.f);
+                            if (p.first) df_mac(t0q.h, t0q.l, vr[q], 0.f, wr[q], 0.f);
                         }
                     } else {  // LL_PREC_DF64
                         float sh = acc[q].h, sl = acc[q].l;
@@ -282,7 +291,7 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
     }
 
     if constexpr (MODE == MODE_DOT) {
-        if constexpr (PREC == LL_PREC_DF64) {
+        if constexpr (PREC != LL_PREC_F64) {
             t_acc = (double)tq.h + (double)tq.l;
             t0_acc = (double)t0q.h + (double)t0q.l;
         }
