@@ -156,15 +156,7 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     p.ldw = ldw;
     p.ldv = ldw;
     p.ldp = ldp;
-    // one row per gather batch (64 registers, two CTAs per SM); the L2 bulk prefetch stays off by
-    // default: on the 96^3 Laplacian it doubled the DRAM reads of the trace step for a 4% gain
-    p.rb = 1;
-    p.pf_dist = 0;
     StepLaunch L = plan_step(precision, mode, n, A->nnz, b, threads_target, rpt, p, h->sm_count);
-    {
-        const double window = (double)h->max_fwd_offset * (double)ldw * (precision == LL_PREC_F32_MIXED ? 4.0 : 8.0);
-        p.pf_far = (h->max_fwd_offset > p.rl * p.rpt && window < 48e6) ? h->max_fwd_offset : 0;
-    }
     if (mode == MODE_DOT) {
         WS(partials, double*, "dot_partials", (size_t)2 * L.grid * b * sizeof(double));
         WS(ticket, unsigned int*, "dot_ticket", sizeof(unsigned int));
@@ -322,7 +314,7 @@ ll_status ll_power_lmax(ll_handle* h, const ll_csr* A, int iters, uint64_t seed,
     WS(ticket, unsigned int*, "pw_ticket", sizeof(unsigned int));
     WS(nrm, double*, "pw_nrm", sizeof(double));
     LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
-    LL_CK(launch_probes(T_F64, LL_PROBE_RADEMACHER, seed, LL_STREAM_POWER, n, 1, x, 1, s));
+    LL_CK(launch_probes(T_F64, LL_PROBE_RADEMACHER, seed, LL_STREAM_POWER, n, 1, 1, x, 1, s));
     LL_CK(launch_dot_f64(x, x, n, partials, ticket, nrm, grid, s));
     LL_CK(launch_scale_f64(x, nrm, n, 0, s));
     h->launches += 3;
@@ -351,7 +343,7 @@ ll_status ll_probes(ll_handle* h, int kind, uint64_t seed, int stream_id, int64_
     if (n >= ((int64_t)1 << 31) || cols >= (1 << 24)) return fail(h, LL_ERR_UNSUPPORTED, "probe block too large");
     if (n * cols == 0) return LL_OK;
     if (!out) return fail(h, LL_ERR_INVALID_ARG, "null output");
-    LL_CK(launch_probes(T_F64, kind, seed, stream_id, (int)n, cols, out, ld, (cudaStream_t)stream));
+    LL_CK(launch_probes(T_F64, kind, seed, stream_id, (int)n, cols, cols, out, ld, (cudaStream_t)stream));
     h->launches++;
     return LL_OK;
 }
@@ -377,13 +369,15 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
     std::vector<double> beta(degree + 1);
     for (int j = 0; j <= degree; ++j) beta[j] = -(c / gamma + xi[j]);
     const int wt = w_type_of(precision), pt = p_type_of(precision);
-    const size_t nb = (size_t)n * b;
+    const int lb = even_ld(b);                 // blocks are stored in column pairs
+    const size_t nb = (size_t)n * lb;
     WS(vprep, void*, "ap_vals", (size_t)A->nnz * elem_size(wt));
     WS(w0, void*, "ap_w0", nb * elem_size(wt));
     WS(wa, void*, "ap_wa", nb * elem_size(wt));
     WS(wb, void*, "ap_wb", nb * elem_size(wt));
+    WS(pp, void*, "ap_p", nb * elem_size(pt));
     LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / gamma, precision, vprep, s));
-    LL_CK(launch_convert_block(V, ldv, precision, w0, b, n, b, s));
+    LL_CK(launch_convert_block(V, ldv, precision, w0, lb, n, b, lb, s));
     h->launches += 2;
     if (degree == 0) {
         // p_0 = d_0: PV = d_0 V
@@ -391,17 +385,10 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
         h->launches++;
         return LL_OK;
     }
-    if (pt == T_F64) {
-        // P is FP64: accumulate straight into the caller's PV (ld = ldp)
-        st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, b, wa, wb, PV, ldp, nullptr, beta, d, 0, 0, s);
-        if (st != LL_OK) return st;
-    } else {
-        WS(pp, void*, "ap_p", nb * elem_size(pt));
-        st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, b, wa, wb, pp, b, nullptr, beta, d, 0, 0, s);
-        if (st != LL_OK) return st;
-        LL_CK(launch_block_to_f64(precision, pp, b, PV, ldp, n, b, s));
-        h->launches++;
-    }
+    st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, lb, wa, wb, pp, lb, nullptr, beta, d, 0, 0, s);
+    if (st != LL_OK) return st;
+    LL_CK(launch_block_to_f64(precision, pp, lb, PV, ldp, n, b, s));
+    h->launches++;
     return LL_OK;
 }
 
@@ -444,18 +431,19 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     const int prec = o.precision;
     const int wt = w_type_of(prec), pt = p_type_of(prec);
     const size_t ew = elem_size(wt), ep = elem_size(pt);
+    const int l1 = even_ld(kq), l2 = even_ld(b2);   // pass-1 and pass-2 blocks (column pairs)
     // workspace
     WS(vprep, void*, "fw_vals", (size_t)A->nnz * ew);
-    WS(S, void*, "fw_S", (size_t)n * kq * ew);
+    WS(S, void*, "fw_S", (size_t)n * l1 * ew);
     WS(G, double*, "fw_G", (size_t)n * kg * sizeof(double));
-    WS(P, void*, "fw_P", (size_t)n * kq * ep);
-    WS(wa, void*, "fw_wa", (size_t)n * b2 * ew);
-    WS(wb, void*, "fw_wb", (size_t)n * b2 * ew);
-    WS(basis, double*, "fw_basis", (size_t)n * b2 * sizeof(double));
+    WS(P, void*, "fw_P", (size_t)n * l1 * ep);
+    WS(wa, void*, "fw_wa", (size_t)n * l2 * ew);
+    WS(wb, void*, "fw_wb", (size_t)n * l2 * ew);
+    WS(basis, double*, "fw_basis", (size_t)n * l2 * sizeof(double));
     WS(q1, double*, "fw_q1", (size_t)n * kq * sizeof(double));
     void* V = basis;
     if (wt != T_F64) {
-        WS(vv, void*, "fw_V", (size_t)n * b2 * ew);
+        WS(vv, void*, "fw_V", (size_t)n * l2 * ew);
         V = vv;
     }
     const int ggrid = h->sm_count * 2;
@@ -473,8 +461,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     // matrix values scaled by 1 / (sigma gamma): B = (A/sigma - c I)/gamma = prepared - (c/gamma) I
     LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
     // Algorithm 3 step 2 (S) and step 6 (G)
-    LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, S, kq, s));
-    LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, G, kg, s));
+    LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, l1, S, l1, s));
+    LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, s));
     h->launches += 3;
     LL_CK(cudaEventRecord(h->ev[1], s));
 
@@ -482,38 +470,40 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         // k >= n: the sketch spans R^n, so Q = I is an orthonormal basis of span(Y) and
         // G' = (I - Q Q^T) G = 0; the estimate is the exact trace of p(A~)
         LL_CK(cudaEventRecord(h->ev[2], s));
-        LL_CK(cudaMemsetAsync(basis, 0, (size_t)n * b2 * sizeof(double), s));
-        LL_CK(launch_unit_diag(T_F64, basis, b2, n, s));
+        LL_CK(cudaMemsetAsync(basis, 0, (size_t)n * l2 * sizeof(double), s));
+        LL_CK(launch_unit_diag(T_F64, basis, l2, n, s));
         h->launches++;
         if (wt != T_F64) {
-            LL_CK(cudaMemsetAsync(V, 0, (size_t)n * b2 * ew, s));
-            LL_CK(launch_unit_diag(wt, V, b2, n, s));
+            LL_CK(cudaMemsetAsync(V, 0, (size_t)n * l2 * ew, s));
+            LL_CK(launch_unit_diag(wt, V, l2, n, s));
             h->launches++;
         }
         LL_CK(cudaEventRecord(h->ev[3], s));
     } else {
         // step 3: Y = p(A~) S
-        st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, kq, S, kq, wa, wb, P, kq, nullptr, beta, d,
+        st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, kq, S, l1, wa, wb, P, l1, nullptr, beta, d,
                       o.threads_per_block, o.rows_per_thread, s);
         if (st != LL_OK) return st;
         LL_CK(cudaEventRecord(h->ev[2], s));
 
         // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']
-        LL_CK(launch_gram(pt, P, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
+        LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
         LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, s));
-        LL_CK(launch_apply_rinv(pt, P, kq, n, kq, rinv, q1, kq, T_F64, nullptr, 0, s));
+        LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv, q1, kq, T_F64, nullptr, 0, s));
         LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
         LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, s));
-        LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, b2, wt, wt != T_F64 ? V : nullptr, b2, s));
-        LL_CK(launch_gram(T_F64, basis, b2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, s));
-        LL_CK(launch_project(basis, b2, kq, G, kg, kg, gram, n, basis + kq, b2, wt,
-                             wt != T_F64 ? (void*)((char*)V + (size_t)kq * ew) : nullptr, b2, s));
+        LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, l2, wt, wt != T_F64 ? V : nullptr, l2, s));
+        LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, s));
+        // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
+        // The typed block pointer of V is offset by kq elements: element index r * l2 + kq + c.
+        LL_CK(launch_project(basis, l2, kq, G, kg, kg, gram, n, basis + kq, l2, wt,
+                             wt != T_F64 ? V : nullptr, l2, (b2 & 1), kq, s));
         h->launches += 8;
         LL_CK(cudaEventRecord(h->ev[3], s));
     }
 
     // steps 5-6: traces t_j[col] = <V_col, W_j col> for j = 0..m
-    st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, b2, wa, wb, nullptr, 0, dots, beta, d,
+    st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d,
                   o.threads_per_block, o.rows_per_thread, s);
     if (st != LL_OK) return st;
     LL_CK(cudaEventRecord(h->ev[4], s));
@@ -622,12 +612,13 @@ ll_status ll_kept_basis(const ll_handle* h, double* out, int64_t ld, int64_t* n_
     auto it = h->ws.find("fw_basis");
     if (it == h->ws.end()) return LL_ERR_NO_FORWARD;
     const int b2 = h->kept_kq + h->kept_kg;
+    const int l2 = even_ld(b2);
     if (n_out) *n_out = h->kept_n;
     if (kq_out) *kq_out = h->kept_kq;
     if (kg_out) *kg_out = h->kept_kg;
     if (!out) return LL_OK;
     if (ld < b2) return LL_ERR_INVALID_ARG;
-    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ld * sizeof(double), it->second.p, (size_t)b2 * sizeof(double),
+    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ld * sizeof(double), it->second.p, (size_t)l2 * sizeof(double),
                                       (size_t)b2 * sizeof(double), (size_t)h->kept_n, cudaMemcpyDeviceToDevice,
                                       (cudaStream_t)stream);
     return e == cudaSuccess ? LL_OK : LL_ERR_CUDA;

@@ -66,6 +66,99 @@ __host__ __device__ __forceinline__ float2 df_split(double x) {
 
 __device__ __forceinline__ double df_to_double(float2 v) { return (double)v.x + (double)v.y; }
 
+// ------------------------------------------------------------------------------------------------
+// Packed FP32 pairs (Blackwell f32x2 instructions): two floats in one 64-bit register, the first
+// in the low word. One instruction performs the operation on both lanes with IEEE RN rounding.
+// ------------------------------------------------------------------------------------------------
+typedef unsigned long long f2x;
+
+__device__ __forceinline__ f2x f2_pack(float a, float b) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2x v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+    f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+    f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2_sub(f2x a, f2x b) {
+    f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// (sh, sl) += a * (xh + xl) on both lanes, a = ah + al a double-float scalar broadcast to both
+// lanes as ah2 = (ah, ah), al2 = (al, al), nah2 = (-ah, -ah). Same operations, in the same order,
+// as df_mac on each lane: q = -round(ah*xh) so fma(ah, xh, q) is the exact product error.
+__device__ __forceinline__ void df2_mac(f2x& sh, f2x& sl, f2x ah2, f2x al2, f2x nah2, f2x xh2, f2x xl2) {
+    const f2x q = f2_mul(nah2, xh2);
+    f2x e = f2_fma(ah2, xh2, q);
+    e = f2_fma(ah2, xl2, e);
+    e = f2_fma(al2, xh2, e);
+    const f2x s = f2_sub(sh, q);
+    const f2x bb = f2_sub(s, sh);
+    const f2x t2 = f2_sub(sh, f2_sub(s, bb));
+    const f2x t3 = f2_add(q, bb);
+    sl = f2_add(sl, f2_add(f2_sub(t2, t3), e));
+    sh = s;
+}
+// (sh, sl) += a * x on both lanes for a double-float scalar a and plain float pairs x (lo = 0).
+__device__ __forceinline__ void df2_mac_f(f2x& sh, f2x& sl, f2x ah2, f2x al2, f2x nah2, f2x x2) {
+    const f2x q = f2_mul(nah2, x2);
+    f2x e = f2_fma(ah2, x2, q);
+    e = f2_fma(al2, x2, e);
+    const f2x s = f2_sub(sh, q);
+    const f2x bb = f2_sub(s, sh);
+    const f2x t2 = f2_sub(sh, f2_sub(s, bb));
+    const f2x t3 = f2_add(q, bb);
+    sl = f2_add(sl, f2_add(f2_sub(t2, t3), e));
+    sh = s;
+}
+// (sh, sl) += (xh + xl) * (yh + yl) lane-wise for two double-float pairs; nxh2 = -xh2.
+__device__ __forceinline__ void df2_mac_pp(f2x& sh, f2x& sl, f2x xh2, f2x xl2, f2x nxh2, f2x yh2, f2x yl2) {
+    const f2x q = f2_mul(nxh2, yh2);
+    f2x e = f2_fma(xh2, yh2, q);
+    e = f2_fma(xh2, yl2, e);
+    e = f2_fma(xl2, yh2, e);
+    const f2x s = f2_sub(sh, q);
+    const f2x bb = f2_sub(s, sh);
+    const f2x t2 = f2_sub(sh, f2_sub(s, bb));
+    const f2x t3 = f2_add(q, bb);
+    sl = f2_add(sl, f2_add(f2_sub(t2, t3), e));
+    sh = s;
+}
+__device__ __forceinline__ void df2_norm(f2x sh, f2x sl, f2x& h, f2x& l) {
+    const f2x s = f2_add(sh, sl);
+    l = f2_sub(sl, f2_sub(s, sh));
+    h = s;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Double-float blocks are stored in column pairs: the 16 bytes of pair (2q, 2q+1) of a row hold
+// (hi_2q, hi_2q+1, lo_2q, lo_2q+1), so one 16-byte load yields the hi pair and the lo pair of two
+// columns, ready for the f32x2 instructions. Leading dimensions (in columns) of such blocks are
+// even, so a flat element index i = row * ld + col keeps the parity of col. `dfp` is the element
+// tag of these blocks (a float array of 2 * n * ld entries).
+// ------------------------------------------------------------------------------------------------
+struct dfp {
+    float f;
+};
+__host__ __device__ __forceinline__ size_t dfp_hi(size_t i) { return (i >> 1) * 4 + (i & 1); }
+
 // Typed load/store of block elements as FP64.
 template <typename T> __device__ __forceinline__ double load_f64(const T* p, size_t i);
 template <> __device__ __forceinline__ double load_f64<double>(const double* p, size_t i) { return p[i]; }
@@ -76,5 +169,15 @@ template <typename T> __device__ __forceinline__ void store_f64(T* p, size_t i, 
 template <> __device__ __forceinline__ void store_f64<double>(double* p, size_t i, double v) { p[i] = v; }
 template <> __device__ __forceinline__ void store_f64<float>(float* p, size_t i, double v) { p[i] = (float)v; }
 template <> __device__ __forceinline__ void store_f64<float2>(float2* p, size_t i, double v) { p[i] = df_split(v); }
+template <> __device__ __forceinline__ double load_f64<dfp>(const dfp* p, size_t i) {
+    const float* f = reinterpret_cast<const float*>(p) + dfp_hi(i);
+    return (double)f[0] + (double)f[2];
+}
+template <> __device__ __forceinline__ void store_f64<dfp>(dfp* p, size_t i, double v) {
+    float* f = reinterpret_cast<float*>(p) + dfp_hi(i);
+    const float2 s = df_split(v);
+    f[0] = s.x;
+    f[2] = s.y;
+}
 
 }  // namespace ll

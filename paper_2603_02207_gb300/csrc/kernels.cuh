@@ -27,12 +27,9 @@ struct StepParams {
     unsigned int* ticket;    // DOT: zero-initialised counter, reset by the last block
     double* dots_next;
     double* dots_first;
-    long long ldw, ldv, ldp;
-    int n, b, rl, rpt, num_tiles, smem_cap;
+    long long ldw, ldv, ldp;     // leading dimensions in columns (even: blocks are stored in column pairs)
+    int n, b, tp, rl, rpt, num_tiles, smem_cap;
     int first;
-    int rb;                  // rows per gather batch and thread (1 or 2)
-    int pf_dist;             // L2 prefetch distance in tiles of this CTA (0 = off)
-    long long pf_far;        // forward row offset of far neighbours to prefetch (0 = none)
     double beta, d0, dn;
     float2 beta_df, d0_df, dn_df;
 };
@@ -49,7 +46,9 @@ StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int thr
                      StepParams& p, int sm_count);
 cudaError_t launch_step(int precision, int mode, const StepLaunch& L, const StepParams& p, cudaStream_t s);
 
-cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols,
+// probes into columns [0, cols) of an n x ld block of element type out_type; columns
+// [cols, pad) are set to zero (pad = cols for none)
+cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols, int pad,
                           void* out, long long ld, cudaStream_t s);
 // flag[0]: error bits (1 rowptr decreasing, 2 column out of range, 4 rowptr[0] != 0 or rowptr[n] != nnz);
 // flag[1]: largest forward offset max(col - row) over the stored entries (>= 0)
@@ -60,9 +59,10 @@ cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, cons
 // out[e] = convert(values[e] * scale) into the storage type of `precision`
 cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, double scale, int precision,
                                   void* out, cudaStream_t s);
-// out (type of `precision` W storage, ld_out) <- in (FP64, ld_in), n x b
+// out (type of `precision` W storage, ld_out) <- in (FP64, ld_in), n x b; columns [b, pad) of out
+// are set to zero
 cudaError_t launch_convert_block(const double* in, long long ld_in, int precision, void* out,
-                                 long long ld_out, int n, int b, cudaStream_t s);
+                                 long long ld_out, int n, int b, int pad, cudaStream_t s);
 // out (FP64, ld_out) <- in (type of `precision` P storage, ld_in)
 cudaError_t launch_block_to_f64(int precision, const void* in, long long ld_in, double* out,
                                 long long ld_out, int n, int b, cudaStream_t s);
@@ -92,13 +92,17 @@ cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, 
 // Out = X * Rinv (upper triangular k x k), X type tx; writes FP64 (out64) and optionally out2 (type t2)
 cudaError_t launch_apply_rinv(int tx, const void* X, long long ldx, int n, int k, const double* Rinv,
                               double* out64, long long ld64, int t2, void* out2, long long ld2, cudaStream_t s);
-// G' = G - Q C, G: FP64 (ldg), Q: FP64 (ldq), C k x kg; writes FP64 (out64) and optionally out2 (type t2)
+// G' = G - Q C, G: FP64 (ldg), Q: FP64 (ldq), C k x kg; writes FP64 (out64, columns [0, kg)) and
+// optionally out2 (type t2, columns [col2, col2 + kg)); zero_pad: also write 0 to the column after
+// the last one (the pad column of a pair layout)
 cudaError_t launch_project(const double* Q, long long ldq, int k, const double* G, long long ldg, int kg,
                            const double* C, int n, double* out64, long long ld64, int t2, void* out2,
-                           long long ld2, cudaStream_t s);
+                           long long ld2, int zero_pad, int col2, cudaStream_t s);
 
-// element types used by the typed helpers above
+// element types used by the typed helpers above; T_DF64 blocks are double-float in column pairs
 enum ElemType { T_F64 = 0, T_F32 = 1, T_DF64 = 2 };
+// even leading dimension of a block of b columns
+inline int even_ld(int b) { return b + (b & 1); }
 inline int w_type_of(int precision) {
     return precision == LL_PREC_F64 ? T_F64 : (precision == LL_PREC_DF64 ? T_DF64 : T_F32);
 }

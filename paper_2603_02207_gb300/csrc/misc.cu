@@ -7,27 +7,28 @@ namespace ll {
 
 // ---------------------------------------------------------------------------- probes (Alg. 3)
 template <typename T>
-__global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols, T* out, long long ld) {
-    const long long total = (long long)n * cols;
+__global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols, int pad, T* out, long long ld) {
+    const long long total = (long long)n * pad;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int row = (int)(e / cols);
-        const int col = (int)(e - (long long)row * cols);
-        const double v = probe_value(kind, seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row);
+        const int row = (int)(e / pad);
+        const int col = (int)(e - (long long)row * pad);
+        const double v = col < cols ? probe_value(kind, seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row) : 0.0;
         store_f64<T>(out, (size_t)row * ld + col, v);
     }
 }
 
-cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols,
+cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols, int pad,
                           void* out, long long ld, cudaStream_t s) {
-    const long long total = (long long)n * cols;
+    if (pad < cols) pad = cols;
+    const long long total = (long long)n * pad;
     if (total <= 0) return cudaSuccess;
     const int threads = 256;
     long long blocks = (total + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     switch (out_type) {
-        case T_F64: k_probes<double><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, (double*)out, ld); break;
-        case T_F32: k_probes<float><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, (float*)out, ld); break;
-        default: k_probes<float2><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, (float2*)out, ld); break;
+        case T_F64: k_probes<double><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (double*)out, ld); break;
+        case T_F32: k_probes<float><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (float*)out, ld); break;
+        default: k_probes<dfp><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (dfp*)out, ld); break;
     }
     return cudaGetLastError();
 }
@@ -136,24 +137,26 @@ cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, doub
 }
 
 // ------------------------------------------------------------------------ block conversions
+// columns [0, b) converted, columns [b, pad) of `out` set to zero
 template <typename TI, typename TO>
-__global__ void k_convert(const TI* in, long long ld_in, TO* out, long long ld_out, int n, int b) {
-    const long long total = (long long)n * b;
+__global__ void k_convert(const TI* in, long long ld_in, TO* out, long long ld_out, int n, int b, int pad) {
+    const long long total = (long long)n * pad;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(e / b);
-        const int c = (int)(e - (long long)r * b);
-        store_f64<TO>(out, (size_t)r * ld_out + c, load_f64<TI>(in, (size_t)r * ld_in + c));
+        const int r = (int)(e / pad);
+        const int c = (int)(e - (long long)r * pad);
+        store_f64<TO>(out, (size_t)r * ld_out + c, c < b ? load_f64<TI>(in, (size_t)r * ld_in + c) : 0.0);
     }
 }
 
 cudaError_t launch_convert_block(const double* in, long long ld_in, int precision, void* out,
-                                 long long ld_out, int n, int b, cudaStream_t s) {
-    if ((long long)n * b <= 0) return cudaSuccess;
+                                 long long ld_out, int n, int b, int pad, cudaStream_t s) {
+    if (pad < b) pad = b;
+    if ((long long)n * pad <= 0) return cudaSuccess;
     const int grid = 152 * 8, threads = 256;
     switch (w_type_of(precision)) {
-        case T_F64: k_convert<double, double><<<grid, threads, 0, s>>>(in, ld_in, (double*)out, ld_out, n, b); break;
-        case T_F32: k_convert<double, float><<<grid, threads, 0, s>>>(in, ld_in, (float*)out, ld_out, n, b); break;
-        default: k_convert<double, float2><<<grid, threads, 0, s>>>(in, ld_in, (float2*)out, ld_out, n, b); break;
+        case T_F64: k_convert<double, double><<<grid, threads, 0, s>>>(in, ld_in, (double*)out, ld_out, n, b, pad); break;
+        case T_F32: k_convert<double, float><<<grid, threads, 0, s>>>(in, ld_in, (float*)out, ld_out, n, b, pad); break;
+        default: k_convert<double, dfp><<<grid, threads, 0, s>>>(in, ld_in, (dfp*)out, ld_out, n, b, pad); break;
     }
     return cudaGetLastError();
 }
@@ -163,9 +166,9 @@ cudaError_t launch_block_to_f64(int precision, const void* in, long long ld_in, 
     if ((long long)n * b <= 0) return cudaSuccess;
     const int grid = 152 * 8, threads = 256;
     if (p_type_of(precision) == T_DF64)
-        k_convert<float2, double><<<grid, threads, 0, s>>>((const float2*)in, ld_in, out, ld_out, n, b);
+        k_convert<dfp, double><<<grid, threads, 0, s>>>((const dfp*)in, ld_in, out, ld_out, n, b, b);
     else
-        k_convert<double, double><<<grid, threads, 0, s>>>((const double*)in, ld_in, out, ld_out, n, b);
+        k_convert<double, double><<<grid, threads, 0, s>>>((const double*)in, ld_in, out, ld_out, n, b, b);
     return cudaGetLastError();
 }
 
@@ -196,7 +199,7 @@ cudaError_t launch_unit_diag(int t, void* out, long long ld, int n, cudaStream_t
     switch (t) {
         case T_F64: k_unit_diag<double><<<152, 256, 0, s>>>((double*)out, ld, n); break;
         case T_F32: k_unit_diag<float><<<152, 256, 0, s>>>((float*)out, ld, n); break;
-        default: k_unit_diag<float2><<<152, 256, 0, s>>>((float2*)out, ld, n); break;
+        default: k_unit_diag<dfp><<<152, 256, 0, s>>>((dfp*)out, ld, n); break;
     }
     return cudaGetLastError();
 }

@@ -87,7 +87,7 @@ extern "C" ll_status ll_power_lmax_noalloc(const ll_csr* A, int iters, uint64_t 
     NA_CK(cudaStreamSynchronize(s));
     if (hflag[0]) return LL_ERR_BAD_CSR;
     // the same sequence of kernels as ll_power_lmax, on the static scratch
-    NA_CK(launch_probes(T_F64, LL_PROBE_RADEMACHER, seed, LL_STREAM_POWER, n, 1, x, 1, s));
+    NA_CK(launch_probes(T_F64, LL_PROBE_RADEMACHER, seed, LL_STREAM_POWER, n, 1, 1, x, 1, s));
     NA_CK(launch_dot_f64(x, x, n, partials, ticket, nrm, grid, s));
     NA_CK(launch_scale_f64(x, nrm, n, 0, s));
     for (int it = 0; it < iters; ++it) {

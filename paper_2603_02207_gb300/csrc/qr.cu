@@ -30,6 +30,11 @@ __device__ __forceinline__ void ld_split(const float* p, size_t i, float& h, flo
     h = p[i];
     l = 0.f;
 }
+__device__ __forceinline__ void ld_split(const dfp* p, size_t i, float& h, float& l) {
+    const float* f = reinterpret_cast<const float*>(p) + dfp_hi(i);
+    h = f[0];
+    l = f[2];
+}
 
 // X^T Z over n rows in double-float arithmetic on the FP32 pipes (GB300's FP64 pipe runs at 1/62
 // of FP32). Each thread owns a 4x4 register tile of the output and a group of rows; per-thread
@@ -200,7 +205,7 @@ cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, co
     switch (tx) {
         case T_F64: return gram_typed<double, double>(X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, grid, s);
         case T_F32: return gram_typed<float, double>(X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, grid, s);
-        default: return gram_typed<float2, double>(X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, grid, s);
+        default: return gram_typed<dfp, double>(X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, grid, s);
     }
 }
 
@@ -269,12 +274,17 @@ cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, 
 // Double-float products on the FP32 pipes; each thread computes 4 consecutive columns of a row.
 __device__ __forceinline__ void st_out2(double* p, size_t i, float h, float l) { p[i] = (double)h + (double)l; }
 __device__ __forceinline__ void st_out2(float* p, size_t i, float h, float l) { p[i] = h + l; }
-__device__ __forceinline__ void st_out2(float2* p, size_t i, float h, float l) { p[i] = df_norm(h, l); }
+__device__ __forceinline__ void st_out2(dfp* p, size_t i, float h, float l) {
+    const float2 v = df_norm(h, l);
+    float* f = reinterpret_cast<float*>(p) + dfp_hi(i);
+    f[0] = v.x;
+    f[2] = v.y;
+}
 
 template <typename TX, typename T2, int MODE>
 __global__ void __launch_bounds__(QR_THREADS) k_rowprod(const TX* X, long long ldx, int kx, const double* M, int kc,
                                                         const double* G, long long ldg, int n, double* out64, long long ld64,
-                                                        T2* out2, long long ld2) {
+                                                        T2* out2, long long ld2, int col2, int zero_pad) {
     extern __shared__ __align__(16) float srp[];
     const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
     const int CG = kcp / 4;
@@ -307,6 +317,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(const TX* X, long long l
         __syncthreads();
         const int row = tile * RG + rr;
         if (!act || row >= n) continue;
+        if (zero_pad && cg == 0) {
+            out64[(size_t)row * ld64 + kc] = 0.0;
+            if (out2) store_f64<T2>(out2, (size_t)row * ld2 + col2 + kc, 0.0);
+        }
         float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
         const int amax = (MODE == 0) ? min(kx, cg * 4 + 4) : kx;
         for (int a = 0; a < amax; ++a) {
@@ -324,11 +338,11 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(const TX* X, long long l
             if (c >= kc) break;
             if (MODE == 0) {
                 out64[(size_t)row * ld64 + c] = (double)h[j] + (double)l[j];
-                if (out2) st_out2(out2, (size_t)row * ld2 + c, h[j], l[j]);
+                if (out2) st_out2(out2, (size_t)row * ld2 + col2 + c, h[j], l[j]);
             } else {
                 const double v = G[(size_t)row * ldg + c] - ((double)h[j] + (double)l[j]);
                 out64[(size_t)row * ld64 + c] = v;
-                if (out2) store_f64<T2>(out2, (size_t)row * ld2 + c, v);
+                if (out2) store_f64<T2>(out2, (size_t)row * ld2 + col2 + c, v);
             }
         }
     }
@@ -336,7 +350,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(const TX* X, long long l
 
 template <typename TX, int MODE>
 static cudaError_t rowprod_dispatch(int t2, const TX* X, long long ldx, int kx, const double* M, int kc, const double* G,
-                                    long long ldg, int n, double* out64, long long ld64, void* out2, long long ld2, cudaStream_t s) {
+                                    long long ldg, int n, double* out64, long long ld64, void* out2, long long ld2,
+                                    int col2, int zero_pad, cudaStream_t s) {
     const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
     const int CG = kcp / 4;
     const int RG = QR_THREADS / CG;
@@ -348,15 +363,15 @@ static cudaError_t rowprod_dispatch(int t2, const TX* X, long long ldx, int kx, 
     switch (t2) {
         case T_F32:
             cudaFuncSetAttribute(k_rowprod<TX, float, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, float, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (float*)out2, ld2);
+            k_rowprod<TX, float, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (float*)out2, ld2, col2, zero_pad);
             break;
         case T_DF64:
-            cudaFuncSetAttribute(k_rowprod<TX, float2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, float2, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (float2*)out2, ld2);
+            cudaFuncSetAttribute(k_rowprod<TX, dfp, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            k_rowprod<TX, dfp, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (dfp*)out2, ld2, col2, zero_pad);
             break;
         default:
             cudaFuncSetAttribute(k_rowprod<TX, double, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, double, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (double*)out2, ld2);
+            k_rowprod<TX, double, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (double*)out2, ld2, col2, zero_pad);
             break;
     }
     return cudaGetLastError();
@@ -365,16 +380,16 @@ static cudaError_t rowprod_dispatch(int t2, const TX* X, long long ldx, int kx, 
 cudaError_t launch_apply_rinv(int tx, const void* X, long long ldx, int n, int k, const double* Rinv,
                               double* out64, long long ld64, int t2, void* out2, long long ld2, cudaStream_t s) {
     switch (tx) {
-        case T_F64: return rowprod_dispatch<double, 0>(t2, (const double*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, s);
-        case T_F32: return rowprod_dispatch<float, 0>(t2, (const float*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, s);
-        default: return rowprod_dispatch<float2, 0>(t2, (const float2*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, s);
+        case T_F64: return rowprod_dispatch<double, 0>(t2, (const double*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, 0, 0, s);
+        case T_F32: return rowprod_dispatch<float, 0>(t2, (const float*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, 0, 0, s);
+        default: return rowprod_dispatch<dfp, 0>(t2, (const dfp*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, 0, 0, s);
     }
 }
 
 cudaError_t launch_project(const double* Q, long long ldq, int k, const double* G, long long ldg, int kg,
                            const double* C, int n, double* out64, long long ld64, int t2, void* out2,
-                           long long ld2, cudaStream_t s) {
-    return rowprod_dispatch<double, 1>(t2, Q, ldq, k, C, kg, G, ldg, n, out64, ld64, out2, ld2, s);
+                           long long ld2, int zero_pad, int col2, cudaStream_t s) {
+    return rowprod_dispatch<double, 1>(t2, Q, ldq, k, C, kg, G, ldg, n, out64, ld64, out2, ld2, col2, zero_pad, s);
 }
 
 }  // namespace ll

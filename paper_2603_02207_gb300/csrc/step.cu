@@ -4,34 +4,43 @@
 // streaming the CSR matrix once, and fuses the per-step epilogue:
 //   pass 1 (MODE_ACCUM): P += d_{j+1} W_{j+1}                (Algorithm 2, P_m = P_{m-1} + d_m w_m)
 //   pass 2 (MODE_DOT):   t_{j+1}[col] = <V[:, col], W_{j+1}[:, col]>   (Algorithm 3 steps 5-6)
+//   MODE_PLAIN:          W_{j+1} only (recomputation in the adjoint).
 //
-// Thread mapping: a CTA owns a tile of R = rl * rpt consecutive rows. Thread tid works on column
-// col = tid % b of rows r0 + tid / b + rl * t, t < rpt, so a warp touches consecutive elements of
-// the row-major block (coalesced own-row traffic), each thread keeps one column for the whole
-// tile (per-column trace partials stay in registers), and the tile's column indices and values
-// are staged once in shared memory and broadcast to the b threads of a row. The grid is
-// persistent: CTA i walks tiles i, i + grid, ..., so concurrently processed tiles form one
+// Thread mapping: every thread owns a pair of adjacent columns (2cp, 2cp+1) of rows
+// r0 + rlane + rl * t, t < rpt, of a CTA tile of R = rl * rpt consecutive rows; a warp touches
+// consecutive pairs of the row-major block (coalesced own-row traffic, 8- or 16-byte accesses)
+// and each thread keeps its pair for the whole launch (per-column trace partials stay in
+// registers). Arithmetic on the pair uses the f32x2 instructions (both columns per instruction);
+// double-float blocks are stored in column pairs (hi, hi, lo, lo) so a 16-byte load feeds them
+// directly. The tile's row pointers, column indices and values are staged in shared memory with
+// cp.async, double-buffered (the next tile's segment loads while the current one computes), and
+// the values are expanded once per CTA into the broadcast pairs the f32x2 instructions take.
+// Neighbour gathers of a row are issued in batches (gather_batch) before any is consumed. The
+// grid is persistent: CTA i walks tiles i, i + grid, ..., so concurrently processed tiles form one
 // contiguous row window and the gathered neighbour rows W_j[c, :] are L2 hits.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace ll {
 
-template <int PREC> struct Storage;
-template <> struct Storage<LL_PREC_F64> { using W = double; using V = double; using P = double; };
-template <> struct Storage<LL_PREC_DF64> { using W = float2; using V = float2; using P = float2; };
-template <> struct Storage<LL_PREC_F32_MIXED> { using W = float; using V = float; using P = float2; };
+template <int PREC> struct PairT;
+// W / V pair, P pair, raw CSR value (as prepared in global memory)
+template <> struct PairT<LL_PREC_F64> { using W = double2; using P = double2; using Raw = double; };
+template <> struct PairT<LL_PREC_DF64> { using W = ulonglong2; using P = ulonglong2; using Raw = float2; };
+template <> struct PairT<LL_PREC_F32_MIXED> { using W = f2x; using P = ulonglong2; using Raw = float; };
+
+// value expanded for the f32x2 instructions: DF64 (ah2, al2, nah2), F32 (a2), F64 (a)
+struct ExDF { f2x ah2, al2, nah2; };
+template <int PREC> struct ExT;
+template <> struct ExT<LL_PREC_F64> { using T = double; };
+template <> struct ExT<LL_PREC_DF64> { using T = ExDF; };
+template <> struct ExT<LL_PREC_F32_MIXED> { using T = f2x; };
+
+__device__ __forceinline__ double expand(double a) { return a; }
+__device__ __forceinline__ ExDF expand(float2 a) { return ExDF{f2_pack(a.x, a.x), f2_pack(a.y, a.y), f2_pack(-a.x, -a.x)}; }
+__device__ __forceinline__ f2x expand(float a) { return f2_pack(a, a); }
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-template <int PREC> struct Acc;
-template <> struct Acc<LL_PREC_F64> { double v; };
-template <> struct Acc<LL_PREC_F32_MIXED> { float v; };
-template <> struct Acc<LL_PREC_DF64> { float h, l; };
-
-__device__ __forceinline__ void mac(Acc<LL_PREC_F64>& a, double v, double x) { a.v = fma(v, x, a.v); }
-__device__ __forceinline__ void mac(Acc<LL_PREC_F32_MIXED>& a, float v, float x) { a.v = fmaf(v, x, a.v); }
-__device__ __forceinline__ void mac(Acc<LL_PREC_DF64>& a, float2 v, float2 x) { df_mac(a.h, a.l, v.x, v.y, x.x, x.y); }
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
@@ -45,69 +54,73 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-constexpr int GATHER_BATCH = 8;   // neighbour rows gathered per round trip and row
-constexpr int STEP_MAX_THREADS = 512;
+// neighbour rows gathered per round trip and row: 8 for 8-byte pairs, 7 for 16-byte pairs (a
+// 7-point stencil row in one round trip within the register budget of two CTAs per SM)
+template <int PREC> __host__ __device__ constexpr int gather_batch() { return PREC == LL_PREC_F32_MIXED ? 8 : 7; }
+// CTA size limit: two CTAs per SM at <= 85 registers (16-byte pairs) or <= 64 (8-byte pairs)
+template <int PREC> __host__ __device__ constexpr int step_max_threads() { return PREC == LL_PREC_F32_MIXED ? 512 : 384; }
+inline int step_max_threads_rt(int precision) { return precision == LL_PREC_F32_MIXED ? 512 : 384; }
 
-// Two staging buffers, each holding a tile's raw row pointers, column indices and values.
+// Shared memory: two staging buffers (raw row pointers, column indices, raw values) and one
+// expanded-value area for the tile being computed.
 template <int PREC>
 struct StepSmem {
-    using Val = typename Storage<PREC>::V;
+    using Raw = typename PairT<PREC>::Raw;
+    using Ex = typename ExT<PREC>::T;
     unsigned char* base;
-    size_t a, c, stride;
-    __device__ StepSmem(unsigned char* base_, int R, int cap) : base(base_) {
+    size_t a, c, stride, ex_off;
+    __device__ __host__ StepSmem(unsigned char* base_, int R, int cap) : base(base_) {
         a = align16((size_t)(R + 1) * 4);
         c = align16((size_t)cap * 4);
-        stride = a + c + align16((size_t)cap * sizeof(Val));
+        stride = a + c + align16((size_t)cap * sizeof(Raw));
+        ex_off = 2 * stride;
     }
+    __device__ __host__ size_t bytes(int cap) const { return ex_off + align16((size_t)cap * sizeof(Ex)); }
     __device__ int* rp(int b) const { return reinterpret_cast<int*>(base + b * stride); }
     __device__ int* col(int b) const { return reinterpret_cast<int*>(base + b * stride + a); }
-    __device__ Val* val(int b) const { return reinterpret_cast<Val*>(base + b * stride + a + c); }
+    __device__ Raw* raw(int b) const { return reinterpret_cast<Raw*>(base + b * stride + a + c); }
+    __device__ Ex* ex() const { return reinterpret_cast<Ex*>(base + ex_off); }
 };
 
-// L2 prefetch of rows [lo, hi) of a row-major block (TMA bulk prefetch, 16-byte granules,
-// split into 4 KB requests over the lanes of warp 0). A hint only: ranges are clamped to the
-// block and an unaligned base skips the prefetch.
-__device__ __forceinline__ void prefetch_rows_l2(const void* base, long long ld, int es, long long lo, long long hi, int n) {
-    if (!base || (((uintptr_t)base) & 15)) return;
-    if (lo < 0) lo = 0;
-    if (hi > n) hi = n;
-    if (lo >= hi) return;
-    const unsigned long long b0 = ((unsigned long long)lo * ld * es) & ~15ull;
-    const unsigned long long b1 = ((unsigned long long)hi * ld * es) & ~15ull;
-    const int lane = threadIdx.x;
-    for (unsigned long long off = b0 + (unsigned long long)lane * 4096; off < b1; off += 32ull * 4096) {
-        const unsigned long long len = (b1 - off < 4096) ? (b1 - off) : 4096;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"((uintptr_t)base + off), "r"((unsigned)len) : "memory");
-    }
-}
-
-template <int PREC, int MODE, int RB>
-__global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_step(const StepParams p) {
-    using W = typename Storage<PREC>::W;
-    using Val = typename Storage<PREC>::V;
-    using PS = typename Storage<PREC>::P;
-    constexpr int U = GATHER_BATCH;
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const StepParams p) {
+    using WP = typename PairT<PREC>::W;
+    using PP = typename PairT<PREC>::P;
+    using Raw = typename PairT<PREC>::Raw;
+    using Ex = typename ExT<PREC>::T;
+    constexpr int U = gather_batch<PREC>();
     extern __shared__ __align__(16) unsigned char smem[];
 
     const int tid = threadIdx.x;
-    const int b = p.b;
-    const int rlane = tid / b;
-    const int col = tid - rlane * b;
+    const int tp = p.tp;                  // column pairs per row = threads per row
+    const int rlane = tid / tp;
+    const int cp = tid - rlane * tp;
     const bool active = rlane < p.rl;
     const int R = p.rl * p.rpt;
     const int n = p.n;
     StepSmem<PREC> sm(smem, R, p.smem_cap);
 
-    const W* __restrict__ win = static_cast<const W*>(p.win);
-    W* __restrict__ wout = static_cast<W*>(p.wout);
-    const Val* __restrict__ vals = static_cast<const Val*>(p.vals);
-    const W* __restrict__ vblk = static_cast<const W*>(p.v);
-    PS* __restrict__ pblk = static_cast<PS*>(p.p);
+    const long long ldq = p.ldw >> 1;     // pairs per row of W
+    const long long ldvq = p.ldv >> 1;
+    const long long ldpq = p.ldp >> 1;
+    const WP* __restrict__ win = static_cast<const WP*>(p.win);
+    WP* __restrict__ wout = static_cast<WP*>(p.wout);
+    const Raw* __restrict__ vals = static_cast<const Raw*>(p.vals);
+    const WP* __restrict__ vblk = static_cast<const WP*>(p.v);
+    PP* __restrict__ pblk = static_cast<PP*>(p.p);
     const int* __restrict__ rowptr = p.rowptr;
     const int* __restrict__ colind = p.colind;
-    const long long ldw = p.ldw;
 
-    // stage the CSR segment of a tile into shared buffer `buf` (asynchronous copies)
+    // per-step scalars broadcast to both lanes (beta_j, d_{j+1}, d_0 as double-float)
+    const f2x bh2 = f2_pack(p.beta_df.x, p.beta_df.x), bl2 = f2_pack(p.beta_df.y, p.beta_df.y);
+    const f2x nbh2 = f2_pack(-p.beta_df.x, -p.beta_df.x);
+    const f2x beta2 = f2_pack((float)p.beta, (float)p.beta);
+    const f2x dnh2 = f2_pack(p.dn_df.x, p.dn_df.x), dnl2 = f2_pack(p.dn_df.y, p.dn_df.y);
+    const f2x ndnh2 = f2_pack(-p.dn_df.x, -p.dn_df.x);
+    const f2x d0h2 = f2_pack(p.d0_df.x, p.d0_df.x), d0l2 = f2_pack(p.d0_df.y, p.d0_df.y);
+    const f2x nd0h2 = f2_pack(-p.d0_df.x, -p.d0_df.x);
+    const f2x zero2 = 0ull;
+
     auto stage = [&](int tile, int buf, int nz0, int nz1) {
         const int r0 = tile * R;
         const int nrows = min(R, n - r0);
@@ -115,36 +128,23 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
         const int cnt = nz1 - nz0;
         if (cnt <= p.smem_cap) {
             int* sc = sm.col(buf);
-            Val* sv = sm.val(buf);
+            Raw* sv = sm.raw(buf);
             for (int i = tid; i < cnt; i += blockDim.x) {
                 cp_async4(sc + i, &colind[nz0 + i]);
-                if constexpr (sizeof(Val) == 8) cp_async8(sv + i, &vals[nz0 + i]);
+                if constexpr (sizeof(Raw) == 8) cp_async8(sv + i, &vals[nz0 + i]);
                 else cp_async4(sv + i, &vals[nz0 + i]);
             }
         }
         cp_async_commit();
     };
-    // prefetch into L2 the streamed operands of a tile ahead: its own W_j, V / P rows and the
-    // far-neighbour rows W_j[r + F] that a banded matrix touches first
-    auto prefetch_tile = [&](int tile) {
-        if (p.pf_dist <= 0 || tile >= p.num_tiles || tid >= 32) return;
-        const long long lo = (long long)tile * R, hi = lo + R;
-        prefetch_rows_l2(win, ldw, (int)sizeof(W), lo, hi, n);
-        if (p.pf_far > 0) prefetch_rows_l2(win, ldw, (int)sizeof(W), lo + p.pf_far, hi + p.pf_far, n);
-        if constexpr (MODE == MODE_DOT) prefetch_rows_l2(vblk, p.ldv, (int)sizeof(W), lo, hi, n);
-        if constexpr (MODE == MODE_ACCUM) {
-            if (!p.first) prefetch_rows_l2(pblk, p.ldp, (int)sizeof(PS), lo, hi, n);
-        }
-    };
 
-    // per-thread trace partials (one column per thread)
-    Acc<LL_PREC_DF64> tq{}, t0q{};   // double-float trace partials (F32 and DF64 modes)
-    double t_acc = 0.0, t0_acc = 0.0;
+    // trace partials of the thread's two columns (double-float; FP64 in the F64 mode)
+    f2x th2 = 0ull, tl2 = 0ull, t0h2 = 0ull, t0l2 = 0ull;
+    double td[2] = {0.0, 0.0}, t0d[2] = {0.0, 0.0};
 
     int tile = blockIdx.x;
     int nz0 = rowptr[tile * R], nz1 = rowptr[min(tile * R + R, n)];
     stage(tile, 0, nz0, nz1);
-    for (int d = 1; d <= p.pf_dist; ++d) prefetch_tile(tile + d * (int)gridDim.x);
     int ntile = tile + gridDim.x;
     int nnz0 = 0, nnz1 = 0;
     if (ntile < p.num_tiles) { nnz0 = rowptr[ntile * R]; nnz1 = rowptr[min(ntile * R + R, n)]; }
@@ -158,8 +158,6 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
             cp_async_wait<0>();
         }
         __syncthreads();
-        if (p.pf_dist > 0) prefetch_tile(tile + (p.pf_dist + 1) * (int)gridDim.x);
-        // bounds of the tile after next, loaded now and consumed one iteration later
         const int ftile = ntile + gridDim.x;
         int fz0 = 0, fz1 = 0;
         if (ftile < p.num_tiles) { fz0 = rowptr[ftile * R]; fz1 = rowptr[min(ftile * R + R, n)]; }
@@ -169,114 +167,107 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
         const bool in_smem = (nz1 - nz0) <= p.smem_cap;
         const int* rp = sm.rp(buf);
         const int* cols = in_smem ? sm.col(buf) : colind + nz0;
-        const Val* vv = in_smem ? sm.val(buf) : vals + nz0;
+        Ex* ex = sm.ex();
+        if constexpr (PREC != LL_PREC_F64) {
+            if (in_smem) {
+                const Raw* sr = sm.raw(buf);
+                for (int i = tid; i < nz1 - nz0; i += blockDim.x) ex[i] = expand(sr[i]);
+                __syncthreads();
+            }
+        }
+        const Raw* rawv = in_smem ? sm.raw(buf) : vals + nz0;
 
         if (active) {
-            for (int t = 0; t < p.rpt; t += RB) {
-                int kq0[RB], nk[RB], rr[RB];
-                bool has[RB];
-                W wr[RB], vr[RB];
-                PS po[RB];
-#pragma unroll
-                for (int q = 0; q < RB; ++q) {
-                    rr[q] = rlane + p.rl * (t + q);
-                    has[q] = (t + q < p.rpt) && (r0 + rr[q] < r1);
-                    kq0[q] = has[q] ? rp[rr[q]] - nz0 : 0;
-                    nk[q] = has[q] ? rp[rr[q] + 1] - rp[rr[q]] : 0;
+            for (int t = 0; t < p.rpt; ++t) {
+                const int rr = rlane + p.rl * t;
+                const int r = r0 + rr;
+                if (r >= r1) break;
+                const int k0 = rp[rr] - nz0;
+                const int nk = rp[rr + 1] - rp[rr];
+                const size_t own = (size_t)r * ldq + cp;
+                const WP wr = win[own];
+                PP po{};
+                WP vr{};
+                if constexpr (MODE == MODE_ACCUM) {
+                    if (!p.first) po = pblk[(size_t)r * ldpq + cp];
                 }
-                if (!has[0]) break;
+                if constexpr (MODE == MODE_DOT) vr = vblk[(size_t)r * ldvq + cp];
+
+                // accumulate sum_k a_k W_j[c_k, pair]
+                double a0 = 0.0, a1 = 0.0;             // F64
+                f2x ah = 0ull, al = 0ull;              // DF64 (hi, lo pairs); F32 uses ah
+                for (int kb = 0; kb < nk; kb += U) {
+                    WP x[U];
 #pragma unroll
-                for (int q = 0; q < RB; ++q) {
-                    wr[q] = W{};
-                    vr[q] = W{};
-                    po[q] = PS{};
-                    if (has[q]) {
-                        const size_t rq = (size_t)(r0 + rr[q]);
-                        wr[q] = win[rq * ldw + col];
-                        if constexpr (MODE == MODE_ACCUM) {
-                            if (!p.first) po[q] = pblk[rq * p.ldp + col];
-                        }
-                        if constexpr (MODE == MODE_DOT) vr[q] = vblk[rq * p.ldv + col];
-                    }
-                }
-                Acc<PREC> acc[RB];
-#pragma unroll
-                for (int q = 0; q < RB; ++q) acc[q] = Acc<PREC>{};
-                int nmax = nk[0];
-#pragma unroll
-                for (int q = 1; q < RB; ++q) nmax = max(nmax, nk[q]);
-                for (int kb = 0; kb < nmax; kb += U) {
-                    W x[RB][U];
+                    for (int u = 0; u < U; ++u)
+                        if (kb + u < nk) x[u] = win[(size_t)cols[k0 + kb + u] * ldq + cp];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-#pragma unroll
-                        for (int q = 0; q < RB; ++q)
-                            if (kb + u < nk[q]) x[q][u] = win[(size_t)cols[kq0[q] + kb + u] * ldw + col];
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-#pragma unroll
-                        for (int q = 0; q < RB; ++q)
-                            if (kb + u < nk[q]) mac(acc[q], vv[kq0[q] + kb + u], x[q][u]);
+                        if (kb + u < nk) {
+                            const int k = k0 + kb + u;
+                            if constexpr (PREC == LL_PREC_F64) {
+                                const double v = rawv[k];
+                                a0 = fma(v, x[u].x, a0);
+                                a1 = fma(v, x[u].y, a1);
+                            } else if constexpr (PREC == LL_PREC_DF64) {
+                                const ExDF v = in_smem ? ex[k] : expand(rawv[k]);
+                                df2_mac(ah, al, v.ah2, v.al2, v.nah2, x[u].x, x[u].y);
+                            } else {
+                                const f2x v = in_smem ? ex[k] : expand(rawv[k]);
+                                ah = f2_fma(v, x[u], ah);
+                            }
+                        }
                     }
                 }
-                // epilogue: shift, store, P-axpy or trace
-#pragma unroll
-                for (int q = 0; q < RB; ++q) {
-                    if (!has[q]) continue;
-                    const size_t rq = (size_t)(r0 + rr[q]);
-                    const size_t own = rq * ldw + col;
-                    if constexpr (PREC == LL_PREC_F64) {
-                        const double wn = fma(p.beta, wr[q], acc[q].v);
-                        wout[own] = wn;
-                        if constexpr (MODE == MODE_ACCUM) {
-                            const double base = p.first ? p.d0 * wr[q] : po[q];
-                            pblk[rq * p.ldp + col] = fma(p.dn, wn, base);
-                        }
-                        if constexpr (MODE == MODE_DOT) {
-                            t_acc = fma(vr[q], wn, t_acc);
-                            if (p.first) t0_acc = fma(vr[q], wr[q], t0_acc);
-                        }
-                    } else if constexpr (PREC == LL_PREC_F32_MIXED) {
-                        const float wn = fmaf((float)p.beta, wr[q], acc[q].v);
-                        wout[own] = wn;
-                        if constexpr (MODE == MODE_ACCUM) {
-                            // P (double-float) += d_{j+1} W_{j+1}, all on the FP32 pipes
-                            float ph, pl;
-                            if (p.first) {
-                                ph = 0.f; pl = 0.f;
-                                df_mac(ph, pl, p.d0_df.x, p.d0_df.y, wr[q], 0.f);
-                            } else {
-                                ph = po[q].x; pl = po[q].y;
-                            }
-                            df_mac(ph, pl, p.dn_df.x, p.dn_df.y, wn, 0.f);
-                            pblk[rq * p.ldp + col] = df_norm(ph, pl);
-                        }
-                        if constexpr (MODE == MODE_DOT) {
-                            // exact FP32 products accumulated in double-float
-                            df_mac(tq.h, tq.l, vr[q], 0.f, wn, 0.f);
-                            if (p.first) df_mac(t0q.h, t0q.l, vr[q], 0.f, wr[q], 0.f);
-                        }
-                    } else {  // LL_PREC_DF64
-                        float sh = acc[q].h, sl = acc[q].l;
-                        df_mac(sh, sl, p.beta_df.x, p.beta_df.y, wr[q].x, wr[q].y);
-                        const float2 wn = df_norm(sh, sl);
-                        wout[own] = wn;
-                        if constexpr (MODE == MODE_ACCUM) {
-                            float ph, pl;
-                            if (p.first) {
-                                ph = 0.f; pl = 0.f;
-                                df_mac(ph, pl, p.d0_df.x, p.d0_df.y, wr[q].x, wr[q].y);
-                            } else {
-                                ph = po[q].x; pl = po[q].y;
-                            }
-                            df_mac(ph, pl, p.dn_df.x, p.dn_df.y, wn.x, wn.y);
-                            pblk[rq * p.ldp + col] = df_norm(ph, pl);
-                        }
-                        if constexpr (MODE == MODE_DOT) {
-                            df_mac(tq.h, tq.l, vr[q].x, vr[q].y, wn.x, wn.y);
-                            if (p.first) df_mac(t0q.h, t0q.l, vr[q].x, vr[q].y, wr[q].x, wr[q].y);
-                        }
+                // epilogue: shift by beta_j, store W_{j+1}, then the P-axpy or the trace
+                if constexpr (PREC == LL_PREC_F64) {
+                    const double w0 = fma(p.beta, wr.x, a0), w1 = fma(p.beta, wr.y, a1);
+                    wout[own] = make_double2(w0, w1);
+                    if constexpr (MODE == MODE_ACCUM) {
+                        const double b0 = p.first ? p.d0 * wr.x : po.x, b1 = p.first ? p.d0 * wr.y : po.y;
+                        pblk[(size_t)r * ldpq + cp] = make_double2(fma(p.dn, w0, b0), fma(p.dn, w1, b1));
+                    }
+                    if constexpr (MODE == MODE_DOT) {
+                        td[0] = fma(vr.x, w0, td[0]);
+                        td[1] = fma(vr.y, w1, td[1]);
+                        if (p.first) { t0d[0] = fma(vr.x, wr.x, t0d[0]); t0d[1] = fma(vr.y, wr.y, t0d[1]); }
+                    }
+                } else if constexpr (PREC == LL_PREC_DF64) {
+                    df2_mac(ah, al, bh2, bl2, nbh2, wr.x, wr.y);
+                    f2x wh, wl;
+                    df2_norm(ah, al, wh, wl);
+                    wout[own] = make_ulonglong2(wh, wl);
+                    if constexpr (MODE == MODE_ACCUM) {
+                        f2x ph = zero2, pl = zero2;
+                        if (p.first) df2_mac(ph, pl, d0h2, d0l2, nd0h2, wr.x, wr.y);
+                        else { ph = po.x; pl = po.y; }
+                        df2_mac(ph, pl, dnh2, dnl2, ndnh2, wh, wl);
+                        f2x oh, ol;
+                        df2_norm(ph, pl, oh, ol);
+                        pblk[(size_t)r * ldpq + cp] = make_ulonglong2(oh, ol);
+                    }
+                    if constexpr (MODE == MODE_DOT) {
+                        const f2x nvh = f2_sub(zero2, vr.x);
+                        df2_mac_pp(th2, tl2, vr.x, vr.y, nvh, wh, wl);
+                        if (p.first) df2_mac_pp(t0h2, t0l2, vr.x, vr.y, nvh, wr.x, wr.y);
+                    }
+                } else {  // LL_PREC_F32_MIXED
+                    const f2x wn = f2_fma(beta2, wr, ah);
+                    wout[own] = wn;
+                    if constexpr (MODE == MODE_ACCUM) {
+                        f2x ph = zero2, pl = zero2;
+                        if (p.first) df2_mac_f(ph, pl, d0h2, d0l2, nd0h2, wr);
+                        else { ph = po.x; pl = po.y; }
+                        df2_mac_f(ph, pl, dnh2, dnl2, ndnh2, wn);
+                        f2x oh, ol;
+                        df2_norm(ph, pl, oh, ol);
+                        pblk[(size_t)r * ldpq + cp] = make_ulonglong2(oh, ol);
+                    }
+                    if constexpr (MODE == MODE_DOT) {
+                        // exact FP32 products v * w accumulated in double-float
+                        const f2x nv = f2_sub(zero2, vr);
+                        df2_mac_f(th2, tl2, vr, zero2, nv, wn);
+                        if (p.first) df2_mac_f(t0h2, t0l2, vr, zero2, nv, wr);
                     }
                 }
             }
@@ -292,20 +283,30 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
 
     if constexpr (MODE == MODE_DOT) {
         if constexpr (PREC != LL_PREC_F64) {
-            t_acc = (double)tq.h + (double)tq.l;
-            t0_acc = (double)t0q.h + (double)t0q.l;
+            float h0, h1, l0, l1;
+            f2_unpack(th2, h0, h1);
+            f2_unpack(tl2, l0, l1);
+            td[0] = (double)h0 + (double)l0;
+            td[1] = (double)h1 + (double)l1;
+            f2_unpack(t0h2, h0, h1);
+            f2_unpack(t0l2, l0, l1);
+            t0d[0] = (double)h0 + (double)l0;
+            t0d[1] = (double)h1 + (double)l1;
         }
         // block reduction per column, in row-lane order (deterministic)
         double* red = reinterpret_cast<double*>(smem);
         __shared__ bool s_last;
+        const int b = p.b;
         const int nred = p.first ? 2 : 1;
         for (int q = 0; q < nred; ++q) {
-            red[tid] = (q == 0) ? t_acc : t0_acc;
+            red[2 * tid] = q ? t0d[0] : td[0];
+            red[2 * tid + 1] = q ? t0d[1] : td[1];
             __syncthreads();
-            if (tid < b) {
+            for (int c = tid; c < b; c += blockDim.x) {
+                const int pc = c >> 1, lane = c & 1;
                 double s = 0.0;
-                for (int l = 0; l < p.rl; ++l) s += red[l * b + tid];
-                p.partials[((size_t)q * gridDim.x + blockIdx.x) * b + tid] = s;
+                for (int l = 0; l < p.rl; ++l) s += red[2 * (l * tp + pc) + lane];
+                p.partials[((size_t)q * gridDim.x + blockIdx.x) * b + c] = s;
             }
             __syncthreads();
         }
@@ -325,70 +326,72 @@ __global__ void __launch_bounds__(STEP_MAX_THREADS, (RB == 1 ? 2 : 1)) k_leja_st
     }
 }
 
-template <int PREC, int MODE, int RB>
+template <int PREC, int MODE>
 static cudaError_t launch_typed(const StepLaunch& L, const StepParams& p, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_leja_step<PREC, MODE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_leja_step<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_leja_step<PREC, MODE, RB><<<L.grid, L.threads, L.smem, s>>>(p);
+    k_leja_step<PREC, MODE><<<L.grid, L.threads, L.smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int PREC, int MODE, int RB>
+template <int PREC, int MODE>
 static int occupancy(int threads, size_t smem) {
-    cudaFuncSetAttribute(k_leja_step<PREC, MODE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_leja_step<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leja_step<PREC, MODE, RB>, threads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leja_step<PREC, MODE>, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     return per_sm;
 }
 
-template <int PREC, int MODE>
-static int occupancy_rb(int rb, int threads, size_t smem) {
-    return rb == 2 ? occupancy<PREC, MODE, 2>(threads, smem) : occupancy<PREC, MODE, 1>(threads, smem);
+template <int PREC>
+static size_t smem_bytes(int R, int cap) {
+    StepSmem<PREC> sm(nullptr, R, cap);
+    return sm.bytes(cap);
 }
-
-static size_t val_size(int precision) { return precision == LL_PREC_F32_MIXED ? 4 : 8; }
 
 StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int threads_target, int rpt,
                      StepParams& p, int sm_count) {
     StepLaunch L{};
-    if (threads_target <= 0) threads_target = 512;
+    const int tmax = step_max_threads_rt(precision);
+    if (threads_target <= 0 || threads_target > tmax) threads_target = tmax;
     if (rpt <= 0) rpt = 8;
-    if (threads_target > STEP_MAX_THREADS) threads_target = STEP_MAX_THREADS;
-    int rl = threads_target / b;
+    const int tp = (b + 1) / 2;
+    int rl = threads_target / tp;
     if (rl < 1) rl = 1;
-    while (rl > 1 && rl * b > STEP_MAX_THREADS) --rl;
-    L.threads = ((rl * b + 31) / 32) * 32;
-    if (p.rb != 1 && p.rb != 2) p.rb = 1;
-    if (p.rb == 2 && (rpt & 1)) ++rpt;
+    while (rl > 1 && rl * tp > tmax) --rl;
+    L.threads = ((rl * tp + 31) / 32) * 32;
     const int R = rl * rpt;
+    p.tp = tp;
     p.rl = rl;
     p.rpt = rpt;
     p.b = b;
     p.n = n;
     p.num_tiles = (n + R - 1) / R;
-    // shared staging (two buffers): expected tile nnz with 2x headroom, capped at 48 KB in all
+    // expected tile nnz with 25% headroom (+64), and at most ~80 KB of shared memory in all
     const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    int64_t cap = (int64_t)(avg * R * 2.0) + 64;
-    const size_t vs = val_size(precision);
-    const size_t fixed = align16((size_t)(R + 1) * 4);
-    const int64_t cap_max = (int64_t)((24 * 1024 - fixed - 32) / (4 + vs));
-    if (cap > cap_max) cap = cap_max;
+    int64_t cap = (int64_t)(avg * R * 1.25) + 64;
+    auto bytes_of = [&](int64_t c) -> size_t {
+        switch (precision) {
+            case LL_PREC_F64: return smem_bytes<LL_PREC_F64>(R, (int)c);
+            case LL_PREC_DF64: return smem_bytes<LL_PREC_DF64>(R, (int)c);
+            default: return smem_bytes<LL_PREC_F32_MIXED>(R, (int)c);
+        }
+    };
+    while (cap > 64 && bytes_of(cap) > 80 * 1024) cap = cap * 7 / 8;
     p.smem_cap = (int)cap;
-    size_t smem = 2 * (fixed + align16((size_t)cap * 4) + align16((size_t)cap * vs));
-    const size_t red = (size_t)L.threads * 8;
+    size_t smem = bytes_of(cap);
+    const size_t red = (size_t)L.threads * 2 * sizeof(double);
     if (mode == MODE_DOT && smem < red) smem = red;
     L.smem = smem;
-    // persistent grid: resident CTAs per SM from the occupancy calculator
     int per_sm = 1;
     switch (precision * 3 + mode) {
-#define OCC(P_, M_) case P_ * 3 + M_: per_sm = occupancy_rb<P_, M_>(p.rb, L.threads, smem); break;
+#define OCC(P_, M_) case P_ * 3 + M_: per_sm = occupancy<P_, M_>(L.threads, smem); break;
         OCC(LL_PREC_F64, MODE_PLAIN) OCC(LL_PREC_F64, MODE_ACCUM) OCC(LL_PREC_F64, MODE_DOT)
         OCC(LL_PREC_DF64, MODE_PLAIN) OCC(LL_PREC_DF64, MODE_ACCUM) OCC(LL_PREC_DF64, MODE_DOT)
         OCC(LL_PREC_F32_MIXED, MODE_PLAIN) OCC(LL_PREC_F32_MIXED, MODE_ACCUM) OCC(LL_PREC_F32_MIXED, MODE_DOT)
@@ -405,9 +408,8 @@ StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int thr
 
 cudaError_t launch_step(int precision, int mode, const StepLaunch& L, const StepParams& p, cudaStream_t s) {
     if (p.num_tiles <= 0) return cudaSuccess;
-    switch ((precision * 3 + mode) * 2 + (p.rb == 2 ? 1 : 0)) {
-#define LCH(P_, M_) case (P_ * 3 + M_) * 2: return launch_typed<P_, M_, 1>(L, p, s); \
-                    case (P_ * 3 + M_) * 2 + 1: return launch_typed<P_, M_, 2>(L, p, s);
+    switch (precision * 3 + mode) {
+#define LCH(P_, M_) case P_ * 3 + M_: return launch_typed<P_, M_>(L, p, s);
         LCH(LL_PREC_F64, MODE_PLAIN) LCH(LL_PREC_F64, MODE_ACCUM) LCH(LL_PREC_F64, MODE_DOT)
         LCH(LL_PREC_DF64, MODE_PLAIN) LCH(LL_PREC_DF64, MODE_ACCUM) LCH(LL_PREC_DF64, MODE_DOT)
         LCH(LL_PREC_F32_MIXED, MODE_PLAIN) LCH(LL_PREC_F32_MIXED, MODE_ACCUM) LCH(LL_PREC_F32_MIXED, MODE_DOT)
