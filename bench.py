@@ -39,8 +39,14 @@ PROBES = 99
 SEED = 1
 
 DTYPE_NAME = {"df64": "df64 (float-float on FP32 pipes, 8-byte storage)", "f64": "f64",
-              "f32": "f32 (FP64 accumulation of P and traces)"}
+              "f32": "f32 (double-float accumulation of P and traces)"}
 ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A, s_W, s_P, s_V
+
+# DRAM bytes (read + write) of one pass-2 trace-step launch per matrix row, from one ncu capture of
+# the current kernel on the 96^3 Laplacian (profiles/k_leja_step_df64_96cubed.md): 1.4777 GB over
+# 884,736 rows. Traffic grows in proportion to the rows of a stencil matrix, so the full-size value
+# is this figure times n. Only valid for the DF64 trace step as captured.
+TRACE_STEP_DRAM_BYTES_PER_ROW = {"df64": 1.477654528e9 / 884736}
 
 
 def step_bytes(n: int, nnz: int, b: int, prec: str, mode: str) -> int:
@@ -184,6 +190,9 @@ def main():
     ap.add_argument("--degree", type=int, default=60)
     ap.add_argument("--variants", type=int, default=1, help="also time the other precisions (1 = yes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=GRID_N, help="side of the 3-D grid (128 = the benchmark workload; "
+                    "smaller sides are for profiler captures)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -201,7 +210,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     _b.build()
-    A = laplacian_3d(GRID_N, SHIFT)
+    A = laplacian_3d(args.grid, SHIFT)
     n, nnz, k, m = A.n, A.nnz, PROBES // 3, args.degree
     h = L.Handle()
     stream = torch.cuda.current_stream()
@@ -252,8 +261,11 @@ def main():
     b_p2 = step_bytes(n, nnz, 2 * k, prec, "dot")
     b_p1 = step_bytes(n, nnz, k, prec, "accum")
     achieved = b_p2 / (p2_launch_ms / 1e3) / 1e9
+    per_row = TRACE_STEP_DRAM_BYTES_PER_ROW.get(prec)
     roof = {"kernel": f"k_leja_step<{prec},DOT> (b={2 * k})", "bound": "hbm", "achieved": achieved,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "traffic": per_row * n if per_row else None,
+            "traffic_source": "ncu dram__bytes_read+write of one launch at 96^3, scaled by rows" if per_row else None,
             "peak_source": peak_src,
             "per_launch_bytes": b_p2, "per_launch_ms": p2_launch_ms,
             "pass1_kernel": {"achieved": b_p1 / (p1_launch_ms / 1e3) / 1e9, "per_launch_bytes": b_p1,
@@ -261,7 +273,7 @@ def main():
 
     # end to end through the C ABI with host buffers (CSR copied host->device every call)
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         opts = r["opts"]
         Ah = A
         for _ in range(1):
@@ -299,13 +311,13 @@ def main():
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
     from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only
-    exact = logdet_laplacian_3d(GRID_N, SHIFT)
+    exact = logdet_laplacian_3d(args.grid, SHIFT)
     info = r["info"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_NAME[prec], "data": "synthetic",
-        "config": {"workload": f"L3D+{SHIFT}I on {GRID_N}^3 (n={n}, nnz={nnz}), bounds {list(BOUNDS)}, "
+        "config": {"workload": f"L3D+{SHIFT}I on {args.grid}^3 (n={n}, nnz={nnz}), bounds {list(BOUNDS)}, "
                                f"degree {m}, Hutch++ {PROBES} Rademacher probes (k={k}), seed {SEED}",
                    "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (probe blocks 0.5-1.1 GB, matrix 175 MB); no flush"},
