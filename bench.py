@@ -43,7 +43,7 @@ DTYPE_NAME = {"df64": "df64 (float-float on FP32 pipes, 8-byte storage)", "f64":
 ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A, s_W, s_P, s_V
 
 # DRAM bytes (read + write) of one pass-2 trace-step launch per matrix row, from one ncu capture of
-# the current kernel on the 96^3 Laplacian (profiles/k_leja_step_df64_96cubed.md): 1.4777 GB over
+# the current kernel on the 96^3 Laplacian (launch 5 of the 96^3 bench run): 1.4777 GB over
 # 884,736 rows. Traffic grows in proportion to the rows of a stencil matrix, so the full-size value
 # is this figure times n. Only valid for the DF64 trace step as captured.
 TRACE_STEP_DRAM_BYTES_PER_ROW = {"df64": 1.477654528e9 / 884736}

@@ -218,6 +218,14 @@ ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* A_host, ll_bounds b
  * grad_values: device, nnz doubles, overwritten. Enqueue only. */
 ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream);
 
+/* Chain to model parameters theta_p of a parameterised matrix A(theta) (e.g. the tau and kappa of a
+ * Matérn GMRF): out[p] = sum_e grad_values[e] * dvalues[p * ld + e], p < nparams, where
+ * dvalues[p * ld + e] = d a_e / d theta_p for every stored entry e < nnz. grad_values and
+ * dvalues are device FP64 arrays; out is host (nparams doubles); synchronises `stream`. With
+ * grad_values from ll_logdet_backward this is d estimate / d theta (chain rule; not in the paper). */
+ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* dvalues, int64_t ld, int64_t nnz,
+                        int nparams, double* out, void* stream);
+
 /* Many independent estimates in one persistent launch per pass (batching, a11): count matrices
  * mats[0..count-1] (device CSR each), bounds b[i], per-matrix degree degrees[i] (NULL = from the
  * bound ratio: m = clamp(ceil(ln 1e6 / ln rho), 10, 250), rho = (sqrt(kappa)+1)/(sqrt(kappa)-1),

@@ -225,6 +225,21 @@ def ll_logdet_backward(h: Handle, A: DeviceCSR, grad_output: float = 1.0, stream
     return g
 
 
+def ll_param_grad(h: Handle, grad_values, dvalues, stream=None) -> np.ndarray:
+    """sum_e grad_values[e] * dvalues[p, e] for every parameter p (dvalues: (nparams, nnz) FP64
+    CUDA tensor of d a_e / d theta_p)."""
+    torch = _torch()
+    assert grad_values.dtype == torch.float64 and dvalues.dtype == torch.float64
+    dv = dvalues.contiguous()
+    if dv.dim() == 1:
+        dv = dv[None, :]
+    npar, nnz = dv.shape
+    out = np.zeros(npar, dtype=np.float64)
+    h.check(h._lib.ll_param_grad(h.ptr, grad_values.data_ptr(), dv.data_ptr(), nnz, nnz, npar,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream)))
+    return out
+
+
 def ll_kept_basis(h: Handle, stream=None):
     """(Q, G') of the last forward with keep_for_backward, as FP64 torch tensors (copies)."""
     torch = _torch()

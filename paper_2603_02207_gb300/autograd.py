@@ -1,0 +1,39 @@
+"""torch.autograd.Function over the C ABI: the Léja/Hutch++ log-determinant estimate as a
+differentiable function of the stored CSR values.
+
+The backward is the library's adjoint (ll_logdet_backward): the derivative of the estimate with
+the Hutch++ basis [Q | G'], the spectral bounds, sigma and the Newton coefficients held fixed.
+Gradients with respect to model parameters follow from torch's chain rule when the values are a
+torch expression of those parameters, or from ll_param_grad given d values / d theta.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+class LejaLogdet(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, values, rowptr, colind, n, lmin, lmax, degree, probes, seed, precision, probe_kind, handle):
+        A = api.DeviceCSR(n=int(n), rowptr=rowptr, colind=colind, values=values.detach().contiguous())
+        opts = api.options(degree=degree, probes=probes, seed=seed, precision=precision, probe_kind=probe_kind,
+                           keep_for_backward=True)
+        est = api.ll_logdet_forward(handle, A, lmin, lmax, opts)
+        ctx.handle = handle
+        ctx.A = A
+        return torch.tensor(est, dtype=torch.float64, device=values.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = api.ll_logdet_backward(ctx.handle, ctx.A, float(grad_out))
+        return g.to(ctx.A.values.dtype), None, None, None, None, None, None, None, None, None, None, None
+
+
+def logdet(values, rowptr, colind, n: int, bounds: tuple[float, float], degree: int, probes: int, seed: int = 0,
+           precision: str = "df64", probe_kind: str = "rademacher", handle: api.Handle | None = None):
+    """Differentiable logdet_leja(csr, bounds, degree, probes, seed) of the CSR matrix
+    (rowptr, colind, values) on the current CUDA device; values may require grad."""
+    h = handle or api.Handle()
+    return LejaLogdet.apply(values, rowptr, colind, n, bounds[0], bounds[1], degree, probes, seed, precision,
+                            probe_kind, h)

@@ -1,5 +1,6 @@
 // C ABI of the Léja log-determinant library: handle and workspace, argument checks, the host
 // coefficient set-up, and the orchestration of the device passes of Algorithm 3.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -587,9 +588,123 @@ ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* Ah, ll_bounds bound
 
 ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream) {
     if (!h) return LL_ERR_INVALID_ARG;
-    (void)A; (void)grad_output; (void)grad_values; (void)stream;
     if (!h->kept) return fail(h, LL_ERR_NO_FORWARD, "no kept forward (call ll_logdet_forward with keep_for_backward = 1)");
-    return fail(h, LL_ERR_UNSUPPORTED, "backward not built yet");
+    ll_status st = check_csr_args(h, A);
+    if (st != LL_OK) return st;
+    if (A->n != h->kept_n || A->nnz != h->kept_nnz) return fail(h, LL_ERR_INVALID_ARG, "matrix shape differs from the kept forward");
+    if (A->nnz > 0 && !grad_values) return fail(h, LL_ERR_INVALID_ARG, "null grad_values");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->launches = 0;
+    const int n = (int)A->n;
+    const int prec = h->kept_prec, kq = h->kept_kq, kg = h->kept_kg, m = h->kept_m;
+    const int b2 = kq + kg, l2 = even_ld(b2);
+    const int wt = w_type_of(prec);
+    const size_t ew = elem_size(wt), blk = (size_t)n * l2 * ew;
+    if (A->nnz > 0) LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
+    if (n == 0 || A->nnz == 0) return LL_OK;
+    auto it_v = h->ws.find(wt == T_F64 ? "fw_basis" : "fw_V");
+    if (it_v == h->ws.end()) return fail(h, LL_ERR_NO_FORWARD, "kept basis missing");
+    const void* V = it_v->second.p;
+    const double sigma = h->kept_sigma, c = h->kept_c, gamma = h->kept_gamma;
+    const std::vector<double>& d = h->kept_d;
+    std::vector<double> beta(m + 1);
+    for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
+    // checkpoints W_{k s} (k >= 1) and a segment buffer for W_{j0+1} .. W_{j1-1}
+    const int sck = h->kept_ckpt > 0 ? h->kept_ckpt : (int)std::ceil(std::sqrt((double)m));
+    const int nseg = (m + sck - 1) / sck;
+    WS(vprep, void*, "bw_vals", (size_t)A->nnz * ew);
+    WS(ckpt, char*, "bw_ckpt", blk * (size_t)(nseg > 1 ? nseg - 1 : 1));
+    WS(seg, char*, "bw_seg", blk * (size_t)(sck > 1 ? sck - 1 : 1));
+    WS(lam, char*, "bw_lam", 2 * blk);
+    WS(tmp, char*, "bw_tmp", 2 * blk);
+    LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
+    h->launches++;
+
+    StepParams pp{};
+    pp.rowptr = A->rowptr;
+    pp.colind = A->colind;
+    pp.vals = vprep;
+    pp.ldw = l2;
+    pp.ldv = l2;
+    pp.ldp = l2;
+    pp.v = V;
+    pp.adj_split = kq;
+    StepParams pa = pp;
+    const StepLaunch Lp = plan_step(prec, MODE_PLAIN, n, A->nnz, b2, 0, 0, pp, h->sm_count);
+    const StepLaunch La = plan_step(prec, MODE_ADJ, n, A->nnz, b2, 0, 0, pa, h->sm_count);
+    auto plain_step = [&](int j, const void* win, void* wout) -> cudaError_t {
+        pp.win = win;
+        pp.wout = wout;
+        pp.beta = beta[j];
+        pp.beta_df = df_split(beta[j]);
+        h->launches++;
+        return launch_step(prec, MODE_PLAIN, Lp, pp, s);
+    };
+    // phase A: W_1 .. W_{(nseg-1) sck}, keeping W_{k sck} in the checkpoint slots
+    const void* cur = V;
+    for (int j = 0; j < (nseg - 1) * sck; ++j) {
+        void* out = ((j + 1) % sck == 0) ? (void*)(ckpt + (size_t)((j + 1) / sck - 1) * blk)
+                                         : (void*)(tmp + (cur == tmp ? blk : 0));
+        LL_CK(plain_step(j, cur, out));
+        cur = out;
+    }
+    // phase B: Lambda_m = d_m U, then segments in reverse
+    const double scale = grad_output / (sigma * gamma);
+    char* lam_cur = lam;
+    LL_CK(launch_scale_cols(prec, V, l2, n, b2, kq, d[m], d[m] / kg, lam_cur, s));
+    h->launches++;
+    for (int kk = nseg - 1; kk >= 0; --kk) {
+        const int j0 = kk * sck, j1 = std::min(j0 + sck, m);
+        const void* wj0 = kk == 0 ? V : (const void*)(ckpt + (size_t)(kk - 1) * blk);
+        const void* w = wj0;
+        for (int t = 1; t < j1 - j0; ++t) {
+            void* out = seg + (size_t)(t - 1) * blk;
+            LL_CK(plain_step(j0 + t - 1, w, out));
+            w = out;
+        }
+        for (int j = j1 - 1; j >= j0; --j) {
+            const void* wj = (j == j0) ? wj0 : (const void*)(seg + (size_t)(j - j0 - 1) * blk);
+            // g_e += (1 / (sigma gamma)) <Lambda_{j+1}[r, :], W_j[c, :]>
+            LL_CK(launch_sddmm(prec, A->rowptr, A->colind, n, lam_cur, wj, l2, b2, scale, grad_values, s));
+            h->launches++;
+            if (j == 0) break;
+            // Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U
+            char* lam_next = (lam_cur == lam) ? lam + blk : lam;
+            pa.win = lam_cur;
+            pa.wout = lam_next;
+            pa.beta = beta[j];
+            pa.beta_df = df_split(beta[j]);
+            pa.adj_q = d[j];
+            pa.adj_g = d[j] / kg;
+            pa.adj_q_df = df_split(d[j]);
+            pa.adj_g_df = df_split(d[j] / kg);
+            LL_CK(launch_step(prec, MODE_ADJ, La, pa, s));
+            h->launches++;
+            lam_cur = lam_next;
+        }
+    }
+    LL_CK(cudaGetLastError());
+    return LL_OK;
+}
+
+ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* dvalues, int64_t ld, int64_t nnz,
+                        int nparams, double* out, void* stream) {
+    if (!h || nparams < 0 || nnz < 0 || ld < nnz || (nparams > 0 && !out)) return LL_ERR_INVALID_ARG;
+    if (nparams == 0) return LL_OK;
+    if (nnz > 0 && (!grad_values || !dvalues)) return fail(h, LL_ERR_INVALID_ARG, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = h->sm_count * 4;
+    WS(partials, double*, "pg_partials", (size_t)nparams * grid * sizeof(double));
+    WS(ticket, unsigned int*, "pg_ticket", sizeof(unsigned int));
+    WS(res, double*, "pg_out", (size_t)nparams * sizeof(double));
+    LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
+    LL_CK(launch_param_dot(grad_values, dvalues, ld, nnz, nparams, partials, ticket, res, grid, s));
+    h->launches++;
+    std::vector<double> hv(nparams);
+    LL_CK(cudaMemcpyAsync(hv.data(), res, nparams * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    for (int p = 0; p < nparams; ++p) out[p] = hv[p];
+    return LL_OK;
 }
 
 ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b, int count, const ll_options* opts,

@@ -8,13 +8,16 @@
 
 namespace ll {
 
-enum StepMode { MODE_PLAIN = 0, MODE_ACCUM = 1, MODE_DOT = 2 };
+enum StepMode { MODE_PLAIN = 0, MODE_ACCUM = 1, MODE_DOT = 2, MODE_ADJ = 3 };
+constexpr int NUM_MODES = 4;
 
 // One Léja step over an n x b block, all columns at once (Algorithm 2 loop body):
 //   Wout = B Win - xi_j Win   with B = (A - c I)/gamma folded into prepared values a_e / gamma
 //          and beta = -(c/gamma + xi_j) applied to the row's own entry,
 //   ACCUM: P = (first ? d0 * Win : P) + dn * Wout
 //   DOT:   dots_next[col] = sum_i V[i, col] * Wout[i, col]   (and dots_first = V . Win if first)
+//   ADJ:   Wout += coef(col) * V[i, col] with coef = adj_q for col < adj_split, adj_g otherwise
+//          (the reverse recurrence Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U, B symmetric)
 struct StepParams {
     const int32_t* rowptr;
     const int32_t* colind;
@@ -32,6 +35,9 @@ struct StepParams {
     int first;
     double beta, d0, dn;
     float2 beta_df, d0_df, dn_df;
+    int adj_split;               // ADJ: first column using adj_g
+    double adj_q, adj_g;         // ADJ: coefficients of V (FP64)
+    float2 adj_q_df, adj_g_df;   // ADJ: the same as double-float pairs
 };
 
 struct StepLaunch {
@@ -66,6 +72,19 @@ cudaError_t launch_convert_block(const double* in, long long ld_in, int precisio
 // out (FP64, ld_out) <- in (type of `precision` P storage, ld_in)
 cudaError_t launch_block_to_f64(int precision, const void* in, long long ld_in, double* out,
                                 long long ld_out, int n, int b, cudaStream_t s);
+
+// out[r, c] = coef(c) * V[r, c] for c < b (coef = cq for c < split, cg otherwise), pad columns zero;
+// V and out in the W storage type of `precision`, leading dimension ld
+cudaError_t launch_scale_cols(int precision, const void* V, long long ld, int n, int b, int split, double cq, double cg,
+                              void* out, cudaStream_t s);
+// rowidx[e] = row of stored entry e
+cudaError_t launch_row_index(const int32_t* rowptr, int n, int32_t* rowidx, cudaStream_t s);
+// g[e] += scale * <Lam[r_e, :], W[c_e, :]> over b columns (W storage type of `precision`, ld even)
+cudaError_t launch_sddmm(int precision, const int32_t* rowptr, const int32_t* colind, int n, const void* lam,
+                         const void* w, long long ld, int b, double scale, double* g, cudaStream_t s);
+// out[p] = sum_e g[e] * dv[p * ldd + e], p < np; partials: np * grid doubles; result in out (device)
+cudaError_t launch_param_dot(const double* g, const double* dv, long long ldd, int64_t nnz, int np, double* partials,
+                             unsigned int* ticket, double* out, int grid, cudaStream_t s);
 
 // out = alpha * in (FP64 blocks)
 cudaError_t launch_scaled_copy_f64(const double* in, long long ld_in, double* out, long long ld_out, int n, int b,

@@ -4,7 +4,9 @@
 // streaming the CSR matrix once, and fuses the per-step epilogue:
 //   pass 1 (MODE_ACCUM): P += d_{j+1} W_{j+1}                (Algorithm 2, P_m = P_{m-1} + d_m w_m)
 //   pass 2 (MODE_DOT):   t_{j+1}[col] = <V[:, col], W_{j+1}[:, col]>   (Algorithm 3 steps 5-6)
-//   MODE_PLAIN:          W_{j+1} only (recomputation in the adjoint).
+//   MODE_PLAIN:          W_{j+1} only (recomputation in the adjoint);
+//   MODE_ADJ:            Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U, U = V with per-column
+//                        weights (the reverse recurrence of the adjoint, B symmetric).
 //
 // Thread mapping: every thread owns a pair of adjacent columns (2cp, 2cp+1) of rows
 // r0 + rlane + rl * t, t < rpt, of a CTA tile of R = rl * rpt consecutive rows; a warp touches
@@ -120,6 +122,12 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
     const f2x d0h2 = f2_pack(p.d0_df.x, p.d0_df.x), d0l2 = f2_pack(p.d0_df.y, p.d0_df.y);
     const f2x nd0h2 = f2_pack(-p.d0_df.x, -p.d0_df.x);
     const f2x zero2 = 0ull;
+    // ADJ: lane-wise coefficients of the thread's two columns
+    const bool q0 = 2 * cp < p.adj_split, q1 = 2 * cp + 1 < p.adj_split;
+    const double cadj0 = q0 ? p.adj_q : p.adj_g, cadj1 = q1 ? p.adj_q : p.adj_g;
+    const float2 cdf0 = q0 ? p.adj_q_df : p.adj_g_df, cdf1 = q1 ? p.adj_q_df : p.adj_g_df;
+    const f2x ch2 = f2_pack(cdf0.x, cdf1.x), cl2 = f2_pack(cdf0.y, cdf1.y), nch2 = f2_pack(-cdf0.x, -cdf1.x);
+    const f2x cf2 = f2_pack((float)cadj0, (float)cadj1);
 
     auto stage = [&](int tile, int buf, int nz0, int nz1) {
         const int r0 = tile * R;
@@ -191,7 +199,7 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
                 if constexpr (MODE == MODE_ACCUM) {
                     if (!p.first) po = pblk[(size_t)r * ldpq + cp];
                 }
-                if constexpr (MODE == MODE_DOT) vr = vblk[(size_t)r * ldvq + cp];
+                if constexpr (MODE == MODE_DOT || MODE == MODE_ADJ) vr = vblk[(size_t)r * ldvq + cp];
 
                 // accumulate sum_k a_k W_j[c_k, pair]
                 double a0 = 0.0, a1 = 0.0;             // F64
@@ -221,7 +229,11 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
                 }
                 // epilogue: shift by beta_j, store W_{j+1}, then the P-axpy or the trace
                 if constexpr (PREC == LL_PREC_F64) {
-                    const double w0 = fma(p.beta, wr.x, a0), w1 = fma(p.beta, wr.y, a1);
+                    double w0 = fma(p.beta, wr.x, a0), w1 = fma(p.beta, wr.y, a1);
+                    if constexpr (MODE == MODE_ADJ) {
+                        w0 = fma(cadj0, vr.x, w0);
+                        w1 = fma(cadj1, vr.y, w1);
+                    }
                     wout[own] = make_double2(w0, w1);
                     if constexpr (MODE == MODE_ACCUM) {
                         const double b0 = p.first ? p.d0 * wr.x : po.x, b1 = p.first ? p.d0 * wr.y : po.y;
@@ -234,6 +246,7 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
                     }
                 } else if constexpr (PREC == LL_PREC_DF64) {
                     df2_mac(ah, al, bh2, bl2, nbh2, wr.x, wr.y);
+                    if constexpr (MODE == MODE_ADJ) df2_mac_pp(ah, al, ch2, cl2, nch2, vr.x, vr.y);
                     f2x wh, wl;
                     df2_norm(ah, al, wh, wl);
                     wout[own] = make_ulonglong2(wh, wl);
@@ -252,7 +265,8 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
                         if (p.first) df2_mac_pp(t0h2, t0l2, vr.x, vr.y, nvh, wr.x, wr.y);
                     }
                 } else {  // LL_PREC_F32_MIXED
-                    const f2x wn = f2_fma(beta2, wr, ah);
+                    f2x wn = f2_fma(beta2, wr, ah);
+                    if constexpr (MODE == MODE_ADJ) wn = f2_fma(cf2, vr, wn);
                     wout[own] = wn;
                     if constexpr (MODE == MODE_ACCUM) {
                         f2x ph = zero2, pl = zero2;
@@ -390,11 +404,11 @@ StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int thr
     if (mode == MODE_DOT && smem < red) smem = red;
     L.smem = smem;
     int per_sm = 1;
-    switch (precision * 3 + mode) {
-#define OCC(P_, M_) case P_ * 3 + M_: per_sm = occupancy<P_, M_>(L.threads, smem); break;
-        OCC(LL_PREC_F64, MODE_PLAIN) OCC(LL_PREC_F64, MODE_ACCUM) OCC(LL_PREC_F64, MODE_DOT)
-        OCC(LL_PREC_DF64, MODE_PLAIN) OCC(LL_PREC_DF64, MODE_ACCUM) OCC(LL_PREC_DF64, MODE_DOT)
-        OCC(LL_PREC_F32_MIXED, MODE_PLAIN) OCC(LL_PREC_F32_MIXED, MODE_ACCUM) OCC(LL_PREC_F32_MIXED, MODE_DOT)
+    switch (precision * NUM_MODES + mode) {
+#define OCC(P_, M_) case P_ * NUM_MODES + M_: per_sm = occupancy<P_, M_>(L.threads, smem); break;
+#define OCC4(P_) OCC(P_, MODE_PLAIN) OCC(P_, MODE_ACCUM) OCC(P_, MODE_DOT) OCC(P_, MODE_ADJ)
+        OCC4(LL_PREC_F64) OCC4(LL_PREC_DF64) OCC4(LL_PREC_F32_MIXED)
+#undef OCC4
 #undef OCC
         default: break;
     }
@@ -408,11 +422,11 @@ StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int thr
 
 cudaError_t launch_step(int precision, int mode, const StepLaunch& L, const StepParams& p, cudaStream_t s) {
     if (p.num_tiles <= 0) return cudaSuccess;
-    switch (precision * 3 + mode) {
-#define LCH(P_, M_) case P_ * 3 + M_: return launch_typed<P_, M_>(L, p, s);
-        LCH(LL_PREC_F64, MODE_PLAIN) LCH(LL_PREC_F64, MODE_ACCUM) LCH(LL_PREC_F64, MODE_DOT)
-        LCH(LL_PREC_DF64, MODE_PLAIN) LCH(LL_PREC_DF64, MODE_ACCUM) LCH(LL_PREC_DF64, MODE_DOT)
-        LCH(LL_PREC_F32_MIXED, MODE_PLAIN) LCH(LL_PREC_F32_MIXED, MODE_ACCUM) LCH(LL_PREC_F32_MIXED, MODE_DOT)
+    switch (precision * NUM_MODES + mode) {
+#define LCH(P_, M_) case P_ * NUM_MODES + M_: return launch_typed<P_, M_>(L, p, s);
+#define LCH4(P_) LCH(P_, MODE_PLAIN) LCH(P_, MODE_ACCUM) LCH(P_, MODE_DOT) LCH(P_, MODE_ADJ)
+        LCH4(LL_PREC_F64) LCH4(LL_PREC_DF64) LCH4(LL_PREC_F32_MIXED)
+#undef LCH4
 #undef LCH
         default: return cudaErrorInvalidValue;
     }

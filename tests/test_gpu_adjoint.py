@@ -1,0 +1,107 @@
+"""GPU adjoint (backward) against the oracle's frozen-basis gradient (needs a GB300).
+
+The gradient of E(A) = n log sigma + tr(Q^T p(A~) Q) + (1/k) tr(G'^T p(A~) G') with Q, G', the
+bounds, sigma and the coefficients frozen does not depend on which orthonormal basis of span(Y)
+is used, so the oracle's Householder Q and the GPU's CholeskyQR2 Q give the same gradient.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import logdet as O
+from synth import laplacian_2d, matern_2d, matern_2d_derivatives, random_spd
+from tests import pins
+from tests.gpu_util import TOL, lib, need_gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    return lib()
+
+
+@pytest.fixture(scope="module")
+def h(L):
+    return L.Handle()
+
+
+def _gpu_grad(L, h, A, lmin, lmax, degree, probes, seed, prec, kind="rademacher", ckpt=0):
+    dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+    opts = L.options(degree=degree, probes=probes, seed=seed, precision=prec, probe_kind=kind,
+                     keep_for_backward=True, ckpt_stride=ckpt)
+    est = L.ll_logdet_forward(h, dA, lmin, lmax, opts)
+    g = L.ll_logdet_backward(h, dA, 1.0).cpu().numpy()
+    return est, g, dA
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("ckpt", [0, 1, 5])
+def test_backward_matches_oracle_gradient(L, h, prec, ckpt):
+    A = random_spd(700, nnz_per_row=7, seed=4, empty_rows=3)
+    lo, hi = O.gershgorin(A)
+    lmin = max(lo, 0.05)
+    m, probes, seed = 23, 18, 6
+    _, g, _ = _gpu_grad(L, h, A, lmin, hi, m, probes, seed, prec, ckpt=ckpt)
+    ref = O.logdet_leja(A, lmin, hi, m, probes, seed)
+    want = O.hutchpp_grad_values(A, lmin, hi, m, ref["Q"], ref["Gp"])
+    assert rel_err(g, want) < (1e-9 if prec != "f32" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["df64", "f64"])
+def test_backward_gaussian_matern_theta(L, h, prec):
+    """Matérn tau (kappa^2 I + L)^2 on 16 x 16 with Gaussian probes: value gradients against the
+    oracle, and the kappa / tau chain through ll_param_grad against the oracle's chain."""
+    torch = need_gpu()
+    N, kappa, tau = 16, 0.3, 1.0
+    A = matern_2d(N, kappa, tau)
+    lo, hi = O.gershgorin(A)
+    lmin = 0.9 * tau * (kappa * kappa + 8 * np.sin(np.pi / (2 * (N + 1))) ** 2) ** 2
+    m, probes, seed = 60, 30, 2
+    _, g, _ = _gpu_grad(L, h, A, lmin, hi, m, probes, seed, prec, kind="gaussian")
+    ref = O.logdet_leja(A, lmin, hi, m, probes, seed, kind="gaussian")
+    want = O.hutchpp_grad_values(A, lmin, hi, m, ref["Q"], ref["Gp"])
+    assert rel_err(g, want) < 1e-9
+    dk, dt = matern_2d_derivatives(N, kappa, tau)
+    dv = torch.as_tensor(np.stack([dk, dt])).cuda()
+    th = L.ll_param_grad(h, torch.as_tensor(g).cuda(), dv)
+    assert th[0] == pytest.approx(float(want @ dk), rel=1e-9)
+    assert th[1] == pytest.approx(float(want @ dt), rel=1e-9)
+
+
+def test_backward_exact_trace_matches_closed_form(L, h):
+    """k >= n: the frozen estimator is the exact polynomial trace and its parameter gradient
+    approaches tr(A^-1 dA/dtheta): n / tau and 4 kappa sum 1/(kappa^2 + mu)."""
+    torch = need_gpu()
+    N, kappa, tau = 6, 0.3, 1.3
+    A = matern_2d(N, kappa, tau)
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    lmin, lmax = 0.95 * lam[0], 1.05 * lam[-1]
+    _, g, _ = _gpu_grad(L, h, A, lmin, lmax, 200, 3 * A.n, 1, "df64")
+    dk, dt = matern_2d_derivatives(N, kappa, tau)
+    th = L.ll_param_grad(h, torch.as_tensor(g).cuda(), torch.as_tensor(np.stack([dk, dt])).cuda())
+    ex_k, ex_t = pins.dlogdet_matern_2d(N, kappa, tau)
+    assert th[0] == pytest.approx(ex_k, rel=1e-5)
+    assert th[1] == pytest.approx(ex_t, rel=1e-5)
+
+
+def test_autograd_function(L, h):
+    torch = need_gpu()
+    A = laplacian_2d(30, 0.1)
+    dA = L.DeviceCSR.from_host(A)
+    values = dA.values.clone().requires_grad_(True)
+    est = L.logdet(values, dA.rowptr, dA.colind, A.n, (0.1, 8.1), 25, 15, 3, handle=h)
+    est.backward()
+    ref = O.logdet_leja(A, 0.1, 8.1, 25, 15, 3)
+    assert float(est.detach()) == pytest.approx(ref["estimate"], rel=1e-10)
+    want = O.hutchpp_grad_values(A, 0.1, 8.1, 25, ref["Q"], ref["Gp"])
+    assert rel_err(values.grad.cpu().numpy(), want) < 1e-9
+
+
+def test_backward_without_forward_is_an_error(L):
+    h2 = L.Handle()
+    A = laplacian_2d(5, 0.1)
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_logdet_backward(h2, L.DeviceCSR.from_host(A), 1.0)
+    assert ei.value.name == "LL_ERR_NO_FORWARD"
