@@ -136,7 +136,11 @@ ll_status ll_leja_points(int count, double* xi_out);
  * z_i = c + gamma xi_i with c = (lmin+lmax)/2 and gamma = (lmax-lmin)/4, by Algorithm 1
  * (Section 3.1): d = log(Q_m) e_1 with Q_m = c I + gamma Qhat_m and a Taylor series of
  * log(I + (Q_m - s I)/s). The series stops when a term's max-norm falls below 1e-18 times the
- * sum's (after >= 10 terms); more than 5e6 terms gives LL_ERR_DD_NOT_CONVERGED.
+ * sum's (after >= 10 terms). When the series would need more than 1e6 terms (its factor
+ * q = max_i |z_i/s - 1| gives ln(1e-18)/ln(q) > 1e6: condition numbers above ~1e5 at s = c, and
+ * every s = lmax/2), the coefficients come from the textbook divided-difference table (Eq. Léja7)
+ * of log(c + gamma xi) in the xi variable instead, and *terms_out is 0. A series that still fails
+ * within 5e6 terms gives LL_ERR_DD_NOT_CONVERGED.
  * d_out: host, degree+1 doubles. terms_out: host, may be NULL. */
 ll_status ll_divided_differences(ll_bounds bounds, int degree, int sval_mode, double* d_out, int* terms_out);
 

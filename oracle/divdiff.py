@@ -20,7 +20,13 @@ Readings fixed by this library (the paper is silent or inconsistent):
     1e-18 times the max-norm of the running sum, after at least 10 terms; more than
     5,000,000 terms raises DividedDifferenceError;
   * s defaults to c, the optimum of Lemma 3.1; s = lambda_max / 2 is the other choice the paper
-    reports.
+    reports;
+  * when the series would need more than 1e6 terms (predicted from its convergence factor
+    q = max_i |z_i / s - 1|, i.e. ln(1e-18) / ln(q) > 1e6, which happens for condition numbers
+    above ~1e5 at s = c and always at s = lambda_max / 2), the divided differences are taken
+    from the textbook table (Eq. Léja7) of g(xi) = log(c + gamma xi) over the Léja points on
+    [-2, 2] instead: since z = c + gamma xi, g[xi_0..xi_j] = gamma^j log[z_0..z_j] = d_j exactly,
+    and in this variable the table neither underflows nor loses accuracy for Léja-ordered nodes.
 """
 from __future__ import annotations
 
@@ -35,6 +41,41 @@ TAYLOR_MAX_TERMS = 5_000_000
 
 class DividedDifferenceError(RuntimeError):
     pass
+
+
+TABLE_THRESHOLD_TERMS = 1_000_000
+
+
+def predicted_taylor_terms(xi: np.ndarray, c: float, gamma: float, s: float) -> float:
+    """ln(1e-18) / ln(q) with q = max_i |z_i / s - 1| (infinite when q >= 1)."""
+    q = float(np.max(np.abs((c + gamma * np.asarray(xi, dtype=np.float64)) / s - 1.0)))
+    if q >= 1.0:
+        return math.inf
+    if q <= 0.0:
+        return 1.0
+    return math.log(TAYLOR_REL_TOL) / math.log(q)
+
+
+def divided_differences_table(xi: np.ndarray, c: float, gamma: float) -> np.ndarray:
+    """d_j = g[xi_0, ..., xi_j] for g(xi) = log(c + gamma xi) by the standard recurrence
+    (Eq. Léja7) in the xi variable: column o holds g[xi_i, ..., xi_{i+o}]."""
+    xi = np.asarray(xi, dtype=np.float64)
+    col = np.log(c + gamma * xi)
+    out = [col[0]]
+    for o in range(1, xi.shape[0]):
+        col = (col[1:] - col[:-1]) / (xi[o:] - xi[:-o])
+        out.append(col[0])
+    return np.array(out)
+
+
+def scaled_divided_differences(xi: np.ndarray, c: float, gamma: float, s: float | None = None) -> tuple[np.ndarray, int]:
+    """Algorithm 1 when its series converges in a reasonable number of terms, otherwise the
+    xi-variable table. Returns (d, p) with p = 0 when the table was used."""
+    if s is None:
+        s = c
+    if predicted_taylor_terms(xi, c, gamma, s) > TABLE_THRESHOLD_TERMS:
+        return divided_differences_table(xi, c, gamma), 0
+    return divided_differences(xi, c, gamma, s)
 
 
 def divided_differences(xi: np.ndarray, c: float, gamma: float, s: float | None = None,

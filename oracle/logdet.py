@@ -33,7 +33,7 @@ import math
 import numpy as np
 import scipy.sparse as sp
 
-from .divdiff import divided_differences
+from .divdiff import scaled_divided_differences
 from .leja import fast_leja_points
 from . import rng as _rng
 
@@ -97,7 +97,8 @@ def degree_from_bounds(lmin: float, lmax: float, target: float = 1e-6, lo: int =
 
 def newton_leja_setup(lmin: float, lmax: float, degree: int, s_mode: str = "center"):
     """Léja points on [-2, 2], the map z = c + gamma xi (Eqs. z_mapping, eq_centre, eq_gamma)
-    and the scaled coefficients d_0..d_degree by Algorithm 1."""
+    and the scaled coefficients d_0..d_degree by Algorithm 1 (or the xi-variable divided
+    difference table when Algorithm 1's series would need more than 1e6 terms; p = 0 then)."""
     if not (0.0 < lmin < lmax):
         raise ValueError("need 0 < lmin < lmax")
     xi = fast_leja_points(degree + 1)
@@ -109,7 +110,7 @@ def newton_leja_setup(lmin: float, lmax: float, degree: int, s_mode: str = "cent
         s = lmax / 2.0
     else:
         raise ValueError(s_mode)
-    d, p = divided_differences(xi, c, gamma, s)
+    d, p = scaled_divided_differences(xi, c, gamma, s)
     return xi, c, gamma, d, p
 
 

@@ -127,7 +127,7 @@ ll_status setup_coefficients(ll_handle* h, double lmin, double lmax, int degree,
     leja_points(degree + 1, xi.data());
     if (!(h->dd_degree == degree && h->dd_sval == sval && h->dd_lmin == lmin && h->dd_lmax == lmax)) {
         std::vector<double> dn(degree + 1);
-        const int terms = divided_differences_alg1(lmin, lmax, degree, sval, dn.data(), kTaylorMaxTerms);
+        const int terms = scaled_divided_differences(lmin, lmax, degree, sval, dn.data());
         if (terms < 0) return fail(h, LL_ERR_DD_NOT_CONVERGED, "Algorithm 1 Taylor series did not converge within 5e6 terms");
         h->dd = dn;
         h->dd_degree = degree;
@@ -270,7 +270,7 @@ ll_status ll_divided_differences(ll_bounds b, int degree, int sval_mode, double*
     if (degree < 0 || !d_out) return LL_ERR_INVALID_ARG;
     if (sval_mode != LL_SVAL_CENTER && sval_mode != LL_SVAL_HALF_LMAX) return LL_ERR_INVALID_ARG;
     if (!std::isfinite(b.lmin) || !std::isfinite(b.lmax) || !(b.lmin > 0.0) || !(b.lmin < b.lmax)) return LL_ERR_BAD_BOUNDS;
-    const int terms = divided_differences_alg1(b.lmin, b.lmax, degree, sval_mode, d_out, kTaylorMaxTerms);
+    const int terms = scaled_divided_differences(b.lmin, b.lmax, degree, sval_mode, d_out);
     if (terms < 0) return LL_ERR_DD_NOT_CONVERGED;
     if (terms_out) *terms_out = terms;
     return LL_OK;

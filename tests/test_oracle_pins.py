@@ -400,3 +400,27 @@ def test_grad_theta_matches_exact_trace_matern():
     # the gradient of a symmetric matrix's estimator is symmetric
     Gm = __import__("scipy.sparse", fromlist=["csr_matrix"]).csr_matrix((g, A.colind, A.rowptr), shape=(A.n, A.n))
     assert abs(Gm - Gm.T).max() <= 1e-10 * abs(Gm).max()
+
+
+@pytest.mark.parametrize("kappa,m", [(81.0, 39), (8080.0, 80), (2.5e6, 150), (1e9, 250)])
+def test_divided_difference_table_vs_high_precision(kappa, m):
+    """The xi-variable table (used when Algorithm 1's series is too long) against the 120-digit
+    table in the z variable (Eq. Léja7)."""
+    xi = leja.fast_leja_points(m + 1)
+    c, g = (1.0 + kappa) / 2, (kappa - 1.0) / 4
+    d = divdiff.divided_differences_table(xi, c, g)
+    ref = pins.hp_scaled_divided_differences(1.0, kappa, xi)
+    assert np.max(np.abs(d - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_divided_difference_method_choice():
+    # config-3-like conditioning stays on Algorithm 1, config-5-like switches to the table
+    _, _, _, d3, p3 = logdet.newton_leja_setup(1.0, 8080.0, 80)
+    assert p3 > 0
+    _, _, _, d5, p5 = logdet.newton_leja_setup(1.0, 2.5e6, 150)
+    assert p5 == 0
+    # s = lambda_max / 2 has q = 1: always the table, and the same coefficients as s = c
+    _, _, _, dh, ph = logdet.newton_leja_setup(1.0, 50.0, 40, s_mode="half_lmax")
+    _, _, _, dc, pc = logdet.newton_leja_setup(1.0, 50.0, 40)
+    assert ph == 0 and pc > 0
+    assert np.max(np.abs(dh - dc)) <= 1e-13 * np.max(np.abs(dc))
