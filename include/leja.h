@@ -95,6 +95,8 @@ typedef struct {
     int threads_per_block;     /* 0 = autotuned; otherwise CTA size of the step kernels          */
     int ckpt_stride;           /* backward: W_j checkpoint stride; 0 = ceil(sqrt(m))            */
     int use_graph;             /* 1: capture the m-step passes in a CUDA graph (default 1)       */
+    int64_t timeout_cycles;    /* batched launch: clock cycles a dependency wait may spin before
+                                  the call fails with LL_ERR_TIMEOUT; 0 = about 2 s              */
 } ll_options;
 
 typedef struct ll_handle ll_handle;

@@ -6,6 +6,6 @@ the library; the first call does, and raises ImportError if it has not been buil
 """
 from .api import (DeviceCSR, Handle, LejaError, ll_apply_poly, ll_divided_differences,  # noqa: F401
                   ll_gershgorin, ll_leja_points, ll_logdet_backward, ll_logdet_forward,
-                  ll_kept_basis, ll_logdet_forward_host, ll_param_grad, ll_power_lmax, ll_power_lmax_noalloc, ll_probes, logdet_leja,
+                  ll_kept_basis, ll_logdet_batched, ll_logdet_forward_host, ll_param_grad, ll_power_lmax, ll_power_lmax_noalloc, ll_probes, logdet_leja,
                   options)
 from .autograd import LejaLogdet, logdet  # noqa: F401

@@ -39,7 +39,8 @@ class ll_options(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("probes", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("probe_kind", ctypes.c_int), ("precision", ctypes.c_int), ("sval_mode", ctypes.c_int),
                 ("keep_for_backward", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
-                ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("timeout_cycles", ctypes.c_int64)]
 
 
 class ll_info(ctypes.Structure):

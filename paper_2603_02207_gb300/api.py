@@ -114,7 +114,7 @@ def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
 def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str = "rademacher",
             precision: str = "df64", sval_mode: int = LL_SVAL_CENTER, keep_for_backward: bool = False,
             rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
-            use_graph: bool = True) -> _ffi.ll_options:
+            use_graph: bool = True, timeout_cycles: int = 0) -> _ffi.ll_options:
     o = _ffi.ll_options()
     _ffi.load().ll_default_options(ctypes.byref(o))
     o.degree = degree
@@ -128,6 +128,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
     o.threads_per_block = threads_per_block
     o.ckpt_stride = ckpt_stride
     o.use_graph = int(use_graph)
+    o.timeout_cycles = timeout_cycles
     return o
 
 
@@ -250,6 +251,21 @@ def ll_kept_basis(h: Handle, stream=None):
     out = torch.empty((n.value, kq.value + kg.value), dtype=torch.float64, device="cuda")
     h.check(h._lib.ll_kept_basis(h.ptr, out.data_ptr(), kq.value + kg.value, None, None, None, _stream_ptr(stream)))
     return out[:, :kq.value], out[:, kq.value:]
+
+
+def ll_logdet_batched(h: Handle, mats: list, bounds: list, opts: _ffi.ll_options, degrees=None, stream=None):
+    """Independent estimates of several device CSR matrices (matrix i uses seed + i) with one
+    persistent launch per pass."""
+    count = len(mats)
+    arr = (_ffi.ll_csr * count)(*[A.c() for A in mats])
+    barr = (_ffi.ll_bounds * count)(*[_ffi.ll_bounds(lo, hi) for lo, hi in bounds])
+    deg = None
+    if degrees is not None:
+        deg = (ctypes.c_int * count)(*[int(x) for x in degrees])
+    out = np.zeros(count, dtype=np.float64)
+    h.check(h._lib.ll_logdet_batched(h.ptr, arr, barr, count, ctypes.byref(opts), deg,
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream)))
+    return out
 
 
 def logdet_leja(A: DeviceCSR, bounds: tuple[float, float], degree: int, probes: int, seed: int,

@@ -257,6 +257,7 @@ void ll_default_options(ll_options* o) {
     o->threads_per_block = 0;
     o->ckpt_stride = 0;
     o->use_graph = 1;
+    o->timeout_cycles = 0;
 }
 
 ll_status ll_leja_points(int count, double* xi_out) {
@@ -707,11 +708,250 @@ ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* d
     return LL_OK;
 }
 
-ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b, int count, const ll_options* opts,
+ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* bnd, int count, const ll_options* opts,
                             const int* degrees, double* estimates, void* stream) {
-    if (!h) return LL_ERR_INVALID_ARG;
-    (void)mats; (void)b; (void)count; (void)opts; (void)degrees; (void)estimates; (void)stream;
-    return fail(h, LL_ERR_UNSUPPORTED, "batched launch not built yet");
+    if (!h || !opts || count < 0 || (count > 0 && (!mats || !bnd || !estimates))) return LL_ERR_INVALID_ARG;
+    if (count == 0) return LL_OK;
+    const ll_options& o = *opts;
+    if (o.probes <= 0 || o.probes % 3 != 0) return fail(h, LL_ERR_INVALID_ARG, "probes must be a positive multiple of 3");
+    if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
+    if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->launches = 0;
+    h->kept = false;
+    const int kg = o.probes / 3;
+    const int prec = o.precision;
+    const int wt = w_type_of(prec), pt = p_type_of(prec);
+    const size_t ew = elem_size(wt), ep = elem_size(pt);
+    for (int i = 0; i < count; ++i) {
+        ll_status st = check_csr_args(h, &mats[i]);
+        if (st != LL_OK) return st;
+        if ((st = check_bounds(h, bnd[i])) != LL_OK) return st;
+        if (mats[i].n <= kg) return fail(h, LL_ERR_UNSUPPORTED, "batched matrices need more rows than m_vec / 3");
+        if (degrees && degrees[i] < 1) return fail(h, LL_ERR_INVALID_ARG, "degree must be >= 1");
+    }
+    if (2 * kg > 512 || kg > 96) return fail(h, LL_ERR_UNSUPPORTED, "m_vec / 3 above 96 is not supported");
+    const int kq = kg, b1 = kq, b2 = kq + kg, l1 = even_ld(b1), l2 = even_ld(b2);
+
+    // validation of every CSR (one synchronisation)
+    {
+        WS(flags, int*, "bt_flags", (size_t)2 * count * sizeof(int));
+        LL_CK(cudaMemsetAsync(flags, 0, (size_t)2 * count * sizeof(int), s));
+        for (int i = 0; i < count; ++i)
+            if (mats[i].n > 0) { LL_CK(launch_validate_csr(mats[i].rowptr, mats[i].colind, (int)mats[i].n, mats[i].nnz, flags + 2 * i, s)); h->launches++; }
+        std::vector<int> hf(2 * count);
+        LL_CK(cudaMemcpyAsync(hf.data(), flags, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+        LL_CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < count; ++i)
+            if (hf[2 * i]) return fail(h, LL_ERR_BAD_CSR, "invalid CSR in batch entry " + std::to_string(i));
+    }
+    // host set-up per matrix: sigma, interval, degree, coefficients
+    struct Host { double sigma, c, gamma; int m; std::vector<double> d, coef; };
+    std::vector<Host> hs(count);
+    int max_m = 0;
+    for (int i = 0; i < count; ++i) {
+        Host& x = hs[i];
+        x.sigma = sigma_of(bnd[i].lmin);
+        const double lt = bnd[i].lmin / x.sigma, ut = bnd[i].lmax / x.sigma;
+        x.m = degrees ? degrees[i] : degree_from_bounds(lt, ut);
+        x.c = (lt + ut) / 2.0;
+        x.gamma = (ut - lt) / 4.0;
+        x.d.resize(x.m + 1);
+        if (scaled_divided_differences(lt, ut, x.m, o.sval_mode, x.d.data()) < 0)
+            return fail(h, LL_ERR_DD_NOT_CONVERGED, "Algorithm 1 did not converge for batch entry " + std::to_string(i));
+        std::vector<double> xi(x.m + 1);
+        leja_points(x.m + 1, xi.data());
+        x.coef.resize(2 * (x.m + 1));
+        for (int j = 0; j <= x.m; ++j) { x.coef[2 * j] = -(x.c / x.gamma + xi[j]); x.coef[2 * j + 1] = x.d[j]; }
+        max_m = std::max(max_m, x.m);
+    }
+    // order by degree (descending): the matrices active at a step are then a prefix
+    std::vector<int> ord(count);
+    for (int i = 0; i < count; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hs[a].m > hs[b].m; });
+
+    BatchParams bp1{}, bp2{};
+    size_t smem1 = 0, smem2 = 0;
+    double avg = 0.0, tot_n = 0.0;
+    for (int i = 0; i < count; ++i) { avg += (double)mats[i].nnz; tot_n += (double)mats[i].n; }
+    avg /= tot_n;
+    plan_batched(b1, avg, bp1, &smem1);
+    plan_batched(b2, avg, bp2, &smem2);
+
+    // one workspace for every per-matrix buffer (256-byte aligned regions)
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    struct Off { size_t vals, S, G, P, wa, wb, basis, q1, V, part, dots, coef; int T1, T2; };
+    std::vector<Off> off(count);
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const size_t n = (size_t)mats[i].n, nnz = (size_t)mats[i].nnz;
+        Off& f = off[i];
+        f.T1 = (int)((n + bp1.R - 1) / bp1.R);
+        f.T2 = (int)((n + bp2.R - 1) / bp2.R);
+        f.vals = total; total += al(nnz * ew);
+        f.S = total; total += al(n * l1 * ew);
+        f.G = total; total += al(n * kg * sizeof(double));
+        f.P = total; total += al(n * l1 * ep);
+        f.wa = total; total += al(n * l2 * ew);
+        f.wb = total; total += al(n * l2 * ew);
+        f.basis = total; total += al(n * l2 * sizeof(double));
+        f.q1 = total; total += al(n * kq * sizeof(double));
+        f.V = total; total += al(n * l2 * ew);
+        f.part = total; total += al((size_t)2 * std::max(f.T1, f.T2) * b2 * sizeof(double));
+        f.dots = total; total += al((size_t)(hs[i].m + 1) * b2 * sizeof(double));
+        f.coef = total; total += al((size_t)2 * (hs[i].m + 1) * sizeof(double));
+    }
+    WS(base, char*, "bt_all", total);
+    const int ggrid = h->sm_count * 2;
+    const size_t gp = std::max(gram_partials_doubles(kq, kq, true, ggrid), gram_partials_doubles(kq, kg, false, ggrid));
+    WS(gpart, double*, "bt_gram_partials", gp * sizeof(double));
+    WS(gticket, unsigned int*, "bt_gram_ticket", sizeof(unsigned int));
+    WS(gram, double*, "bt_gram", (size_t)kq * kg * sizeof(double));
+    WS(rinv, double*, "bt_rinv", (size_t)kq * kq * sizeof(double));
+    WS(qrstat, int*, "bt_qr_status", (size_t)count * sizeof(int));
+    WS(ctr, unsigned long long*, "bt_counters", (size_t)(2 * count + 8) * sizeof(unsigned long long));
+    WS(dmats, BatchMat*, "bt_mats", (size_t)2 * count * sizeof(BatchMat));
+    WS(dtab, int*, "bt_tables", (size_t)2 * (2 * (max_m + 1) + count + 1) * sizeof(int));
+
+    // descriptors and item tables of both passes
+    std::vector<BatchMat> hm(2 * count);
+    std::vector<int> tabs(2 * (2 * (max_m + 1) + count + 1));
+    for (int pass = 0; pass < 2; ++pass) {
+        int* t_off = tabs.data() + pass * (2 * (max_m + 1) + count + 1);
+        int* t_act = t_off + (max_m + 1);
+        int* t_pre = t_act + (max_m + 1);
+        t_pre[0] = 0;
+        for (int q = 0; q < count; ++q) {
+            const int i = ord[q];
+            const Off& f = off[i];
+            BatchMat& M = hm[pass * count + q];
+            M.rowptr = mats[i].rowptr;
+            M.colind = mats[i].colind;
+            M.vals = base + f.vals;
+            M.w0 = base + (pass == 0 ? f.S : f.V);
+            M.wa = base + f.wa;
+            M.wb = base + f.wb;
+            M.p = base + f.P;
+            M.partials = (double*)(base + f.part);
+            M.dots = (double*)(base + f.dots);
+            M.coef = (const double*)(base + f.coef);
+            M.n = (int)mats[i].n;
+            M.T = pass == 0 ? f.T1 : f.T2;
+            M.m = hs[i].m;
+            t_pre[q + 1] = t_pre[q] + M.T;
+        }
+        int acc = 0;
+        for (int j = 0; j < max_m; ++j) {
+            int a = 0;
+            while (a < count && hs[ord[a]].m > j) ++a;
+            t_act[j] = a;
+            t_off[j] = acc;
+            acc += t_pre[a];
+        }
+        t_off[max_m] = acc;
+        BatchParams& bp = pass == 0 ? bp1 : bp2;
+        bp.mats = dmats + pass * count;
+        bp.step_off = dtab + pass * (2 * (max_m + 1) + count + 1);
+        bp.step_active = bp.step_off + (max_m + 1);
+        bp.tile_prefix = bp.step_active + (max_m + 1);
+        bp.ticket = (unsigned int*)(ctr + 2 * count) + pass;
+        bp.error = (int*)(ctr + 2 * count + 2);
+        bp.arrived = ctr;
+        bp.released = ctr + count;
+        bp.spin_budget = o.timeout_cycles > 0 ? o.timeout_cycles : 4000000000LL;   // default: about 2 s at 2 GHz
+        bp.ld = pass == 0 ? l1 : l2;
+        bp.total_items = acc;
+        bp.max_m = max_m;
+    }
+    LL_CK(cudaMemcpyAsync(dmats, hm.data(), hm.size() * sizeof(BatchMat), cudaMemcpyHostToDevice, s));
+    LL_CK(cudaMemcpyAsync(dtab, tabs.data(), tabs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < count; ++i)
+        LL_CK(cudaMemcpyAsync(base + off[i].coef, hs[i].coef.data(), hs[i].coef.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+
+    LL_CK(cudaEventRecord(h->ev[0], s));
+    LL_CK(cudaMemsetAsync(ctr, 0, (size_t)(2 * count + 8) * sizeof(unsigned long long), s));
+    LL_CK(cudaMemsetAsync(qrstat, 0, (size_t)count * sizeof(int), s));
+    LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), s));
+    for (int i = 0; i < count; ++i) {
+        const Off& f = off[i];
+        const int n = (int)mats[i].n;
+        const uint64_t seed = o.seed + (uint64_t)i;
+        LL_CK(launch_prepare_values(mats[i].values, mats[i].dtype, mats[i].nnz, 1.0 / (hs[i].sigma * hs[i].gamma), prec, base + f.vals, s));
+        LL_CK(launch_probes(wt, o.probe_kind, seed, LL_STREAM_S, n, kq, l1, base + f.S, l1, s));
+        LL_CK(launch_probes(T_F64, o.probe_kind, seed, LL_STREAM_G, n, kg, kg, base + f.G, kg, s));
+        h->launches += 3;
+    }
+    int per_sm = 2;
+    const int grid1 = h->sm_count * per_sm, grid2 = h->sm_count * per_sm;
+    LL_CK(cudaEventRecord(h->ev[1], s));
+    // pass 1 of every matrix: one persistent launch
+    LL_CK(launch_batched(prec, MODE_ACCUM, bp1, grid1, smem1, s));
+    h->launches++;
+    LL_CK(cudaEventRecord(h->ev[2], s));
+    // CholeskyQR2 and deflation per matrix
+    for (int i = 0; i < count; ++i) {
+        const Off& f = off[i];
+        const int n = (int)mats[i].n;
+        void* P = base + f.P;
+        double* q1 = (double*)(base + f.q1);
+        double* basis = (double*)(base + f.basis);
+        double* G = (double*)(base + f.G);
+        void* V = base + f.V;
+        LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
+        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat + i, s));
+        LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv, q1, kq, T_F64, nullptr, 0, s));
+        LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
+        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat + i, s));
+        LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, l2, wt, V, l2, s));
+        LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, s));
+        LL_CK(launch_project(basis, l2, kq, G, kg, kg, gram, n, basis + kq, l2, wt, V, l2, (b2 & 1), kq, s));
+        h->launches += 8;
+    }
+    LL_CK(cudaEventRecord(h->ev[3], s));
+    // pass 2 of every matrix: one persistent launch (arrival / release counters start at zero)
+    LL_CK(cudaMemsetAsync(ctr, 0, (size_t)2 * count * sizeof(unsigned long long), s));
+    LL_CK(launch_batched(prec, MODE_DOT, bp2, grid2, smem2, s));
+    h->launches++;
+    LL_CK(cudaEventRecord(h->ev[4], s));
+
+    int herr = 0;
+    std::vector<int> hqr(count);
+    LL_CK(cudaMemcpyAsync(&herr, ctr + 2 * count + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaMemcpyAsync(hqr.data(), qrstat, count * sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<std::vector<double>> hd(count);
+    for (int i = 0; i < count; ++i) {
+        hd[i].resize((size_t)(hs[i].m + 1) * b2);
+        LL_CK(cudaMemcpyAsync(hd[i].data(), base + off[i].dots, hd[i].size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    LL_CK(cudaStreamSynchronize(s));
+    if (herr) return fail(h, LL_ERR_TIMEOUT, "batched launch: a bounded wait ran out");
+    for (int i = 0; i < count; ++i)
+        if (hqr[i]) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2 breakdown in batch entry " + std::to_string(i));
+    std::vector<double> est(count);
+    for (int i = 0; i < count; ++i) {
+        double tq = 0.0, tr = 0.0;
+        for (int j = 0; j <= hs[i].m; ++j) {
+            double sq = 0.0, sr = 0.0;
+            for (int col = 0; col < kq; ++col) sq += hd[i][(size_t)j * b2 + col];
+            for (int col = kq; col < b2; ++col) sr += hd[i][(size_t)j * b2 + col];
+            tq += hs[i].d[j] * sq;
+            tr += hs[i].d[j] * sr;
+        }
+        tr /= (double)kg;
+        if (!std::isfinite(tq) || !std::isfinite(tr)) return fail(h, LL_ERR_NONFINITE, "non-finite trace in batch entry " + std::to_string(i));
+        est[i] = (double)mats[i].n * std::log(hs[i].sigma) + tq + tr;
+    }
+    for (int i = 0; i < count; ++i) estimates[i] = est[i];
+    ll_info& I = h->info;
+    I = ll_info{};
+    I.k = kq;
+    I.kernel_launches = h->launches;
+    cudaEventElapsedTime(&I.ms_probes, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&I.ms_pass1, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&I.ms_pass2, h->ev[3], h->ev[4]);
+    cudaEventElapsedTime(&I.ms_total, h->ev[0], h->ev[4]);
+    return LL_OK;
 }
 
 ll_status ll_get_info(const ll_handle* h, ll_info* out) {

@@ -118,6 +118,38 @@ cudaError_t launch_project(const double* Q, long long ldq, int k, const double* 
                            const double* C, int n, double* out64, long long ld64, int t2, void* out2,
                            long long ld2, int zero_pad, int col2, cudaStream_t s);
 
+// ---- batched passes (many matrices, one persistent launch per pass) ----------------------------
+struct BatchMat {
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const void* vals;         // prepared values (storage type of the precision)
+    const void* w0;           // W_0: the probe block S (pass 1) or V = [Q | G'] (pass 2)
+    void* wa;                 // ping-pong blocks
+    void* wb;
+    void* p;                  // pass 1: P (P storage type), leading dimension as W
+    double* partials;         // pass 2: 2 * T * b per-tile trace partials
+    double* dots;             // pass 2: (m + 1) * b traces
+    const double* coef;       // (beta_j, d_j) for j = 0..m
+    int n, T, m;
+};
+
+struct BatchParams {
+    const BatchMat* mats;          // sorted by degree, descending
+    const int* step_off;           // first item of each step (max_m + 1 entries)
+    const int* step_active;        // matrices still active at each step (a prefix)
+    const int* tile_prefix;        // tile prefix sums over the sorted matrices (count + 1)
+    unsigned int* ticket;          // zero-initialised item counter
+    int* error;                    // set when a bounded wait runs out
+    unsigned long long* arrived;   // per matrix: tiles finished
+    unsigned long long* released;  // per matrix: tiles of fully completed steps
+    long long spin_budget;         // clock64 cycles a wait may spin
+    long long ld;                  // leading dimension (columns, even) of every block
+    int total_items, max_m, tp, rl, rpt, R, b, smem_cap;
+};
+
+void plan_batched(int b, double avg_nnz_per_row, BatchParams& bp, size_t* smem);
+cudaError_t launch_batched(int precision, int mode, const BatchParams& bp, int grid, size_t smem, cudaStream_t s);
+
 // element types used by the typed helpers above; T_DF64 blocks are double-float in column pairs
 enum ElemType { T_F64 = 0, T_F32 = 1, T_DF64 = 2 };
 // even leading dimension of a block of b columns

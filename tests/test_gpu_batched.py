@@ -1,0 +1,77 @@
+"""Batched persistent launch (many GMRFs of uneven size) against single-matrix estimates and the
+oracle (needs a GB300)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import logdet as O
+from synth import gmrf_batch_params, laplacian_2d, random_spd
+from tests.gpu_util import TOL, lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    return lib()
+
+
+@pytest.fixture(scope="module")
+def h(L):
+    return L.Handle()
+
+
+def _batch(scale=8, count=9, seed=2):
+    params = gmrf_batch_params(count=count, seed=seed, side_lo=64 // scale, side_hi=512 // scale)
+    mats = [laplacian_2d(side, tau) for side, tau in params]
+    bounds = [(tau, 8.0 + tau) for _, tau in params]
+    return mats, bounds
+
+
+@pytest.mark.parametrize("prec", ["df64", "f32", "f64"])
+def test_batched_matches_oracle(L, h, prec):
+    mats, bounds = _batch()
+    dm = [L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64") for A in mats]
+    opts = L.options(probes=30, seed=5, precision=prec)
+    got = L.ll_logdet_batched(h, dm, bounds, opts)
+    for i, (A, (lo, hi)) in enumerate(zip(mats, bounds)):
+        sigma = O.sigma_of(lo)
+        m = O.degree_from_bounds(lo / sigma, hi / sigma)
+        want = O.logdet_leja(A, lo, hi, m, 30, 5 + i)["estimate"]
+        assert abs(got[i] - want) / abs(want) < TOL[prec], (i, got[i], want)
+
+
+def test_batched_matches_single_matrix_calls(L, h):
+    mats, bounds = _batch(scale=4, count=12, seed=7)
+    dm = [L.DeviceCSR.from_host(A) for A in mats]
+    degrees = [10 + 7 * i for i in range(len(mats))]
+    got = L.ll_logdet_batched(h, dm, bounds, L.options(probes=24, seed=1, precision="df64"), degrees=degrees)
+    for i, A in enumerate(dm):
+        single = L.ll_logdet_forward(h, A, *bounds[i], L.options(degree=degrees[i], probes=24, seed=1 + i, precision="df64"))
+        assert got[i] == pytest.approx(single, rel=1e-12)
+
+
+def test_batched_irregular_matrices(L, h):
+    mats = [random_spd(n, seed=n, empty_rows=2, dense_row=(n % 2 == 0)) for n in (300, 517, 1000, 77)]
+    bounds = []
+    for A in mats:
+        lo, hi = O.gershgorin(A)
+        bounds.append((max(lo, 0.05), hi))
+    dm = [L.DeviceCSR.from_host(A) for A in mats]
+    got = L.ll_logdet_batched(h, dm, bounds, L.options(probes=15, seed=3, precision="df64"), degrees=[20, 25, 30, 35])
+    for i, A in enumerate(mats):
+        want = O.logdet_leja(A, *bounds[i], [20, 25, 30, 35][i], 15, 3 + i)["estimate"]
+        assert abs(got[i] - want) / abs(want) < 1e-10
+
+
+def test_batched_wait_timeout_is_reported(L, h):
+    """A zero spin budget makes every dependency wait that is not already satisfied give up at
+    once: the call reports LL_ERR_TIMEOUT, nothing hangs, and the handle keeps working."""
+    mats, bounds = _batch(scale=2, count=6, seed=3)
+    dm = [L.DeviceCSR.from_host(A) for A in mats]
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_logdet_batched(h, dm, bounds, L.options(probes=30, seed=1, timeout_cycles=1))
+    assert ei.value.name == "LL_ERR_TIMEOUT"
+    est = L.ll_logdet_batched(h, dm[:2], bounds[:2], L.options(probes=30, seed=1))
+    assert np.all(np.isfinite(est))
