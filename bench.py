@@ -180,6 +180,109 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def time_calls(fn, reps: int, warmup: int = 1):
+    """Device time of `reps` calls of fn() (CUDA events on the current stream), in ms per call."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def workload_config1(L, h):
+    """2-D Laplacian + 0.1 I on 100 x 100, bounds [0.1, 8.1], 40 Léja points, 30 Rademacher
+    probes from seed 0: a latency-bound estimate (n = 10,000)."""
+    from synth import laplacian_2d
+    from tests.pins import logdet_laplacian_2d
+    A = laplacian_2d(100, 0.1)
+    dA = L.DeviceCSR.from_host(A)
+    out = {}
+    for prec in ("df64", "f32"):
+        opts = L.options(degree=39, probes=30, seed=0, precision=prec)
+        ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, 0.1, 8.1, opts), 20, 3)
+        exact = logdet_laplacian_2d(100, 0.1)
+        out[prec] = {"ms_per_estimate": ms, "estimate": est, "rel_err_vs_exact": abs(est - exact) / exact,
+                     "launches": h.info()["kernel_launches"]}
+    return {"workload": "L2D+0.1I 100^2 (n=10000, nnz=49600), degree 39, 30 Rademacher probes, seed 0", **out}
+
+
+def workload_config3(L, h, grid: int = 1024, degree: int = 80):
+    """Matérn GMRF tau (kappa^2 I + L_2D)^2 on grid x grid (13-point stencil), kappa = 0.3,
+    tau = 1, degree 80, 60 Gaussian probes: forward estimate, adjoint (value gradients) and the
+    chain to (kappa, tau), against the closed forms."""
+    import numpy as np
+    import torch
+    from synth import matern_2d, matern_2d_derivatives
+    from tests.pins import dlogdet_matern_2d, logdet_matern_2d
+    kappa, tau = 0.3, 1.0
+    A = matern_2d(grid, kappa, tau)
+    dk, dt = matern_2d_derivatives(grid, kappa, tau)
+    from oracle.logdet import gershgorin  # bounds only (host-side input preparation)
+    lmax = gershgorin(A)[1]
+    lmin = tau * kappa ** 4
+    dA = L.DeviceCSR.from_host(A)
+    dv = torch.as_tensor(np.stack([dk, dt])).cuda()
+    exact = logdet_matern_2d(grid, kappa, tau)
+    ex_k, ex_t = dlogdet_matern_2d(grid, kappa, tau)
+    out = {}
+    for prec in ("df64", "f32"):
+        opts = L.options(degree=degree, probes=60, seed=0, precision=prec, probe_kind="gaussian", keep_for_backward=True)
+        ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), 2, 1)
+        inf = h.info()
+        ms_b, g = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 2, 1)
+        th = L.ll_param_grad(h, g, dv)
+        out[prec] = {"ms_forward": ms_f, "ms_backward": ms_b, "ms_forward_plus_gradient": ms_f + ms_b,
+                     "estimate": est, "rel_err_vs_exact": abs(est - exact) / abs(exact),
+                     "dlogdet_dkappa": th[0], "dlogdet_dtau": th[1],
+                     "rel_err_dkappa": abs(th[0] - ex_k) / abs(ex_k), "rel_err_dtau": abs(th[1] - ex_t) / abs(ex_t),
+                     "forward_phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
+    return {"workload": f"Matern tau(kappa^2 I + L2D)^2 {grid}^2 (n={A.n}, nnz={A.nnz}), kappa={kappa}, tau={tau}, "
+                        f"bounds [{lmin}, {lmax:.4f}], degree {degree}, 60 Gaussian probes, seed 0", **out}
+
+
+def workload_config4(L, h, count: int = 64):
+    """64 GMRFs L_2D + tau_i I, sides log-uniform in [64, 512], tau_i ~ U[0.01, 1] (seed 2), degree
+    from the bound ratio, 30 probes each: one persistent launch per pass vs one call per matrix."""
+    from synth import gmrf_batch_params, laplacian_2d
+    from tests.pins import logdet_laplacian_2d
+    params = gmrf_batch_params(count=count, seed=2)
+    mats = [laplacian_2d(side, t) for side, t in params]
+    bounds = [(t, 8.0 + t) for _, t in params]
+    out = {"n_total": sum(A.n for A in mats), "nnz_total": sum(A.nnz for A in mats)}
+    for prec in ("df64", "f32"):
+        dm = [L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64") for A in mats]
+        opts = L.options(probes=30, seed=2, precision=prec)
+        ms_b, est = time_calls(lambda: L.ll_logdet_batched(h, dm, bounds, opts), 2, 1)
+        inf = h.info()
+        import math as _m
+
+        def one_by_one():
+            res = []
+            for i, A in enumerate(dm):
+                lo, hi = bounds[i]
+                sg = lo if lo < 1 else 1.0
+                kap = (hi / sg) / (lo / sg)
+                rho = (_m.sqrt(kap) + 1) / (_m.sqrt(kap) - 1)
+                m = max(10, min(250, _m.ceil(_m.log(1e6) / _m.log(rho))))
+                res.append(L.ll_logdet_forward(h, A, lo, hi, L.options(degree=m, probes=30, seed=2 + i, precision=prec)))
+            return res
+        ms_s, est_s = time_calls(one_by_one, 1, 1)
+        exact = [logdet_laplacian_2d(side, t) for side, t in params]
+        errs = [abs(e - x) / abs(x) for e, x in zip(est, exact)]
+        out[prec] = {"ms_batched": ms_b, "ms_one_call_per_matrix": ms_s, "speedup": ms_s / ms_b,
+                     "max_rel_diff_batched_vs_single": max(abs(a - b) / abs(b) for a, b in zip(est, est_s)),
+                     "max_rel_err_vs_exact": max(errs), "median_rel_err_vs_exact": sorted(errs)[len(errs) // 2],
+                     "phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
+    return {"workload": f"{count} x (L2D + tau_i I), sides log-uniform [64,512], tau U[0.01,1], seed 2, 30 probes", **out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +296,8 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID_N, help="side of the 3-D grid (128 = the benchmark workload; "
                     "smaller sides are for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workloads", default="c1,c3,c4",
+                    help="extra workloads reported beside the headline (comma list of c1,c3,c4; '' for none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -309,6 +414,10 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
+    extra = {}
+    for w in [x for x in args.workloads.split(",") if x]:
+        fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4}[w]
+        extra[w] = fn(L, h)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
     from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only
     exact = logdet_laplacian_3d(args.grid, SHIFT)
@@ -327,7 +436,7 @@ def main():
         "phase_ms": {"probes": info["ms_probes"], "pass1": info["ms_pass1"], "qr": info["ms_qr"],
                      "pass2": info["ms_pass2"], "total": info["ms_total"]},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": r["launches"], "clocks": r["clocks"], "variants": variants,
+        "gpu_launches": r["launches"], "clocks": r["clocks"], "variants": variants, "workloads": extra,
     }
     print(json.dumps(line))
     if world > 1:
