@@ -46,7 +46,7 @@ ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A,
 # the current kernel on the 96^3 Laplacian (launch 5 of the 96^3 bench run): 1.4777 GB over
 # 884,736 rows. Traffic grows in proportion to the rows of a stencil matrix, so the full-size value
 # is this figure times n. Only valid for the DF64 trace step as captured.
-TRACE_STEP_DRAM_BYTES_PER_ROW = {"df64": 1.477654528e9 / 884736}
+TRACE_STEP_DRAM_BYTES_PER_ROW = {("gather", "df64"): 1.477654528e9 / 884736}
 
 
 def step_bytes(n: int, nnz: int, b: int, prec: str, mode: str) -> int:
@@ -224,10 +224,9 @@ def workload_config3(L, h, grid: int = 1024, degree: int = 80):
     kappa, tau = 0.3, 1.0
     A = matern_2d(grid, kappa, tau)
     dk, dt = matern_2d_derivatives(grid, kappa, tau)
-    from oracle.logdet import gershgorin  # bounds only (host-side input preparation)
-    lmax = gershgorin(A)[1]
-    lmin = tau * kappa ** 4
     dA = L.DeviceCSR.from_host(A)
+    lmax = L.ll_gershgorin(h, dA)[1]
+    lmin = tau * kappa ** 4
     dv = torch.as_tensor(np.stack([dk, dt])).cuda()
     exact = logdet_matern_2d(grid, kappa, tau)
     ex_k, ex_t = dlogdet_matern_2d(grid, kappa, tau)
@@ -283,6 +282,42 @@ def workload_config4(L, h, count: int = 64):
     return {"workload": f"{count} x (L2D + tau_i I), sides log-uniform [64,512], tau U[0.01,1], seed 2, 30 probes", **out}
 
 
+def workload_config5(L, h, log2n: int = 22, degree: int = 150, probes: int = 120):
+    """Weighted graph Laplacian + 1e-2 I of a power-law (Chung-Lu) graph, n = 2^22, mean degree 16,
+    exponent 2.3, weights U[0.5, 1.5], seed 3. Bounds from Gershgorin plus 20 power iterations
+    (lmax = min(Gershgorin, 1.05 x Rayleigh quotient), lmin = 0.01); degree 150, Hutch++ 120
+    probes. FP32-mixed throughput and its difference from the plain FP64 form on the same GPU (no
+    closed form exists at this size)."""
+    import time as _t
+    from synth import powerlaw_laplacian
+    t0 = _t.perf_counter()
+    A = powerlaw_laplacian(1 << log2n, seed=3, device="cuda")
+    t_gen = _t.perf_counter() - t0
+    d64 = L.DeviceCSR.from_host(A, "f64")
+    d32 = L.DeviceCSR.from_host(A, "f32")
+    glo, ghi = L.ll_gershgorin(h, d64)
+    lp = L.ll_power_lmax(h, d64, iters=20, seed=3)
+    lmin, lmax = 0.01, min(ghi, 1.05 * lp)
+    n, nnz, k = A.n, A.nnz, probes // 3
+    out = {"n": n, "nnz": nnz, "max_row_nnz": int((A.rowptr[1:] - A.rowptr[:-1]).max()), "generate_s": t_gen,
+           "gershgorin": [glo, ghi], "lambda_power": lp, "bounds": [lmin, lmax]}
+    for prec, dA, reps in (("f32", d32, 2), ("f64", d64, 1)):
+        opts = L.options(degree=degree, probes=probes, seed=3, precision=prec)
+        ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), reps, 1)
+        inf = h.info()
+        b2 = step_bytes(n, nnz, 2 * k, prec, "dot")
+        b1 = step_bytes(n, nnz, k, prec, "accum")
+        out[prec] = {"ms_per_estimate": ms, "estimate": est, "GBps_estimate": estimate_bytes(n, nnz, k, degree, prec) / (ms / 1e3) / 1e9,
+                     "pass1_launch_GBps": b1 / (inf["ms_pass1"] / degree / 1e3) / 1e9,
+                     "pass2_launch_GBps": b2 / (inf["ms_pass2"] / degree / 1e3) / 1e9,
+                     "kernels": [inf["kernel_pass1"], inf["kernel_pass2"]],
+                     "phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
+    out["rel_diff_f32_vs_f64"] = abs(out["f32"]["estimate"] - out["f64"]["estimate"]) / abs(out["f64"]["estimate"])
+    out["workload"] = (f"power-law Laplacian + 1e-2 I, n=2^{log2n} ({n}), nnz={nnz}, mean degree 16, exponent 2.3, "
+                       f"seed 3, degree {degree}, {probes} probes")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,7 +332,7 @@ def main():
                     "smaller sides are for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workloads", default="c1,c3,c4",
-                    help="extra workloads reported beside the headline (comma list of c1,c3,c4; '' for none)")
+                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5; '' for none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -366,8 +401,11 @@ def main():
     b_p2 = step_bytes(n, nnz, 2 * k, prec, "dot")
     b_p1 = step_bytes(n, nnz, k, prec, "accum")
     achieved = b_p2 / (p2_launch_ms / 1e3) / 1e9
-    per_row = TRACE_STEP_DRAM_BYTES_PER_ROW.get(prec)
-    roof = {"kernel": f"k_leja_step<{prec},DOT> (b={2 * k})", "bound": "hbm", "achieved": achieved,
+    kname = {L.LL_KERNEL_TMA: "tma", L.LL_KERNEL_GATHER: "gather"}.get(r["info"]["kernel_pass2"], "gather")
+    per_row = TRACE_STEP_DRAM_BYTES_PER_ROW.get((kname, prec))
+    kfun = "k_leja_tma" if kname == "tma" else "k_leja_step"
+    roof = {"kernel": f"{kfun}<{prec},DOT> (b={2 * k}, {r['info']['threads_pass2']} threads/CTA)", "bound": "hbm",
+            "achieved": achieved,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "traffic": per_row * n if per_row else None,
             "traffic_source": "ncu dram__bytes_read+write of one launch at 96^3, scaled by rows" if per_row else None,
@@ -416,7 +454,7 @@ def main():
         return
     extra = {}
     for w in [x for x in args.workloads.split(",") if x]:
-        fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4}[w]
+        fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4, "c5": workload_config5}[w]
         extra[w] = fn(L, h)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
     from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only

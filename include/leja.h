@@ -67,6 +67,15 @@ enum { LL_PROBE_RADEMACHER = 0, LL_PROBE_GAUSSIAN = 1 };
 /* s_val of Algorithm 1: the Lemma 3.1 optimum c = (lmin+lmax)/2, or lmax/2. */
 enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
 
+/* Step kernel of the m-step passes:
+ *   LL_KERNEL_AUTO    autotuned: the kernel and its launch shape are timed once per
+ *                     (precision, pass, n, nnz, block width) on the handle and the fastest is kept;
+ *   LL_KERNEL_GATHER  neighbour rows gathered into registers by each thread (k_leja_step);
+ *   LL_KERNEL_TMA     neighbour rows gathered into shared memory by TMA (tile::gather4) in a
+ *                     multi-stage mbarrier pipeline (k_leja_tma); falls back to LL_KERNEL_GATHER
+ *                     when a block row is wider than 256 elements.                               */
+enum { LL_KERNEL_AUTO = 0, LL_KERNEL_GATHER = 1, LL_KERNEL_TMA = 2 };
+
 /* Probe streams of the counter-based generator (see ll_probes). */
 enum { LL_STREAM_S = 0, LL_STREAM_G = 1, LL_STREAM_POWER = 2 };
 
@@ -91,12 +100,16 @@ typedef struct {
     int precision;             /* LL_PREC_*                                                      */
     int sval_mode;             /* LL_SVAL_*                                                      */
     int keep_for_backward;     /* 1: keep [Q | G'] and the coefficients for ll_logdet_backward   */
-    int rows_per_thread;       /* 0 = autotuned; otherwise rows each thread handles per tile     */
-    int threads_per_block;     /* 0 = autotuned; otherwise CTA size of the step kernels          */
+    int rows_per_thread;       /* LL_KERNEL_GATHER: rows each thread handles per tile (0 = 8)    */
+    int threads_per_block;     /* CTA size of the step kernel (0 = kernel default: 384 or 512
+                                  for LL_KERNEL_GATHER, 512 for LL_KERNEL_TMA; a TMA CTA of at
+                                  most 256 threads runs two per SM). Ignored by LL_KERNEL_AUTO.  */
     int ckpt_stride;           /* backward: W_j checkpoint stride; 0 = ceil(sqrt(m))            */
     int use_graph;             /* 1: capture the m-step passes in a CUDA graph (default 1)       */
     int64_t timeout_cycles;    /* batched launch: clock cycles a dependency wait may spin before
-                                  the call fails with LL_ERR_TIMEOUT; 0 = about 2 s              */
+                                  the call fails with LL_ERR_TIMEOUT; 0 = about 2 s. Also bounds
+                                  the pipeline waits of the TMA step kernel.                     */
+    int step_kernel;           /* LL_KERNEL_* (default LL_KERNEL_AUTO)                           */
 } ll_options;
 
 typedef struct ll_handle ll_handle;
@@ -110,6 +123,8 @@ typedef struct {
     int k;                           /* sketch columns used (min(m_vec/3, n))                     */
     int kernel_launches;             /* library kernels launched by the call                      */
     float ms_probes, ms_pass1, ms_qr, ms_pass2, ms_total;   /* device times (CUDA events)         */
+    int kernel_pass1, kernel_pass2;  /* LL_KERNEL_GATHER or LL_KERNEL_TMA used by each pass       */
+    int threads_pass1, threads_pass2;   /* CTA size used by each pass                             */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */
@@ -122,8 +137,21 @@ const char* ll_status_string(ll_status s);
 /* Text of the last failure on this handle (empty when none). Owned by the handle. */
 const char* ll_last_error(const ll_handle* h);
 /* Fill *opts with defaults: degree 40, probes 30, seed 0, Rademacher, LL_PREC_DF64, s_val = c,
- * no backward, autotuned launch shape, ckpt_stride 0, CUDA graphs on. */
+ * no backward, autotuned step kernel, ckpt_stride 0, CUDA graphs on. */
 void ll_default_options(ll_options* opts);
+/* Step kernel and launch shape used by ll_apply_poly and ll_logdet_backward on this handle
+ * (LL_KERNEL_*, with threads_per_block and rows_per_thread as in ll_options; the default is
+ * LL_KERNEL_AUTO). LL_ERR_INVALID_ARG for an unknown kernel or a negative shape. */
+ll_status ll_set_step_config(ll_handle* h, int step_kernel, int threads_per_block, int rows_per_thread);
+
+/* Test hook for failure detection. LL_INJECT_STALL: from now on, the TMA step kernel launched by
+ * this handle expects 16 bytes for its first tile that no copy delivers, so that tile's pipeline
+ * waits run out after the options' timeout_cycles; the kernel then records the error, stops
+ * issuing copies, waits (bounded) for the copies it issued, and returns, and the call fails with
+ * LL_ERR_TIMEOUT while the context stays usable. LL_INJECT_NONE clears it. No other kernel is
+ * affected. LL_ERR_INVALID_ARG for an unknown value. */
+enum { LL_INJECT_NONE = 0, LL_INJECT_STALL = 1 };
+ll_status ll_debug_inject(ll_handle* h, int what);
 
 /* ---- host-side method pieces (FP64 on the host: their stability needs it) ------------------ */
 

@@ -23,6 +23,8 @@ LL_PREC_F64, LL_PREC_DF64, LL_PREC_F32_MIXED = 0, 1, 2
 LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
+LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA = 0, 1, 2
+LL_INJECT_NONE, LL_INJECT_STALL = 0, 1
 LL_NOALLOC_MAX_ROWS = 1 << 18
 
 
@@ -40,7 +42,7 @@ class ll_options(ctypes.Structure):
                 ("probe_kind", ctypes.c_int), ("precision", ctypes.c_int), ("sval_mode", ctypes.c_int),
                 ("keep_for_backward", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("timeout_cycles", ctypes.c_int64)]
+                ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int)]
 
 
 class ll_info(ctypes.Structure):
@@ -48,7 +50,8 @@ class ll_info(ctypes.Structure):
                 ("trace_q", ctypes.c_double), ("trace_res", ctypes.c_double), ("estimate", ctypes.c_double),
                 ("taylor_terms", ctypes.c_int), ("k", ctypes.c_int), ("kernel_launches", ctypes.c_int),
                 ("ms_probes", ctypes.c_float), ("ms_pass1", ctypes.c_float), ("ms_qr", ctypes.c_float),
-                ("ms_pass2", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_pass2", ctypes.c_float), ("ms_total", ctypes.c_float), ("kernel_pass1", ctypes.c_int),
+                ("kernel_pass2", ctypes.c_int), ("threads_pass1", ctypes.c_int), ("threads_pass2", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -65,6 +68,8 @@ SIGNATURES = {
     "ll_status_string": (ctypes.c_char_p, [_I]),
     "ll_last_error": (ctypes.c_char_p, [_P]),
     "ll_default_options": (None, [ctypes.POINTER(ll_options)]),
+    "ll_set_step_config": (_I, [_P, _I, _I, _I]),
+    "ll_debug_inject": (_I, [_P, _I]),
     "ll_leja_points": (_I, [_I, _PD]),
     "ll_divided_differences": (_I, [ll_bounds, _I, _I, _PD, ctypes.POINTER(_I)]),
     "ll_gershgorin": (_I, [_P, ctypes.POINTER(ll_csr), ctypes.POINTER(ll_bounds), _P]),

@@ -11,12 +11,13 @@ import dataclasses
 import numpy as np
 
 from . import _ffi
-from ._ffi import (LL_F32, LL_F64, LL_PREC_DF64, LL_PREC_F32_MIXED, LL_PREC_F64,  # noqa: F401
-                   LL_PROBE_GAUSSIAN, LL_PROBE_RADEMACHER, LL_STREAM_G, LL_STREAM_POWER, LL_STREAM_S,
+from ._ffi import (LL_F32, LL_F64, LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA,  # noqa: F401
+                   LL_PREC_DF64, LL_PREC_F32_MIXED, LL_PREC_F64, LL_PROBE_GAUSSIAN, LL_PROBE_RADEMACHER, LL_STREAM_G, LL_STREAM_POWER, LL_STREAM_S,
                    LL_SVAL_CENTER, LL_SVAL_HALF_LMAX)
 
 PRECISIONS = {"f64": LL_PREC_F64, "df64": LL_PREC_DF64, "f32": LL_PREC_F32_MIXED}
 PROBE_KINDS = {"rademacher": LL_PROBE_RADEMACHER, "gaussian": LL_PROBE_GAUSSIAN}
+STEP_KERNELS = {"auto": LL_KERNEL_AUTO, "gather": LL_KERNEL_GATHER, "tma": LL_KERNEL_TMA}
 
 
 class LejaError(RuntimeError):
@@ -63,6 +64,14 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+    def set_step_config(self, kernel: str = "auto", threads_per_block: int = 0, rows_per_thread: int = 0):
+        """Step kernel of ll_apply_poly and ll_logdet_backward on this handle."""
+        self.check(self._lib.ll_set_step_config(self.ptr, STEP_KERNELS[kernel], threads_per_block, rows_per_thread))
+
+    def debug_inject(self, what: str = "none"):
+        """Test hook: "stall" makes the TMA step kernel's first-tile waits run out (LL_ERR_TIMEOUT)."""
+        self.check(self._lib.ll_debug_inject(self.ptr, {"none": _ffi.LL_INJECT_NONE, "stall": _ffi.LL_INJECT_STALL}[what]))
 
     def info(self) -> dict:
         inf = _ffi.ll_info()
@@ -114,7 +123,7 @@ def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
 def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str = "rademacher",
             precision: str = "df64", sval_mode: int = LL_SVAL_CENTER, keep_for_backward: bool = False,
             rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
-            use_graph: bool = True, timeout_cycles: int = 0) -> _ffi.ll_options:
+            use_graph: bool = True, timeout_cycles: int = 0, step_kernel: str = "auto") -> _ffi.ll_options:
     o = _ffi.ll_options()
     _ffi.load().ll_default_options(ctypes.byref(o))
     o.degree = degree
@@ -129,6 +138,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
     o.ckpt_stride = ckpt_stride
     o.use_graph = int(use_graph)
     o.timeout_cycles = timeout_cycles
+    o.step_kernel = STEP_KERNELS[step_kernel]
     return o
 
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -29,8 +30,25 @@ struct ll_handle {
     std::string err;
     std::map<std::string, Buf> ws;
     ll_info info{};
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[8] = {};
     int launches = 0;
+    // step kernel of ll_apply_poly and ll_logdet_backward (ll_set_step_config)
+    int cfg_kernel = LL_KERNEL_AUTO, cfg_threads = 0, cfg_rpt = 0;
+    // autotuned step launches: (precision, mode, n, nnz, b, ld) -> (kernel, threads, rows per thread)
+    std::map<std::tuple<int, int, int, int64_t, int, long long>, std::tuple<int, int, int>> tuned;
+    long long spin_budget = 4000000000LL;   // clock cycles a TMA pipeline wait may spin (about 2 s)
+    int inject = LL_INJECT_NONE;            // ll_debug_inject
+    bool tma_used = false;                  // a TMA step ran since the last error-flag check
+    int last_kernel = 0, last_threads = 0;  // choice of the last run_pass
+    // CUDA graph of the last forward's device work (replayed when the next call is identical)
+    uint64_t ws_gen = 0;                    // bumped whenever a workspace buffer moves
+    cudaStream_t cap_stream = nullptr;      // capture stream (the caller's may be the legacy stream)
+    struct Graph {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;
+        int launches = 0, k1 = 0, t1 = 0, k2 = 0, t2 = 0;
+        bool tma = false;
+    } gfwd;
     int max_fwd_offset = 0;   // largest col - row of the last validated matrix
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
@@ -66,6 +84,7 @@ void* ws_get(ll_handle* h, const char* name, size_t bytes, cudaError_t* err) {
     b.p = nullptr;
     b.bytes = 0;
     cudaError_t e = cudaMalloc(&b.p, bytes);
+    h->ws_gen++;
     if (e != cudaSuccess) {
         cudaGetLastError();
         *err = e;
@@ -142,13 +161,135 @@ ll_status setup_coefficients(ll_handle* h, double lmin, double lmax, int degree,
 
 int64_t pad_elems(int64_t x) { return (x + 31) & ~(int64_t)31; }
 
+// A planned step launch: the register-gather kernel (k_leja_step) or the TMA-fed one (k_leja_tma).
+struct StepExec {
+    int kind = LL_KERNEL_GATHER;
+    int threads = 0, rpt = 0;   // requested shape (0 = kernel default)
+    StepLaunch gl{};
+    TmaLaunch tl{};
+    int grid() const { return kind == LL_KERNEL_TMA ? tl.grid : gl.grid; }
+    int cta() const { return kind == LL_KERNEL_TMA ? tl.threads : gl.threads; }
+};
+
+// Plans a launch of the given kind (shape fields of p are filled); false when not applicable.
+bool plan_exec(ll_handle* h, int kind, int precision, int mode, int n, int64_t nnz, int b, int threads, int rpt,
+               StepParams& p, StepExec& E) {
+    E.kind = kind;
+    E.threads = threads;
+    E.rpt = rpt;
+    if (kind == LL_KERNEL_TMA) {
+        const int ctas = (threads > 0 && threads <= 256) ? 2 : 1;
+        if (!plan_step_tma(precision, mode, n, nnz, b, threads, ctas, p, E.tl, h->sm_count)) return false;
+        E.tl.q.spin_budget = h->spin_budget;
+        E.tl.q.inject = h->inject;
+        return true;
+    }
+    E.gl = plan_step(precision, mode, n, nnz, b, threads, rpt, p, h->sm_count);
+    return true;
+}
+
+cudaError_t exec_step(ll_handle* h, int precision, int mode, const StepExec& E, const StepParams& p, cudaStream_t s) {
+    h->launches++;
+    if (E.kind == LL_KERNEL_TMA) {
+        h->tma_used = true;
+        return launch_step_tma(precision, mode, E.tl, p, s);
+    }
+    return launch_step(precision, mode, E.gl, p, s);
+}
+
+// Workspace of a step launch: DOT partials for the plan's grid, and the TMA error flag.
+ll_status bind_exec(ll_handle* h, int mode, int b, StepExec& E, StepParams& p) {
+    if (mode == MODE_DOT) {
+        WS(partials, double*, "dot_partials", (size_t)2 * E.grid() * b * sizeof(double));
+        p.partials = partials;
+    }
+    if (E.kind == LL_KERNEL_TMA) {
+        WS(err, int*, "tma_error", sizeof(int));
+        E.tl.q.error = err;
+    }
+    return LL_OK;
+}
+
+// Reads and clears the TMA pipeline's error flag (synchronises the stream); LL_ERR_TIMEOUT if set.
+ll_status check_tma_flag(ll_handle* h, cudaStream_t s) {
+    if (!h->tma_used) return LL_OK;
+    h->tma_used = false;
+    WS(err, int*, "tma_error", sizeof(int));
+    int v = 0;
+    LL_CK(cudaMemcpyAsync(&v, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    if (v) {
+        LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+        return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out");
+    }
+    return LL_OK;
+}
+
+// Chooses the step launch for (precision, mode, n, nnz, b). kernel = LL_KERNEL_AUTO times the
+// candidates on the real operands once (p holds a representative non-first step: its outputs are
+// overwritten by the pass) and caches the fastest on the handle.
+ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz, int b, int kernel, int threads,
+                      int rpt, StepParams& p, StepExec& E, cudaStream_t s) {
+    ll_status st;
+    if (kernel == LL_KERNEL_TMA) {
+        StepParams q = p;
+        if (plan_exec(h, LL_KERNEL_TMA, precision, mode, n, nnz, b, threads, 0, q, E)) {
+            p = q;
+            return bind_exec(h, mode, b, E, p);
+        }
+        kernel = LL_KERNEL_GATHER;
+        threads = 0;
+        rpt = 0;
+    }
+    if (kernel == LL_KERNEL_GATHER) {
+        plan_exec(h, LL_KERNEL_GATHER, precision, mode, n, nnz, b, threads, rpt, p, E);
+        return bind_exec(h, mode, b, E, p);
+    }
+    const auto key = std::make_tuple(precision, mode, n, nnz, b, p.ldw);
+    auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) {
+        const int kind = std::get<0>(it->second);
+        plan_exec(h, kind, precision, mode, n, nnz, b, std::get<1>(it->second), std::get<2>(it->second), p, E);
+        return bind_exec(h, mode, b, E, p);
+    }
+    struct Cand { int kind, threads, rpt; };
+    const Cand cands[] = {{LL_KERNEL_TMA, 512, 0}, {LL_KERNEL_TMA, 256, 0}, {LL_KERNEL_GATHER, 0, 8},
+                          {LL_KERNEL_GATHER, 0, 4}, {LL_KERNEL_GATHER, 0, 2}, {LL_KERNEL_GATHER, 256, 2}};
+    float best_ms = 0.f;
+    Cand best{LL_KERNEL_GATHER, 0, 8};
+    bool have = false;
+    for (const Cand& c : cands) {
+        StepParams q = p;
+        StepExec C;
+        if (!plan_exec(h, c.kind, precision, mode, n, nnz, b, c.threads, c.rpt, q, C)) continue;
+        if ((st = bind_exec(h, mode, b, C, q)) != LL_OK) return st;
+        LL_CK(exec_step(h, precision, mode, C, q, s));
+        LL_CK(cudaEventRecord(h->ev[6], s));
+        LL_CK(exec_step(h, precision, mode, C, q, s));
+        LL_CK(exec_step(h, precision, mode, C, q, s));
+        LL_CK(cudaEventRecord(h->ev[7], s));
+        LL_CK(cudaEventSynchronize(h->ev[7]));
+        if ((st = check_tma_flag(h, s)) != LL_OK) return st;
+        float ms = 0.f;
+        LL_CK(cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]));
+        if (!have || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+            have = true;
+        }
+    }
+    h->tuned[key] = std::make_tuple(best.kind, best.threads, best.rpt);
+    plan_exec(h, best.kind, precision, mode, n, nnz, b, best.threads, best.rpt, p, E);
+    return bind_exec(h, mode, b, E, p);
+}
+
 // Runs m Léja steps over an n x b block.
 //   mode ACCUM: W_0 = win0 (ld = ldw), P accumulates sum_j d_j W_j (P type, ld = ldp)
 //   mode DOT:   W_0 = V = win0, dots[(j) * b + col] = <V_col, W_j col> for j = 0..m
 ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int precision, int mode, int n, int b,
                    const void* win0, long long ldw, void* wa, void* wb, void* P, long long ldp, double* dots,
-                   const std::vector<double>& beta, const std::vector<double>& d, int threads_target, int rpt,
-                   cudaStream_t s) {
+                   const std::vector<double>& beta, const std::vector<double>& d, int kernel, int threads_target,
+                   int rpt, cudaStream_t s) {
     const int m = (int)d.size() - 1;
     StepParams p{};
     p.rowptr = A->rowptr;
@@ -157,16 +298,37 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     p.ldw = ldw;
     p.ldv = ldw;
     p.ldp = ldp;
-    StepLaunch L = plan_step(precision, mode, n, A->nnz, b, threads_target, rpt, p, h->sm_count);
+    p.p = P;
     if (mode == MODE_DOT) {
-        WS(partials, double*, "dot_partials", (size_t)2 * L.grid * b * sizeof(double));
         WS(ticket, unsigned int*, "dot_ticket", sizeof(unsigned int));
         LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
-        p.partials = partials;
         p.ticket = ticket;
         p.v = win0;
     }
-    p.p = P;
+    {
+        WS(err, int*, "tma_error", sizeof(int));
+        LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    }
+    // a representative non-first step for the autotuner (the pass overwrites what it writes)
+    const int jt = m > 1 ? 1 : 0;
+    p.win = win0;
+    p.wout = wa;
+    p.first = 0;
+    p.beta = beta[jt];
+    p.d0 = d[0];
+    p.dn = d[jt + 1];
+    p.beta_df = df_split(beta[jt]);
+    p.d0_df = df_split(d[0]);
+    p.dn_df = df_split(d[jt + 1]);
+    if (mode == MODE_DOT) {
+        p.dots_next = dots + (size_t)(jt + 1) * b;
+        p.dots_first = dots;
+    }
+    StepExec E;
+    ll_status st = choose_exec(h, precision, mode, n, A->nnz, b, kernel, threads_target, rpt, p, E, s);
+    if (st != LL_OK) return st;
+    h->last_kernel = E.kind;
+    h->last_threads = E.cta();
     for (int j = 0; j < m; ++j) {
         p.win = (j == 0) ? win0 : ((j & 1) ? wa : wb);
         p.wout = (j & 1) ? wb : wa;
@@ -181,8 +343,7 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
             p.dots_next = dots + (size_t)(j + 1) * b;
             p.dots_first = dots;
         }
-        LL_CK(launch_step(precision, mode, L, p, s));
-        h->launches++;
+        LL_CK(exec_step(h, precision, mode, E, p, s));
     }
     return LL_OK;
 }
@@ -220,6 +381,8 @@ void ll_destroy(ll_handle* h) {
         if (kv.second.p) cudaFree(kv.second.p);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
+    if (h->gfwd.exec) cudaGraphExecDestroy(h->gfwd.exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
@@ -258,6 +421,22 @@ void ll_default_options(ll_options* o) {
     o->ckpt_stride = 0;
     o->use_graph = 1;
     o->timeout_cycles = 0;
+    o->step_kernel = LL_KERNEL_AUTO;
+}
+
+ll_status ll_debug_inject(ll_handle* h, int what) {
+    if (!h || what < LL_INJECT_NONE || what > LL_INJECT_STALL) return LL_ERR_INVALID_ARG;
+    h->inject = what;
+    return LL_OK;
+}
+
+ll_status ll_set_step_config(ll_handle* h, int step_kernel, int threads_per_block, int rows_per_thread) {
+    if (!h || step_kernel < LL_KERNEL_AUTO || step_kernel > LL_KERNEL_TMA || threads_per_block < 0 || rows_per_thread < 0)
+        return LL_ERR_INVALID_ARG;
+    h->cfg_kernel = step_kernel;
+    h->cfg_threads = threads_per_block;
+    h->cfg_rpt = rows_per_thread;
+    return LL_OK;
 }
 
 ll_status ll_leja_points(int count, double* xi_out) {
@@ -371,7 +550,7 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
     std::vector<double> beta(degree + 1);
     for (int j = 0; j <= degree; ++j) beta[j] = -(c / gamma + xi[j]);
     const int wt = w_type_of(precision), pt = p_type_of(precision);
-    const int lb = even_ld(b);                 // blocks are stored in column pairs
+    const int lb = block_ld(precision, b);     // blocks are stored in column pairs
     const size_t nb = (size_t)n * lb;
     WS(vprep, void*, "ap_vals", (size_t)A->nnz * elem_size(wt));
     WS(w0, void*, "ap_w0", nb * elem_size(wt));
@@ -387,11 +566,15 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
         h->launches++;
         return LL_OK;
     }
-    st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, lb, wa, wb, pp, lb, nullptr, beta, d, 0, 0, s);
+    st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, lb, wa, wb, pp, lb, nullptr, beta, d, h->cfg_kernel,
+                  h->cfg_threads, h->cfg_rpt, s);
     if (st != LL_OK) return st;
+    h->info = ll_info{};
+    h->info.kernel_pass1 = h->last_kernel;
+    h->info.threads_pass1 = h->last_threads;
     LL_CK(launch_block_to_f64(precision, pp, lb, PV, ldp, n, b, s));
     h->launches++;
-    return LL_OK;
+    return check_tma_flag(h, s);
 }
 
 ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, const ll_options* opts, double* estimate,
@@ -409,6 +592,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     cudaStream_t s = (cudaStream_t)stream;
     h->launches = 0;
     h->kept = false;
+    h->spin_budget = o.timeout_cycles > 0 ? o.timeout_cycles : 4000000000LL;
     const int n = (int)A->n;
     if (n == 0) {
         *estimate = 0.0;
@@ -433,7 +617,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     const int prec = o.precision;
     const int wt = w_type_of(prec), pt = p_type_of(prec);
     const size_t ew = elem_size(wt), ep = elem_size(pt);
-    const int l1 = even_ld(kq), l2 = even_ld(b2);   // pass-1 and pass-2 blocks (column pairs)
+    const int l1 = block_ld(prec, kq), l2 = block_ld(prec, b2);   // pass-1 and pass-2 blocks (column pairs)
     // workspace
     WS(vprep, void*, "fw_vals", (size_t)A->nnz * ew);
     WS(S, void*, "fw_S", (size_t)n * l1 * ew);
@@ -456,65 +640,155 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     WS(rinv, double*, "fw_rinv", (size_t)kq * kq * sizeof(double));
     WS(qrstat, int*, "fw_qr_status", sizeof(int));
     WS(dots, double*, "fw_dots", (size_t)(m + 1) * b2 * sizeof(double));
+    WS(tma_err, int*, "tma_error", sizeof(int));
+    int k1 = 0, t1 = 0;   // step kernel and CTA size of pass 1
 
-    LL_CK(cudaEventRecord(h->ev[0], s));
-    LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), s));
-    LL_CK(cudaMemsetAsync(qrstat, 0, sizeof(int), s));
-    // matrix values scaled by 1 / (sigma gamma): B = (A/sigma - c I)/gamma = prepared - (c/gamma) I
-    LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
-    // Algorithm 3 step 2 (S) and step 6 (G)
-    LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, l1, S, l1, s));
-    LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, s));
-    h->launches += 3;
-    LL_CK(cudaEventRecord(h->ev[1], s));
+    // the device work of the call (Algorithm 3 steps 2-6), enqueued on q; with capture, the
+    // phase events become event-record nodes of the graph
+    bool capturing = false;
+    auto rec = [&](cudaEvent_t ev, cudaStream_t q) {
+        return capturing ? cudaEventRecordWithFlags(ev, q, cudaEventRecordExternal) : cudaEventRecord(ev, q);
+    };
+    auto enqueue = [&](cudaStream_t q) -> ll_status {
+        LL_CK(rec(h->ev[0], q));
+        LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), q));
+        LL_CK(cudaMemsetAsync(qrstat, 0, sizeof(int), q));
+        // matrix values scaled by 1 / (sigma gamma): B = (A/sigma - c I)/gamma = prepared - (c/gamma) I
+        LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, q));
+        // Algorithm 3 step 2 (S) and step 6 (G)
+        LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, l1, S, l1, q));
+        LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, q));
+        h->launches += 3;
+        LL_CK(rec(h->ev[1], q));
 
-    if (kq == n) {
-        // k >= n: the sketch spans R^n, so Q = I is an orthonormal basis of span(Y) and
-        // G' = (I - Q Q^T) G = 0; the estimate is the exact trace of p(A~)
-        LL_CK(cudaEventRecord(h->ev[2], s));
-        LL_CK(cudaMemsetAsync(basis, 0, (size_t)n * l2 * sizeof(double), s));
-        LL_CK(launch_unit_diag(T_F64, basis, l2, n, s));
-        h->launches++;
-        if (wt != T_F64) {
-            LL_CK(cudaMemsetAsync(V, 0, (size_t)n * l2 * ew, s));
-            LL_CK(launch_unit_diag(wt, V, l2, n, s));
+        if (kq == n) {
+            // k >= n: the sketch spans R^n, so Q = I is an orthonormal basis of span(Y) and
+            // G' = (I - Q Q^T) G = 0; the estimate is the exact trace of p(A~)
+            LL_CK(rec(h->ev[2], q));
+            LL_CK(cudaMemsetAsync(basis, 0, (size_t)n * l2 * sizeof(double), q));
+            LL_CK(launch_unit_diag(T_F64, basis, l2, n, q));
             h->launches++;
-        }
-        LL_CK(cudaEventRecord(h->ev[3], s));
-    } else {
-        // step 3: Y = p(A~) S
-        st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, kq, S, l1, wa, wb, P, l1, nullptr, beta, d,
-                      o.threads_per_block, o.rows_per_thread, s);
-        if (st != LL_OK) return st;
-        LL_CK(cudaEventRecord(h->ev[2], s));
+            if (wt != T_F64) {
+                LL_CK(cudaMemsetAsync(V, 0, (size_t)n * l2 * ew, q));
+                LL_CK(launch_unit_diag(wt, V, l2, n, q));
+                h->launches++;
+            }
+            LL_CK(rec(h->ev[3], q));
+        } else {
+            // step 3: Y = p(A~) S
+            st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, kq, S, l1, wa, wb, P, l1, nullptr, beta, d, o.step_kernel,
+                          o.threads_per_block, o.rows_per_thread, q);
+            if (st != LL_OK) return st;
+            k1 = h->last_kernel;
+            t1 = h->last_threads;
+            LL_CK(rec(h->ev[2], q));
 
-        // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']
-        LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
-        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, s));
-        LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv, q1, kq, T_F64, nullptr, 0, s));
-        LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
-        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, s));
-        LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, l2, wt, wt != T_F64 ? V : nullptr, l2, s));
-        LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, s));
-        // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
-        // The typed block pointer of V is offset by kq elements: element index r * l2 + kq + c.
-        LL_CK(launch_project(basis, l2, kq, G, kg, kg, gram, n, basis + kq, l2, wt,
-                             wt != T_F64 ? V : nullptr, l2, (b2 & 1), kq, s));
-        h->launches += 8;
-        LL_CK(cudaEventRecord(h->ev[3], s));
+            // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']
+            LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
+            LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
+            LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv, q1, kq, T_F64, nullptr, 0, q));
+            LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
+            LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
+            LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, l2, wt, wt != T_F64 ? V : nullptr, l2, q));
+            LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, q));
+            // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
+            // The typed block pointer of V is offset by kq elements: element index r * l2 + kq + c.
+            LL_CK(launch_project(basis, l2, kq, G, kg, kg, gram, n, basis + kq, l2, wt,
+                                 wt != T_F64 ? V : nullptr, l2, (b2 & 1), kq, q));
+            h->launches += 8;
+            LL_CK(rec(h->ev[3], q));
+        }
+
+        // steps 5-6: traces t_j[col] = <V_col, W_j col> for j = 0..m
+        st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d, o.step_kernel,
+                      o.threads_per_block, o.rows_per_thread, q);
+        if (st != LL_OK) return st;
+        LL_CK(rec(h->ev[4], q));
+        return LL_OK;
+    };
+
+    // graph key: every input the enqueued work depends on (operands, coefficients, options, workspace)
+    struct Key {
+        const void* rp; const void* ci; const void* va;
+        int64_t n, nnz;
+        int dtype;
+        double lmin, lmax;
+        ll_options o;
+        uint64_t ws_gen;
+        int inject;
+    };
+    Key key;
+    memset(&key, 0, sizeof key);
+    key.rp = A->rowptr; key.ci = A->colind; key.va = A->values;
+    key.n = A->n; key.nnz = A->nnz; key.dtype = A->dtype;
+    key.lmin = bounds.lmin; key.lmax = bounds.lmax;
+    key.o = o;
+    key.o.keep_for_backward = 0;
+    key.ws_gen = h->ws_gen;
+    key.inject = h->inject;
+    const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
+    ll_handle::Graph& gr = h->gfwd;
+    const bool hit = o.use_graph && gr.exec && gr.key.size() == sizeof key && memcmp(gr.key.data(), kb, sizeof key) == 0;
+    if (hit) {
+        LL_CK(cudaGraphLaunch(gr.exec, s));
+        h->launches += gr.launches;
+        k1 = gr.k1;
+        t1 = gr.t1;
+        h->last_kernel = gr.k2;
+        h->last_threads = gr.t2;
+        h->tma_used = gr.tma;
+    } else {
+        const int before = h->launches;
+        if ((st = enqueue(s)) != LL_OK) return st;
+        if (o.use_graph) {
+            // capture the same work for the next identical call (tuning is cached by now and the
+            // workspace allocated, so the capture only records launches and memsets)
+            const int launched = h->launches - before;
+            const bool tma = h->tma_used;
+            if (gr.exec) {
+                cudaGraphExecDestroy(gr.exec);
+                gr.exec = nullptr;
+            }
+            if (!h->cap_stream) LL_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            LL_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+            capturing = true;
+            const int kk1 = k1, tt1 = t1, kk2 = h->last_kernel, tt2 = h->last_threads;
+            ll_status cst = enqueue(h->cap_stream);
+            capturing = false;
+            cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+            if (cst == LL_OK && ce == cudaSuccess && graph && h->ws_gen == key.ws_gen &&
+                cudaGraphInstantiate(&gr.exec, graph, 0) == cudaSuccess) {
+                gr.key.assign(kb, kb + sizeof key);
+                gr.launches = launched;
+                gr.k1 = kk1;
+                gr.t1 = tt1;
+                gr.k2 = kk2;
+                gr.t2 = tt2;
+                gr.tma = tma;
+            } else {
+                gr.exec = nullptr;
+                gr.key.clear();
+            }
+            cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            h->launches = before + launched;
+            k1 = kk1;
+            t1 = tt1;
+            h->last_kernel = kk2;
+            h->last_threads = tt2;
+            h->tma_used = tma;
+        }
     }
 
-    // steps 5-6: traces t_j[col] = <V_col, W_j col> for j = 0..m
-    st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d,
-                  o.threads_per_block, o.rows_per_thread, s);
-    if (st != LL_OK) return st;
-    LL_CK(cudaEventRecord(h->ev[4], s));
-
     std::vector<double> hd((size_t)(m + 1) * b2);
-    int hstat = 0;
+    int hstat = 0, herr = 0;
     LL_CK(cudaMemcpyAsync(hd.data(), dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     LL_CK(cudaMemcpyAsync(&hstat, qrstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (h->tma_used) LL_CK(cudaMemcpyAsync(&herr, tma_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     LL_CK(cudaStreamSynchronize(s));
+    h->tma_used = false;
+    if (herr) return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out");
     if (hstat) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2: non-positive pivot (rank-deficient sketch)");
 
     // step 7 and output: n log sigma + tr(Q^T F Q) + (1/k) tr(G'^T F G')
@@ -545,6 +819,10 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
     cudaEventElapsedTime(&I.ms_pass2, h->ev[3], h->ev[4]);
     cudaEventElapsedTime(&I.ms_total, h->ev[0], h->ev[4]);
+    I.kernel_pass1 = k1;
+    I.threads_pass1 = t1;
+    I.kernel_pass2 = h->last_kernel;
+    I.threads_pass2 = h->last_threads;
 
     if (o.keep_for_backward) {
         h->kept = true;
@@ -598,7 +876,7 @@ ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, 
     h->launches = 0;
     const int n = (int)A->n;
     const int prec = h->kept_prec, kq = h->kept_kq, kg = h->kept_kg, m = h->kept_m;
-    const int b2 = kq + kg, l2 = even_ld(b2);
+    const int b2 = kq + kg, l2 = block_ld(prec, b2);
     const int wt = w_type_of(prec);
     const size_t ew = elem_size(wt), blk = (size_t)n * l2 * ew;
     if (A->nnz > 0) LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
@@ -630,16 +908,36 @@ ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, 
     pp.ldp = l2;
     pp.v = V;
     pp.adj_split = kq;
+    {
+        WS(err, int*, "tma_error", sizeof(int));
+        LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    }
     StepParams pa = pp;
-    const StepLaunch Lp = plan_step(prec, MODE_PLAIN, n, A->nnz, b2, 0, 0, pp, h->sm_count);
-    const StepLaunch La = plan_step(prec, MODE_ADJ, n, A->nnz, b2, 0, 0, pa, h->sm_count);
+    // representative steps for the autotuner: W_1 from V into the segment buffer, and one
+    // reverse step between the two Lambda buffers (both rewritten below)
+    pp.win = V;
+    pp.wout = tmp;
+    pp.beta = beta[0];
+    pp.beta_df = df_split(beta[0]);
+    pa.win = lam;
+    pa.wout = lam + blk;
+    pa.beta = beta[0];
+    pa.beta_df = df_split(beta[0]);
+    pa.adj_q = d[0];
+    pa.adj_g = d[0] / kg;
+    pa.adj_q_df = df_split(d[0]);
+    pa.adj_g_df = df_split(d[0] / kg);
+    StepExec Ep, Ea;
+    ll_status cs = choose_exec(h, prec, MODE_PLAIN, n, A->nnz, b2, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pp, Ep, s);
+    if (cs != LL_OK) return cs;
+    cs = choose_exec(h, prec, MODE_ADJ, n, A->nnz, b2, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pa, Ea, s);
+    if (cs != LL_OK) return cs;
     auto plain_step = [&](int j, const void* win, void* wout) -> cudaError_t {
         pp.win = win;
         pp.wout = wout;
         pp.beta = beta[j];
         pp.beta_df = df_split(beta[j]);
-        h->launches++;
-        return launch_step(prec, MODE_PLAIN, Lp, pp, s);
+        return exec_step(h, prec, MODE_PLAIN, Ep, pp, s);
     };
     // phase A: W_1 .. W_{(nseg-1) sck}, keeping W_{k sck} in the checkpoint slots
     const void* cur = V;
@@ -679,13 +977,12 @@ ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, 
             pa.adj_g = d[j] / kg;
             pa.adj_q_df = df_split(d[j]);
             pa.adj_g_df = df_split(d[j] / kg);
-            LL_CK(launch_step(prec, MODE_ADJ, La, pa, s));
-            h->launches++;
+            LL_CK(exec_step(h, prec, MODE_ADJ, Ea, pa, s));
             lam_cur = lam_next;
         }
     }
     LL_CK(cudaGetLastError());
-    return LL_OK;
+    return check_tma_flag(h, s);
 }
 
 ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* dvalues, int64_t ld, int64_t nnz,
@@ -731,7 +1028,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         if (degrees && degrees[i] < 1) return fail(h, LL_ERR_INVALID_ARG, "degree must be >= 1");
     }
     if (2 * kg > 512 || kg > 96) return fail(h, LL_ERR_UNSUPPORTED, "m_vec / 3 above 96 is not supported");
-    const int kq = kg, b1 = kq, b2 = kq + kg, l1 = even_ld(b1), l2 = even_ld(b2);
+    const int kq = kg, b1 = kq, b2 = kq + kg, l1 = block_ld(prec, b1), l2 = block_ld(prec, b2);
 
     // validation of every CSR (one synchronisation)
     {
@@ -780,7 +1077,8 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
 
     // one workspace for every per-matrix buffer (256-byte aligned regions)
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    struct Off { size_t vals, S, G, P, wa, wb, basis, q1, V, part, dots, coef; int T1, T2; };
+    struct Off { size_t vals, S, G, P, wa, wb, basis, q1, V, part, dots, coef, qpart, gram, rinv; int T1, T2, gxs, gxc; };
+    const int ggrid = h->sm_count * 2;
     std::vector<Off> off(count);
     size_t total = 0;
     for (int i = 0; i < count; ++i) {
@@ -800,15 +1098,20 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         f.part = total; total += al((size_t)2 * std::max(f.T1, f.T2) * b2 * sizeof(double));
         f.dots = total; total += al((size_t)(hs[i].m + 1) * b2 * sizeof(double));
         f.coef = total; total += al((size_t)2 * (hs[i].m + 1) * sizeof(double));
+        // CholeskyQR2 of this matrix: Gram partials of its row blocks, ticket, Gram and R^{-1}
+        f.gxs = gram_blocks(kq, kq, true, (int)n, ggrid);
+        f.gxc = gram_blocks(kq, kg, false, (int)n, ggrid);
+        const size_t qp = std::max(gram_partials_doubles(kq, kq, true, f.gxs), gram_partials_doubles(kq, kg, false, f.gxc));
+        f.qpart = total; total += al(qp * sizeof(double));
+        f.gram = total; total += al((size_t)kq * kg * sizeof(double));
+        f.rinv = total; total += al((size_t)kq * kq * sizeof(double));
     }
     WS(base, char*, "bt_all", total);
-    const int ggrid = h->sm_count * 2;
-    const size_t gp = std::max(gram_partials_doubles(kq, kq, true, ggrid), gram_partials_doubles(kq, kg, false, ggrid));
-    WS(gpart, double*, "bt_gram_partials", gp * sizeof(double));
-    WS(gticket, unsigned int*, "bt_gram_ticket", sizeof(unsigned int));
-    WS(gram, double*, "bt_gram", (size_t)kq * kg * sizeof(double));
-    WS(rinv, double*, "bt_rinv", (size_t)kq * kq * sizeof(double));
     WS(qrstat, int*, "bt_qr_status", (size_t)count * sizeof(int));
+    WS(qticks, unsigned int*, "bt_qr_tickets", (size_t)count * sizeof(unsigned int));
+    WS(gjobs, GramJob*, "bt_gram_jobs", (size_t)3 * count * sizeof(GramJob));
+    WS(cjobs, CholJob*, "bt_chol_jobs", (size_t)count * sizeof(CholJob));
+    WS(rjobs, RowJob*, "bt_row_jobs", (size_t)3 * count * sizeof(RowJob));
     WS(ctr, unsigned long long*, "bt_counters", (size_t)(2 * count + 8) * sizeof(unsigned long long));
     WS(dmats, BatchMat*, "bt_mats", (size_t)2 * count * sizeof(BatchMat));
     WS(dtab, int*, "bt_tables", (size_t)2 * (2 * (max_m + 1) + count + 1) * sizeof(int));
@@ -871,7 +1174,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     LL_CK(cudaEventRecord(h->ev[0], s));
     LL_CK(cudaMemsetAsync(ctr, 0, (size_t)(2 * count + 8) * sizeof(unsigned long long), s));
     LL_CK(cudaMemsetAsync(qrstat, 0, (size_t)count * sizeof(int), s));
-    LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), s));
+    LL_CK(cudaMemsetAsync(qticks, 0, (size_t)count * sizeof(unsigned int), s));
     for (int i = 0; i < count; ++i) {
         const Off& f = off[i];
         const int n = (int)mats[i].n;
@@ -888,23 +1191,51 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     LL_CK(launch_batched(prec, MODE_ACCUM, bp1, grid1, smem1, s));
     h->launches++;
     LL_CK(cudaEventRecord(h->ev[2], s));
-    // CholeskyQR2 and deflation per matrix
-    for (int i = 0; i < count; ++i) {
-        const Off& f = off[i];
-        const int n = (int)mats[i].n;
-        void* P = base + f.P;
-        double* q1 = (double*)(base + f.q1);
-        double* basis = (double*)(base + f.basis);
-        double* G = (double*)(base + f.G);
-        void* V = base + f.V;
-        LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
-        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat + i, s));
-        LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv, q1, kq, T_F64, nullptr, 0, s));
-        LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, s));
-        LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat + i, s));
-        LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, l2, wt, V, l2, s));
-        LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, s));
-        LL_CK(launch_project(basis, l2, kq, G, kg, kg, gram, n, basis + kq, l2, wt, V, l2, (b2 & 1), kq, s));
+    // CholeskyQR2 and deflation of every matrix: eight launches over per-matrix job lists
+    // (Gram of Y, Cholesky, Y R^{-1}; Gram of Q1, Cholesky, Q1 R^{-1}; C = Q^T G; G' = G - Q C)
+    {
+        std::vector<GramJob> gj(3 * count);
+        std::vector<CholJob> cj(count);
+        std::vector<RowJob> rj(3 * count);
+        int gxs_max = 1, gxc_max = 1, n_max = 1;
+        for (int i = 0; i < count; ++i) {
+            const Off& f = off[i];
+            const int n = (int)mats[i].n;
+            double* part = (double*)(base + f.qpart);
+            unsigned int* tick = qticks + i;
+            double* gram = (double*)(base + f.gram);
+            double* rinv = (double*)(base + f.rinv);
+            void* P = base + f.P;
+            double* q1 = (double*)(base + f.q1);
+            double* basis = (double*)(base + f.basis);
+            double* G = (double*)(base + f.G);
+            void* V = base + f.V;
+            gj[i] = GramJob{P, nullptr, n, f.gxs, part, tick, gram};
+            gj[count + i] = GramJob{q1, nullptr, n, f.gxs, part, tick, gram};
+            gj[2 * count + i] = GramJob{basis, G, n, f.gxc, part, tick, gram};
+            cj[i] = CholJob{gram, rinv, qrstat + i};
+            rj[i] = RowJob{P, rinv, nullptr, q1, nullptr, n};
+            rj[count + i] = RowJob{q1, rinv, nullptr, basis, V, n};
+            // G' into columns [kq, kq + kg) of [Q | G']; the typed block is offset by kq elements
+            rj[2 * count + i] = RowJob{basis, gram, G, basis + kq, V, n};
+            gxs_max = std::max(gxs_max, f.gxs);
+            gxc_max = std::max(gxc_max, f.gxc);
+            n_max = std::max(n_max, n);
+        }
+        LL_CK(cudaMemcpyAsync(gjobs, gj.data(), gj.size() * sizeof(GramJob), cudaMemcpyHostToDevice, s));
+        LL_CK(cudaMemcpyAsync(cjobs, cj.data(), cj.size() * sizeof(CholJob), cudaMemcpyHostToDevice, s));
+        LL_CK(cudaMemcpyAsync(rjobs, rj.data(), rj.size() * sizeof(RowJob), cudaMemcpyHostToDevice, s));
+        const GramJob g0 = gj[0];
+        const CholJob c0 = cj[0];
+        const RowJob r0 = rj[0];
+        LL_CK(launch_gram_jobs(pt, l1, kq, T_F64, 0, kq, true, g0, gjobs, count, gxs_max, s));
+        LL_CK(launch_chol_jobs(kq, c0, cjobs, count, s));
+        LL_CK(launch_apply_rinv_jobs(pt, l1, kq, kq, T_F64, 0, r0, rjobs, count, n_max, s));
+        LL_CK(launch_gram_jobs(T_F64, kq, kq, T_F64, 0, kq, true, g0, gjobs + count, count, gxs_max, s));
+        LL_CK(launch_chol_jobs(kq, c0, cjobs, count, s));
+        LL_CK(launch_apply_rinv_jobs(T_F64, kq, kq, l2, wt, l2, r0, rjobs + count, count, n_max, s));
+        LL_CK(launch_gram_jobs(T_F64, l2, kq, T_F64, kg, kg, false, g0, gjobs + 2 * count, count, gxc_max, s));
+        LL_CK(launch_project_jobs(l2, kq, kg, kg, l2, wt, l2, (b2 & 1), kq, r0, rjobs + 2 * count, count, n_max, s));
         h->launches += 8;
     }
     LL_CK(cudaEventRecord(h->ev[3], s));
@@ -967,7 +1298,7 @@ ll_status ll_kept_basis(const ll_handle* h, double* out, int64_t ld, int64_t* n_
     auto it = h->ws.find("fw_basis");
     if (it == h->ws.end()) return LL_ERR_NO_FORWARD;
     const int b2 = h->kept_kq + h->kept_kg;
-    const int l2 = even_ld(b2);
+    const int l2 = block_ld(h->kept_prec, b2);
     if (n_out) *n_out = h->kept_n;
     if (kq_out) *kq_out = h->kept_kq;
     if (kg_out) *kg_out = h->kept_kg;

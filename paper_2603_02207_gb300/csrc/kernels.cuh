@@ -100,7 +100,41 @@ cudaError_t launch_dot_f64(const double* x, const double* y, int n, double* part
                            double* out, int grid, cudaStream_t s);
 cudaError_t launch_scale_f64(double* x, const double* num, int n, int mode, cudaStream_t s);
 
-// CholeskyQR pieces
+// CholeskyQR pieces. Each launch takes one job by value or, for a batch of matrices with the same
+// widths and leading dimensions, a device array of jobs (one matrix per blockIdx.z for the Gram and
+// row-product kernels, per CTA for the Cholesky).
+struct GramJob {
+    const void* X;            // n x kx (type tx)
+    const void* Z;            // n x kz (FP64); unused when symmetric
+    int n;
+    int gx;                   // row blocks of this matrix (<= the launch's gridDim.x)
+    double* partials;         // gx * OT * 16 doubles
+    unsigned int* ticket;     // zero-initialised; reset by the last CTA
+    double* out;              // kx x kz
+};
+struct CholJob {
+    const double* G;          // k x k
+    double* Rinv;             // k x k
+    int* status;
+};
+struct RowJob {
+    const void* X;            // n x kx rows (type tx): Y or Q1 (apply_rinv), Q (project)
+    const double* M;          // kx x kc: R^{-1} or C
+    const double* G;          // project: the residual probes (FP64)
+    double* out64;            // FP64 output
+    void* out2;               // optional second output (type t2); may be null
+    int n;
+};
+// row blocks the Gram kernel uses for n rows under a budget of `grid` CTAs
+int gram_blocks(int kx, int kz, bool sym, int n, int grid);
+cudaError_t launch_gram_jobs(int tx, long long ldx, int kx, int tz, long long ldz, int kz, bool sym, const GramJob& one,
+                             const GramJob* jobs, int count, int gx_max, cudaStream_t s);
+cudaError_t launch_chol_jobs(int k, const CholJob& one, const CholJob* jobs, int count, cudaStream_t s);
+cudaError_t launch_apply_rinv_jobs(int tx, long long ldx, int k, long long ld64, int t2, long long ld2, const RowJob& one,
+                                   const RowJob* jobs, int count, int n_max, cudaStream_t s);
+cudaError_t launch_project_jobs(long long ldq, int k, long long ldg, int kg, long long ld64, int t2, long long ld2,
+                                int zero_pad, int col2, const RowJob& one, const RowJob* jobs, int count, int n_max,
+                                cudaStream_t s);
 // doubles of Gram partials needed for a launch with `grid` CTAs
 size_t gram_partials_doubles(int kx, int kz, bool sym, int grid);
 // out (kx x kz, row-major) = X^T Z, X: n x kx (type tx), Z: n x kz (type tz); sym: X == Z
@@ -147,6 +181,34 @@ struct BatchParams {
     int total_items, max_m, tp, rl, rpt, R, b, smem_cap;
 };
 
+// ---- TMA-fed step (k_leja_tma): geometry of the shared-memory pipeline -------------------------
+struct TmaParams {
+    int R;             // rows per tile (one row lane each)
+    int rbox;          // rows of the own / aux tile boxes
+    int gcap;          // entries per tile gathered by TMA (multiple of 4); later entries load directly
+    int nst;           // pipeline stages (tiles in flight + 1)
+    int slot;          // bytes of one gather4 slot (4 rows, 128-byte aligned)
+    int rowbytes;      // bytes of one W row (ld * element size)
+    int auxbytes;      // bytes of one V (pass 2, adjoint) or P (pass 1) row; 0 without
+    int stage_bytes;   // bytes per stage: gathered rows, own rows, aux rows, expanded values, row pointers
+    int off_own, off_aux, off_ex, off_rp;
+    int csr_bytes, csr_col, csr_val, csr_base;   // CSR ring (three slots) after the stages
+    int* error;                                  // set to 1 when a bounded wait runs out
+    long long spin_budget;                       // clock64 cycles a wait may spin
+    int inject;                                  // test hook: tile 0 expects bytes no copy delivers
+};
+struct TmaLaunch {
+    TmaParams q;
+    int threads, grid;
+    size_t smem;
+};
+// Shape of a TMA-fed step launch; false when the block layout does not allow TMA (a row wider than
+// 256 elements or not a multiple of 16 bytes) or the pipeline does not fit in shared memory.
+// ctas_per_sm: 1 (one 512-thread CTA with ~223 KB of stages) or 2 (two of half the size).
+bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int b, int threads_target, int ctas_per_sm,
+                   StepParams& p, TmaLaunch& L, int sm_count);
+cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s);
+
 void plan_batched(int b, double avg_nnz_per_row, BatchParams& bp, size_t* smem);
 cudaError_t launch_batched(int precision, int mode, const BatchParams& bp, int grid, size_t smem, cudaStream_t s);
 
@@ -154,6 +216,9 @@ cudaError_t launch_batched(int precision, int mode, const BatchParams& bp, int g
 enum ElemType { T_F64 = 0, T_F32 = 1, T_DF64 = 2 };
 // even leading dimension of a block of b columns
 inline int even_ld(int b) { return b + (b & 1); }
+// leading dimension of an n x b block in the W storage of `precision`: column pairs (even), and
+// for FP32 a multiple of 4 so that a row is a whole number of 16-byte units (the TMA row stride)
+inline int block_ld(int precision, int b) { return precision == LL_PREC_F32_MIXED ? (b + 3) & ~3 : b + (b & 1); }
 inline int w_type_of(int precision) {
     return precision == LL_PREC_F64 ? T_F64 : (precision == LL_PREC_DF64 ? T_DF64 : T_F32);
 }

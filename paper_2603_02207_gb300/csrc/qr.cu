@@ -42,10 +42,19 @@ __device__ __forceinline__ void ld_split(const dfp* p, size_t i, float& h, float
 // accumulators, so the error stays near FP64's. Per-CTA partials are reduced by the last CTA in
 // a fixed order. sym: Z == X and only the upper-triangular 4x4 tiles are computed.
 template <typename TX, typename TZ>
-__global__ void __launch_bounds__(QR_THREADS) k_gram(const TX* X, long long ldx, int kx, const TZ* Z, long long ldz, int kz,
-                                                     int n, int sym, double* partials, unsigned int* ticket, double* out) {
+__global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long long ldz, int kz, int sym, GramJob one,
+                                                     const GramJob* jobs) {
     extern __shared__ __align__(16) float sgf[];
     __shared__ bool s_last;
+    // one matrix per blockIdx.z in a batch; CTAs beyond the matrix's row-block count leave
+    const GramJob J = jobs ? jobs[blockIdx.z] : one;
+    if ((int)blockIdx.x >= J.gx) return;
+    const TX* X = static_cast<const TX*>(J.X);
+    const TZ* Z = static_cast<const TZ*>(J.Z);
+    const int n = J.n;
+    double* partials = J.partials;
+    unsigned int* ticket = J.ticket;
+    double* out = J.out;
     const int kxp = (kx + 3) & ~3;
     const int kzp = sym ? kxp : ((kz + 3) & ~3);
     float* xh = sgf;
@@ -77,7 +86,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(const TX* X, long long ldx,
     for (int e = 0; e < 16; ++e) { h[e] = 0.f; l[e] = 0.f; a64[e] = 0.0; }
     const int ntiles = (n + QR_TR - 1) / QR_TR;
     int cnt = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += J.gx) {
         for (int i = t; i < QR_TR * kxp; i += QR_THREADS) {
             const int r = i / kxp, a = i - r * kxp;
             const int row = tile * QR_TR + r;
@@ -138,14 +147,14 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(const TX* X, long long ldx,
     }
     __threadfence();
     __syncthreads();
-    if (t == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
+    if (t == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)J.gx * gridDim.y - 1);
     __syncthreads();
     if (s_last) {
         __threadfence();
         for (int q = t; q < OT * 16; q += QR_THREADS) {
             const int o = q / 16, e = q - o * 16;
             double sacc = 0.0;
-            for (int bx = 0; bx < (int)gridDim.x; ++bx) sacc += __ldcg(&partials[((size_t)bx * OT + o) * 16 + e]);
+            for (int bx = 0; bx < J.gx; ++bx) sacc += __ldcg(&partials[((size_t)bx * OT + o) * 16 + e]);
             int oa, oc;
             if (sym) {
                 int rem = o;
@@ -170,8 +179,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(const TX* X, long long ldx,
 }
 
 template <typename TX, typename TZ>
-static cudaError_t gram_typed(const void* X, long long ldx, int kx, const void* Z, long long ldz, int kz, int n, bool sym,
-                              double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s) {
+static cudaError_t gram_typed(long long ldx, int kx, long long ldz, int kz, bool sym, const GramJob& one,
+                              const GramJob* jobs, int count, int gx, cudaStream_t s) {
     const int kxp = (kx + 3) & ~3, kzp = sym ? kxp : ((kz + 3) & ~3);
     const int ta = kxp / 4, tc = kzp / 4;
     const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
@@ -185,11 +194,22 @@ static cudaError_t gram_typed(const void* X, long long ldx, int kx, const void* 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    int gx = grid / chunks;
-    if (gx < 1) gx = 1;
-    dim3 gd(gx, chunks);
-    k_gram<TX, TZ><<<gd, QR_THREADS, smem, s>>>((const TX*)X, ldx, kx, (const TZ*)Z, ldz, kz, n, sym ? 1 : 0, partials, ticket, out);
+    dim3 gd(gx, chunks, count);
+    k_gram<TX, TZ><<<gd, QR_THREADS, smem, s>>>(ldx, kx, ldz, kz, sym ? 1 : 0, one, jobs);
     return cudaGetLastError();
+}
+
+// row blocks of a Gram launch over n rows: at most grid / chunks, and at least four row tiles each
+int gram_blocks(int kx, int kz, bool sym, int n, int grid) {
+    const int kxp = (kx + 3) & ~3, kzp = sym ? kxp : ((kz + 3) & ~3);
+    const int ta = kxp / 4, tc = kzp / 4;
+    const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
+    const int chunks = (OT + QR_THREADS - 1) / QR_THREADS;
+    int gx = grid / chunks;
+    const int ntiles = (n + QR_TR - 1) / QR_TR;
+    const int by_rows = (ntiles + 3) / 4;
+    if (gx > by_rows) gx = by_rows;
+    return gx < 1 ? 1 : gx;
 }
 
 size_t gram_partials_doubles(int kx, int kz, bool sym, int grid) {
@@ -199,19 +219,29 @@ size_t gram_partials_doubles(int kx, int kz, bool sym, int grid) {
     return (size_t)grid * OT * 16;
 }
 
-cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, const void* Z, long long ldz, int kz,
-                        int n, bool sym, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s) {
-    if (tz != T_F64) return cudaErrorInvalidValue;
+cudaError_t launch_gram_jobs(int tx, long long ldx, int kx, int tz, long long ldz, int kz, bool sym, const GramJob& one,
+                             const GramJob* jobs, int count, int gx_max, cudaStream_t s) {
+    if (tz != T_F64 || count < 1 || gx_max < 1) return cudaErrorInvalidValue;
     switch (tx) {
-        case T_F64: return gram_typed<double, double>(X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, grid, s);
-        case T_F32: return gram_typed<float, double>(X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, grid, s);
-        default: return gram_typed<dfp, double>(X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, grid, s);
+        case T_F64: return gram_typed<double, double>(ldx, kx, ldz, kz, sym, one, jobs, count, gx_max, s);
+        case T_F32: return gram_typed<float, double>(ldx, kx, ldz, kz, sym, one, jobs, count, gx_max, s);
+        default: return gram_typed<dfp, double>(ldx, kx, ldz, kz, sym, one, jobs, count, gx_max, s);
     }
 }
 
+cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, const void* Z, long long ldz, int kz,
+                        int n, bool sym, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s) {
+    GramJob one{X, Z, n, gram_blocks(kx, kz, sym, n, grid), partials, ticket, out};
+    return launch_gram_jobs(tx, ldx, kx, tz, ldz, kz, sym, one, nullptr, 1, one.gx, s);
+}
+
 // ---------------------------------------------------------------- Cholesky + triangular inverse
-__global__ void k_chol_rinv(const double* G, int k, double* Rinv, int* status) {
+__global__ void k_chol_rinv(int k, CholJob one, const CholJob* jobs) {
     extern __shared__ __align__(16) double sc[];
+    const CholJob J = jobs ? jobs[blockIdx.x] : one;
+    const double* G = J.G;
+    double* Rinv = J.Rinv;
+    int* status = J.status;
     double* a = sc;            // k x k working copy; its upper triangle becomes R
     double* ri = sc + k * k;   // k x k R^{-1}
     __shared__ double s_piv;
@@ -256,7 +286,7 @@ __global__ void k_chol_rinv(const double* G, int k, double* Rinv, int* status) {
     if (threadIdx.x == 0 && s_bad) *status = 1;
 }
 
-cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, cudaStream_t s) {
+cudaError_t launch_chol_jobs(int k, const CholJob& one, const CholJob* jobs, int count, cudaStream_t s) {
     const size_t smem = (size_t)2 * k * k * sizeof(double);
     static bool attr = false;
     if (!attr) {
@@ -264,8 +294,13 @@ cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_chol_rinv<<<1, 256, smem, s>>>(G, k, Rinv, status);
+    if (count < 1) return cudaErrorInvalidValue;
+    k_chol_rinv<<<count, 256, smem, s>>>(k, one, jobs);
     return cudaGetLastError();
+}
+
+cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, cudaStream_t s) {
+    return launch_chol_jobs(k, CholJob{G, Rinv, status}, nullptr, 1, s);
 }
 
 // ------------------------------------------------------------------- row-wise small products
@@ -282,10 +317,17 @@ __device__ __forceinline__ void st_out2(dfp* p, size_t i, float h, float l) {
 }
 
 template <typename TX, typename T2, int MODE>
-__global__ void __launch_bounds__(QR_THREADS) k_rowprod(const TX* X, long long ldx, int kx, const double* M, int kc,
-                                                        const double* G, long long ldg, int n, double* out64, long long ld64,
-                                                        T2* out2, long long ld2, int col2, int zero_pad) {
+__global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, int kc, long long ldg, long long ld64,
+                                                        long long ld2, int col2, int zero_pad, RowJob one,
+                                                        const RowJob* jobs) {
     extern __shared__ __align__(16) float srp[];
+    const RowJob J = jobs ? jobs[blockIdx.z] : one;
+    const TX* X = static_cast<const TX*>(J.X);
+    const double* M = J.M;
+    const double* G = J.G;
+    const int n = J.n;
+    double* out64 = J.out64;
+    T2* out2 = static_cast<T2*>(J.out2);
     const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
     const int CG = kcp / 4;
     const int RG = QR_THREADS / CG;
@@ -348,48 +390,67 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(const TX* X, long long l
     }
 }
 
+template <typename TX, typename T2, int MODE>
+static cudaError_t rowprod_launch(long long ldx, int kx, int kc, long long ldg, long long ld64, long long ld2, int col2,
+                                  int zero_pad, const RowJob& one, const RowJob* jobs, dim3 gd, size_t smem, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_rowprod<TX, T2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_rowprod<TX, T2, MODE><<<gd, QR_THREADS, smem, s>>>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs);
+    return cudaGetLastError();
+}
+
+// n_max: the largest row count of the jobs (sizes the grid); count: jobs (blockIdx.z)
 template <typename TX, int MODE>
-static cudaError_t rowprod_dispatch(int t2, const TX* X, long long ldx, int kx, const double* M, int kc, const double* G,
-                                    long long ldg, int n, double* out64, long long ld64, void* out2, long long ld2,
-                                    int col2, int zero_pad, cudaStream_t s) {
+static cudaError_t rowprod_dispatch(int t2, long long ldx, int kx, int kc, long long ldg, long long ld64, long long ld2,
+                                    int col2, int zero_pad, const RowJob& one, const RowJob* jobs, int count, int n_max,
+                                    cudaStream_t s) {
     const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
     const int CG = kcp / 4;
     const int RG = QR_THREADS / CG;
-    if (RG < 1) return cudaErrorInvalidValue;
-    int blocks = (n + RG - 1) / RG;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (RG < 1 || count < 1) return cudaErrorInvalidValue;
+    int blocks = (n_max + RG - 1) / RG;
+    const int cap = count > 1 ? 64 : 152 * 4;
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) return cudaSuccess;
     const size_t smem = ((size_t)2 * kx * kcp + (size_t)2 * RG * kxp) * sizeof(float);
+    const dim3 gd(blocks, 1, count);
     switch (t2) {
-        case T_F32:
-            cudaFuncSetAttribute(k_rowprod<TX, float, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, float, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (float*)out2, ld2, col2, zero_pad);
-            break;
-        case T_DF64:
-            cudaFuncSetAttribute(k_rowprod<TX, dfp, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, dfp, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (dfp*)out2, ld2, col2, zero_pad);
-            break;
-        default:
-            cudaFuncSetAttribute(k_rowprod<TX, double, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            k_rowprod<TX, double, MODE><<<blocks, QR_THREADS, smem, s>>>(X, ldx, kx, M, kc, G, ldg, n, out64, ld64, (double*)out2, ld2, col2, zero_pad);
-            break;
+        case T_F32: return rowprod_launch<TX, float, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, smem, s);
+        case T_DF64: return rowprod_launch<TX, dfp, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, smem, s);
+        default: return rowprod_launch<TX, double, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, smem, s);
     }
-    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_rinv_jobs(int tx, long long ldx, int k, long long ld64, int t2, long long ld2, const RowJob& one,
+                                   const RowJob* jobs, int count, int n_max, cudaStream_t s) {
+    switch (tx) {
+        case T_F64: return rowprod_dispatch<double, 0>(t2, ldx, k, k, 0, ld64, ld2, 0, 0, one, jobs, count, n_max, s);
+        case T_F32: return rowprod_dispatch<float, 0>(t2, ldx, k, k, 0, ld64, ld2, 0, 0, one, jobs, count, n_max, s);
+        default: return rowprod_dispatch<dfp, 0>(t2, ldx, k, k, 0, ld64, ld2, 0, 0, one, jobs, count, n_max, s);
+    }
 }
 
 cudaError_t launch_apply_rinv(int tx, const void* X, long long ldx, int n, int k, const double* Rinv,
                               double* out64, long long ld64, int t2, void* out2, long long ld2, cudaStream_t s) {
-    switch (tx) {
-        case T_F64: return rowprod_dispatch<double, 0>(t2, (const double*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, 0, 0, s);
-        case T_F32: return rowprod_dispatch<float, 0>(t2, (const float*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, 0, 0, s);
-        default: return rowprod_dispatch<dfp, 0>(t2, (const dfp*)X, ldx, k, Rinv, k, nullptr, 0, n, out64, ld64, out2, ld2, 0, 0, s);
-    }
+    const RowJob one{X, Rinv, nullptr, out64, out2, n};
+    return launch_apply_rinv_jobs(tx, ldx, k, ld64, t2, ld2, one, nullptr, 1, n, s);
+}
+
+cudaError_t launch_project_jobs(long long ldq, int k, long long ldg, int kg, long long ld64, int t2, long long ld2,
+                                int zero_pad, int col2, const RowJob& one, const RowJob* jobs, int count, int n_max,
+                                cudaStream_t s) {
+    return rowprod_dispatch<double, 1>(t2, ldq, k, kg, ldg, ld64, ld2, col2, zero_pad, one, jobs, count, n_max, s);
 }
 
 cudaError_t launch_project(const double* Q, long long ldq, int k, const double* G, long long ldg, int kg,
                            const double* C, int n, double* out64, long long ld64, int t2, void* out2,
                            long long ld2, int zero_pad, int col2, cudaStream_t s) {
-    return rowprod_dispatch<double, 1>(t2, Q, ldq, k, C, kg, G, ldg, n, out64, ld64, out2, ld2, col2, zero_pad, s);
+    const RowJob one{Q, C, G, out64, out2, n};
+    return launch_project_jobs(ldq, k, ldg, kg, ld64, t2, ld2, zero_pad, col2, one, nullptr, 1, n, s);
 }
 
 }  // namespace ll

@@ -22,25 +22,9 @@
 // contiguous row window and the gathered neighbour rows W_j[c, :] are L2 hits.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "step_common.cuh"
 
 namespace ll {
-
-template <int PREC> struct PairT;
-// W / V pair, P pair, raw CSR value (as prepared in global memory)
-template <> struct PairT<LL_PREC_F64> { using W = double2; using P = double2; using Raw = double; };
-template <> struct PairT<LL_PREC_DF64> { using W = ulonglong2; using P = ulonglong2; using Raw = float2; };
-template <> struct PairT<LL_PREC_F32_MIXED> { using W = f2x; using P = ulonglong2; using Raw = float; };
-
-// value expanded for the f32x2 instructions: DF64 (ah2, al2, nah2), F32 (a2), F64 (a)
-struct ExDF { f2x ah2, al2, nah2; };
-template <int PREC> struct ExT;
-template <> struct ExT<LL_PREC_F64> { using T = double; };
-template <> struct ExT<LL_PREC_DF64> { using T = ExDF; };
-template <> struct ExT<LL_PREC_F32_MIXED> { using T = f2x; };
-
-__device__ __forceinline__ double expand(double a) { return a; }
-__device__ __forceinline__ ExDF expand(float2 a) { return ExDF{f2_pack(a.x, a.x), f2_pack(a.y, a.y), f2_pack(-a.x, -a.x)}; }
-__device__ __forceinline__ f2x expand(float a) { return f2_pack(a, a); }
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -113,21 +97,7 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
     const int* __restrict__ rowptr = p.rowptr;
     const int* __restrict__ colind = p.colind;
 
-    // per-step scalars broadcast to both lanes (beta_j, d_{j+1}, d_0 as double-float)
-    const f2x bh2 = f2_pack(p.beta_df.x, p.beta_df.x), bl2 = f2_pack(p.beta_df.y, p.beta_df.y);
-    const f2x nbh2 = f2_pack(-p.beta_df.x, -p.beta_df.x);
-    const f2x beta2 = f2_pack((float)p.beta, (float)p.beta);
-    const f2x dnh2 = f2_pack(p.dn_df.x, p.dn_df.x), dnl2 = f2_pack(p.dn_df.y, p.dn_df.y);
-    const f2x ndnh2 = f2_pack(-p.dn_df.x, -p.dn_df.x);
-    const f2x d0h2 = f2_pack(p.d0_df.x, p.d0_df.x), d0l2 = f2_pack(p.d0_df.y, p.d0_df.y);
-    const f2x nd0h2 = f2_pack(-p.d0_df.x, -p.d0_df.x);
-    const f2x zero2 = 0ull;
-    // ADJ: lane-wise coefficients of the thread's two columns
-    const bool q0 = 2 * cp < p.adj_split, q1 = 2 * cp + 1 < p.adj_split;
-    const double cadj0 = q0 ? p.adj_q : p.adj_g, cadj1 = q1 ? p.adj_q : p.adj_g;
-    const float2 cdf0 = q0 ? p.adj_q_df : p.adj_g_df, cdf1 = q1 ? p.adj_q_df : p.adj_g_df;
-    const f2x ch2 = f2_pack(cdf0.x, cdf1.x), cl2 = f2_pack(cdf0.y, cdf1.y), nch2 = f2_pack(-cdf0.x, -cdf1.x);
-    const f2x cf2 = f2_pack((float)cadj0, (float)cadj1);
+    const StepScalars<PREC> S(p, cp);
 
     auto stage = [&](int tile, int buf, int nz0, int nz1) {
         const int r0 = tile * R;
@@ -146,9 +116,7 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
         cp_async_commit();
     };
 
-    // trace partials of the thread's two columns (double-float; FP64 in the F64 mode)
-    f2x th2 = 0ull, tl2 = 0ull, t0h2 = 0ull, t0l2 = 0ull;
-    double td[2] = {0.0, 0.0}, t0d[2] = {0.0, 0.0};
+    TracePart T;
 
     int tile = blockIdx.x;
     int nz0 = rowptr[tile * R], nz1 = rowptr[min(tile * R + R, n)];
@@ -202,8 +170,7 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
                 if constexpr (MODE == MODE_DOT || MODE == MODE_ADJ) vr = vblk[(size_t)r * ldvq + cp];
 
                 // accumulate sum_k a_k W_j[c_k, pair]
-                double a0 = 0.0, a1 = 0.0;             // F64
-                f2x ah = 0ull, al = 0ull;              // DF64 (hi, lo pairs); F32 uses ah
+                RowAcc A;
                 for (int kb = 0; kb < nk; kb += U) {
                     WP x[U];
 #pragma unroll
@@ -213,77 +180,12 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
                     for (int u = 0; u < U; ++u) {
                         if (kb + u < nk) {
                             const int k = k0 + kb + u;
-                            if constexpr (PREC == LL_PREC_F64) {
-                                const double v = rawv[k];
-                                a0 = fma(v, x[u].x, a0);
-                                a1 = fma(v, x[u].y, a1);
-                            } else if constexpr (PREC == LL_PREC_DF64) {
-                                const ExDF v = in_smem ? ex[k] : expand(rawv[k]);
-                                df2_mac(ah, al, v.ah2, v.al2, v.nah2, x[u].x, x[u].y);
-                            } else {
-                                const f2x v = in_smem ? ex[k] : expand(rawv[k]);
-                                ah = f2_fma(v, x[u], ah);
-                            }
+                            if constexpr (PREC == LL_PREC_F64) row_mac<PREC>(A, rawv[k], x[u]);
+                            else row_mac<PREC>(A, in_smem ? ex[k] : expand(rawv[k]), x[u]);
                         }
                     }
                 }
-                // epilogue: shift by beta_j, store W_{j+1}, then the P-axpy or the trace
-                if constexpr (PREC == LL_PREC_F64) {
-                    double w0 = fma(p.beta, wr.x, a0), w1 = fma(p.beta, wr.y, a1);
-                    if constexpr (MODE == MODE_ADJ) {
-                        w0 = fma(cadj0, vr.x, w0);
-                        w1 = fma(cadj1, vr.y, w1);
-                    }
-                    wout[own] = make_double2(w0, w1);
-                    if constexpr (MODE == MODE_ACCUM) {
-                        const double b0 = p.first ? p.d0 * wr.x : po.x, b1 = p.first ? p.d0 * wr.y : po.y;
-                        pblk[(size_t)r * ldpq + cp] = make_double2(fma(p.dn, w0, b0), fma(p.dn, w1, b1));
-                    }
-                    if constexpr (MODE == MODE_DOT) {
-                        td[0] = fma(vr.x, w0, td[0]);
-                        td[1] = fma(vr.y, w1, td[1]);
-                        if (p.first) { t0d[0] = fma(vr.x, wr.x, t0d[0]); t0d[1] = fma(vr.y, wr.y, t0d[1]); }
-                    }
-                } else if constexpr (PREC == LL_PREC_DF64) {
-                    df2_mac(ah, al, bh2, bl2, nbh2, wr.x, wr.y);
-                    if constexpr (MODE == MODE_ADJ) df2_mac_pp(ah, al, ch2, cl2, nch2, vr.x, vr.y);
-                    f2x wh, wl;
-                    df2_norm(ah, al, wh, wl);
-                    wout[own] = make_ulonglong2(wh, wl);
-                    if constexpr (MODE == MODE_ACCUM) {
-                        f2x ph = zero2, pl = zero2;
-                        if (p.first) df2_mac(ph, pl, d0h2, d0l2, nd0h2, wr.x, wr.y);
-                        else { ph = po.x; pl = po.y; }
-                        df2_mac(ph, pl, dnh2, dnl2, ndnh2, wh, wl);
-                        f2x oh, ol;
-                        df2_norm(ph, pl, oh, ol);
-                        pblk[(size_t)r * ldpq + cp] = make_ulonglong2(oh, ol);
-                    }
-                    if constexpr (MODE == MODE_DOT) {
-                        const f2x nvh = f2_sub(zero2, vr.x);
-                        df2_mac_pp(th2, tl2, vr.x, vr.y, nvh, wh, wl);
-                        if (p.first) df2_mac_pp(t0h2, t0l2, vr.x, vr.y, nvh, wr.x, wr.y);
-                    }
-                } else {  // LL_PREC_F32_MIXED
-                    f2x wn = f2_fma(beta2, wr, ah);
-                    if constexpr (MODE == MODE_ADJ) wn = f2_fma(cf2, vr, wn);
-                    wout[own] = wn;
-                    if constexpr (MODE == MODE_ACCUM) {
-                        f2x ph = zero2, pl = zero2;
-                        if (p.first) df2_mac_f(ph, pl, d0h2, d0l2, nd0h2, wr);
-                        else { ph = po.x; pl = po.y; }
-                        df2_mac_f(ph, pl, dnh2, dnl2, ndnh2, wn);
-                        f2x oh, ol;
-                        df2_norm(ph, pl, oh, ol);
-                        pblk[(size_t)r * ldpq + cp] = make_ulonglong2(oh, ol);
-                    }
-                    if constexpr (MODE == MODE_DOT) {
-                        // exact FP32 products v * w accumulated in double-float
-                        const f2x nv = f2_sub(zero2, vr);
-                        df2_mac_f(th2, tl2, vr, zero2, nv, wn);
-                        if (p.first) df2_mac_f(t0h2, t0l2, vr, zero2, nv, wr);
-                    }
-                }
+                row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wout + own, pblk + (size_t)r * ldpq + cp, T);
             }
         }
         __syncthreads();
@@ -296,47 +198,8 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
     }
 
     if constexpr (MODE == MODE_DOT) {
-        if constexpr (PREC != LL_PREC_F64) {
-            float h0, h1, l0, l1;
-            f2_unpack(th2, h0, h1);
-            f2_unpack(tl2, l0, l1);
-            td[0] = (double)h0 + (double)l0;
-            td[1] = (double)h1 + (double)l1;
-            f2_unpack(t0h2, h0, h1);
-            f2_unpack(t0l2, l0, l1);
-            t0d[0] = (double)h0 + (double)l0;
-            t0d[1] = (double)h1 + (double)l1;
-        }
-        // block reduction per column, in row-lane order (deterministic)
-        double* red = reinterpret_cast<double*>(smem);
         __shared__ bool s_last;
-        const int b = p.b;
-        const int nred = p.first ? 2 : 1;
-        for (int q = 0; q < nred; ++q) {
-            red[2 * tid] = q ? t0d[0] : td[0];
-            red[2 * tid + 1] = q ? t0d[1] : td[1];
-            __syncthreads();
-            for (int c = tid; c < b; c += blockDim.x) {
-                const int pc = c >> 1, lane = c & 1;
-                double s = 0.0;
-                for (int l = 0; l < p.rl; ++l) s += red[2 * (l * tp + pc) + lane];
-                p.partials[((size_t)q * gridDim.x + blockIdx.x) * b + c] = s;
-            }
-            __syncthreads();
-        }
-        __threadfence();
-        if (tid == 0) s_last = (atomicAdd(p.ticket, 1u) == gridDim.x - 1);
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            for (int c = tid; c < nred * b; c += blockDim.x) {
-                const int q = c / b, cc = c - q * b;
-                double s = 0.0;
-                for (int g = 0; g < (int)gridDim.x; ++g) s += __ldcg(&p.partials[((size_t)q * gridDim.x + g) * b + cc]);
-                if (q == 0) p.dots_next[cc] = s; else p.dots_first[cc] = s;
-            }
-            if (tid == 0) *p.ticket = 0u;
-        }
+        trace_reduce<PREC>(p, T, reinterpret_cast<double*>(smem), tp, p.rl, &s_last);
     }
 }
 

@@ -133,13 +133,20 @@ def gmrf_batch_params(count: int = 64, seed: int = 2, side_lo: int = 64, side_hi
 
 
 def powerlaw_laplacian(n: int, mean_degree: float = 16.0, beta: float = 2.3, seed: int = 3,
-                       shift: float = 1e-2, w_lo: float = 0.5, w_hi: float = 1.5) -> CSR:
+                       shift: float = 1e-2, w_lo: float = 0.5, w_hi: float = 1.5, device=None) -> CSR:
     """Weighted Laplacian (D - W) + shift*I of a Chung-Lu random graph with power-law degrees.
 
     Expected degrees w_i proportional to (i+1)^(-1/(beta-1)), rescaled to the requested mean and
     capped at sqrt(sum w). mean_degree*n/2 endpoint pairs are drawn with probability
-    proportional to w; self-loops are dropped, repeated pairs are merged into one edge, each edge
-    gets a weight U[w_lo, w_hi], and vertices are relabelled by a random permutation.
+    proportional to w (inverse CDF of uniform draws); self-loops are dropped, repeated pairs are
+    merged into one edge, each edge gets a weight U[w_lo, w_hi], and vertices are relabelled by a
+    random permutation. Degrees are summed per vertex in edge order (bincount), and the CSR lists
+    each row's entries by ascending column.
+
+    device: None runs everything in NumPy; a torch device (e.g. "cuda") runs the inverse-CDF
+    search, the duplicate merge and the CSR sort there. The random draws come from the same NumPy
+    generator and the degree sums are taken on the host in the same order, so both give the same
+    CSR bit for bit; the device path only makes the n = 2^22 instance quick to build.
     """
     rng = np.random.default_rng(seed)
     w = np.arange(1, n + 1, dtype=np.float64) ** (-1.0 / (beta - 1.0))
@@ -148,26 +155,52 @@ def powerlaw_laplacian(n: int, mean_degree: float = 16.0, beta: float = 2.3, see
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
     n_pairs = int(round(mean_degree * n / 2))
-    u = np.searchsorted(cdf, rng.random(n_pairs), side="right")
-    v = np.searchsorted(cdf, rng.random(n_pairs), side="right")
-    np.minimum(u, n - 1, out=u)
-    np.minimum(v, n - 1, out=v)
-    keep = u != v
-    u, v = u[keep], v[keep]
-    lo = np.minimum(u, v).astype(np.int64)
-    hi = np.maximum(u, v).astype(np.int64)
-    key = np.unique(lo * n + hi)
+    r1 = rng.random(n_pairs)
+    r2 = rng.random(n_pairs)
+    if device is None:
+        u = np.searchsorted(cdf, r1, side="right")
+        v = np.searchsorted(cdf, r2, side="right")
+        np.minimum(u, n - 1, out=u)
+        np.minimum(v, n - 1, out=v)
+        keep = u != v
+        u, v = u[keep], v[keep]
+        lo = np.minimum(u, v).astype(np.int64)
+        hi = np.maximum(u, v).astype(np.int64)
+        key = np.unique(lo * n + hi)
+    else:
+        import torch
+        tc = torch.from_numpy(cdf).to(device)
+        u = torch.searchsorted(tc, torch.from_numpy(r1).to(device), right=True).clamp_(max=n - 1)
+        v = torch.searchsorted(tc, torch.from_numpy(r2).to(device), right=True).clamp_(max=n - 1)
+        keep = u != v
+        u, v = u[keep], v[keep]
+        tkey = torch.unique(torch.minimum(u, v) * n + torch.maximum(u, v), sorted=True)
+        key = tkey.cpu().numpy()
+        del u, v, keep, tc
     lo, hi = key // n, key % n
     wt = w_lo + (w_hi - w_lo) * rng.random(key.shape[0])
     perm = rng.permutation(n)
     lo, hi = perm[lo], perm[hi]
-    rows = np.concatenate([lo, hi])
-    cols = np.concatenate([hi, lo])
-    vals = np.concatenate([-wt, -wt])
-    W = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
-    deg = -np.asarray(W.sum(axis=1)).ravel()
-    L = W + sp.diags(deg + shift, 0, format="csr")
-    return CSR.from_scipy(L)
+    deg = np.bincount(lo, weights=wt, minlength=n) + np.bincount(hi, weights=wt, minlength=n)
+    diag = np.arange(n, dtype=np.int64)
+    rows = np.concatenate([lo, hi, diag])
+    cols = np.concatenate([hi, lo, diag])
+    vals = np.concatenate([-wt, -wt, deg + shift])
+    if device is None:
+        order = np.argsort(rows * n + cols, kind="stable")
+        rows, cols, vals = rows[order], cols[order], vals[order]
+    else:
+        import torch
+        tr = torch.from_numpy(rows).to(device)
+        tcl = torch.from_numpy(cols).to(device)
+        order = torch.argsort(tr * n + tcl)
+        rows = tr[order].cpu().numpy()
+        cols = tcl[order].cpu().numpy()
+        vals = torch.from_numpy(vals).to(device)[order].cpu().numpy()
+        del tr, tcl, order
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
+    return CSR(n=n, rowptr=rowptr.astype(np.int32), colind=cols.astype(np.int32), values=vals)
 
 
 def pentadiagonal(n: int, seed: int = 0) -> CSR:
