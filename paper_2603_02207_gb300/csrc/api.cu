@@ -49,7 +49,7 @@ struct ll_handle {
         int launches = 0, k1 = 0, t1 = 0, k2 = 0, t2 = 0;
         bool tma = false;
     } gfwd;
-    int max_fwd_offset = 0;   // largest col - row of the last validated matrix
+    int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
     int dd_degree = -1, dd_sval = -1, dd_terms = 0;
@@ -129,7 +129,7 @@ ll_status validate_csr(ll_handle* h, const ll_csr* A, cudaStream_t s) {
     LL_CK(cudaMemcpyAsync(hv, flag, sizeof hv, cudaMemcpyDeviceToHost, s));
     LL_CK(cudaStreamSynchronize(s));
     const int hf = hv[0];
-    h->max_fwd_offset = hv[1];
+    h->far_entries = hv[1];
     if (hf) {
         char buf[160];
         snprintf(buf, sizeof buf, "invalid CSR:%s%s%s", (hf & 4) ? " rowptr[0]!=0 or rowptr[n]!=nnz;" : "",
@@ -179,7 +179,7 @@ bool plan_exec(ll_handle* h, int kind, int precision, int mode, int n, int64_t n
     E.rpt = rpt;
     if (kind == LL_KERNEL_TMA) {
         const int ctas = (threads > 0 && threads <= 256) ? 2 : 1;
-        if (!plan_step_tma(precision, mode, n, nnz, b, threads, ctas, p, E.tl, h->sm_count)) return false;
+        if (!plan_step_tma(precision, mode, n, nnz, h->far_entries, b, threads, ctas, p, E.tl, h->sm_count)) return false;
         E.tl.q.spin_budget = h->spin_budget;
         E.tl.q.inject = h->inject;
         return true;

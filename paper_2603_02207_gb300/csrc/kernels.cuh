@@ -56,8 +56,11 @@ cudaError_t launch_step(int precision, int mode, const StepLaunch& L, const Step
 // [cols, pad) are set to zero (pad = cols for none)
 cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols, int pad,
                           void* out, long long ld, cudaStream_t s);
+// rows of halo on each side of a TMA step tile's window (entries with |col - row| <= TMA_HALO are
+// always served from the window)
+constexpr int TMA_HALO = 2;
 // flag[0]: error bits (1 rowptr decreasing, 2 column out of range, 4 rowptr[0] != 0 or rowptr[n] != nnz);
-// flag[1]: largest forward offset max(col - row) over the stored entries (>= 0)
+// flag[1]: stored entries with |col - row| > TMA_HALO (int32; saturates nowhere below 2^31)
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz,
                                 int* flag, cudaStream_t s);
 cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype,
@@ -184,15 +187,17 @@ struct BatchParams {
 // ---- TMA-fed step (k_leja_tma): geometry of the shared-memory pipeline -------------------------
 struct TmaParams {
     int R;             // rows per tile (one row lane each)
-    int rbox;          // rows of the own / aux tile boxes
-    int gcap;          // entries per tile gathered by TMA (multiple of 4); later entries load directly
+    int ecap;          // entries per tile with a record in shared memory; later entries load directly
+    int fcap;          // far entries per tile gathered by TMA (multiple of 4); later far entries load directly
     int nst;           // pipeline stages (tiles in flight + 1)
+    int nprod;         // producer warps
     int slot;          // bytes of one gather4 slot (4 rows, 128-byte aligned)
     int rowbytes;      // bytes of one W row (ld * element size)
     int auxbytes;      // bytes of one V (pass 2, adjoint) or P (pass 1) row; 0 without
-    int stage_bytes;   // bytes per stage: gathered rows, own rows, aux rows, expanded values, row pointers
-    int off_own, off_aux, off_ex, off_rp;
-    int csr_bytes, csr_col, csr_val, csr_base;   // CSR ring (three slots) after the stages
+    int recbytes;      // bytes of one entry record (expanded value, operand offset, column)
+    int stage_bytes;   // bytes per stage: window, aux rows, gathered rows, records, gather columns, row offsets
+    int off_aux, off_gat, off_rec, off_gcol, off_rp;   // the window is at offset 0
+    int csr_bytes, csr_col, csr_val, csr_base;   // CSR ring after the stages
     int* error;                                  // set to 1 when a bounded wait runs out
     long long spin_budget;                       // clock64 cycles a wait may spin
     int inject;                                  // test hook: tile 0 expects bytes no copy delivers
@@ -205,8 +210,9 @@ struct TmaLaunch {
 // Shape of a TMA-fed step launch; false when the block layout does not allow TMA (a row wider than
 // 256 elements or not a multiple of 16 bytes) or the pipeline does not fit in shared memory.
 // ctas_per_sm: 1 (one 512-thread CTA with ~223 KB of stages) or 2 (two of half the size).
-bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int b, int threads_target, int ctas_per_sm,
-                   StepParams& p, TmaLaunch& L, int sm_count);
+// nfar: entries with |col - row| > TMA_HALO (sizes the gather slots; a hint, not a bound)
+bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int b, int threads_target,
+                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count);
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s);
 
 void plan_batched(int b, double avg_nnz_per_row, BatchParams& bp, size_t* smem);

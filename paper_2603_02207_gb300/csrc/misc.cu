@@ -40,7 +40,7 @@ __global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (tid == 0 && (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) atomicOr(flag, 4);
-    int maxoff = 0;
+    int far = 0;
     for (int i = tid; i < n; i += stride) {
         const int a = rowptr[i], e = rowptr[i + 1];
         if (e < a) { atomicOr(flag, 1); continue; }
@@ -48,10 +48,10 @@ __global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int
         for (int k = a; k < e; ++k) {
             const int c = colind[k];
             if (c < 0 || c >= n) atomicOr(flag, 2);
-            else maxoff = max(maxoff, c - i);
+            else far += (c - i > TMA_HALO || i - c > TMA_HALO) ? 1 : 0;
         }
     }
-    if (maxoff > 0) atomicMax(flag + 1, maxoff);
+    if (far > 0) atomicAdd(flag + 1, far);
 }
 
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, cudaStream_t s) {

@@ -7,13 +7,16 @@
 //     row-major block per instruction, rows given by the column indices),
 //   * the tile's own rows W_j[r, :] and its V (pass 2, adjoint) or P (pass 1) rows by 2-D tile
 //     loads,
-// all completing on one mbarrier per pipeline stage. The CTA runs a software pipeline over its
-// tiles (persistent, round robin): while tile i is computed, the copies of tiles i+1 .. i+D are in
-// flight and the CSR segment of tile i+D+1 is staged with cp.async. A thread owns one row of the
-// tile and one column pair, reads the gathered rows from shared memory, and writes W_{j+1} (and P)
-// straight to global memory. Entries of a tile beyond the gather capacity (long rows) are read
-// directly from global memory. Every wait on an mbarrier is bounded (clock64 budget); when one runs
-// out the kernel records the error, stops issuing copies, drains what it issued and returns.
+// all completing on one mbarrier per pipeline stage. The CTA is warp-specialised and persistent
+// (tiles i, i + grid, ...): its last warp produces (stages each tile's CSR segment two tiles ahead
+// with cp.async, writes the tile's row offsets and expanded values into a free stage, and issues
+// the copies), the other warps consume (a thread owns one row of the tile and one column pair,
+// reads the gathered rows from shared memory and writes W_{j+1} (and P) straight to global memory,
+// then its warp releases the stage). Full and empty barriers per stage replace block-wide
+// barriers, so consumer warps drift up to the stage count apart. Entries of a tile beyond the
+// gather capacity (long rows) are read directly from global memory. Every wait on an mbarrier is
+// bounded (clock64 budget); when one runs out the kernel records the error, stops issuing copies,
+// waits (bounded) for the copies it issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -26,8 +29,8 @@
 namespace ll {
 
 constexpr int TMA_MAX_STAGES = 6;
-constexpr int TMA_MAX_THREADS = 512;
-constexpr int TMA_CSR_SLOTS = 3;
+constexpr int TMA_MAX_THREADS = 640;   // up to 512 consumer threads and four producer warps
+constexpr int TMA_CSR_SLOTS = 5;   // CSR segments staged up to four tiles ahead
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -88,179 +91,280 @@ __device__ __forceinline__ void cp_async8_(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// Entry record written by the producer for every staged entry of a tile: the matrix value expanded
+// for the f32x2 instructions, the byte offset of its operand row W_j[c, :] in the stage (window or
+// gather slot; -1 when the row is read from global memory) and the column c.
+template <int PREC> struct Rec;
+template <> struct Rec<LL_PREC_F64> { double a; int off, col; };
+template <> struct Rec<LL_PREC_DF64> { ExDF a; int off, col; };
+template <> struct Rec<LL_PREC_F32_MIXED> { f2x a; int off, col; };
+
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
-    k_leja_tma(const __grid_constant__ CUtensorMap tm_gather, const __grid_constant__ CUtensorMap tm_own,
+    k_leja_tma(const __grid_constant__ CUtensorMap tm_gather, const __grid_constant__ CUtensorMap tm_win,
                const __grid_constant__ CUtensorMap tm_aux, const StepParams p, const TmaParams q) {
     using WP = typename PairT<PREC>::W;
     using PP = typename PairT<PREC>::P;
     using Raw = typename PairT<PREC>::Raw;
-    using Ex = typename ExT<PREC>::T;
+    using RecT = Rec<PREC>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full[TMA_MAX_STAGES];
+    __shared__ __align__(8) unsigned long long empty[TMA_MAX_STAGES];
+    __shared__ bool s_last;
     // TMA destinations are 128-byte aligned: the plan reserves 128 bytes for this offset
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    __shared__ bool s_last;
 
     const int tid = threadIdx.x;
     const int tp = p.tp;
     const int R = q.R;
     const int NST = q.nst;
-    const int D = NST - 1;
-    const int rlane = tid / tp;
-    const int cp = tid - rlane * tp;
-    const bool active = rlane < R;
+    const int nprod = q.nprod;                        // producer warps (the last warps of the CTA)
+    const int cthreads = (int)blockDim.x - 32 * nprod;   // consumer threads
+    const int cwarps = cthreads >> 5;
     const int n = p.n;
-    const long long ldq = p.ldw >> 1;
-    const long long ldpq = p.ldp >> 1;
-    const WP* __restrict__ win = static_cast<const WP*>(p.win);
-    WP* __restrict__ wout = static_cast<WP*>(p.wout);
-    const Raw* __restrict__ vals = static_cast<const Raw*>(p.vals);
-    PP* __restrict__ pblk = static_cast<PP*>(p.p);
-    const int* __restrict__ rowptr = p.rowptr;
-    const int* __restrict__ colind = p.colind;
     const bool has_aux = (MODE == MODE_DOT || MODE == MODE_ADJ) || (MODE == MODE_ACCUM && !p.first);
 
     if (tid == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(smem_u32(&full[s]), 1);
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);         // the issuing producer's lane 0 (with the byte count)
+            mbar_init(smem_u32(&empty[s]), cwarps);   // one arrival per consumer warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
 
-    const StepScalars<PREC> S(p, cp);
-    TracePart T;
-
     const int nt = p.num_tiles;
     const int my = (int)blockIdx.x < nt ? (nt - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto row0_of = [&](int i) { return ((int)blockIdx.x + i * (int)gridDim.x) * R; };
-    unsigned char* csr = smem + q.csr_base;
-
-    // nnz range [zs0, zs1) of the next tile whose CSR segment is staged (loaded one iteration ahead)
-    int zs0 = 0, zs1 = 0;
-    if (my > 0) {
-        const int r0 = row0_of(0);
-        zs0 = rowptr[r0];
-        zs1 = rowptr[min(r0 + R, n)];
-    }
-
+    const int rstep = (int)gridDim.x * R;   // rows between this CTA's consecutive tiles
     bool dead = false;
-    int issued = 0;   // tiles whose copies were issued (the same on every thread)
-    int waited = 0;   // tiles this thread saw complete
-    for (int i = -D - 1; i < my; ++i) {
-        // (A) CSR segment (row pointers, the first gcap column indices and values) of tile i + D + 1
-        const int js = i + D + 1;
-        if (js < my) {
-            unsigned char* slot = csr + (js % TMA_CSR_SLOTS) * q.csr_bytes;
-            int* drp = reinterpret_cast<int*>(slot);
-            int* dcol = reinterpret_cast<int*>(slot + q.csr_col);
-            Raw* dval = reinterpret_cast<Raw*>(slot + q.csr_val);
-            const int r0 = row0_of(js);
-            const int nr = min(R, n - r0);
-            const int g = min(zs1 - zs0, q.gcap);
-            for (int e = tid; e <= nr; e += blockDim.x) cp_async4_(drp + e, rowptr + r0 + e);
-            for (int e = tid; e < g; e += blockDim.x) {
-                cp_async4_(dcol + e, colind + zs0 + e);
-                if constexpr (sizeof(Raw) == 8) cp_async8_(dval + e, vals + zs0 + e);
-                else cp_async4_(dval + e, vals + zs0 + e);
-            }
-            if (js + 1 < my) {
-                const int r0n = row0_of(js + 1);
-                zs0 = rowptr[r0n];
-                zs1 = rowptr[min(r0n + R, n)];
-            }
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        // (B) every group but the newest has landed: the segment of tile i + D is here
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        // (C) publish it; every thread is done with tile i - 1 (its stage and CSR slot are free)
-        const int any_dead = __syncthreads_or(dead ? 1 : 0);
+    TracePart T;
 
-        // (D) issue the copies of tile i + D into stage (i + D) % NST
-        const int ji = i + D;
-        if (!any_dead && ji >= 0 && ji < my) {
-            unsigned char* st = smem + (ji % NST) * q.stage_bytes;
-            const unsigned char* slot = csr + (ji % TMA_CSR_SLOTS) * q.csr_bytes;
+    if (tid >= cthreads) {
+        // ------------------------------------------------------------------ producer warps
+        // warp w of the nprod producers issues tiles w, w + nprod, ... from its own CSR ring
+        const int pw = (tid - cthreads) >> 5;
+        const int lane = (tid - cthreads) & 31;
+        const Raw* __restrict__ vals = static_cast<const Raw*>(p.vals);
+        const int* __restrict__ rowptr = p.rowptr;
+        const int* __restrict__ colind = p.colind;
+        unsigned char* csr = smem + q.csr_base + pw * TMA_CSR_SLOTS * q.csr_bytes;
+        constexpr int LOOK = TMA_CSR_SLOTS - 1;   // CSR segments staged ahead of the issue
+        // nnz ranges of the CTA's tiles, 32 tiles per batch (lane l holds tile zb + l), the next
+        // batch loaded one batch ahead
+        const int myp = my > pw ? (my - 1 - pw) / nprod + 1 : 0;   // tiles of this producer
+        auto tile_range = [&](int t, int& lo, int& hi) {   // t: this producer's tile count
+            lo = hi = 0;
+            if (t < myp) {
+                const int rr = ((int)blockIdx.x + (pw + t * nprod) * (int)gridDim.x) * R;
+                lo = rowptr[rr];
+                hi = rowptr[min(rr + R, n)];
+            }
+        };
+        int zb = 0, zlo, zhi, nlo, nhi;
+        tile_range(lane, zlo, zhi);
+        tile_range(32 + lane, nlo, nhi);
+        int sslot = 0;   // CSR slot of the next tile to stage
+        // stage the CSR segment (row pointers, the first ecap indices and values) of tile js
+        auto stage_next = [&](int js) {
+            if (js < myp) {
+                if (js >= zb + 32) {
+                    zb += 32;
+                    zlo = nlo;
+                    zhi = nhi;
+                    tile_range(zb + 32 + lane, nlo, nhi);
+                }
+                const int zs0 = __shfl_sync(0xffffffffu, zlo, js - zb);
+                const int zs1 = __shfl_sync(0xffffffffu, zhi, js - zb);
+                const int zrow = ((int)blockIdx.x + (pw + js * nprod) * (int)gridDim.x) * R;
+                unsigned char* slot = csr + sslot * q.csr_bytes;
+                int* drp = reinterpret_cast<int*>(slot);
+                int* dcol = reinterpret_cast<int*>(slot + q.csr_col);
+                Raw* dval = reinterpret_cast<Raw*>(slot + q.csr_val);
+                const int nr = min(R, n - zrow);
+                const int g = min(zs1 - zs0, q.ecap);
+                for (int e = lane; e <= nr; e += 32) cp_async4_(drp + e, rowptr + zrow + e);
+                for (int e = lane; e < g; e += 32) {
+                    cp_async4_(dcol + e, colind + zs0 + e);
+                    if constexpr (sizeof(Raw) == 8) cp_async8_(dval + e, vals + zs0 + e);
+                    else cp_async4_(dval + e, vals + zs0 + e);
+                }
+                if (++sslot == TMA_CSR_SLOTS) sslot = 0;
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        };
+        for (int js = 0; js < LOOK; ++js) stage_next(js);
+        const unsigned lt_mask = (1u << lane) - 1u;
+        int islot = 0;          // CSR slot of the tile being issued
+        int issued = 0;
+        for (int ii = 0; ii < myp; ++ii) {
+            const int i = pw + ii * nprod;   // the CTA's tile index
+            const int s = i % NST, ph = (i / NST) & 1;
+            const int r0 = ((int)blockIdx.x + i * (int)gridDim.x) * R;
+            stage_next(ii + LOOK);
+            asm volatile("cp.async.wait_group %0;\n" ::"n"(LOOK) : "memory");   // tile i's segment is here
+            __syncwarp();
+            // the stage is free once every consumer warp released its previous tile
+            if (i >= NST) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait_bounded(smem_u32(&empty[s]), (uint32_t)(ph ^ 1), q.spin_budget);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) {
+                    dead = true;
+                    if (lane == 0) *((volatile int*)q.error) = 1;
+                    break;
+                }
+            }
+            unsigned char* st = smem + s * q.stage_bytes;
+            const unsigned char* slot = csr + islot * q.csr_bytes;
             const int* crp = reinterpret_cast<const int*>(slot);
             const int* ccol = reinterpret_cast<const int*>(slot + q.csr_col);
             const Raw* cval = reinterpret_cast<const Raw*>(slot + q.csr_val);
-            const int r0 = row0_of(ji);
             const int nr = min(R, n - r0);
             const int z0 = crp[0];
-            const int g = min(crp[nr] - z0, q.gcap);
-            const int ngr = (g + 3) >> 2;
+            const int g = min(crp[nr] - z0, q.ecap);
+            // entry records: columns inside the window [r0 - HALO, r0 + R + HALO) read the window,
+            // the others get the next gather slot (in entry order) while slots last
+            RecT* rec = reinterpret_cast<RecT*>(st + q.off_rec);
+            int* gcol = reinterpret_cast<int*>(st + q.off_gcol);
+            const int wlo = r0 - TMA_HALO, whi = r0 + R + TMA_HALO;
+            int nfar = 0;
+            for (int e0 = 0; e0 < g; e0 += 32) {
+                const int e = e0 + lane;
+                const bool valid = e < g;
+                const int c = valid ? ccol[e] : 0;
+                const bool near = c >= wlo && c < whi;
+                const unsigned farm = __ballot_sync(0xffffffffu, valid && !near);
+                if (valid) {
+                    int off;
+                    if (near) {
+                        off = (c - wlo) * q.rowbytes;
+                    } else {
+                        const int fs = nfar + __popc(farm & lt_mask);
+                        if (fs < q.fcap) {
+                            off = q.off_gat + (fs >> 2) * q.slot + (fs & 3) * q.rowbytes;
+                            gcol[fs] = c;
+                        } else {
+                            off = -1;
+                        }
+                    }
+                    RecT rr;
+                    rr.a = expand(cval[e]);
+                    rr.off = off;
+                    rr.col = c;
+                    rec[e] = rr;
+                }
+                nfar += __popc(farm);
+            }
+            const int ng = min(nfar, q.fcap);
+            const int ngr = (ng + 3) >> 2;
             int* srp = reinterpret_cast<int*>(st + q.off_rp);
-            for (int e = tid; e <= nr; e += blockDim.x) srp[e] = crp[e] - z0;
-            if (tid == 0) {
+            for (int e = lane; e <= nr; e += 32) srp[e] = crp[e] - z0;
+            if (lane == 0) {
                 srp[R + 1] = z0;
                 srp[R + 2] = g;
             }
-            Ex* sex = reinterpret_cast<Ex*>(st + q.off_ex);
-            for (int e = tid; e < g; e += blockDim.x) sex[e] = expand(cval[e]);
-            const uint32_t bar = smem_u32(&full[ji % NST]);
-            if (tid == 0) {
+            __syncwarp();   // gather columns and records written (published by lane 0's release-arrive)
+            const uint32_t bar = smem_u32(&full[s]);
+            if (lane == 0) {
                 // (the test hook adds 16 bytes to tile 0 that no copy delivers: its waits run out)
-                const uint32_t bytes = (uint32_t)ngr * 4u * (uint32_t)q.rowbytes + (uint32_t)q.rbox * (uint32_t)q.rowbytes +
-                                       (has_aux ? (uint32_t)q.rbox * (uint32_t)q.auxbytes : 0u) +
-                                       ((q.inject && ji == 0) ? 16u : 0u);
+                const uint32_t bytes = (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
+                                       (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
+                                       (has_aux ? (uint32_t)R * (uint32_t)q.auxbytes : 0u) +
+                                       ((q.inject && i == 0) ? 16u : 0u);
                 mbar_arrive_expect_tx(bar, bytes);
-                tma_load_rows(smem_u32(st + q.off_own), &tm_own, r0, bar);
+                // the window may start above row 0 or end below row n: those rows are zero-filled
+                tma_load_rows(smem_u32(st), &tm_win, wlo, bar);
                 if (has_aux) tma_load_rows(smem_u32(st + q.off_aux), &tm_aux, r0, bar);
             }
-            for (int gi = tid; gi < ngr; gi += blockDim.x) {
+            __syncwarp();
+            for (int gi = lane; gi < ngr; gi += 32) {
                 const int e = 4 * gi;
-                tma_gather4(smem_u32(st + (size_t)gi * q.slot), &tm_gather, ccol[e], ccol[min(e + 1, g - 1)],
-                            ccol[min(e + 2, g - 1)], ccol[min(e + 3, g - 1)], bar);
+                tma_gather4(smem_u32(st + q.off_gat + gi * q.slot), &tm_gather, gcol[e], gcol[min(e + 1, ng - 1)],
+                            gcol[min(e + 2, ng - 1)], gcol[min(e + 3, ng - 1)], bar);
             }
+            __syncwarp();
             ++issued;
+            if (++islot == TMA_CSR_SLOTS) islot = 0;
         }
-
-        // (E) compute tile i
-        if (i >= 0 && i < issued && !dead) {
-            const int s = i % NST;
-            if (mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((i / NST) & 1), q.spin_budget)) {
-                waited = i + 1;
-            } else {
-                dead = true;
-                *((volatile int*)q.error) = 1;
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        // after a timeout, wait (bounded) for the copies of the last tiles issued (earlier uses of
+        // its stages were released by the consumers, so their copies completed), so that none lands
+        // in shared memory after the CTA exits
+        if (dead && lane == 0) {
+            const long long drain = q.spin_budget > TMA_DRAIN_MIN ? q.spin_budget : TMA_DRAIN_MIN;
+            // this producer owns stages pw, pw + nprod, ...: its last nst / nprod tiles are the most
+            // recent use of each of them
+            for (int jj = max(0, issued - NST / nprod); jj < issued; ++jj) {
+                const int j = pw + jj * nprod;
+                mbar_wait_bounded(smem_u32(&full[j % NST]), (uint32_t)((j / NST) & 1), drain);
             }
-            const int r0 = row0_of(i);
-            const int r = r0 + rlane;
-            if (!dead && active && r < n) {
-                const unsigned char* st = smem + s * q.stage_bytes;
+        }
+    } else {
+        // ------------------------------------------------------------------ consumer warps
+        const int rlane = tid / tp;
+        const int cp = tid - rlane * tp;
+        const bool active = rlane < R;
+        const long long ldq = p.ldw >> 1;
+        const long long ldpq = p.ldp >> 1;
+        const WP* __restrict__ win = static_cast<const WP*>(p.win);
+        WP* __restrict__ wout = static_cast<WP*>(p.wout);
+        const Raw* __restrict__ vals = static_cast<const Raw*>(p.vals);
+        PP* __restrict__ pblk = static_cast<PP*>(p.p);
+        const int* __restrict__ colind = p.colind;
+        const StepScalars<PREC> S(p, cp);
+        const unsigned cpoff = (unsigned)(cp * sizeof(WP));
+        const unsigned own_off = (unsigned)(rlane + TMA_HALO) * (unsigned)q.rowbytes + cpoff;
+        const unsigned aux_off = (unsigned)q.off_aux + (unsigned)rlane * (unsigned)q.auxbytes +
+                                 (unsigned)(cp * (MODE == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
+        int s = 0, ph = 0;
+        int r = (int)blockIdx.x * R + rlane;
+        for (int i = 0; i < my; ++i) {
+            // every lane waits (acquiring the stage's copies); the warp gives up together
+            const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)ph, q.spin_budget);
+            if (!__all_sync(0xffffffffu, ok)) {
+                dead = true;
+                if ((tid & 31) == 0) *((volatile int*)q.error) = 1;
+                break;
+            }
+            const unsigned char* st = smem + s * q.stage_bytes;
+            if (active && r < n) {
                 const int* srp = reinterpret_cast<const int*>(st + q.off_rp);
-                const Ex* sex = reinterpret_cast<const Ex*>(st + q.off_ex);
+                const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_rec);
                 const int k0 = srp[rlane], k1 = srp[rlane + 1];
-                const int z0 = srp[R + 1], g = srp[R + 2];
-                const WP wr = *reinterpret_cast<const WP*>(st + q.off_own + (size_t)rlane * q.rowbytes + cp * sizeof(WP));
+                const int g = srp[R + 2];
+                const WP wr = *reinterpret_cast<const WP*>(st + own_off);
                 WP vr{};
                 PP po{};
-                if constexpr (MODE == MODE_DOT || MODE == MODE_ADJ)
-                    vr = *reinterpret_cast<const WP*>(st + q.off_aux + (size_t)rlane * q.auxbytes + cp * sizeof(WP));
+                if constexpr (MODE == MODE_DOT || MODE == MODE_ADJ) vr = *reinterpret_cast<const WP*>(st + aux_off);
                 if constexpr (MODE == MODE_ACCUM) {
-                    if (!p.first) po = *reinterpret_cast<const PP*>(st + q.off_aux + (size_t)rlane * q.auxbytes + cp * sizeof(PP));
+                    if (!p.first) po = *reinterpret_cast<const PP*>(st + aux_off);
                 }
                 RowAcc A;
                 const int kend = min(k1, g);
-                const unsigned char* gcol = st + cp * sizeof(WP);
+                const unsigned char* stc = st + cpoff;
 #pragma unroll 4
                 for (int k = k0; k < kend; ++k) {
-                    const WP x = *reinterpret_cast<const WP*>(gcol + (size_t)(k >> 2) * q.slot + (size_t)(k & 3) * q.rowbytes);
-                    row_mac<PREC>(A, sex[k], x);
+                    const RecT rk = rec[k];
+                    const WP x = rk.off >= 0 ? *reinterpret_cast<const WP*>(stc + rk.off) : win[(size_t)rk.col * ldq + cp];
+                    row_mac<PREC>(A, rk.a, x);
                 }
-                for (int k = max(k0, g); k < k1; ++k) {   // beyond the gather capacity: direct loads
-                    const WP x = win[(size_t)colind[z0 + k] * ldq + cp];
-                    row_mac<PREC>(A, expand(vals[z0 + k]), x);
+                if (k1 > g) {   // beyond the record capacity: direct loads
+                    const int z0 = srp[R + 1];
+                    for (int k = max(k0, g); k < k1; ++k) {
+                        const WP x = win[(size_t)colind[z0 + k] * ldq + cp];
+                        row_mac<PREC>(A, expand(vals[z0 + k]), x);
+                    }
                 }
                 row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wout + (size_t)r * ldq + cp, pblk + (size_t)r * ldpq + cp, T);
             }
+            __syncwarp();
+            if ((tid & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&empty[s])) : "memory");
+            r += rstep;
+            if (++s == NST) {
+                s = 0;
+                ph ^= 1;
+            }
         }
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    // after a timeout, wait (bounded, tile by tile) for the copies this CTA issued but did not
-    // consume, so that none lands in shared memory after the CTA exits
-    if (tid == 0 && dead) {
-        const long long drain = q.spin_budget > TMA_DRAIN_MIN ? q.spin_budget : TMA_DRAIN_MIN;
-        for (int j = waited; j < issued; ++j) mbar_wait_bounded(smem_u32(&full[j % NST]), (uint32_t)((j / NST) & 1), drain);
     }
     const int any_dead = __syncthreads_or(dead ? 1 : 0);
     if constexpr (MODE == MODE_DOT) {
@@ -304,7 +408,9 @@ size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
 
 size_t raw_size(int precision) { return precision == LL_PREC_F64 ? 8 : (precision == LL_PREC_DF64 ? 8 : 4); }
-size_t ex_size(int precision) { return precision == LL_PREC_F64 ? 8 : (precision == LL_PREC_DF64 ? 24 : 8); }
+size_t rec_size(int precision) {
+    return precision == LL_PREC_F64 ? sizeof(Rec<LL_PREC_F64>) : (precision == LL_PREC_DF64 ? sizeof(Rec<LL_PREC_DF64>) : sizeof(Rec<LL_PREC_F32_MIXED>));
+}
 
 template <int PREC, int MODE>
 int occupancy_tma(int threads, size_t smem) {
@@ -328,8 +434,8 @@ cudaError_t launch_tma_typed(const TmaLaunch& L, const CUtensorMap& g, const CUt
 
 }  // namespace
 
-bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int b, int threads_target, int ctas_per_sm,
-                   StepParams& p, TmaLaunch& L, int sm_count) {
+bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int b, int threads_target,
+                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count) {
     L = TmaLaunch{};
     if (n <= 0 || b <= 0 || !encode_fn()) return false;
     if (ctas_per_sm < 1 || ctas_per_sm > 2) ctas_per_sm = 1;
@@ -344,44 +450,79 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int b, int threa
         if (p.ldp > 256 || (p.ldp * 8) % 16 != 0) return false;
         auxbytes = (int)(p.ldp * 8);
     }
-    if (threads_target <= 0 || threads_target > TMA_MAX_THREADS) threads_target = TMA_MAX_THREADS / ctas_per_sm;
+    if (threads_target <= 0 || threads_target > 512) threads_target = 512 / ctas_per_sm;
     const int tp = (b + 1) / 2;
     int R = threads_target / tp;
     if (R < 1) R = 1;
-    if (R > 256) R = 256;
-    if (R > n) R = n;
-    if (R * tp > TMA_MAX_THREADS) return false;
+    if (R > 256 - 2 * TMA_HALO) R = 256 - 2 * TMA_HALO;   // window box rows <= 256
+    if (R + 2 * TMA_HALO > n) R = n - 2 * TMA_HALO;        // a box no taller than the matrix
+    if (R < 1 || R * tp > 512) return false;
     TmaParams& q = L.q;
-    q.R = R;
-    q.rbox = R;
     q.rowbytes = (int)(ld * ew);
     q.auxbytes = auxbytes;
     q.slot = (int)a128((size_t)4 * q.rowbytes);
+    q.recbytes = (int)rec_size(precision);
     const double avg = (double)nnz / (double)n;
+    const double avgfar = nfar >= 0 && nfar <= nnz ? (double)nfar / (double)n : avg;
     const size_t budget = (ctas_per_sm == 2 ? 112 : 224) * 1024 - 1024;
-    int gcap = (((int)(avg * R * 1.15) + 8) + 3) & ~3;
-    if (gcap > 4096) gcap = 4096;
-    for (int attempt = 0; attempt < 8; ++attempt) {
-        q.gcap = gcap;
-        q.off_own = (gcap / 4) * q.slot;
-        q.off_aux = q.off_own + (int)a128((size_t)R * q.rowbytes);
-        q.off_ex = q.off_aux + (int)a128((size_t)R * auxbytes);
-        q.off_rp = q.off_ex + (int)a16((size_t)gcap * ex_size(precision));
-        q.stage_bytes = (int)a128((size_t)q.off_rp + (size_t)(R + 3) * 4);
-        q.csr_col = (int)a16((size_t)(R + 1) * 4);
-        q.csr_val = q.csr_col + (int)a16((size_t)gcap * 4);
-        q.csr_bytes = (int)a16((size_t)q.csr_val + (size_t)gcap * raw_size(precision));
-        const size_t csr_total = (size_t)TMA_CSR_SLOTS * q.csr_bytes;
+    // producer warps: one warp cannot keep up with the consumers. A stage must belong to one
+    // producer (tiles s, s + nst, ... all from the same warp, issued in order), or a producer could
+    // wait on an empty-barrier phase two ahead of the current one, which parity cannot tell apart;
+    // so nprod divides nst (the layout's CSR rings are sized for the largest nprod tried).
+    const int np_cap = ctas_per_sm == 2 ? 2 : 4;
+    int nprod = np_cap;
+    // layout for R rows per tile; returns the stage count that fits
+    auto layout = [&](int Rt) {
+        int ecap = (((int)(avg * Rt * 1.25) + 8) + 3) & ~3;
+        if (ecap > 4096) ecap = 4096;
+        int fcap = (((int)(avgfar * Rt * 1.25) + 8) + 3) & ~3;
+        if (fcap > ecap) fcap = ecap;
+        q.R = Rt;
+        q.ecap = ecap;
+        q.fcap = fcap;
+        q.off_aux = (int)a128((size_t)(Rt + 2 * TMA_HALO) * q.rowbytes);
+        q.off_gat = q.off_aux + (int)a128((size_t)Rt * auxbytes);
+        q.off_rec = q.off_gat + (fcap / 4) * q.slot;
+        q.off_gcol = q.off_rec + (int)a16((size_t)ecap * q.recbytes);
+        q.off_rp = q.off_gcol + (int)a16((size_t)fcap * 4);
+        q.stage_bytes = (int)a128((size_t)q.off_rp + (size_t)(Rt + 3) * 4);
+        q.csr_col = (int)a16((size_t)(Rt + 1) * 4);
+        q.csr_val = q.csr_col + (int)a16((size_t)ecap * 4);
+        q.csr_bytes = (int)a16((size_t)q.csr_val + (size_t)ecap * raw_size(precision));
+        const size_t csr_total = (size_t)nprod * TMA_CSR_SLOTS * q.csr_bytes;
         const int nst = budget > csr_total ? (int)((budget - csr_total) / q.stage_bytes) : 0;
         q.nst = nst > TMA_MAX_STAGES ? TMA_MAX_STAGES : nst;
-        if (q.nst >= 3 || (q.nst == 2 && gcap <= 64)) break;
-        gcap = ((gcap * 3 / 4) + 3) & ~3;
-        if (gcap < 16) break;
+        return q.nst;
+    };
+    // the most rows per tile that keep three stages (two at the least) in shared memory
+    int Rbest = 0;
+    for (int Rt = R; Rt >= 1; Rt = Rt > 4 ? Rt * 3 / 4 : Rt - 1) {
+        const int nst = layout(Rt);
+        if (nst >= 3) { Rbest = Rt; break; }
+        if (nst >= 2 && Rbest == 0) Rbest = Rt;
     }
+    if (Rbest == 0) return false;
+    R = Rbest;
+    layout(R);
     if (q.nst < 2) return false;
+    {
+        int best_np = 1, best_nst = q.nst;
+        bool have = false;
+        for (int np = np_cap; np >= 2; --np) {
+            const int adj = q.nst - q.nst % np;
+            if (adj >= 2 && (!have || adj > best_nst)) {
+                best_np = np;
+                best_nst = adj;
+                have = true;
+            }
+        }
+        nprod = best_np;
+        q.nst = best_nst;
+    }
+    q.nprod = nprod;
     q.csr_base = q.nst * q.stage_bytes;
-    L.smem = (size_t)q.csr_base + (size_t)TMA_CSR_SLOTS * q.csr_bytes;
-    L.threads = ((R * tp + 31) / 32) * 32;
+    L.smem = (size_t)q.csr_base + (size_t)nprod * TMA_CSR_SLOTS * q.csr_bytes;
+    L.threads = ((R * tp + 31) / 32) * 32 + 32 * nprod;   // consumer warps and the producer warps
     if (L.smem < (size_t)L.threads * 2 * sizeof(double)) L.smem = (size_t)L.threads * 2 * sizeof(double);
     L.smem += 128;
     p.tp = tp;
@@ -410,16 +551,16 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int b, int threa
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s) {
     if (p.num_tiles <= 0) return cudaSuccess;
     const int ew = (int)elem_size(w_type_of(precision));
-    CUtensorMap g{}, o{}, a{};
-    if (!encode_rows(&g, p.win, ew, p.ldw, p.n, 1) || !encode_rows(&o, p.win, ew, p.ldw, p.n, L.q.rbox))
+    CUtensorMap g{}, w{}, a{};
+    if (!encode_rows(&g, p.win, ew, p.ldw, p.n, 1) || !encode_rows(&w, p.win, ew, p.ldw, p.n, L.q.R + 2 * TMA_HALO))
         return cudaErrorInvalidValue;
     bool aux_ok = true;
-    if (mode == MODE_DOT || mode == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, p.n, L.q.rbox);
-    else if (mode == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, p.n, L.q.rbox);
-    else a = o;
+    if (mode == MODE_DOT || mode == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, p.n, L.q.R);
+    else if (mode == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, p.n, L.q.R);
+    else a = w;
     if (!aux_ok) return cudaErrorInvalidValue;
     switch (precision * NUM_MODES + mode) {
-#define LCH(P_, M_) case P_ * NUM_MODES + M_: return launch_tma_typed<P_, M_>(L, g, o, a, p, s);
+#define LCH(P_, M_) case P_ * NUM_MODES + M_: return launch_tma_typed<P_, M_>(L, g, w, a, p, s);
 #define LCH4(P_) LCH(P_, MODE_PLAIN) LCH(P_, MODE_ACCUM) LCH(P_, MODE_DOT) LCH(P_, MODE_ADJ)
         LCH4(LL_PREC_F64) LCH4(LL_PREC_DF64) LCH4(LL_PREC_F32_MIXED)
 #undef LCH4
