@@ -198,7 +198,10 @@ cudaError_t exec_step(ll_handle* h, int precision, int mode, const StepExec& E, 
 }
 
 // Workspace of a step launch: DOT partials for the plan's grid, and the TMA error flag.
-ll_status bind_exec(ll_handle* h, int mode, int b, StepExec& E, StepParams& p) {
+// Workspace of a step launch: DOT partials for the plan's grid; for the TMA kernel the error flag
+// and the pass's tile descriptors (one set per mode, built here from the CSR and the prepared
+// values in p, on the stream, before the pass's steps).
+ll_status bind_exec(ll_handle* h, int precision, int mode, int b, StepExec& E, StepParams& p, cudaStream_t s) {
     if (mode == MODE_DOT) {
         WS(partials, double*, "dot_partials", (size_t)2 * E.grid() * b * sizeof(double));
         p.partials = partials;
@@ -206,6 +209,20 @@ ll_status bind_exec(ll_handle* h, int mode, int b, StepExec& E, StepParams& p) {
     if (E.kind == LL_KERNEL_TMA) {
         WS(err, int*, "tma_error", sizeof(int));
         E.tl.q.error = err;
+        static const char* dn[NUM_MODES] = {"tma_desc_plain", "tma_desc_accum", "tma_desc_dot", "tma_desc_adj"};
+        static const char* gn[NUM_MODES] = {"tma_gcol_plain", "tma_gcol_accum", "tma_gcol_dot", "tma_gcol_adj"};
+        static const char* mn[NUM_MODES] = {"tma_meta_plain", "tma_meta_accum", "tma_meta_dot", "tma_meta_adj"};
+        WS(desc, unsigned char*, dn[mode], E.tl.desc_bytes);
+        WS(gcol, int*, gn[mode], E.tl.gcol_bytes);
+        WS(meta, int2*, mn[mode], E.tl.meta_bytes);
+        E.tl.q.desc = desc;
+        E.tl.q.gcol = gcol;
+        E.tl.q.meta = meta;
+        E.tl.q.desc_w = desc;
+        E.tl.q.gcol_w = gcol;
+        E.tl.q.meta_w = meta;
+        LL_CK(launch_tma_describe(precision, E.tl, p, s));
+        h->launches++;
     }
     return LL_OK;
 }
@@ -235,7 +252,7 @@ ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz,
         StepParams q = p;
         if (plan_exec(h, LL_KERNEL_TMA, precision, mode, n, nnz, b, threads, 0, q, E)) {
             p = q;
-            return bind_exec(h, mode, b, E, p);
+            return bind_exec(h, precision, mode, b, E, p, s);
         }
         kernel = LL_KERNEL_GATHER;
         threads = 0;
@@ -243,14 +260,14 @@ ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz,
     }
     if (kernel == LL_KERNEL_GATHER) {
         plan_exec(h, LL_KERNEL_GATHER, precision, mode, n, nnz, b, threads, rpt, p, E);
-        return bind_exec(h, mode, b, E, p);
+        return bind_exec(h, precision, mode, b, E, p, s);
     }
     const auto key = std::make_tuple(precision, mode, n, nnz, b, p.ldw);
     auto it = h->tuned.find(key);
     if (it != h->tuned.end()) {
         const int kind = std::get<0>(it->second);
         plan_exec(h, kind, precision, mode, n, nnz, b, std::get<1>(it->second), std::get<2>(it->second), p, E);
-        return bind_exec(h, mode, b, E, p);
+        return bind_exec(h, precision, mode, b, E, p, s);
     }
     struct Cand { int kind, threads, rpt; };
     const Cand cands[] = {{LL_KERNEL_TMA, 512, 0}, {LL_KERNEL_TMA, 256, 0}, {LL_KERNEL_GATHER, 0, 8},
@@ -262,7 +279,7 @@ ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz,
         StepParams q = p;
         StepExec C;
         if (!plan_exec(h, c.kind, precision, mode, n, nnz, b, c.threads, c.rpt, q, C)) continue;
-        if ((st = bind_exec(h, mode, b, C, q)) != LL_OK) return st;
+        if ((st = bind_exec(h, precision, mode, b, C, q, s)) != LL_OK) return st;
         LL_CK(exec_step(h, precision, mode, C, q, s));
         LL_CK(cudaEventRecord(h->ev[6], s));
         LL_CK(exec_step(h, precision, mode, C, q, s));
@@ -280,7 +297,7 @@ ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz,
     }
     h->tuned[key] = std::make_tuple(best.kind, best.threads, best.rpt);
     plan_exec(h, best.kind, precision, mode, n, nnz, b, best.threads, best.rpt, p, E);
-    return bind_exec(h, mode, b, E, p);
+    return bind_exec(h, precision, mode, b, E, p, s);
 }
 
 // Runs m Léja steps over an n x b block.

@@ -187,17 +187,26 @@ struct BatchParams {
 // ---- TMA-fed step (k_leja_tma): geometry of the shared-memory pipeline -------------------------
 struct TmaParams {
     int R;             // rows per tile (one row lane each)
-    int ecap;          // entries per tile with a record in shared memory; later entries load directly
-    int fcap;          // far entries per tile gathered by TMA (multiple of 4); later far entries load directly
+    int ecap;          // entries per tile with a record; later entries load directly
+    int fcap;          // far entries per tile gathered by TMA (multiple of 4)
     int nst;           // pipeline stages (tiles in flight + 1)
-    int nprod;         // producer warps
+    int nprod;         // producer warps (divides nst)
     int slot;          // bytes of one gather4 slot (4 rows, 128-byte aligned)
     int rowbytes;      // bytes of one W row (ld * element size)
     int auxbytes;      // bytes of one V (pass 2, adjoint) or P (pass 1) row; 0 without
-    int recbytes;      // bytes of one entry record (expanded value, operand offset, column)
-    int stage_bytes;   // bytes per stage: window, aux rows, gathered rows, records, gather columns, row offsets
-    int off_aux, off_gat, off_rec, off_gcol, off_rp;   // the window is at offset 0
-    int csr_bytes, csr_col, csr_val, csr_base;   // CSR ring after the stages
+    int recbytes;      // bytes of one entry record (prepared value, operand offset)
+    int hdr_bytes;     // descriptor header: R + 1 row offsets, z0, record count (16-byte padded)
+    int desc_stride;   // bytes per tile of the descriptor array (header and ecap records)
+    int gcol_stride;   // bytes per tile of the gather-column array (fcap ints)
+    int stage_bytes;   // bytes per stage: window, aux rows, gathered rows, descriptor
+    int off_aux, off_gat, off_desc;   // the window is at offset 0
+    int ring_base;     // gather-column rings of the producer warps, after the stages
+    const unsigned char* desc;   // per-tile descriptors (built once per pass)
+    const int* gcol;             // per-tile gather columns
+    const int2* meta;            // per tile: (records, gathered rows)
+    unsigned char* desc_w;       // the same arrays, writable (for the describe kernel)
+    int* gcol_w;
+    int2* meta_w;
     int* error;                                  // set to 1 when a bounded wait runs out
     long long spin_budget;                       // clock64 cycles a wait may spin
     int inject;                                  // test hook: tile 0 expects bytes no copy delivers
@@ -206,6 +215,7 @@ struct TmaLaunch {
     TmaParams q;
     int threads, grid;
     size_t smem;
+    size_t desc_bytes, gcol_bytes, meta_bytes;   // global descriptor arrays of the pass
 };
 // Shape of a TMA-fed step launch; false when the block layout does not allow TMA (a row wider than
 // 256 elements or not a multiple of 16 bytes) or the pipeline does not fit in shared memory.
@@ -214,6 +224,9 @@ struct TmaLaunch {
 bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int b, int threads_target,
                    int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count);
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s);
+// builds the tile descriptors of a plan (L.q.desc_w, gcol_w, meta_w) from the CSR and the prepared
+// values in p; once per pass, before its steps
+cudaError_t launch_tma_describe(int precision, const TmaLaunch& L, const StepParams& p, cudaStream_t s);
 
 void plan_batched(int b, double avg_nnz_per_row, BatchParams& bp, size_t* smem);
 cudaError_t launch_batched(int precision, int mode, const BatchParams& bp, int grid, size_t smem, cudaStream_t s);

@@ -29,8 +29,9 @@
 namespace ll {
 
 constexpr int TMA_MAX_STAGES = 6;
-constexpr int TMA_MAX_THREADS = 640;   // up to 512 consumer threads and four producer warps
-constexpr int TMA_CSR_SLOTS = 5;   // CSR segments staged up to four tiles ahead
+constexpr int TMA_MAX_THREADS = 576;   // up to 512 consumer threads and two producer warps
+constexpr int TMA_MAX_PROD = 2;
+constexpr int TMA_GRING = 3;           // gather-column blocks staged up to two tiles ahead
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -84,20 +85,86 @@ __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map
         "l"(map), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
         : "memory");
 }
-__device__ __forceinline__ void cp_async4_(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+// 1-D bulk copy global -> shared (both 16-byte aligned, size a multiple of 16) completing on bar
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
-__device__ __forceinline__ void cp_async8_(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
-// Entry record written by the producer for every staged entry of a tile: the matrix value expanded
-// for the f32x2 instructions, the byte offset of its operand row W_j[c, :] in the stage (window or
-// gather slot; -1 when the row is read from global memory) and the column c.
+// Entry record of a tile's descriptor: the matrix value as prepared (FP64, float pair, FP32) and
+// the byte offset of its operand row W_j[c, :] in the stage (window or gather slot). One
+// broadcast shared-memory load per entry in the consumer loop.
 template <int PREC> struct Rec;
-template <> struct Rec<LL_PREC_F64> { double a; int off, col; };
-template <> struct Rec<LL_PREC_DF64> { ExDF a; int off, col; };
-template <> struct Rec<LL_PREC_F32_MIXED> { f2x a; int off, col; };
+template <> struct __align__(16) Rec<LL_PREC_F64> { double a; int off, pad; };
+template <> struct __align__(16) Rec<LL_PREC_DF64> { float2 a; int off, pad; };   // (hi, lo)
+template <> struct __align__(8) Rec<LL_PREC_F32_MIXED> { float a; int off; };
+
+// Tile descriptors, built once per pass (the matrix and the tile geometry do not change between
+// the m steps). One warp per tile of R rows:
+//   desc[t]: row offsets rowptr[r0 .. r0 + nr] - z0, then z0 and the record count g, padded to
+//            16 bytes; then one record per entry e < g. Columns inside the window
+//            [r0 - HALO, r0 + R + HALO) point into the window, the others into the next gather
+//            slot in entry order; when the fcap slots run out (or after ecap entries) the records
+//            stop, and that entry and every later entry of the tile load directly;
+//   gcol[t]: the gathered columns in slot order, padded with the last one to a multiple of 4;
+//   meta[t]: (g, gathered rows).
+template <int PREC>
+__global__ void k_tma_describe(const int32_t* rowptr, const int32_t* colind, const typename PairT<PREC>::Raw* vals, int n,
+                               int num_tiles, const TmaParams q, unsigned char* desc, int* gcol, int2* meta) {
+    using RecT = Rec<PREC>;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int R = q.R;
+    for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < num_tiles; t += (int)((gridDim.x * blockDim.x) >> 5)) {
+        const int r0 = t * R;
+        const int nr = min(R, n - r0);
+        const int z0 = rowptr[r0];
+        const int g = min(rowptr[r0 + nr] - z0, q.ecap);
+        int* hdr = reinterpret_cast<int*>(desc + (size_t)t * q.desc_stride);
+        RecT* rec = reinterpret_cast<RecT*>(desc + (size_t)t * q.desc_stride + q.hdr_bytes);
+        int* gc = gcol + (size_t)t * q.fcap;
+        for (int e = lane; e <= nr; e += 32) hdr[e] = rowptr[r0 + e] - z0;
+        const int wlo = r0 - TMA_HALO, whi = r0 + R + TMA_HALO;
+        int nfar = 0, gcut = g;
+        for (int e0 = 0; e0 < gcut; e0 += 32) {
+            const int e = e0 + lane;
+            const bool valid = e < gcut;
+            const int c = valid ? colind[z0 + e] : 0;
+            const bool near = c >= wlo && c < whi;
+            const unsigned farm = __ballot_sync(0xffffffffu, valid && !near);
+            const int fs = nfar + __popc(farm & lt_mask);
+            const unsigned over = __ballot_sync(0xffffffffu, valid && !near && fs >= q.fcap);
+            if (over) gcut = e0 + __ffs(over) - 1;   // first entry without a gather slot
+            if (valid && e < gcut) {
+                RecT rr;
+                rr.a = vals[z0 + e];
+                if (near) {
+                    rr.off = (c - wlo) * q.rowbytes;
+                } else {
+                    rr.off = q.off_gat + (fs >> 2) * q.slot + (fs & 3) * q.rowbytes;
+                    gc[fs] = c;
+                }
+                rec[e] = rr;
+            }
+            nfar += __popc(farm);
+        }
+        const int ng = min(nfar, q.fcap);
+        __syncwarp();
+        if (ng > 0) {
+            const int last = gc[ng - 1];
+            for (int e = ng + lane; e < ((ng + 3) & ~3); e += 32) gc[e] = last;
+        }
+        if (lane == 0) {
+            hdr[R + 1] = z0;
+            hdr[R + 2] = gcut;
+            meta[t] = make_int2(gcut, ng);
+        }
+    }
+}
 
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
@@ -110,6 +177,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full[TMA_MAX_STAGES];
     __shared__ __align__(8) unsigned long long empty[TMA_MAX_STAGES];
+    __shared__ __align__(8) unsigned long long gbar[TMA_MAX_PROD * TMA_GRING];
+    __shared__ int2 gmeta[TMA_MAX_PROD * TMA_GRING];
     __shared__ bool s_last;
     // TMA destinations are 128-byte aligned: the plan reserves 128 bytes for this offset
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -118,7 +187,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     const int tp = p.tp;
     const int R = q.R;
     const int NST = q.nst;
-    const int nprod = q.nprod;                        // producer warps (the last warps of the CTA)
+    const int nprod = q.nprod;                           // producer warps (the last warps of the CTA)
     const int cthreads = (int)blockDim.x - 32 * nprod;   // consumer threads
     const int cwarps = cthreads >> 5;
     const int n = p.n;
@@ -129,6 +198,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
             mbar_init(smem_u32(&full[s]), 1);         // the issuing producer's lane 0 (with the byte count)
             mbar_init(smem_u32(&empty[s]), cwarps);   // one arrival per consumer warp
         }
+        for (int s = 0; s < nprod * TMA_GRING; ++s) mbar_init(smem_u32(&gbar[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -141,163 +211,103 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
 
     if (tid >= cthreads) {
         // ------------------------------------------------------------------ producer warps
-        // warp w of the nprod producers issues tiles w, w + nprod, ... from its own CSR ring
+        // warp w of the nprod producers issues tiles w, w + nprod, ... (nprod <= nst: see the plan)
         const int pw = (tid - cthreads) >> 5;
         const int lane = (tid - cthreads) & 31;
-        const Raw* __restrict__ vals = static_cast<const Raw*>(p.vals);
-        const int* __restrict__ rowptr = p.rowptr;
-        const int* __restrict__ colind = p.colind;
-        unsigned char* csr = smem + q.csr_base + pw * TMA_CSR_SLOTS * q.csr_bytes;
-        constexpr int LOOK = TMA_CSR_SLOTS - 1;   // CSR segments staged ahead of the issue
-        // nnz ranges of the CTA's tiles, 32 tiles per batch (lane l holds tile zb + l), the next
-        // batch loaded one batch ahead
         const int myp = my > pw ? (my - 1 - pw) / nprod + 1 : 0;   // tiles of this producer
-        auto tile_range = [&](int t, int& lo, int& hi) {   // t: this producer's tile count
-            lo = hi = 0;
-            if (t < myp) {
-                const int rr = ((int)blockIdx.x + (pw + t * nprod) * (int)gridDim.x) * R;
-                lo = rowptr[rr];
-                hi = rowptr[min(rr + R, n)];
+        auto tile_of = [&](int t) { return (int)blockIdx.x + (pw + t * nprod) * (int)gridDim.x; };
+        unsigned char* ring = smem + q.ring_base + pw * TMA_GRING * q.gcol_stride;
+        unsigned long long* gb = gbar + pw * TMA_GRING;
+        int2* gm = gmeta + pw * TMA_GRING;
+        // per-tile (records, gathered rows) of this producer's tiles, 32 per batch (lane l holds
+        // tile zb + l), the next batch loaded one batch ahead
+        auto meta_of = [&](int t) { return t < myp ? q.meta[tile_of(t)] : make_int2(0, 0); };
+        int zb = 0;
+        int2 mcur = meta_of(lane), mnext = meta_of(32 + lane);
+        int cslot = 0;   // ring slot of the next gather-column block to stage
+        // stage the gather columns of this producer's tile t (t increasing by one per call)
+        auto stage_gcol = [&](int t) {
+            if (t >= zb + 32) {
+                zb += 32;
+                mcur = mnext;
+                mnext = meta_of(zb + 32 + lane);
             }
-        };
-        int zb = 0, zlo, zhi, nlo, nhi;
-        tile_range(lane, zlo, zhi);
-        tile_range(32 + lane, nlo, nhi);
-        int sslot = 0;   // CSR slot of the next tile to stage
-        // stage the CSR segment (row pointers, the first ecap indices and values) of tile js
-        auto stage_next = [&](int js) {
-            if (js < myp) {
-                if (js >= zb + 32) {
-                    zb += 32;
-                    zlo = nlo;
-                    zhi = nhi;
-                    tile_range(zb + 32 + lane, nlo, nhi);
+            const int nrec = __shfl_sync(0xffffffffu, mcur.x, t - zb);
+            const int ng = __shfl_sync(0xffffffffu, mcur.y, t - zb);
+            if (lane == 0) {
+                gm[cslot] = make_int2(nrec, ng);
+                const uint32_t bar = smem_u32(&gb[cslot]);
+                const uint32_t bytes = (uint32_t)((ng + 3) & ~3) * 4u;
+                if (bytes) {
+                    mbar_arrive_expect_tx(bar, bytes);
+                    bulk_copy(smem_u32(ring + cslot * q.gcol_stride), q.gcol + (size_t)tile_of(t) * q.fcap, bytes, bar);
+                } else {
+                    mbar_arrive(bar);
                 }
-                const int zs0 = __shfl_sync(0xffffffffu, zlo, js - zb);
-                const int zs1 = __shfl_sync(0xffffffffu, zhi, js - zb);
-                const int zrow = ((int)blockIdx.x + (pw + js * nprod) * (int)gridDim.x) * R;
-                unsigned char* slot = csr + sslot * q.csr_bytes;
-                int* drp = reinterpret_cast<int*>(slot);
-                int* dcol = reinterpret_cast<int*>(slot + q.csr_col);
-                Raw* dval = reinterpret_cast<Raw*>(slot + q.csr_val);
-                const int nr = min(R, n - zrow);
-                const int g = min(zs1 - zs0, q.ecap);
-                for (int e = lane; e <= nr; e += 32) cp_async4_(drp + e, rowptr + zrow + e);
-                for (int e = lane; e < g; e += 32) {
-                    cp_async4_(dcol + e, colind + zs0 + e);
-                    if constexpr (sizeof(Raw) == 8) cp_async8_(dval + e, vals + zs0 + e);
-                    else cp_async4_(dval + e, vals + zs0 + e);
-                }
-                if (++sslot == TMA_CSR_SLOTS) sslot = 0;
             }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            if (++cslot == TMA_GRING) cslot = 0;
         };
-        for (int js = 0; js < LOOK; ++js) stage_next(js);
-        const unsigned lt_mask = (1u << lane) - 1u;
-        int islot = 0;          // CSR slot of the tile being issued
+        constexpr int LOOK = TMA_GRING - 1;
+        for (int t = 0; t < LOOK && t < myp; ++t) stage_gcol(t);
+        int gslot = 0, gph = 0;   // ring slot and phase of the tile being issued
         int issued = 0;
         for (int ii = 0; ii < myp; ++ii) {
             const int i = pw + ii * nprod;   // the CTA's tile index
             const int s = i % NST, ph = (i / NST) & 1;
-            const int r0 = ((int)blockIdx.x + i * (int)gridDim.x) * R;
-            stage_next(ii + LOOK);
-            asm volatile("cp.async.wait_group %0;\n" ::"n"(LOOK) : "memory");   // tile i's segment is here
-            __syncwarp();
-            // the stage is free once every consumer warp released its previous tile
-            if (i >= NST) {
-                bool ok = true;
-                if (lane == 0) ok = mbar_wait_bounded(smem_u32(&empty[s]), (uint32_t)(ph ^ 1), q.spin_budget);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (!ok) {
-                    dead = true;
-                    if (lane == 0) *((volatile int*)q.error) = 1;
-                    break;
-                }
+            const int tile = tile_of(ii);
+            const int r0 = tile * R;
+            if (ii + LOOK < myp) stage_gcol(ii + LOOK);
+            // this tile's gather columns, and a free stage (every consumer warp released the
+            // stage's previous tile)
+            bool ok = mbar_wait_bounded(smem_u32(&gb[gslot]), (uint32_t)gph, q.spin_budget);
+            if (ok && i >= NST && lane == 0) ok = mbar_wait_bounded(smem_u32(&empty[s]), (uint32_t)(ph ^ 1), q.spin_budget);
+            if (!__all_sync(0xffffffffu, ok)) {
+                dead = true;
+                if (lane == 0) *((volatile int*)q.error) = 1;
+                break;
             }
+            const int2 mt = gm[gslot];
+            const int ngr = (mt.y + 3) >> 2;
             unsigned char* st = smem + s * q.stage_bytes;
-            const unsigned char* slot = csr + islot * q.csr_bytes;
-            const int* crp = reinterpret_cast<const int*>(slot);
-            const int* ccol = reinterpret_cast<const int*>(slot + q.csr_col);
-            const Raw* cval = reinterpret_cast<const Raw*>(slot + q.csr_val);
-            const int nr = min(R, n - r0);
-            const int z0 = crp[0];
-            const int g = min(crp[nr] - z0, q.ecap);
-            // entry records: columns inside the window [r0 - HALO, r0 + R + HALO) read the window,
-            // the others get the next gather slot (in entry order) while slots last
-            RecT* rec = reinterpret_cast<RecT*>(st + q.off_rec);
-            int* gcol = reinterpret_cast<int*>(st + q.off_gcol);
-            const int wlo = r0 - TMA_HALO, whi = r0 + R + TMA_HALO;
-            int nfar = 0;
-            for (int e0 = 0; e0 < g; e0 += 32) {
-                const int e = e0 + lane;
-                const bool valid = e < g;
-                const int c = valid ? ccol[e] : 0;
-                const bool near = c >= wlo && c < whi;
-                const unsigned farm = __ballot_sync(0xffffffffu, valid && !near);
-                if (valid) {
-                    int off;
-                    if (near) {
-                        off = (c - wlo) * q.rowbytes;
-                    } else {
-                        const int fs = nfar + __popc(farm & lt_mask);
-                        if (fs < q.fcap) {
-                            off = q.off_gat + (fs >> 2) * q.slot + (fs & 3) * q.rowbytes;
-                            gcol[fs] = c;
-                        } else {
-                            off = -1;
-                        }
-                    }
-                    RecT rr;
-                    rr.a = expand(cval[e]);
-                    rr.off = off;
-                    rr.col = c;
-                    rec[e] = rr;
-                }
-                nfar += __popc(farm);
-            }
-            const int ng = min(nfar, q.fcap);
-            const int ngr = (ng + 3) >> 2;
-            int* srp = reinterpret_cast<int*>(st + q.off_rp);
-            for (int e = lane; e <= nr; e += 32) srp[e] = crp[e] - z0;
-            if (lane == 0) {
-                srp[R + 1] = z0;
-                srp[R + 2] = g;
-            }
-            __syncwarp();   // gather columns and records written (published by lane 0's release-arrive)
             const uint32_t bar = smem_u32(&full[s]);
             if (lane == 0) {
                 // (the test hook adds 16 bytes to tile 0 that no copy delivers: its waits run out)
-                const uint32_t bytes = (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
+                const uint32_t dbytes = (uint32_t)q.hdr_bytes + (uint32_t)mt.x * (uint32_t)q.recbytes;
+                const uint32_t dbytes16 = (dbytes + 15u) & ~15u;
+                const uint32_t bytes = dbytes16 + (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
                                        (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
                                        (has_aux ? (uint32_t)R * (uint32_t)q.auxbytes : 0u) +
                                        ((q.inject && i == 0) ? 16u : 0u);
                 mbar_arrive_expect_tx(bar, bytes);
+                bulk_copy(smem_u32(st + q.off_desc), q.desc + (size_t)tile * q.desc_stride, dbytes16, bar);
                 // the window may start above row 0 or end below row n: those rows are zero-filled
-                tma_load_rows(smem_u32(st), &tm_win, wlo, bar);
+                tma_load_rows(smem_u32(st), &tm_win, r0 - TMA_HALO, bar);
                 if (has_aux) tma_load_rows(smem_u32(st + q.off_aux), &tm_aux, r0, bar);
             }
-            __syncwarp();
+            const int* gcs = reinterpret_cast<const int*>(ring + gslot * q.gcol_stride);
             for (int gi = lane; gi < ngr; gi += 32) {
-                const int e = 4 * gi;
-                tma_gather4(smem_u32(st + q.off_gat + gi * q.slot), &tm_gather, gcol[e], gcol[min(e + 1, ng - 1)],
-                            gcol[min(e + 2, ng - 1)], gcol[min(e + 3, ng - 1)], bar);
+                const int4 c4 = *reinterpret_cast<const int4*>(gcs + 4 * gi);
+                tma_gather4(smem_u32(st + q.off_gat + gi * q.slot), &tm_gather, c4.x, c4.y, c4.z, c4.w, bar);
             }
-            __syncwarp();
+            __syncwarp();   // the ring slot is read before the next copy into it
             ++issued;
-            if (++islot == TMA_CSR_SLOTS) islot = 0;
+            if (++gslot == TMA_GRING) {
+                gslot = 0;
+                gph ^= 1;
+            }
         }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        // after a timeout, wait (bounded) for the copies of the last tiles issued (earlier uses of
-        // its stages were released by the consumers, so their copies completed), so that none lands
-        // in shared memory after the CTA exits
+        // after a timeout, wait (bounded) for the copies this warp issued and the consumers did not
+        // release (all among its last nst tiles: tile i was issued after tile i - nst was
+        // released), and for the gather-column blocks staged ahead, so that none lands in shared
+        // memory after the CTA exits
         if (dead && lane == 0) {
             const long long drain = q.spin_budget > TMA_DRAIN_MIN ? q.spin_budget : TMA_DRAIN_MIN;
-            // this producer owns stages pw, pw + nprod, ...: its last nst / nprod tiles are the most
-            // recent use of each of them
-            for (int jj = max(0, issued - NST / nprod); jj < issued; ++jj) {
+            for (int jj = max(0, issued - NST); jj < issued; ++jj) {
                 const int j = pw + jj * nprod;
                 mbar_wait_bounded(smem_u32(&full[j % NST]), (uint32_t)((j / NST) & 1), drain);
             }
+            for (int t = issued; t < min(myp, issued + LOOK + 1); ++t)
+                mbar_wait_bounded(smem_u32(&gb[t % TMA_GRING]), (uint32_t)((t / TMA_GRING) & 1), drain);
         }
     } else {
         // ------------------------------------------------------------------ consumer warps
@@ -318,6 +328,9 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                                  (unsigned)(cp * (MODE == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
         int s = 0, ph = 0;
         int r = (int)blockIdx.x * R + rlane;
+        WP* wo = wout + (size_t)r * ldq + cp;   // this thread's W_{j+1} and P pairs, advanced per tile
+        PP* po_ptr = pblk + (size_t)r * ldpq + cp;
+        const size_t wstep = (size_t)rstep * ldq, pstep = (size_t)rstep * ldpq;
         for (int i = 0; i < my; ++i) {
             // every lane waits (acquiring the stage's copies); the warp gives up together
             const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)ph, q.spin_budget);
@@ -328,8 +341,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
             }
             const unsigned char* st = smem + s * q.stage_bytes;
             if (active && r < n) {
-                const int* srp = reinterpret_cast<const int*>(st + q.off_rp);
-                const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_rec);
+                const int* srp = reinterpret_cast<const int*>(st + q.off_desc);
+                const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_desc + q.hdr_bytes);
                 const int k0 = srp[rlane], k1 = srp[rlane + 1];
                 const int g = srp[R + 2];
                 const WP wr = *reinterpret_cast<const WP*>(st + own_off);
@@ -345,21 +358,22 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
 #pragma unroll 4
                 for (int k = k0; k < kend; ++k) {
                     const RecT rk = rec[k];
-                    const WP x = rk.off >= 0 ? *reinterpret_cast<const WP*>(stc + rk.off) : win[(size_t)rk.col * ldq + cp];
-                    row_mac<PREC>(A, rk.a, x);
+                    row_mac<PREC>(A, expand(rk.a), *reinterpret_cast<const WP*>(stc + rk.off));
                 }
-                if (k1 > g) {   // beyond the record capacity: direct loads
+                if (k1 > g) {   // beyond the records: direct loads
                     const int z0 = srp[R + 1];
                     for (int k = max(k0, g); k < k1; ++k) {
                         const WP x = win[(size_t)colind[z0 + k] * ldq + cp];
                         row_mac<PREC>(A, expand(vals[z0 + k]), x);
                     }
                 }
-                row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wout + (size_t)r * ldq + cp, pblk + (size_t)r * ldpq + cp, T);
+                row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wo, po_ptr, T);
             }
             __syncwarp();
-            if ((tid & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&empty[s])) : "memory");
+            if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[s]));
             r += rstep;
+            wo += wstep;
+            po_ptr += pstep;
             if (++s == NST) {
                 s = 0;
                 ph ^= 1;
@@ -407,7 +421,6 @@ bool encode_rows(CUtensorMap* m, const void* base, int elem, long long ld, int n
 size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
 
-size_t raw_size(int precision) { return precision == LL_PREC_F64 ? 8 : (precision == LL_PREC_DF64 ? 8 : 4); }
 size_t rec_size(int precision) {
     return precision == LL_PREC_F64 ? sizeof(Rec<LL_PREC_F64>) : (precision == LL_PREC_DF64 ? sizeof(Rec<LL_PREC_DF64>) : sizeof(Rec<LL_PREC_F32_MIXED>));
 }
@@ -465,12 +478,11 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     const double avg = (double)nnz / (double)n;
     const double avgfar = nfar >= 0 && nfar <= nnz ? (double)nfar / (double)n : avg;
     const size_t budget = (ctas_per_sm == 2 ? 112 : 224) * 1024 - 1024;
-    // producer warps: one warp cannot keep up with the consumers. A stage must belong to one
-    // producer (tiles s, s + nst, ... all from the same warp, issued in order), or a producer could
-    // wait on an empty-barrier phase two ahead of the current one, which parity cannot tell apart;
-    // so nprod divides nst (the layout's CSR rings are sized for the largest nprod tried).
-    const int np_cap = ctas_per_sm == 2 ? 2 : 4;
-    int nprod = np_cap;
+    // Producer warps: two keep up with the consumers now that the per-step work is copies only.
+    // A producer waits for the release of tile i - nst only after the release of its previous
+    // wait target i - nprod - nst, so with nprod <= nst the stage's empty barrier is never more
+    // than one phase behind and the parity wait is unambiguous.
+    const int np_cap = TMA_MAX_PROD;
     // layout for R rows per tile; returns the stage count that fits
     auto layout = [&](int Rt) {
         int ecap = (((int)(avg * Rt * 1.25) + 8) + 3) & ~3;
@@ -480,17 +492,15 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
         q.R = Rt;
         q.ecap = ecap;
         q.fcap = fcap;
+        q.hdr_bytes = (int)a16((size_t)(Rt + 3) * 4);
+        q.desc_stride = (int)a16((size_t)q.hdr_bytes + (size_t)ecap * q.recbytes);
+        q.gcol_stride = (int)a16((size_t)fcap * 4);
         q.off_aux = (int)a128((size_t)(Rt + 2 * TMA_HALO) * q.rowbytes);
         q.off_gat = q.off_aux + (int)a128((size_t)Rt * auxbytes);
-        q.off_rec = q.off_gat + (fcap / 4) * q.slot;
-        q.off_gcol = q.off_rec + (int)a16((size_t)ecap * q.recbytes);
-        q.off_rp = q.off_gcol + (int)a16((size_t)fcap * 4);
-        q.stage_bytes = (int)a128((size_t)q.off_rp + (size_t)(Rt + 3) * 4);
-        q.csr_col = (int)a16((size_t)(Rt + 1) * 4);
-        q.csr_val = q.csr_col + (int)a16((size_t)ecap * 4);
-        q.csr_bytes = (int)a16((size_t)q.csr_val + (size_t)ecap * raw_size(precision));
-        const size_t csr_total = (size_t)nprod * TMA_CSR_SLOTS * q.csr_bytes;
-        const int nst = budget > csr_total ? (int)((budget - csr_total) / q.stage_bytes) : 0;
+        q.off_desc = q.off_gat + (fcap / 4) * q.slot;
+        q.stage_bytes = (int)a128((size_t)q.off_desc + (size_t)q.desc_stride);
+        const size_t ring_total = (size_t)np_cap * TMA_GRING * q.gcol_stride;
+        const int nst = budget > ring_total ? (int)((budget - ring_total) / q.stage_bytes) : 0;
         q.nst = nst > TMA_MAX_STAGES ? TMA_MAX_STAGES : nst;
         return q.nst;
     };
@@ -505,23 +515,10 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     R = Rbest;
     layout(R);
     if (q.nst < 2) return false;
-    {
-        int best_np = 1, best_nst = q.nst;
-        bool have = false;
-        for (int np = np_cap; np >= 2; --np) {
-            const int adj = q.nst - q.nst % np;
-            if (adj >= 2 && (!have || adj > best_nst)) {
-                best_np = np;
-                best_nst = adj;
-                have = true;
-            }
-        }
-        nprod = best_np;
-        q.nst = best_nst;
-    }
+    const int nprod = np_cap < q.nst ? np_cap : q.nst;
     q.nprod = nprod;
-    q.csr_base = q.nst * q.stage_bytes;
-    L.smem = (size_t)q.csr_base + (size_t)nprod * TMA_CSR_SLOTS * q.csr_bytes;
+    q.ring_base = q.nst * q.stage_bytes;
+    L.smem = (size_t)q.ring_base + (size_t)nprod * TMA_GRING * q.gcol_stride;
     L.threads = ((R * tp + 31) / 32) * 32 + 32 * nprod;   // consumer warps and the producer warps
     if (L.smem < (size_t)L.threads * 2 * sizeof(double)) L.smem = (size_t)L.threads * 2 * sizeof(double);
     L.smem += 128;
@@ -531,6 +528,9 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     p.b = b;
     p.n = n;
     p.num_tiles = (n + R - 1) / R;
+    L.desc_bytes = (size_t)p.num_tiles * q.desc_stride;
+    L.gcol_bytes = (size_t)p.num_tiles * q.gcol_stride;
+    L.meta_bytes = (size_t)p.num_tiles * sizeof(int2);
     int per_sm = 0;
     switch (precision * NUM_MODES + mode) {
 #define OCC(P_, M_) case P_ * NUM_MODES + M_: per_sm = occupancy_tma<P_, M_>(L.threads, L.smem); break;
@@ -546,6 +546,28 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     if (grid > p.num_tiles) grid = p.num_tiles;
     L.grid = grid < 1 ? 1 : grid;
     return true;
+}
+
+cudaError_t launch_tma_describe(int precision, const TmaLaunch& L, const StepParams& p, cudaStream_t s) {
+    const int warps_per_cta = 8;
+    int grid = (p.num_tiles + warps_per_cta - 1) / warps_per_cta;
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) return cudaSuccess;
+    switch (precision) {
+        case LL_PREC_F64:
+            k_tma_describe<LL_PREC_F64><<<grid, 32 * warps_per_cta, 0, s>>>(p.rowptr, p.colind, static_cast<const double*>(p.vals),
+                                                                        p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w);
+            break;
+        case LL_PREC_DF64:
+            k_tma_describe<LL_PREC_DF64><<<grid, 32 * warps_per_cta, 0, s>>>(p.rowptr, p.colind, static_cast<const float2*>(p.vals),
+                                                                         p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w);
+            break;
+        default:
+            k_tma_describe<LL_PREC_F32_MIXED><<<grid, 32 * warps_per_cta, 0, s>>>(p.rowptr, p.colind, static_cast<const float*>(p.vals),
+                                                                              p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w);
+            break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s) {
