@@ -43,10 +43,11 @@ DTYPE_NAME = {"df64": "df64 (float-float on FP32 pipes, 8-byte storage)", "f64":
 ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A, s_W, s_P, s_V
 
 # DRAM bytes (read + write) of one pass-2 trace-step launch per matrix row, from one ncu capture of
-# the current kernel on the 96^3 Laplacian (launch 5 of the 96^3 bench run): 1.4777 GB over
-# 884,736 rows. Traffic grows in proportion to the rows of a stencil matrix, so the full-size value
-# is this figure times n. Only valid for the DF64 trace step as captured.
-TRACE_STEP_DRAM_BYTES_PER_ROW = {("gather", "df64"): 1.477654528e9 / 884736}
+# each kernel on the 96^3 Laplacian (n = 884,736): register gathers 1.4777 GB, TMA 1.5066 GB.
+# Traffic grows in proportion to the rows of a stencil matrix, so the full-size value is this figure
+# times n. Only valid for the DF64 trace step of the kernel as captured.
+TRACE_STEP_DRAM_BYTES_PER_ROW = {("gather", "df64"): 1.477654528e9 / 884736,
+                                 ("tma", "df64"): (1.064147e9 + 0.4424896e9) / 884736}
 
 
 def step_bytes(n: int, nnz: int, b: int, prec: str, mode: str) -> int:
@@ -331,6 +332,8 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID_N, help="side of the 3-D grid (128 = the benchmark workload; "
                     "smaller sides are for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
+                    help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
     ap.add_argument("--workloads", default="c1,c3,c4",
                     help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5; '' for none)")
     args = ap.parse_args()
@@ -362,7 +365,7 @@ def main():
 
     def time_precision(prec: str, steps: int, warmup: int, sampler=None):
         dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
-        opts = L.options(degree=m, probes=PROBES, seed=SEED + rank, precision=prec)
+        opts = L.options(degree=m, probes=PROBES, seed=SEED + rank, precision=prec, step_kernel=args.step_kernel)
         for _ in range(warmup):
             L.ll_logdet_forward(h, dA, *BOUNDS, opts)
         barrier()
@@ -408,7 +411,7 @@ def main():
             "achieved": achieved,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "traffic": per_row * n if per_row else None,
-            "traffic_source": "ncu dram__bytes_read+write of one launch at 96^3, scaled by rows" if per_row else None,
+            "traffic_source": f"ncu dram__bytes_read+write of one {kfun} launch at 96^3, scaled by rows" if per_row else None,
             "peak_source": peak_src,
             "per_launch_bytes": b_p2, "per_launch_ms": p2_launch_ms,
             "pass1_kernel": {"achieved": b_p1 / (p1_launch_ms / 1e3) / 1e9, "per_launch_bytes": b_p1,

@@ -41,132 +41,79 @@ cudaError_t launch_scale_cols(int precision, const void* V, long long ld, int n,
     return cudaGetLastError();
 }
 
-// Warp-wide sum of a double-float value (TwoSum at every level), result in lane 0.
-__device__ __forceinline__ void warp_df_sum(float& h, float& l) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float oh = __shfl_down_sync(0xffffffffu, h, off);
-        const float ol = __shfl_down_sync(0xffffffffu, l, off);
-        const float s = __fadd_rn(h, oh);
-        const float bb = __fsub_rn(s, h);
-        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
-        h = s;
-        l = __fadd_rn(l, __fadd_rn(ol, err));
-    }
-}
 
-// One warp per row r: each lane holds column pairs of Lambda_{j+1}[r, :]; for every stored entry
-// (r, c) the lanes multiply it with W_j[c, :] (coalesced pair loads), the warp sums, lane 0 adds
-// scale * sum to g[e]. Double-float products and sums for the F32 and DF64 storage, FP64 for F64.
+// g[e] += scale * <Lambda_{j+1}[r_e, :], W_j[c_e, :]> for every stored entry e = (r_e, c_e): one
+// thread per entry walks the column pairs of both rows (Lambda's row is shared by the entries of a
+// row, so it is an L1 hit for all but the first) and accumulates in double-float (FP64 for F64),
+// column pairs in order, the two lanes of a pair added at the end. Each g[e] is written by one
+// thread: no reduction across threads, deterministic.
 template <int PREC>
-__global__ void __launch_bounds__(256) k_sddmm(const int32_t* rowptr, const int32_t* colind, int n, const void* lam_,
+__global__ void __launch_bounds__(256) k_sddmm(const int32_t* rowidx, const int32_t* colind, int64_t nnz, const void* lam_,
                                                const void* w_, long long ld, int b, double scale, double* g) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const long long ldq = ld >> 1;
     const int npairs = (b + 1) / 2;
-    constexpr int MAXP = 4;   // pairs per lane (b <= 256)
-    for (int r = warp; r < n; r += nwarps) {
-        const int e0 = rowptr[r], e1 = rowptr[r + 1];
-        if (e0 == e1) continue;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const size_t rb = (size_t)rowidx[e] * ldq, cb = (size_t)colind[e] * ldq;
+        double acc;
         if constexpr (PREC == LL_PREC_F64) {
-            const double2* lam = static_cast<const double2*>(lam_);
-            const double2* w = static_cast<const double2*>(w_);
-            double2 lr[MAXP];
-#pragma unroll
-            for (int q = 0; q < MAXP; ++q) {
-                const int pq = lane + 32 * q;
-                lr[q] = pq < npairs ? lam[(size_t)r * ldq + pq] : make_double2(0.0, 0.0);
+            const double2* lam = static_cast<const double2*>(lam_) + rb;
+            const double2* w = static_cast<const double2*>(w_) + cb;
+            double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
+            for (int q = 0; q < npairs; ++q) {
+                const double2 l = __ldg(&lam[q]), x = __ldg(&w[q]);
+                a0 = fma(l.x, x.x, a0);
+                a1 = fma(l.y, x.y, a1);
             }
-            for (int e = e0; e < e1; ++e) {
-                const size_t cb = (size_t)colind[e] * ldq;
-                double acc = 0.0;
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) {
-                    const int pq = lane + 32 * q;
-                    if (pq < npairs) {
-                        const double2 x = w[cb + pq];
-                        acc = fma(lr[q].x, x.x, acc);
-                        acc = fma(lr[q].y, x.y, acc);
-                    }
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-                if (lane == 0) g[e] += scale * acc;
-            }
+            acc = a0 + a1;
         } else if constexpr (PREC == LL_PREC_DF64) {
-            const ulonglong2* lam = static_cast<const ulonglong2*>(lam_);
-            const ulonglong2* w = static_cast<const ulonglong2*>(w_);
-            ulonglong2 lr[MAXP];
-            f2x nlh[MAXP];
-#pragma unroll
-            for (int q = 0; q < MAXP; ++q) {
-                const int pq = lane + 32 * q;
-                lr[q] = pq < npairs ? lam[(size_t)r * ldq + pq] : make_ulonglong2(0ull, 0ull);
-                nlh[q] = f2_sub(0ull, lr[q].x);
+            const ulonglong2* lam = static_cast<const ulonglong2*>(lam_) + rb;
+            const ulonglong2* w = static_cast<const ulonglong2*>(w_) + cb;
+            f2x sh = 0ull, sl = 0ull;
+#pragma unroll 4
+            for (int q = 0; q < npairs; ++q) {
+                const ulonglong2 l = __ldg(&lam[q]), x = __ldg(&w[q]);
+                df2_mac_pp(sh, sl, l.x, l.y, f2_sub(0ull, l.x), x.x, x.y);
             }
-            for (int e = e0; e < e1; ++e) {
-                const size_t cb = (size_t)colind[e] * ldq;
-                f2x sh = 0ull, sl = 0ull;
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) {
-                    const int pq = lane + 32 * q;
-                    if (pq < npairs) {
-                        const ulonglong2 x = w[cb + pq];
-                        df2_mac_pp(sh, sl, lr[q].x, lr[q].y, nlh[q], x.x, x.y);
-                    }
-                }
-                float h0, h1, l0, l1;
-                f2_unpack(sh, h0, h1);
-                f2_unpack(sl, l0, l1);
-                float h = 0.f, l = 0.f;
-                df_mac(h, l, h0, l0, 1.f, 0.f);
-                df_mac(h, l, h1, l1, 1.f, 0.f);
-                warp_df_sum(h, l);
-                if (lane == 0) g[e] += scale * ((double)h + (double)l);
+            float h0, h1, l0, l1;
+            f2_unpack(sh, h0, h1);
+            f2_unpack(sl, l0, l1);
+            float h = 0.f, lo = 0.f;
+            df_mac(h, lo, h0, l0, 1.f, 0.f);
+            df_mac(h, lo, h1, l1, 1.f, 0.f);
+            acc = (double)h + (double)lo;
+        } else {  // LL_PREC_F32_MIXED: exact FP32 products accumulated in double-float
+            const f2x* lam = static_cast<const f2x*>(lam_) + rb;
+            const f2x* w = static_cast<const f2x*>(w_) + cb;
+            f2x sh = 0ull, sl = 0ull;
+#pragma unroll 4
+            for (int q = 0; q < npairs; ++q) {
+                const f2x l = __ldg(reinterpret_cast<const unsigned long long*>(&lam[q]));
+                const f2x x = __ldg(reinterpret_cast<const unsigned long long*>(&w[q]));
+                df2_mac_f(sh, sl, l, 0ull, f2_sub(0ull, l), x);
             }
-        } else {  // LL_PREC_F32_MIXED
-            const f2x* lam = static_cast<const f2x*>(lam_);
-            const f2x* w = static_cast<const f2x*>(w_);
-            f2x lr[MAXP], nlr[MAXP];
-#pragma unroll
-            for (int q = 0; q < MAXP; ++q) {
-                const int pq = lane + 32 * q;
-                lr[q] = pq < npairs ? lam[(size_t)r * ldq + pq] : 0ull;
-                nlr[q] = f2_sub(0ull, lr[q]);
-            }
-            for (int e = e0; e < e1; ++e) {
-                const size_t cb = (size_t)colind[e] * ldq;
-                f2x sh = 0ull, sl = 0ull;
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) {
-                    const int pq = lane + 32 * q;
-                    if (pq < npairs) df2_mac_f(sh, sl, lr[q], 0ull, nlr[q], w[cb + pq]);
-                }
-                float h0, h1, l0, l1;
-                f2_unpack(sh, h0, h1);
-                f2_unpack(sl, l0, l1);
-                float h = 0.f, l = 0.f;
-                df_mac(h, l, h0, l0, 1.f, 0.f);
-                df_mac(h, l, h1, l1, 1.f, 0.f);
-                warp_df_sum(h, l);
-                if (lane == 0) g[e] += scale * ((double)h + (double)l);
-            }
+            float h0, h1, l0, l1;
+            f2_unpack(sh, h0, h1);
+            f2_unpack(sl, l0, l1);
+            float h = 0.f, lo = 0.f;
+            df_mac(h, lo, h0, l0, 1.f, 0.f);
+            df_mac(h, lo, h1, l1, 1.f, 0.f);
+            acc = (double)h + (double)lo;
         }
+        g[e] += scale * acc;
     }
 }
 
-cudaError_t launch_sddmm(int precision, const int32_t* rowptr, const int32_t* colind, int n, const void* lam,
+cudaError_t launch_sddmm(int precision, const int32_t* rowidx, const int32_t* colind, int64_t nnz, const void* lam,
                          const void* w, long long ld, int b, double scale, double* g, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    if (b > 256) return cudaErrorInvalidValue;
+    if (nnz <= 0) return cudaSuccess;
     const int threads = 256;
-    const int grid = 152 * 8;
+    int64_t grid = (nnz + threads - 1) / threads;
+    if (grid > 152 * 16) grid = 152 * 16;
     switch (precision) {
-        case LL_PREC_F64: k_sddmm<LL_PREC_F64><<<grid, threads, 0, s>>>(rowptr, colind, n, lam, w, ld, b, scale, g); break;
-        case LL_PREC_DF64: k_sddmm<LL_PREC_DF64><<<grid, threads, 0, s>>>(rowptr, colind, n, lam, w, ld, b, scale, g); break;
-        default: k_sddmm<LL_PREC_F32_MIXED><<<grid, threads, 0, s>>>(rowptr, colind, n, lam, w, ld, b, scale, g); break;
+        case LL_PREC_F64: k_sddmm<LL_PREC_F64><<<(int)grid, threads, 0, s>>>(rowidx, colind, nnz, lam, w, ld, b, scale, g); break;
+        case LL_PREC_DF64: k_sddmm<LL_PREC_DF64><<<(int)grid, threads, 0, s>>>(rowidx, colind, nnz, lam, w, ld, b, scale, g); break;
+        default: k_sddmm<LL_PREC_F32_MIXED><<<(int)grid, threads, 0, s>>>(rowidx, colind, nnz, lam, w, ld, b, scale, g); break;
     }
     return cudaGetLastError();
 }

@@ -915,6 +915,10 @@ ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, 
     WS(tmp, char*, "bw_tmp", 2 * blk);
     LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
     h->launches++;
+    // row of every stored entry, for the gradient contraction
+    WS(rowidx, int32_t*, "bw_rowidx", (size_t)A->nnz * sizeof(int32_t));
+    LL_CK(launch_row_index(A->rowptr, n, rowidx, s));
+    h->launches++;
 
     StepParams pp{};
     pp.rowptr = A->rowptr;
@@ -981,7 +985,7 @@ ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, 
         for (int j = j1 - 1; j >= j0; --j) {
             const void* wj = (j == j0) ? wj0 : (const void*)(seg + (size_t)(j - j0 - 1) * blk);
             // g_e += (1 / (sigma gamma)) <Lambda_{j+1}[r, :], W_j[c, :]>
-            LL_CK(launch_sddmm(prec, A->rowptr, A->colind, n, lam_cur, wj, l2, b2, scale, grad_values, s));
+            LL_CK(launch_sddmm(prec, rowidx, A->colind, A->nnz, lam_cur, wj, l2, b2, scale, grad_values, s));
             h->launches++;
             if (j == 0) break;
             // Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U

@@ -82,8 +82,9 @@ cudaError_t launch_scale_cols(int precision, const void* V, long long ld, int n,
                               void* out, cudaStream_t s);
 // rowidx[e] = row of stored entry e
 cudaError_t launch_row_index(const int32_t* rowptr, int n, int32_t* rowidx, cudaStream_t s);
-// g[e] += scale * <Lam[r_e, :], W[c_e, :]> over b columns (W storage type of `precision`, ld even)
-cudaError_t launch_sddmm(int precision, const int32_t* rowptr, const int32_t* colind, int n, const void* lam,
+// g[e] += scale * <Lam[r_e, :], W[c_e, :]> over b columns for every stored entry (W storage type of
+// `precision`, ld even; rowidx[e] = r_e from launch_row_index)
+cudaError_t launch_sddmm(int precision, const int32_t* rowidx, const int32_t* colind, int64_t nnz, const void* lam,
                          const void* w, long long ld, int b, double scale, double* g, cudaStream_t s);
 // out[p] = sum_e g[e] * dv[p * ldd + e], p < np; partials: np * grid doubles; result in out (device)
 cudaError_t launch_param_dot(const double* g, const double* dv, long long ldd, int64_t nnz, int np, double* partials,
