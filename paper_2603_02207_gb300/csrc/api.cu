@@ -50,6 +50,7 @@ struct ll_handle {
         bool tma = false;
     } gfwd;
     int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
+    int max_row = 0;          // longest row of the last validated matrix
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
     int dd_degree = -1, dd_sval = -1, dd_terms = 0;
@@ -121,15 +122,16 @@ ll_status check_bounds(ll_handle* h, ll_bounds b) {
 // Validates the device CSR (synchronises the stream).
 ll_status validate_csr(ll_handle* h, const ll_csr* A, cudaStream_t s) {
     if (A->n == 0) return LL_OK;
-    WS(flag, int*, "csr_flag", 2 * sizeof(int));
-    LL_CK(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
-    LL_CK(launch_validate_csr(A->rowptr, A->colind, (int)A->n, A->nnz, flag, s));
+    WS(flag, int*, "csr_flag", 3 * sizeof(int));
+    LL_CK(cudaMemsetAsync(flag, 0, 3 * sizeof(int), s));
+    LL_CK(launch_validate_csr(A->rowptr, A->colind, (int)A->n, A->nnz, flag, s, flag + 2));
     h->launches++;
-    int hv[2] = {0, 0};
+    int hv[3] = {0, 0, 0};
     LL_CK(cudaMemcpyAsync(hv, flag, sizeof hv, cudaMemcpyDeviceToHost, s));
     LL_CK(cudaStreamSynchronize(s));
     const int hf = hv[0];
     h->far_entries = hv[1];
+    h->max_row = hv[2];
     if (hf) {
         char buf[160];
         snprintf(buf, sizeof buf, "invalid CSR:%s%s%s", (hf & 4) ? " rowptr[0]!=0 or rowptr[n]!=nnz;" : "",
@@ -179,7 +181,8 @@ bool plan_exec(ll_handle* h, int kind, int precision, int mode, int n, int64_t n
     E.rpt = rpt;
     if (kind == LL_KERNEL_TMA) {
         const int ctas = (threads > 0 && threads <= 256) ? 2 : 1;
-        if (!plan_step_tma(precision, mode, n, nnz, h->far_entries, b, threads, ctas, p, E.tl, h->sm_count)) return false;
+        if (!plan_step_tma(precision, mode, n, nnz, h->far_entries, h->max_row, b, threads, ctas, p, E.tl, h->sm_count))
+            return false;
         E.tl.q.spin_budget = h->spin_budget;
         E.tl.q.inject = h->inject;
         return true;

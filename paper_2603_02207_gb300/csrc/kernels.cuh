@@ -61,8 +61,9 @@ cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, 
 constexpr int TMA_HALO = 2;
 // flag[0]: error bits (1 rowptr decreasing, 2 column out of range, 4 rowptr[0] != 0 or rowptr[n] != nnz);
 // flag[1]: stored entries with |col - row| > TMA_HALO (int32; saturates nowhere below 2^31)
+// rowmax (optional): atomicMax of the longest row's entry count
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz,
-                                int* flag, cudaStream_t s);
+                                int* flag, cudaStream_t s, int* rowmax = nullptr);
 cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype,
                               int n, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
 // out[e] = convert(values[e] * scale) into the storage type of `precision`
@@ -221,8 +222,9 @@ struct TmaLaunch {
 // Shape of a TMA-fed step launch; false when the block layout does not allow TMA (a row wider than
 // 256 elements or not a multiple of 16 bytes) or the pipeline does not fit in shared memory.
 // ctas_per_sm: 1 (one 512-thread CTA with ~223 KB of stages) or 2 (two of half the size).
-// nfar: entries with |col - row| > TMA_HALO (sizes the gather slots; a hint, not a bound)
-bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int b, int threads_target,
+// nfar: entries with |col - row| > TMA_HALO; maxrow: the longest row (both size the per-tile record
+// and gather capacities; hints, not bounds)
+bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int maxrow, int b, int threads_target,
                    int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count);
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s);
 // builds the tile descriptors of a plan (L.q.desc_w, gcol_w, meta_w) from the CSR and the prepared

@@ -36,14 +36,15 @@ cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, 
 // ----------------------------------------------------------------------------- CSR validation
 // flag[0] bits: 1 = rowptr decreasing, 2 = column index out of range, 4 = rowptr[0] != 0 or
 // rowptr[n] != nnz. flag[1]: largest forward offset col - row (rows with a valid range only).
-__global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag) {
+__global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, int* rowmax) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (tid == 0 && (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) atomicOr(flag, 4);
-    int far = 0;
+    int far = 0, longest = 0;
     for (int i = tid; i < n; i += stride) {
         const int a = rowptr[i], e = rowptr[i + 1];
         if (e < a) { atomicOr(flag, 1); continue; }
+        longest = max(longest, e - a);
         if (a < 0 || (int64_t)e > nnz) { atomicOr(flag, 4); continue; }
         for (int k = a; k < e; ++k) {
             const int c = colind[k];
@@ -52,10 +53,12 @@ __global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int
         }
     }
     if (far > 0) atomicAdd(flag + 1, far);
+    if (rowmax && longest > 0) atomicMax(rowmax, longest);
 }
 
-cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, cudaStream_t s) {
-    k_validate_csr<<<152 * 4, 256, 0, s>>>(rowptr, colind, n, nnz, flag);
+cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, cudaStream_t s,
+                                int* rowmax) {
+    k_validate_csr<<<152 * 4, 256, 0, s>>>(rowptr, colind, n, nnz, flag, rowmax);
     return cudaGetLastError();
 }
 

@@ -80,10 +80,14 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
             ic = ot - ia * tc;
         }
     }
-    float h[16], l[16];
+    // 4 x 4 output tile as 4 rows x 2 column pairs of double-float sums (f32x2: both columns of a
+    // pair per instruction, the same operations per lane as the scalar double-float MAC)
+    f2x h2[8], l2[8];
     double a64[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) { h[e] = 0.f; l[e] = 0.f; a64[e] = 0.0; }
+    for (int e = 0; e < 8; ++e) { h2[e] = 0ull; l2[e] = 0ull; }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) a64[e] = 0.0;
     const int ntiles = (n + QR_TR - 1) / QR_TR;
     int cnt = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += J.gx) {
@@ -113,22 +117,39 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
                 const float4 c4h = *reinterpret_cast<const float4*>(&zh[rr * kzp + ic * 4]);
                 const float4 c4l = *reinterpret_cast<const float4*>(&zl[rr * kzp + ic * 4]);
                 const float ah[4] = {a4h.x, a4h.y, a4h.z, a4h.w}, al[4] = {a4l.x, a4l.y, a4l.z, a4l.w};
-                const float ch[4] = {c4h.x, c4h.y, c4h.z, c4h.w}, cl[4] = {c4l.x, c4l.y, c4l.z, c4l.w};
+                const f2x c0h = f2_pack(c4h.x, c4h.y), c1h = f2_pack(c4h.z, c4h.w);
+                const f2x c0l = f2_pack(c4l.x, c4l.y), c1l = f2_pack(c4l.z, c4l.w);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) df_mac(h[i * 4 + j], l[i * 4 + j], ah[i], al[i], ch[j], cl[j]);
+                for (int i = 0; i < 4; ++i) {
+                    const f2x a2h = f2_pack(ah[i], ah[i]), a2l = f2_pack(al[i], al[i]), na2h = f2_pack(-ah[i], -ah[i]);
+                    df2_mac(h2[2 * i], l2[2 * i], a2h, a2l, na2h, c0h, c0l);
+                    df2_mac(h2[2 * i + 1], l2[2 * i + 1], a2h, a2l, na2h, c1h, c1l);
+                }
             }
         }
         __syncthreads();
         if (++cnt == QR_FLUSH) {
             cnt = 0;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) { a64[e] += (double)h[e] + (double)l[e]; h[e] = 0.f; l[e] = 0.f; }
+            for (int e = 0; e < 8; ++e) {
+                float h0, h1, l0, l1;
+                f2_unpack(h2[e], h0, h1);
+                f2_unpack(l2[e], l0, l1);
+                a64[2 * e] += (double)h0 + (double)l0;
+                a64[2 * e + 1] += (double)h1 + (double)l1;
+                h2[e] = 0ull;
+                l2[e] = 0ull;
+            }
         }
     }
 #pragma unroll
-    for (int e = 0; e < 16; ++e) a64[e] += (double)h[e] + (double)l[e];
+    for (int e = 0; e < 8; ++e) {
+        float h0, h1, l0, l1;
+        f2_unpack(h2[e], h0, h1);
+        f2_unpack(l2[e], l0, l1);
+        a64[2 * e] += (double)h0 + (double)l0;
+        a64[2 * e + 1] += (double)h1 + (double)l1;
+    }
     // reduce the row groups (fixed order) and write this CTA's partial
     double* red = reinterpret_cast<double*>(sgf);
     __syncthreads();
@@ -153,8 +174,15 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
         __threadfence();
         for (int q = t; q < OT * 16; q += QR_THREADS) {
             const int o = q / 16, e = q - o * 16;
-            double sacc = 0.0;
-            for (int bx = 0; bx < J.gx; ++bx) sacc += __ldcg(&partials[((size_t)bx * OT + o) * 16 + e]);
+            // eight running sums over the CTAs (CTA bx into sum bx % 8), added in a fixed order
+            double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            int bx = 0;
+            for (; bx + 8 <= J.gx; bx += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s8[u] += __ldcg(&partials[((size_t)(bx + u) * OT + o) * 16 + e]);
+            }
+            for (int u = 0; bx < J.gx; ++bx, ++u) s8[u] += __ldcg(&partials[((size_t)bx * OT + o) * 16 + e]);
+            const double sacc = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
             int oa, oc;
             if (sym) {
                 int rem = o;

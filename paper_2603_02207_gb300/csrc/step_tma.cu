@@ -360,12 +360,21 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                     const RecT rk = rec[k];
                     row_mac<PREC>(A, expand(rk.a), *reinterpret_cast<const WP*>(stc + rk.off));
                 }
-                if (k1 > g) {   // beyond the records: direct loads
+                if (k1 > g) {   // beyond the records: direct loads, eight in flight, added in entry order
                     const int z0 = srp[R + 1];
-                    for (int k = max(k0, g); k < k1; ++k) {
-                        const WP x = win[(size_t)colind[z0 + k] * ldq + cp];
-                        row_mac<PREC>(A, expand(vals[z0 + k]), x);
+                    int k = max(k0, g);
+                    for (; k + 8 <= k1; k += 8) {
+                        WP x[8];
+                        Raw v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            v[u] = vals[z0 + k + u];
+                            x[u] = win[(size_t)colind[z0 + k + u] * ldq + cp];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) row_mac<PREC>(A, expand(v[u]), x[u]);
                     }
+                    for (; k < k1; ++k) row_mac<PREC>(A, expand(vals[z0 + k]), win[(size_t)colind[z0 + k] * ldq + cp]);
                 }
                 row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wo, po_ptr, T);
             }
@@ -447,7 +456,7 @@ cudaError_t launch_tma_typed(const TmaLaunch& L, const CUtensorMap& g, const CUt
 
 }  // namespace
 
-bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int b, int threads_target,
+bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int maxrow, int b, int threads_target,
                    int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count) {
     L = TmaLaunch{};
     if (n <= 0 || b <= 0 || !encode_fn()) return false;
@@ -477,6 +486,9 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     q.recbytes = (int)rec_size(precision);
     const double avg = (double)nnz / (double)n;
     const double avgfar = nfar >= 0 && nfar <= nnz ? (double)nfar / (double)n : avg;
+    // tile capacity slack over the mean: more for irregular row lengths (power-law graphs), where
+    // tiles above the mean by far are common
+    const double slack = maxrow > 4.0 * avg + 16.0 ? 2.0 : 1.25;
     const size_t budget = (ctas_per_sm == 2 ? 112 : 224) * 1024 - 1024;
     // Producer warps: two keep up with the consumers now that the per-step work is copies only.
     // A producer waits for the release of tile i - nst only after the release of its previous
@@ -485,9 +497,9 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     const int np_cap = TMA_MAX_PROD;
     // layout for R rows per tile; returns the stage count that fits
     auto layout = [&](int Rt) {
-        int ecap = (((int)(avg * Rt * 1.25) + 8) + 3) & ~3;
+        int ecap = (((int)(avg * Rt * slack) + 8) + 3) & ~3;
         if (ecap > 4096) ecap = 4096;
-        int fcap = (((int)(avgfar * Rt * 1.25) + 8) + 3) & ~3;
+        int fcap = (((int)(avgfar * Rt * slack) + 8) + 3) & ~3;
         if (fcap > ecap) fcap = ecap;
         q.R = Rt;
         q.ecap = ecap;
