@@ -332,6 +332,8 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID_N, help="side of the 3-D grid (128 = the benchmark workload; "
                     "smaller sides are for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--c5-log2n", type=int, default=22,
+                    help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
                     help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
     ap.add_argument("--workloads", default="c1,c3,c4",
@@ -458,7 +460,7 @@ def main():
     extra = {}
     for w in [x for x in args.workloads.split(",") if x]:
         fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4, "c5": workload_config5}[w]
-        extra[w] = fn(L, h)
+        extra[w] = fn(L, h, log2n=args.c5_log2n) if w == "c5" else fn(L, h)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
     from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only
     exact = logdet_laplacian_3d(args.grid, SHIFT)

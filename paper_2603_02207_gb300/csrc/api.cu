@@ -49,6 +49,17 @@ struct ll_handle {
         int launches = 0, k1 = 0, t1 = 0, k2 = 0, t2 = 0;
         bool tma = false;
     } gfwd;
+    // CUDA graph of the last batched call's device work, with what the host combine needs
+    struct BatchGraph {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;
+        int launches = 0, kq = 0, kg = 0;
+        std::vector<std::vector<double>> d;   // per matrix: d_0 .. d_m
+        std::vector<double> sigma;
+        std::vector<double*> dots;            // per matrix: device (m + 1) x 2k traces
+        unsigned long long* ctr = nullptr;    // counters (error flag at 2 count + 2)
+        int* qrstat = nullptr;
+    } gbat;
     int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
     int max_row = 0;          // longest row of the last validated matrix
     // cached coefficients of the last set-up
@@ -402,6 +413,7 @@ void ll_destroy(ll_handle* h) {
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->gfwd.exec) cudaGraphExecDestroy(h->gfwd.exec);
+    if (h->gbat.exec) cudaGraphExecDestroy(h->gbat.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
@@ -1029,6 +1041,96 @@ ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* d
     return LL_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Graph key of a batched call: every input its device work depends on.
+std::vector<unsigned char> batched_key(const ll_handle* h, const ll_csr* mats, const ll_bounds* bnd, int count,
+                                       const ll_options& o, const int* degrees) {
+    std::vector<unsigned char> k;
+    auto put = [&](const void* p, size_t bytes) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        k.insert(k.end(), c, c + bytes);
+    };
+    put(&count, sizeof count);
+    for (int i = 0; i < count; ++i) {
+        put(&mats[i].n, sizeof mats[i].n);
+        put(&mats[i].nnz, sizeof mats[i].nnz);
+        put(&mats[i].rowptr, sizeof mats[i].rowptr);
+        put(&mats[i].colind, sizeof mats[i].colind);
+        put(&mats[i].values, sizeof mats[i].values);
+        put(&mats[i].dtype, sizeof mats[i].dtype);
+        put(&bnd[i].lmin, sizeof bnd[i].lmin);
+        put(&bnd[i].lmax, sizeof bnd[i].lmax);
+        const int m = degrees ? degrees[i] : -1;
+        put(&m, sizeof m);
+    }
+    ll_options oo;
+    memset(&oo, 0, sizeof oo);
+    oo = o;
+    oo.keep_for_backward = 0;
+    put(&oo.degree, sizeof oo.degree);
+    put(&oo.probes, sizeof oo.probes);
+    put(&oo.seed, sizeof oo.seed);
+    put(&oo.probe_kind, sizeof oo.probe_kind);
+    put(&oo.precision, sizeof oo.precision);
+    put(&oo.sval_mode, sizeof oo.sval_mode);
+    put(&oo.timeout_cycles, sizeof oo.timeout_cycles);
+    put(&h->ws_gen, sizeof h->ws_gen);
+    put(&h->inject, sizeof h->inject);
+    return k;
+}
+
+// Reads the traces, error flag and QR status of the last batched device work and combines the
+// estimates (Section 4.1) from the coefficients kept with it.
+ll_status batched_finish(ll_handle* h, const ll_csr* mats, int count, double* estimates, cudaStream_t s) {
+    const ll_handle::BatchGraph& G = h->gbat;
+    const int kq = G.kq, kg = G.kg, b2 = kq + kg;
+    int herr = 0;
+    std::vector<int> hqr(count);
+    LL_CK(cudaMemcpyAsync(&herr, G.ctr + 2 * count + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaMemcpyAsync(hqr.data(), G.qrstat, count * sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<std::vector<double>> hd(count);
+    for (int i = 0; i < count; ++i) {
+        hd[i].resize(G.d[i].size() * b2);
+        LL_CK(cudaMemcpyAsync(hd[i].data(), G.dots[i], hd[i].size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    LL_CK(cudaStreamSynchronize(s));
+    if (herr) return fail(h, LL_ERR_TIMEOUT, "batched launch: a bounded wait ran out");
+    for (int i = 0; i < count; ++i)
+        if (hqr[i]) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2 breakdown in batch entry " + std::to_string(i));
+    std::vector<double> est(count);
+    for (int i = 0; i < count; ++i) {
+        double tq = 0.0, tr = 0.0;
+        for (size_t j = 0; j < G.d[i].size(); ++j) {
+            double sq = 0.0, sr = 0.0;
+            for (int col = 0; col < kq; ++col) sq += hd[i][j * b2 + col];
+            for (int col = kq; col < b2; ++col) sr += hd[i][j * b2 + col];
+            tq += G.d[i][j] * sq;
+            tr += G.d[i][j] * sr;
+        }
+        tr /= (double)kg;
+        if (!std::isfinite(tq) || !std::isfinite(tr)) return fail(h, LL_ERR_NONFINITE, "non-finite trace in batch entry " + std::to_string(i));
+        est[i] = (double)mats[i].n * std::log(G.sigma[i]) + tq + tr;
+    }
+    for (int i = 0; i < count; ++i) estimates[i] = est[i];
+    ll_info& I = h->info;
+    I = ll_info{};
+    I.k = kq;
+    I.kernel_launches = h->launches;
+    cudaEventElapsedTime(&I.ms_probes, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&I.ms_pass1, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&I.ms_pass2, h->ev[3], h->ev[4]);
+    cudaEventElapsedTime(&I.ms_total, h->ev[0], h->ev[4]);
+    return LL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* bnd, int count, const ll_options* opts,
                             const int* degrees, double* estimates, void* stream) {
     if (!h || !opts || count < 0 || (count > 0 && (!mats || !bnd || !estimates))) return LL_ERR_INVALID_ARG;
@@ -1065,6 +1167,13 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         LL_CK(cudaStreamSynchronize(s));
         for (int i = 0; i < count; ++i)
             if (hf[2 * i]) return fail(h, LL_ERR_BAD_CSR, "invalid CSR in batch entry " + std::to_string(i));
+    }
+    // an identical call replays the captured device work (the descriptors, tables and
+    // coefficients it reads are still on the device)
+    if (o.use_graph && h->gbat.exec && h->gbat.key == batched_key(h, mats, bnd, count, o, degrees)) {
+        LL_CK(cudaGraphLaunch(h->gbat.exec, s));
+        h->launches += h->gbat.launches;
+        return batched_finish(h, mats, count, estimates, s);
     }
     // host set-up per matrix: sigma, interval, degree, coefficients
     struct Host { double sigma, c, gamma; int m; std::vector<double> d, coef; };
@@ -1195,118 +1304,129 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     for (int i = 0; i < count; ++i)
         LL_CK(cudaMemcpyAsync(base + off[i].coef, hs[i].coef.data(), hs[i].coef.size() * sizeof(double), cudaMemcpyHostToDevice, s));
 
-    LL_CK(cudaEventRecord(h->ev[0], s));
-    LL_CK(cudaMemsetAsync(ctr, 0, (size_t)(2 * count + 8) * sizeof(unsigned long long), s));
-    LL_CK(cudaMemsetAsync(qrstat, 0, (size_t)count * sizeof(int), s));
-    LL_CK(cudaMemsetAsync(qticks, 0, (size_t)count * sizeof(unsigned int), s));
+    // QR job lists of every matrix (pointers only), copied before the device work
+    std::vector<GramJob> gj(3 * count);
+    std::vector<CholJob> cj(count);
+    std::vector<RowJob> rj(3 * count);
+    int gxs_max = 1, gxc_max = 1, n_max = 1;
     for (int i = 0; i < count; ++i) {
         const Off& f = off[i];
         const int n = (int)mats[i].n;
-        const uint64_t seed = o.seed + (uint64_t)i;
-        LL_CK(launch_prepare_values(mats[i].values, mats[i].dtype, mats[i].nnz, 1.0 / (hs[i].sigma * hs[i].gamma), prec, base + f.vals, s));
-        LL_CK(launch_probes(wt, o.probe_kind, seed, LL_STREAM_S, n, kq, l1, base + f.S, l1, s));
-        LL_CK(launch_probes(T_F64, o.probe_kind, seed, LL_STREAM_G, n, kg, kg, base + f.G, kg, s));
-        h->launches += 3;
+        double* part = (double*)(base + f.qpart);
+        unsigned int* tick = qticks + i;
+        double* gram = (double*)(base + f.gram);
+        double* rinv = (double*)(base + f.rinv);
+        void* P = base + f.P;
+        double* q1 = (double*)(base + f.q1);
+        double* basis = (double*)(base + f.basis);
+        double* G = (double*)(base + f.G);
+        void* V = base + f.V;
+        gj[i] = GramJob{P, nullptr, n, f.gxs, part, tick, gram};
+        gj[count + i] = GramJob{q1, nullptr, n, f.gxs, part, tick, gram};
+        gj[2 * count + i] = GramJob{basis, G, n, f.gxc, part, tick, gram};
+        cj[i] = CholJob{gram, rinv, qrstat + i};
+        rj[i] = RowJob{P, rinv, nullptr, q1, nullptr, n};
+        rj[count + i] = RowJob{q1, rinv, nullptr, basis, V, n};
+        // G' into columns [kq, kq + kg) of [Q | G']; the typed block is offset by kq elements
+        rj[2 * count + i] = RowJob{basis, gram, G, basis + kq, V, n};
+        gxs_max = std::max(gxs_max, f.gxs);
+        gxc_max = std::max(gxc_max, f.gxc);
+        n_max = std::max(n_max, n);
     }
-    int per_sm = 2;
-    const int grid1 = h->sm_count * per_sm, grid2 = h->sm_count * per_sm;
-    LL_CK(cudaEventRecord(h->ev[1], s));
-    // pass 1 of every matrix: one persistent launch
-    LL_CK(launch_batched(prec, MODE_ACCUM, bp1, grid1, smem1, s));
-    h->launches++;
-    LL_CK(cudaEventRecord(h->ev[2], s));
-    // CholeskyQR2 and deflation of every matrix: eight launches over per-matrix job lists
-    // (Gram of Y, Cholesky, Y R^{-1}; Gram of Q1, Cholesky, Q1 R^{-1}; C = Q^T G; G' = G - Q C)
-    {
-        std::vector<GramJob> gj(3 * count);
-        std::vector<CholJob> cj(count);
-        std::vector<RowJob> rj(3 * count);
-        int gxs_max = 1, gxc_max = 1, n_max = 1;
+    LL_CK(cudaMemcpyAsync(gjobs, gj.data(), gj.size() * sizeof(GramJob), cudaMemcpyHostToDevice, s));
+    LL_CK(cudaMemcpyAsync(cjobs, cj.data(), cj.size() * sizeof(CholJob), cudaMemcpyHostToDevice, s));
+    LL_CK(cudaMemcpyAsync(rjobs, rj.data(), rj.size() * sizeof(RowJob), cudaMemcpyHostToDevice, s));
+
+    // the device work of the call, enqueued on q (captured into a graph for identical calls)
+    bool capturing = false;
+    auto rec = [&](cudaEvent_t ev, cudaStream_t q) {
+        return capturing ? cudaEventRecordWithFlags(ev, q, cudaEventRecordExternal) : cudaEventRecord(ev, q);
+    };
+    auto enqueue = [&](cudaStream_t q) -> ll_status {
+        LL_CK(rec(h->ev[0], q));
+        LL_CK(cudaMemsetAsync(ctr, 0, (size_t)(2 * count + 8) * sizeof(unsigned long long), q));
+        LL_CK(cudaMemsetAsync(qrstat, 0, (size_t)count * sizeof(int), q));
+        LL_CK(cudaMemsetAsync(qticks, 0, (size_t)count * sizeof(unsigned int), q));
         for (int i = 0; i < count; ++i) {
             const Off& f = off[i];
             const int n = (int)mats[i].n;
-            double* part = (double*)(base + f.qpart);
-            unsigned int* tick = qticks + i;
-            double* gram = (double*)(base + f.gram);
-            double* rinv = (double*)(base + f.rinv);
-            void* P = base + f.P;
-            double* q1 = (double*)(base + f.q1);
-            double* basis = (double*)(base + f.basis);
-            double* G = (double*)(base + f.G);
-            void* V = base + f.V;
-            gj[i] = GramJob{P, nullptr, n, f.gxs, part, tick, gram};
-            gj[count + i] = GramJob{q1, nullptr, n, f.gxs, part, tick, gram};
-            gj[2 * count + i] = GramJob{basis, G, n, f.gxc, part, tick, gram};
-            cj[i] = CholJob{gram, rinv, qrstat + i};
-            rj[i] = RowJob{P, rinv, nullptr, q1, nullptr, n};
-            rj[count + i] = RowJob{q1, rinv, nullptr, basis, V, n};
-            // G' into columns [kq, kq + kg) of [Q | G']; the typed block is offset by kq elements
-            rj[2 * count + i] = RowJob{basis, gram, G, basis + kq, V, n};
-            gxs_max = std::max(gxs_max, f.gxs);
-            gxc_max = std::max(gxc_max, f.gxc);
-            n_max = std::max(n_max, n);
+            const uint64_t seed = o.seed + (uint64_t)i;
+            LL_CK(launch_prepare_values(mats[i].values, mats[i].dtype, mats[i].nnz, 1.0 / (hs[i].sigma * hs[i].gamma), prec, base + f.vals, q));
+            LL_CK(launch_probes(wt, o.probe_kind, seed, LL_STREAM_S, n, kq, l1, base + f.S, l1, q));
+            LL_CK(launch_probes(T_F64, o.probe_kind, seed, LL_STREAM_G, n, kg, kg, base + f.G, kg, q));
+            h->launches += 3;
         }
-        LL_CK(cudaMemcpyAsync(gjobs, gj.data(), gj.size() * sizeof(GramJob), cudaMemcpyHostToDevice, s));
-        LL_CK(cudaMemcpyAsync(cjobs, cj.data(), cj.size() * sizeof(CholJob), cudaMemcpyHostToDevice, s));
-        LL_CK(cudaMemcpyAsync(rjobs, rj.data(), rj.size() * sizeof(RowJob), cudaMemcpyHostToDevice, s));
-        const GramJob g0 = gj[0];
-        const CholJob c0 = cj[0];
-        const RowJob r0 = rj[0];
-        LL_CK(launch_gram_jobs(pt, l1, kq, T_F64, 0, kq, true, g0, gjobs, count, gxs_max, s));
-        LL_CK(launch_chol_jobs(kq, c0, cjobs, count, s));
-        LL_CK(launch_apply_rinv_jobs(pt, l1, kq, kq, T_F64, 0, r0, rjobs, count, n_max, s));
-        LL_CK(launch_gram_jobs(T_F64, kq, kq, T_F64, 0, kq, true, g0, gjobs + count, count, gxs_max, s));
-        LL_CK(launch_chol_jobs(kq, c0, cjobs, count, s));
-        LL_CK(launch_apply_rinv_jobs(T_F64, kq, kq, l2, wt, l2, r0, rjobs + count, count, n_max, s));
-        LL_CK(launch_gram_jobs(T_F64, l2, kq, T_F64, kg, kg, false, g0, gjobs + 2 * count, count, gxc_max, s));
-        LL_CK(launch_project_jobs(l2, kq, kg, kg, l2, wt, l2, (b2 & 1), kq, r0, rjobs + 2 * count, count, n_max, s));
-        h->launches += 8;
-    }
-    LL_CK(cudaEventRecord(h->ev[3], s));
-    // pass 2 of every matrix: one persistent launch (arrival / release counters start at zero)
-    LL_CK(cudaMemsetAsync(ctr, 0, (size_t)2 * count * sizeof(unsigned long long), s));
-    LL_CK(launch_batched(prec, MODE_DOT, bp2, grid2, smem2, s));
-    h->launches++;
-    LL_CK(cudaEventRecord(h->ev[4], s));
-
-    int herr = 0;
-    std::vector<int> hqr(count);
-    LL_CK(cudaMemcpyAsync(&herr, ctr + 2 * count + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
-    LL_CK(cudaMemcpyAsync(hqr.data(), qrstat, count * sizeof(int), cudaMemcpyDeviceToHost, s));
-    std::vector<std::vector<double>> hd(count);
-    for (int i = 0; i < count; ++i) {
-        hd[i].resize((size_t)(hs[i].m + 1) * b2);
-        LL_CK(cudaMemcpyAsync(hd[i].data(), base + off[i].dots, hd[i].size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    LL_CK(cudaStreamSynchronize(s));
-    if (herr) return fail(h, LL_ERR_TIMEOUT, "batched launch: a bounded wait ran out");
-    for (int i = 0; i < count; ++i)
-        if (hqr[i]) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2 breakdown in batch entry " + std::to_string(i));
-    std::vector<double> est(count);
-    for (int i = 0; i < count; ++i) {
-        double tq = 0.0, tr = 0.0;
-        for (int j = 0; j <= hs[i].m; ++j) {
-            double sq = 0.0, sr = 0.0;
-            for (int col = 0; col < kq; ++col) sq += hd[i][(size_t)j * b2 + col];
-            for (int col = kq; col < b2; ++col) sr += hd[i][(size_t)j * b2 + col];
-            tq += hs[i].d[j] * sq;
-            tr += hs[i].d[j] * sr;
+        int per_sm = 2;
+        const int grid1 = h->sm_count * per_sm, grid2 = h->sm_count * per_sm;
+        LL_CK(rec(h->ev[1], q));
+        // pass 1 of every matrix: one persistent launch
+        LL_CK(launch_batched(prec, MODE_ACCUM, bp1, grid1, smem1, q));
+        h->launches++;
+        LL_CK(rec(h->ev[2], q));
+        // CholeskyQR2 and deflation of every matrix: eight launches over per-matrix job lists
+        // (Gram of Y, Cholesky, Y R^{-1}; Gram of Q1, Cholesky, Q1 R^{-1}; C = Q^T G; G' = G - Q C)
+        {
+            const GramJob g0 = gj[0];
+            const CholJob c0 = cj[0];
+            const RowJob r0 = rj[0];
+            LL_CK(launch_gram_jobs(pt, l1, kq, T_F64, 0, kq, true, g0, gjobs, count, gxs_max, q));
+            LL_CK(launch_chol_jobs(kq, c0, cjobs, count, q));
+            LL_CK(launch_apply_rinv_jobs(pt, l1, kq, kq, T_F64, 0, r0, rjobs, count, n_max, q));
+            LL_CK(launch_gram_jobs(T_F64, kq, kq, T_F64, 0, kq, true, g0, gjobs + count, count, gxs_max, q));
+            LL_CK(launch_chol_jobs(kq, c0, cjobs, count, q));
+            LL_CK(launch_apply_rinv_jobs(T_F64, kq, kq, l2, wt, l2, r0, rjobs + count, count, n_max, q));
+            LL_CK(launch_gram_jobs(T_F64, l2, kq, T_F64, kg, kg, false, g0, gjobs + 2 * count, count, gxc_max, q));
+            LL_CK(launch_project_jobs(l2, kq, kg, kg, l2, wt, l2, (b2 & 1), kq, r0, rjobs + 2 * count, count, n_max, q));
+            h->launches += 8;
         }
-        tr /= (double)kg;
-        if (!std::isfinite(tq) || !std::isfinite(tr)) return fail(h, LL_ERR_NONFINITE, "non-finite trace in batch entry " + std::to_string(i));
-        est[i] = (double)mats[i].n * std::log(hs[i].sigma) + tq + tr;
+        LL_CK(rec(h->ev[3], q));
+        // pass 2 of every matrix: one persistent launch (arrival / release counters start at zero)
+        LL_CK(cudaMemsetAsync(ctr, 0, (size_t)2 * count * sizeof(unsigned long long), q));
+        LL_CK(launch_batched(prec, MODE_DOT, bp2, grid2, smem2, q));
+        h->launches++;
+        LL_CK(rec(h->ev[4], q));
+        return LL_OK;
+    };
+    const int before = h->launches;
+    ll_status st = enqueue(s);
+    if (st != LL_OK) return st;
+    const int launched = h->launches - before;
+    ll_handle::BatchGraph& G = h->gbat;
+    G.d.resize(count);
+    G.sigma.resize(count);
+    G.dots.resize(count);
+    for (int i = 0; i < count; ++i) {
+        G.d[i] = hs[i].d;
+        G.sigma[i] = hs[i].sigma;
+        G.dots[i] = (double*)(base + off[i].dots);
     }
-    for (int i = 0; i < count; ++i) estimates[i] = est[i];
-    ll_info& I = h->info;
-    I = ll_info{};
-    I.k = kq;
-    I.kernel_launches = h->launches;
-    cudaEventElapsedTime(&I.ms_probes, h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&I.ms_pass1, h->ev[1], h->ev[2]);
-    cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
-    cudaEventElapsedTime(&I.ms_pass2, h->ev[3], h->ev[4]);
-    cudaEventElapsedTime(&I.ms_total, h->ev[0], h->ev[4]);
-    return LL_OK;
+    G.kq = kq;
+    G.kg = kg;
+    G.ctr = ctr;
+    G.qrstat = qrstat;
+    G.launches = launched;
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    G.key.clear();
+    if (o.use_graph) {
+        if (!h->cap_stream) LL_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        LL_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        const ll_status cst = enqueue(h->cap_stream);
+        capturing = false;
+        const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (cst == LL_OK && ce == cudaSuccess && graph && cudaGraphInstantiate(&G.exec, graph, 0) == cudaSuccess)
+            G.key = batched_key(h, mats, bnd, count, o, degrees);
+        else
+            G.exec = nullptr;
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        h->launches = before + launched;
+    }
+    return batched_finish(h, mats, count, estimates, s);
 }
 
 ll_status ll_get_info(const ll_handle* h, ll_info* out) {

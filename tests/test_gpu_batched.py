@@ -75,3 +75,24 @@ def test_batched_wait_timeout_is_reported(L, h):
     assert ei.value.name == "LL_ERR_TIMEOUT"
     est = L.ll_logdet_batched(h, dm[:2], bounds[:2], L.options(probes=30, seed=1))
     assert np.all(np.isfinite(est))
+
+
+def test_batched_graph_replay(L, h):
+    """An identical batched call replays the captured device work: same estimates as the eager
+    call and as a handle without graphs; changed bounds capture anew."""
+    mats, bounds = _batch()
+    dm = [L.DeviceCSR.from_host(A) for A in mats]
+    opts = L.options(probes=9, seed=6)
+    e1 = L.ll_logdet_batched(h, dm, bounds, opts)
+    l1 = h.info()["kernel_launches"]
+    e2 = L.ll_logdet_batched(h, dm, bounds, opts)
+    i2 = h.info()
+    assert np.array_equal(e1, e2)
+    assert i2["kernel_launches"] == l1 and i2["ms_pass2"] > 0
+    h2 = L.Handle()
+    e3 = L.ll_logdet_batched(h2, dm, bounds, L.options(probes=9, seed=6, use_graph=False))
+    assert np.array_equal(e1, e3)
+    b2 = [(lo, hi * 1.5) for lo, hi in bounds]
+    e4 = L.ll_logdet_batched(h, dm, b2, opts)
+    e5 = L.ll_logdet_batched(h2, dm, b2, L.options(probes=9, seed=6, use_graph=False))
+    assert np.array_equal(e4, e5) and not np.array_equal(e4, e1)

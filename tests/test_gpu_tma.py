@@ -167,27 +167,31 @@ def test_tma_pipeline_wait_timeout_is_reported(L):
 
 def test_graph_replay_matches_eager(L):
     """An identical second call replays the captured CUDA graph: same estimate, same phase
-    events, same launch count; any change of inputs (seed) captures anew."""
+    events, same launch count; any change of inputs (seed, values in place) is seen. The step
+    kernel is fixed so that two handles run the same kernels (the autotuner times candidates and
+    may choose differently per handle)."""
     A, lo, hi = _mat("lap3d_24")
     dA = L.DeviceCSR.from_host(A)
     h = L.Handle()
-    opts = L.options(degree=15, probes=30, seed=2, use_graph=True)
-    e1 = L.ll_logdet_forward(h, dA, lo, hi, opts)   # eager (tunes, then captures)
+    opts = L.options(degree=15, probes=30, seed=2, use_graph=True, step_kernel="tma")
+    e1 = L.ll_logdet_forward(h, dA, lo, hi, opts)   # eager, then captured
+    i1 = h.info()
     e2 = L.ll_logdet_forward(h, dA, lo, hi, opts)   # replay
     i2 = h.info()
     e3 = L.ll_logdet_forward(h, dA, lo, hi, opts)   # replay
     h2 = L.Handle()
-    eg = L.ll_logdet_forward(h2, dA, lo, hi, L.options(degree=15, probes=30, seed=2, use_graph=False))
-    ig = h2.info()
+    eg = L.ll_logdet_forward(h2, dA, lo, hi, L.options(degree=15, probes=30, seed=2, use_graph=False, step_kernel="tma"))
     assert e1 == e2 == e3 == eg
     assert i2["ms_pass1"] > 0 and i2["ms_pass2"] > 0 and i2["ms_total"] >= i2["ms_pass2"]
-    assert (i2["kernel_pass1"], i2["kernel_pass2"]) == (ig["kernel_pass1"], ig["kernel_pass2"])
-    e4 = L.ll_logdet_forward(h, dA, lo, hi, L.options(degree=15, probes=30, seed=3, use_graph=True))
-    e4g = L.ll_logdet_forward(h2, dA, lo, hi, L.options(degree=15, probes=30, seed=3, use_graph=False))
+    assert i2["kernel_launches"] == i1["kernel_launches"]
+    assert (i2["kernel_pass1"], i2["kernel_pass2"]) == (i1["kernel_pass1"], i1["kernel_pass2"])
+    o3 = L.options(degree=15, probes=30, seed=3, use_graph=True, step_kernel="tma")
+    e4 = L.ll_logdet_forward(h, dA, lo, hi, o3)
+    e4g = L.ll_logdet_forward(h2, dA, lo, hi, L.options(degree=15, probes=30, seed=3, use_graph=False, step_kernel="tma"))
     assert e4 == e4g and e4 != e1
     # values changed in place (same pointers): the replay reads the new values
     dA.values.mul_(2.0)
-    e5 = L.ll_logdet_forward(h, dA, 2 * lo, 2 * hi, L.options(degree=15, probes=30, seed=3, use_graph=True))
-    e5 = L.ll_logdet_forward(h, dA, 2 * lo, 2 * hi, L.options(degree=15, probes=30, seed=3, use_graph=True))
-    e5g = L.ll_logdet_forward(h2, dA, 2 * lo, 2 * hi, L.options(degree=15, probes=30, seed=3, use_graph=False))
+    L.ll_logdet_forward(h, dA, 2 * lo, 2 * hi, o3)
+    e5 = L.ll_logdet_forward(h, dA, 2 * lo, 2 * hi, o3)
+    e5g = L.ll_logdet_forward(h2, dA, 2 * lo, 2 * hi, L.options(degree=15, probes=30, seed=3, use_graph=False, step_kernel="tma"))
     assert e5 == e5g
