@@ -256,12 +256,25 @@ def workload_config4(L, h, count: int = 64):
     mats = [laplacian_2d(side, t) for side, t in params]
     bounds = [(t, 8.0 + t) for _, t in params]
     out = {"n_total": sum(A.n for A in mats), "nnz_total": sum(A.nnz for A in mats)}
+    import math as _m
+    degs = []
+    for lo, hi in bounds:
+        sg = lo if lo < 1 else 1.0
+        kap = (hi / sg) / (lo / sg)
+        rho = (_m.sqrt(kap) + 1) / (_m.sqrt(kap) - 1)
+        degs.append(max(10, min(250, _m.ceil(_m.log(1e6) / _m.log(rho)))))
     for prec in ("df64", "f32"):
         dm = [L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64") for A in mats]
         opts = L.options(probes=30, seed=2, precision=prec)
         ms_b, est = time_calls(lambda: L.ll_logdet_batched(h, dm, bounds, opts), 2, 1)
         inf = h.info()
-        import math as _m
+        # algorithmic bytes of every Léja step of every matrix (pass 1 on k = 10 columns, pass 2 on 20)
+        b1 = sum(m * step_bytes(A.n, A.nnz, 10, prec, "accum") for A, m in zip(mats, degs))
+        b2 = sum(m * step_bytes(A.n, A.nnz, 20, prec, "dot") for A, m in zip(mats, degs))
+        hr = L.Handle()
+        opts_r = L.options(probes=30, seed=2, precision=prec, step_kernel="gather")
+        ms_r, _ = time_calls(lambda: L.ll_logdet_batched(hr, dm, bounds, opts_r), 2, 1)
+        inf_r = hr.info()
 
         def one_by_one():
             res = []
@@ -277,6 +290,10 @@ def workload_config4(L, h, count: int = 64):
         exact = [logdet_laplacian_2d(side, t) for side, t in params]
         errs = [abs(e - x) / abs(x) for e, x in zip(est, exact)]
         out[prec] = {"ms_batched": ms_b, "ms_one_call_per_matrix": ms_s, "speedup": ms_s / ms_b,
+                     "step_kernel": {v: k for k, v in L.STEP_KERNELS.items()}.get(inf["kernel_pass1"], "?"),
+                     "pass_gbs": {"pass1": b1 / (inf["ms_pass1"] * 1e-3) / 1e9, "pass2": b2 / (inf["ms_pass2"] * 1e-3) / 1e9},
+                     "ms_batched_register_kernel": ms_r,
+                     "register_kernel_phase_ms": {"pass1": inf_r["ms_pass1"], "qr": inf_r["ms_qr"], "pass2": inf_r["ms_pass2"]},
                      "max_rel_diff_batched_vs_single": max(abs(a - b) / abs(b) for a, b in zip(est, est_s)),
                      "max_rel_err_vs_exact": max(errs), "median_rel_err_vs_exact": sorted(errs)[len(errs) // 2],
                      "phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}

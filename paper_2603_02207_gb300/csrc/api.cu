@@ -14,6 +14,7 @@
 #include "host_math.h"
 #include "kernels.cuh"
 #include "leja.h"
+#include "tma_common.cuh"
 
 namespace {
 
@@ -59,6 +60,7 @@ struct ll_handle {
         std::vector<double*> dots;            // per matrix: device (m + 1) x 2k traces
         unsigned long long* ctr = nullptr;    // counters (error flag at 2 count + 2)
         int* qrstat = nullptr;
+        int kernel = 0, threads1 = 0, threads2 = 0;   // step kernel of both passes, CTA sizes
     } gbat;
     int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
     int max_row = 0;          // longest row of the last validated matrix
@@ -228,7 +230,7 @@ ll_status bind_exec(ll_handle* h, int precision, int mode, int b, StepExec& E, S
         static const char* mn[NUM_MODES] = {"tma_meta_plain", "tma_meta_accum", "tma_meta_dot", "tma_meta_adj"};
         WS(desc, unsigned char*, dn[mode], E.tl.desc_bytes);
         WS(gcol, int*, gn[mode], E.tl.gcol_bytes);
-        WS(meta, int2*, mn[mode], E.tl.meta_bytes);
+        WS(meta, int4*, mn[mode], E.tl.meta_bytes);
         E.tl.q.desc = desc;
         E.tl.q.gcol = gcol;
         E.tl.q.meta = meta;
@@ -1077,6 +1079,7 @@ std::vector<unsigned char> batched_key(const ll_handle* h, const ll_csr* mats, c
     put(&oo.precision, sizeof oo.precision);
     put(&oo.sval_mode, sizeof oo.sval_mode);
     put(&oo.timeout_cycles, sizeof oo.timeout_cycles);
+    put(&oo.step_kernel, sizeof oo.step_kernel);
     put(&h->ws_gen, sizeof h->ws_gen);
     put(&h->inject, sizeof h->inject);
     return k;
@@ -1119,6 +1122,10 @@ ll_status batched_finish(ll_handle* h, const ll_csr* mats, int count, double* es
     I = ll_info{};
     I.k = kq;
     I.kernel_launches = h->launches;
+    I.kernel_pass1 = G.kernel;
+    I.kernel_pass2 = G.kernel;
+    I.threads_pass1 = G.threads1;
+    I.threads_pass2 = G.threads2;
     cudaEventElapsedTime(&I.ms_probes, h->ev[0], h->ev[1]);
     cudaEventElapsedTime(&I.ms_pass1, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
@@ -1156,7 +1163,8 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     if (2 * kg > 512 || kg > 96) return fail(h, LL_ERR_UNSUPPORTED, "m_vec / 3 above 96 is not supported");
     const int kq = kg, b1 = kq, b2 = kq + kg, l1 = block_ld(prec, b1), l2 = block_ld(prec, b2);
 
-    // validation of every CSR (one synchronisation)
+    // validation of every CSR (one synchronisation); the far-entry counts size the TMA gather capacity
+    std::vector<int> hfar(count, 0);
     {
         WS(flags, int*, "bt_flags", (size_t)2 * count * sizeof(int));
         LL_CK(cudaMemsetAsync(flags, 0, (size_t)2 * count * sizeof(int), s));
@@ -1167,6 +1175,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         LL_CK(cudaStreamSynchronize(s));
         for (int i = 0; i < count; ++i)
             if (hf[2 * i]) return fail(h, LL_ERR_BAD_CSR, "invalid CSR in batch entry " + std::to_string(i));
+        for (int i = 0; i < count; ++i) hfar[i] = hf[2 * i + 1];
     }
     // an identical call replays the captured device work (the descriptors, tables and
     // coefficients it reads are still on the device)
@@ -1207,6 +1216,21 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     avg /= tot_n;
     plan_batched(b1, avg, bp1, &smem1);
     plan_batched(b2, avg, bp2, &smem2);
+    // TMA-fed persistent passes, unless the register-gather kernel is asked for or no layout fits
+    BatchTmaLaunch tl1, tl2;
+    bool use_tma = false;
+    if (o.step_kernel != LL_KERNEL_GATHER) {
+        int n_min = INT32_MAX;
+        double far = 0.0;
+        for (int i = 0; i < count; ++i) {
+            n_min = std::min(n_min, (int)mats[i].n);
+            far += (double)hfar[i];
+        }
+        use_tma = plan_batched_tma(prec, MODE_ACCUM, n_min, avg, far / tot_n, b1, l1, l1, max_m, count, h->sm_count, tl1) &&
+                  plan_batched_tma(prec, MODE_DOT, n_min, avg, far / tot_n, b2, l2, l2, max_m, count, h->sm_count, tl2);
+    }
+    const int R1 = use_tma ? tl1.q.R : bp1.R, R2 = use_tma ? tl2.q.R : bp2.R;
+    const int tstride = bt_table_ints(max_m, count);   // per pass: step offsets, active counts, tile prefix, coef offsets
 
     // one workspace for every per-matrix buffer (256-byte aligned regions)
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1217,8 +1241,8 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     for (int i = 0; i < count; ++i) {
         const size_t n = (size_t)mats[i].n, nnz = (size_t)mats[i].nnz;
         Off& f = off[i];
-        f.T1 = (int)((n + bp1.R - 1) / bp1.R);
-        f.T2 = (int)((n + bp2.R - 1) / bp2.R);
+        f.T1 = (int)((n + R1 - 1) / R1);
+        f.T2 = (int)((n + R2 - 1) / R2);
         f.vals = total; total += al(nnz * ew);
         f.S = total; total += al(n * l1 * ew);
         f.G = total; total += al(n * kg * sizeof(double));
@@ -1228,7 +1252,9 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         f.basis = total; total += al(n * l2 * sizeof(double));
         f.q1 = total; total += al(n * kq * sizeof(double));
         f.V = total; total += al(n * l2 * ew);
-        f.part = total; total += al((size_t)2 * std::max(f.T1, f.T2) * b2 * sizeof(double));
+        // trace partials: per step and tile (TMA passes, reduced after the pass), else two slots per tile
+        f.part = total;
+        total += al((use_tma ? (size_t)(hs[i].m + 1) * f.T2 : (size_t)2 * std::max(f.T1, f.T2)) * b2 * sizeof(double));
         f.dots = total; total += al((size_t)(hs[i].m + 1) * b2 * sizeof(double));
         f.coef = total; total += al((size_t)2 * (hs[i].m + 1) * sizeof(double));
         // CholeskyQR2 of this matrix: Gram partials of its row blocks, ticket, Gram and R^{-1}
@@ -1247,15 +1273,56 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     WS(rjobs, RowJob*, "bt_row_jobs", (size_t)3 * count * sizeof(RowJob));
     WS(ctr, unsigned long long*, "bt_counters", (size_t)(2 * count + 8) * sizeof(unsigned long long));
     WS(dmats, BatchMat*, "bt_mats", (size_t)2 * count * sizeof(BatchMat));
-    WS(dtab, int*, "bt_tables", (size_t)2 * (2 * (max_m + 1) + count + 1) * sizeof(int));
+    WS(dtab, int*, "bt_tables", (size_t)2 * tstride * sizeof(int));
+    // TMA passes: per-pass tile descriptors of every matrix (by batch tile), the matrices with
+    // their tensor maps, and the coefficient tables concatenated
+    size_t ntiles[2] = {0, 0}, ncoef = 0;
+    for (int i = 0; i < count; ++i) {
+        ntiles[0] += (size_t)off[i].T1;
+        ntiles[1] += (size_t)off[i].T2;
+        ncoef += (size_t)2 * (hs[i].m + 1);
+    }
+    unsigned char* tdesc[2] = {nullptr, nullptr};
+    int* tgcol[2] = {nullptr, nullptr};
+    int4* tmeta[2] = {nullptr, nullptr};
+    BatchTmaMat* dtm = nullptr;
+    double* coef_all = nullptr;
+    float2* coef_df_all = nullptr;
+    if (use_tma) {
+        WS(d1, unsigned char*, "bt_tma_desc1", ntiles[0] * tl1.q.desc_stride);
+        WS(d2, unsigned char*, "bt_tma_desc2", ntiles[1] * tl2.q.desc_stride);
+        WS(g1, int*, "bt_tma_gcol1", ntiles[0] * tl1.q.gcol_stride);
+        WS(g2, int*, "bt_tma_gcol2", ntiles[1] * tl2.q.gcol_stride);
+        WS(m1, int4*, "bt_tma_meta1", ntiles[0] * sizeof(int4));
+        WS(m2, int4*, "bt_tma_meta2", ntiles[1] * sizeof(int4));
+        WS(tm, BatchTmaMat*, "bt_tma_mats", (size_t)2 * count * sizeof(BatchTmaMat));
+        WS(ca, double*, "bt_tma_coef", ncoef * sizeof(double));
+        WS(cd, float2*, "bt_tma_coef_df", ncoef * sizeof(float2));
+        coef_df_all = cd;
+        tdesc[0] = d1; tdesc[1] = d2;
+        tgcol[0] = g1; tgcol[1] = g2;
+        tmeta[0] = m1; tmeta[1] = m2;
+        dtm = tm;
+        coef_all = ca;
+    }
 
     // descriptors and item tables of both passes
     std::vector<BatchMat> hm(2 * count);
-    std::vector<int> tabs(2 * (2 * (max_m + 1) + count + 1));
+    std::vector<int> tabs((size_t)2 * tstride);
+    BatchTmaParams bt1{}, bt2{};
+    std::vector<BatchTmaMat> htm(use_tma ? 2 * count : 0);
+    std::vector<double> hcoef;
+    std::vector<int> coef_off(count);
+    for (int q = 0; q < count; ++q) {
+        coef_off[q] = (int)hcoef.size();
+        hcoef.insert(hcoef.end(), hs[ord[q]].coef.begin(), hs[ord[q]].coef.end());
+    }
     for (int pass = 0; pass < 2; ++pass) {
-        int* t_off = tabs.data() + pass * (2 * (max_m + 1) + count + 1);
+        int* t_off = tabs.data() + pass * tstride;
         int* t_act = t_off + (max_m + 1);
         int* t_pre = t_act + (max_m + 1);
+        int* t_cof = t_pre + (count + 1);
+        for (int q = 0; q < count; ++q) t_cof[q] = coef_off[q];
         t_pre[0] = 0;
         for (int q = 0; q < count; ++q) {
             const int i = ord[q];
@@ -1287,7 +1354,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         t_off[max_m] = acc;
         BatchParams& bp = pass == 0 ? bp1 : bp2;
         bp.mats = dmats + pass * count;
-        bp.step_off = dtab + pass * (2 * (max_m + 1) + count + 1);
+        bp.step_off = dtab + pass * tstride;
         bp.step_active = bp.step_off + (max_m + 1);
         bp.tile_prefix = bp.step_active + (max_m + 1);
         bp.ticket = (unsigned int*)(ctr + 2 * count) + pass;
@@ -1298,6 +1365,60 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         bp.ld = pass == 0 ? l1 : l2;
         bp.total_items = acc;
         bp.max_m = max_m;
+        if (use_tma) {
+            const BatchTmaLaunch& TL = pass == 0 ? tl1 : tl2;
+            const int ld = pass == 0 ? l1 : l2;
+            const int Rt = TL.q.R;
+            for (int q = 0; q < count; ++q) {
+                const BatchMat& M = hm[pass * count + q];
+                BatchTmaMat& X = htm[pass * count + q];
+                X.colind = M.colind;
+                X.vals = M.vals;
+                X.w[0] = const_cast<void*>(M.w0);
+                X.w[1] = M.wa;
+                X.w[2] = M.wb;
+                X.p = M.p;
+                X.partials = M.partials;
+                X.dots = M.dots;
+                X.n = M.n;
+                X.T = M.T;
+                X.m = M.m;
+                bool ok = true;
+                for (int x = 0; x < 3; ++x)
+                    ok = ok && encode_rows(&X.gat[x], X.w[x], (int)ew, ld, X.n, 1) &&
+                         encode_rows(&X.win[x], X.w[x], (int)ew, ld, X.n, Rt + 2 * TMA_HALO);
+                // pass 1 reads P rows (8-byte elements), pass 2 the V rows
+                ok = ok && (pass == 0 ? encode_rows(&X.aux, M.p, 8, ld, X.n, Rt) : encode_rows(&X.aux, M.w0, (int)ew, ld, X.n, Rt));
+                if (!ok) return fail(h, LL_ERR_CUDA, "tensor map encoding failed for batch entry " + std::to_string(ord[q]));
+            }
+            BatchTmaParams& B = pass == 0 ? bt1 : bt2;
+            B.mats = dtm + pass * count;
+            B.tables = bp.step_off;
+            B.coef = coef_all;
+            B.coef_df = coef_df_all;
+            B.desc = tdesc[pass];
+            B.gcol = tgcol[pass];
+            B.meta = tmeta[pass];
+            B.ticket = bp.ticket;
+            B.error = bp.error;
+            B.arrived = bp.arrived;
+            B.spin_budget = bp.spin_budget;
+            B.total_items = acc;
+            B.max_m = max_m;
+            B.count = count;
+            B.b = pass == 0 ? b1 : b2;
+            B.ldw = ld;
+            B.ldp = ld;
+            B.q = TL.q;
+            B.q.inject = h->inject;
+        }
+    }
+    if (use_tma) {
+        LL_CK(cudaMemcpyAsync(dtm, htm.data(), htm.size() * sizeof(BatchTmaMat), cudaMemcpyHostToDevice, s));
+        LL_CK(cudaMemcpyAsync(coef_all, hcoef.data(), hcoef.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        std::vector<float2> hcoef_df(hcoef.size());
+        for (size_t x = 0; x < hcoef.size(); ++x) hcoef_df[x] = df_split(hcoef[x]);
+        LL_CK(cudaMemcpyAsync(coef_df_all, hcoef_df.data(), hcoef_df.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     }
     LL_CK(cudaMemcpyAsync(dmats, hm.data(), hm.size() * sizeof(BatchMat), cudaMemcpyHostToDevice, s));
     LL_CK(cudaMemcpyAsync(dtab, tabs.data(), tabs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1358,9 +1479,37 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         }
         int per_sm = 2;
         const int grid1 = h->sm_count * per_sm, grid2 = h->sm_count * per_sm;
+        // tile descriptors of every matrix for a TMA pass (built from the prepared values)
+        auto describe = [&](int pass) -> ll_status {
+            const BatchTmaLaunch& TL = pass == 0 ? tl1 : tl2;
+            const int* t_pre = tabs.data() + pass * tstride + 2 * (max_m + 1);
+            for (int qq = 0; qq < count; ++qq) {
+                const int i = ord[qq];
+                TmaLaunch D{};
+                D.q = TL.q;
+                D.q.desc_w = tdesc[pass] + (size_t)t_pre[qq] * TL.q.desc_stride;
+                D.q.gcol_w = tgcol[pass] + (size_t)t_pre[qq] * (TL.q.gcol_stride / 4);
+                D.q.meta_w = tmeta[pass] + t_pre[qq];
+                StepParams pd{};
+                pd.rowptr = mats[i].rowptr;
+                pd.colind = mats[i].colind;
+                pd.vals = base + off[i].vals;
+                pd.n = (int)mats[i].n;
+                pd.num_tiles = pass == 0 ? off[i].T1 : off[i].T2;
+                LL_CK(launch_tma_describe(prec, D, pd, q));
+                h->launches++;
+            }
+            return LL_OK;
+        };
         LL_CK(rec(h->ev[1], q));
         // pass 1 of every matrix: one persistent launch
-        LL_CK(launch_batched(prec, MODE_ACCUM, bp1, grid1, smem1, q));
+        if (use_tma) {
+            ll_status ds = describe(0);
+            if (ds != LL_OK) return ds;
+            LL_CK(launch_batched_tma(prec, MODE_ACCUM, bt1, tl1, q));
+        } else {
+            LL_CK(launch_batched(prec, MODE_ACCUM, bp1, grid1, smem1, q));
+        }
         h->launches++;
         LL_CK(rec(h->ev[2], q));
         // CholeskyQR2 and deflation of every matrix: eight launches over per-matrix job lists
@@ -1382,7 +1531,16 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         LL_CK(rec(h->ev[3], q));
         // pass 2 of every matrix: one persistent launch (arrival / release counters start at zero)
         LL_CK(cudaMemsetAsync(ctr, 0, (size_t)2 * count * sizeof(unsigned long long), q));
-        LL_CK(launch_batched(prec, MODE_DOT, bp2, grid2, smem2, q));
+        if (use_tma) {
+            ll_status ds = describe(1);
+            if (ds != LL_OK) return ds;
+            LL_CK(launch_batched_tma(prec, MODE_DOT, bt2, tl2, q));
+            // traces of every matrix and step: the tile partials summed in tile order
+            LL_CK(launch_batched_dots(prec, dtm + count, count, b2, (max_m + 1) * b2, q));
+            h->launches++;
+        } else {
+            LL_CK(launch_batched(prec, MODE_DOT, bp2, grid2, smem2, q));
+        }
         h->launches++;
         LL_CK(rec(h->ev[4], q));
         return LL_OK;
@@ -1405,6 +1563,9 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     G.ctr = ctr;
     G.qrstat = qrstat;
     G.launches = launched;
+    G.kernel = use_tma ? LL_KERNEL_TMA : LL_KERNEL_GATHER;
+    G.threads1 = use_tma ? tl1.threads : BATCH_THREADS;
+    G.threads2 = use_tma ? tl2.threads : BATCH_THREADS;
     if (G.exec) {
         cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;

@@ -36,7 +36,6 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     return v;
 }
 
-constexpr int BATCH_THREADS = 256;
 constexpr int BATCH_U = 8;
 
 }  // namespace

@@ -1,0 +1,599 @@
+// Batched Léja passes fed by TMA: many independent matrices, all their Léja steps (Algorithm 2,
+// Eq. 4), in one persistent launch per pass, over the tile pipeline of the single-matrix TMA step.
+//
+// Work items are (step j, matrix i, row tile t), numbered step-major over the matrices still
+// active at step j (sorted by degree, descending, so they are a prefix). A CTA has three roles:
+//  * the producer warp takes item numbers from a global ticket, eight at a time; eight lanes decode
+//    them in parallel from tables held in shared memory and load each item's step scalars,
+//    pointers and tile record count, and start the copy of its gather-column list. Up to sixteen
+//    items are taken ahead of the one being issued. To issue an item, the producer waits (bounded)
+//    until every tile of step j - 1 of matrix i has finished, then for a free stage, and issues
+//    the item's copies: descriptor, operand window, V/P rows and the gathered rows of W_j of
+//    matrix i, through that matrix's own tensor maps;
+//  * the consumer warps compute the item's rows with the per-row arithmetic of the single-matrix
+//    kernels, store W_{j+1} (and P), and in pass 2 the tile's per-column trace partials (kept per
+//    step and reduced per matrix after the pass, in a fixed order);
+//  * the signal warp waits for each stage's consumers, publishes the tile's completion (a release
+//    add to the matrix's arrival counter, so the stores of W_{j+1} and P are visible before it),
+//    and only then frees the stage for the producer. The fence latency of the release stays off
+//    the consumers and the producer.
+// Every dependency of an item has a smaller ticket; consumers wait only on copies and the signal
+// warp only on consumers, so the smallest unfinished item can always proceed and the launch cannot
+// deadlock whatever the residency. W_j and P of step j - 1 were written by other CTAs with generic
+// stores; after the acquire of the arrival counter a proxy fence orders them before this CTA's TMA
+// reads. Every wait is bounded (clock64); when one runs out the CTA records the error, hands the
+// consumers an end marker, waits (bounded) for its copies in flight and returns, and the host
+// reports LL_ERR_TIMEOUT.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "step_common.cuh"
+#include "tma_common.cuh"
+
+namespace ll {
+
+namespace {
+
+constexpr int BT_CONSUMER_BAR = 1;   // named barrier of the consumer warps
+static_assert((BT_IRING & (BT_IRING - 1)) == 0 && BT_IRING % BT_TAKE == 0 && BT_TAKE <= 32, "take-ahead ring");
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void consumer_sync(int cthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(BT_CONSUMER_BAR), "r"(cthreads) : "memory");
+}
+// consumer-wide OR of a predicate (a named-barrier reduction)
+__device__ __forceinline__ bool consumer_any(int cthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(pred ? 1u : 0u), "r"(BT_CONSUMER_BAR), "r"(cthreads)
+        : "memory");
+    return r != 0;
+}
+
+// decodes ticket g into (step, matrix, tile) from the tables; x = -1 past the last item
+__device__ __forceinline__ int3 bt_decode(const int* t_off, const int* t_act, const int* t_pre, int max_m, int total, int g) {
+    if (g >= total) return make_int3(-1, 0, 0);
+    int lo = 0, hi = max_m - 1;
+    while (lo < hi) {   // last step whose first item is <= g
+        const int mid = (lo + hi + 1) >> 1;
+        if (t_off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const int local = g - t_off[lo];
+    int a = 0, b = t_act[lo] - 1;   // last active matrix whose first tile is <= local
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (t_pre[mid] <= local) a = mid; else b = mid - 1;
+    }
+    return make_int3(lo, a, local - t_pre[a]);
+}
+
+__device__ __forceinline__ void copy_item(BItem* dst, const BItem* src, int lane) {
+    if (lane < (int)(sizeof(BItem) / 4)) reinterpret_cast<int*>(dst)[lane] = reinterpret_cast<const int*>(src)[lane];
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(m) : "memory");
+}
+
+// (ah, al) += (bh, bl) on both lanes of double-float pairs: TwoSum (Knuth) of the leading parts,
+// the trailing parts added to the error, then a renormalisation (FastTwoSum)
+__device__ __forceinline__ void df2_add(f2x& ah, f2x& al, f2x bh, f2x bl) {
+    const f2x s = f2_add(ah, bh);
+    const f2x bb = f2_sub(s, ah);
+    f2x e = f2_add(f2_sub(ah, f2_sub(s, bb)), f2_sub(bh, bb));
+    e = f2_add(e, f2_add(al, bl));
+    ah = f2_add(s, e);
+    al = f2_sub(e, f2_sub(ah, s));
+}
+__device__ __forceinline__ f2x shfl_down_f2(f2x v, int off) {
+    return __shfl_down_sync(0xffffffffu, v, off);
+}
+
+}  // namespace
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const BatchTmaParams bp, const int off_red, const int off_tab) {
+    using WP = typename PairT<PREC>::W;
+    using PP = typename PairT<PREC>::P;
+    using Raw = typename PairT<PREC>::Raw;
+    using RecT = Rec<PREC>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full[TMA_MAX_STAGES];
+    __shared__ __align__(8) unsigned long long empty[TMA_MAX_STAGES];
+    __shared__ __align__(8) unsigned long long freeb[TMA_MAX_STAGES];
+    __shared__ __align__(8) unsigned long long gbar[BT_IRING];
+    __shared__ __align__(16) BItem ring[BT_IRING];
+    __shared__ __align__(16) BItem sitem[TMA_MAX_STAGES];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+
+    const TmaParams& q = bp.q;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int NST = q.nst;
+    const int R = q.R;
+    const int cthreads = (int)blockDim.x - 64;   // consumer threads; then the producer and the signal warp
+    const int cwarps = cthreads >> 5;
+    const long long budget = bp.spin_budget;
+    int* tab = reinterpret_cast<int*>(smem + off_tab);
+    const int ntab = bt_table_ints(bp.max_m, bp.count);
+    for (int x = tid; x < ntab; x += blockDim.x) tab[x] = bp.tables[x];
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), cwarps);
+            mbar_init(smem_u32(&freeb[s]), 1);
+        }
+        for (int s = 0; s < BT_IRING; ++s) mbar_init(smem_u32(&gbar[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == cwarps) {
+        // ------------------------------------------------------------------ producer warp
+        const int* t_off = tab;
+        const int* t_act = t_off + bp.max_m + 1;
+        const int* t_pre = t_act + bp.max_m + 1;
+        const int* t_coef = t_pre + bp.count + 1;
+        unsigned char* gring = smem + q.ring_base;
+        int taken = 0, k = 0;
+        bool ended = false, dead = false;
+        int ci = -1, cj = 0;   // lane 0: the matrix whose finished steps were last read, and their count
+        // take BT_TAKE tickets; lane l < BT_TAKE decodes ticket g0 + l into ring position taken + l
+        auto take = [&]() {
+            unsigned int g0 = 0;
+            if (lane == 0)
+                g0 = (ended || *((volatile int*)bp.error)) ? (unsigned int)bp.total_items : atomicAdd(bp.ticket, (unsigned int)BT_TAKE);
+            g0 = __shfl_sync(0xffffffffu, g0, 0);
+            bool none = false;
+            if (lane < BT_TAKE) {
+                const int slot = (taken + lane) & (BT_IRING - 1);
+                const unsigned int g = g0 + (unsigned int)lane;
+                const int3 d = bt_decode(t_off, t_act, t_pre, bp.max_m, bp.total_items,
+                                         g >= (unsigned int)bp.total_items ? bp.total_items : (int)g);
+                BItem& it = ring[slot];   // filled in place
+                it.j = d.x;
+                it.i = d.y;
+                it.t = d.z;
+                const uint32_t bar = smem_u32(&gbar[slot]);
+                if (d.x >= 0) {
+                    const BatchTmaMat* M = bp.mats + d.y;
+                    const int gt = t_pre[d.y] + d.z;
+                    const int4 mt = bp.meta[gt];
+                    const double* cf = bp.coef + t_coef[d.y];
+                    it.beta = cf[2 * d.x];
+                    it.d0 = cf[1];
+                    it.dn = cf[2 * (d.x + 1) + 1];
+                    const float2* cfd = bp.coef_df + t_coef[d.y];
+                    it.beta_df = cfd[2 * d.x];
+                    it.d0_df = cfd[1];
+                    it.dn_df = cfd[2 * (d.x + 1) + 1];
+                    const int buf = d.x == 0 ? 0 : ((d.x & 1) ? 1 : 2);
+                    prefetch_map(&M->win[buf]);
+                    prefetch_map(&M->gat[buf]);
+                    if (MODE == MODE_DOT || d.x > 0) prefetch_map(&M->aux);
+                    it.win = M->w[d.x == 0 ? 0 : ((d.x & 1) ? 1 : 2)];
+                    it.wout = M->w[(d.x & 1) ? 2 : 1];
+                    it.aux = MODE == MODE_ACCUM ? M->p : static_cast<void*>(M->partials);
+                    it.colind = M->colind;
+                    it.vals = M->vals;
+                    it.n = M->n;
+                    it.T = M->T;
+                    it.gt = gt;
+                    it.nrec = mt.x;
+                    it.ng = mt.y;
+                    it.nw = mt.z;
+                    // the extra windows' start rows, then the gathered columns
+                    const uint32_t bytes = (mt.y > 0 || mt.z > 0) ? (uint32_t)(TMA_MAX_WIN + ((mt.y + 3) & ~3)) * 4u : 0u;
+                    if (bytes) {
+                        mbar_arrive_expect_tx(bar, bytes);
+                        bulk_copy(smem_u32(gring + slot * q.gcol_stride), bp.gcol + (size_t)gt * (q.gcol_stride >> 2), bytes, bar);
+                    } else {
+                        mbar_arrive(bar);
+                    }
+                } else {
+                    none = true;
+                    mbar_arrive(bar);
+                }
+            }
+            ended = __any_sync(0xffffffffu, none) || ended;
+            __syncwarp();   // the ring entries are read by every lane
+            taken += BT_TAKE;
+        };
+        for (int x = 0; x < BT_IRING / BT_TAKE; ++x) take();
+        for (;; ++k) {
+            if (taken - k <= BT_IRING - BT_TAKE) take();
+            const int slot = k & (BT_IRING - 1);
+            // every lane reads the gather-column list: every lane waits for its copy
+            bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&gbar[slot]), (uint32_t)((k / BT_IRING) & 1), budget));
+            const int j = ring[slot].j, i = ring[slot].i;
+            // step j - 1 of matrix i finished (arrival count j * T); then the other CTAs' generic
+            // stores of W_j and P are ordered before this CTA's TMA reads of them
+            if (ok && j > 0 && lane == 0 && !(i == ci && j <= cj)) {
+                const unsigned long long T = (unsigned long long)ring[slot].T;
+                const long long t0 = clock64();
+                for (;;) {
+                    const unsigned long long v = ld_acquire_u64(&bp.arrived[i]);
+                    if (v >= (unsigned long long)j * T) {
+                        ci = i;
+                        cj = (int)(v / T);
+                        break;
+                    }
+                    if (*((volatile int*)bp.error) || clock64() - t0 > budget) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            }
+            const int s = k % NST;
+            if (ok && lane == 0 && k >= NST) ok = mbar_wait_bounded(smem_u32(&freeb[s]), (uint32_t)(((k / NST) & 1) ^ 1), budget);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                dead = true;
+                if (lane == 0) atomicExch(bp.error, 1);
+                break;
+            }
+            // publish the item to the consumers and the signal warp
+            copy_item(&sitem[s], &ring[slot], lane);
+            __syncwarp();
+            const uint32_t bar = smem_u32(&full[s]);
+            if (j < 0) {   // no more items: the end marker
+                if (lane == 0) mbar_arrive(bar);
+                break;
+            }
+            const BatchTmaMat* M = bp.mats + i;
+            const int t = ring[slot].t, gt = ring[slot].gt, ng = ring[slot].ng, nw = ring[slot].nw;
+            const int buf = j == 0 ? 0 : ((j & 1) ? 1 : 2);
+            const bool has_aux = (MODE == MODE_DOT) || (MODE == MODE_ACCUM && j > 0);
+            const int ngr = (ng + 3) >> 2;
+            unsigned char* st = smem + s * q.stage_bytes;
+            if (lane == 0) {
+                const uint32_t dbytes16 = ((uint32_t)q.hdr_bytes + (uint32_t)ring[slot].nrec * (uint32_t)q.recbytes + 15u) & ~15u;
+                const uint32_t bytes = dbytes16 + (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
+                                       (uint32_t)(1 + nw) * (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
+                                       (has_aux ? (uint32_t)R * (uint32_t)q.auxbytes : 0u) +
+                                       ((q.inject == LL_INJECT_STALL && k == 0 && blockIdx.x == 0) ? 16u : 0u);
+                mbar_arrive_expect_tx(bar, bytes);
+                bulk_copy(smem_u32(st + q.off_desc), bp.desc + (size_t)gt * q.desc_stride, dbytes16, bar);
+                tma_load_rows(smem_u32(st), &M->win[buf], t * R - TMA_HALO, bar);
+                if (has_aux) tma_load_rows(smem_u32(st + q.off_aux), &M->aux, t * R, bar);
+            }
+            const int* gcs = reinterpret_cast<const int*>(gring + slot * q.gcol_stride);
+            // extra windows (runs of far columns) in the first gather slots, then the gathers
+            if (lane < nw) tma_load_rows(smem_u32(st + q.off_gat + lane * q.wslots * q.slot), &M->win[buf], gcs[lane], bar);
+            const int gs0 = nw * q.wslots;
+            for (int gi = lane; gi < ngr; gi += 32) {
+                const int4 c4 = *reinterpret_cast<const int4*>(gcs + TMA_MAX_WIN + 4 * gi);
+                tma_gather4(smem_u32(st + q.off_gat + (gs0 + gi) * q.slot), &M->gat[buf], c4.x, c4.y, c4.z, c4.w, bar);
+            }
+            __syncwarp();
+        }
+        bool marked = false;
+        if (dead) {
+            // hand the consumers an end marker once the stage is free (bounded), so that they stop
+            // after the items already issued
+            const int s = k % NST;
+            bool ok = true;
+            if (lane == 0 && k >= NST) ok = mbar_wait_bounded(smem_u32(&freeb[s]), (uint32_t)(((k / NST) & 1) ^ 1), budget);
+            marked = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (marked && lane == 0) {
+                sitem[s].j = -1;
+                mbar_arrive(smem_u32(&full[s]));
+            }
+        }
+        // wait (bounded) for the copies still in flight so that none lands in shared memory after
+        // the CTA exits: after a failure, the stages the consumers may not have waited for (the
+        // last nst issued items; with an end marker in place, the stage it took was freed, so its
+        // previous item is complete); always, the gather-column lists taken ahead and not issued
+        if (lane == 0) {
+            const long long drain = budget > TMA_DRAIN_MIN ? budget : TMA_DRAIN_MIN;
+            if (dead)
+                for (int kk = (k > NST ? k - NST : 0) + (marked && k >= NST ? 1 : 0); kk < k; ++kk)
+                    mbar_wait_bounded(smem_u32(&full[kk % NST]), (uint32_t)((kk / NST) & 1), drain);
+            for (int pos = k; pos < taken; ++pos)
+                mbar_wait_bounded(smem_u32(&gbar[pos & (BT_IRING - 1)]), (uint32_t)((pos / BT_IRING) & 1), drain);
+        }
+    } else if (warp == cwarps + 1) {
+        // ------------------------------------------------------------------ signal warp (lane 0)
+        if (lane == 0) {
+            for (int k = 0;; ++k) {
+                const int s = k % NST;
+                const uint32_t par = (uint32_t)((k / NST) & 1);
+                // the item is published (full), then its consumers are done with it (empty)
+                bool ok = mbar_wait_bounded(smem_u32(&full[s]), par, budget);
+                const int j = sitem[s].j, i = sitem[s].i;
+                if (ok && j < 0) break;
+                if (ok) ok = mbar_wait_bounded(smem_u32(&empty[s]), par, budget);
+                if (!ok) {
+                    atomicExch(bp.error, 1);
+                    break;
+                }
+                // the consumers' stores of W_{j+1}, P and the partials happen before this add
+                red_release_add(&bp.arrived[i], 1ull);
+                mbar_arrive(smem_u32(&freeb[s]));
+            }
+        }
+    } else {
+        // ------------------------------------------------------------------ consumer warps
+        const int b = bp.b;
+        const int tp = (b + 1) / 2;
+        const int rlane = tid / tp;
+        const int cp = tid - rlane * tp;
+        const bool active = rlane < R;
+        const long long ldq = bp.ldw >> 1;
+        const long long ldpq = bp.ldp >> 1;
+        const unsigned cpoff = (unsigned)(cp * sizeof(WP));
+        const unsigned own_off = (unsigned)(rlane + TMA_HALO) * (unsigned)q.rowbytes + cpoff;
+        const unsigned aux_off = (unsigned)q.off_aux + (unsigned)rlane * (unsigned)q.auxbytes +
+                                 (unsigned)(cp * (MODE == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
+        double* red = reinterpret_cast<double*>(smem + off_red);
+        for (int k = 0;; ++k) {
+            const int s = k % NST;
+            const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((k / NST) & 1), budget);
+            if (consumer_any(cthreads, !ok)) {
+                if (tid == 0) atomicExch(bp.error, 1);
+                break;
+            }
+            const int j = sitem[s].j;
+            if (j < 0) break;
+            const int t = sitem[s].t, n = sitem[s].n, T = sitem[s].T;
+            const int r = t * R + rlane;
+            const unsigned char* st = smem + s * q.stage_bytes;
+            StepParams p{};
+            p.first = (j == 0);
+            p.beta = sitem[s].beta;
+            p.d0 = sitem[s].d0;
+            p.dn = sitem[s].dn;
+            p.beta_df = sitem[s].beta_df;
+            p.d0_df = sitem[s].d0_df;
+            p.dn_df = sitem[s].dn_df;
+            const StepScalars<PREC> S(p, cp);
+            TracePart TP;
+            if (active && r < n) {
+                const WP* __restrict__ win = static_cast<const WP*>(sitem[s].win);
+                WP* wout = static_cast<WP*>(sitem[s].wout);
+                PP* pblk = static_cast<PP*>(sitem[s].aux);
+                const int* srp = reinterpret_cast<const int*>(st + q.off_desc);
+                const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_desc + q.hdr_bytes);
+                const int k0 = srp[rlane], k1 = srp[rlane + 1];
+                const int g = srp[R + 2];
+                const WP wr = *reinterpret_cast<const WP*>(st + own_off);
+                WP vr{};
+                PP po{};
+                if constexpr (MODE == MODE_DOT) vr = *reinterpret_cast<const WP*>(st + aux_off);
+                if constexpr (MODE == MODE_ACCUM) {
+                    if (j > 0) po = *reinterpret_cast<const PP*>(st + aux_off);
+                }
+                RowAcc A;
+                const int kend = min(k1, g);
+                const unsigned char* stc = st + cpoff;
+#pragma unroll 4
+                for (int kk = k0; kk < kend; ++kk) {
+                    const RecT rk = rec[kk];
+                    row_mac<PREC>(A, expand(rk.a), *reinterpret_cast<const WP*>(stc + rk.off));
+                }
+                if (k1 > g) {   // beyond the records: direct loads through L2 (W_j was written during the launch)
+                    const int z0 = srp[R + 1];
+                    const int32_t* colind = sitem[s].colind;
+                    const Raw* vals = static_cast<const Raw*>(sitem[s].vals);
+                    for (int kk = max(k0, g); kk < k1; ++kk) {
+                        WP x;
+                        const WP* src = win + (size_t)colind[z0 + kk] * ldq + cp;
+                        if constexpr (sizeof(WP) == 16) x = __ldcg(src);
+                        else x = __ldcg(reinterpret_cast<const unsigned long long*>(src));
+                        row_mac<PREC>(A, expand(vals[z0 + kk]), x);
+                    }
+                }
+                row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wout + (size_t)r * ldq + cp, pblk + (size_t)r * ldpq + cp, TP);
+            }
+            if constexpr (MODE == MODE_DOT) {
+                // The tile's trace partial of every column (slot j + 1: the step's W_{j+1} traces;
+                // slot 0: the W_0 traces). Row lanes are summed in a fixed order: group g of G
+                // sums rows g, g + G, ..., then the G groups of a column pair (G consecutive
+                // lanes) combine by a shuffle tree. Double-float arithmetic on the FP32 pipes in
+                // the DF64 and FP32 modes (the partials are stored as (hi, lo) float pairs).
+                const int nred = j == 0 ? 2 : 1;
+                int G = 8;
+                while (G > 1 && G * tp > cthreads) G >>= 1;
+                const int x = tid, cpx = x / G, g = x - cpx * G;
+                for (int qq = 0; qq < nred; ++qq) {
+                    const int slot = qq ? 0 : j + 1;
+                    if constexpr (PREC == LL_PREC_F64) {
+                        double* rd = red;
+                        rd[2 * tid] = qq ? TP.t0d[0] : TP.td[0];
+                        rd[2 * tid + 1] = qq ? TP.t0d[1] : TP.td[1];
+                        consumer_sync(cthreads);
+                        double a0 = 0.0, a1 = 0.0;
+                        if (cpx < tp)
+                            for (int l = g; l < R; l += G) {
+                                a0 += rd[2 * (l * tp + cpx)];
+                                a1 += rd[2 * (l * tp + cpx) + 1];
+                            }
+                        for (int off = G >> 1; off > 0; off >>= 1) {
+                            a0 += __shfl_down_sync(0xffffffffu, a0, off);
+                            a1 += __shfl_down_sync(0xffffffffu, a1, off);
+                        }
+                        double* part = static_cast<double*>(sitem[s].aux) + ((size_t)slot * T + t) * b;
+                        if (cpx < tp && g == 0) {
+                            part[2 * cpx] = a0;
+                            if (2 * cpx + 1 < b) part[2 * cpx + 1] = a1;
+                        }
+                    } else {
+                        ulonglong2* rd = reinterpret_cast<ulonglong2*>(red);
+                        rd[tid] = qq ? make_ulonglong2(TP.t0h2, TP.t0l2) : make_ulonglong2(TP.th2, TP.tl2);
+                        consumer_sync(cthreads);
+                        f2x ah = 0ull, al = 0ull;
+                        if (cpx < tp)
+                            for (int l = g; l < R; l += G) {
+                                const ulonglong2 v = rd[l * tp + cpx];
+                                df2_add(ah, al, v.x, v.y);
+                            }
+                        for (int off = G >> 1; off > 0; off >>= 1) {
+                            const f2x oh = shfl_down_f2(ah, off), ol = shfl_down_f2(al, off);
+                            df2_add(ah, al, oh, ol);
+                        }
+                        float2* part = reinterpret_cast<float2*>(sitem[s].aux) + ((size_t)slot * T + t) * b;
+                        if (cpx < tp && g == 0) {
+                            float h0, h1, l0, l1;
+                            f2_unpack(ah, h0, h1);
+                            f2_unpack(al, l0, l1);
+                            part[2 * cpx] = make_float2(h0, l0);
+                            if (2 * cpx + 1 < b) part[2 * cpx + 1] = make_float2(h1, l1);
+                        }
+                    }
+                    consumer_sync(cthreads);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+        }
+    }
+    __syncthreads();
+}
+
+// dots[j][c] = sum_t partials[j][t][c] (tiles in order, in FP64) of every matrix (blockIdx.y), step
+// slot and column; one thread per (slot, column). DF: the partials are double-float pairs.
+template <bool DF>
+__global__ void k_batched_dots(const BatchTmaMat* mats, int b) {
+    const BatchTmaMat& M = mats[blockIdx.y];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (M.m + 1) * b) return;
+    const int slot = idx / b, c = idx - slot * b;
+    const size_t base = (size_t)slot * M.T * b + c;
+    double s = 0.0;
+    if constexpr (DF) {
+        const float2* part = reinterpret_cast<const float2*>(M.partials) + base;
+        for (int t = 0; t < M.T; ++t) {
+            const float2 v = part[(size_t)t * b];
+            s += (double)v.x + (double)v.y;
+        }
+    } else {
+        const double* part = M.partials + base;
+        for (int t = 0; t < M.T; ++t) s += part[(size_t)t * b];
+    }
+    M.dots[(size_t)slot * b + c] = s;
+}
+
+namespace {
+
+template <int PREC, int MODE>
+cudaError_t launch_bt_typed(const BatchTmaParams& bp, const BatchTmaLaunch& L, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_leja_tma_batched<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    k_leja_tma_batched<PREC, MODE><<<L.grid, L.threads, L.smem, s>>>(bp, (int)L.off_red, (int)L.off_tab);
+    return cudaGetLastError();
+}
+
+template <int PREC, int MODE>
+int occupancy_bt(int threads, size_t smem) {
+    if (cudaFuncSetAttribute(k_leja_tma_batched<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leja_tma_batched<PREC, MODE>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
+}  // namespace
+
+bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double avg_far, int b, long long ldw,
+                      long long ldp, int max_m, int count, int sm_count, BatchTmaLaunch& L) {
+    L = BatchTmaLaunch{};
+    if (n_min <= 0 || b <= 0 || max_m < 1 || count < 1 || !encode_fn()) return false;
+    if (mode != MODE_ACCUM && mode != MODE_DOT) return false;
+    const int ew = (int)elem_size(w_type_of(precision));
+    if (ldw > 256 || (ldw * ew) % 16 != 0) return false;
+    TmaParams& q = L.q;
+    q.rowbytes = (int)(ldw * ew);
+    if (mode == MODE_ACCUM) {
+        if (ldp > 256 || (ldp * 8) % 16 != 0) return false;
+        q.auxbytes = (int)(ldp * 8);
+    } else {
+        q.auxbytes = q.rowbytes;
+    }
+    q.slot = (int)a128((size_t)4 * q.rowbytes);
+    q.recbytes = (int)rec_size(precision);
+    const int tp = (b + 1) / 2;
+    int R = 512 / tp;
+    if (R > 256 - 2 * TMA_HALO) R = 256 - 2 * TMA_HALO;   // window box rows <= 256
+    if (R + 2 * TMA_HALO > n_min) R = n_min - 2 * TMA_HALO;  // a box no taller than the smallest matrix
+    if (R < 1) return false;
+    const double avgfar = avg_far >= 0.0 && avg_far <= avg_nnz ? avg_far : avg_nnz;
+    const size_t tab_bytes = a16((size_t)bt_table_ints(max_m, count) * 4);
+    const size_t budget = 220 * 1024;   // dynamic shared memory (the static part holds the barriers and items)
+    auto fit = [&](int Rt) {
+        tma_stage_layout(q, Rt, avg_nnz, avgfar, 1.25);
+        const size_t ct = (size_t)((Rt * tp + 31) / 32) * 32;
+        const size_t extra = a128((size_t)BT_IRING * q.gcol_stride) + (mode == MODE_DOT ? ct * 16 : 0) + tab_bytes + 128;
+        const int nst = budget > extra ? (int)((budget - extra) / q.stage_bytes) : 0;
+        q.nst = nst > TMA_MAX_STAGES ? TMA_MAX_STAGES : nst;
+        return q.nst;
+    };
+    // the most rows per tile that keep three stages (two at the least)
+    int Rbest = 0;
+    for (int Rt = R; Rt >= 1; Rt = Rt > 4 ? Rt * 3 / 4 : Rt - 1) {
+        const int nst = fit(Rt);
+        if (nst >= 3) { Rbest = Rt; break; }
+        if (nst >= 2 && Rbest == 0) Rbest = Rt;
+    }
+    if (Rbest == 0) return false;
+    fit(Rbest);
+    if (q.nst < 2) return false;
+    q.nprod = 1;
+    q.ring_base = q.nst * q.stage_bytes;
+    const int cthreads = ((Rbest * tp + 31) / 32) * 32;
+    L.threads = cthreads + 64;
+    L.off_red = a128((size_t)q.ring_base + (size_t)BT_IRING * q.gcol_stride);
+    L.off_tab = L.off_red + (mode == MODE_DOT ? (size_t)cthreads * 16 : 0);
+    L.smem = L.off_tab + tab_bytes + 128;
+    if (L.threads > TMA_MAX_THREADS) return false;
+    int per_sm = 0;
+    switch (precision * NUM_MODES + mode) {
+        case LL_PREC_F64 * NUM_MODES + MODE_ACCUM: per_sm = occupancy_bt<LL_PREC_F64, MODE_ACCUM>(L.threads, L.smem); break;
+        case LL_PREC_F64 * NUM_MODES + MODE_DOT: per_sm = occupancy_bt<LL_PREC_F64, MODE_DOT>(L.threads, L.smem); break;
+        case LL_PREC_DF64 * NUM_MODES + MODE_ACCUM: per_sm = occupancy_bt<LL_PREC_DF64, MODE_ACCUM>(L.threads, L.smem); break;
+        case LL_PREC_DF64 * NUM_MODES + MODE_DOT: per_sm = occupancy_bt<LL_PREC_DF64, MODE_DOT>(L.threads, L.smem); break;
+        case LL_PREC_F32_MIXED * NUM_MODES + MODE_ACCUM: per_sm = occupancy_bt<LL_PREC_F32_MIXED, MODE_ACCUM>(L.threads, L.smem); break;
+        case LL_PREC_F32_MIXED * NUM_MODES + MODE_DOT: per_sm = occupancy_bt<LL_PREC_F32_MIXED, MODE_DOT>(L.threads, L.smem); break;
+        default: break;
+    }
+    if (per_sm < 1) return false;
+    L.grid = sm_count;
+    return true;
+}
+
+cudaError_t launch_batched_tma(int precision, int mode, const BatchTmaParams& bp, const BatchTmaLaunch& L, cudaStream_t s) {
+    switch (precision * NUM_MODES + mode) {
+        case LL_PREC_F64 * NUM_MODES + MODE_ACCUM: return launch_bt_typed<LL_PREC_F64, MODE_ACCUM>(bp, L, s);
+        case LL_PREC_F64 * NUM_MODES + MODE_DOT: return launch_bt_typed<LL_PREC_F64, MODE_DOT>(bp, L, s);
+        case LL_PREC_DF64 * NUM_MODES + MODE_ACCUM: return launch_bt_typed<LL_PREC_DF64, MODE_ACCUM>(bp, L, s);
+        case LL_PREC_DF64 * NUM_MODES + MODE_DOT: return launch_bt_typed<LL_PREC_DF64, MODE_DOT>(bp, L, s);
+        case LL_PREC_F32_MIXED * NUM_MODES + MODE_ACCUM: return launch_bt_typed<LL_PREC_F32_MIXED, MODE_ACCUM>(bp, L, s);
+        case LL_PREC_F32_MIXED * NUM_MODES + MODE_DOT: return launch_bt_typed<LL_PREC_F32_MIXED, MODE_DOT>(bp, L, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batched_dots(int precision, const BatchTmaMat* mats, int count, int b, int max_span, cudaStream_t s) {
+    if (max_span <= 0 || count <= 0) return cudaSuccess;
+    const int threads = 128;
+    const dim3 grid((unsigned)((max_span + threads - 1) / threads), (unsigned)count);
+    if (precision == LL_PREC_F64) k_batched_dots<false><<<grid, threads, 0, s>>>(mats, b);
+    else k_batched_dots<true><<<grid, threads, 0, s>>>(mats, b);
+    return cudaGetLastError();
+}
+
+}  // namespace ll

@@ -172,6 +172,8 @@ struct BatchMat {
     int n, T, m;
 };
 
+constexpr int BATCH_THREADS = 256;   // CTA size of the register-gather persistent kernel
+
 struct BatchParams {
     const BatchMat* mats;          // sorted by degree, descending
     const int* step_off;           // first item of each step (max_m + 1 entries)
@@ -194,21 +196,22 @@ struct TmaParams {
     int nst;           // pipeline stages (tiles in flight + 1)
     int nprod;         // producer warps (divides nst)
     int slot;          // bytes of one gather4 slot (4 rows, 128-byte aligned)
+    int wslots;        // gather slots taken by one extra window (R + 2 HALO rows)
     int rowbytes;      // bytes of one W row (ld * element size)
     int auxbytes;      // bytes of one V (pass 2, adjoint) or P (pass 1) row; 0 without
     int recbytes;      // bytes of one entry record (prepared value, operand offset)
     int hdr_bytes;     // descriptor header: R + 1 row offsets, z0, record count (16-byte padded)
     int desc_stride;   // bytes per tile of the descriptor array (header and ecap records)
-    int gcol_stride;   // bytes per tile of the gather-column array (fcap ints)
+    int gcol_stride;   // bytes per tile of the gather-column array (4 window rows, then fcap columns)
     int stage_bytes;   // bytes per stage: window, aux rows, gathered rows, descriptor
     int off_aux, off_gat, off_desc;   // the window is at offset 0
     int ring_base;     // gather-column rings of the producer warps, after the stages
     const unsigned char* desc;   // per-tile descriptors (built once per pass)
     const int* gcol;             // per-tile gather columns
-    const int2* meta;            // per tile: (records, gathered rows)
+    const int4* meta;            // per tile: (records, gathered rows, extra windows, 0)
     unsigned char* desc_w;       // the same arrays, writable (for the describe kernel)
     int* gcol_w;
-    int2* meta_w;
+    int4* meta_w;
     int* error;                                  // set to 1 when a bounded wait runs out
     long long spin_budget;                       // clock64 cycles a wait may spin
     int inject;                                  // test hook: tile 0 expects bytes no copy delivers

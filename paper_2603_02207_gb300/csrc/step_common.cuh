@@ -64,7 +64,7 @@ struct StepScalars {
         bh2 = f2_pack(p.beta_df.x, p.beta_df.x);
         bl2 = f2_pack(p.beta_df.y, p.beta_df.y);
         nbh2 = f2_pack(-p.beta_df.x, -p.beta_df.x);
-        beta2 = f2_pack((float)p.beta, (float)p.beta);
+        beta2 = f2_pack(p.beta_df.x, p.beta_df.x);   // the leading float of beta_j: (float)beta_j
         dnh2 = f2_pack(p.dn_df.x, p.dn_df.x);
         dnl2 = f2_pack(p.dn_df.y, p.dn_df.y);
         ndnh2 = f2_pack(-p.dn_df.x, -p.dn_df.x);
@@ -78,7 +78,7 @@ struct StepScalars {
         ch2 = f2_pack(cdf0.x, cdf1.x);
         cl2 = f2_pack(cdf0.y, cdf1.y);
         nch2 = f2_pack(-cdf0.x, -cdf1.x);
-        cf2 = f2_pack((float)cadj0, (float)cadj1);
+        cf2 = f2_pack(cdf0.x, cdf1.x);
     }
 };
 

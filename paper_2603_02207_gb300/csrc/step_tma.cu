@@ -3,168 +3,28 @@
 // Same step as k_leja_step (W_{j+1} = (B - xi_j I) W_j on every column, fused with the P-axpy of
 // pass 1, the traces of pass 2 or the adjoint's U term; the per-row arithmetic is shared), but the
 // operand rows reach shared memory through the tensor memory accelerator instead of registers:
-//   * the neighbour rows W_j[c_k, :] of a tile's entries by tile::gather4 (four rows of the
-//     row-major block per instruction, rows given by the column indices),
-//   * the tile's own rows W_j[r, :] and its V (pass 2, adjoint) or P (pass 1) rows by 2-D tile
-//     loads,
+//   * a window of the tile's rows +-2 by a 2-D tile load (the diagonal and the near columns),
+//   * runs of far columns (a stencil's off-diagonal bands) by further windows of the same size,
+//   * the remaining (far) neighbour rows W_j[c_k, :] by tile::gather4 (four rows per instruction,
+//     rows given by the column indices),
+//   * the tile's V (pass 2, adjoint) or P (pass 1) rows by a 2-D tile load,
+//   * the tile's descriptor (row offsets and one record per entry: prepared value and the
+//     operand row's offset in the stage), built once per pass, by a 1-D bulk copy,
 // all completing on one mbarrier per pipeline stage. The CTA is warp-specialised and persistent
-// (tiles i, i + grid, ...): its last warp produces (stages each tile's CSR segment two tiles ahead
-// with cp.async, writes the tile's row offsets and expanded values into a free stage, and issues
-// the copies), the other warps consume (a thread owns one row of the tile and one column pair,
-// reads the gathered rows from shared memory and writes W_{j+1} (and P) straight to global memory,
-// then its warp releases the stage). Full and empty barriers per stage replace block-wide
-// barriers, so consumer warps drift up to the stage count apart. Entries of a tile beyond the
-// gather capacity (long rows) are read directly from global memory. Every wait on an mbarrier is
-// bounded (clock64 budget); when one runs out the kernel records the error, stops issuing copies,
-// waits (bounded) for the copies it issued and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include <mutex>
-
+// (tiles i, i + grid, ...): its last warps produce (stage each tile's gather columns two tiles
+// ahead and issue the copies of a free stage), the other warps consume (a thread owns one row of
+// the tile and one column pair, reads its operands from shared memory and writes W_{j+1} (and P)
+// straight to global memory, then its warp releases the stage). Full and empty barriers per
+// stage replace block-wide barriers. Entries past a tile's record or gather capacity (long rows)
+// are read directly from global memory. Every wait on an mbarrier is bounded (clock64 budget);
+// when one runs out the kernel records the error, stops issuing copies, waits (bounded) for the
+// copies it issued and returns.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "step_common.cuh"
+#include "tma_common.cuh"
 
 namespace ll {
-
-constexpr int TMA_MAX_STAGES = 6;
-constexpr int TMA_MAX_THREADS = 576;   // up to 512 consumer threads and two producer warps
-constexpr int TMA_MAX_PROD = 2;
-constexpr int TMA_GRING = 3;           // gather-column blocks staged up to two tiles ahead
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// waits for the phase of parity `parity` to complete; false when `budget` clock cycles pass first.
-// Budgets below 1e5 cycles poll with the non-blocking test_wait (try_wait may itself suspend the
-// thread for longer than such a budget).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget) {
-    const bool poll = budget < 100000;
-    if (poll ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!(poll ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)))
-        if (clock64() - t0 > budget) return false;
-    return true;
-}
-// least cycles the drain after a timeout waits for each tile's copies (copies of valid rows
-// complete in microseconds; this only bounds the wait)
-constexpr long long TMA_DRAIN_MIN = 10000000LL;
-__device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap* map, int row, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
-        "l"(map), "r"(0), "r"(row), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map, int r0, int r1, int r2, int r3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
-        "l"(map), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
-        : "memory");
-}
-// 1-D bulk copy global -> shared (both 16-byte aligned, size a multiple of 16) completing on bar
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-
-// Entry record of a tile's descriptor: the matrix value as prepared (FP64, float pair, FP32) and
-// the byte offset of its operand row W_j[c, :] in the stage (window or gather slot). One
-// broadcast shared-memory load per entry in the consumer loop.
-template <int PREC> struct Rec;
-template <> struct __align__(16) Rec<LL_PREC_F64> { double a; int off, pad; };
-template <> struct __align__(16) Rec<LL_PREC_DF64> { float2 a; int off, pad; };   // (hi, lo)
-template <> struct __align__(8) Rec<LL_PREC_F32_MIXED> { float a; int off; };
-
-// Tile descriptors, built once per pass (the matrix and the tile geometry do not change between
-// the m steps). One warp per tile of R rows:
-//   desc[t]: row offsets rowptr[r0 .. r0 + nr] - z0, then z0 and the record count g, padded to
-//            16 bytes; then one record per entry e < g. Columns inside the window
-//            [r0 - HALO, r0 + R + HALO) point into the window, the others into the next gather
-//            slot in entry order; when the fcap slots run out (or after ecap entries) the records
-//            stop, and that entry and every later entry of the tile load directly;
-//   gcol[t]: the gathered columns in slot order, padded with the last one to a multiple of 4;
-//   meta[t]: (g, gathered rows).
-template <int PREC>
-__global__ void k_tma_describe(const int32_t* rowptr, const int32_t* colind, const typename PairT<PREC>::Raw* vals, int n,
-                               int num_tiles, const TmaParams q, unsigned char* desc, int* gcol, int2* meta) {
-    using RecT = Rec<PREC>;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int R = q.R;
-    for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < num_tiles; t += (int)((gridDim.x * blockDim.x) >> 5)) {
-        const int r0 = t * R;
-        const int nr = min(R, n - r0);
-        const int z0 = rowptr[r0];
-        const int g = min(rowptr[r0 + nr] - z0, q.ecap);
-        int* hdr = reinterpret_cast<int*>(desc + (size_t)t * q.desc_stride);
-        RecT* rec = reinterpret_cast<RecT*>(desc + (size_t)t * q.desc_stride + q.hdr_bytes);
-        int* gc = gcol + (size_t)t * q.fcap;
-        for (int e = lane; e <= nr; e += 32) hdr[e] = rowptr[r0 + e] - z0;
-        const int wlo = r0 - TMA_HALO, whi = r0 + R + TMA_HALO;
-        int nfar = 0, gcut = g;
-        for (int e0 = 0; e0 < gcut; e0 += 32) {
-            const int e = e0 + lane;
-            const bool valid = e < gcut;
-            const int c = valid ? colind[z0 + e] : 0;
-            const bool near = c >= wlo && c < whi;
-            const unsigned farm = __ballot_sync(0xffffffffu, valid && !near);
-            const int fs = nfar + __popc(farm & lt_mask);
-            const unsigned over = __ballot_sync(0xffffffffu, valid && !near && fs >= q.fcap);
-            if (over) gcut = e0 + __ffs(over) - 1;   // first entry without a gather slot
-            if (valid && e < gcut) {
-                RecT rr;
-                rr.a = vals[z0 + e];
-                if (near) {
-                    rr.off = (c - wlo) * q.rowbytes;
-                } else {
-                    rr.off = q.off_gat + (fs >> 2) * q.slot + (fs & 3) * q.rowbytes;
-                    gc[fs] = c;
-                }
-                rec[e] = rr;
-            }
-            nfar += __popc(farm);
-        }
-        const int ng = min(nfar, q.fcap);
-        __syncwarp();
-        if (ng > 0) {
-            const int last = gc[ng - 1];
-            for (int e = ng + lane; e < ((ng + 3) & ~3); e += 32) gc[e] = last;
-        }
-        if (lane == 0) {
-            hdr[R + 1] = z0;
-            hdr[R + 2] = gcut;
-            meta[t] = make_int2(gcut, ng);
-        }
-    }
-}
 
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
@@ -178,7 +38,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     __shared__ __align__(8) unsigned long long full[TMA_MAX_STAGES];
     __shared__ __align__(8) unsigned long long empty[TMA_MAX_STAGES];
     __shared__ __align__(8) unsigned long long gbar[TMA_MAX_PROD * TMA_GRING];
-    __shared__ int2 gmeta[TMA_MAX_PROD * TMA_GRING];
+    __shared__ int4 gmeta[TMA_MAX_PROD * TMA_GRING];
     __shared__ bool s_last;
     // TMA destinations are 128-byte aligned: the plan reserves 128 bytes for this offset
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -218,12 +78,12 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
         auto tile_of = [&](int t) { return (int)blockIdx.x + (pw + t * nprod) * (int)gridDim.x; };
         unsigned char* ring = smem + q.ring_base + pw * TMA_GRING * q.gcol_stride;
         unsigned long long* gb = gbar + pw * TMA_GRING;
-        int2* gm = gmeta + pw * TMA_GRING;
-        // per-tile (records, gathered rows) of this producer's tiles, 32 per batch (lane l holds
-        // tile zb + l), the next batch loaded one batch ahead
-        auto meta_of = [&](int t) { return t < myp ? q.meta[tile_of(t)] : make_int2(0, 0); };
+        int4* gm = gmeta + pw * TMA_GRING;
+        // per-tile (records, gathered rows, extra windows) of this producer's tiles, 32 per batch
+        // (lane l holds tile zb + l), the next batch loaded one batch ahead
+        auto meta_of = [&](int t) { return t < myp ? q.meta[tile_of(t)] : make_int4(0, 0, 0, 0); };
         int zb = 0;
-        int2 mcur = meta_of(lane), mnext = meta_of(32 + lane);
+        int4 mcur = meta_of(lane), mnext = meta_of(32 + lane);
         int cslot = 0;   // ring slot of the next gather-column block to stage
         // stage the gather columns of this producer's tile t (t increasing by one per call)
         auto stage_gcol = [&](int t) {
@@ -234,13 +94,15 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
             }
             const int nrec = __shfl_sync(0xffffffffu, mcur.x, t - zb);
             const int ng = __shfl_sync(0xffffffffu, mcur.y, t - zb);
+            const int nw = __shfl_sync(0xffffffffu, mcur.z, t - zb);
             if (lane == 0) {
-                gm[cslot] = make_int2(nrec, ng);
+                gm[cslot] = make_int4(nrec, ng, nw, 0);
                 const uint32_t bar = smem_u32(&gb[cslot]);
-                const uint32_t bytes = (uint32_t)((ng + 3) & ~3) * 4u;
+                // the window start rows, then the gathered columns
+                const uint32_t bytes = (ng > 0 || nw > 0) ? (uint32_t)(TMA_MAX_WIN + ((ng + 3) & ~3)) * 4u : 0u;
                 if (bytes) {
                     mbar_arrive_expect_tx(bar, bytes);
-                    bulk_copy(smem_u32(ring + cslot * q.gcol_stride), q.gcol + (size_t)tile_of(t) * q.fcap, bytes, bar);
+                    bulk_copy(smem_u32(ring + cslot * q.gcol_stride), q.gcol + (size_t)tile_of(t) * (q.gcol_stride >> 2), bytes, bar);
                 } else {
                     mbar_arrive(bar);
                 }
@@ -266,8 +128,9 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 if (lane == 0) *((volatile int*)q.error) = 1;
                 break;
             }
-            const int2 mt = gm[gslot];
+            const int4 mt = gm[gslot];
             const int ngr = (mt.y + 3) >> 2;
+            const int nw = mt.z;
             unsigned char* st = smem + s * q.stage_bytes;
             const uint32_t bar = smem_u32(&full[s]);
             if (lane == 0) {
@@ -275,7 +138,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 const uint32_t dbytes = (uint32_t)q.hdr_bytes + (uint32_t)mt.x * (uint32_t)q.recbytes;
                 const uint32_t dbytes16 = (dbytes + 15u) & ~15u;
                 const uint32_t bytes = dbytes16 + (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
-                                       (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
+                                       (uint32_t)(1 + nw) * (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
                                        (has_aux ? (uint32_t)R * (uint32_t)q.auxbytes : 0u) +
                                        ((q.inject && i == 0) ? 16u : 0u);
                 mbar_arrive_expect_tx(bar, bytes);
@@ -285,9 +148,12 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 if (has_aux) tma_load_rows(smem_u32(st + q.off_aux), &tm_aux, r0, bar);
             }
             const int* gcs = reinterpret_cast<const int*>(ring + gslot * q.gcol_stride);
+            // extra windows (runs of far columns) in the first gather slots, then the gathers
+            if (lane < nw) tma_load_rows(smem_u32(st + q.off_gat + lane * q.wslots * q.slot), &tm_win, gcs[lane], bar);
+            const int gs0 = nw * q.wslots;
             for (int gi = lane; gi < ngr; gi += 32) {
-                const int4 c4 = *reinterpret_cast<const int4*>(gcs + 4 * gi);
-                tma_gather4(smem_u32(st + q.off_gat + gi * q.slot), &tm_gather, c4.x, c4.y, c4.z, c4.w, bar);
+                const int4 c4 = *reinterpret_cast<const int4*>(gcs + TMA_MAX_WIN + 4 * gi);
+                tma_gather4(smem_u32(st + q.off_gat + (gs0 + gi) * q.slot), &tm_gather, c4.x, c4.y, c4.z, c4.w, bar);
             }
             __syncwarp();   // the ring slot is read before the next copy into it
             ++issued;
@@ -399,41 +265,6 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
 
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult r{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &r) == cudaSuccess &&
-            r == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-        else
-            cudaGetLastError();
-    });
-    return fn;
-}
-
-// 2-D map over the rows of an n x ld block of `elem` bytes per element; a box is `box_rows` whole rows
-bool encode_rows(CUtensorMap* m, const void* base, int elem, long long ld, int n, int box_rows) {
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn || !base || ((uintptr_t)base & 15) != 0) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)elem};
-    const cuuint32_t box[2] = {(cuuint32_t)ld, (cuuint32_t)box_rows};
-    const cuuint32_t es[2] = {1, 1};
-    return fn(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dims,
-              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
-size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
-
-size_t rec_size(int precision) {
-    return precision == LL_PREC_F64 ? sizeof(Rec<LL_PREC_F64>) : (precision == LL_PREC_DF64 ? sizeof(Rec<LL_PREC_DF64>) : sizeof(Rec<LL_PREC_F32_MIXED>));
-}
-
 template <int PREC, int MODE>
 int occupancy_tma(int threads, size_t smem) {
     cudaFuncSetAttribute(k_leja_tma<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -497,20 +328,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     const int np_cap = TMA_MAX_PROD;
     // layout for R rows per tile; returns the stage count that fits
     auto layout = [&](int Rt) {
-        int ecap = (((int)(avg * Rt * slack) + 8) + 3) & ~3;
-        if (ecap > 4096) ecap = 4096;
-        int fcap = (((int)(avgfar * Rt * slack) + 8) + 3) & ~3;
-        if (fcap > ecap) fcap = ecap;
-        q.R = Rt;
-        q.ecap = ecap;
-        q.fcap = fcap;
-        q.hdr_bytes = (int)a16((size_t)(Rt + 3) * 4);
-        q.desc_stride = (int)a16((size_t)q.hdr_bytes + (size_t)ecap * q.recbytes);
-        q.gcol_stride = (int)a16((size_t)fcap * 4);
-        q.off_aux = (int)a128((size_t)(Rt + 2 * TMA_HALO) * q.rowbytes);
-        q.off_gat = q.off_aux + (int)a128((size_t)Rt * auxbytes);
-        q.off_desc = q.off_gat + (fcap / 4) * q.slot;
-        q.stage_bytes = (int)a128((size_t)q.off_desc + (size_t)q.desc_stride);
+        tma_stage_layout(q, Rt, avg, avgfar, slack);
         const size_t ring_total = (size_t)np_cap * TMA_GRING * q.gcol_stride;
         const int nst = budget > ring_total ? (int)((budget - ring_total) / q.stage_bytes) : 0;
         q.nst = nst > TMA_MAX_STAGES ? TMA_MAX_STAGES : nst;
@@ -542,7 +360,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     p.num_tiles = (n + R - 1) / R;
     L.desc_bytes = (size_t)p.num_tiles * q.desc_stride;
     L.gcol_bytes = (size_t)p.num_tiles * q.gcol_stride;
-    L.meta_bytes = (size_t)p.num_tiles * sizeof(int2);
+    L.meta_bytes = (size_t)p.num_tiles * sizeof(int4);
     int per_sm = 0;
     switch (precision * NUM_MODES + mode) {
 #define OCC(P_, M_) case P_ * NUM_MODES + M_: per_sm = occupancy_tma<P_, M_>(L.threads, L.smem); break;

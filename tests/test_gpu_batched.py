@@ -96,3 +96,52 @@ def test_batched_graph_replay(L, h):
     e4 = L.ll_logdet_batched(h, dm, b2, opts)
     e5 = L.ll_logdet_batched(h2, dm, b2, L.options(probes=9, seed=6, use_graph=False))
     assert np.array_equal(e4, e5) and not np.array_equal(e4, e1)
+
+
+@pytest.mark.parametrize("prec", ["df64", "f32", "f64"])
+def test_batched_tma_matches_register_kernel(L, prec):
+    """The TMA-fed persistent passes and the register-gather persistent passes run the same per-row
+    arithmetic: estimates agree to the rounding of the trace sums (tiles differ in size, so the
+    per-tile partials are summed in a different order). Many small matrices of uneven degree keep
+    several matrices and steps in flight in every CTA."""
+    params = gmrf_batch_params(count=24, seed=11, side_lo=12, side_hi=96)
+    mats = [laplacian_2d(side, tau) for side, tau in params]
+    bounds = [(tau, 8.0 + tau) for _, tau in params]
+    dm = [L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64") for A in mats]
+    res = {}
+    for kernel in ("gather", "tma"):
+        h = L.Handle()
+        est = L.ll_logdet_batched(h, dm, bounds, L.options(probes=30, seed=4, precision=prec, step_kernel=kernel))
+        res[kernel] = (est, h.info())
+    assert res["gather"][1]["kernel_pass1"] == L.LL_KERNEL_GATHER
+    assert res["tma"][1]["kernel_pass1"] == L.LL_KERNEL_TMA and res["tma"][1]["kernel_pass2"] == L.LL_KERNEL_TMA
+    np.testing.assert_allclose(res["tma"][0], res["gather"][0], rtol=1e-12 if prec != "f32" else 1e-9)
+    # auto picks the TMA passes when they fit
+    h = L.Handle()
+    est = L.ll_logdet_batched(h, dm, bounds, L.options(probes=30, seed=4, precision=prec))
+    assert h.info()["kernel_pass1"] == L.LL_KERNEL_TMA
+    assert np.array_equal(est, res["tma"][0])
+    for i in (0, 7, 23):
+        A, (lo, hi) = mats[i], bounds[i]
+        sigma = O.sigma_of(lo)
+        m = O.degree_from_bounds(lo / sigma, hi / sigma)
+        want = O.logdet_leja(A, lo, hi, m, 30, 4 + i, f32=(prec == "f32"))["estimate"]
+        assert abs(res["tma"][0][i] - want) / abs(want) < TOL[prec], (i, res["tma"][0][i], want)
+
+
+def test_batched_tma_stall_timeout_is_reported(L):
+    """The stall hook leaves the first tile of one CTA incomplete (16 expected bytes no copy
+    delivers): its consumers give up, the other CTAs stop at their next dependency on it, every
+    CTA drains its copies and returns, the call reports LL_ERR_TIMEOUT and the handle stays usable."""
+    mats, bounds = _batch(scale=4, count=5, seed=9)
+    dm = [L.DeviceCSR.from_host(A) for A in mats]
+    h = L.Handle()
+    h.debug_inject("stall")
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_logdet_batched(h, dm, bounds, L.options(probes=30, seed=1, timeout_cycles=1_000_000, use_graph=False,
+                                                     step_kernel="tma"))
+    assert ei.value.name == "LL_ERR_TIMEOUT"
+    h.debug_inject("none")
+    a = L.ll_logdet_batched(h, dm, bounds, L.options(probes=30, seed=1, step_kernel="tma"))
+    b = L.ll_logdet_batched(L.Handle(), dm, bounds, L.options(probes=30, seed=1, step_kernel="gather"))
+    np.testing.assert_allclose(a, b, rtol=1e-12)
