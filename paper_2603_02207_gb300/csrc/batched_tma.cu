@@ -2,28 +2,33 @@
 // Eq. 4), in one persistent launch per pass, over the tile pipeline of the single-matrix TMA step.
 //
 // Work items are (step j, matrix i, row tile t), numbered step-major over the matrices still
-// active at step j (sorted by degree, descending, so they are a prefix). A CTA has three roles:
-//  * the producer warp takes item numbers from a global ticket, eight at a time; eight lanes decode
-//    them in parallel from tables held in shared memory and load each item's step scalars,
-//    pointers and tile record count, and start the copy of its gather-column list. Up to sixteen
-//    items are taken ahead of the one being issued. To issue an item, the producer waits (bounded)
-//    until every tile of step j - 1 of matrix i has finished, then for a free stage, and issues
-//    the item's copies: descriptor, operand window, V/P rows and the gathered rows of W_j of
-//    matrix i, through that matrix's own tensor maps;
+// active at step j (sorted by degree, descending, so they are a prefix). A CTA has these roles:
+//  * the producer warp takes item numbers from a global ticket, eight at a time, one batch ahead:
+//    eight lanes decode a batch from tables held in shared memory and start the loads of each
+//    item's step scalars, pointers, tile counts and arrival counter; one batch later the batch is
+//    written into a ring of taken items and the copies of its gather-column lists start. To issue
+//    an item, the producer makes sure every tile of step j - 1 of matrix i has finished (known
+//    when the item was taken, else a bounded wait), waits for a free stage, and issues the item's
+//    copies: descriptor, operand windows, V/P rows and the gathered rows of W_j of matrix i,
+//    through that matrix's own tensor maps;
 //  * the consumer warps compute the item's rows with the per-row arithmetic of the single-matrix
-//    kernels, store W_{j+1} (and P), and in pass 2 the tile's per-column trace partials (kept per
-//    step and reduced per matrix after the pass, in a fixed order);
-//  * the signal warp waits for each stage's consumers, publishes the tile's completion (a release
-//    add to the matrix's arrival counter, so the stores of W_{j+1} and P are visible before it),
-//    and only then frees the stage for the producer. The fence latency of the release stays off
-//    the consumers and the producer.
-// Every dependency of an item has a smaller ticket; consumers wait only on copies and the signal
-// warp only on consumers, so the smallest unfinished item can always proceed and the launch cannot
-// deadlock whatever the residency. W_j and P of step j - 1 were written by other CTAs with generic
-// stores; after the acquire of the arrival counter a proxy fence orders them before this CTA's TMA
-// reads. Every wait is bounded (clock64); when one runs out the CTA records the error, hands the
-// consumers an end marker, waits (bounded) for its copies in flight and returns, and the host
-// reports LL_ERR_TIMEOUT.
+//    kernels and store W_{j+1} (and P); in pass 2 they hand their trace terms to the reducing warp;
+//  * the freeing warp waits for each stage's consumers, frees the stage for the producer and
+//    queues the finished tile's matrix;
+//  * the releasing warp publishes the queued tiles' completion: one release fence for all the
+//    tiles queued so far (so the stores of W_{j+1} and P are visible before it), then one add per
+//    run of tiles of the same matrix to its arrival counter. The fence latency stays off the
+//    consumers, the producer and the stage recycling;
+//  * pass 2: the reducing warp sums each tile's trace terms over its rows, per column, in a fixed
+//    order; the per-tile partials of every step are reduced per matrix after the pass.
+// Every dependency of an item has a smaller ticket; consumers wait only on copies (and trace
+// buffers), the freeing warp only on consumers (and queue room), the releasing and reducing warps
+// only on what the others hand them, so the smallest unfinished item can always proceed and the
+// launch cannot deadlock whatever the residency. W_j and P of step j - 1 were written by other
+// CTAs with generic stores; after the acquire of the arrival counter a proxy fence orders them
+// before this CTA's TMA reads. Every wait is bounded (clock64); when one runs out the CTA records
+// the error, hands the consumers an end marker, waits (bounded) for its copies in flight and
+// returns, and the host reports LL_ERR_TIMEOUT.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "step_common.cuh"
@@ -34,18 +39,32 @@ namespace ll {
 namespace {
 
 constexpr int BT_CONSUMER_BAR = 1;   // named barrier of the consumer warps
+constexpr int BT_SIGQ = 64;          // finished tiles queued from the freeing warp to the releasing warp
+constexpr int BT_RACC = 4;           // independent accumulators per lane of the reducing warp
 static_assert((BT_IRING & (BT_IRING - 1)) == 0 && BT_IRING % BT_TAKE == 0 && BT_TAKE <= 32, "take-ahead ring");
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void red_relaxed_add(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ void consumer_sync(int cthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(BT_CONSUMER_BAR), "r"(cthreads) : "memory");
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ unsigned int ld_acquire_cta(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
 // consumer-wide OR of a predicate (a named-barrier reduction)
 __device__ __forceinline__ bool consumer_any(int cthreads, bool pred) {
@@ -100,7 +119,7 @@ __device__ __forceinline__ f2x shfl_down_f2(f2x v, int off) {
 }  // namespace
 
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const BatchTmaParams bp, const int off_red, const int off_tab) {
+__global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const BatchTmaParams bp, const int off_red, const int off_tab) {
     using WP = typename PairT<PREC>::W;
     using PP = typename PairT<PREC>::P;
     using Raw = typename PairT<PREC>::Raw;
@@ -110,8 +129,13 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
     __shared__ __align__(8) unsigned long long empty[TMA_MAX_STAGES];
     __shared__ __align__(8) unsigned long long freeb[TMA_MAX_STAGES];
     __shared__ __align__(8) unsigned long long gbar[BT_IRING];
+    __shared__ __align__(8) unsigned long long rfull[BT_NRB];    // pass 2: trace terms written (every consumer warp)
+    __shared__ __align__(8) unsigned long long rempty[BT_NRB];   // pass 2: trace terms reduced
     __shared__ __align__(16) BItem ring[BT_IRING];
     __shared__ __align__(16) BItem sitem[TMA_MAX_STAGES];
+    __shared__ int sigq[BT_SIGQ];            // matrices of freed tiles, in item order
+    __shared__ unsigned int q_head, q_tail;  // tiles queued (freeing warp) and published (releasing warp)
+    __shared__ void* rpart[BT_NRB];          // pass 2: where the reduced terms go (null: no more)
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
 
     const TmaParams& q = bp.q;
@@ -119,7 +143,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
     const int warp = tid >> 5, lane = tid & 31;
     const int NST = q.nst;
     const int R = q.R;
-    const int cthreads = (int)blockDim.x - 64;   // consumer threads; then the producer and the signal warp
+    // consumer threads; then the producer, freeing and releasing warps (and in pass 2 the reducing warp)
+    const int cthreads = (int)blockDim.x - (MODE == MODE_DOT ? 128 : 96);
     const int cwarps = cthreads >> 5;
     const long long budget = bp.spin_budget;
     int* tab = reinterpret_cast<int*>(smem + off_tab);
@@ -132,6 +157,12 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
             mbar_init(smem_u32(&freeb[s]), 1);
         }
         for (int s = 0; s < BT_IRING; ++s) mbar_init(smem_u32(&gbar[s]), 1);
+        for (int x = 0; x < BT_NRB; ++x) {
+            mbar_init(smem_u32(&rfull[x]), cwarps);
+            mbar_init(smem_u32(&rempty[x]), 1);
+        }
+        q_head = 0u;
+        q_tail = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -146,77 +177,143 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
         int taken = 0, k = 0;
         bool ended = false, dead = false;
         int ci = -1, cj = 0;   // lane 0: the matrix whose finished steps were last read, and their count
-        // take BT_TAKE tickets; lane l < BT_TAKE decodes ticket g0 + l into ring position taken + l
-        auto take = [&]() {
+        // Items are taken in batches of BT_TAKE tickets, in two phases one batch apart so that the
+        // issue path waits for no global load: fetch() decodes a batch (lane l < BT_TAKE: ticket
+        // g + l) and starts the loads of its step scalars, pointers, tile counts and arrival
+        // counter into registers (and the ticket increment of the batch after it); put() writes
+        // the fetched batch into the ring, starts the copies of its gather-column lists and, with
+        // one acquire fence for the batch, turns the arrival counts it read into dependencies
+        // known to be met.
+        unsigned int g_next = 0;   // lane 0: first ticket of the batch after the fetched one
+        int err_seen = 0;          // lane 0: the error flag as last read
+        int fj = -1, fi = 0, ft = 0, fgt = 0, fn = 0, fT = 0;
+        int4 fmt = make_int4(0, 0, 0, 0);
+        double fbeta = 0.0, fd0 = 0.0, fdn = 0.0;
+        float2 fbd = make_float2(0.f, 0.f), fd0d = fbd, fdnd = fbd;
+        const void* fwin = nullptr;
+        void* fwout = nullptr;
+        void* faux = nullptr;
+        const int32_t* fcol = nullptr;
+        const void* fvals = nullptr;
+        unsigned long long farr = 0;
+        auto fetch = [&]() {
             unsigned int g0 = 0;
-            if (lane == 0)
-                g0 = (ended || *((volatile int*)bp.error)) ? (unsigned int)bp.total_items : atomicAdd(bp.ticket, (unsigned int)BT_TAKE);
+            if (lane == 0) {
+                const bool stop = ended || err_seen;
+                g0 = stop ? (unsigned int)bp.total_items : g_next;
+                if (!stop) g_next = atomicAdd(bp.ticket, (unsigned int)BT_TAKE);
+                err_seen = *((volatile int*)bp.error);
+            }
             g0 = __shfl_sync(0xffffffffu, g0, 0);
-            bool none = false;
             if (lane < BT_TAKE) {
-                const int slot = (taken + lane) & (BT_IRING - 1);
                 const unsigned int g = g0 + (unsigned int)lane;
                 const int3 d = bt_decode(t_off, t_act, t_pre, bp.max_m, bp.total_items,
                                          g >= (unsigned int)bp.total_items ? bp.total_items : (int)g);
-                BItem& it = ring[slot];   // filled in place
-                it.j = d.x;
-                it.i = d.y;
-                it.t = d.z;
-                const uint32_t bar = smem_u32(&gbar[slot]);
+                fj = d.x;
+                fi = d.y;
+                ft = d.z;
                 if (d.x >= 0) {
                     const BatchTmaMat* M = bp.mats + d.y;
-                    const int gt = t_pre[d.y] + d.z;
-                    const int4 mt = bp.meta[gt];
+                    fgt = t_pre[d.y] + d.z;
+                    fmt = bp.meta[fgt];
                     const double* cf = bp.coef + t_coef[d.y];
-                    it.beta = cf[2 * d.x];
-                    it.d0 = cf[1];
-                    it.dn = cf[2 * (d.x + 1) + 1];
                     const float2* cfd = bp.coef_df + t_coef[d.y];
-                    it.beta_df = cfd[2 * d.x];
-                    it.d0_df = cfd[1];
-                    it.dn_df = cfd[2 * (d.x + 1) + 1];
+                    fbeta = cf[2 * d.x];
+                    fd0 = cf[1];
+                    fdn = cf[2 * (d.x + 1) + 1];
+                    fbd = cfd[2 * d.x];
+                    fd0d = cfd[1];
+                    fdnd = cfd[2 * (d.x + 1) + 1];
                     const int buf = d.x == 0 ? 0 : ((d.x & 1) ? 1 : 2);
+                    fwin = M->w[buf];
+                    fwout = M->w[(d.x & 1) ? 2 : 1];
+                    faux = MODE == MODE_ACCUM ? M->p : static_cast<void*>(M->partials);
+                    fcol = M->colind;
+                    fvals = M->vals;
+                    fn = M->n;
+                    fT = M->T;
+                    if (d.x > 0) farr = ld_relaxed_u64(&bp.arrived[d.y]);
                     prefetch_map(&M->win[buf]);
                     prefetch_map(&M->gat[buf]);
                     if (MODE == MODE_DOT || d.x > 0) prefetch_map(&M->aux);
-                    it.win = M->w[d.x == 0 ? 0 : ((d.x & 1) ? 1 : 2)];
-                    it.wout = M->w[(d.x & 1) ? 2 : 1];
-                    it.aux = MODE == MODE_ACCUM ? M->p : static_cast<void*>(M->partials);
-                    it.colind = M->colind;
-                    it.vals = M->vals;
-                    it.n = M->n;
-                    it.T = M->T;
-                    it.gt = gt;
-                    it.nrec = mt.x;
-                    it.ng = mt.y;
-                    it.nw = mt.z;
+                }
+            }
+        };
+        auto put = [&]() {
+            bool none = false, acq = false;
+            if (lane < BT_TAKE) {
+                const int slot = (taken + lane) & (BT_IRING - 1);
+                BItem& it = ring[slot];   // filled in place
+                it.j = fj;
+                it.i = fi;
+                it.t = ft;
+                const uint32_t bar = smem_u32(&gbar[slot]);
+                if (fj >= 0) {
+                    it.beta = fbeta;
+                    it.d0 = fd0;
+                    it.dn = fdn;
+                    it.beta_df = fbd;
+                    it.d0_df = fd0d;
+                    it.dn_df = fdnd;
+                    it.win = fwin;
+                    it.wout = fwout;
+                    it.aux = faux;
+                    it.colind = fcol;
+                    it.vals = fvals;
+                    it.n = fn;
+                    it.T = fT;
+                    it.gt = fgt;
+                    it.nrec = fmt.x;
+                    it.ng = fmt.y;
+                    it.nw = fmt.z;
+                    // the dependency (every tile of step j - 1 finished) was already met when read
+                    it.dep = (fj == 0 || farr >= (unsigned long long)fj * (unsigned long long)fT) ? 1 : 0;
+                    acq = fj > 0 && it.dep;
                     // the extra windows' start rows, then the gathered columns
-                    const uint32_t bytes = (mt.y > 0 || mt.z > 0) ? (uint32_t)(TMA_MAX_WIN + ((mt.y + 3) & ~3)) * 4u : 0u;
+                    const uint32_t bytes = (fmt.y > 0 || fmt.z > 0) ? (uint32_t)(TMA_MAX_WIN + ((fmt.y + 3) & ~3)) * 4u : 0u;
                     if (bytes) {
                         mbar_arrive_expect_tx(bar, bytes);
-                        bulk_copy(smem_u32(gring + slot * q.gcol_stride), bp.gcol + (size_t)gt * (q.gcol_stride >> 2), bytes, bar);
+                        bulk_copy(smem_u32(gring + slot * q.gcol_stride), bp.gcol + (size_t)fgt * (q.gcol_stride >> 2), bytes, bar);
                     } else {
                         mbar_arrive(bar);
                     }
                 } else {
+                    it.dep = 1;
                     none = true;
                     mbar_arrive(bar);
                 }
             }
             ended = __any_sync(0xffffffffu, none) || ended;
+            // acquire pattern: the relaxed reads of the arrival counters, then a fence (every lane
+            // that read one); after the warp barrier, the proxy fence of every lane orders the
+            // other CTAs' generic stores before this warp's TMA reads
+            const bool any_acq = __any_sync(0xffffffffu, acq);
+            if (any_acq) fence_acq_rel_gpu();
             __syncwarp();   // the ring entries are read by every lane
+            if (any_acq) fence_proxy_async();
             taken += BT_TAKE;
         };
-        for (int x = 0; x < BT_IRING / BT_TAKE; ++x) take();
+        if (lane == 0) g_next = atomicAdd(bp.ticket, (unsigned int)BT_TAKE);
+        for (int x = 0; x < BT_IRING / BT_TAKE; ++x) {
+            fetch();
+            put();
+        }
+        fetch();
         for (;; ++k) {
-            if (taken - k <= BT_IRING - BT_TAKE) take();
+            if (taken - k <= BT_IRING - BT_TAKE) {
+                put();
+                fetch();
+            }
             const int slot = k & (BT_IRING - 1);
             // every lane reads the gather-column list: every lane waits for its copy
             bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&gbar[slot]), (uint32_t)((k / BT_IRING) & 1), budget));
             const int j = ring[slot].j, i = ring[slot].i;
-            // step j - 1 of matrix i finished (arrival count j * T); then the other CTAs' generic
-            // stores of W_j and P are ordered before this CTA's TMA reads of them
-            if (ok && j > 0 && lane == 0 && !(i == ci && j <= cj)) {
+            // a dependency not yet met when the item was taken: wait (bounded) until step j - 1
+            // of matrix i finished (arrival count j * T), then order the other CTAs' generic
+            // stores of W_j and P before this warp's TMA reads of them (the cache ci, cj lives in
+            // lane 0: its decision is the warp's)
+            const bool wait_dep = __shfl_sync(0xffffffffu, (ok && j > 0 && !ring[slot].dep && !(i == ci && j <= cj)) ? 1 : 0, 0) != 0;
+            if (wait_dep && lane == 0) {
                 const unsigned long long T = (unsigned long long)ring[slot].T;
                 const long long t0 = clock64();
                 for (;;) {
@@ -232,7 +329,10 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
                     }
                     __nanosleep(64);
                 }
-                asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            }
+            if (wait_dep) {
+                __syncwarp();
+                fence_proxy_async();
             }
             const int s = k % NST;
             if (ok && lane == 0 && k >= NST) ok = mbar_wait_bounded(smem_u32(&freeb[s]), (uint32_t)(((k / NST) & 1) ^ 1), budget);
@@ -242,7 +342,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
                 if (lane == 0) atomicExch(bp.error, 1);
                 break;
             }
-            // publish the item to the consumers and the signal warp
+            // publish the item to the consumers and the freeing warp
             copy_item(&sitem[s], &ring[slot], lane);
             __syncwarp();
             const uint32_t bar = smem_u32(&full[s]);
@@ -303,26 +403,174 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
                 mbar_wait_bounded(smem_u32(&gbar[pos & (BT_IRING - 1)]), (uint32_t)((pos / BT_IRING) & 1), drain);
         }
     } else if (warp == cwarps + 1) {
-        // ------------------------------------------------------------------ signal warp (lane 0)
+        // ------------------------------------------------------------------ freeing warp (lane 0)
         if (lane == 0) {
+            unsigned int head = 0;
+            bool ok = true;
             for (int k = 0;; ++k) {
                 const int s = k % NST;
                 const uint32_t par = (uint32_t)((k / NST) & 1);
                 // the item is published (full), then its consumers are done with it (empty)
-                bool ok = mbar_wait_bounded(smem_u32(&full[s]), par, budget);
+                ok = mbar_wait_bounded(smem_u32(&full[s]), par, budget);
                 const int j = sitem[s].j, i = sitem[s].i;
                 if (ok && j < 0) break;
                 if (ok) ok = mbar_wait_bounded(smem_u32(&empty[s]), par, budget);
-                if (!ok) {
-                    atomicExch(bp.error, 1);
-                    break;
+                if (ok) {
+                    const long long t0 = clock64();
+                    while (head - ld_acquire_cta(&q_tail) >= (unsigned int)BT_SIGQ) {
+                        if (clock64() - t0 > budget) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
                 }
-                // the consumers' stores of W_{j+1}, P and the partials happen before this add
-                red_release_add(&bp.arrived[i], 1ull);
+                if (!ok) break;
                 mbar_arrive(smem_u32(&freeb[s]));
+                sigq[head % BT_SIGQ] = i;
+                st_release_cta(&q_head, ++head);
+            }
+            if (!ok) atomicExch(bp.error, 1);
+            // the end marker, when there is room (else the releasing warp's wait runs out)
+            if (head - ld_acquire_cta(&q_tail) < (unsigned int)BT_SIGQ) {
+                sigq[head % BT_SIGQ] = -1;
+                st_release_cta(&q_head, ++head);
             }
         }
-    } else {
+    } else if (warp == cwarps + 2) {
+        // ------------------------------------------------------------------ releasing warp (lane 0)
+        if (lane == 0) {
+            unsigned int tail = 0;
+            for (bool done = false; !done;) {
+                unsigned int head;
+                const long long t0 = clock64();
+                while ((head = ld_acquire_cta(&q_head)) == tail) {
+                    if (clock64() - t0 > budget) {
+                        atomicExch(bp.error, 1);
+                        done = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                if (done) break;
+                // the consumers' stores of the queued tiles (W_{j+1}, P) happen before the adds:
+                // one fence for all of them
+                fence_acq_rel_gpu();
+                int cur = -1;
+                unsigned long long cnt = 0;
+                for (; tail != head; ++tail) {
+                    const int i = sigq[tail % BT_SIGQ];
+                    if (i < 0) {
+                        done = true;
+                        break;
+                    }
+                    if (i != cur) {
+                        if (cnt) red_relaxed_add(&bp.arrived[cur], cnt);
+                        cur = i;
+                        cnt = 0;
+                    }
+                    ++cnt;
+                }
+                if (cnt) red_relaxed_add(&bp.arrived[cur], cnt);
+                st_release_cta(&q_tail, tail);
+            }
+        }
+    } else if (MODE == MODE_DOT && warp == cwarps + 3) {
+        // ------------------------------------------------------------------ reducing warp (pass 2)
+        // Sums each tile's trace terms over its R row lanes, per column, in a fixed order: G lanes
+        // per column pair (G = 32 / column pairs, at most 8) take rows g, g + G, ..., into BT_RACC
+        // independent accumulators (row l0 + u G goes to accumulator u), which are then added in
+        // order; lane g = 0 adds the other lanes' sums in lane order. Double-float arithmetic on
+        // the FP32 pipes in the DF64 and FP32 modes (the partials are stored as (hi, lo) float
+        // pairs), FP64 in the F64 mode.
+        const int b = bp.b;
+        const int tp = (b + 1) / 2;
+        int G = 32 / tp;
+        G = G < 1 ? 1 : (G > 8 ? 8 : G);
+        const int cpl = lane / G, g = lane - cpl * G;
+        const int cpstride = 32 / G;
+        const double* red = reinterpret_cast<const double*>(smem + off_red);
+        for (int r = 0;; ++r) {
+            const int rb = r % BT_NRB;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&rfull[rb]), (uint32_t)((r / BT_NRB) & 1), budget))) {
+                if (lane == 0) atomicExch(bp.error, 1);
+                break;
+            }
+            void* part = rpart[rb];
+            if (!part) break;
+            const double* rbuf = red + (size_t)rb * 2 * cthreads;
+            for (int cp0 = 0; cp0 < tp; cp0 += cpstride) {
+                const int cp = cpl < cpstride ? cp0 + cpl : tp;   // lanes past cpstride * G idle
+                if constexpr (PREC == LL_PREC_F64) {
+                    double a0[BT_RACC], a1[BT_RACC];
+#pragma unroll
+                    for (int u = 0; u < BT_RACC; ++u) a0[u] = a1[u] = 0.0;
+                    if (cp < tp)
+                        for (int l0 = g; l0 < R; l0 += BT_RACC * G) {
+#pragma unroll
+                            for (int u = 0; u < BT_RACC; ++u) {
+                                const int l = l0 + u * G;
+                                if (l < R) {
+                                    a0[u] += rbuf[2 * (l * tp + cp)];
+                                    a1[u] += rbuf[2 * (l * tp + cp) + 1];
+                                }
+                            }
+                        }
+                    double s0 = a0[0], s1 = a1[0];
+#pragma unroll
+                    for (int u = 1; u < BT_RACC; ++u) {
+                        s0 += a0[u];
+                        s1 += a1[u];
+                    }
+                    double x0 = s0, x1 = s1;
+                    for (int off = 1; off < G; ++off) {
+                        const double o0 = __shfl_down_sync(0xffffffffu, s0, off);
+                        const double o1 = __shfl_down_sync(0xffffffffu, s1, off);
+                        x0 += o0;
+                        x1 += o1;
+                    }
+                    if (cp < tp && g == 0) {
+                        double* pd = static_cast<double*>(part);
+                        pd[2 * cp] = x0;
+                        if (2 * cp + 1 < b) pd[2 * cp + 1] = x1;
+                    }
+                } else {
+                    const ulonglong2* rd = reinterpret_cast<const ulonglong2*>(rbuf);
+                    f2x ah[BT_RACC], al[BT_RACC];
+#pragma unroll
+                    for (int u = 0; u < BT_RACC; ++u) ah[u] = al[u] = 0ull;
+                    if (cp < tp)
+                        for (int l0 = g; l0 < R; l0 += BT_RACC * G) {
+#pragma unroll
+                            for (int u = 0; u < BT_RACC; ++u) {
+                                const int l = l0 + u * G;
+                                if (l < R) {
+                                    const ulonglong2 v = rd[l * tp + cp];
+                                    df2_add(ah[u], al[u], v.x, v.y);
+                                }
+                            }
+                        }
+#pragma unroll
+                    for (int u = 1; u < BT_RACC; ++u) df2_add(ah[0], al[0], ah[u], al[u]);
+                    f2x th = ah[0], tl = al[0];
+                    for (int off = 1; off < G; ++off) {
+                        const f2x oh = shfl_down_f2(ah[0], off), ol = shfl_down_f2(al[0], off);
+                        df2_add(th, tl, oh, ol);
+                    }
+                    if (cp < tp && g == 0) {
+                        float h0, h1, l0, l1;
+                        f2_unpack(th, h0, h1);
+                        f2_unpack(tl, l0, l1);
+                        float2* pf = static_cast<float2*>(part);
+                        pf[2 * cp] = make_float2(h0, l0);
+                        if (2 * cp + 1 < b) pf[2 * cp + 1] = make_float2(h1, l1);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&rempty[rb]));
+        }
+    } else if (warp < cwarps) {
         // ------------------------------------------------------------------ consumer warps
         const int b = bp.b;
         const int tp = (b + 1) / 2;
@@ -335,7 +583,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
         const unsigned own_off = (unsigned)(rlane + TMA_HALO) * (unsigned)q.rowbytes + cpoff;
         const unsigned aux_off = (unsigned)q.off_aux + (unsigned)rlane * (unsigned)q.auxbytes +
                                  (unsigned)(cp * (MODE == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
-        double* red = reinterpret_cast<double*>(smem + off_red);
+        double* red = reinterpret_cast<double*>(smem + off_red);   // BT_NRB buffers of cthreads x 16 bytes
+        int nreduce = 0;   // trace-term hand-overs so far
         for (int k = 0;; ++k) {
             const int s = k % NST;
             const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((k / NST) & 1), budget);
@@ -396,69 +645,43 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1) k_leja_tma_batched(const B
                 row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wout + (size_t)r * ldq + cp, pblk + (size_t)r * ldpq + cp, TP);
             }
             if constexpr (MODE == MODE_DOT) {
-                // The tile's trace partial of every column (slot j + 1: the step's W_{j+1} traces;
-                // slot 0: the W_0 traces). Row lanes are summed in a fixed order: group g of G
-                // sums rows g, g + G, ..., then the G groups of a column pair (G consecutive
-                // lanes) combine by a shuffle tree. Double-float arithmetic on the FP32 pipes in
-                // the DF64 and FP32 modes (the partials are stored as (hi, lo) float pairs).
+                // hand the tile's per-thread trace terms to the reducing warp (slot j + 1: the
+                // step's W_{j+1} traces; slot 0: the W_0 traces), in BT_NRB buffers in turn
                 const int nred = j == 0 ? 2 : 1;
-                int G = 8;
-                while (G > 1 && G * tp > cthreads) G >>= 1;
-                const int x = tid, cpx = x / G, g = x - cpx * G;
-                for (int qq = 0; qq < nred; ++qq) {
+                for (int qq = 0; qq < nred; ++qq, ++nreduce) {
                     const int slot = qq ? 0 : j + 1;
+                    const int rb = nreduce % BT_NRB;
+                    const bool okr = nreduce < BT_NRB ||
+                                     mbar_wait_bounded(smem_u32(&rempty[rb]), (uint32_t)(((nreduce / BT_NRB) - 1) & 1), budget);
+                    if (__any_sync(0xffffffffu, !okr) && lane == 0) atomicExch(bp.error, 1);
+                    double* rbuf = red + (size_t)rb * 2 * cthreads;
                     if constexpr (PREC == LL_PREC_F64) {
-                        double* rd = red;
-                        rd[2 * tid] = qq ? TP.t0d[0] : TP.td[0];
-                        rd[2 * tid + 1] = qq ? TP.t0d[1] : TP.td[1];
-                        consumer_sync(cthreads);
-                        double a0 = 0.0, a1 = 0.0;
-                        if (cpx < tp)
-                            for (int l = g; l < R; l += G) {
-                                a0 += rd[2 * (l * tp + cpx)];
-                                a1 += rd[2 * (l * tp + cpx) + 1];
-                            }
-                        for (int off = G >> 1; off > 0; off >>= 1) {
-                            a0 += __shfl_down_sync(0xffffffffu, a0, off);
-                            a1 += __shfl_down_sync(0xffffffffu, a1, off);
-                        }
-                        double* part = static_cast<double*>(sitem[s].aux) + ((size_t)slot * T + t) * b;
-                        if (cpx < tp && g == 0) {
-                            part[2 * cpx] = a0;
-                            if (2 * cpx + 1 < b) part[2 * cpx + 1] = a1;
-                        }
+                        rbuf[2 * tid] = qq ? TP.t0d[0] : TP.td[0];
+                        rbuf[2 * tid + 1] = qq ? TP.t0d[1] : TP.td[1];
+                        if (tid == 0) rpart[rb] = static_cast<double*>(sitem[s].aux) + ((size_t)slot * T + t) * b;
                     } else {
-                        ulonglong2* rd = reinterpret_cast<ulonglong2*>(red);
-                        rd[tid] = qq ? make_ulonglong2(TP.t0h2, TP.t0l2) : make_ulonglong2(TP.th2, TP.tl2);
-                        consumer_sync(cthreads);
-                        f2x ah = 0ull, al = 0ull;
-                        if (cpx < tp)
-                            for (int l = g; l < R; l += G) {
-                                const ulonglong2 v = rd[l * tp + cpx];
-                                df2_add(ah, al, v.x, v.y);
-                            }
-                        for (int off = G >> 1; off > 0; off >>= 1) {
-                            const f2x oh = shfl_down_f2(ah, off), ol = shfl_down_f2(al, off);
-                            df2_add(ah, al, oh, ol);
-                        }
-                        float2* part = reinterpret_cast<float2*>(sitem[s].aux) + ((size_t)slot * T + t) * b;
-                        if (cpx < tp && g == 0) {
-                            float h0, h1, l0, l1;
-                            f2_unpack(ah, h0, h1);
-                            f2_unpack(al, l0, l1);
-                            part[2 * cpx] = make_float2(h0, l0);
-                            if (2 * cpx + 1 < b) part[2 * cpx + 1] = make_float2(h1, l1);
-                        }
+                        reinterpret_cast<ulonglong2*>(rbuf)[tid] = qq ? make_ulonglong2(TP.t0h2, TP.t0l2) : make_ulonglong2(TP.th2, TP.tl2);
+                        if (tid == 0) rpart[rb] = static_cast<float2*>(sitem[s].aux) + ((size_t)slot * T + t) * b;
                     }
-                    consumer_sync(cthreads);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&rfull[rb]));
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
         }
+        if constexpr (MODE == MODE_DOT) {
+            // no more trace terms: a null destination stops the reducing warp
+            const int rb = nreduce % BT_NRB;
+            if (nreduce >= BT_NRB) mbar_wait_bounded(smem_u32(&rempty[rb]), (uint32_t)(((nreduce / BT_NRB) - 1) & 1), budget);
+            if (tid == 0) rpart[rb] = nullptr;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&rfull[rb]));
+        }
     }
     __syncthreads();
 }
+
 
 // dots[j][c] = sum_t partials[j][t][c] (tiles in order, in FP64) of every matrix (blockIdx.y), step
 // slot and column; one thread per (slot, column). DF: the partials are double-float pairs.
@@ -533,11 +756,11 @@ bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double
     if (R < 1) return false;
     const double avgfar = avg_far >= 0.0 && avg_far <= avg_nnz ? avg_far : avg_nnz;
     const size_t tab_bytes = a16((size_t)bt_table_ints(max_m, count) * 4);
-    const size_t budget = 220 * 1024;   // dynamic shared memory (the static part holds the barriers and items)
+    const size_t budget = 220 * 1024;   // dynamic shared memory (the static part holds the barriers, items and queue)
     auto fit = [&](int Rt) {
         tma_stage_layout(q, Rt, avg_nnz, avgfar, 1.25);
         const size_t ct = (size_t)((Rt * tp + 31) / 32) * 32;
-        const size_t extra = a128((size_t)BT_IRING * q.gcol_stride) + (mode == MODE_DOT ? ct * 16 : 0) + tab_bytes + 128;
+        const size_t extra = a128((size_t)BT_IRING * q.gcol_stride) + (mode == MODE_DOT ? BT_NRB * ct * 16 : 0) + tab_bytes + 128;
         const int nst = budget > extra ? (int)((budget - extra) / q.stage_bytes) : 0;
         q.nst = nst > TMA_MAX_STAGES ? TMA_MAX_STAGES : nst;
         return q.nst;
@@ -555,11 +778,11 @@ bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double
     q.nprod = 1;
     q.ring_base = q.nst * q.stage_bytes;
     const int cthreads = ((Rbest * tp + 31) / 32) * 32;
-    L.threads = cthreads + 64;
+    L.threads = cthreads + (mode == MODE_DOT ? 128 : 96);
     L.off_red = a128((size_t)q.ring_base + (size_t)BT_IRING * q.gcol_stride);
-    L.off_tab = L.off_red + (mode == MODE_DOT ? (size_t)cthreads * 16 : 0);
+    L.off_tab = L.off_red + (mode == MODE_DOT ? (size_t)BT_NRB * cthreads * 16 : 0);
     L.smem = L.off_tab + tab_bytes + 128;
-    if (L.threads > TMA_MAX_THREADS) return false;
+    if (L.threads > BT_MAX_THREADS) return false;
     int per_sm = 0;
     switch (precision * NUM_MODES + mode) {
         case LL_PREC_F64 * NUM_MODES + MODE_ACCUM: per_sm = occupancy_bt<LL_PREC_F64, MODE_ACCUM>(L.threads, L.smem); break;

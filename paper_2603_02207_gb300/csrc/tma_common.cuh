@@ -290,6 +290,8 @@ inline void tma_stage_layout(TmaParams& q, int Rt, double avg, double avgfar, do
 // ---- batched TMA passes ----------------------------------------------------------------------
 constexpr int BT_IRING = 16;   // work items taken ahead of the one being issued
 constexpr int BT_TAKE = 8;     // items taken per ticket increment (decoded by eight lanes)
+constexpr int BT_NRB = 3;      // trace-term buffers handed from the consumers to the reducing warp
+constexpr int BT_MAX_THREADS = 512 + 128;  // consumers, then the producer, freeing, releasing (and reducing) warps
 
 // Per matrix of a batch, in degree order (device array; the tensor maps make it 128-byte aligned)
 struct BatchTmaMat {
@@ -319,7 +321,7 @@ struct BItem {
     const void* vals;
     int j, i, t, gt;             // step (-1: no more items), matrix, tile, tile number in the batch
     int nrec, ng, n, T;          // records and gathered rows of the tile; rows and tiles of the matrix
-    int nw, pad;                 // extra windows of the tile
+    int nw, dep;                 // extra windows of the tile; 1: step j - 1 known finished when taken
 };
 static_assert(sizeof(BItem) == 128, "BItem is copied as 32 words");
 
