@@ -12,18 +12,19 @@
 //    copies: descriptor, operand windows, V/P rows and the gathered rows of W_j of matrix i,
 //    through that matrix's own tensor maps;
 //  * the consumer warps compute the item's rows with the per-row arithmetic of the single-matrix
-//    kernels and store W_{j+1} (and P); in pass 2 they hand their trace terms to the reducing warp;
+//    kernels and store W_{j+1} (and P). In pass 2 each thread writes its trace terms to one of
+//    BT_NRB buffers, and after writing those of a tile each warp sums its share of column pairs of
+//    the previous tile's buffer over the rows (so no warp waits for all the others to finish a
+//    tile); the per-tile partials of every step are reduced per matrix after the pass;
 //  * the freeing warp waits for each stage's consumers, frees the stage for the producer and
 //    queues the finished tile's matrix;
 //  * the releasing warp publishes the queued tiles' completion: one release fence for all the
 //    tiles queued so far (so the stores of W_{j+1} and P are visible before it), then one add per
 //    run of tiles of the same matrix to its arrival counter. The fence latency stays off the
-//    consumers, the producer and the stage recycling;
-//  * pass 2: the reducing warp sums each tile's trace terms over its rows, per column, in a fixed
-//    order; the per-tile partials of every step are reduced per matrix after the pass.
-// Every dependency of an item has a smaller ticket; consumers wait only on copies (and trace
-// buffers), the freeing warp only on consumers (and queue room), the releasing and reducing warps
-// only on what the others hand them, so the smallest unfinished item can always proceed and the
+//    consumers, the producer and the stage recycling.
+// Every dependency of an item has a smaller ticket; consumers wait only on copies (and on one
+// another's earlier trace buffers), the freeing warp only on consumers (and queue room), the
+// releasing warp only on the queue, so the smallest unfinished item can always proceed and the
 // launch cannot deadlock whatever the residency. W_j and P of step j - 1 were written by other
 // CTAs with generic stores; after the acquire of the arrival counter a proxy fence orders them
 // before this CTA's TMA reads. Every wait is bounded (clock64); when one runs out the CTA records
@@ -40,7 +41,6 @@ namespace {
 
 constexpr int BT_CONSUMER_BAR = 1;   // named barrier of the consumer warps
 constexpr int BT_SIGQ = 64;          // finished tiles queued from the freeing warp to the releasing warp
-constexpr int BT_RACC = 4;           // independent accumulators per lane of the reducing warp
 static_assert((BT_IRING & (BT_IRING - 1)) == 0 && BT_IRING % BT_TAKE == 0 && BT_TAKE <= 32, "take-ahead ring");
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
@@ -130,12 +130,12 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
     __shared__ __align__(8) unsigned long long freeb[TMA_MAX_STAGES];
     __shared__ __align__(8) unsigned long long gbar[BT_IRING];
     __shared__ __align__(8) unsigned long long rfull[BT_NRB];    // pass 2: trace terms written (every consumer warp)
-    __shared__ __align__(8) unsigned long long rempty[BT_NRB];   // pass 2: trace terms reduced
+    __shared__ __align__(8) unsigned long long rempty[BT_NRB];   // pass 2: trace terms reduced (every consumer warp)
     __shared__ __align__(16) BItem ring[BT_IRING];
     __shared__ __align__(16) BItem sitem[TMA_MAX_STAGES];
     __shared__ int sigq[BT_SIGQ];            // matrices of freed tiles, in item order
     __shared__ unsigned int q_head, q_tail;  // tiles queued (freeing warp) and published (releasing warp)
-    __shared__ void* rpart[BT_NRB];          // pass 2: where the reduced terms go (null: no more)
+    __shared__ void* rpart[BT_NRB];          // pass 2: where the reduced terms go
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
 
     const TmaParams& q = bp.q;
@@ -143,8 +143,7 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
     const int warp = tid >> 5, lane = tid & 31;
     const int NST = q.nst;
     const int R = q.R;
-    // consumer threads; then the producer, freeing and releasing warps (and in pass 2 the reducing warp)
-    const int cthreads = (int)blockDim.x - (MODE == MODE_DOT ? 128 : 96);
+    const int cthreads = (int)blockDim.x - 96;   // consumer threads; then the producer, freeing and releasing warps
     const int cwarps = cthreads >> 5;
     const long long budget = bp.spin_budget;
     int* tab = reinterpret_cast<int*>(smem + off_tab);
@@ -159,7 +158,7 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
         for (int s = 0; s < BT_IRING; ++s) mbar_init(smem_u32(&gbar[s]), 1);
         for (int x = 0; x < BT_NRB; ++x) {
             mbar_init(smem_u32(&rfull[x]), cwarps);
-            mbar_init(smem_u32(&rempty[x]), 1);
+            mbar_init(smem_u32(&rempty[x]), cwarps);
         }
         q_head = 0u;
         q_tail = 0u;
@@ -475,101 +474,6 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                 st_release_cta(&q_tail, tail);
             }
         }
-    } else if (MODE == MODE_DOT && warp == cwarps + 3) {
-        // ------------------------------------------------------------------ reducing warp (pass 2)
-        // Sums each tile's trace terms over its R row lanes, per column, in a fixed order: G lanes
-        // per column pair (G = 32 / column pairs, at most 8) take rows g, g + G, ..., into BT_RACC
-        // independent accumulators (row l0 + u G goes to accumulator u), which are then added in
-        // order; lane g = 0 adds the other lanes' sums in lane order. Double-float arithmetic on
-        // the FP32 pipes in the DF64 and FP32 modes (the partials are stored as (hi, lo) float
-        // pairs), FP64 in the F64 mode.
-        const int b = bp.b;
-        const int tp = (b + 1) / 2;
-        int G = 32 / tp;
-        G = G < 1 ? 1 : (G > 8 ? 8 : G);
-        const int cpl = lane / G, g = lane - cpl * G;
-        const int cpstride = 32 / G;
-        const double* red = reinterpret_cast<const double*>(smem + off_red);
-        for (int r = 0;; ++r) {
-            const int rb = r % BT_NRB;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&rfull[rb]), (uint32_t)((r / BT_NRB) & 1), budget))) {
-                if (lane == 0) atomicExch(bp.error, 1);
-                break;
-            }
-            void* part = rpart[rb];
-            if (!part) break;
-            const double* rbuf = red + (size_t)rb * 2 * cthreads;
-            for (int cp0 = 0; cp0 < tp; cp0 += cpstride) {
-                const int cp = cpl < cpstride ? cp0 + cpl : tp;   // lanes past cpstride * G idle
-                if constexpr (PREC == LL_PREC_F64) {
-                    double a0[BT_RACC], a1[BT_RACC];
-#pragma unroll
-                    for (int u = 0; u < BT_RACC; ++u) a0[u] = a1[u] = 0.0;
-                    if (cp < tp)
-                        for (int l0 = g; l0 < R; l0 += BT_RACC * G) {
-#pragma unroll
-                            for (int u = 0; u < BT_RACC; ++u) {
-                                const int l = l0 + u * G;
-                                if (l < R) {
-                                    a0[u] += rbuf[2 * (l * tp + cp)];
-                                    a1[u] += rbuf[2 * (l * tp + cp) + 1];
-                                }
-                            }
-                        }
-                    double s0 = a0[0], s1 = a1[0];
-#pragma unroll
-                    for (int u = 1; u < BT_RACC; ++u) {
-                        s0 += a0[u];
-                        s1 += a1[u];
-                    }
-                    double x0 = s0, x1 = s1;
-                    for (int off = 1; off < G; ++off) {
-                        const double o0 = __shfl_down_sync(0xffffffffu, s0, off);
-                        const double o1 = __shfl_down_sync(0xffffffffu, s1, off);
-                        x0 += o0;
-                        x1 += o1;
-                    }
-                    if (cp < tp && g == 0) {
-                        double* pd = static_cast<double*>(part);
-                        pd[2 * cp] = x0;
-                        if (2 * cp + 1 < b) pd[2 * cp + 1] = x1;
-                    }
-                } else {
-                    const ulonglong2* rd = reinterpret_cast<const ulonglong2*>(rbuf);
-                    f2x ah[BT_RACC], al[BT_RACC];
-#pragma unroll
-                    for (int u = 0; u < BT_RACC; ++u) ah[u] = al[u] = 0ull;
-                    if (cp < tp)
-                        for (int l0 = g; l0 < R; l0 += BT_RACC * G) {
-#pragma unroll
-                            for (int u = 0; u < BT_RACC; ++u) {
-                                const int l = l0 + u * G;
-                                if (l < R) {
-                                    const ulonglong2 v = rd[l * tp + cp];
-                                    df2_add(ah[u], al[u], v.x, v.y);
-                                }
-                            }
-                        }
-#pragma unroll
-                    for (int u = 1; u < BT_RACC; ++u) df2_add(ah[0], al[0], ah[u], al[u]);
-                    f2x th = ah[0], tl = al[0];
-                    for (int off = 1; off < G; ++off) {
-                        const f2x oh = shfl_down_f2(ah[0], off), ol = shfl_down_f2(al[0], off);
-                        df2_add(th, tl, oh, ol);
-                    }
-                    if (cp < tp && g == 0) {
-                        float h0, h1, l0, l1;
-                        f2_unpack(th, h0, h1);
-                        f2_unpack(tl, l0, l1);
-                        float2* pf = static_cast<float2*>(part);
-                        pf[2 * cp] = make_float2(h0, l0);
-                        if (2 * cp + 1 < b) pf[2 * cp + 1] = make_float2(h1, l1);
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&rempty[rb]));
-        }
     } else if (warp < cwarps) {
         // ------------------------------------------------------------------ consumer warps
         const int b = bp.b;
@@ -585,6 +489,56 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                                  (unsigned)(cp * (MODE == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
         double* red = reinterpret_cast<double*>(smem + off_red);   // BT_NRB buffers of cthreads x 16 bytes
         int nreduce = 0;   // trace-term hand-overs so far
+        // This warp's share of reduction x: column pairs warp, warp + cwarps, ...; lane l sums rows
+        // l, l + 32, ... in order, then a shuffle tree (fixed order) gives lane 0 the column sums.
+        // It waits until every consumer warp has written reduction x (they do so one reduction
+        // earlier in their own sequence, so the wait is short and cannot close a cycle).
+        auto reduce_share = [&](int x) {
+            const int rb = x % BT_NRB;
+            const bool okw = mbar_wait_bounded(smem_u32(&rfull[rb]), (uint32_t)((x / BT_NRB) & 1), budget);
+            if (__any_sync(0xffffffffu, !okw) && lane == 0) atomicExch(bp.error, 1);
+            const double* rbuf = red + (size_t)rb * 2 * cthreads;
+            void* part = rpart[rb];
+            for (int c2 = warp; c2 < tp; c2 += cwarps) {
+                if constexpr (PREC == LL_PREC_F64) {
+                    double a0 = 0.0, a1 = 0.0;
+                    for (int l = lane; l < R; l += 32) {
+                        a0 += rbuf[2 * (l * tp + c2)];
+                        a1 += rbuf[2 * (l * tp + c2) + 1];
+                    }
+                    for (int off = 16; off > 0; off >>= 1) {
+                        a0 += __shfl_down_sync(0xffffffffu, a0, off);
+                        a1 += __shfl_down_sync(0xffffffffu, a1, off);
+                    }
+                    if (lane == 0) {
+                        double* pd = static_cast<double*>(part);
+                        pd[2 * c2] = a0;
+                        if (2 * c2 + 1 < b) pd[2 * c2 + 1] = a1;
+                    }
+                } else {
+                    const ulonglong2* rd = reinterpret_cast<const ulonglong2*>(rbuf);
+                    f2x ah = 0ull, al = 0ull;
+                    for (int l = lane; l < R; l += 32) {
+                        const ulonglong2 v = rd[l * tp + c2];
+                        df2_add(ah, al, v.x, v.y);
+                    }
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const f2x oh = shfl_down_f2(ah, off), ol = shfl_down_f2(al, off);
+                        df2_add(ah, al, oh, ol);
+                    }
+                    if (lane == 0) {
+                        float h0, h1, l0, l1;
+                        f2_unpack(ah, h0, h1);
+                        f2_unpack(al, l0, l1);
+                        float2* pf = static_cast<float2*>(part);
+                        pf[2 * c2] = make_float2(h0, l0);
+                        if (2 * c2 + 1 < b) pf[2 * c2 + 1] = make_float2(h1, l1);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&rempty[rb]));
+        };
         for (int k = 0;; ++k) {
             const int s = k % NST;
             const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((k / NST) & 1), budget);
@@ -645,8 +599,9 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                 row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wout + (size_t)r * ldq + cp, pblk + (size_t)r * ldpq + cp, TP);
             }
             if constexpr (MODE == MODE_DOT) {
-                // hand the tile's per-thread trace terms to the reducing warp (slot j + 1: the
-                // step's W_{j+1} traces; slot 0: the W_0 traces), in BT_NRB buffers in turn
+                // write the tile's per-thread trace terms (slot j + 1: the step's W_{j+1} traces;
+                // slot 0: the W_0 traces) to the next of BT_NRB buffers, then sum this warp's share
+                // of the reduction before it
                 const int nred = j == 0 ? 2 : 1;
                 for (int qq = 0; qq < nred; ++qq, ++nreduce) {
                     const int slot = qq ? 0 : j + 1;
@@ -665,18 +620,14 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&rfull[rb]));
+                    if (nreduce > 0) reduce_share(nreduce - 1);
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
         }
         if constexpr (MODE == MODE_DOT) {
-            // no more trace terms: a null destination stops the reducing warp
-            const int rb = nreduce % BT_NRB;
-            if (nreduce >= BT_NRB) mbar_wait_bounded(smem_u32(&rempty[rb]), (uint32_t)(((nreduce / BT_NRB) - 1) & 1), budget);
-            if (tid == 0) rpart[rb] = nullptr;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&rfull[rb]));
+            if (nreduce > 0) reduce_share(nreduce - 1);   // the last tile's terms
         }
     }
     __syncthreads();
@@ -778,7 +729,7 @@ bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double
     q.nprod = 1;
     q.ring_base = q.nst * q.stage_bytes;
     const int cthreads = ((Rbest * tp + 31) / 32) * 32;
-    L.threads = cthreads + (mode == MODE_DOT ? 128 : 96);
+    L.threads = cthreads + 96;
     L.off_red = a128((size_t)q.ring_base + (size_t)BT_IRING * q.gcol_stride);
     L.off_tab = L.off_red + (mode == MODE_DOT ? (size_t)BT_NRB * cthreads * 16 : 0);
     L.smem = L.off_tab + tab_bytes + 128;

@@ -290,8 +290,8 @@ inline void tma_stage_layout(TmaParams& q, int Rt, double avg, double avgfar, do
 // ---- batched TMA passes ----------------------------------------------------------------------
 constexpr int BT_IRING = 16;   // work items taken ahead of the one being issued
 constexpr int BT_TAKE = 8;     // items taken per ticket increment (decoded by eight lanes)
-constexpr int BT_NRB = 3;      // trace-term buffers handed from the consumers to the reducing warp
-constexpr int BT_MAX_THREADS = 512 + 128;  // consumers, then the producer, freeing, releasing (and reducing) warps
+constexpr int BT_NRB = 3;      // trace-term buffers of the consumer warps (a tile's terms are summed one tile later)
+constexpr int BT_MAX_THREADS = 512 + 96;   // consumers, then the producer, freeing and releasing warps
 
 // Per matrix of a batch, in degree order (device array; the tensor maps make it 128-byte aligned)
 struct BatchTmaMat {
