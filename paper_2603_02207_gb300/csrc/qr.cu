@@ -15,11 +15,87 @@ constexpr int QR_THREADS = 256;
 constexpr int QR_TR = 32;       // rows per shared-memory tile of the Gram kernel
 constexpr int QR_FLUSH = 8;     // tiles summed in double-float before an FP64 flush
 
+// A double as an unevaluated float pair hi + lo, from its bit fields with integer operations and
+// one integer-to-float conversion (GB300 runs FP64 instructions, conversions from double among
+// them, at a small fraction of the FP32 rate): hi takes the sign, the exponent and the leading 23
+// stored mantissa bits (truncated), lo the remaining 29 bits rounded to 24, scaled by
+// 2^(e - 52). |x - hi - lo| <= 2^-47 |x|. Values outside the float pair's exponent range (zero,
+// subnormals, |x| >= 2^128, inf, nan) take the plain conversion and lo = 0.
+__device__ __forceinline__ void split_bits(double x, float& h, float& l) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hw = (unsigned int)(u >> 32);
+    const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+    if (e < -126 || e > 127) {
+        h = (e < -126) ? __uint_as_float(hw & 0x80000000u) : __double2float_rn(x);
+        l = 0.f;
+        return;
+    }
+    const unsigned int sign = hw & 0x80000000u;
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    h = __uint_as_float(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29));
+    const float lf = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull));
+    l = ldexpf(sign ? -lf : lf, e - 52);
+}
+
 // Element (i) of a block as an unevaluated float pair hi + lo.
-__device__ __forceinline__ void ld_split(const double* p, size_t i, float& h, float& l) {
-    const double x = p[i];
-    h = __double2float_rn(x);
-    l = __double2float_rn(x - (double)h);
+__device__ __forceinline__ void ld_split(const double* p, size_t i, float& h, float& l) { split_bits(p[i], h, l); }
+
+// Asynchronous staging of block tiles in shared memory (cp.async, completion waited for by the
+// hardware): one copy unit is an element (double, float) or a column pair (dfp, 16 bytes).
+template <typename T> struct Stg;
+template <> struct Stg<double> { static constexpr int cp = 8, per = 1; };
+template <> struct Stg<float> { static constexpr int cp = 4, per = 1; };
+template <> struct Stg<dfp> { static constexpr int cp = 16, per = 2; };
+
+template <int CP>
+__device__ __forceinline__ void cp_async_unit(void* sdst, const void* gsrc, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc),
+                 "n"(CP), "r"(valid ? CP : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// global address of the copy unit holding element a of row `row`
+__device__ __forceinline__ const void* unit_src(const double* X, long long ld, long long row, int a) { return X + row * ld + a; }
+__device__ __forceinline__ const void* unit_src(const float* X, long long ld, long long row, int a) { return X + row * ld + a; }
+__device__ __forceinline__ const void* unit_src(const dfp* X, long long ld, long long row, int a) {
+    return reinterpret_cast<const float*>(X) + ((row * ld + a) >> 1) * 4;   // a and ld are even
+}
+// element `sub` of a staged unit as a float pair
+__device__ __forceinline__ void unit_split(const double* u, int, float& h, float& l) { split_bits(*u, h, l); }
+__device__ __forceinline__ void unit_split(const float* u, int, float& h, float& l) { h = *u; l = 0.f; }
+__device__ __forceinline__ void unit_split(const dfp* u, int sub, float& h, float& l) {
+    const float* f = reinterpret_cast<const float*>(u);
+    h = f[sub];
+    l = f[2 + sub];
+}
+
+// Issues the copies of rows [tile * TR, tile * TR + TR) x columns [0, kp) of X (ld) into `stage`
+// (TR x kp / per units); rows >= n and columns >= k are zero-filled.
+template <typename T> __host__ __device__ constexpr size_t stage_bytes(int TR, int kp) { return (size_t)TR * (kp / Stg<T>::per) * Stg<T>::cp; }
+template <typename T>
+__device__ __forceinline__ void stage_tile(unsigned char* stage, const T* X, long long ld, int k, int kp, int n, int tile, int TR) {
+    constexpr int CP = Stg<T>::cp, PER = Stg<T>::per;
+    const int U = kp / PER;
+    for (int u = threadIdx.x; u < TR * U; u += blockDim.x) {
+        const int r = u / U, a = (u - r * U) * PER;
+        const long long row = (long long)tile * TR + r;
+        const bool valid = row < n && a < k;
+        cp_async_unit<CP>(stage + (size_t)u * CP, valid ? unit_src(X, ld, row, a) : (const void*)X, valid);
+    }
+}
+// Splits a staged tile into float pairs: h[r * kp + a], l[r * kp + a] (columns >= k are zero)
+template <typename T>
+__device__ __forceinline__ void split_tile(const unsigned char* stage, int k, int kp, float* h, float* l, int TR) {
+    constexpr int CP = Stg<T>::cp, PER = Stg<T>::per;
+    for (int i = threadIdx.x; i < TR * kp; i += blockDim.x) {
+        const int r = i / kp, a = i - r * kp;
+        float hh = 0.f, ll = 0.f;
+        if (a < k) unit_split(reinterpret_cast<const T*>(stage + ((size_t)r * (kp / PER) + a / PER) * CP), a % PER, hh, ll);
+        h[i] = hh;
+        l[i] = ll;
+    }
 }
 __device__ __forceinline__ void ld_split(const float2* p, size_t i, float& h, float& l) {
     const float2 v = p[i];
@@ -89,26 +165,27 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
 #pragma unroll
     for (int e = 0; e < 16; ++e) a64[e] = 0.0;
     const int ntiles = (n + QR_TR - 1) / QR_TR;
-    int cnt = 0;
+    // raw tiles staged asynchronously one tile ahead (two buffers after the split arrays), so that
+    // the next tile's loads are in flight while this one is computed
+    unsigned char* stg = reinterpret_cast<unsigned char*>(zl + QR_TR * kzp);
+    const size_t sxb = stage_bytes<TX>(QR_TR, kxp), szb = sym ? 0 : stage_bytes<TZ>(QR_TR, kzp);
+    auto stage = [&](int tile, int b) {
+        unsigned char* sb = stg + (size_t)b * (sxb + szb);
+        stage_tile<TX>(sb, X, ldx, kx, kxp, n, tile, QR_TR);
+        if (!sym) stage_tile<TZ>(sb + sxb, Z, ldz, kz, kzp, n, tile, QR_TR);
+        cp_async_commit();
+    };
+    int cnt = 0, buf = 0;
+    stage(blockIdx.x, 0);
     for (int tile = blockIdx.x; tile < ntiles; tile += J.gx) {
-        for (int i = t; i < QR_TR * kxp; i += QR_THREADS) {
-            const int r = i / kxp, a = i - r * kxp;
-            const int row = tile * QR_TR + r;
-            float hh = 0.f, ll = 0.f;
-            if (row < n && a < kx) ld_split(X, (size_t)row * ldx + a, hh, ll);
-            xh[i] = hh;
-            xl[i] = ll;
-        }
-        if (!sym) {
-            for (int i = t; i < QR_TR * kzp; i += QR_THREADS) {
-                const int r = i / kzp, c = i - r * kzp;
-                const int row = tile * QR_TR + r;
-                float hh = 0.f, ll = 0.f;
-                if (row < n && c < kz) ld_split(Z, (size_t)row * ldz + c, hh, ll);
-                zh[i] = hh;
-                zl[i] = ll;
-            }
-        }
+        if (tile + J.gx < ntiles) stage(tile + J.gx, buf ^ 1);
+        else cp_async_commit();
+        cp_async_wait<1>();   // this thread's copies of `tile`
+        __syncthreads();
+        const unsigned char* sb = stg + (size_t)buf * (sxb + szb);
+        split_tile<TX>(sb, kx, kxp, xh, xl, QR_TR);
+        if (!sym) split_tile<TZ>(sb + sxb, kz, kzp, zh, zl, QR_TR);
+        buf ^= 1;
         __syncthreads();
         if (act) {
             for (int rr = g; rr < QR_TR; rr += G) {
@@ -152,6 +229,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
     }
     // reduce the row groups (fixed order) and write this CTA's partial
     double* red = reinterpret_cast<double*>(sgf);
+    cp_async_wait<0>();
     __syncthreads();
     if (act) {
 #pragma unroll
@@ -213,7 +291,8 @@ static cudaError_t gram_typed(long long ldx, int kx, long long ldz, int kz, bool
     const int ta = kxp / 4, tc = kzp / 4;
     const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
     const int chunks = (OT + QR_THREADS - 1) / QR_THREADS;
-    size_t smem = (size_t)QR_TR * (kxp + (sym ? 0 : kzp)) * 2 * sizeof(float);
+    size_t smem = (size_t)QR_TR * (kxp + (sym ? 0 : kzp)) * 2 * sizeof(float) +
+                  2 * (stage_bytes<TX>(QR_TR, kxp) + (sym ? 0 : stage_bytes<TZ>(QR_TR, kzp)));
     const size_t red = (size_t)QR_THREADS * 16 * sizeof(double);
     if (smem < red) smem = red;
     static bool attr = false;
@@ -374,16 +453,19 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
     const int rr = threadIdx.x / CG;
     const bool act = rr < RG;
     const int ntiles = (n + RG - 1) / RG;
+    // raw row tiles staged asynchronously one tile ahead (two buffers after the split arrays)
+    unsigned char* stg = reinterpret_cast<unsigned char*>(xl + (size_t)RG * kxp);
+    const size_t sxb = stage_bytes<TX>(RG, kxp);
+    int buf = 0;
+    if ((int)blockIdx.x < ntiles) stage_tile<TX>(stg, X, ldx, kx, kxp, n, blockIdx.x, RG);
+    cp_async_commit();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < RG * kxp; i += blockDim.x) {
-            const int r = i / kxp, a = i - r * kxp;
-            const int row = tile * RG + r;
-            float hh = 0.f, ll = 0.f;
-            if (row < n && a < kx) ld_split(X, (size_t)row * ldx + a, hh, ll);
-            xh[i] = hh;
-            xl[i] = ll;
-        }
+        if (tile + (int)gridDim.x < ntiles) stage_tile<TX>(stg + (size_t)(buf ^ 1) * sxb, X, ldx, kx, kxp, n, tile + gridDim.x, RG);
+        cp_async_commit();
+        cp_async_wait<1>();   // this thread's copies of `tile`
+        __syncthreads();      // ... everyone's, and every thread is done with the previous tile
+        split_tile<TX>(stg + (size_t)buf * sxb, kx, kxp, xh, xl, RG);
+        buf ^= 1;
         __syncthreads();
         const int row = tile * RG + rr;
         if (!act || row >= n) continue;
@@ -444,7 +526,7 @@ static cudaError_t rowprod_dispatch(int t2, long long ldx, int kx, int kc, long 
     const int cap = count > 1 ? 64 : 152 * 4;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) return cudaSuccess;
-    const size_t smem = ((size_t)2 * kx * kcp + (size_t)2 * RG * kxp) * sizeof(float);
+    const size_t smem = ((size_t)2 * kx * kcp + (size_t)2 * RG * kxp) * sizeof(float) + 2 * stage_bytes<TX>(RG, kxp);
     const dim3 gd(blocks, 1, count);
     switch (t2) {
         case T_F32: return rowprod_launch<TX, float, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, smem, s);
