@@ -39,7 +39,6 @@ namespace ll {
 
 namespace {
 
-constexpr int BT_CONSUMER_BAR = 1;   // named barrier of the consumer warps
 constexpr int BT_SIGQ = 64;          // finished tiles queued from the freeing warp to the releasing warp
 static_assert((BT_IRING & (BT_IRING - 1)) == 0 && BT_IRING % BT_TAKE == 0 && BT_TAKE <= 32, "take-ahead ring");
 
@@ -66,17 +65,6 @@ __device__ __forceinline__ unsigned int ld_acquire_cta(const unsigned int* p) {
 __device__ __forceinline__ void st_release_cta(unsigned int* p, unsigned int v) {
     asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
-// consumer-wide OR of a predicate (a named-barrier reduction)
-__device__ __forceinline__ bool consumer_any(int cthreads, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"(pred ? 1u : 0u), "r"(BT_CONSUMER_BAR), "r"(cthreads)
-        : "memory");
-    return r != 0;
-}
-
 // decodes ticket g into (step, matrix, tile) from the tables; x = -1 past the last item
 __device__ __forceinline__ int3 bt_decode(const int* t_off, const int* t_act, const int* t_pre, int max_m, int total, int g) {
     if (g >= total) return make_int3(-1, 0, 0);
@@ -541,9 +529,11 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
         };
         for (int k = 0;; ++k) {
             const int s = k % NST;
+            // a warp-wide vote (a consumer-wide one would couple the warps every tile): a warp whose
+            // wait ran out leaves; the others' waits run out in turn (every wait is bounded)
             const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((k / NST) & 1), budget);
-            if (consumer_any(cthreads, !ok)) {
-                if (tid == 0) atomicExch(bp.error, 1);
+            if (__any_sync(0xffffffffu, !ok)) {
+                if (lane == 0) atomicExch(bp.error, 1);
                 break;
             }
             const int j = sitem[s].j;
