@@ -1258,8 +1258,11 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         f.dots = total; total += al((size_t)(hs[i].m + 1) * b2 * sizeof(double));
         f.coef = total; total += al((size_t)2 * (hs[i].m + 1) * sizeof(double));
         // CholeskyQR2 of this matrix: Gram partials of its row blocks, ticket, Gram and R^{-1}
-        f.gxs = gram_blocks(kq, kq, true, (int)n, ggrid);
-        f.gxc = gram_blocks(kq, kg, false, (int)n, ggrid);
+        // Gram row blocks: this matrix's share of about four CTAs per SM over the whole batch (a
+        // grid sized for one matrix, 64 times over, spent the time in per-CTA reductions)
+        const int gshare = (int)std::max(1.0, std::ceil(4.0 * ggrid * (double)n / tot_n));
+        f.gxs = gram_blocks(kq, kq, true, (int)n, gshare);
+        f.gxc = gram_blocks(kq, kg, false, (int)n, gshare);
         const size_t qp = std::max(gram_partials_doubles(kq, kq, true, f.gxs), gram_partials_doubles(kq, kg, false, f.gxc));
         f.qpart = total; total += al(qp * sizeof(double));
         f.gram = total; total += al((size_t)kq * kg * sizeof(double));

@@ -523,7 +523,7 @@ static cudaError_t rowprod_dispatch(int t2, long long ldx, int kx, int kc, long 
     const int RG = QR_THREADS / CG;
     if (RG < 1 || count < 1) return cudaErrorInvalidValue;
     int blocks = (n_max + RG - 1) / RG;
-    const int cap = count > 1 ? 64 : 152 * 4;
+    const int cap = 152 * 4;   // per matrix: the largest matrix of a batch sets the time; CTAs past a matrix's tiles leave
     if (blocks > cap) blocks = cap;
     if (blocks < 1) return cudaSuccess;
     const size_t smem = ((size_t)2 * kx * kcp + (size_t)2 * RG * kxp) * sizeof(float) + 2 * stage_bytes<TX>(RG, kxp);
