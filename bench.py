@@ -336,6 +336,44 @@ def workload_config5(L, h, log2n: int = 22, degree: int = 150, probes: int = 120
     return out
 
 
+def workload_f3(L, h, n: int = 10_000_000, probes: int = 30):
+    """Section 5.1's synthetic pentadiagonal SPD family at the paper's largest size: five
+    diagonals U[0,1] (seed 0), Q + Q^T + n I, n = 10^7. Gershgorin bounds (lambda_min >= 1, so
+    sigma = 1), degree from the bounds, Hutch++ with 30 Rademacher probes (seed 0). Throughput,
+    and the error against the banded-Cholesky log-determinant (the error is Hutch++'s residual
+    variance on a spectrum close to n I; the interpolant is exact to rounding)."""
+    import math as _m
+    import time as _t
+    from synth import pentadiagonal
+    from tests.pins import logdet_banded
+    t0 = _t.perf_counter()
+    A = pentadiagonal(n, seed=0)
+    t_gen = _t.perf_counter() - t0
+    exact = logdet_banded(A)
+    nnz, k = A.nnz, probes // 3
+    out = {"n": n, "nnz": nnz, "generate_s": t_gen, "exact_logdet": exact}
+    for prec in ("df64", "f32"):
+        dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+        lo, hi = L.ll_gershgorin(h, dA)
+        sg = lo if lo < 1 else 1.0
+        kap = (hi / sg) / (lo / sg)
+        rho = (_m.sqrt(kap) + 1) / (_m.sqrt(kap) - 1)
+        m = max(10, min(250, _m.ceil(_m.log(1e6) / _m.log(rho))))
+        opts = L.options(degree=m, probes=probes, seed=0, precision=prec)
+        ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lo, hi, opts), 3, 1)
+        inf = h.info()
+        out[prec] = {"ms_per_estimate": ms, "degree": m, "bounds": [lo, hi], "estimate": est,
+                     "rel_err_vs_exact": abs(est - exact) / abs(exact),
+                     "GBps_estimate": estimate_bytes(n, nnz, k, m, prec) / (ms / 1e3) / 1e9,
+                     "pass1_launch_GBps": step_bytes(n, nnz, k, prec, "accum") / (inf["ms_pass1"] / m / 1e3) / 1e9,
+                     "pass2_launch_GBps": step_bytes(n, nnz, 2 * k, prec, "dot") / (inf["ms_pass2"] / m / 1e3) / 1e9,
+                     "kernels": [inf["kernel_pass1"], inf["kernel_pass2"]],
+                     "phase_ms": {"probes": inf["ms_probes"], "pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
+        del dA
+    out["workload"] = f"pentadiagonal U[0,1] diagonals, Q + Q^T + n I, n={n}, nnz={nnz}, seed 0, {probes} Rademacher probes"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,8 +391,8 @@ def main():
                     help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
                     help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
-    ap.add_argument("--workloads", default="c1,c3,c4",
-                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5; '' for none)")
+    ap.add_argument("--workloads", default="c1,c3,c4,f3",
+                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5,f3; '' for none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -476,7 +514,8 @@ def main():
         return
     extra = {}
     for w in [x for x in args.workloads.split(",") if x]:
-        fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4, "c5": workload_config5}[w]
+        fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4, "c5": workload_config5,
+              "f3": workload_f3}[w]
         extra[w] = fn(L, h, log2n=args.c5_log2n) if w == "c5" else fn(L, h)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
     from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only

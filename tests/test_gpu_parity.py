@@ -171,6 +171,31 @@ def test_forward_probes_ge_n(L, h):
     assert abs(got - want) < 1e-10 * abs(want) + 1e-12
 
 
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+def test_forward_pentadiagonal_matches_oracle(L, h, prec):
+    """Section 5.1's synthetic pentadiagonal family (n = 4000, Gershgorin bounds, degree from the
+    bounds, 30 Rademacher probes): the GPU estimate matches the oracle on the same probes."""
+    from synth import pentadiagonal
+    A = pentadiagonal(4000, seed=4)
+    lo, hi = O.gershgorin(A)
+    m = O.degree_from_bounds(lo, hi)   # sigma = 1: lambda_min >= 1
+    got = _forward(L, h, A, lo, hi, m, 30, 1, prec)
+    want = O.logdet_leja(A, lo, hi, m, 30, 1, f32=(prec == "f32"))["estimate"]
+    assert abs(got - want) / abs(want) < TOL[prec]
+
+
+def test_forward_pentadiagonal_exact_trace_equals_banded_cholesky(L, h):
+    """With as many sketch columns as rows (the Q = I branch) the GPU estimate is the exact
+    polynomial trace, which on this spectrum equals the banded-Cholesky log-determinant."""
+    from synth import pentadiagonal
+    from tests import pins
+    A = pentadiagonal(90, seed=2)
+    lo, hi = O.gershgorin(A)
+    m = O.degree_from_bounds(lo, hi)
+    got = _forward(L, h, A, lo, hi, m, 270, 5, "df64")
+    assert got == pytest.approx(pins.logdet_banded(A), rel=1e-11)
+
+
 def test_forward_empty_matrix(L, h):
     A = CSR(n=0, rowptr=np.zeros(1, dtype=np.int32), colind=np.zeros(0, dtype=np.int32), values=np.zeros(0))
     torch = need_gpu()

@@ -32,3 +32,20 @@ def test_powerlaw_is_a_shifted_laplacian():
         assert np.all(np.diff(c) > 0)
     # mean stored entries per row about mean degree + 1 (duplicates merged)
     assert 12.0 < A.nnz / A.n < 17.5
+
+
+def test_pentadiagonal_family():
+    """Section 5.1's synthetic matrices: symmetric, entries within two of the diagonal, diagonal
+    dominant with the n I shift, seeded."""
+    from synth import pentadiagonal
+    A = pentadiagonal(500, seed=4)
+    M = A.to_scipy()
+    assert (abs(M - M.T)).max() == 0.0
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    assert np.abs(A.colind - rows).max() == 2
+    assert A.nnz == 5 * A.n - 6
+    d = M.diagonal()
+    off = np.asarray(abs(M).sum(axis=1)).ravel() - d
+    assert np.all(d - off > 0) and d.min() >= A.n
+    B = pentadiagonal(500, seed=4)
+    assert np.array_equal(A.values, B.values) and not np.array_equal(A.values, pentadiagonal(500, seed=5).values)
