@@ -12,7 +12,14 @@
 namespace ll {
 
 constexpr int QR_THREADS = 256;
-constexpr int QR_TR = 32;       // rows per shared-memory tile of the Gram kernel
+// Rows per shared-memory tile of the Gram kernel: about 1152 staged elements (32 rows at k = 33),
+// more rows for narrow blocks so that a tile carries enough loads and products to hide its
+// latency (k = 10: 96 rows), between 32 and 256 in multiples of 16.
+__host__ __device__ inline int gram_tile_rows(int kxp, int kzp, bool sym) {
+    const int cols = kxp + (sym ? 0 : kzp);
+    int tr = (1152 / cols) / 16 * 16;
+    return tr < 32 ? 32 : (tr > 256 ? 256 : tr);
+}
 constexpr int QR_FLUSH = 8;     // tiles summed in double-float before an FP64 flush
 
 // A double as an unevaluated float pair hi + lo, from its bit fields with integer operations and
@@ -114,7 +121,7 @@ __device__ __forceinline__ void ld_split(const dfp* p, size_t i, float& h, float
 
 // X^T Z over n rows in double-float arithmetic on the FP32 pipes (GB300's FP64 pipe runs at 1/62
 // of FP32). Each thread owns a 4x4 register tile of the output and a group of rows; per-thread
-// double-float sums cover QR_FLUSH * QR_TR rows at most before they are added into FP64
+// double-float sums cover QR_FLUSH tiles (at most 2048 rows) before they are added into FP64
 // accumulators, so the error stays near FP64's. Per-CTA partials are reduced by the last CTA in
 // a fixed order. sym: Z == X and only the upper-triangular 4x4 tiles are computed.
 template <typename TX, typename TZ>
@@ -133,10 +140,11 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
     double* out = J.out;
     const int kxp = (kx + 3) & ~3;
     const int kzp = sym ? kxp : ((kz + 3) & ~3);
+    const int trows = gram_tile_rows(kxp, kzp, sym != 0);
     float* xh = sgf;
-    float* xl = xh + QR_TR * kxp;
-    float* zh = sym ? xh : xl + QR_TR * kxp;
-    float* zl = sym ? xl : zh + QR_TR * kzp;
+    float* xl = xh + trows * kxp;
+    float* zh = sym ? xh : xl + trows * kxp;
+    float* zl = sym ? xl : zh + trows * kzp;
     const int ta = kxp / 4, tc = kzp / 4;
     const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
     const int otc = min(OT, QR_THREADS);
@@ -164,15 +172,15 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
     for (int e = 0; e < 8; ++e) { h2[e] = 0ull; l2[e] = 0ull; }
 #pragma unroll
     for (int e = 0; e < 16; ++e) a64[e] = 0.0;
-    const int ntiles = (n + QR_TR - 1) / QR_TR;
+    const int ntiles = (n + trows - 1) / trows;
     // raw tiles staged asynchronously one tile ahead (two buffers after the split arrays), so that
     // the next tile's loads are in flight while this one is computed
-    unsigned char* stg = reinterpret_cast<unsigned char*>(zl + QR_TR * kzp);
-    const size_t sxb = stage_bytes<TX>(QR_TR, kxp), szb = sym ? 0 : stage_bytes<TZ>(QR_TR, kzp);
+    unsigned char* stg = reinterpret_cast<unsigned char*>(zl + trows * kzp);
+    const size_t sxb = stage_bytes<TX>(trows, kxp), szb = sym ? 0 : stage_bytes<TZ>(trows, kzp);
     auto stage = [&](int tile, int b) {
         unsigned char* sb = stg + (size_t)b * (sxb + szb);
-        stage_tile<TX>(sb, X, ldx, kx, kxp, n, tile, QR_TR);
-        if (!sym) stage_tile<TZ>(sb + sxb, Z, ldz, kz, kzp, n, tile, QR_TR);
+        stage_tile<TX>(sb, X, ldx, kx, kxp, n, tile, trows);
+        if (!sym) stage_tile<TZ>(sb + sxb, Z, ldz, kz, kzp, n, tile, trows);
         cp_async_commit();
     };
     int cnt = 0, buf = 0;
@@ -183,12 +191,12 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
         cp_async_wait<1>();   // this thread's copies of `tile`
         __syncthreads();
         const unsigned char* sb = stg + (size_t)buf * (sxb + szb);
-        split_tile<TX>(sb, kx, kxp, xh, xl, QR_TR);
-        if (!sym) split_tile<TZ>(sb + sxb, kz, kzp, zh, zl, QR_TR);
+        split_tile<TX>(sb, kx, kxp, xh, xl, trows);
+        if (!sym) split_tile<TZ>(sb + sxb, kz, kzp, zh, zl, trows);
         buf ^= 1;
         __syncthreads();
         if (act) {
-            for (int rr = g; rr < QR_TR; rr += G) {
+            for (int rr = g; rr < trows; rr += G) {
                 const float4 a4h = *reinterpret_cast<const float4*>(&xh[rr * kxp + ia * 4]);
                 const float4 a4l = *reinterpret_cast<const float4*>(&xl[rr * kxp + ia * 4]);
                 const float4 c4h = *reinterpret_cast<const float4*>(&zh[rr * kzp + ic * 4]);
@@ -291,8 +299,9 @@ static cudaError_t gram_typed(long long ldx, int kx, long long ldz, int kz, bool
     const int ta = kxp / 4, tc = kzp / 4;
     const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
     const int chunks = (OT + QR_THREADS - 1) / QR_THREADS;
-    size_t smem = (size_t)QR_TR * (kxp + (sym ? 0 : kzp)) * 2 * sizeof(float) +
-                  2 * (stage_bytes<TX>(QR_TR, kxp) + (sym ? 0 : stage_bytes<TZ>(QR_TR, kzp)));
+    const int trows = gram_tile_rows(kxp, kzp, sym);
+    size_t smem = (size_t)trows * (kxp + (sym ? 0 : kzp)) * 2 * sizeof(float) +
+                  2 * (stage_bytes<TX>(trows, kxp) + (sym ? 0 : stage_bytes<TZ>(trows, kzp)));
     const size_t red = (size_t)QR_THREADS * 16 * sizeof(double);
     if (smem < red) smem = red;
     static bool attr = false;
@@ -313,7 +322,8 @@ int gram_blocks(int kx, int kz, bool sym, int n, int grid) {
     const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
     const int chunks = (OT + QR_THREADS - 1) / QR_THREADS;
     int gx = grid / chunks;
-    const int ntiles = (n + QR_TR - 1) / QR_TR;
+    const int trows = gram_tile_rows(kxp, kzp, sym);
+    const int ntiles = (n + trows - 1) / trows;
     const int by_rows = (ntiles + 3) / 4;
     if (gx > by_rows) gx = by_rows;
     return gx < 1 ? 1 : gx;
