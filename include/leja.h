@@ -64,6 +64,14 @@ enum { LL_PREC_F64 = 0, LL_PREC_DF64 = 1, LL_PREC_F32_MIXED = 2 };
 
 enum { LL_PROBE_RADEMACHER = 0, LL_PROBE_GAUSSIAN = 1 };
 
+/* Trace estimator of ll_logdet_forward:
+ *   LL_EST_HUTCHPP     Hutch++ (Section 4.1, Algorithm 3): probes/3 sketch columns, a QR, and
+ *                      the deflated Hutchinson part;
+ *   LL_EST_HUTCHINSON  plain Hutchinson (Eq. Léja8): estimate = n log sigma +
+ *                      (1/m) sum_i g_i^T p(A~) g_i over m = probes vectors from stream
+ *                      LL_STREAM_G (1 <= m <= 192), with no sketch and no QR. */
+enum { LL_EST_HUTCHPP = 0, LL_EST_HUTCHINSON = 1 };
+
 /* s_val of Algorithm 1: the Lemma 3.1 optimum c = (lmin+lmax)/2, or lmax/2. */
 enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
 
@@ -94,7 +102,8 @@ typedef struct {
 
 typedef struct {
     int degree;                /* m: m+1 Léja points, m operator applications per pass          */
-    int probes;                /* m_vec, a positive multiple of 3; k = m_vec / 3                */
+    int probes;                /* m_vec: Hutch++, a positive multiple of 3 (k = m_vec / 3);
+                                  Hutchinson, the number of probe vectors (1 to 192)            */
     uint64_t seed;             /* probe seed                                                     */
     int probe_kind;            /* LL_PROBE_RADEMACHER or LL_PROBE_GAUSSIAN                      */
     int precision;             /* LL_PREC_*                                                      */
@@ -110,6 +119,7 @@ typedef struct {
                                   the call fails with LL_ERR_TIMEOUT; 0 = about 2 s. Also bounds
                                   the pipeline waits of the TMA step kernel.                     */
     int step_kernel;           /* LL_KERNEL_* (default LL_KERNEL_AUTO)                           */
+    int estimator;             /* LL_EST_HUTCHPP (default) or LL_EST_HUTCHINSON                  */
 } ll_options;
 
 typedef struct ll_handle ll_handle;
@@ -231,8 +241,11 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
  *   S, G: n x k probes (k = probes/3; streams LL_STREAM_S, LL_STREAM_G);
  *   Y = p(A~) S; Q = CholeskyQR2(Y) (FP64); G' = G - Q (Q^T G);
  *   estimate = n log sigma + tr(Q^T p(A~) Q) + (1/k) tr(G'^T p(A~) G').
+ * With opts->estimator = LL_EST_HUTCHINSON the call skips S, pass 1 and the QR and applies p(A~)
+ * to G (probes columns) in the trace pass: estimate = n log sigma + (1/m) tr(G^T p(A~) G).
  * The matrix is device-resident (A). *estimate: host; synchronises `stream`.
- * With opts->keep_for_backward the handle keeps [Q | G'] for ll_logdet_backward. */
+ * With opts->keep_for_backward the handle keeps [Q | G'] (Hutchinson: G) for ll_logdet_backward;
+ * ll_kept_basis returns LL_ERR_UNSUPPORTED after a Hutchinson forward. */
 ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, const ll_options* opts,
                             double* estimate, void* stream);
 

@@ -9,6 +9,7 @@ Follows arXiv 2603.02207:
   * Algorithm 2 (Newton-Léja action p(Q~)v), applied column by column, fixed degree;
   * Hutch++ as in Algorithm 3 / Section 4.1 (sketch, Householder QR, deterministic part,
     Hutchinson part on the deflated probes);
+  * the plain Hutchinson estimator the paper starts from (Eq. Léja8), on the same probes;
   * the derivative of the frozen-basis estimator with respect to the stored matrix values.
 
 Readings fixed by this library where the paper is silent or ambiguous:
@@ -208,6 +209,35 @@ def logdet_leja(A, lmin: float, lmax: float, degree: int, probes: int, seed: int
     k = probes // 3
     S, G = make_probes(A.n, k, seed, kind)
     return hutchpp_logdet(A, lmin, lmax, degree, S, G, s_mode, f32)
+
+
+# ---------------------------------------------------------------------------------------------
+# plain Hutchinson (Eq. Léja8)
+# ---------------------------------------------------------------------------------------------
+
+def hutchinson_logdet(A, lmin: float, lmax: float, degree: int, G: np.ndarray, s_mode: str = "center",
+                      f32: bool = False) -> dict:
+    """Eq. Léja8 with the sigma-normalisation: log det A ~ n log sigma + (1/m) sum_j g_j^T F g_j
+    over the m columns g_j of G, F = p(A / sigma)."""
+    n = A.n
+    m = G.shape[1]
+    sigma = sigma_of(lmin)
+    lt, ut = lmin / sigma, lmax / sigma
+    xi, c, gamma, d, p_terms = newton_leja_setup(lt, ut, degree, s_mode)
+    Gin = _round32(G) if f32 else G
+    FG = leja_apply_columns(_scipy(A), Gin, xi, d, c, gamma, sigma, f32)
+    t = float(np.sum(Gin * FG)) / m
+    return dict(estimate=n * math.log(sigma) + t, trace_res=t, sigma=sigma, c=c, gamma=gamma, xi=xi, d=d,
+                taylor_terms=p_terms)
+
+
+def logdet_hutchinson(A, lmin: float, lmax: float, degree: int, probes: int, seed: int,
+                      kind: str = "rademacher", s_mode: str = "center", f32: bool = False) -> dict:
+    """Eq. Léja8 over `probes` vectors of the G stream (the columns Algorithm 3 uses for G)."""
+    if probes <= 0:
+        raise ValueError("probes must be positive")
+    G = _rng.probes(kind, seed, _rng.STREAM_G, A.n, probes)
+    return hutchinson_logdet(A, lmin, lmax, degree, G, s_mode, f32)
 
 
 # ---------------------------------------------------------------------------------------------

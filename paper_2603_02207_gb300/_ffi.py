@@ -24,6 +24,7 @@ LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
 LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA = 0, 1, 2
+LL_EST_HUTCHPP, LL_EST_HUTCHINSON = 0, 1
 LL_INJECT_NONE, LL_INJECT_STALL = 0, 1
 LL_NOALLOC_MAX_ROWS = 1 << 18
 
@@ -42,7 +43,7 @@ class ll_options(ctypes.Structure):
                 ("probe_kind", ctypes.c_int), ("precision", ctypes.c_int), ("sval_mode", ctypes.c_int),
                 ("keep_for_backward", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int)]
+                ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int), ("estimator", ctypes.c_int)]
 
 
 class ll_info(ctypes.Structure):

@@ -11,13 +11,14 @@ import dataclasses
 import numpy as np
 
 from . import _ffi
-from ._ffi import (LL_F32, LL_F64, LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA,  # noqa: F401
+from ._ffi import (LL_EST_HUTCHINSON, LL_EST_HUTCHPP, LL_F32, LL_F64, LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA,  # noqa: F401
                    LL_PREC_DF64, LL_PREC_F32_MIXED, LL_PREC_F64, LL_PROBE_GAUSSIAN, LL_PROBE_RADEMACHER, LL_STREAM_G, LL_STREAM_POWER, LL_STREAM_S,
                    LL_SVAL_CENTER, LL_SVAL_HALF_LMAX)
 
 PRECISIONS = {"f64": LL_PREC_F64, "df64": LL_PREC_DF64, "f32": LL_PREC_F32_MIXED}
 PROBE_KINDS = {"rademacher": LL_PROBE_RADEMACHER, "gaussian": LL_PROBE_GAUSSIAN}
 STEP_KERNELS = {"auto": LL_KERNEL_AUTO, "gather": LL_KERNEL_GATHER, "tma": LL_KERNEL_TMA}
+ESTIMATORS = {"hutchpp": LL_EST_HUTCHPP, "hutchinson": LL_EST_HUTCHINSON}
 
 
 class LejaError(RuntimeError):
@@ -123,7 +124,8 @@ def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
 def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str = "rademacher",
             precision: str = "df64", sval_mode: int = LL_SVAL_CENTER, keep_for_backward: bool = False,
             rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
-            use_graph: bool = True, timeout_cycles: int = 0, step_kernel: str = "auto") -> _ffi.ll_options:
+            use_graph: bool = True, timeout_cycles: int = 0, step_kernel: str = "auto",
+            estimator: str = "hutchpp") -> _ffi.ll_options:
     o = _ffi.ll_options()
     _ffi.load().ll_default_options(ctypes.byref(o))
     o.degree = degree
@@ -139,6 +141,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
     o.use_graph = int(use_graph)
     o.timeout_cycles = timeout_cycles
     o.step_kernel = STEP_KERNELS[step_kernel]
+    o.estimator = ESTIMATORS[estimator]
     return o
 
 

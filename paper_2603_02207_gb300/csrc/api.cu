@@ -72,6 +72,7 @@ struct ll_handle {
     bool kept = false;
     int64_t kept_n = 0, kept_nnz = 0;
     int kept_kq = 0, kept_kg = 0, kept_m = 0, kept_prec = 0, kept_ckpt = 0;
+    bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
     double kept_sigma = 1, kept_c = 0, kept_gamma = 1;
     std::vector<double> kept_d, kept_xi;
 };
@@ -456,6 +457,7 @@ void ll_default_options(ll_options* o) {
     o->use_graph = 1;
     o->timeout_cycles = 0;
     o->step_kernel = LL_KERNEL_AUTO;
+    o->estimator = LL_EST_HUTCHPP;
 }
 
 ll_status ll_debug_inject(ll_handle* h, int what) {
@@ -619,7 +621,10 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if ((st = check_bounds(h, bounds)) != LL_OK) return st;
     const ll_options& o = *opts;
     if (o.degree < 1) return fail(h, LL_ERR_INVALID_ARG, "degree must be >= 1");
-    if (o.probes <= 0 || o.probes % 3 != 0) return fail(h, LL_ERR_INVALID_ARG, "probes must be a positive multiple of 3");
+    if (o.estimator != LL_EST_HUTCHPP && o.estimator != LL_EST_HUTCHINSON) return fail(h, LL_ERR_INVALID_ARG, "unknown estimator");
+    const bool hutch = o.estimator == LL_EST_HUTCHINSON;   // plain Hutchinson: no sketch, no QR
+    if (hutch ? o.probes <= 0 : (o.probes <= 0 || o.probes % 3 != 0))
+        return fail(h, LL_ERR_INVALID_ARG, hutch ? "probes must be positive" : "probes must be a positive multiple of 3");
     if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
     if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
     if (o.sval_mode != LL_SVAL_CENTER && o.sval_mode != LL_SVAL_HALF_LMAX) return fail(h, LL_ERR_INVALID_ARG, "unknown s_val mode");
@@ -632,9 +637,10 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         *estimate = 0.0;
         return LL_OK;
     }
-    const int kg = o.probes / 3;
-    const int kq = kg < n ? kg : n;
+    const int kg = hutch ? o.probes : o.probes / 3;
+    const int kq = hutch ? 0 : (kg < n ? kg : n);
     const int b2 = kq + kg;
+    if (hutch && kg > 192) return fail(h, LL_ERR_UNSUPPORTED, "more than 192 Hutchinson probes are not supported");
     if (b2 > 512 || kq > 96) return fail(h, LL_ERR_UNSUPPORTED, "m_vec / 3 above 96 is not supported");
     if ((st = validate_csr(h, A, s)) != LL_OK) return st;
 
@@ -689,13 +695,25 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         LL_CK(cudaMemsetAsync(qrstat, 0, sizeof(int), q));
         // matrix values scaled by 1 / (sigma gamma): B = (A/sigma - c I)/gamma = prepared - (c/gamma) I
         LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, q));
-        // Algorithm 3 step 2 (S) and step 6 (G)
-        LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, l1, S, l1, q));
-        LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, q));
-        h->launches += 3;
-        LL_CK(rec(h->ev[1], q));
+        if (hutch) {
+            // plain Hutchinson (Eq. Léja8): G straight into the trace pass's block (the pad
+            // column zeroed); no pass 1 and no QR
+            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_G, n, kg, l2, V, l2, q));
+            h->launches += 2;
+            LL_CK(rec(h->ev[1], q));
+            LL_CK(rec(h->ev[2], q));
+            LL_CK(rec(h->ev[3], q));
+        } else {
+            // Algorithm 3 step 2 (S) and step 6 (G)
+            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, l1, S, l1, q));
+            LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, q));
+            h->launches += 3;
+            LL_CK(rec(h->ev[1], q));
+        }
 
-        if (kq == n) {
+        if (hutch) {
+            // the trace pass below is the whole estimator
+        } else if (kq == n) {
             // k >= n: the sketch spans R^n, so Q = I is an orthonormal basis of span(Y) and
             // G' = (I - Q Q^T) G = 0; the estimate is the exact trace of p(A~)
             LL_CK(rec(h->ev[2], q));
@@ -864,6 +882,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_nnz = A->nnz;
         h->kept_kq = kq;
         h->kept_kg = kg;
+        h->kept_hutch = hutch;
         h->kept_m = m;
         h->kept_prec = prec;
         h->kept_ckpt = o.ckpt_stride;
@@ -1144,6 +1163,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     if (count == 0) return LL_OK;
     const ll_options& o = *opts;
     if (o.probes <= 0 || o.probes % 3 != 0) return fail(h, LL_ERR_INVALID_ARG, "probes must be a positive multiple of 3");
+    if (o.estimator != LL_EST_HUTCHPP) return fail(h, LL_ERR_UNSUPPORTED, "the batched call runs Hutch++ only");
     if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
     if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1603,6 +1623,7 @@ ll_status ll_kept_basis(const ll_handle* h, double* out, int64_t ld, int64_t* n_
                         void* stream) {
     if (!h) return LL_ERR_INVALID_ARG;
     if (!h->kept) return LL_ERR_NO_FORWARD;
+    if (h->kept_hutch) return LL_ERR_UNSUPPORTED;   // no sketch basis in a Hutchinson forward
     auto it = h->ws.find("fw_basis");
     if (it == h->ws.end()) return LL_ERR_NO_FORWARD;
     const int b2 = h->kept_kq + h->kept_kg;

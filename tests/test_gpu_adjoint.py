@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import logdet as O
+from oracle import rng as ORNG
 from synth import laplacian_2d, matern_2d, matern_2d_derivatives, random_spd
 from tests import pins
 from tests.gpu_util import TOL, lib, need_gpu, rel_err
@@ -105,3 +106,26 @@ def test_backward_without_forward_is_an_error(L):
     with pytest.raises(L.LejaError) as ei:
         L.ll_logdet_backward(h2, L.DeviceCSR.from_host(A), 1.0)
     assert ei.value.name == "LL_ERR_NO_FORWARD"
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+def test_backward_hutchinson_matches_oracle_gradient(L, h, prec):
+    """Plain Hutchinson (Eq. Léja8): the kept block is G itself (no sketch), and the adjoint's
+    per-column weight is d_j / m, so the value gradients equal the oracle's frozen-probe
+    gradient with an empty basis and U = G / m."""
+    A = random_spd(500, nnz_per_row=6, seed=8, empty_rows=2)
+    lo, hi = O.gershgorin(A)
+    lmin = max(lo, 0.05)
+    m, probes, seed = 21, 14, 3
+    dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+    opts = L.options(degree=m, probes=probes, seed=seed, precision=prec, keep_for_backward=True, estimator="hutchinson")
+    est = L.ll_logdet_forward(h, dA, lmin, hi, opts)
+    g = L.ll_logdet_backward(h, dA, 1.0).cpu().numpy()
+    want_est = O.logdet_hutchinson(A, lmin, hi, m, probes, seed, f32=(prec == "f32"))["estimate"]
+    assert abs(est - want_est) / abs(want_est) < (1e-10 if prec != "f32" else 2e-5)
+    G = ORNG.probes("rademacher", seed, ORNG.STREAM_G, A.n, probes)
+    want = O.hutchpp_grad_values(A, lmin, hi, m, np.zeros((A.n, 0)), G)
+    assert rel_err(g, want) < (1e-9 if prec != "f32" else 1e-4)
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_kept_basis(h)
+    assert ei.value.name == "LL_ERR_UNSUPPORTED"

@@ -196,6 +196,41 @@ def test_forward_pentadiagonal_exact_trace_equals_banded_cholesky(L, h):
     assert got == pytest.approx(pins.logdet_banded(A), rel=1e-11)
 
 
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("kind", ["rademacher", "gaussian"])
+def test_forward_hutchinson_matches_oracle(L, h, prec, kind):
+    """Plain Hutchinson (Eq. Léja8, `estimator="hutchinson"`): no sketch and no QR; the GPU
+    estimate over 25 probes of the G stream matches the oracle's."""
+    A = matern_2d(40, 0.3, 1.0)
+    lo, hi = O.gershgorin(A)
+    lmin = 0.0081
+    dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+    got = L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=50, probes=25, seed=2, precision=prec, probe_kind=kind,
+                                                         estimator="hutchinson"))
+    info = h.info()
+    want = O.logdet_hutchinson(A, lmin, hi, 50, 25, 2, kind=kind, f32=(prec == "f32"))["estimate"]
+    assert abs(got - want) / abs(want) < TOL[prec]
+    assert info["k"] == 0 and info["ms_qr"] < 0.05
+
+
+def test_forward_hutchinson_exact_on_diagonal_and_limits(L, h):
+    """Rademacher Hutchinson is exact on a diagonal matrix for any probe count; probe counts
+    need not be multiples of 3; more than 192 probes are refused, and the batched call runs
+    Hutch++ only."""
+    dvals = np.linspace(0.3, 5.0, 333)
+    A = diagonal(dvals)
+    dA = L.DeviceCSR.from_host(A)
+    got = L.ll_logdet_forward(h, dA, 0.3, 5.0, L.options(degree=30, probes=4, seed=9, estimator="hutchinson"))
+    want = O.logdet_hutchinson(A, 0.3, 5.0, 30, 4, 9)["estimate"]
+    assert got == pytest.approx(want, rel=1e-10)
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_logdet_forward(h, dA, 0.3, 5.0, L.options(degree=30, probes=193, estimator="hutchinson"))
+    assert ei.value.name == "LL_ERR_UNSUPPORTED"
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_logdet_batched(h, [dA], [(0.3, 5.0)], L.options(probes=30, estimator="hutchinson"))
+    assert ei.value.name == "LL_ERR_UNSUPPORTED"
+
+
 def test_forward_empty_matrix(L, h):
     A = CSR(n=0, rowptr=np.zeros(1, dtype=np.int32), colind=np.zeros(0, dtype=np.int32), values=np.zeros(0))
     torch = need_gpu()

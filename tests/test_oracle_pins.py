@@ -463,3 +463,37 @@ def test_hutchpp_pentadiagonal_residual_variance():
     exact = pins.logdet_banded(A)
     errs = [abs(logdet.logdet_leja(A, lo, hi, m, probes, seed)["estimate"] - exact) for probes, seed in ((30, 1), (30, 2), (30, 3))]
     assert max(errs) < 6.0 * math.log(A.n) * math.sqrt(2.0)
+
+
+def test_hutchinson_all_sign_vectors_is_the_exact_polynomial_trace():
+    """Eq. Léja8: the mean of g^T F g over all 2^n sign vectors is tr F exactly (the cross terms
+    cancel pairwise), so with every sign vector as a probe the estimate is n log sigma +
+    sum_i p(lambda_i / sigma), computed here from a dense eigendecomposition."""
+    import itertools
+    A = random_spd(8, seed=3)
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    lmin, lmax = 0.9 * lam[0], 1.1 * lam[-1]
+    G = np.array(list(itertools.product([-1.0, 1.0], repeat=A.n))).T   # 8 x 256
+    r = logdet.hutchinson_logdet(A, lmin, lmax, 25, G)
+    sigma = logdet.sigma_of(lmin)
+    p = pins.interpolant(lmin / sigma, lmax / sigma, leja.fast_leja_points(26))
+    assert r["estimate"] == pytest.approx(A.n * math.log(sigma) + float(np.sum(p(lam / sigma))), rel=1e-12)
+
+
+def test_hutchinson_rademacher_exact_on_diagonal_matrices():
+    """For a diagonal matrix every Rademacher probe gives g^T F g = tr F (g_i^2 = 1)."""
+    dvals = np.linspace(0.3, 5.0, 57)
+    A = diagonal(dvals)
+    r = logdet.logdet_hutchinson(A, 0.3, 5.0, 30, 3, seed=9)
+    sigma = logdet.sigma_of(0.3)
+    p = pins.interpolant(0.3 / sigma, 5.0 / sigma, leja.fast_leja_points(31))
+    assert r["estimate"] == pytest.approx(A.n * math.log(sigma) + float(np.sum(p(dvals / sigma))), rel=1e-12)
+
+
+def test_hutchinson_uses_the_g_stream_columns():
+    """The Hutchinson probes are the first columns of Algorithm 3's G stream."""
+    A = laplacian_2d(10, 0.5)
+    G = rng.probes("gaussian", 4, rng.STREAM_G, A.n, 6)
+    a = logdet.hutchinson_logdet(A, 0.5, 8.5, 20, G)["estimate"]
+    b = logdet.logdet_hutchinson(A, 0.5, 8.5, 20, 6, 4, kind="gaussian")["estimate"]
+    assert a == b
