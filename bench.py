@@ -374,6 +374,44 @@ def workload_f3(L, h, n: int = 10_000_000, probes: int = 30):
     return out
 
 
+def workload_f1(L, h, A, grid: int, degree: int, seeds: int = 3):
+    """Plain Hutchinson (Eq. Léja8) beside Hutch++ on the headline 3-D Laplacian at the same
+    matvec budget (99 probes): Hutchinson runs the 99 probes through the trace step alone (width
+    99, no pass 1 and no QR), Hutch++ runs 33 columns in pass 1 and 66 in pass 2. Time, bytes per
+    estimate, and the error against the closed form over a few probe seeds."""
+    from tests.pins import logdet_laplacian_3d
+    exact = logdet_laplacian_3d(grid, SHIFT)
+    n, nnz, m = A.n, A.nnz, degree
+    out = {"exact_logdet": exact}
+    for prec in ("df64", "f32"):
+        dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+        row = {}
+        for name in ("hutchinson", "hutchpp"):
+            ms_l, errs = [], []
+            for s in range(seeds):
+                opts = L.options(degree=m, probes=PROBES, seed=SEED + s, precision=prec, estimator=name)
+                ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, *BOUNDS, opts), 3, 1)
+                ms_l.append(ms)
+                errs.append(abs(est - exact) / abs(exact))
+            inf = h.info()
+            if name == "hutchinson":
+                b = m * step_bytes(n, nnz, PROBES, prec, "dot")
+                p2 = step_bytes(n, nnz, PROBES, prec, "dot") / (inf["ms_pass2"] / m / 1e3) / 1e9
+            else:
+                b = estimate_bytes(n, nnz, PROBES // 3, m, prec)
+                p2 = step_bytes(n, nnz, 2 * (PROBES // 3), prec, "dot") / (inf["ms_pass2"] / m / 1e3) / 1e9
+            ms = statistics.median(ms_l)
+            row[name] = {"ms_per_estimate": ms, "GBps_estimate": b / (ms / 1e3) / 1e9, "pass2_launch_GBps": p2,
+                         "rel_err_vs_exact": errs, "seeds": list(range(SEED, SEED + seeds)),
+                         "phase_ms": {"probes": inf["ms_probes"], "pass1": inf["ms_pass1"], "qr": inf["ms_qr"],
+                                      "pass2": inf["ms_pass2"]}}
+        out[prec] = row
+        del dA
+    out["workload"] = (f"L3D+{SHIFT}I on {grid}^3 (n={n}), bounds {list(BOUNDS)}, degree {m}, {PROBES} Rademacher "
+                       f"probes: plain Hutchinson vs Hutch++ at equal matvecs, seeds {SEED}..{SEED + seeds - 1}")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,8 +429,8 @@ def main():
                     help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
                     help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
-    ap.add_argument("--workloads", default="c1,c3,c4,f3",
-                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5,f3; '' for none)")
+    ap.add_argument("--workloads", default="c1,c3,c4,f1,f3",
+                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5,f1,f3; '' for none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -514,6 +552,9 @@ def main():
         return
     extra = {}
     for w in [x for x in args.workloads.split(",") if x]:
+        if w == "f1":
+            extra[w] = workload_f1(L, h, A, args.grid, m)
+            continue
         fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4, "c5": workload_config5,
               "f3": workload_f3}[w]
         extra[w] = fn(L, h, log2n=args.c5_log2n) if w == "c5" else fn(L, h)
