@@ -6,7 +6,8 @@ Follows arXiv 2603.02207:
     the spirit of the Lanczos alternative (Appendix A);
   * sigma-normalisation Q~ = Q / sigma when lambda_min < 1 (Section 4, Eq. scaled_sigma_matrix)
     and log det Q = n log sigma + tr log Q~;
-  * Algorithm 2 (Newton-Léja action p(Q~)v), applied column by column, fixed degree;
+  * Algorithm 2 (Newton-Léja action p(Q~)v), applied column by column, to a fixed degree or
+    with its stopping rule |d_m| ||w_m||_2 <= tol;
   * Hutch++ as in Algorithm 3 / Section 4.1 (sketch, Householder QR, deterministic part,
     Hutchinson part on the deflated probes);
   * the plain Hutchinson estimator the paper starts from (Eq. Léja8), on the same probes;
@@ -18,7 +19,11 @@ Readings fixed by this library where the paper is silent or ambiguous:
     Algorithm 1 this equals the unscaled Newton form at z_j = c + gamma xi_j exactly in exact
     arithmetic, and keeps the Newton basis O(1);
   * "degree m" means m+1 Léja points, coefficients d_0..d_m and m operator applications;
-  * the stopping rule of Algorithm 2 is replaced by a fixed degree;
+  * Algorithm 2 runs either to a fixed degree (tol = 0) or with its stopping rule (tol > 0):
+    column by column, the loop stops at the first m with |d_m| ||w_m||_2 <= tol, and the term
+    d_m w_m that met the rule is kept (P_m already holds it when the test is made); the number
+    of Léja points caps m at the degree given; in Hutch++ both the sketch pass and the trace
+    pass use the rule, each column on its own;
   * a non-positive lower bound is an error (the caller supplies a positive one);
   * sigma = lambda_min when lambda_min < 1, else 1;
   * the residual normalisation of Eq. eq_lej_residual_def is 1/k with k = m_vec / 3;
@@ -149,6 +154,43 @@ def leja_apply_columns(M: sp.csr_matrix, V: np.ndarray, xi, d, c: float, gamma: 
     return out
 
 
+def leja_apply_columns_adaptive(M: sp.csr_matrix, V: np.ndarray, xi, d, c: float, gamma: float, tol: float,
+                                scale: float = 1.0, f32: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """Algorithm 2 with its stopping rule, one column at a time: w_0 = v, P_0 = d_0 w_0, m = 0;
+    while |d_m| ||w_m||_2 > tol and m < len(d) - 1: w_{m+1} = (B - xi_m I) w_m, m = m + 1,
+    P_m = P_{m-1} + d_m w_m. Returns (P for every column, the final m of every column).
+
+    f32=True mirrors FP32 storage of the matrix values and of every w_j, as in
+    leja_apply_columns; the norms are taken in FP64 of the stored w_j.
+    """
+    if not (tol > 0.0):
+        raise ValueError("tol must be positive")
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    if f32:
+        M = sp.csr_matrix((_round32(M.data), M.indices, M.indptr), shape=M.shape)
+    mmax = len(d) - 1
+    out = np.empty_like(V)
+    degrees = np.zeros(V.shape[1], dtype=np.int64)
+    for col in range(V.shape[1]):
+        w = V[:, col].copy()
+        if f32:
+            w = _round32(w)
+        P = d[0] * w
+        m = 0
+        while m < mmax and abs(d[m]) * np.linalg.norm(w) > tol:
+            Bw = ((M @ w) / scale - c * w) / gamma
+            w = Bw - xi[m] * w
+            if f32:
+                w = _round32(w)
+            m += 1
+            P = P + d[m] * w
+        out[:, col] = P
+        degrees[col] = m
+    return out, degrees
+
+
 def apply_poly(A, V: np.ndarray, lmin: float, lmax: float, degree: int, f32: bool = False,
                s_mode: str = "center") -> np.ndarray:
     """p_m(A) V, with p_m the degree-m Newton-Léja interpolant of log on [lmin, lmax]."""
@@ -166,9 +208,11 @@ def make_probes(n: int, k: int, seed: int, kind: str = "rademacher") -> tuple[np
 
 
 def hutchpp_logdet(A, lmin: float, lmax: float, degree: int, S: np.ndarray, G: np.ndarray,
-                   s_mode: str = "center", f32: bool = False) -> dict:
+                   s_mode: str = "center", f32: bool = False, tol: float = 0.0) -> dict:
     """Algorithm 3: log det A ~ n log sigma + tr(Q^T F Q) + (1/k) sum_j g'_j^T F g'_j, with
-    F = p(A / sigma), Q = orth(F S) and g'_j = (I - Q Q^T) g_j."""
+    F = p(A / sigma), Q = orth(F S) and g'_j = (I - Q Q^T) g_j. With tol > 0 every application
+    of F stops column by column by Algorithm 2's rule (degree is then the cap); the result holds
+    the final degrees of the sketch pass (deg_s) and of the trace pass (deg_q, deg_g)."""
     n = A.n
     k = S.shape[1]
     sigma = sigma_of(lmin)
@@ -176,8 +220,13 @@ def hutchpp_logdet(A, lmin: float, lmax: float, degree: int, S: np.ndarray, G: n
     lt, ut = lmin / sigma, lmax / sigma
     xi, c, gamma, d, p_terms = newton_leja_setup(lt, ut, degree, s_mode)
     M = _scipy(A)
+    degs = []
 
     def F(X):
+        if tol > 0.0:
+            out, dg = leja_apply_columns_adaptive(M, X, xi, d, c, gamma, tol, sigma, f32)
+            degs.append(dg)
+            return out
         return leja_apply_columns(M, X, xi, d, c, gamma, sigma, f32)
 
     # step 3: Y = F S
@@ -196,19 +245,22 @@ def hutchpp_logdet(A, lmin: float, lmax: float, degree: int, S: np.ndarray, G: n
     t_r = float(np.sum(Gin * FG)) / kk if kk > 0 else 0.0
     # step 7 and output
     est = n * math.log(sigma) + t_q + t_r
-    return dict(estimate=est, trace_q=t_q, trace_res=t_r, sigma=sigma, c=c, gamma=gamma, xi=xi, d=d,
-                taylor_terms=p_terms, Y=Y, Q=Q, Gp=Gp, k=k)
+    out = dict(estimate=est, trace_q=t_q, trace_res=t_r, sigma=sigma, c=c, gamma=gamma, xi=xi, d=d,
+               taylor_terms=p_terms, Y=Y, Q=Q, Gp=Gp, k=k)
+    if tol > 0.0:
+        out.update(deg_s=degs[0], deg_q=degs[1], deg_g=degs[2])
+    return out
 
 
 def logdet_leja(A, lmin: float, lmax: float, degree: int, probes: int, seed: int,
-                kind: str = "rademacher", s_mode: str = "center", f32: bool = False) -> dict:
+                kind: str = "rademacher", s_mode: str = "center", f32: bool = False, tol: float = 0.0) -> dict:
     """logdet_leja(csr, bounds, degree, probes, seed): Algorithm 3 with probes = m_vec
     (a multiple of 3; k = m_vec / 3 columns each for S and G)."""
     if probes % 3 != 0 or probes <= 0:
         raise ValueError("probes must be a positive multiple of 3")
     k = probes // 3
     S, G = make_probes(A.n, k, seed, kind)
-    return hutchpp_logdet(A, lmin, lmax, degree, S, G, s_mode, f32)
+    return hutchpp_logdet(A, lmin, lmax, degree, S, G, s_mode, f32, tol)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -216,28 +268,36 @@ def logdet_leja(A, lmin: float, lmax: float, degree: int, probes: int, seed: int
 # ---------------------------------------------------------------------------------------------
 
 def hutchinson_logdet(A, lmin: float, lmax: float, degree: int, G: np.ndarray, s_mode: str = "center",
-                      f32: bool = False) -> dict:
+                      f32: bool = False, tol: float = 0.0) -> dict:
     """Eq. Léja8 with the sigma-normalisation: log det A ~ n log sigma + (1/m) sum_j g_j^T F g_j
-    over the m columns g_j of G, F = p(A / sigma)."""
+    over the m columns g_j of G, F = p(A / sigma); with tol > 0, F stops column by column by
+    Algorithm 2's rule (the final degrees are returned as deg_g)."""
     n = A.n
     m = G.shape[1]
     sigma = sigma_of(lmin)
     lt, ut = lmin / sigma, lmax / sigma
     xi, c, gamma, d, p_terms = newton_leja_setup(lt, ut, degree, s_mode)
     Gin = _round32(G) if f32 else G
-    FG = leja_apply_columns(_scipy(A), Gin, xi, d, c, gamma, sigma, f32)
+    dg = None
+    if tol > 0.0:
+        FG, dg = leja_apply_columns_adaptive(_scipy(A), Gin, xi, d, c, gamma, tol, sigma, f32)
+    else:
+        FG = leja_apply_columns(_scipy(A), Gin, xi, d, c, gamma, sigma, f32)
     t = float(np.sum(Gin * FG)) / m
-    return dict(estimate=n * math.log(sigma) + t, trace_res=t, sigma=sigma, c=c, gamma=gamma, xi=xi, d=d,
-                taylor_terms=p_terms)
+    out = dict(estimate=n * math.log(sigma) + t, trace_res=t, sigma=sigma, c=c, gamma=gamma, xi=xi, d=d,
+               taylor_terms=p_terms)
+    if dg is not None:
+        out["deg_g"] = dg
+    return out
 
 
 def logdet_hutchinson(A, lmin: float, lmax: float, degree: int, probes: int, seed: int,
-                      kind: str = "rademacher", s_mode: str = "center", f32: bool = False) -> dict:
+                      kind: str = "rademacher", s_mode: str = "center", f32: bool = False, tol: float = 0.0) -> dict:
     """Eq. Léja8 over `probes` vectors of the G stream (the columns Algorithm 3 uses for G)."""
     if probes <= 0:
         raise ValueError("probes must be positive")
     G = _rng.probes(kind, seed, _rng.STREAM_G, A.n, probes)
-    return hutchinson_logdet(A, lmin, lmax, degree, G, s_mode, f32)
+    return hutchinson_logdet(A, lmin, lmax, degree, G, s_mode, f32, tol)
 
 
 # ---------------------------------------------------------------------------------------------

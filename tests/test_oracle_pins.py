@@ -497,3 +497,136 @@ def test_hutchinson_uses_the_g_stream_columns():
     a = logdet.hutchinson_logdet(A, 0.5, 8.5, 20, G)["estimate"]
     b = logdet.logdet_hutchinson(A, 0.5, 8.5, 20, 6, 4, kind="gaussian")["estimate"]
     assert a == b
+
+
+# ------------------------------------------------------------------ Algorithm 2's stopping rule
+
+def _first_at_or_below(e, tol):
+    """Algorithm 2's loop: the first m with e_m <= tol, else the last index."""
+    for m, em in enumerate(e):
+        if not em > tol:
+            return m
+    return len(e) - 1
+
+
+def _tol_stopping_at(e, lo):
+    """A tolerance at which the rule stops at some m >= lo, with a wide margin on both sides:
+    e_m below half of every earlier e_j, and tol their geometric mean."""
+    for m in range(max(lo, 1), len(e)):
+        prev = min(e[:m])
+        if e[m] < 0.5 * prev:
+            return m, math.sqrt(e[m] * prev)
+    raise AssertionError("no clear stopping point")
+
+
+def test_adaptive_degree_diagonal_closed_form():
+    """Algorithm 2's stopping rule on a diagonal matrix, where w_m = prod_{j<m} (b_i - xi_j) v_i
+    elementwise (b_i the scaled eigenvalues): the term norms |d_m| ||w_m|| come from these
+    products and 120-digit divided differences, the result from the barycentric interpolant of
+    the stopping degree. Columns of different scale stop at different degrees."""
+    n, lmin, lmax, mmax = 64, 0.3, 7.0, 60
+    lam = np.linspace(lmin, lmax, n)
+    A = diagonal(lam)
+    sigma = logdet.sigma_of(lmin)
+    lt, ut = lmin / sigma, lmax / sigma
+    xi = leja.fast_leja_points(mmax + 1)
+    c, g = (lt + ut) / 2, (ut - lt) / 4
+    dh = pins.hp_scaled_divided_differences(lt, ut, xi)
+    b = (lam / sigma - c) / g
+    omega = np.concatenate([np.ones((n, 1)), np.cumprod(b[:, None] - xi[None, :mmax], axis=1)], axis=1)
+    v0 = rng.rademacher(5, 0, n, 1)[:, 0]
+    scales = [1.0, 1e-3, 1e3]
+    V = np.stack([s * v0 for s in scales], axis=1)
+    e0 = np.abs(dh) * np.sqrt(np.sum((omega * v0[:, None]) ** 2, axis=0))
+    m0, tol = _tol_stopping_at(e0, 12)
+    want = [_first_at_or_below(s * e0, tol) for s in scales]
+    assert want[1] < want[0] < want[2]
+    xi_o, c_o, g_o, d_o, _ = logdet.newton_leja_setup(lt, ut, mmax)
+    P, deg = logdet.leja_apply_columns_adaptive(logdet._scipy(A), V, xi_o, d_o, c_o, g_o, tol, sigma)
+    assert deg.tolist() == want
+    for col, m in enumerate(want):
+        p = pins.interpolant(lt, ut, xi[: m + 1])
+        ref = p(lam / sigma) * V[:, col]
+        assert np.max(np.abs(P[:, col] - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_adaptive_degree_dense_brute_force():
+    """On a small dense SPD matrix the Newton basis is formed as explicit matrix products
+    prod_{j<m} (B - xi_j I), B = (A / sigma - c I) / gamma, and applied to each column; the
+    stopping degrees and the truncated sums match the recurrence of the oracle."""
+    A = random_spd(7, seed=11)
+    Ad = A.to_scipy().toarray()
+    lam = np.linalg.eigvalsh(Ad)
+    lmin, lmax, mmax = 0.8 * lam[0], 1.2 * lam[-1], 40
+    sigma = logdet.sigma_of(lmin)
+    xi, c, g, d, _ = logdet.newton_leja_setup(lmin / sigma, lmax / sigma, mmax)
+    B = (Ad / sigma - c * np.eye(A.n)) / g
+    mats = [np.eye(A.n)]
+    for j in range(mmax):
+        mats.append((B - xi[j] * np.eye(A.n)) @ mats[-1])
+    V = np.random.default_rng(2).standard_normal((A.n, 3)) * np.array([1.0, 50.0, 0.02])
+    e = np.array([[abs(d[m]) * np.linalg.norm(mats[m] @ V[:, col]) for m in range(mmax + 1)] for col in range(3)])
+    _, tol = _tol_stopping_at(e[0], 8)
+    want = [_first_at_or_below(e[col], tol) for col in range(3)]
+    P, deg = logdet.leja_apply_columns_adaptive(logdet._scipy(A), V, xi, d, c, g, tol, sigma)
+    assert deg.tolist() == want
+    for col, m in enumerate(want):
+        ref = sum(d[j] * (mats[j] @ V[:, col]) for j in range(m + 1))
+        assert np.max(np.abs(P[:, col] - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_adaptive_degree_tiny_tol_is_the_fixed_degree():
+    """A tolerance below every term norm runs every column to the cap, with the fixed-degree
+    arithmetic unchanged."""
+    A = laplacian_2d(9, 0.4)
+    V = rng.rademacher(2, 0, A.n, 3)
+    xi, c, g, d, _ = logdet.newton_leja_setup(0.4, 8.4, 30)
+    M = logdet._scipy(A)
+    P, deg = logdet.leja_apply_columns_adaptive(M, V, xi, d, c, g, 1e-300)
+    assert deg.tolist() == [30, 30, 30]
+    assert np.array_equal(P, logdet.leja_apply_columns(M, V, xi, d, c, g))
+    with pytest.raises(ValueError):
+        logdet.leja_apply_columns_adaptive(M, V, xi, d, c, g, 0.0)
+
+
+def test_adaptive_hutchinson_diagonal_closed_form():
+    """Rademacher probes on a diagonal matrix: every column has the same term norms
+    |d_m| sqrt(sum_i omega_m(b_i)^2), so every column stops at the same degree, and the
+    estimate is n log sigma + sum_i p(lambda_i / sigma) with p the interpolant of that degree."""
+    n, lmin, lmax, mmax = 80, 0.2, 6.0, 70
+    lam = np.linspace(lmin, lmax, n) ** 1.0
+    A = diagonal(lam)
+    sigma = logdet.sigma_of(lmin)
+    lt, ut = lmin / sigma, lmax / sigma
+    xi = leja.fast_leja_points(mmax + 1)
+    c, g = (lt + ut) / 2, (ut - lt) / 4
+    dh = pins.hp_scaled_divided_differences(lt, ut, xi)
+    b = (lam / sigma - c) / g
+    omega = np.concatenate([np.ones((n, 1)), np.cumprod(b[:, None] - xi[None, :mmax], axis=1)], axis=1)
+    e = np.abs(dh) * np.sqrt(np.sum(omega ** 2, axis=0))
+    m, tol = _tol_stopping_at(e, 15)
+    r = logdet.logdet_hutchinson(A, lmin, lmax, mmax, 4, seed=3, tol=tol)
+    assert r["deg_g"].tolist() == [m] * 4
+    p = pins.interpolant(lt, ut, xi[: m + 1])
+    assert r["estimate"] == pytest.approx(n * math.log(sigma) + float(np.sum(p(lam / sigma))), rel=1e-12)
+
+
+def test_adaptive_hutchpp_degrees_and_accuracy_follow_tol():
+    """Hutch++ with the rule in both passes: a smaller tolerance never stops a column earlier,
+    the estimate approaches the fixed-degree estimate at the cap, and at a tolerance below
+    every term it equals it."""
+    A = laplacian_2d(16, 0.2)
+    lo, hi = 0.2, 8.2
+    fixed = logdet.logdet_leja(A, lo, hi, 80, 12, seed=4)["estimate"]
+    prev, errs = None, []
+    for tol in (1e-1, 1e-3, 1e-5, 1e-7):
+        r = logdet.logdet_leja(A, lo, hi, 80, 12, seed=4, tol=tol)
+        degs = np.concatenate([r["deg_s"], r["deg_q"], r["deg_g"]])
+        assert degs.min() >= 1 and degs.max() <= 80
+        if prev is not None:
+            assert np.all(degs >= prev)
+        prev = degs
+        errs.append(abs(r["estimate"] - fixed))
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    r = logdet.logdet_leja(A, lo, hi, 80, 12, seed=4, tol=1e-300)
+    assert r["estimate"] == fixed
