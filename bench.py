@@ -405,10 +405,28 @@ def workload_f1(L, h, A, grid: int, degree: int, seeds: int = 3):
                          "rel_err_vs_exact": errs, "seeds": list(range(SEED, SEED + seeds)),
                          "phase_ms": {"probes": inf["ms_probes"], "pass1": inf["ms_pass1"], "qr": inf["ms_qr"],
                                       "pass2": inf["ms_pass2"]}}
+        # Algorithm 2's stopping rule in both passes of Hutch++ (degree cap 150): every step runs
+        # over the whole block until its last column stops, so the bytes are those of the
+        # longest-running column of each pass
+        for tol in (1e-2, 1e-4):
+            opts = L.options(degree=150, probes=PROBES, seed=SEED, precision=prec, tol=tol)
+            ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, *BOUNDS, opts), 3, 1)
+            inf = h.info()
+            k = PROBES // 3
+            b = (inf["deg_max_pass1"] * step_bytes(n, nnz, k, prec, "accum") +
+                 inf["deg_max_pass2"] * step_bytes(n, nnz, 2 * k, prec, "dot"))
+            row[f"hutchpp_tol_{tol:g}"] = {
+                "ms_per_estimate": ms, "GBps_estimate": b / (ms / 1e3) / 1e9,
+                "rel_err_vs_exact": abs(est - exact) / abs(exact),
+                "deg_max_pass1": inf["deg_max_pass1"], "deg_max_pass2": inf["deg_max_pass2"],
+                "deg_mean_pass2": inf["deg_mean_pass2"],
+                "phase_ms": {"probes": inf["ms_probes"], "pass1": inf["ms_pass1"], "qr": inf["ms_qr"],
+                             "pass2": inf["ms_pass2"]}}
         out[prec] = row
         del dA
     out["workload"] = (f"L3D+{SHIFT}I on {grid}^3 (n={n}), bounds {list(BOUNDS)}, degree {m}, {PROBES} Rademacher "
-                       f"probes: plain Hutchinson vs Hutch++ at equal matvecs, seeds {SEED}..{SEED + seeds - 1}")
+                       f"probes: plain Hutchinson vs Hutch++ at equal matvecs, seeds {SEED}..{SEED + seeds - 1}; "
+                       f"Hutch++ under Algorithm 2's stopping rule (degree cap 150, tol 1e-2 and 1e-4, seed {SEED})")
     return out
 
 

@@ -45,7 +45,7 @@ typedef enum {
     LL_ERR_OOM = 8,               /* device workspace allocation failed                          */
     LL_ERR_CUDA = 9,              /* a CUDA runtime error                                        */
     LL_ERR_UNSUPPORTED = 10,      /* a valid but unimplemented option combination                */
-    LL_ERR_NO_FORWARD = 11        /* backward called without a kept forward                      */
+    LL_ERR_NO_FORWARD = 11        /* no kept forward (backward) or no forward yet                 */
 } ll_status;
 
 /* Storage type of the CSR values. */
@@ -120,6 +120,11 @@ typedef struct {
                                   the pipeline waits of the TMA step kernel.                     */
     int step_kernel;           /* LL_KERNEL_* (default LL_KERNEL_AUTO)                           */
     int estimator;             /* LL_EST_HUTCHPP (default) or LL_EST_HUTCHINSON                  */
+    double tol;                /* Algorithm 2's stopping rule (Section 3.1): 0 (default) = fixed
+                                  degree; > 0: in each pass every column stops at the first m
+                                  with |d_m| ||w_m||_2 <= tol (w_m the Newton basis vector of
+                                  the scaled operator), degree being the cap. Not with
+                                  keep_for_backward nor ll_logdet_batched (LL_ERR_UNSUPPORTED).  */
 } ll_options;
 
 typedef struct ll_handle ll_handle;
@@ -135,6 +140,9 @@ typedef struct {
     float ms_probes, ms_pass1, ms_qr, ms_pass2, ms_total;   /* device times (CUDA events)         */
     int kernel_pass1, kernel_pass2;  /* LL_KERNEL_GATHER or LL_KERNEL_TMA used by each pass       */
     int threads_pass1, threads_pass2;   /* CTA size used by each pass                             */
+    int deg_max_pass1, deg_max_pass2;   /* largest final degree over the columns of each pass
+                                           (the degree itself under a fixed degree)              */
+    double deg_mean_pass2;              /* mean final degree over the trace pass's columns        */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */
@@ -234,6 +242,16 @@ ll_status ll_probes(ll_handle* h, int kind, uint64_t seed, int stream_id, int64_
 ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int degree, int precision,
                         const double* V, int64_t ldv, int b, double* PV, int64_t ldp, void* stream);
 
+/* Algorithm 2 with its stopping rule (Section 3.1), column by column, on the same block as
+ * ll_apply_poly: for every column c, m_c is the first m with |d_m| ||W_m[:, c]||_2 <= tol (m_c =
+ * degree when none), and PV[:, c] = sum_{j <= m_c} d_j W_j[:, c]. The kernels reduce the norms
+ * of every W_{j+1} with the step, retire the columns that meet the rule, and skip the remaining
+ * steps once no column is left. degrees_out: host, b ints, receives m_c. tol > 0 (else
+ * LL_ERR_INVALID_ARG), degree >= 1. Synchronises `stream`. */
+ll_status ll_apply_poly_tol(ll_handle* h, const ll_csr* A, ll_bounds bounds, int degree, double tol, int precision,
+                            const double* V, int64_t ldv, int b, double* PV, int64_t ldp, int* degrees_out,
+                            void* stream);
+
 /* ---- the estimator ------------------------------------------------------------------------- */
 
 /* logdet_leja(csr, bounds, degree, probes, seed): Algorithm 3.
@@ -283,6 +301,13 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
 
 /* Diagnostics of the last ll_logdet_forward on this handle. */
 ll_status ll_get_info(const ll_handle* h, ll_info* out);
+
+/* Final degree of every column of one pass of the last ll_logdet_forward (pass 1: the k sketch
+ * columns; pass 2: the columns of [Q | G'], or the Hutchinson probes), as fixed by Algorithm 2's
+ * stopping rule (ll_options.tol), or the degree for every column under a fixed degree. out: host,
+ * up to cap ints (may be NULL with cap 0); *count (host, may be NULL) receives the column count.
+ * LL_ERR_NO_FORWARD before a forward; LL_ERR_INVALID_ARG for a pass other than 1 or 2. */
+ll_status ll_stop_degrees(const ll_handle* h, int pass, int* out, int cap, int* count);
 
 /* Copy the kept basis [Q | G'] of the last forward with keep_for_backward (FP64, n x (kq + kg):
  * columns [0, kq) hold Q, columns [kq, kq + kg) hold G' = (I - Q Q^T) G) into `out` (device,

@@ -43,7 +43,8 @@ class ll_options(ctypes.Structure):
                 ("probe_kind", ctypes.c_int), ("precision", ctypes.c_int), ("sval_mode", ctypes.c_int),
                 ("keep_for_backward", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int), ("estimator", ctypes.c_int)]
+                ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int), ("estimator", ctypes.c_int),
+                ("tol", ctypes.c_double)]
 
 
 class ll_info(ctypes.Structure):
@@ -52,7 +53,8 @@ class ll_info(ctypes.Structure):
                 ("taylor_terms", ctypes.c_int), ("k", ctypes.c_int), ("kernel_launches", ctypes.c_int),
                 ("ms_probes", ctypes.c_float), ("ms_pass1", ctypes.c_float), ("ms_qr", ctypes.c_float),
                 ("ms_pass2", ctypes.c_float), ("ms_total", ctypes.c_float), ("kernel_pass1", ctypes.c_int),
-                ("kernel_pass2", ctypes.c_int), ("threads_pass1", ctypes.c_int), ("threads_pass2", ctypes.c_int)]
+                ("kernel_pass2", ctypes.c_int), ("threads_pass1", ctypes.c_int), ("threads_pass2", ctypes.c_int),
+                ("deg_max_pass1", ctypes.c_int), ("deg_max_pass2", ctypes.c_int), ("deg_mean_pass2", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -78,6 +80,8 @@ SIGNATURES = {
     "ll_power_lmax_noalloc": (_I, [ctypes.POINTER(ll_csr), _I, _U64, _PD, _P]),
     "ll_probes": (_I, [_P, _I, _U64, _I, _I64, _I, _P, _I64, _P]),
     "ll_apply_poly": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, _I, _I, _P, _I64, _I, _P, _I64, _P]),
+    "ll_apply_poly_tol": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, _I, _D, _I, _P, _I64, _I, _P, _I64,
+                               ctypes.POINTER(_I), _P]),
     "ll_logdet_forward": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, ctypes.POINTER(ll_options), _PD, _P]),
     "ll_logdet_forward_host": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, ctypes.POINTER(ll_options), _PD, _P]),
     "ll_logdet_backward": (_I, [_P, ctypes.POINTER(ll_csr), _D, _P, _P]),
@@ -85,6 +89,7 @@ SIGNATURES = {
     "ll_logdet_batched": (_I, [_P, ctypes.POINTER(ll_csr), ctypes.POINTER(ll_bounds), _I,
                                ctypes.POINTER(ll_options), ctypes.POINTER(_I), _PD, _P]),
     "ll_get_info": (_I, [_P, ctypes.POINTER(ll_info)]),
+    "ll_stop_degrees": (_I, [_P, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]),
     "ll_kept_basis": (_I, [_P, _P, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
 }
 

@@ -125,7 +125,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
             precision: str = "df64", sval_mode: int = LL_SVAL_CENTER, keep_for_backward: bool = False,
             rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
             use_graph: bool = True, timeout_cycles: int = 0, step_kernel: str = "auto",
-            estimator: str = "hutchpp") -> _ffi.ll_options:
+            estimator: str = "hutchpp", tol: float = 0.0) -> _ffi.ll_options:
     o = _ffi.ll_options()
     _ffi.load().ll_default_options(ctypes.byref(o))
     o.degree = degree
@@ -142,6 +142,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
     o.timeout_cycles = timeout_cycles
     o.step_kernel = STEP_KERNELS[step_kernel]
     o.estimator = ESTIMATORS[estimator]
+    o.tol = tol
     return o
 
 
@@ -212,6 +213,30 @@ def ll_apply_poly(h: Handle, A: DeviceCSR, lmin: float, lmax: float, degree: int
     h.check(h._lib.ll_apply_poly(h.ptr, ctypes.byref(a), _ffi.ll_bounds(lmin, lmax), degree, PRECISIONS[precision],
                                  V.data_ptr(), V.stride(0), b, out.data_ptr(), b, _stream_ptr(stream)))
     return out
+
+
+def ll_apply_poly_tol(h: Handle, A: DeviceCSR, lmin: float, lmax: float, degree: int, tol: float, V,
+                      precision: str = "f64", stream=None):
+    """Algorithm 2 with its stopping rule, column by column: (PV, final degree of every column)."""
+    torch = _torch()
+    assert V.dtype == torch.float64 and V.is_cuda and V.dim() == 2 and V.stride(1) == 1
+    n, b = V.shape
+    out = torch.empty((n, b), dtype=torch.float64, device=V.device)
+    deg = (ctypes.c_int * max(b, 1))()
+    a = A.c()
+    h.check(h._lib.ll_apply_poly_tol(h.ptr, ctypes.byref(a), _ffi.ll_bounds(lmin, lmax), degree, tol,
+                                     PRECISIONS[precision], V.data_ptr(), V.stride(0), b, out.data_ptr(), b, deg,
+                                     _stream_ptr(stream)))
+    return out, np.array(deg[:b], dtype=np.int64)
+
+
+def ll_stop_degrees(h: Handle, pass_: int) -> np.ndarray:
+    """Final degree of every column of pass 1 or 2 of the last forward."""
+    cnt = ctypes.c_int()
+    h.check(h._lib.ll_stop_degrees(h.ptr, pass_, None, 0, ctypes.byref(cnt)))
+    buf = (ctypes.c_int * max(cnt.value, 1))()
+    h.check(h._lib.ll_stop_degrees(h.ptr, pass_, buf, cnt.value, None))
+    return np.array(buf[:cnt.value], dtype=np.int64)
 
 
 def ll_logdet_forward(h: Handle, A: DeviceCSR, lmin: float, lmax: float, opts: _ffi.ll_options, stream=None) -> float:

@@ -73,6 +73,9 @@ struct ll_handle {
     int64_t kept_n = 0, kept_nnz = 0;
     int kept_kq = 0, kept_kg = 0, kept_m = 0, kept_prec = 0, kept_ckpt = 0;
     bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
+    // final degree of every column of both passes of the last forward (Algorithm 2's rule)
+    bool have_forward = false;
+    std::vector<int> last_deg1, last_deg2;
     double kept_sigma = 1, kept_c = 0, kept_gamma = 1;
     std::vector<double> kept_d, kept_xi;
 };
@@ -219,16 +222,19 @@ cudaError_t exec_step(ll_handle* h, int precision, int mode, const StepExec& E, 
 // and the pass's tile descriptors (one set per mode, built here from the CSR and the prepared
 // values in p, on the stream, before the pass's steps).
 ll_status bind_exec(ll_handle* h, int precision, int mode, int b, StepExec& E, StepParams& p, cudaStream_t s) {
-    if (mode == MODE_DOT) {
-        WS(partials, double*, "dot_partials", (size_t)2 * E.grid() * b * sizeof(double));
+    if (base_mode(mode) == MODE_DOT || stop_mode(mode)) {
+        WS(partials, double*, "dot_partials", (size_t)3 * E.grid() * b * sizeof(double));
         p.partials = partials;
     }
     if (E.kind == LL_KERNEL_TMA) {
         WS(err, int*, "tma_error", sizeof(int));
         E.tl.q.error = err;
-        static const char* dn[NUM_MODES] = {"tma_desc_plain", "tma_desc_accum", "tma_desc_dot", "tma_desc_adj"};
-        static const char* gn[NUM_MODES] = {"tma_gcol_plain", "tma_gcol_accum", "tma_gcol_dot", "tma_gcol_adj"};
-        static const char* mn[NUM_MODES] = {"tma_meta_plain", "tma_meta_accum", "tma_meta_dot", "tma_meta_adj"};
+        static const char* dn[NUM_MODES] = {"tma_desc_plain", "tma_desc_accum", "tma_desc_dot", "tma_desc_adj",
+                                            "tma_desc_4", "tma_desc_accum_stop", "tma_desc_dot_stop", "tma_desc_7"};
+        static const char* gn[NUM_MODES] = {"tma_gcol_plain", "tma_gcol_accum", "tma_gcol_dot", "tma_gcol_adj",
+                                            "tma_gcol_4", "tma_gcol_accum_stop", "tma_gcol_dot_stop", "tma_gcol_7"};
+        static const char* mn[NUM_MODES] = {"tma_meta_plain", "tma_meta_accum", "tma_meta_dot", "tma_meta_adj",
+                                            "tma_meta_4", "tma_meta_accum_stop", "tma_meta_dot_stop", "tma_meta_7"};
         WS(desc, unsigned char*, dn[mode], E.tl.desc_bytes);
         WS(gcol, int*, gn[mode], E.tl.gcol_bytes);
         WS(meta, int4*, mn[mode], E.tl.meta_bytes);
@@ -317,13 +323,27 @@ ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz,
     return bind_exec(h, precision, mode, b, E, p, s);
 }
 
+// Per-column state of a pass under Algorithm 2's stopping rule (device; live and stop_deg hold
+// b rounded up to even ints). tol = 0: fixed degree.
+struct StopState {
+    double tol = 0.0;
+    int* live = nullptr;
+    int* stop_deg = nullptr;
+    int* done = nullptr;
+};
+
 // Runs m Léja steps over an n x b block.
 //   mode ACCUM: W_0 = win0 (ld = ldw), P accumulates sum_j d_j W_j (P type, ld = ldp)
 //   mode DOT:   W_0 = V = win0, dots[(j) * b + col] = <V_col, W_j col> for j = 0..m
+// With stop.tol > 0 the pass runs the STOP variant of the mode: the launch that starts it sets
+// the column state from ||W_0||, each step retires the columns that meet the rule (P stops
+// growing there; the dots of later steps are still written for the columns that run), and once
+// no column runs the remaining steps return at once. stop.stop_deg then holds each column's
+// final degree. The step kernel is the one chosen for the plain mode.
 ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int precision, int mode, int n, int b,
                    const void* win0, long long ldw, void* wa, void* wb, void* P, long long ldp, double* dots,
                    const std::vector<double>& beta, const std::vector<double>& d, int kernel, int threads_target,
-                   int rpt, cudaStream_t s) {
+                   int rpt, cudaStream_t s, const StopState& stop = StopState{}) {
     const int m = (int)d.size() - 1;
     StepParams p{};
     p.rowptr = A->rowptr;
@@ -333,12 +353,13 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     p.ldv = ldw;
     p.ldp = ldp;
     p.p = P;
-    if (mode == MODE_DOT) {
+    const bool adaptive = stop.tol > 0.0;
+    if (mode == MODE_DOT || adaptive) {
         WS(ticket, unsigned int*, "dot_ticket", sizeof(unsigned int));
         LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
         p.ticket = ticket;
-        p.v = win0;
     }
+    if (mode == MODE_DOT) p.v = win0;
     {
         WS(err, int*, "tma_error", sizeof(int));
         LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
@@ -361,6 +382,25 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     StepExec E;
     ll_status st = choose_exec(h, precision, mode, n, A->nnz, b, kernel, threads_target, rpt, p, E, s);
     if (st != LL_OK) return st;
+    int run_mode = mode;
+    if (adaptive) {
+        // the same kernel and shape in the STOP variant (the gather kernel when a TMA plan of it
+        // does not fit), then the column state from W_0
+        run_mode = mode | MODE_STOP;
+        StepExec ES;
+        if (!plan_exec(h, E.kind, precision, run_mode, n, A->nnz, b, E.threads, E.rpt, p, ES))
+            plan_exec(h, LL_KERNEL_GATHER, precision, run_mode, n, A->nnz, b, 0, 0, p, ES);
+        if ((st = bind_exec(h, precision, run_mode, b, ES, p, s)) != LL_OK) return st;
+        E = ES;
+        p.live = stop.live;
+        p.stop_deg = stop.stop_deg;
+        p.done = stop.done;
+        p.tol = stop.tol;
+        WS(ipart, double*, "stop_init_partials", (size_t)STOP_INIT_GRID * b * sizeof(double));
+        LL_CK(launch_stop_init(precision, win0, ldw, n, b, d[0], stop.tol, m, ipart, p.ticket, stop.live,
+                               stop.stop_deg, stop.done, s));
+        h->launches++;
+    }
     h->last_kernel = E.kind;
     h->last_threads = E.cta();
     for (int j = 0; j < m; ++j) {
@@ -377,7 +417,8 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
             p.dots_next = dots + (size_t)(j + 1) * b;
             p.dots_first = dots;
         }
-        LL_CK(exec_step(h, precision, mode, E, p, s));
+        p.jnext = j + 1;
+        LL_CK(exec_step(h, precision, run_mode, E, p, s));
     }
     return LL_OK;
 }
@@ -458,6 +499,7 @@ void ll_default_options(ll_options* o) {
     o->timeout_cycles = 0;
     o->step_kernel = LL_KERNEL_AUTO;
     o->estimator = LL_EST_HUTCHPP;
+    o->tol = 0.0;
 }
 
 ll_status ll_debug_inject(ll_handle* h, int what) {
@@ -613,6 +655,54 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
     return check_tma_flag(h, s);
 }
 
+ll_status ll_apply_poly_tol(ll_handle* h, const ll_csr* A, ll_bounds bounds, int degree, double tol, int precision,
+                            const double* V, int64_t ldv, int b, double* PV, int64_t ldp, int* degrees_out,
+                            void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    ll_status st = check_csr_args(h, A);
+    if (st != LL_OK) return st;
+    if ((st = check_bounds(h, bounds)) != LL_OK) return st;
+    if (degree < 1 || b < 0 || ldv < b || ldp < b) return fail(h, LL_ERR_INVALID_ARG, "bad degree or block shape");
+    if (!std::isfinite(tol) || !(tol > 0.0)) return fail(h, LL_ERR_INVALID_ARG, "tol must be finite and > 0");
+    if (precision < LL_PREC_F64 || precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
+    const int n = (int)A->n;
+    if (n == 0 || b == 0) return LL_OK;
+    if (b > 512) return fail(h, LL_ERR_UNSUPPORTED, "block width above 512");
+    if (!V || !PV || !degrees_out) return fail(h, LL_ERR_INVALID_ARG, "null block or degree array");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->launches = 0;
+    if ((st = validate_csr(h, A, s)) != LL_OK) return st;
+    std::vector<double> xi, d;
+    if ((st = setup_coefficients(h, bounds.lmin, bounds.lmax, degree, LL_SVAL_CENTER, xi, d)) != LL_OK) return st;
+    const double c = (bounds.lmin + bounds.lmax) / 2.0, gamma = (bounds.lmax - bounds.lmin) / 4.0;
+    std::vector<double> beta(degree + 1);
+    for (int j = 0; j <= degree; ++j) beta[j] = -(c / gamma + xi[j]);
+    const int wt = w_type_of(precision), pt = p_type_of(precision);
+    const int lb = block_ld(precision, b);
+    const size_t nb = (size_t)n * lb;
+    WS(vprep, void*, "ap_vals", (size_t)A->nnz * elem_size(wt));
+    WS(w0, void*, "ap_w0", nb * elem_size(wt));
+    WS(wa, void*, "ap_wa", nb * elem_size(wt));
+    WS(wb, void*, "ap_wb", nb * elem_size(wt));
+    WS(pp, void*, "ap_p", nb * elem_size(pt));
+    WS(sst, int*, "ap_stop_state", (size_t)(2 * (b + 2) + 1) * sizeof(int));
+    LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / gamma, precision, vprep, s));
+    LL_CK(launch_convert_block(V, ldv, precision, w0, lb, n, b, lb, s));
+    h->launches += 2;
+    const StopState stop{tol, sst, sst + (b + 2), sst + 2 * (b + 2)};
+    st = run_pass(h, A, vprep, precision, MODE_ACCUM, n, b, w0, lb, wa, wb, pp, lb, nullptr, beta, d, h->cfg_kernel,
+                  h->cfg_threads, h->cfg_rpt, s, stop);
+    if (st != LL_OK) return st;
+    h->info = ll_info{};
+    h->info.kernel_pass1 = h->last_kernel;
+    h->info.threads_pass1 = h->last_threads;
+    LL_CK(launch_block_to_f64(precision, pp, lb, PV, ldp, n, b, s));
+    h->launches++;
+    LL_CK(cudaMemcpyAsync(degrees_out, stop.stop_deg, (size_t)b * sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    return check_tma_flag(h, s);
+}
+
 ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, const ll_options* opts, double* estimate,
                             void* stream) {
     if (!h || !opts || !estimate) return LL_ERR_INVALID_ARG;
@@ -628,9 +718,14 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
     if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
     if (o.sval_mode != LL_SVAL_CENTER && o.sval_mode != LL_SVAL_HALF_LMAX) return fail(h, LL_ERR_INVALID_ARG, "unknown s_val mode");
+    if (!std::isfinite(o.tol) || o.tol < 0.0) return fail(h, LL_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    const bool adaptive = o.tol > 0.0;   // Algorithm 2's stopping rule in both passes
+    if (adaptive && o.keep_for_backward)
+        return fail(h, LL_ERR_UNSUPPORTED, "the backward needs a fixed degree (tol = 0)");
     cudaStream_t s = (cudaStream_t)stream;
     h->launches = 0;
     h->kept = false;
+    h->have_forward = false;
     h->spin_budget = o.timeout_cycles > 0 ? o.timeout_cycles : 4000000000LL;
     const int n = (int)A->n;
     if (n == 0) {
@@ -681,6 +776,14 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     WS(qrstat, int*, "fw_qr_status", sizeof(int));
     WS(dots, double*, "fw_dots", (size_t)(m + 1) * b2 * sizeof(double));
     WS(tma_err, int*, "tma_error", sizeof(int));
+    // column state of both passes under the stopping rule: live and final degree (b rounded up
+    // to even), and the done flag
+    StopState stop1, stop2;
+    if (adaptive) {
+        WS(sst, int*, "fw_stop_state", (size_t)(2 * (kq + 2) + 2 * (b2 + 2) + 2) * sizeof(int));
+        stop1 = StopState{o.tol, sst, sst + (kq + 2), sst + 2 * (kq + 2) + 2 * (b2 + 2)};
+        stop2 = StopState{o.tol, sst + 2 * (kq + 2), sst + 2 * (kq + 2) + (b2 + 2), sst + 2 * (kq + 2) + 2 * (b2 + 2) + 1};
+    }
     int k1 = 0, t1 = 0;   // step kernel and CTA size of pass 1
 
     // the device work of the call (Algorithm 3 steps 2-6), enqueued on q; with capture, the
@@ -729,7 +832,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         } else {
             // step 3: Y = p(A~) S
             st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, kq, S, l1, wa, wb, P, l1, nullptr, beta, d, o.step_kernel,
-                          o.threads_per_block, o.rows_per_thread, q);
+                          o.threads_per_block, o.rows_per_thread, q, stop1);
             if (st != LL_OK) return st;
             k1 = h->last_kernel;
             t1 = h->last_threads;
@@ -753,7 +856,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
 
         // steps 5-6: traces t_j[col] = <V_col, W_j col> for j = 0..m
         st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d, o.step_kernel,
-                      o.threads_per_block, o.rows_per_thread, q);
+                      o.threads_per_block, o.rows_per_thread, q, stop2);
         if (st != LL_OK) return st;
         LL_CK(rec(h->ev[4], q));
         return LL_OK;
@@ -835,7 +938,14 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
 
     std::vector<double> hd((size_t)(m + 1) * b2);
     int hstat = 0, herr = 0;
+    // final degrees: the pass-1 columns (not run: Hutchinson, or k >= n) count as 0
+    std::vector<int> deg1(kq, (hutch || kq == n) ? 0 : m), deg2(b2, m);
     LL_CK(cudaMemcpyAsync(hd.data(), dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (adaptive) {
+        if (kq > 0 && !hutch && kq < n)
+            LL_CK(cudaMemcpyAsync(deg1.data(), stop1.stop_deg, kq * sizeof(int), cudaMemcpyDeviceToHost, s));
+        LL_CK(cudaMemcpyAsync(deg2.data(), stop2.stop_deg, b2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
     LL_CK(cudaMemcpyAsync(&hstat, qrstat, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (h->tma_used) LL_CK(cudaMemcpyAsync(&herr, tma_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     LL_CK(cudaStreamSynchronize(s));
@@ -843,12 +953,15 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if (herr) return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out");
     if (hstat) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2: non-positive pivot (rank-deficient sketch)");
 
-    // step 7 and output: n log sigma + tr(Q^T F Q) + (1/k) tr(G'^T F G')
+    // step 7 and output: n log sigma + tr(Q^T F Q) + (1/k) tr(G'^T F G'); under the stopping
+    // rule, column col takes the terms j <= deg2[col] (the later dots are not its terms)
     double tq = 0.0, tr = 0.0;
     for (int j = 0; j <= m; ++j) {
         double sq = 0.0, sr = 0.0;
-        for (int col = 0; col < kq; ++col) sq += hd[(size_t)j * b2 + col];
-        for (int col = kq; col < b2; ++col) sr += hd[(size_t)j * b2 + col];
+        for (int col = 0; col < kq; ++col)
+            if (deg2[col] >= j) sq += hd[(size_t)j * b2 + col];
+        for (int col = kq; col < b2; ++col)
+            if (deg2[col] >= j) sr += hd[(size_t)j * b2 + col];
         tq += d[j] * sq;
         tr += d[j] * sr;
     }
@@ -875,6 +988,18 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     I.threads_pass1 = t1;
     I.kernel_pass2 = h->last_kernel;
     I.threads_pass2 = h->last_threads;
+    I.deg_max_pass1 = 0;
+    for (int v : deg1) I.deg_max_pass1 = v > I.deg_max_pass1 ? v : I.deg_max_pass1;
+    I.deg_max_pass2 = 0;
+    double dsum = 0.0;
+    for (int v : deg2) {
+        I.deg_max_pass2 = v > I.deg_max_pass2 ? v : I.deg_max_pass2;
+        dsum += v;
+    }
+    I.deg_mean_pass2 = b2 > 0 ? dsum / b2 : 0.0;
+    h->last_deg1 = deg1;
+    h->last_deg2 = deg2;
+    h->have_forward = true;
 
     if (o.keep_for_backward) {
         h->kept = true;
@@ -1164,6 +1289,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     const ll_options& o = *opts;
     if (o.probes <= 0 || o.probes % 3 != 0) return fail(h, LL_ERR_INVALID_ARG, "probes must be a positive multiple of 3");
     if (o.estimator != LL_EST_HUTCHPP) return fail(h, LL_ERR_UNSUPPORTED, "the batched call runs Hutch++ only");
+    if (o.tol != 0.0) return fail(h, LL_ERR_UNSUPPORTED, "the batched call runs a fixed degree per matrix (tol = 0)");
     if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
     if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1616,6 +1742,15 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
 ll_status ll_get_info(const ll_handle* h, ll_info* out) {
     if (!h || !out) return LL_ERR_INVALID_ARG;
     *out = h->info;
+    return LL_OK;
+}
+
+ll_status ll_stop_degrees(const ll_handle* h, int pass, int* out, int cap, int* count) {
+    if (!h || (pass != 1 && pass != 2) || cap < 0 || (cap > 0 && !out)) return LL_ERR_INVALID_ARG;
+    if (!h->have_forward) return LL_ERR_NO_FORWARD;
+    const std::vector<int>& v = pass == 1 ? h->last_deg1 : h->last_deg2;
+    if (count) *count = (int)v.size();
+    for (int i = 0; i < cap && i < (int)v.size(); ++i) out[i] = v[i];
     return LL_OK;
 }
 

@@ -9,7 +9,16 @@
 namespace ll {
 
 enum StepMode { MODE_PLAIN = 0, MODE_ACCUM = 1, MODE_DOT = 2, MODE_ADJ = 3 };
-constexpr int NUM_MODES = 4;
+// Algorithm 2's stopping rule on top of ACCUM or DOT: the step also reduces ||W_{j+1} col||^2,
+// the last CTA retires every column with |d_{j+1}| ||W_{j+1} col|| <= tol, P stops growing in
+// retired columns, and once no column is left the following steps of the pass (all but the
+// first) return at once.
+constexpr int MODE_STOP = 4;
+constexpr int MODE_ACCUM_STOP = MODE_ACCUM | MODE_STOP;
+constexpr int MODE_DOT_STOP = MODE_DOT | MODE_STOP;
+constexpr int NUM_MODES = 8;
+__host__ __device__ constexpr int base_mode(int mode) { return mode & 3; }
+__host__ __device__ constexpr bool stop_mode(int mode) { return (mode & MODE_STOP) != 0; }
 
 // One Léja step over an n x b block, all columns at once (Algorithm 2 loop body):
 //   Wout = B Win - xi_j Win   with B = (A - c I)/gamma folded into prepared values a_e / gamma
@@ -18,6 +27,8 @@ constexpr int NUM_MODES = 4;
 //   DOT:   dots_next[col] = sum_i V[i, col] * Wout[i, col]   (and dots_first = V . Win if first)
 //   ADJ:   Wout += coef(col) * V[i, col] with coef = adj_q for col < adj_split, adj_g otherwise
 //          (the reverse recurrence Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U, B symmetric)
+//   ACCUM_STOP / DOT_STOP: ACCUM / DOT with Algorithm 2's stopping rule (dn is applied only to
+//          live columns; see MODE_STOP)
 struct StepParams {
     const int32_t* rowptr;
     const int32_t* colind;
@@ -38,6 +49,12 @@ struct StepParams {
     int adj_split;               // ADJ: first column using adj_g
     double adj_q, adj_g;         // ADJ: coefficients of V (FP64)
     float2 adj_q_df, adj_g_df;   // ADJ: the same as double-float pairs
+    // STOP modes (partials then hold 3 * grid * b doubles: the norms are quantity 2)
+    int* live;                   // per column (b rounded up to even): 1 while the column runs
+    int* stop_deg;               // per column: the degree at which the column stopped
+    int* done;                   // 1 once no column runs: the step returns at once
+    double tol;                  // Algorithm 2's tolerance
+    int jnext;                   // j + 1: the index of the W this step writes
 };
 
 struct StepLaunch {
@@ -97,6 +114,15 @@ cudaError_t launch_scaled_copy_f64(const double* in, long long ld_in, double* ou
 
 // out[i * ld + i] = 1 for i < n (type t); the rest of `out` is left as is
 cudaError_t launch_unit_diag(int t, void* out, long long ld, int n, cudaStream_t s);
+
+// Start of a pass under Algorithm 2's stopping rule: e_0 = |d_0| ||W_0 col||_2 for every column
+// c < b of the n x b block W0 (element type of `precision`'s W blocks, ld columns); live[c] =
+// (e_0 > tol), stop_deg[c] = live ? mmax : 0, live[b] = 0 when b is odd, *done = no column live.
+// partials holds grid * b doubles (grid = STOP_INIT_GRID), ticket a zeroed counter (left zeroed).
+constexpr int STOP_INIT_GRID = 304;
+cudaError_t launch_stop_init(int precision, const void* W0, long long ld, int n, int b, double d0, double tol,
+                             int mmax, double* partials, unsigned int* ticket, int* live, int* stop_deg, int* done,
+                             cudaStream_t s);
 
 // Power iteration helpers (FP64): y = A x; and reductions
 cudaError_t launch_spmv_f64(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype, int n,

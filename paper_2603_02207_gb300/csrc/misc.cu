@@ -256,6 +256,77 @@ cudaError_t launch_dot_f64(const double* x, const double* y, int n, double* part
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- Algorithm 2's stopping rule, m = 0
+// Thread t of a 512-thread CTA owns column t % b of rows (t / b) + lanes * i of the CTA's share,
+// accumulating squares in FP64; the lanes are summed in lane order, the CTAs in CTA order by the
+// last CTA to finish, which takes the decision for every column.
+template <typename T>
+__global__ void __launch_bounds__(512) k_stop_init(const T* W, long long ld, int n, int b, double d0, double tol,
+                                                   int mmax, double* partials, unsigned int* ticket, int* live,
+                                                   int* stop_deg, int* done) {
+    __shared__ double red[512];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x;
+    const int lanes = (int)blockDim.x / b;
+    const int rlane = tid / b, c = tid - rlane * b;
+    double acc = 0.0;
+    if (rlane < lanes)
+        for (long long r = (long long)blockIdx.x * lanes + rlane; r < n; r += (long long)gridDim.x * lanes) {
+            const double x = load_f64<T>(W, (size_t)r * ld + c);
+            acc = fma(x, x, acc);
+        }
+    red[tid] = acc;
+    __syncthreads();
+    for (int cc = tid; cc < b; cc += blockDim.x) {
+        double sum = 0.0;
+        for (int l = 0; l < lanes; ++l) sum += red[l * b + cc];
+        partials[(size_t)blockIdx.x * b + cc] = sum;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    int any = 0;
+    for (int cc = tid; cc < b; cc += blockDim.x) {
+        double sum = 0.0;
+        for (int g = 0; g < (int)gridDim.x; ++g) sum += __ldcg(&partials[(size_t)g * b + cc]);
+        const int l = fabs(d0) * sqrt(sum) > tol ? 1 : 0;
+        live[cc] = l;
+        stop_deg[cc] = l ? mmax : 0;
+        any |= l;
+    }
+    if (tid == 0 && (b & 1)) {
+        live[b] = 0;
+        stop_deg[b] = 0;
+    }
+    any = __syncthreads_or(any);
+    if (tid == 0) {
+        *done = any ? 0 : 1;
+        *ticket = 0u;
+    }
+}
+
+cudaError_t launch_stop_init(int precision, const void* W0, long long ld, int n, int b, double d0, double tol,
+                             int mmax, double* partials, unsigned int* ticket, int* live, int* stop_deg, int* done,
+                             cudaStream_t s) {
+    if (b <= 0 || b > 512 || n < 0) return cudaErrorInvalidValue;
+    const int G = STOP_INIT_GRID;
+    switch (w_type_of(precision)) {
+        case T_F64:
+            k_stop_init<double><<<G, 512, 0, s>>>((const double*)W0, ld, n, b, d0, tol, mmax, partials, ticket, live, stop_deg, done);
+            break;
+        case T_F32:
+            k_stop_init<float><<<G, 512, 0, s>>>((const float*)W0, ld, n, b, d0, tol, mmax, partials, ticket, live, stop_deg, done);
+            break;
+        default:
+            k_stop_init<dfp><<<G, 512, 0, s>>>((const dfp*)W0, ld, n, b, d0, tol, mmax, partials, ticket, live, stop_deg, done);
+            break;
+    }
+    return cudaGetLastError();
+}
+
 // mode 0: x /= sqrt(*num)
 __global__ void k_scale(double* x, const double* num, int n, int mode) {
     const double f = 1.0 / sqrt(*num);

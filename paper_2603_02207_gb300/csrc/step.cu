@@ -5,6 +5,8 @@
 //   pass 1 (MODE_ACCUM): P += d_{j+1} W_{j+1}                (Algorithm 2, P_m = P_{m-1} + d_m w_m)
 //   pass 2 (MODE_DOT):   t_{j+1}[col] = <V[:, col], W_{j+1}[:, col]>   (Algorithm 3 steps 5-6)
 //   MODE_PLAIN:          W_{j+1} only (recomputation in the adjoint);
+//   MODE_ACCUM_STOP / MODE_DOT_STOP: pass 1 / pass 2 under Algorithm 2's stopping rule (the
+//                        norms of W_{j+1} are reduced with the traces; see MODE_STOP);
 //   MODE_ADJ:            Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U, U = V with per-column
 //                        weights (the reverse recurrence of the adjoint, B symmetric).
 //
@@ -75,7 +77,13 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
     using Raw = typename PairT<PREC>::Raw;
     using Ex = typename ExT<PREC>::T;
     constexpr int U = gather_batch<PREC>();
+    constexpr int MB = base_mode(MODE);
     extern __shared__ __align__(16) unsigned char smem[];
+    if constexpr (stop_mode(MODE)) {
+        // every column of the pass has met the stopping rule (the first step always runs: it
+        // writes P = d_0 W_0 and the traces of W_0 that degree-0 columns keep)
+        if (!p.first && *p.done) return;
+    }
 
     const int tid = threadIdx.x;
     const int tp = p.tp;                  // column pairs per row = threads per row
@@ -97,7 +105,7 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
     const int* __restrict__ rowptr = p.rowptr;
     const int* __restrict__ colind = p.colind;
 
-    const StepScalars<PREC> S(p, cp);
+    const StepScalars<PREC> S(p, cp, stop_mode(MODE) && MB == MODE_ACCUM);
 
     auto stage = [&](int tile, int buf, int nz0, int nz1) {
         const int r0 = tile * R;
@@ -164,10 +172,10 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
                 const WP wr = win[own];
                 PP po{};
                 WP vr{};
-                if constexpr (MODE == MODE_ACCUM) {
+                if constexpr (MB == MODE_ACCUM) {
                     if (!p.first) po = pblk[(size_t)r * ldpq + cp];
                 }
-                if constexpr (MODE == MODE_DOT || MODE == MODE_ADJ) vr = vblk[(size_t)r * ldvq + cp];
+                if constexpr (MB == MODE_DOT || MB == MODE_ADJ) vr = vblk[(size_t)r * ldvq + cp];
 
                 // accumulate sum_k a_k W_j[c_k, pair]
                 RowAcc A;
@@ -197,9 +205,9 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
         nnz1 = fz1;
     }
 
-    if constexpr (MODE == MODE_DOT) {
+    if constexpr (MB == MODE_DOT || stop_mode(MODE)) {
         __shared__ bool s_last;
-        trace_reduce<PREC>(p, T, reinterpret_cast<double*>(smem), tp, p.rl, &s_last);
+        trace_reduce<PREC, MODE>(p, T, reinterpret_cast<double*>(smem), tp, p.rl, &s_last);
     }
 }
 
@@ -264,12 +272,13 @@ StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int thr
     p.smem_cap = (int)cap;
     size_t smem = bytes_of(cap);
     const size_t red = (size_t)L.threads * 2 * sizeof(double);
-    if (mode == MODE_DOT && smem < red) smem = red;
+    if ((base_mode(mode) == MODE_DOT || stop_mode(mode)) && smem < red) smem = red;
     L.smem = smem;
     int per_sm = 1;
     switch (precision * NUM_MODES + mode) {
 #define OCC(P_, M_) case P_ * NUM_MODES + M_: per_sm = occupancy<P_, M_>(L.threads, smem); break;
-#define OCC4(P_) OCC(P_, MODE_PLAIN) OCC(P_, MODE_ACCUM) OCC(P_, MODE_DOT) OCC(P_, MODE_ADJ)
+#define OCC4(P_) OCC(P_, MODE_PLAIN) OCC(P_, MODE_ACCUM) OCC(P_, MODE_DOT) OCC(P_, MODE_ADJ) \
+    OCC(P_, MODE_ACCUM_STOP) OCC(P_, MODE_DOT_STOP)
         OCC4(LL_PREC_F64) OCC4(LL_PREC_DF64) OCC4(LL_PREC_F32_MIXED)
 #undef OCC4
 #undef OCC
@@ -287,7 +296,8 @@ cudaError_t launch_step(int precision, int mode, const StepLaunch& L, const Step
     if (p.num_tiles <= 0) return cudaSuccess;
     switch (precision * NUM_MODES + mode) {
 #define LCH(P_, M_) case P_ * NUM_MODES + M_: return launch_typed<P_, M_>(L, p, s);
-#define LCH4(P_) LCH(P_, MODE_PLAIN) LCH(P_, MODE_ACCUM) LCH(P_, MODE_DOT) LCH(P_, MODE_ADJ)
+#define LCH4(P_) LCH(P_, MODE_PLAIN) LCH(P_, MODE_ACCUM) LCH(P_, MODE_DOT) LCH(P_, MODE_ADJ) \
+    LCH(P_, MODE_ACCUM_STOP) LCH(P_, MODE_DOT_STOP)
         LCH4(LL_PREC_F64) LCH4(LL_PREC_DF64) LCH4(LL_PREC_F32_MIXED)
 #undef LCH4
 #undef LCH

@@ -52,6 +52,8 @@ __device__ __forceinline__ void row_mac(RowAcc& A, const typename ExT<PREC>::T& 
 struct TracePart {
     f2x th2 = 0ull, tl2 = 0ull, t0h2 = 0ull, t0l2 = 0ull;
     double td[2] = {0.0, 0.0}, t0d[2] = {0.0, 0.0};
+    f2x nh2 = 0ull, nl2 = 0ull;    // STOP modes: ||W_{j+1} col||^2 partials
+    double nd[2] = {0.0, 0.0};
 };
 
 // per-step scalars broadcast to both lanes, and the adjoint's per-column coefficients
@@ -60,14 +62,19 @@ struct StepScalars {
     f2x bh2, bl2, nbh2, beta2, dnh2, dnl2, ndnh2, d0h2, d0l2, nd0h2;
     double cadj0, cadj1;
     f2x ch2, cl2, nch2, cf2;
-    __device__ __forceinline__ StepScalars(const StepParams& p, int cp) {
+    double dn0, dn1;   // d_{j+1} per column (zero in retired columns under the stopping rule)
+    // masked = true: d_{j+1} applies only to the columns with live[col] set
+    __device__ __forceinline__ StepScalars(const StepParams& p, int cp, bool masked = false) {
         bh2 = f2_pack(p.beta_df.x, p.beta_df.x);
         bl2 = f2_pack(p.beta_df.y, p.beta_df.y);
         nbh2 = f2_pack(-p.beta_df.x, -p.beta_df.x);
         beta2 = f2_pack(p.beta_df.x, p.beta_df.x);   // the leading float of beta_j: (float)beta_j
-        dnh2 = f2_pack(p.dn_df.x, p.dn_df.x);
-        dnl2 = f2_pack(p.dn_df.y, p.dn_df.y);
-        ndnh2 = f2_pack(-p.dn_df.x, -p.dn_df.x);
+        const bool l0 = !masked || p.live[2 * cp] != 0, l1 = !masked || p.live[2 * cp + 1] != 0;
+        dn0 = l0 ? p.dn : 0.0;
+        dn1 = l1 ? p.dn : 0.0;
+        dnh2 = f2_pack(l0 ? p.dn_df.x : 0.f, l1 ? p.dn_df.x : 0.f);
+        dnl2 = f2_pack(l0 ? p.dn_df.y : 0.f, l1 ? p.dn_df.y : 0.f);
+        ndnh2 = f2_pack(l0 ? -p.dn_df.x : 0.f, l1 ? -p.dn_df.x : 0.f);
         d0h2 = f2_pack(p.d0_df.x, p.d0_df.x);
         d0l2 = f2_pack(p.d0_df.y, p.d0_df.y);
         nd0h2 = f2_pack(-p.d0_df.x, -p.d0_df.x);
@@ -91,29 +98,37 @@ __device__ __forceinline__ void row_epilogue(const StepParams& p, const StepScal
                                              const typename PairT<PREC>::P& po, typename PairT<PREC>::W* wout,
                                              typename PairT<PREC>::P* pout, TracePart& T) {
     const f2x zero2 = 0ull;
+    constexpr int MB = base_mode(MODE);
+    constexpr bool STOP = stop_mode(MODE);
     if constexpr (PREC == LL_PREC_F64) {
         double w0 = fma(p.beta, wr.x, A.a0), w1 = fma(p.beta, wr.y, A.a1);
-        if constexpr (MODE == MODE_ADJ) {
+        if constexpr (MB == MODE_ADJ) {
             w0 = fma(S.cadj0, vr.x, w0);
             w1 = fma(S.cadj1, vr.y, w1);
         }
         *wout = make_double2(w0, w1);
-        if constexpr (MODE == MODE_ACCUM) {
+        if constexpr (MB == MODE_ACCUM) {
             const double b0 = p.first ? p.d0 * wr.x : po.x, b1 = p.first ? p.d0 * wr.y : po.y;
-            *pout = make_double2(fma(p.dn, w0, b0), fma(p.dn, w1, b1));
+            if constexpr (STOP) *pout = make_double2(fma(S.dn0, w0, b0), fma(S.dn1, w1, b1));
+            else *pout = make_double2(fma(p.dn, w0, b0), fma(p.dn, w1, b1));
         }
-        if constexpr (MODE == MODE_DOT) {
+        if constexpr (MB == MODE_DOT) {
             T.td[0] = fma(vr.x, w0, T.td[0]);
             T.td[1] = fma(vr.y, w1, T.td[1]);
             if (p.first) { T.t0d[0] = fma(vr.x, wr.x, T.t0d[0]); T.t0d[1] = fma(vr.y, wr.y, T.t0d[1]); }
         }
+        if constexpr (STOP) {
+            T.nd[0] = fma(w0, w0, T.nd[0]);
+            T.nd[1] = fma(w1, w1, T.nd[1]);
+        }
     } else if constexpr (PREC == LL_PREC_DF64) {
         df2_mac(A.ah, A.al, S.bh2, S.bl2, S.nbh2, wr.x, wr.y);
-        if constexpr (MODE == MODE_ADJ) df2_mac_pp(A.ah, A.al, S.ch2, S.cl2, S.nch2, vr.x, vr.y);
+        if constexpr (MB == MODE_ADJ) df2_mac_pp(A.ah, A.al, S.ch2, S.cl2, S.nch2, vr.x, vr.y);
         f2x wh, wl;
         df2_norm(A.ah, A.al, wh, wl);
         *wout = make_ulonglong2(wh, wl);
-        if constexpr (MODE == MODE_ACCUM) {
+        if constexpr (STOP) df2_mac_pp(T.nh2, T.nl2, wh, wl, f2_sub(zero2, wh), wh, wl);
+        if constexpr (MB == MODE_ACCUM) {
             f2x ph = zero2, pl = zero2;
             if (p.first) df2_mac(ph, pl, S.d0h2, S.d0l2, S.nd0h2, wr.x, wr.y);
             else { ph = po.x; pl = po.y; }
@@ -122,16 +137,17 @@ __device__ __forceinline__ void row_epilogue(const StepParams& p, const StepScal
             df2_norm(ph, pl, oh, ol);
             *pout = make_ulonglong2(oh, ol);
         }
-        if constexpr (MODE == MODE_DOT) {
+        if constexpr (MB == MODE_DOT) {
             const f2x nvh = f2_sub(zero2, vr.x);
             df2_mac_pp(T.th2, T.tl2, vr.x, vr.y, nvh, wh, wl);
             if (p.first) df2_mac_pp(T.t0h2, T.t0l2, vr.x, vr.y, nvh, wr.x, wr.y);
         }
     } else {  // LL_PREC_F32_MIXED
         f2x wn = f2_fma(S.beta2, wr, A.ah);
-        if constexpr (MODE == MODE_ADJ) wn = f2_fma(S.cf2, vr, wn);
+        if constexpr (MB == MODE_ADJ) wn = f2_fma(S.cf2, vr, wn);
         *wout = wn;
-        if constexpr (MODE == MODE_ACCUM) {
+        if constexpr (STOP) df2_mac_f(T.nh2, T.nl2, wn, zero2, f2_sub(zero2, wn), wn);
+        if constexpr (MB == MODE_ACCUM) {
             f2x ph = zero2, pl = zero2;
             if (p.first) df2_mac_f(ph, pl, S.d0h2, S.d0l2, S.nd0h2, wr);
             else { ph = po.x; pl = po.y; }
@@ -140,7 +156,7 @@ __device__ __forceinline__ void row_epilogue(const StepParams& p, const StepScal
             df2_norm(ph, pl, oh, ol);
             *pout = make_ulonglong2(oh, ol);
         }
-        if constexpr (MODE == MODE_DOT) {
+        if constexpr (MB == MODE_DOT) {
             // exact FP32 products v * w accumulated in double-float
             const f2x nv = f2_sub(zero2, vr);
             df2_mac_f(T.th2, T.tl2, vr, zero2, nv, wn);
@@ -149,29 +165,43 @@ __device__ __forceinline__ void row_epilogue(const StepParams& p, const StepScal
     }
 }
 
-// Block reduction of the trace partials per column in row-lane order, then the last CTA sums the
-// per-CTA partials in CTA order (both orders fixed: the result is deterministic). `red` must hold
-// 2 * blockDim.x doubles; every thread of the CTA calls this.
-template <int PREC>
+// Block reduction of the per-column partials in row-lane order, then the last CTA sums the
+// per-CTA partials in CTA order (both orders fixed: the result is deterministic). Quantities:
+// 0 = V . W_{j+1} and 1 = V . W_0 (first step) in the DOT modes, 2 = ||W_{j+1}||^2 in the STOP
+// modes, where the last CTA then applies Algorithm 2's test |d_{j+1}| ||W_{j+1}|| > tol to every
+// live column. `red` must hold 2 * blockDim.x doubles; every thread of the CTA calls this.
+template <int PREC, int MODE>
 __device__ __forceinline__ void trace_reduce(const StepParams& p, TracePart& T, double* red, int tp, int rows,
                                              bool* s_last) {
+    constexpr int MB = base_mode(MODE);
+    constexpr bool STOP = stop_mode(MODE);
     const int tid = threadIdx.x;
     if constexpr (PREC != LL_PREC_F64) {
         float h0, h1, l0, l1;
-        f2_unpack(T.th2, h0, h1);
-        f2_unpack(T.tl2, l0, l1);
-        T.td[0] = (double)h0 + (double)l0;
-        T.td[1] = (double)h1 + (double)l1;
-        f2_unpack(T.t0h2, h0, h1);
-        f2_unpack(T.t0l2, l0, l1);
-        T.t0d[0] = (double)h0 + (double)l0;
-        T.t0d[1] = (double)h1 + (double)l1;
+        if constexpr (MB == MODE_DOT) {
+            f2_unpack(T.th2, h0, h1);
+            f2_unpack(T.tl2, l0, l1);
+            T.td[0] = (double)h0 + (double)l0;
+            T.td[1] = (double)h1 + (double)l1;
+            f2_unpack(T.t0h2, h0, h1);
+            f2_unpack(T.t0l2, l0, l1);
+            T.t0d[0] = (double)h0 + (double)l0;
+            T.t0d[1] = (double)h1 + (double)l1;
+        }
+        if constexpr (STOP) {
+            f2_unpack(T.nh2, h0, h1);
+            f2_unpack(T.nl2, l0, l1);
+            T.nd[0] = (double)h0 + (double)l0;
+            T.nd[1] = (double)h1 + (double)l1;
+        }
     }
     const int b = p.b;
-    const int nred = p.first ? 2 : 1;
-    for (int q = 0; q < nred; ++q) {
-        red[2 * tid] = q ? T.t0d[0] : T.td[0];
-        red[2 * tid + 1] = q ? T.t0d[1] : T.td[1];
+    for (int q = 0; q < 3; ++q) {
+        if (q < 2 && MB != MODE_DOT) continue;
+        if (q == 1 && !p.first) continue;
+        if (q == 2 && !STOP) continue;
+        red[2 * tid] = q == 0 ? T.td[0] : (q == 1 ? T.t0d[0] : T.nd[0]);
+        red[2 * tid + 1] = q == 0 ? T.td[1] : (q == 1 ? T.t0d[1] : T.nd[1]);
         __syncthreads();
         for (int c = tid; c < b; c += blockDim.x) {
             const int pc = c >> 1, lane = c & 1;
@@ -186,11 +216,30 @@ __device__ __forceinline__ void trace_reduce(const StepParams& p, TracePart& T, 
     __syncthreads();
     if (*s_last) {
         __threadfence();
-        for (int c = tid; c < nred * b; c += blockDim.x) {
-            const int q = c / b, cc = c - q * b;
-            double s = 0.0;
-            for (int g = 0; g < (int)gridDim.x; ++g) s += __ldcg(&p.partials[((size_t)q * gridDim.x + g) * b + cc]);
-            if (q == 0) p.dots_next[cc] = s; else p.dots_first[cc] = s;
+        if constexpr (MB == MODE_DOT) {
+            const int nred = p.first ? 2 : 1;
+            for (int c = tid; c < nred * b; c += blockDim.x) {
+                const int q = c / b, cc = c - q * b;
+                double s = 0.0;
+                for (int g = 0; g < (int)gridDim.x; ++g) s += __ldcg(&p.partials[((size_t)q * gridDim.x + g) * b + cc]);
+                if (q == 0) p.dots_next[cc] = s; else p.dots_first[cc] = s;
+            }
+        }
+        if constexpr (STOP) {
+            int any = 0;
+            for (int c = tid; c < b; c += blockDim.x) {
+                double s = 0.0;
+                for (int g = 0; g < (int)gridDim.x; ++g) s += __ldcg(&p.partials[((size_t)2 * gridDim.x + g) * b + c]);
+                int l = p.live[c];
+                if (l && !(fabs(p.dn) * sqrt(s) > p.tol)) {
+                    p.live[c] = 0;
+                    p.stop_deg[c] = p.jnext;
+                    l = 0;
+                }
+                any |= l;
+            }
+            any = __syncthreads_or(any);
+            if (tid == 0 && !any) *p.done = 1;
         }
         if (tid == 0) *p.ticket = 0u;
     }

@@ -34,6 +34,12 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     using PP = typename PairT<PREC>::P;
     using Raw = typename PairT<PREC>::Raw;
     using RecT = Rec<PREC>;
+    constexpr int MB = base_mode(MODE);
+    if constexpr (stop_mode(MODE)) {
+        // every column of the pass has met the stopping rule (the first step always runs: it
+        // writes P = d_0 W_0 and the traces of W_0 that degree-0 columns keep)
+        if (!p.first && *p.done) return;
+    }
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full[TMA_MAX_STAGES];
     __shared__ __align__(8) unsigned long long empty[TMA_MAX_STAGES];
@@ -51,7 +57,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     const int cthreads = (int)blockDim.x - 32 * nprod;   // consumer threads
     const int cwarps = cthreads >> 5;
     const int n = p.n;
-    const bool has_aux = (MODE == MODE_DOT || MODE == MODE_ADJ) || (MODE == MODE_ACCUM && !p.first);
+    const bool has_aux = (MB == MODE_DOT || MB == MODE_ADJ) || (MB == MODE_ACCUM && !p.first);
 
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -187,11 +193,11 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
         const Raw* __restrict__ vals = static_cast<const Raw*>(p.vals);
         PP* __restrict__ pblk = static_cast<PP*>(p.p);
         const int* __restrict__ colind = p.colind;
-        const StepScalars<PREC> S(p, cp);
+        const StepScalars<PREC> S(p, cp, stop_mode(MODE) && MB == MODE_ACCUM);
         const unsigned cpoff = (unsigned)(cp * sizeof(WP));
         const unsigned own_off = (unsigned)(rlane + TMA_HALO) * (unsigned)q.rowbytes + cpoff;
         const unsigned aux_off = (unsigned)q.off_aux + (unsigned)rlane * (unsigned)q.auxbytes +
-                                 (unsigned)(cp * (MODE == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
+                                 (unsigned)(cp * (MB == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
         int s = 0, ph = 0;
         int r = (int)blockIdx.x * R + rlane;
         WP* wo = wout + (size_t)r * ldq + cp;   // this thread's W_{j+1} and P pairs, advanced per tile
@@ -214,8 +220,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 const WP wr = *reinterpret_cast<const WP*>(st + own_off);
                 WP vr{};
                 PP po{};
-                if constexpr (MODE == MODE_DOT || MODE == MODE_ADJ) vr = *reinterpret_cast<const WP*>(st + aux_off);
-                if constexpr (MODE == MODE_ACCUM) {
+                if constexpr (MB == MODE_DOT || MB == MODE_ADJ) vr = *reinterpret_cast<const WP*>(st + aux_off);
+                if constexpr (MB == MODE_ACCUM) {
                     if (!p.first) po = *reinterpret_cast<const PP*>(st + aux_off);
                 }
                 RowAcc A;
@@ -256,8 +262,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
         }
     }
     const int any_dead = __syncthreads_or(dead ? 1 : 0);
-    if constexpr (MODE == MODE_DOT) {
-        if (!any_dead) trace_reduce<PREC>(p, T, reinterpret_cast<double*>(smem), tp, R, &s_last);
+    if constexpr (MB == MODE_DOT || stop_mode(MODE)) {
+        if (!any_dead) trace_reduce<PREC, MODE>(p, T, reinterpret_cast<double*>(smem), tp, R, &s_last);
     }
 }
 
@@ -296,10 +302,10 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     const long long ld = p.ldw;
     if (ld > 256 || (ld * ew) % 16 != 0) return false;
     int auxbytes = 0;
-    if (mode == MODE_DOT || mode == MODE_ADJ) {
+    if (base_mode(mode) == MODE_DOT || mode == MODE_ADJ) {
         if (p.ldv != ld) return false;
         auxbytes = (int)(ld * ew);
-    } else if (mode == MODE_ACCUM) {
+    } else if (base_mode(mode) == MODE_ACCUM) {
         if (p.ldp > 256 || (p.ldp * 8) % 16 != 0) return false;
         auxbytes = (int)(p.ldp * 8);
     }
@@ -364,7 +370,8 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     int per_sm = 0;
     switch (precision * NUM_MODES + mode) {
 #define OCC(P_, M_) case P_ * NUM_MODES + M_: per_sm = occupancy_tma<P_, M_>(L.threads, L.smem); break;
-#define OCC4(P_) OCC(P_, MODE_PLAIN) OCC(P_, MODE_ACCUM) OCC(P_, MODE_DOT) OCC(P_, MODE_ADJ)
+#define OCC4(P_) OCC(P_, MODE_PLAIN) OCC(P_, MODE_ACCUM) OCC(P_, MODE_DOT) OCC(P_, MODE_ADJ) \
+    OCC(P_, MODE_ACCUM_STOP) OCC(P_, MODE_DOT_STOP)
         OCC4(LL_PREC_F64) OCC4(LL_PREC_DF64) OCC4(LL_PREC_F32_MIXED)
 #undef OCC4
 #undef OCC
@@ -407,13 +414,14 @@ cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const S
     if (!encode_rows(&g, p.win, ew, p.ldw, p.n, 1) || !encode_rows(&w, p.win, ew, p.ldw, p.n, L.q.R + 2 * TMA_HALO))
         return cudaErrorInvalidValue;
     bool aux_ok = true;
-    if (mode == MODE_DOT || mode == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, p.n, L.q.R);
-    else if (mode == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, p.n, L.q.R);
+    if (base_mode(mode) == MODE_DOT || mode == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, p.n, L.q.R);
+    else if (base_mode(mode) == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, p.n, L.q.R);
     else a = w;
     if (!aux_ok) return cudaErrorInvalidValue;
     switch (precision * NUM_MODES + mode) {
 #define LCH(P_, M_) case P_ * NUM_MODES + M_: return launch_tma_typed<P_, M_>(L, g, w, a, p, s);
-#define LCH4(P_) LCH(P_, MODE_PLAIN) LCH(P_, MODE_ACCUM) LCH(P_, MODE_DOT) LCH(P_, MODE_ADJ)
+#define LCH4(P_) LCH(P_, MODE_PLAIN) LCH(P_, MODE_ACCUM) LCH(P_, MODE_DOT) LCH(P_, MODE_ADJ) \
+    LCH(P_, MODE_ACCUM_STOP) LCH(P_, MODE_DOT_STOP)
         LCH4(LL_PREC_F64) LCH4(LL_PREC_DF64) LCH4(LL_PREC_F32_MIXED)
 #undef LCH4
 #undef LCH
