@@ -430,6 +430,60 @@ def workload_f1(L, h, A, grid: int, degree: int, seeds: int = 3):
     return out
 
 
+def workload_f4(L, h, N: int = 5000, thetas=(-0.24, -0.23, -0.22, -0.21, -0.20), probes: int = 30):
+    """Section 5.3's GMRF: Q(theta) = I + theta Adj on the 5000 x 5000 4-neighbour grid (n = 2.5e7,
+    nnz = 1.25e8). For each theta of the grid: Gershgorin bounds [1 - 4|theta|, 1 + 4|theta|]
+    (sigma = 1 - 4|theta|), degree from the bounds, Hutch++ with 30 Rademacher probes (seed 0),
+    log det Q(theta) and its theta-derivative (adjoint + chain, d a_e / d theta = 1 on the
+    neighbour entries) against the closed forms. The structure is built once; the values of each
+    theta are written on the device."""
+    import math as _m
+    import time as _t
+    import torch
+    from synth import gmrf_theta
+    from tests.pins import dlogdet_gmrf_theta, logdet_gmrf_theta
+    t0 = _t.perf_counter()
+    A = gmrf_theta(N, 1.0)
+    t_gen = _t.perf_counter() - t0
+    dA = L.DeviceCSR.from_host(A)
+    n, nnz, k = A.n, A.nnz, probes // 3
+    del A
+    counts = dA.rowptr[1:] - dA.rowptr[:-1]
+    rows = torch.repeat_interleave(torch.arange(n, device="cuda", dtype=torch.int32), counts)
+    offd = (dA.colind != rows).to(torch.float64)          # d a_e / d theta
+    del rows
+    out = {"n": n, "nnz": nnz, "generate_s": t_gen, "thetas": list(thetas), "rows": []}
+    for theta in thetas:
+        dA.values = torch.where(offd > 0, torch.full_like(offd, theta), torch.ones_like(offd))
+        lo, hi = L.ll_gershgorin(h, dA)
+        sg = lo if lo < 1 else 1.0
+        kap = hi / lo
+        rho = (_m.sqrt(kap) + 1) / (_m.sqrt(kap) - 1)
+        m = max(10, min(250, _m.ceil(_m.log(1e6) / _m.log(rho))))
+        exact, dexact = logdet_gmrf_theta(N, theta), dlogdet_gmrf_theta(N, theta)
+        row = {"theta": theta, "bounds": [lo, hi], "sigma": sg, "degree": m, "exact_logdet": exact,
+               "exact_dlogdet_dtheta": dexact}
+        for prec in ("df64", "f32"):
+            opts = L.options(degree=m, probes=probes, seed=0, precision=prec, keep_for_backward=(prec == "df64"))
+            ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lo, hi, opts), 2, 1)
+            inf = h.info()
+            r = {"ms_forward": ms_f, "estimate": est, "rel_err_vs_exact": abs(est - exact) / abs(exact),
+                 "GBps_estimate": estimate_bytes(n, nnz, k, m, prec) / (ms_f / 1e3) / 1e9,
+                 "phase_ms": {"probes": inf["ms_probes"], "pass1": inf["ms_pass1"], "qr": inf["ms_qr"],
+                              "pass2": inf["ms_pass2"]}}
+            if prec == "df64":
+                ms_b, g = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 1, 0)
+                th = float(L.ll_param_grad(h, g, offd[None, :])[0])
+                del g
+                r.update({"ms_backward": ms_b, "dlogdet_dtheta": th,
+                          "rel_err_dtheta": abs(th - dexact) / abs(dexact)})
+            row[prec] = r
+        out["rows"].append(row)
+    out["workload"] = (f"GMRF Q(theta) = I + theta Adj on {N}^2 (n={n}, nnz={nnz}), theta in {list(thetas)}, "
+                       f"Gershgorin bounds, degree from the bounds, Hutch++ {probes} Rademacher probes, seed 0")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -447,8 +501,8 @@ def main():
                     help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
                     help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
-    ap.add_argument("--workloads", default="c1,c3,c4,f1,f3",
-                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5,f1,f3; '' for none)")
+    ap.add_argument("--workloads", default="c1,c3,c4,f1,f3,f4",
+                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5,f1,f3,f4; '' for none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -574,7 +628,7 @@ def main():
             extra[w] = workload_f1(L, h, A, args.grid, m)
             continue
         fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4, "c5": workload_config5,
-              "f3": workload_f3}[w]
+              "f3": workload_f3, "f4": workload_f4}[w]
         extra[w] = fn(L, h, log2n=args.c5_log2n) if w == "c5" else fn(L, h)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
     from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only

@@ -13,6 +13,7 @@ from .matrices import (  # noqa: F401
     gmrf_batch_params,
     powerlaw_laplacian,
     pentadiagonal,
+    gmrf_theta,
     diagonal,
     random_spd,
     csr_from_dense,

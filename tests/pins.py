@@ -92,6 +92,23 @@ def dlogdet_matern_2d(N: int, kappa: float, tau: float) -> tuple[float, float]:
     return 4.0 * kappa * math.fsum(1.0 / (kappa * kappa + s2)), N * N / tau
 
 
+def adj_eigs_1d(N: int) -> np.ndarray:
+    """Eigenvalues of the path graph's adjacency: 2 cos(i pi / (N + 1)), i = 1..N."""
+    return 2.0 * np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+
+
+def logdet_gmrf_theta(N: int, theta: float) -> float:
+    """log det (I + theta Adj) on the N x N grid: sum_ij log(1 + theta (a_i + a_j))."""
+    a = adj_eigs_1d(N)
+    return math.fsum(math.fsum(np.log1p(theta * (a + ai))) for ai in a)
+
+
+def dlogdet_gmrf_theta(N: int, theta: float) -> float:
+    """d/dtheta log det (I + theta Adj) = sum_ij (a_i + a_j) / (1 + theta (a_i + a_j))."""
+    a = adj_eigs_1d(N)
+    return math.fsum(math.fsum((a + ai) / (1.0 + theta * (a + ai))) for ai in a)
+
+
 def logdet_banded(A, bandwidth: int = 2) -> float:
     """log det A = 2 sum_i log(R_ii) for a symmetric positive definite CSR matrix whose entries lie
     within `bandwidth` of the diagonal, from LAPACK's banded Cholesky (SciPy) in O(n)."""

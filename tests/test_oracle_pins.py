@@ -630,3 +630,42 @@ def test_adaptive_hutchpp_degrees_and_accuracy_follow_tol():
     assert errs[0] > errs[1] > errs[2] > errs[3]
     r = logdet.logdet_leja(A, lo, hi, 80, 12, seed=4, tol=1e-300)
     assert r["estimate"] == fixed
+
+
+# ------------------------------------------------ the GMRF of the maximum-likelihood experiment
+
+@pytest.mark.parametrize("theta", [-0.24, -0.22, -0.1, 0.2])
+def test_gmrf_theta_closed_form_vs_dense(theta):
+    """Q(theta) = I + theta Adj on a 9 x 9 grid: the closed-form log-determinant and its
+    theta-derivative (Section 5.3's model) against a dense LU and tr(Q^-1 Adj)."""
+    from synth import gmrf_theta
+    N = 9
+    Q = gmrf_theta(N, theta).to_scipy().toarray()
+    Adj = Q - np.eye(N * N)
+    Adj = Adj / theta
+    sign, ld = np.linalg.slogdet(Q)
+    assert sign > 0
+    assert pins.logdet_gmrf_theta(N, theta) == pytest.approx(ld, rel=1e-13)
+    assert pins.dlogdet_gmrf_theta(N, theta) == pytest.approx(np.trace(np.linalg.solve(Q, Adj)), rel=1e-11)
+
+
+def test_gmrf_theta_bounds_and_sigma():
+    """Gershgorin gives the paper's interval [1 - 4|theta|, 1 + 4|theta|] (interior rows have four
+    neighbours), so sigma = 1 - 4|theta| as Section 5.3 sets it."""
+    from synth import gmrf_theta
+    for theta in (-0.22, 0.15):
+        lo, hi = logdet.gershgorin(gmrf_theta(12, theta))
+        assert lo == pytest.approx(1 - 4 * abs(theta), abs=1e-15)
+        assert hi == pytest.approx(1 + 4 * abs(theta), abs=1e-15)
+        assert logdet.sigma_of(lo) == pytest.approx(1 - 4 * abs(theta), abs=1e-15)
+
+
+def test_gmrf_theta_exact_trace_against_closed_form():
+    """With k >= n the Hutch++ estimate is the exact polynomial trace n log sigma + tr p(Q~);
+    at degree 70 on kappa <= 49 it matches the closed-form log-determinant to 1e-9."""
+    from synth import gmrf_theta
+    N, theta = 7, -0.24
+    A = gmrf_theta(N, theta)
+    lo, hi = logdet.gershgorin(A)
+    r = logdet.logdet_leja(A, lo, hi, 70, 3 * A.n, seed=2)
+    assert r["estimate"] == pytest.approx(pins.logdet_gmrf_theta(N, theta), rel=1e-9, abs=1e-9)

@@ -49,3 +49,20 @@ def test_pentadiagonal_family():
     assert np.all(d - off > 0) and d.min() >= A.n
     B = pentadiagonal(500, seed=4)
     assert np.array_equal(A.values, B.values) and not np.array_equal(A.values, pentadiagonal(500, seed=5).values)
+
+
+def test_gmrf_theta_matches_kronecker_form():
+    """The direct CSR construction equals I + theta (Adj_path (x) I + I (x) Adj_path)."""
+    import scipy.sparse as sp
+    from synth import gmrf_theta
+    for N, theta in ((1, -0.22), (2, 0.1), (9, -0.22), (16, 0.24)):
+        A = gmrf_theta(N, theta)
+        e = np.ones(N)
+        P = sp.diags([e[:-1], e[:-1]], [-1, 1], shape=(N, N), format="csr")
+        I = sp.identity(N, format="csr")
+        ref = (sp.identity(N * N) + theta * (sp.kron(P, I) + sp.kron(I, P))).tocsr()
+        ref.eliminate_zeros()
+        ref.sort_indices()
+        assert np.array_equal(A.rowptr, ref.indptr) and np.array_equal(A.colind, ref.indices)
+        assert np.array_equal(A.values, ref.data)
+        assert A.rowptr.dtype == np.int32 and A.colind.dtype == np.int32
