@@ -11,7 +11,8 @@ Follows arXiv 2603.02207:
   * Hutch++ as in Algorithm 3 / Section 4.1 (sketch, Householder QR, deterministic part,
     Hutchinson part on the deflated probes);
   * the plain Hutchinson estimator the paper starts from (Eq. Léja8), on the same probes;
-  * the derivative of the frozen-basis estimator with respect to the stored matrix values.
+  * the derivative of the frozen-basis estimator with respect to the stored matrix values, and
+    the derivative through the sketch's QR (Algorithm 3 step 4).
 
 Readings fixed by this library where the paper is silent or ambiguous:
   * the operator in Algorithm 2's update (Q - xi_m I) is the scaled operator
@@ -30,7 +31,8 @@ Readings fixed by this library where the paper is silent or ambiguous:
   * the QR of step 4 is Householder (NumPy/LAPACK); any orthonormal basis of span(Y) gives the
     same estimate;
   * the gradient differentiates the estimator with Q, the deflated probes, the bounds, sigma
-    and the coefficients d held fixed, per stored CSR entry.
+    and the coefficients d held fixed, per stored CSR entry; the full gradient also carries the
+    derivative through Q = orth(p(A~) S) and G' (the bounds, sigma and d still fixed);
 """
 from __future__ import annotations
 
@@ -304,24 +306,14 @@ def logdet_hutchinson(A, lmin: float, lmax: float, degree: int, probes: int, see
 # gradient of the frozen-basis estimator
 # ---------------------------------------------------------------------------------------------
 
-def hutchpp_grad_values(A, lmin: float, lmax: float, degree: int, Q: np.ndarray, Gp: np.ndarray,
-                        s_mode: str = "center") -> np.ndarray:
-    """d E / d a_e for every stored entry e = (r, c) of A, where
-    E(A) = n log sigma + sum_j d_j <U, W_j>,  U = [Q | Gp / k],  W_0 = [Q | Gp],
-    W_{j+1} = (B - xi_j I) W_j,  B = (A / sigma - c I) / gamma,
-    with Q, Gp, the bounds, sigma and d held fixed.
+def _grad_values_uv(A, sigma: float, c: float, gamma: float, xi, d, V: np.ndarray, U: np.ndarray) -> np.ndarray:
+    """d/d a_e of sum_j d_j <U, W_j> with W_0 = V, W_{j+1} = (B - xi_j I) W_j, U and V held fixed.
 
     Reverse recurrence: Lambda_m = d_m U, Lambda_j = d_j U + (B - xi_j I)^T Lambda_{j+1};
     dE/dB = sum_{j<m} Lambda_{j+1} W_j^T and dB/da_e = E_rc / (sigma gamma).
     """
-    sigma = sigma_of(lmin)
-    lt, ut = lmin / sigma, lmax / sigma
-    xi, c, gamma, d, _ = newton_leja_setup(lt, ut, degree, s_mode)
     M = _scipy(A)
     MT = M.T.tocsr()
-    k = Gp.shape[1]
-    V = np.concatenate([Q, Gp], axis=1)
-    U = np.concatenate([Q, Gp / k], axis=1) if k > 0 else Q.copy()
     rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
     cols = np.asarray(A.colind, dtype=np.int64)
     m = len(d) - 1
@@ -337,6 +329,59 @@ def hutchpp_grad_values(A, lmin: float, lmax: float, degree: int, Q: np.ndarray,
             g += lam[rows] * Ws[j][cols] / (sigma * gamma)
             lam = d[j] * u + (((MT @ lam) / sigma - c * lam) / gamma - xi[j] * lam)
     return g
+
+
+def hutchpp_grad_values(A, lmin: float, lmax: float, degree: int, Q: np.ndarray, Gp: np.ndarray,
+                        s_mode: str = "center") -> np.ndarray:
+    """d E / d a_e for every stored entry e = (r, c) of A, where
+    E(A) = n log sigma + sum_j d_j <U, W_j>,  U = [Q | Gp / k],  W_0 = [Q | Gp],
+    W_{j+1} = (B - xi_j I) W_j,  B = (A / sigma - c I) / gamma,
+    with Q, Gp, the bounds, sigma and d held fixed."""
+    sigma = sigma_of(lmin)
+    lt, ut = lmin / sigma, lmax / sigma
+    xi, c, gamma, d, _ = newton_leja_setup(lt, ut, degree, s_mode)
+    k = Gp.shape[1]
+    V = np.concatenate([Q, Gp], axis=1)
+    U = np.concatenate([Q, Gp / k], axis=1) if k > 0 else Q.copy()
+    return _grad_values_uv(A, sigma, c, gamma, xi, d, V, U)
+
+
+def hutchpp_qr_weights(A, lmin: float, lmax: float, degree: int, S: np.ndarray, G: np.ndarray,
+                       s_mode: str = "center") -> dict:
+    """The weights that carry the derivative of Algorithm 3's estimate through the sketch's QR.
+
+    E = tr(F Pi) + (1/k) tr(F (I - Pi) G G^T (I - Pi)), Pi = Q Q^T the projector onto
+    span(Y), Y = F S = Q R, F = p(A~). With the bounds, sigma and d fixed,
+      dE = tr(dF [Pi + G' G'^T / k]) + tr(dPi Z),  Z = F - H (I - Pi) F - F (I - Pi) H,  H = G G^T / k,
+      dPi = (I - Pi) dY Y^+ + (Y^+)^T dY^T (I - Pi),  Y^+ = R^-1 Q^T,  dY = dF S,
+    so tr(dPi Z) = tr(Gamma^T dF S) with Gamma = 2 (I - Pi) Z Q R^-T, where
+    Z Q = F Q - (1/k) G (G'^T F Q) - (1/k) (F G') (G^T Q).
+    Returns Q, R, G', F Q, F G' and Gamma."""
+    sigma = sigma_of(lmin)
+    lt, ut = lmin / sigma, lmax / sigma
+    xi, c, gamma, d, _ = newton_leja_setup(lt, ut, degree, s_mode)
+    M = _scipy(A)
+    k = G.shape[1]
+    Y = leja_apply_columns(M, S, xi, d, c, gamma, sigma)
+    Q, R = np.linalg.qr(Y, mode="reduced")
+    Gp = G - Q @ (Q.T @ G)
+    FQ = leja_apply_columns(M, Q, xi, d, c, gamma, sigma)
+    FG = leja_apply_columns(M, Gp, xi, d, c, gamma, sigma)
+    ZQ = FQ - G @ (Gp.T @ FQ) / k - FG @ (G.T @ Q) / k
+    X = ZQ - Q @ (Q.T @ ZQ)
+    Gamma = 2.0 * np.linalg.solve(R, X.T).T     # 2 X R^-T
+    return dict(Q=Q, R=R, Gp=Gp, FQ=FQ, FG=FG, Gamma=Gamma, sigma=sigma, c=c, gamma=gamma, xi=xi, d=d)
+
+
+def hutchpp_full_grad_values(A, lmin: float, lmax: float, degree: int, S: np.ndarray, G: np.ndarray,
+                             s_mode: str = "center") -> np.ndarray:
+    """d E / d a_e of Algorithm 3's estimate with Q = orth(p(A~) S) and G' = (I - QQ^T) G
+    differentiated too (the bounds, sigma and d held fixed): the frozen-basis gradient plus the
+    term sum_c Gamma_c^T (dF) S_c of hutchpp_qr_weights, by the same reverse recurrence with
+    W_0 = S and U = Gamma."""
+    w = hutchpp_qr_weights(A, lmin, lmax, degree, S, G, s_mode)
+    g = hutchpp_grad_values(A, lmin, lmax, degree, w["Q"], w["Gp"], s_mode)
+    return g + _grad_values_uv(A, w["sigma"], w["c"], w["gamma"], w["xi"], w["d"], S, w["Gamma"])
 
 
 def frozen_estimate(A, values: np.ndarray, lmin: float, lmax: float, degree: int, Q: np.ndarray,

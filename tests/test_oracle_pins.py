@@ -669,3 +669,47 @@ def test_gmrf_theta_exact_trace_against_closed_form():
     lo, hi = logdet.gershgorin(A)
     r = logdet.logdet_leja(A, lo, hi, 70, 3 * A.n, seed=2)
     assert r["estimate"] == pytest.approx(pins.logdet_gmrf_theta(N, theta), rel=1e-9, abs=1e-9)
+
+
+# ------------------------------------------------------ derivative through the sketch's QR
+
+def _estimate_with_values(A, values, lmin, lmax, degree, S, G):
+    from synth import CSR
+    B = CSR(A.n, A.rowptr, A.colind, np.asarray(values, dtype=np.float64))
+    return logdet.hutchpp_logdet(B, lmin, lmax, degree, S, G)["estimate"]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_full_gradient_matches_finite_differences(seed):
+    """Central differences of Algorithm 3's estimate (S, G, bounds and degree fixed; Q and G'
+    recomputed from the perturbed matrix by Householder QR) against the frozen-basis gradient
+    plus the term through the QR. The QR term is far above the differencing error, so dropping
+    it, or a wrong sign or factor in it, fails."""
+    A = random_spd(40, nnz_per_row=5, seed=seed)
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    lmin, lmax, degree = 0.9 * lam[0], 1.1 * lam[-1], 18
+    S = rng.rademacher(seed, rng.STREAM_S, A.n, 4)
+    G = rng.rademacher(seed, rng.STREAM_G, A.n, 4)
+    full = logdet.hutchpp_full_grad_values(A, lmin, lmax, degree, S, G)
+    r = logdet.hutchpp_logdet(A, lmin, lmax, degree, S, G)
+    frozen = logdet.hutchpp_grad_values(A, lmin, lmax, degree, r["Q"], r["Gp"])
+    picks = np.random.default_rng(seed).choice(A.nnz, 14, replace=False)
+    for e in picks:
+        h = 1e-5 * max(1.0, abs(A.values[e]))
+        vp, vm = A.values.copy(), A.values.copy()
+        vp[e] += h
+        vm[e] -= h
+        fd = (_estimate_with_values(A, vp, lmin, lmax, degree, S, G) -
+              _estimate_with_values(A, vm, lmin, lmax, degree, S, G)) / (2 * h)
+        assert full[e] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    assert np.max(np.abs(full - frozen)) > 1e3 * 1e-6 * np.max(np.abs(full))
+
+
+def test_full_gradient_equals_frozen_when_the_sketch_spans_everything():
+    """k = n: span(Y) = R^n, Pi = I, G' = 0 and Gamma = 2 (I - Pi) Z Q R^-T = 0."""
+    A = random_spd(9, seed=2)
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    S = rng.gaussian(1, rng.STREAM_S, A.n, A.n)
+    G = rng.gaussian(1, rng.STREAM_G, A.n, A.n)
+    w = logdet.hutchpp_qr_weights(A, 0.9 * lam[0], 1.1 * lam[-1], 20, S, G)
+    assert np.max(np.abs(w["Gamma"])) < 1e-10 * np.max(np.abs(w["FQ"]))
