@@ -238,10 +238,18 @@ def workload_config3(L, h, grid: int = 1024, degree: int = 80):
         inf = h.info()
         ms_b, g = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 2, 1)
         th = L.ll_param_grad(h, g, dv)
+        del g
+        # the exact derivative of the estimate (through the sketch's QR)
+        ms_bq, gq = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0, through_qr=True), 1, 1)
+        thq = L.ll_param_grad(h, gq, dv)
+        del gq
         out[prec] = {"ms_forward": ms_f, "ms_backward": ms_b, "ms_forward_plus_gradient": ms_f + ms_b,
+                     "ms_backward_through_qr": ms_bq,
                      "estimate": est, "rel_err_vs_exact": abs(est - exact) / abs(exact),
                      "dlogdet_dkappa": th[0], "dlogdet_dtau": th[1],
                      "rel_err_dkappa": abs(th[0] - ex_k) / abs(ex_k), "rel_err_dtau": abs(th[1] - ex_t) / abs(ex_t),
+                     "through_qr_rel_err_dkappa": abs(thq[0] - ex_k) / abs(ex_k),
+                     "through_qr_rel_err_dtau": abs(thq[1] - ex_t) / abs(ex_t),
                      "forward_phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
     return {"workload": f"Matern tau(kappa^2 I + L2D)^2 {grid}^2 (n={A.n}, nnz={A.nnz}), kappa={kappa}, tau={tau}, "
                         f"bounds [{lmin}, {lmax:.4f}], degree {degree}, 60 Gaussian probes, seed 0", **out}

@@ -283,6 +283,19 @@ ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* A_host, ll_bounds b
  * grad_values: device, nnz doubles, overwritten. Enqueue only. */
 ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream);
 
+/* Derivative of the last kept forward estimate through the sketch's QR as well (Algorithm 3
+ * step 4: Q = orth(Y), Y = p(A~) S, and G' = (I - Q Q^T) G move with A; the bounds, sigma and the
+ * coefficients stay fixed): ll_logdet_backward's gradient plus the term
+ *   grad_output * d/da_e tr(Gamma^T p(A~) S),  Gamma = 2 (I - Q Q^T) Z Q R^-T,
+ *   Z Q = F Q - (1/k) G (G'^T F Q) - (1/k) (F G') (G^T Q),  F = p(A~),  Y = Q R,
+ * which is the derivative of tr(dPi Z) for the projector Pi = Q Q^T onto span(Y). F [Q | G'] is
+ * recomputed by one pass-1 sweep, the n x k products run on the GPU in FP64, R^-1 = R1^-1 R2^-1
+ * (the two CholeskyQR factors) is formed on the host, and the second term runs the same reverse
+ * recurrence with W_0 = S and U = Gamma. After a Hutchinson forward, or with k >= n (Q spans
+ * R^n, so Gamma = 0), it equals ll_logdet_backward. Same arguments and requirements as
+ * ll_logdet_backward; synchronises `stream`. */
+ll_status ll_logdet_backward_qr(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream);
+
 /* Chain to model parameters theta_p of a parameterised matrix A(theta) (e.g. the tau and kappa of a
  * Matérn GMRF): out[p] = sum_e grad_values[e] * dvalues[p * ld + e], p < nparams, where
  * dvalues[p * ld + e] = d a_e / d theta_p for every stored entry e < nnz. grad_values and

@@ -85,6 +85,7 @@ SIGNATURES = {
     "ll_logdet_forward": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, ctypes.POINTER(ll_options), _PD, _P]),
     "ll_logdet_forward_host": (_I, [_P, ctypes.POINTER(ll_csr), ll_bounds, ctypes.POINTER(ll_options), _PD, _P]),
     "ll_logdet_backward": (_I, [_P, ctypes.POINTER(ll_csr), _D, _P, _P]),
+    "ll_logdet_backward_qr": (_I, [_P, ctypes.POINTER(ll_csr), _D, _P, _P]),
     "ll_param_grad": (_I, [_P, _P, _P, _I64, _I64, _I, _PD, _P]),
     "ll_logdet_batched": (_I, [_P, ctypes.POINTER(ll_csr), ctypes.POINTER(ll_bounds), _I,
                                ctypes.POINTER(ll_options), ctypes.POINTER(_I), _PD, _P]),

@@ -256,11 +256,14 @@ def ll_logdet_forward_host(h: Handle, csr, lmin: float, lmax: float, opts: _ffi.
     return est.value
 
 
-def ll_logdet_backward(h: Handle, A: DeviceCSR, grad_output: float = 1.0, stream=None):
+def ll_logdet_backward(h: Handle, A: DeviceCSR, grad_output: float = 1.0, stream=None, through_qr: bool = False):
+    """Gradient of the kept forward estimate with respect to the stored values: with Q and G'
+    frozen, or (through_qr) with the derivative through the sketch's QR as well."""
     torch = _torch()
     g = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
     a = A.c()
-    h.check(h._lib.ll_logdet_backward(h.ptr, ctypes.byref(a), grad_output, g.data_ptr(), _stream_ptr(stream)))
+    fn = h._lib.ll_logdet_backward_qr if through_qr else h._lib.ll_logdet_backward
+    h.check(fn(h.ptr, ctypes.byref(a), grad_output, g.data_ptr(), _stream_ptr(stream)))
     return g
 
 

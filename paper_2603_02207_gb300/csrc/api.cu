@@ -73,6 +73,7 @@ struct ll_handle {
     int64_t kept_n = 0, kept_nnz = 0;
     int kept_kq = 0, kept_kg = 0, kept_m = 0, kept_prec = 0, kept_ckpt = 0;
     bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
+    bool kept_qr = false;     // the kept forward ran the sketch and its CholeskyQR2 (S, G, R1^-1, R2^-1 kept)
     // final degree of every column of both passes of the last forward (Algorithm 2's rule)
     bool have_forward = false;
     std::vector<int> last_deg1, last_deg2;
@@ -423,6 +424,227 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     return LL_OK;
 }
 
+// Adds grad_output * d/da_e sum_j d_j <U_w, W_j> to grad_values for the kept forward's coefficients,
+// with W_0 = W0 and U_w = coef(col) U (coef = cq for col < split, 1 / gdiv otherwise); W0 and U are
+// n x b blocks of the W storage type with leading dimension l. Reverse recurrence of the adjoint,
+// Lambda_m = d_m U_w, Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U_w (B symmetric), with the W_j
+// recomputed from sqrt(m)-spaced checkpoints; vprep holds the values prepared for B, rowidx the
+// row of every stored entry.
+ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, const int32_t* rowidx, const void* W0,
+                             const void* U, long long l, int b, int split, double cq, double gdiv, double grad_output,
+                             double* grad_values, cudaStream_t s) {
+    const int n = (int)A->n;
+    const int prec = h->kept_prec, m = h->kept_m;
+    const int wt = w_type_of(prec);
+    const size_t ew = elem_size(wt), blk = (size_t)n * l * ew;
+    const double sigma = h->kept_sigma, c = h->kept_c, gamma = h->kept_gamma;
+    const std::vector<double>& d = h->kept_d;
+    std::vector<double> beta(m + 1);
+    for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
+    // checkpoints W_{k s} (k >= 1) and a segment buffer for W_{j0+1} .. W_{j1-1}
+    const int sck = h->kept_ckpt > 0 ? h->kept_ckpt : (int)std::ceil(std::sqrt((double)m));
+    const int nseg = (m + sck - 1) / sck;
+    WS(ckpt, char*, "bw_ckpt", blk * (size_t)(nseg > 1 ? nseg - 1 : 1));
+    WS(seg, char*, "bw_seg", blk * (size_t)(sck > 1 ? sck - 1 : 1));
+    WS(lam, char*, "bw_lam", 2 * blk);
+    WS(tmp, char*, "bw_tmp", 2 * blk);
+
+    StepParams pp{};
+    pp.rowptr = A->rowptr;
+    pp.colind = A->colind;
+    pp.vals = vprep;
+    pp.ldw = l;
+    pp.ldv = l;
+    pp.ldp = l;
+    pp.v = U;
+    pp.adj_split = split;
+    {
+        WS(err, int*, "tma_error", sizeof(int));
+        LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    }
+    StepParams pa = pp;
+    // representative steps for the autotuner: W_1 from W_0 into the segment buffer, and one
+    // reverse step between the two Lambda buffers (both rewritten below)
+    pp.win = W0;
+    pp.wout = tmp;
+    pp.beta = beta[0];
+    pp.beta_df = df_split(beta[0]);
+    pa.win = lam;
+    pa.wout = lam + blk;
+    pa.beta = beta[0];
+    pa.beta_df = df_split(beta[0]);
+    pa.adj_q = d[0] * cq;
+    pa.adj_g = d[0] / gdiv;
+    pa.adj_q_df = df_split(d[0] * cq);
+    pa.adj_g_df = df_split(d[0] / gdiv);
+    StepExec Ep, Ea;
+    ll_status cs = choose_exec(h, prec, MODE_PLAIN, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pp, Ep, s);
+    if (cs != LL_OK) return cs;
+    cs = choose_exec(h, prec, MODE_ADJ, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pa, Ea, s);
+    if (cs != LL_OK) return cs;
+    auto plain_step = [&](int j, const void* win, void* wout) -> cudaError_t {
+        pp.win = win;
+        pp.wout = wout;
+        pp.beta = beta[j];
+        pp.beta_df = df_split(beta[j]);
+        return exec_step(h, prec, MODE_PLAIN, Ep, pp, s);
+    };
+    // phase A: W_1 .. W_{(nseg-1) sck}, keeping W_{k sck} in the checkpoint slots
+    const void* cur = W0;
+    for (int j = 0; j < (nseg - 1) * sck; ++j) {
+        void* out = ((j + 1) % sck == 0) ? (void*)(ckpt + (size_t)((j + 1) / sck - 1) * blk)
+                                         : (void*)(tmp + (cur == tmp ? blk : 0));
+        LL_CK(plain_step(j, cur, out));
+        cur = out;
+    }
+    // phase B: Lambda_m = d_m U, then segments in reverse
+    const double scale = grad_output / (sigma * gamma);
+    char* lam_cur = lam;
+    LL_CK(launch_scale_cols(prec, U, l, n, b, split, d[m] * cq, d[m] / gdiv, lam_cur, s));
+    h->launches++;
+    for (int kk = nseg - 1; kk >= 0; --kk) {
+        const int j0 = kk * sck, j1 = std::min(j0 + sck, m);
+        const void* wj0 = kk == 0 ? W0 : (const void*)(ckpt + (size_t)(kk - 1) * blk);
+        const void* w = wj0;
+        for (int t = 1; t < j1 - j0; ++t) {
+            void* out = seg + (size_t)(t - 1) * blk;
+            LL_CK(plain_step(j0 + t - 1, w, out));
+            w = out;
+        }
+        for (int j = j1 - 1; j >= j0; --j) {
+            const void* wj = (j == j0) ? wj0 : (const void*)(seg + (size_t)(j - j0 - 1) * blk);
+            // g_e += (1 / (sigma gamma)) <Lambda_{j+1}[r, :], W_j[c, :]>
+            LL_CK(launch_sddmm(prec, rowidx, A->colind, A->nnz, lam_cur, wj, l, b, scale, grad_values, s));
+            h->launches++;
+            if (j == 0) break;
+            // Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U
+            char* lam_next = (lam_cur == lam) ? lam + blk : lam;
+            pa.win = lam_cur;
+            pa.wout = lam_next;
+            pa.beta = beta[j];
+            pa.beta_df = df_split(beta[j]);
+            pa.adj_q = d[j] * cq;
+            pa.adj_g = d[j] / gdiv;
+            pa.adj_q_df = df_split(d[j] * cq);
+            pa.adj_g_df = df_split(d[j] / gdiv);
+            LL_CK(exec_step(h, prec, MODE_ADJ, Ea, pa, s));
+            lam_cur = lam_next;
+        }
+    }
+    LL_CK(cudaGetLastError());
+    return check_tma_flag(h, s);
+}
+
+
+// The adjoint of the kept forward: the frozen-basis gradient, and with through_qr the derivative
+// through the sketch's CholeskyQR2 as well (Algorithm 3 step 4; bounds, sigma and d fixed):
+//   E = tr(F Pi) + (1/k) tr(F (I - Pi) G G^T (I - Pi)),  Pi = Q Q^T,  Y = F S = Q R,
+//   dE = tr(dF [Q Q^T + G' G'^T / k]) + tr(Gamma^T dF S),  Gamma = 2 (I - Pi) Z Q R^-T,
+//   Z Q = F Q - (1/k) G (G'^T F Q) - (1/k) (F G') (G^T Q).
+// The second term is the same reverse recurrence with W_0 = S and U = Gamma.
+ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream,
+                        bool through_qr) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    if (!h->kept) return fail(h, LL_ERR_NO_FORWARD, "no kept forward (call ll_logdet_forward with keep_for_backward = 1)");
+    ll_status st = check_csr_args(h, A);
+    if (st != LL_OK) return st;
+    if (A->n != h->kept_n || A->nnz != h->kept_nnz) return fail(h, LL_ERR_INVALID_ARG, "matrix shape differs from the kept forward");
+    if (A->nnz > 0 && !grad_values) return fail(h, LL_ERR_INVALID_ARG, "null grad_values");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->launches = 0;
+    const int n = (int)A->n;
+    const int prec = h->kept_prec, kq = h->kept_kq, kg = h->kept_kg, m = h->kept_m;
+    const int b2 = kq + kg, l2 = block_ld(prec, b2);
+    const int wt = w_type_of(prec);
+    const size_t ew = elem_size(wt), blk = (size_t)n * l2 * ew;
+    if (A->nnz > 0) LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
+    if (n == 0 || A->nnz == 0) return LL_OK;
+    auto it_v = h->ws.find(wt == T_F64 ? "fw_basis" : "fw_V");
+    if (it_v == h->ws.end()) return fail(h, LL_ERR_NO_FORWARD, "kept basis missing");
+    const void* V = it_v->second.p;
+    const double sigma = h->kept_sigma, c = h->kept_c, gamma = h->kept_gamma;
+    WS(vprep, void*, "bw_vals", (size_t)A->nnz * ew);
+    LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
+    h->launches++;
+    // row of every stored entry, for the gradient contraction
+    WS(rowidx, int32_t*, "bw_rowidx", (size_t)A->nnz * sizeof(int32_t));
+    LL_CK(launch_row_index(A->rowptr, n, rowidx, s));
+    h->launches++;
+    // frozen basis: W_0 = [Q | G'], U = [Q | G' / k]
+    st = adjoint_accumulate(h, A, vprep, rowidx, V, V, l2, b2, kq, 1.0, (double)kg, grad_output, grad_values, s);
+    if (st != LL_OK || !through_qr || !h->kept_qr) return st;
+
+    // ---- through the QR: F [Q | G'] by the pass-1 arithmetic on the kept block
+    auto kept_buf = [&](const char* name) -> void* {
+        auto it = h->ws.find(name);
+        return it == h->ws.end() ? nullptr : it->second.p;
+    };
+    void* S = kept_buf("fw_S");
+    const double* Gb = static_cast<const double*>(kept_buf("fw_G"));
+    const double* basis = static_cast<const double*>(kept_buf("fw_basis"));
+    const double* rinv1 = static_cast<const double*>(kept_buf("fw_rinv1"));
+    const double* rinv2 = static_cast<const double*>(kept_buf("fw_rinv"));
+    if (!S || !Gb || !basis || !rinv1 || !rinv2) return fail(h, LL_ERR_NO_FORWARD, "kept sketch missing");
+    const int l1 = block_ld(prec, kq);
+    const size_t ep = elem_size(p_type_of(prec));
+    std::vector<double> beta(m + 1);
+    for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
+    WS(scratch, char*, "bw_tmp", 2 * blk);
+    WS(FV, void*, "bw_FV", (size_t)n * l2 * ep);
+    WS(FV64, double*, "bw_FV64", (size_t)n * b2 * sizeof(double));
+    st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, b2, V, l2, scratch, scratch + blk, FV, l2, nullptr, beta, h->kept_d,
+                  h->cfg_kernel, h->cfg_threads, h->cfg_rpt, s);
+    if (st != LL_OK) return st;
+    LL_CK(launch_block_to_f64(prec, FV, l2, FV64, b2, n, b2, s));
+    h->launches++;
+
+    // ---- Gamma = 2 (I - Pi) Z Q R^-T (tall-skinny FP64 products)
+    const int ggrid = h->sm_count * 2;
+    const size_t gpn = gram_partials_doubles(kg > kq ? kg : kq, kq, false, ggrid);
+    WS(gpart, double*, "bw_gram_partials", gpn * sizeof(double));
+    WS(gticket, unsigned int*, "bw_gram_ticket", sizeof(unsigned int));
+    WS(small, double*, "bw_small", (size_t)5 * (kg > kq ? kg : kq) * kq * sizeof(double));
+    double* C1 = small;                              // G'^T F Q / k   (kg x kq)
+    double* C2 = small + (size_t)kg * kq;            // G^T Q / k      (kg x kq)
+    double* C3 = small + (size_t)2 * kg * kq;        // Q^T Z Q        (kq x kq)
+    double* Mt = C3 + (size_t)kq * kq;               // 2 R^-T         (kq x kq)
+    WS(zq, double*, "bw_zq", (size_t)3 * n * kq * sizeof(double));
+    double* ZQa = zq;
+    double* ZQ = zq + (size_t)n * kq;
+    double* Xb = zq + (size_t)2 * n * kq;
+    LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), s));
+    LL_CK(launch_gram(T_F64, basis + kq, l2, kg, T_F64, FV64, b2, kq, n, false, gpart, gticket, C1, ggrid, s));
+    LL_CK(launch_gram(T_F64, Gb, kg, kg, T_F64, basis, l2, kq, n, false, gpart, gticket, C2, ggrid, s));
+    LL_CK(launch_scaled_copy_f64(C1, kq, C1, kq, 2 * kg, kq, 1.0 / kg, s));
+    LL_CK(launch_project(Gb, kg, kg, FV64, b2, kq, C1, n, ZQa, kq, T_F64, nullptr, 0, 0, 0, s));
+    LL_CK(launch_project(FV64 + kq, b2, kg, ZQa, kq, kq, C2, n, ZQ, kq, T_F64, nullptr, 0, 0, 0, s));
+    LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, ZQ, kq, kq, n, false, gpart, gticket, C3, ggrid, s));
+    LL_CK(launch_project(basis, l2, kq, ZQ, kq, kq, C3, n, Xb, kq, T_F64, nullptr, 0, 0, 0, s));
+    h->launches += 8;
+    // R^-1 = R1^-1 R2^-1 (Y R1^-1 = Q1, Q1 R2^-1 = Q), and M = 2 R^-T, on the host (kq x kq)
+    std::vector<double> r1((size_t)kq * kq), r2((size_t)kq * kq), mt((size_t)kq * kq, 0.0);
+    LL_CK(cudaMemcpyAsync(r1.data(), rinv1, r1.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaMemcpyAsync(r2.data(), rinv2, r2.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    for (int a = 0; a < kq; ++a)
+        for (int b = 0; b < kq; ++b) {
+            double t = 0.0;
+            for (int x = 0; x < kq; ++x) t += r1[(size_t)a * kq + x] * r2[(size_t)x * kq + b];
+            mt[(size_t)b * kq + a] = 2.0 * t;   // (R^-1)^T
+        }
+    LL_CK(cudaMemcpyAsync(Mt, mt.data(), mt.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    WS(gam, void*, "bw_gamma", (size_t)n * l1 * ew);
+    WS(gam64, double*, "bw_gamma64", (size_t)n * kq * sizeof(double));
+    LL_CK(cudaMemsetAsync(gam, 0, (size_t)n * l1 * ew, s));
+    LL_CK(launch_mul_small(Xb, kq, n, kq, kq, Mt, gam64, kq, wt, gam, l1, s));
+    h->launches++;
+    LL_CK(cudaStreamSynchronize(s));   // the host copy of mt stays alive until the upload is done
+
+    // ---- the QR term: W_0 = S, U = Gamma
+    return adjoint_accumulate(h, A, vprep, rowidx, S, gam, l1, kq, kq, 1.0, 1.0, grad_output, grad_values, s);
+}
+
+
 }  // namespace
 }  // namespace ll
 
@@ -772,7 +994,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     WS(gpart, double*, "fw_gram_partials", (gp1 > gp2 ? gp1 : gp2) * sizeof(double));
     WS(gticket, unsigned int*, "fw_gram_ticket", sizeof(unsigned int));
     WS(gram, double*, "fw_gram", (size_t)kq * (kq > kg ? kq : kg) * sizeof(double));
-    WS(rinv, double*, "fw_rinv", (size_t)kq * kq * sizeof(double));
+    WS(rinv1, double*, "fw_rinv1", (size_t)kq * kq * sizeof(double));   // R1^-1 (first CholeskyQR)
+    WS(rinv, double*, "fw_rinv", (size_t)kq * kq * sizeof(double));     // R2^-1 (second)
     WS(qrstat, int*, "fw_qr_status", sizeof(int));
     WS(dots, double*, "fw_dots", (size_t)(m + 1) * b2 * sizeof(double));
     WS(tma_err, int*, "tma_error", sizeof(int));
@@ -840,8 +1063,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
 
             // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']
             LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
-            LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
-            LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv, q1, kq, T_F64, nullptr, 0, q));
+            LL_CK(launch_chol_rinv(gram, kq, rinv1, qrstat, q));
+            LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, q1, kq, T_F64, nullptr, 0, q));
             LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
             LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
             LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, l2, wt, wt != T_F64 ? V : nullptr, l2, q));
@@ -1008,6 +1231,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_kq = kq;
         h->kept_kg = kg;
         h->kept_hutch = hutch;
+        h->kept_qr = !hutch && kq < n;
         h->kept_m = m;
         h->kept_prec = prec;
         h->kept_ckpt = o.ckpt_stride;
@@ -1044,127 +1268,11 @@ ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* Ah, ll_bounds bound
 }
 
 ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream) {
-    if (!h) return LL_ERR_INVALID_ARG;
-    if (!h->kept) return fail(h, LL_ERR_NO_FORWARD, "no kept forward (call ll_logdet_forward with keep_for_backward = 1)");
-    ll_status st = check_csr_args(h, A);
-    if (st != LL_OK) return st;
-    if (A->n != h->kept_n || A->nnz != h->kept_nnz) return fail(h, LL_ERR_INVALID_ARG, "matrix shape differs from the kept forward");
-    if (A->nnz > 0 && !grad_values) return fail(h, LL_ERR_INVALID_ARG, "null grad_values");
-    cudaStream_t s = (cudaStream_t)stream;
-    h->launches = 0;
-    const int n = (int)A->n;
-    const int prec = h->kept_prec, kq = h->kept_kq, kg = h->kept_kg, m = h->kept_m;
-    const int b2 = kq + kg, l2 = block_ld(prec, b2);
-    const int wt = w_type_of(prec);
-    const size_t ew = elem_size(wt), blk = (size_t)n * l2 * ew;
-    if (A->nnz > 0) LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
-    if (n == 0 || A->nnz == 0) return LL_OK;
-    auto it_v = h->ws.find(wt == T_F64 ? "fw_basis" : "fw_V");
-    if (it_v == h->ws.end()) return fail(h, LL_ERR_NO_FORWARD, "kept basis missing");
-    const void* V = it_v->second.p;
-    const double sigma = h->kept_sigma, c = h->kept_c, gamma = h->kept_gamma;
-    const std::vector<double>& d = h->kept_d;
-    std::vector<double> beta(m + 1);
-    for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
-    // checkpoints W_{k s} (k >= 1) and a segment buffer for W_{j0+1} .. W_{j1-1}
-    const int sck = h->kept_ckpt > 0 ? h->kept_ckpt : (int)std::ceil(std::sqrt((double)m));
-    const int nseg = (m + sck - 1) / sck;
-    WS(vprep, void*, "bw_vals", (size_t)A->nnz * ew);
-    WS(ckpt, char*, "bw_ckpt", blk * (size_t)(nseg > 1 ? nseg - 1 : 1));
-    WS(seg, char*, "bw_seg", blk * (size_t)(sck > 1 ? sck - 1 : 1));
-    WS(lam, char*, "bw_lam", 2 * blk);
-    WS(tmp, char*, "bw_tmp", 2 * blk);
-    LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
-    h->launches++;
-    // row of every stored entry, for the gradient contraction
-    WS(rowidx, int32_t*, "bw_rowidx", (size_t)A->nnz * sizeof(int32_t));
-    LL_CK(launch_row_index(A->rowptr, n, rowidx, s));
-    h->launches++;
+    return backward_impl(h, A, grad_output, grad_values, stream, false);
+}
 
-    StepParams pp{};
-    pp.rowptr = A->rowptr;
-    pp.colind = A->colind;
-    pp.vals = vprep;
-    pp.ldw = l2;
-    pp.ldv = l2;
-    pp.ldp = l2;
-    pp.v = V;
-    pp.adj_split = kq;
-    {
-        WS(err, int*, "tma_error", sizeof(int));
-        LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
-    }
-    StepParams pa = pp;
-    // representative steps for the autotuner: W_1 from V into the segment buffer, and one
-    // reverse step between the two Lambda buffers (both rewritten below)
-    pp.win = V;
-    pp.wout = tmp;
-    pp.beta = beta[0];
-    pp.beta_df = df_split(beta[0]);
-    pa.win = lam;
-    pa.wout = lam + blk;
-    pa.beta = beta[0];
-    pa.beta_df = df_split(beta[0]);
-    pa.adj_q = d[0];
-    pa.adj_g = d[0] / kg;
-    pa.adj_q_df = df_split(d[0]);
-    pa.adj_g_df = df_split(d[0] / kg);
-    StepExec Ep, Ea;
-    ll_status cs = choose_exec(h, prec, MODE_PLAIN, n, A->nnz, b2, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pp, Ep, s);
-    if (cs != LL_OK) return cs;
-    cs = choose_exec(h, prec, MODE_ADJ, n, A->nnz, b2, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pa, Ea, s);
-    if (cs != LL_OK) return cs;
-    auto plain_step = [&](int j, const void* win, void* wout) -> cudaError_t {
-        pp.win = win;
-        pp.wout = wout;
-        pp.beta = beta[j];
-        pp.beta_df = df_split(beta[j]);
-        return exec_step(h, prec, MODE_PLAIN, Ep, pp, s);
-    };
-    // phase A: W_1 .. W_{(nseg-1) sck}, keeping W_{k sck} in the checkpoint slots
-    const void* cur = V;
-    for (int j = 0; j < (nseg - 1) * sck; ++j) {
-        void* out = ((j + 1) % sck == 0) ? (void*)(ckpt + (size_t)((j + 1) / sck - 1) * blk)
-                                         : (void*)(tmp + (cur == tmp ? blk : 0));
-        LL_CK(plain_step(j, cur, out));
-        cur = out;
-    }
-    // phase B: Lambda_m = d_m U, then segments in reverse
-    const double scale = grad_output / (sigma * gamma);
-    char* lam_cur = lam;
-    LL_CK(launch_scale_cols(prec, V, l2, n, b2, kq, d[m], d[m] / kg, lam_cur, s));
-    h->launches++;
-    for (int kk = nseg - 1; kk >= 0; --kk) {
-        const int j0 = kk * sck, j1 = std::min(j0 + sck, m);
-        const void* wj0 = kk == 0 ? V : (const void*)(ckpt + (size_t)(kk - 1) * blk);
-        const void* w = wj0;
-        for (int t = 1; t < j1 - j0; ++t) {
-            void* out = seg + (size_t)(t - 1) * blk;
-            LL_CK(plain_step(j0 + t - 1, w, out));
-            w = out;
-        }
-        for (int j = j1 - 1; j >= j0; --j) {
-            const void* wj = (j == j0) ? wj0 : (const void*)(seg + (size_t)(j - j0 - 1) * blk);
-            // g_e += (1 / (sigma gamma)) <Lambda_{j+1}[r, :], W_j[c, :]>
-            LL_CK(launch_sddmm(prec, rowidx, A->colind, A->nnz, lam_cur, wj, l2, b2, scale, grad_values, s));
-            h->launches++;
-            if (j == 0) break;
-            // Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U
-            char* lam_next = (lam_cur == lam) ? lam + blk : lam;
-            pa.win = lam_cur;
-            pa.wout = lam_next;
-            pa.beta = beta[j];
-            pa.beta_df = df_split(beta[j]);
-            pa.adj_q = d[j];
-            pa.adj_g = d[j] / kg;
-            pa.adj_q_df = df_split(d[j]);
-            pa.adj_g_df = df_split(d[j] / kg);
-            LL_CK(exec_step(h, prec, MODE_ADJ, Ea, pa, s));
-            lam_cur = lam_next;
-        }
-    }
-    LL_CK(cudaGetLastError());
-    return check_tma_flag(h, s);
+ll_status ll_logdet_backward_qr(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream) {
+    return backward_impl(h, A, grad_output, grad_values, stream, true);
 }
 
 ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* dvalues, int64_t ld, int64_t nnz,

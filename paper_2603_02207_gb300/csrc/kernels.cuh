@@ -166,6 +166,10 @@ cudaError_t launch_apply_rinv_jobs(int tx, long long ldx, int k, long long ld64,
 cudaError_t launch_project_jobs(long long ldq, int k, long long ldg, int kg, long long ld64, int t2, long long ld2,
                                 int zero_pad, int col2, const RowJob& one, const RowJob* jobs, int count, int n_max,
                                 cudaStream_t s);
+// out = X M for an n x kx FP64 block X and a full kx x kc matrix M (row-major, device), the
+// products in double-float as in apply_rinv; out64 FP64 (ld64), out2 (type t2, ld2) optional
+cudaError_t launch_mul_small(const double* X, long long ldx, int n, int kx, int kc, const double* M, double* out64,
+                             long long ld64, int t2, void* out2, long long ld2, cudaStream_t s);
 // doubles of Gram partials needed for a launch with `grid` CTAs
 size_t gram_partials_doubles(int kx, int kz, bool sym, int grid);
 // out (kx x kz, row-major) = X^T Z, X: n x kx (type tx), Z: n x kz (type tz); sym: X == Z

@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
         for (int j = 0; j < 4; ++j) {
             const int c = cg * 4 + j;
             if (c >= kc) break;
-            if (MODE == 0) {
+            if (MODE != 1) {
                 out64[(size_t)row * ld64 + c] = (double)h[j] + (double)l[j];
                 if (out2) st_out2(out2, (size_t)row * ld2 + col2 + c, h[j], l[j]);
             } else {
@@ -558,6 +558,12 @@ cudaError_t launch_apply_rinv(int tx, const void* X, long long ldx, int n, int k
                               double* out64, long long ld64, int t2, void* out2, long long ld2, cudaStream_t s) {
     const RowJob one{X, Rinv, nullptr, out64, out2, n};
     return launch_apply_rinv_jobs(tx, ldx, k, ld64, t2, ld2, one, nullptr, 1, n, s);
+}
+
+cudaError_t launch_mul_small(const double* X, long long ldx, int n, int kx, int kc, const double* M, double* out64,
+                             long long ld64, int t2, void* out2, long long ld2, cudaStream_t s) {
+    const RowJob one{X, M, nullptr, out64, out2, n};
+    return rowprod_dispatch<double, 2>(t2, ldx, kx, kc, 0, ld64, ld2, 0, 0, one, nullptr, 1, n, s);
 }
 
 cudaError_t launch_project_jobs(long long ldq, int k, long long ldg, int kg, long long ld64, int t2, long long ld2,

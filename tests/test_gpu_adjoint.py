@@ -129,3 +129,80 @@ def test_backward_hutchinson_matches_oracle_gradient(L, h, prec):
     with pytest.raises(L.LejaError) as ei:
         L.ll_kept_basis(h)
     assert ei.value.name == "LL_ERR_UNSUPPORTED"
+
+
+# --------------------------------------------------- derivative through the sketch's QR
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+def test_backward_qr_matches_oracle_full_gradient(L, h, prec):
+    """ll_logdet_backward_qr against the oracle's frozen-basis gradient plus the term through
+    Q = orth(p(A~) S) (same S and G: streams 0 and 1 of the seed)."""
+    A = random_spd(700, nnz_per_row=7, seed=4, empty_rows=3)
+    lo, hi = O.gershgorin(A)
+    lmin = max(lo, 0.05)
+    m, probes, seed = 23, 18, 6
+    dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+    L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=m, probes=probes, seed=seed, precision=prec,
+                                                    keep_for_backward=True))
+    g = L.ll_logdet_backward(h, dA, 1.0, through_qr=True).cpu().numpy()
+    S, G = O.make_probes(A.n, probes // 3, seed)
+    want = O.hutchpp_full_grad_values(A, lmin, hi, m, S, G)
+    assert rel_err(g, want) < (1e-9 if prec != "f32" else 1e-4)
+    frozen = L.ll_logdet_backward(h, dA, 1.0).cpu().numpy()
+    assert rel_err(frozen, want) > 1e-3   # the QR term is not negligible here
+
+
+def test_backward_qr_is_the_frozen_gradient_without_a_qr(L, h):
+    """Hutchinson (no sketch) and k >= n (Q spans R^n, Gamma = 0): both backwards agree."""
+    A = random_spd(300, seed=2)
+    lo, hi = O.gershgorin(A)
+    lmin = max(lo, 0.05)
+    dA = L.DeviceCSR.from_host(A)
+    L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=20, probes=7, seed=1, estimator="hutchinson",
+                                                    keep_for_backward=True))
+    assert L.ll_logdet_backward(h, dA, 2.0, through_qr=True).equal(L.ll_logdet_backward(h, dA, 2.0))
+    B = random_spd(12, seed=5)
+    lo, hi = O.gershgorin(B)
+    dB = L.DeviceCSR.from_host(B)
+    L.ll_logdet_forward(h, dB, max(lo, 0.05), hi, L.options(degree=20, probes=36, seed=1, keep_for_backward=True))
+    assert L.ll_logdet_backward(h, dB, 1.0, through_qr=True).equal(L.ll_logdet_backward(h, dB, 1.0))
+
+
+@pytest.mark.parametrize("prec", ["df64", "f64"])
+def test_backward_qr_theta_chain_matches_finite_differences_of_the_gpu_estimate(L, h, prec):
+    """GMRF Q(theta) = I + theta Adj on 30 x 30: d/dtheta of the GPU estimate (same probes, fixed
+    bounds and degree; Q and G' recomputed) by central differences, against the through-QR
+    gradient chained to theta."""
+    torch = need_gpu()
+    from synth import gmrf_theta
+    theta, eps = -0.2, 1e-5
+    A = gmrf_theta(30, theta)
+    lo, hi = 1 - 4 * 0.21, 1 + 4 * 0.21
+    opts = L.options(degree=40, probes=24, seed=3, precision=prec, keep_for_backward=True)
+    est = {}
+    for t in (theta - eps, theta + eps):
+        dA = L.DeviceCSR.from_host(gmrf_theta(30, t))
+        est[t] = L.ll_logdet_forward(h, dA, lo, hi, opts)
+    fd = (est[theta + eps] - est[theta - eps]) / (2 * eps)
+    dA = L.DeviceCSR.from_host(A)
+    L.ll_logdet_forward(h, dA, lo, hi, opts)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    dv = torch.as_tensor((A.colind != rows).astype(np.float64)).cuda()
+    full = L.ll_param_grad(h, L.ll_logdet_backward(h, dA, 1.0, through_qr=True), dv)[0]
+    frozen = L.ll_param_grad(h, L.ll_logdet_backward(h, dA, 1.0), dv)[0]
+    assert full == pytest.approx(fd, rel=1e-6)
+    assert abs(frozen - fd) > 100 * abs(full - fd)
+
+
+def test_autograd_through_qr(L, h):
+    torch = need_gpu()
+    A = random_spd(500, seed=8)
+    lo, hi = O.gershgorin(A)
+    lmin = max(lo, 0.05)
+    dA = L.DeviceCSR.from_host(A)
+    vals = dA.values.clone().requires_grad_(True)
+    est = L.logdet(vals, dA.rowptr, dA.colind, A.n, (lmin, hi), 25, 15, seed=2, handle=h, through_qr=True)
+    est.backward()
+    S, G = O.make_probes(A.n, 5, 2)
+    want = O.hutchpp_full_grad_values(A, lmin, hi, 25, S, G)
+    assert rel_err(vals.grad.cpu().numpy(), want) < 1e-9
