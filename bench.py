@@ -182,7 +182,9 @@ def run_reference(args):
 
 
 def time_calls(fn, reps: int, warmup: int = 1):
-    """Device time of `reps` calls of fn() (CUDA events on the current stream), in ms per call."""
+    """Device time of `reps` calls of fn() (CUDA events on the current stream), in ms per call.
+    Forward calls need two warm-ups to reach the graph replay: the first tunes the step kernels
+    and may grow the workspace (which voids that call's capture), the second captures."""
     import torch
     for _ in range(warmup):
         fn()
@@ -234,7 +236,7 @@ def workload_config3(L, h, grid: int = 1024, degree: int = 80):
     out = {}
     for prec in ("df64", "f32"):
         opts = L.options(degree=degree, probes=60, seed=0, precision=prec, probe_kind="gaussian", keep_for_backward=True)
-        ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), 2, 1)
+        ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), 2, 2)
         inf = h.info()
         ms_b, g = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 2, 1)
         th = L.ll_param_grad(h, g, dv)
@@ -274,14 +276,14 @@ def workload_config4(L, h, count: int = 64):
     for prec in ("df64", "f32"):
         dm = [L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64") for A in mats]
         opts = L.options(probes=30, seed=2, precision=prec)
-        ms_b, est = time_calls(lambda: L.ll_logdet_batched(h, dm, bounds, opts), 2, 1)
+        ms_b, est = time_calls(lambda: L.ll_logdet_batched(h, dm, bounds, opts), 2, 2)
         inf = h.info()
         # algorithmic bytes of every Léja step of every matrix (pass 1 on k = 10 columns, pass 2 on 20)
         b1 = sum(m * step_bytes(A.n, A.nnz, 10, prec, "accum") for A, m in zip(mats, degs))
         b2 = sum(m * step_bytes(A.n, A.nnz, 20, prec, "dot") for A, m in zip(mats, degs))
         hr = L.Handle()
         opts_r = L.options(probes=30, seed=2, precision=prec, step_kernel="gather")
-        ms_r, _ = time_calls(lambda: L.ll_logdet_batched(hr, dm, bounds, opts_r), 2, 1)
+        ms_r, _ = time_calls(lambda: L.ll_logdet_batched(hr, dm, bounds, opts_r), 2, 2)
         inf_r = hr.info()
 
         def one_by_one():
@@ -368,7 +370,7 @@ def workload_f3(L, h, n: int = 10_000_000, probes: int = 30):
         rho = (_m.sqrt(kap) + 1) / (_m.sqrt(kap) - 1)
         m = max(10, min(250, _m.ceil(_m.log(1e6) / _m.log(rho))))
         opts = L.options(degree=m, probes=probes, seed=0, precision=prec)
-        ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lo, hi, opts), 3, 1)
+        ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lo, hi, opts), 3, 2)
         inf = h.info()
         out[prec] = {"ms_per_estimate": ms, "degree": m, "bounds": [lo, hi], "estimate": est,
                      "rel_err_vs_exact": abs(est - exact) / abs(exact),
@@ -398,7 +400,7 @@ def workload_f1(L, h, A, grid: int, degree: int, seeds: int = 3):
             ms_l, errs = [], []
             for s in range(seeds):
                 opts = L.options(degree=m, probes=PROBES, seed=SEED + s, precision=prec, estimator=name)
-                ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, *BOUNDS, opts), 3, 1)
+                ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, *BOUNDS, opts), 3, 2)
                 ms_l.append(ms)
                 errs.append(abs(est - exact) / abs(exact))
             inf = h.info()
@@ -418,7 +420,7 @@ def workload_f1(L, h, A, grid: int, degree: int, seeds: int = 3):
         # longest-running column of each pass
         for tol in (1e-2, 1e-4):
             opts = L.options(degree=150, probes=PROBES, seed=SEED, precision=prec, tol=tol)
-            ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, *BOUNDS, opts), 3, 1)
+            ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, *BOUNDS, opts), 3, 2)
             inf = h.info()
             k = PROBES // 3
             b = (inf["deg_max_pass1"] * step_bytes(n, nnz, k, prec, "accum") +
@@ -473,7 +475,7 @@ def workload_f4(L, h, N: int = 5000, thetas=(-0.24, -0.23, -0.22, -0.21, -0.20),
                "exact_dlogdet_dtheta": dexact}
         for prec in ("df64", "f32"):
             opts = L.options(degree=m, probes=probes, seed=0, precision=prec, keep_for_backward=(prec == "df64"))
-            ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lo, hi, opts), 2, 1)
+            ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lo, hi, opts), 2, 2)
             inf = h.info()
             r = {"ms_forward": ms_f, "estimate": est, "rel_err_vs_exact": abs(est - exact) / abs(exact),
                  "GBps_estimate": estimate_bytes(n, nnz, k, m, prec) / (ms_f / 1e3) / 1e9,

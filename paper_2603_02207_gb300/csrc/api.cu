@@ -1120,7 +1120,9 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         if ((st = enqueue(s)) != LL_OK) return st;
         if (o.use_graph) {
             // capture the same work for the next identical call (tuning is cached by now and the
-            // workspace allocated, so the capture only records launches and memsets)
+            // workspace allocated, so the capture only records launches and memsets); the key
+            // takes the workspace as the eager run left it
+            key.ws_gen = h->ws_gen;
             const int launched = h->launches - before;
             const bool tma = h->tma_used;
             if (gr.exec) {
@@ -1132,13 +1134,15 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             LL_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
             capturing = true;
             const int kk1 = k1, tt1 = t1, kk2 = h->last_kernel, tt2 = h->last_threads;
+            const int cap0 = h->launches;
             ll_status cst = enqueue(h->cap_stream);
+            const int in_graph = h->launches - cap0;   // without the autotuner's launches of the eager run
             capturing = false;
             cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
             if (cst == LL_OK && ce == cudaSuccess && graph && h->ws_gen == key.ws_gen &&
                 cudaGraphInstantiate(&gr.exec, graph, 0) == cudaSuccess) {
                 gr.key.assign(kb, kb + sizeof key);
-                gr.launches = launched;
+                gr.launches = in_graph;
                 gr.k1 = kk1;
                 gr.t1 = tt1;
                 gr.k2 = kk2;
