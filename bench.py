@@ -123,6 +123,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest x over the ranks (the slowest replica's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -560,11 +571,7 @@ def main():
         e1.record(stream)
         barrier()
         clocks = sampler.stop() if sampler else None
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         return dict(ms=ms, est=est, p1=p1, p2=p2, launches=launches, clocks=clocks, info=h.info(), dA=dA, opts=opts)
 
     prec = args.precision
@@ -609,7 +616,7 @@ def main():
             L.ll_logdet_forward_host(h, Ah, *BOUNDS, opts)
         e1.record(stream)
         barrier()
-        wall = time.perf_counter() - t0
+        wall = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         vs = 4 if prec == "f32" else 8
         h2d = 4 * (n + 1) + 4 * nnz + vs * nnz
         d2h = (m + 1) * (2 * k) * 8 + 2 * 4
