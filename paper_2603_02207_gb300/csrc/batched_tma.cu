@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
         unsigned int g_next = 0;   // lane 0: first ticket of the batch after the fetched one
         int err_seen = 0;          // lane 0: the error flag as last read
         int fj = -1, fi = 0, ft = 0, fgt = 0, fn = 0, fT = 0;
+        bool flast = true;   // the last item of its run (same matrix and step) within the batch
         int4 fmt = make_int4(0, 0, 0, 0);
         double fbeta = 0.0, fd0 = 0.0, fdn = 0.0;
         float2 fbd = make_float2(0.f, 0.f), fd0d = fbd, fdnd = fbd;
@@ -225,6 +226,11 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                     if (MODE == MODE_DOT || d.x > 0) prefetch_map(&M->aux);
                 }
             }
+            // runs of consecutive tickets with the same (step, matrix) inside a batch share one
+            // trace reduction (tickets are step-major, then matrix, then tile; batches start at
+            // multiples of BT_TAKE, so the runs do not depend on which CTA takes a batch)
+            const int nj = __shfl_down_sync(0xffffffffu, fj, 1), ni = __shfl_down_sync(0xffffffffu, fi, 1);
+            flast = lane >= BT_TAKE - 1 || nj != fj || ni != fi;
         };
         auto put = [&]() {
             bool none = false, acq = false;
@@ -254,8 +260,11 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                     it.ng = fmt.y;
                     it.nw = fmt.z;
                     // the dependency (every tile of step j - 1 finished) was already met when read
-                    it.dep = (fj == 0 || farr >= (unsigned long long)fj * (unsigned long long)fT) ? 1 : 0;
-                    acq = fj > 0 && it.dep;
+                    // bit 0: the dependency (every tile of step j - 1 finished) was already met when
+                    // read; bit 1: the item ends its run
+                    const int met = (fj == 0 || farr >= (unsigned long long)fj * (unsigned long long)fT) ? 1 : 0;
+                    it.dep = met | (flast ? 2 : 0);
+                    acq = fj > 0 && met;
                     // the extra windows' start rows, then the gathered columns
                     const uint32_t bytes = (fmt.y > 0 || fmt.z > 0) ? (uint32_t)(TMA_MAX_WIN + ((fmt.y + 3) & ~3)) * 4u : 0u;
                     if (bytes) {
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
             // of matrix i finished (arrival count j * T), then order the other CTAs' generic
             // stores of W_j and P before this warp's TMA reads of them (the cache ci, cj lives in
             // lane 0: its decision is the warp's)
-            const bool wait_dep = __shfl_sync(0xffffffffu, (ok && j > 0 && !ring[slot].dep && !(i == ci && j <= cj)) ? 1 : 0, 0) != 0;
+            const bool wait_dep = __shfl_sync(0xffffffffu, (ok && j > 0 && !(ring[slot].dep & 1) && !(i == ci && j <= cj)) ? 1 : 0, 0) != 0;
             if (wait_dep && lane == 0) {
                 const unsigned long long T = (unsigned long long)ring[slot].T;
                 const long long t0 = clock64();
@@ -527,6 +536,7 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&rempty[rb]));
         };
+        TracePart TP;   // pass 2: this thread's trace terms of the current run
         for (int k = 0;; ++k) {
             const int s = k % NST;
             // a warp-wide vote (a consumer-wide one would couple the warps every tile): a warp whose
@@ -550,7 +560,6 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
             p.d0_df = sitem[s].d0_df;
             p.dn_df = sitem[s].dn_df;
             const StepScalars<PREC> S(p, cp);
-            TracePart TP;
             if (active && r < n) {
                 const WP* __restrict__ win = static_cast<const WP*>(sitem[s].win);
                 WP* wout = static_cast<WP*>(sitem[s].wout);
@@ -589,11 +598,25 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                 row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wout + (size_t)r * ldq + cp, pblk + (size_t)r * ldpq + cp, TP);
             }
             if constexpr (MODE == MODE_DOT) {
-                // write the tile's per-thread trace terms (slot j + 1: the step's W_{j+1} traces;
-                // slot 0: the W_0 traces) to the next of BT_NRB buffers, then sum this warp's share
-                // of the reduction before it
+                // At the end of a run, write the run's per-thread trace terms (slot j + 1: the
+                // step's W_{j+1} traces; slot 0: the W_0 traces) to the next of BT_NRB buffers,
+                // then sum this warp's share of the reduction before it; the run's sums go to the
+                // partials of its last tile. The other tiles of the run get zero partials, so the
+                // per-tile sum in tile order stays fixed.
                 const int nred = j == 0 ? 2 : 1;
-                for (int qq = 0; qq < nred; ++qq, ++nreduce) {
+                const bool run_end = (sitem[s].dep & 2) != 0;
+                if (!run_end && warp == 0) {
+                    for (int qq = 0; qq < nred; ++qq) {
+                        const int slot = qq ? 0 : j + 1;
+                        for (int c = lane; c < b; c += 32) {
+                            if constexpr (PREC == LL_PREC_F64)
+                                static_cast<double*>(sitem[s].aux)[((size_t)slot * T + t) * b + c] = 0.0;
+                            else
+                                static_cast<float2*>(sitem[s].aux)[((size_t)slot * T + t) * b + c] = make_float2(0.f, 0.f);
+                        }
+                    }
+                }
+                for (int qq = 0; run_end && qq < nred; ++qq, ++nreduce) {
                     const int slot = qq ? 0 : j + 1;
                     const int rb = nreduce % BT_NRB;
                     const bool okr = nreduce < BT_NRB ||
@@ -612,6 +635,7 @@ __global__ void __launch_bounds__(BT_MAX_THREADS, 1) k_leja_tma_batched(const Ba
                     if (lane == 0) mbar_arrive(smem_u32(&rfull[rb]));
                     if (nreduce > 0) reduce_share(nreduce - 1);
                 }
+                if (run_end) TP = TracePart{};
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
