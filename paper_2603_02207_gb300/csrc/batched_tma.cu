@@ -3,8 +3,8 @@
 //
 // Work items are (step j, matrix i, row tile t), numbered step-major over the matrices still
 // active at step j (sorted by degree, descending, so they are a prefix). A CTA has these roles:
-//  * the producer warp takes item numbers from a global ticket, eight at a time, one batch ahead:
-//    eight lanes decode a batch from tables held in shared memory and start the loads of each
+//  * the producer warp takes item numbers from a global ticket, BT_TAKE at a time, one batch
+//    ahead: BT_TAKE lanes decode a batch from tables held in shared memory and start the loads of each
 //    item's step scalars, pointers, tile counts and arrival counter; one batch later the batch is
 //    written into a ring of taken items and the copies of its gather-column lists start. To issue
 //    an item, the producer makes sure every tile of step j - 1 of matrix i has finished (known
@@ -12,10 +12,12 @@
 //    copies: descriptor, operand windows, V/P rows and the gathered rows of W_j of matrix i,
 //    through that matrix's own tensor maps;
 //  * the consumer warps compute the item's rows with the per-row arithmetic of the single-matrix
-//    kernels and store W_{j+1} (and P). In pass 2 each thread writes its trace terms to one of
-//    BT_NRB buffers, and after writing those of a tile each warp sums its share of column pairs of
-//    the previous tile's buffer over the rows (so no warp waits for all the others to finish a
-//    tile); the per-tile partials of every step are reduced per matrix after the pass;
+//    kernels and store W_{j+1} (and P). In pass 2 each thread keeps its trace terms over a run of
+//    tiles (consecutive items of one batch with the same step and matrix), then writes them to
+//    one of BT_NRB buffers, and after writing those of a run each warp sums its share of column
+//    pairs of the previous run's buffer over the rows (so no warp waits for all the others to
+//    finish a run); the run's sums are the partials of its last tile (its other tiles get zero),
+//    and the per-tile partials of every step are reduced per matrix after the pass;
 //  * the freeing warp waits for each stage's consumers, frees the stage for the producer and
 //    queues the finished tile's matrix;
 //  * the releasing warp publishes the queued tiles' completion: one release fence for all the

@@ -288,8 +288,8 @@ inline void tma_stage_layout(TmaParams& q, int Rt, double avg, double avgfar, do
 }
 
 // ---- batched TMA passes ----------------------------------------------------------------------
-constexpr int BT_IRING = 16;   // work items taken ahead of the one being issued
-constexpr int BT_TAKE = 8;     // items taken per ticket increment (decoded by eight lanes)
+constexpr int BT_IRING = 32;   // work items taken ahead of the one being issued
+constexpr int BT_TAKE = 16;    // items taken per ticket increment (decoded by sixteen lanes)
 constexpr int BT_NRB = 3;      // trace-term buffers of the consumer warps (a tile's terms are summed one tile later)
 constexpr int BT_MAX_THREADS = 512 + 96;   // consumers, then the producer, freeing and releasing warps
 
