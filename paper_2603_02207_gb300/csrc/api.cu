@@ -582,6 +582,13 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     void* S = kept_buf("fw_S");
     const double* Gb = static_cast<const double*>(kept_buf("fw_G"));
     const double* basis = static_cast<const double*>(kept_buf("fw_basis"));
+    if (prec == LL_PREC_DF64) {
+        // the DF64 forward keeps [Q | G'] only as double-float column pairs (V)
+        WS(b64, double*, "bw_basis64", (size_t)n * l2 * sizeof(double));
+        LL_CK(launch_block_to_f64(prec, V, l2, b64, l2, n, b2, s));
+        h->launches++;
+        basis = b64;
+    }
     const double* rinv1 = static_cast<const double*>(kept_buf("fw_rinv1"));
     const double* rinv2 = static_cast<const double*>(kept_buf("fw_rinv"));
     if (!S || !Gb || !basis || !rinv1 || !rinv2) return fail(h, LL_ERR_NO_FORWARD, "kept sketch missing");
@@ -616,10 +623,10 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     LL_CK(launch_gram(T_F64, basis + kq, l2, kg, T_F64, FV64, b2, kq, n, false, gpart, gticket, C1, ggrid, s));
     LL_CK(launch_gram(T_F64, Gb, kg, kg, T_F64, basis, l2, kq, n, false, gpart, gticket, C2, ggrid, s));
     LL_CK(launch_scaled_copy_f64(C1, kq, C1, kq, 2 * kg, kq, 1.0 / kg, s));
-    LL_CK(launch_project(Gb, kg, kg, FV64, b2, kq, C1, n, ZQa, kq, T_F64, nullptr, 0, 0, 0, s));
-    LL_CK(launch_project(FV64 + kq, b2, kg, ZQa, kq, kq, C2, n, ZQ, kq, T_F64, nullptr, 0, 0, 0, s));
+    LL_CK(launch_project(T_F64, Gb, kg, kg, FV64, b2, kq, C1, n, ZQa, kq, T_F64, nullptr, 0, 0, 0, s));
+    LL_CK(launch_project(T_F64, FV64 + kq, b2, kg, ZQa, kq, kq, C2, n, ZQ, kq, T_F64, nullptr, 0, 0, 0, s));
     LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, ZQ, kq, kq, n, false, gpart, gticket, C3, ggrid, s));
-    LL_CK(launch_project(basis, l2, kq, ZQ, kq, kq, C3, n, Xb, kq, T_F64, nullptr, 0, 0, 0, s));
+    LL_CK(launch_project(T_F64, basis, l2, kq, ZQ, kq, kq, C3, n, Xb, kq, T_F64, nullptr, 0, 0, 0, s));
     h->launches += 8;
     // R^-1 = R1^-1 R2^-1 (Y R1^-1 = Q1, Q1 R2^-1 = Q), and M = 2 R^-T, on the host (kq x kq)
     std::vector<double> r1((size_t)kq * kq), r2((size_t)kq * kq), mt((size_t)kq * kq, 0.0);
@@ -983,7 +990,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     WS(wa, void*, "fw_wa", (size_t)n * l2 * ew);
     WS(wb, void*, "fw_wb", (size_t)n * l2 * ew);
     WS(basis, double*, "fw_basis", (size_t)n * l2 * sizeof(double));
-    WS(q1, double*, "fw_q1", (size_t)n * kq * sizeof(double));
+    WS(q1, double*, "fw_q1", (size_t)n * (l1 > kq ? l1 : kq) * sizeof(double));   // FP64, or DF64 column pairs
     void* V = basis;
     if (wt != T_F64) {
         WS(vv, void*, "fw_V", (size_t)n * l2 * ew);
@@ -1061,17 +1068,25 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             t1 = h->last_threads;
             LL_CK(rec(h->ev[2], q));
 
-            // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']
+            // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']. In the DF64
+            // mode Q1 and Q stay double-float column pairs (Q in V itself): the products are
+            // double-float anyway, and FP64 intermediates would only add conversions on GB300's
+            // slow FP64 pipe. The other modes keep FP64 Q1 and Q (the basis block).
+            const bool dfq = prec == LL_PREC_DF64;
+            const int tq = dfq ? wt : T_F64;
+            const long long ldq1 = dfq ? l1 : kq;
+            const void* Qb = dfq ? V : static_cast<const void*>(basis);
             LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
             LL_CK(launch_chol_rinv(gram, kq, rinv1, qrstat, q));
-            LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, q1, kq, T_F64, nullptr, 0, q));
-            LL_CK(launch_gram(T_F64, q1, kq, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
+            if (dfq) LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, nullptr, 0, wt, q1, l1, q));
+            else LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, q1, kq, T_F64, nullptr, 0, q));
+            LL_CK(launch_gram(tq, q1, ldq1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
             LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
-            LL_CK(launch_apply_rinv(T_F64, q1, kq, n, kq, rinv, basis, l2, wt, wt != T_F64 ? V : nullptr, l2, q));
-            LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, q));
+            LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, dfq ? nullptr : basis, l2, wt, wt != T_F64 ? V : nullptr, l2, q));
+            LL_CK(launch_gram(tq, Qb, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, q));
             // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
             // The typed block pointer of V is offset by kq elements: element index r * l2 + kq + c.
-            LL_CK(launch_project(basis, l2, kq, G, kg, kg, gram, n, basis + kq, l2, wt,
+            LL_CK(launch_project(tq, Qb, l2, kq, G, kg, kg, gram, n, dfq ? nullptr : basis + kq, l2, wt,
                                  wt != T_F64 ? V : nullptr, l2, (b2 & 1), kq, q));
             h->launches += 8;
             LL_CK(rec(h->ev[3], q));
@@ -1880,6 +1895,13 @@ ll_status ll_kept_basis(const ll_handle* h, double* out, int64_t ld, int64_t* n_
     if (kg_out) *kg_out = h->kept_kg;
     if (!out) return LL_OK;
     if (ld < b2) return LL_ERR_INVALID_ARG;
+    if (h->kept_prec == LL_PREC_DF64) {
+        // the DF64 forward keeps [Q | G'] as double-float column pairs (V) only
+        auto iv = h->ws.find("fw_V");
+        if (iv == h->ws.end()) return LL_ERR_NO_FORWARD;
+        cudaError_t e = launch_block_to_f64(h->kept_prec, iv->second.p, l2, out, ld, (int)h->kept_n, b2, (cudaStream_t)stream);
+        return e == cudaSuccess ? LL_OK : LL_ERR_CUDA;
+    }
     cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ld * sizeof(double), it->second.p, (size_t)l2 * sizeof(double),
                                       (size_t)b2 * sizeof(double), (size_t)h->kept_n, cudaMemcpyDeviceToDevice,
                                       (cudaStream_t)stream);

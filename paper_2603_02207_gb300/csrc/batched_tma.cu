@@ -92,16 +92,6 @@ __device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(m) : "memory");
 }
 
-// (ah, al) += (bh, bl) on both lanes of double-float pairs: TwoSum (Knuth) of the leading parts,
-// the trailing parts added to the error, then a renormalisation (FastTwoSum)
-__device__ __forceinline__ void df2_add(f2x& ah, f2x& al, f2x bh, f2x bl) {
-    const f2x s = f2_add(ah, bh);
-    const f2x bb = f2_sub(s, ah);
-    f2x e = f2_add(f2_sub(ah, f2_sub(s, bb)), f2_sub(bh, bb));
-    e = f2_add(e, f2_add(al, bl));
-    ah = f2_add(s, e);
-    al = f2_sub(e, f2_sub(ah, s));
-}
 __device__ __forceinline__ f2x shfl_down_f2(f2x v, int off) {
     return __shfl_down_sync(0xffffffffu, v, off);
 }

@@ -141,6 +141,16 @@ __device__ __forceinline__ void df2_mac_pp(f2x& sh, f2x& sl, f2x xh2, f2x xl2, f
     sl = f2_add(sl, f2_add(f2_sub(t2, t3), e));
     sh = s;
 }
+// (ah, al) += (bh, bl) on both lanes of double-float pairs: TwoSum (Knuth) of the leading parts,
+// the trailing parts added to the error, then a renormalisation (FastTwoSum)
+__device__ __forceinline__ void df2_add(f2x& ah, f2x& al, f2x bh, f2x bl) {
+    const f2x s = f2_add(ah, bh);
+    const f2x bb = f2_sub(s, ah);
+    f2x e = f2_add(f2_sub(ah, f2_sub(s, bb)), f2_sub(bh, bb));
+    e = f2_add(e, f2_add(al, bl));
+    ah = f2_add(s, e);
+    al = f2_sub(e, f2_sub(ah, s));
+}
 __device__ __forceinline__ void df2_norm(f2x sh, f2x sl, f2x& h, f2x& l) {
     const f2x s = f2_add(sh, sl);
     l = f2_sub(sl, f2_sub(s, sh));

@@ -177,13 +177,15 @@ cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, co
                         int n, bool sym, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
 // Cholesky G = R^T R (upper R) and Rinv = R^{-1}; status[0] = 1 on a non-positive pivot
 cudaError_t launch_chol_rinv(const double* G, int k, double* Rinv, int* status, cudaStream_t s);
-// Out = X * Rinv (upper triangular k x k), X type tx; writes FP64 (out64) and optionally out2 (type t2)
+// Out = X * Rinv (upper triangular k x k), X type tx; writes FP64 (out64; may be null) and
+// optionally out2 (type t2)
 cudaError_t launch_apply_rinv(int tx, const void* X, long long ldx, int n, int k, const double* Rinv,
                               double* out64, long long ld64, int t2, void* out2, long long ld2, cudaStream_t s);
-// G' = G - Q C, G: FP64 (ldg), Q: FP64 (ldq), C k x kg; writes FP64 (out64, columns [0, kg)) and
-// optionally out2 (type t2, columns [col2, col2 + kg)); zero_pad: also write 0 to the column after
-// the last one (the pad column of a pair layout)
-cudaError_t launch_project(const double* Q, long long ldq, int k, const double* G, long long ldg, int kg,
+// G' = G - Q C in double-float arithmetic, G: FP64 (ldg), Q: type tq (T_F64 or T_DF64 column
+// pairs, ldq), C k x kg; writes FP64 (out64, columns [0, kg); may be null) and optionally out2
+// (type t2, columns [col2, col2 + kg)); zero_pad: also write 0 to the column after the last one
+// (the pad column of a pair layout)
+cudaError_t launch_project(int tq, const void* Q, long long ldq, int k, const double* G, long long ldg, int kg,
                            const double* C, int n, double* out64, long long ld64, int t2, void* out2,
                            long long ld2, int zero_pad, int col2, cudaStream_t s);
 

@@ -20,7 +20,7 @@ __host__ __device__ inline int gram_tile_rows(int kxp, int kzp, bool sym) {
     int tr = (1152 / cols) / 16 * 16;
     return tr < 32 ? 32 : (tr > 256 ? 256 : tr);
 }
-constexpr int QR_FLUSH = 8;     // tiles summed in double-float before an FP64 flush
+constexpr int QR_FLUSH = 8;     // tiles summed in double-float before they join the running sum
 
 // A double as an unevaluated float pair hi + lo, from its bit fields with integer operations and
 // one integer-to-float conversion (GB300 runs FP64 instructions, conversions from double among
@@ -121,9 +121,10 @@ __device__ __forceinline__ void ld_split(const dfp* p, size_t i, float& h, float
 
 // X^T Z over n rows in double-float arithmetic on the FP32 pipes (GB300's FP64 pipe runs at 1/62
 // of FP32). Each thread owns a 4x4 register tile of the output and a group of rows; per-thread
-// double-float sums cover QR_FLUSH tiles (at most 2048 rows) before they are added into FP64
-// accumulators, so the error stays near FP64's. Per-CTA partials are reduced by the last CTA in
-// a fixed order. sym: Z == X and only the upper-triangular 4x4 tiles are computed.
+// double-float sums cover QR_FLUSH tiles (at most 2048 rows) before they are added (TwoSum, still
+// on the FP32 pipes) into a running double-float sum, converted to FP64 once at the end, so the
+// error stays near FP64's. Per-CTA partials are reduced by the last CTA in a fixed order. sym:
+// Z == X and only the upper-triangular 4x4 tiles are computed.
 template <typename TX, typename TZ>
 __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long long ldz, int kz, int sym, GramJob one,
                                                      const GramJob* jobs) {
@@ -166,12 +167,9 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
     }
     // 4 x 4 output tile as 4 rows x 2 column pairs of double-float sums (f32x2: both columns of a
     // pair per instruction, the same operations per lane as the scalar double-float MAC)
-    f2x h2[8], l2[8];
-    double a64[16];
+    f2x h2[8], l2[8], H2[8], L2[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) { h2[e] = 0ull; l2[e] = 0ull; }
-#pragma unroll
-    for (int e = 0; e < 16; ++e) a64[e] = 0.0;
+    for (int e = 0; e < 8; ++e) { h2[e] = 0ull; l2[e] = 0ull; H2[e] = 0ull; L2[e] = 0ull; }
     const int ntiles = (n + trows - 1) / trows;
     // raw tiles staged asynchronously one tile ahead (two buffers after the split arrays), so that
     // the next tile's loads are in flight while this one is computed
@@ -217,23 +215,21 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
             cnt = 0;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                float h0, h1, l0, l1;
-                f2_unpack(h2[e], h0, h1);
-                f2_unpack(l2[e], l0, l1);
-                a64[2 * e] += (double)h0 + (double)l0;
-                a64[2 * e + 1] += (double)h1 + (double)l1;
+                df2_add(H2[e], L2[e], h2[e], l2[e]);
                 h2[e] = 0ull;
                 l2[e] = 0ull;
             }
         }
     }
+    double a64[16];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
+        df2_add(H2[e], L2[e], h2[e], l2[e]);
         float h0, h1, l0, l1;
-        f2_unpack(h2[e], h0, h1);
-        f2_unpack(l2[e], l0, l1);
-        a64[2 * e] += (double)h0 + (double)l0;
-        a64[2 * e + 1] += (double)h1 + (double)l1;
+        f2_unpack(H2[e], h0, h1);
+        f2_unpack(L2[e], l0, l1);
+        a64[2 * e] = (double)h0 + (double)l0;
+        a64[2 * e + 1] = (double)h1 + (double)l1;
     }
     // reduce the row groups (fixed order) and write this CTA's partial
     double* red = reinterpret_cast<double*>(sgf);
@@ -480,7 +476,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
         const int row = tile * RG + rr;
         if (!act || row >= n) continue;
         if (zero_pad && cg == 0) {
-            out64[(size_t)row * ld64 + kc] = 0.0;
+            if (out64) out64[(size_t)row * ld64 + kc] = 0.0;
             if (out2) store_f64<T2>(out2, (size_t)row * ld2 + col2 + kc, 0.0);
         }
         float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
@@ -499,12 +495,20 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
             const int c = cg * 4 + j;
             if (c >= kc) break;
             if (MODE != 1) {
-                out64[(size_t)row * ld64 + c] = (double)h[j] + (double)l[j];
+                if (out64) out64[(size_t)row * ld64 + c] = (double)h[j] + (double)l[j];
                 if (out2) st_out2(out2, (size_t)row * ld2 + col2 + c, h[j], l[j]);
             } else {
-                const double v = G[(size_t)row * ldg + c] - ((double)h[j] + (double)l[j]);
-                out64[(size_t)row * ld64 + c] = v;
-                if (out2) store_f64<T2>(out2, (size_t)row * ld2 + col2 + c, v);
+                // G - (h + l) in double-float on the FP32 pipes: G split from its bits, TwoSum of
+                // the leading parts, the trailing parts added to the error, renormalised
+                float gh, gl;
+                split_bits(G[(size_t)row * ldg + c], gh, gl);
+                const float sd = gh - h[j];
+                const float bb = sd - gh;
+                float e = (gh - (sd - bb)) + (-h[j] - bb);
+                e += gl - l[j];
+                const float2 r = df_norm(sd, e);
+                if (out64) out64[(size_t)row * ld64 + c] = (double)r.x + (double)r.y;
+                if (out2) st_out2(out2, (size_t)row * ld2 + col2 + c, r.x, r.y);
             }
         }
     }
@@ -572,10 +576,11 @@ cudaError_t launch_project_jobs(long long ldq, int k, long long ldg, int kg, lon
     return rowprod_dispatch<double, 1>(t2, ldq, k, kg, ldg, ld64, ld2, col2, zero_pad, one, jobs, count, n_max, s);
 }
 
-cudaError_t launch_project(const double* Q, long long ldq, int k, const double* G, long long ldg, int kg,
+cudaError_t launch_project(int tq, const void* Q, long long ldq, int k, const double* G, long long ldg, int kg,
                            const double* C, int n, double* out64, long long ld64, int t2, void* out2,
                            long long ld2, int zero_pad, int col2, cudaStream_t s) {
     const RowJob one{Q, C, G, out64, out2, n};
+    if (tq == T_DF64) return rowprod_dispatch<dfp, 1>(t2, ldq, k, kg, ldg, ld64, ld2, col2, zero_pad, one, nullptr, 1, n, s);
     return launch_project_jobs(ldq, k, ldg, kg, ld64, t2, ld2, zero_pad, col2, one, nullptr, 1, n, s);
 }
 
