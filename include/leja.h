@@ -76,13 +76,20 @@ enum { LL_EST_HUTCHPP = 0, LL_EST_HUTCHINSON = 1 };
 enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
 
 /* Step kernel of the m-step passes:
- *   LL_KERNEL_AUTO    autotuned: the kernel and its launch shape are timed once per
- *                     (precision, pass, n, nnz, block width) on the handle and the fastest is kept;
+ *   LL_KERNEL_AUTO    banded matrices (every row's columns strictly increasing and within 2 of
+ *                     the diagonal) take LL_KERNEL_BAND; otherwise autotuned: the kernel and its
+ *                     launch shape are timed once per (precision, pass, n, nnz, block width) on
+ *                     the handle and the fastest is kept;
  *   LL_KERNEL_GATHER  neighbour rows gathered into registers by each thread (k_leja_step);
  *   LL_KERNEL_TMA     neighbour rows gathered into shared memory by TMA (tile::gather4) in a
  *                     multi-stage mbarrier pipeline (k_leja_tma); falls back to LL_KERNEL_GATHER
- *                     when a block row is wider than 256 elements.                               */
-enum { LL_KERNEL_AUTO = 0, LL_KERNEL_GATHER = 1, LL_KERNEL_TMA = 2 };
+ *                     when a block row is wider than 256 elements;
+ *   LL_KERNEL_BAND    banded matrices only (else as LL_KERNEL_AUTO): up to four steps per launch
+ *                     on row tiles with halos, W_j between the steps in shared memory
+ *                     (k_leja_band); W_{j+1} and P equal the one-step kernels' bit for bit. Not
+ *                     with the stopping rule (tol > 0), the adjoint or the batched call, which
+ *                     run the one-step kernels.                                                  */
+enum { LL_KERNEL_AUTO = 0, LL_KERNEL_GATHER = 1, LL_KERNEL_TMA = 2, LL_KERNEL_BAND = 3 };
 
 /* Probe streams of the counter-based generator (see ll_probes). */
 enum { LL_STREAM_S = 0, LL_STREAM_G = 1, LL_STREAM_POWER = 2 };

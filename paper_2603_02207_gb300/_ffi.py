@@ -23,7 +23,7 @@ LL_PREC_F64, LL_PREC_DF64, LL_PREC_F32_MIXED = 0, 1, 2
 LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
-LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA = 0, 1, 2
+LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA, LL_KERNEL_BAND = 0, 1, 2, 3
 LL_EST_HUTCHPP, LL_EST_HUTCHINSON = 0, 1
 LL_INJECT_NONE, LL_INJECT_STALL = 0, 1
 LL_NOALLOC_MAX_ROWS = 1 << 18

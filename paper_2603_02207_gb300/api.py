@@ -11,13 +11,13 @@ import dataclasses
 import numpy as np
 
 from . import _ffi
-from ._ffi import (LL_EST_HUTCHINSON, LL_EST_HUTCHPP, LL_F32, LL_F64, LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA,  # noqa: F401
+from ._ffi import (LL_EST_HUTCHINSON, LL_EST_HUTCHPP, LL_F32, LL_F64, LL_KERNEL_AUTO, LL_KERNEL_BAND, LL_KERNEL_GATHER, LL_KERNEL_TMA,  # noqa: F401
                    LL_PREC_DF64, LL_PREC_F32_MIXED, LL_PREC_F64, LL_PROBE_GAUSSIAN, LL_PROBE_RADEMACHER, LL_STREAM_G, LL_STREAM_POWER, LL_STREAM_S,
                    LL_SVAL_CENTER, LL_SVAL_HALF_LMAX)
 
 PRECISIONS = {"f64": LL_PREC_F64, "df64": LL_PREC_DF64, "f32": LL_PREC_F32_MIXED}
 PROBE_KINDS = {"rademacher": LL_PROBE_RADEMACHER, "gaussian": LL_PROBE_GAUSSIAN}
-STEP_KERNELS = {"auto": LL_KERNEL_AUTO, "gather": LL_KERNEL_GATHER, "tma": LL_KERNEL_TMA}
+STEP_KERNELS = {"auto": LL_KERNEL_AUTO, "gather": LL_KERNEL_GATHER, "tma": LL_KERNEL_TMA, "band": LL_KERNEL_BAND}
 ESTIMATORS = {"hutchpp": LL_EST_HUTCHPP, "hutchinson": LL_EST_HUTCHINSON}
 
 

@@ -63,6 +63,7 @@ struct ll_handle {
         int kernel = 0, threads1 = 0, threads2 = 0;   // step kernel of both passes, CTA sizes
     } gbat;
     int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
+    bool band_ok = false;     // the last validated matrix suits the banded kernel
     int max_row = 0;          // longest row of the last validated matrix
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
@@ -140,16 +141,19 @@ ll_status check_bounds(ll_handle* h, ll_bounds b) {
 // Validates the device CSR (synchronises the stream).
 ll_status validate_csr(ll_handle* h, const ll_csr* A, cudaStream_t s) {
     if (A->n == 0) return LL_OK;
-    WS(flag, int*, "csr_flag", 3 * sizeof(int));
-    LL_CK(cudaMemsetAsync(flag, 0, 3 * sizeof(int), s));
-    LL_CK(launch_validate_csr(A->rowptr, A->colind, (int)A->n, A->nnz, flag, s, flag + 2));
+    WS(flag, int*, "csr_flag", 4 * sizeof(int));
+    LL_CK(cudaMemsetAsync(flag, 0, 4 * sizeof(int), s));
+    LL_CK(launch_validate_csr(A->rowptr, A->colind, (int)A->n, A->nnz, flag, s, flag + 2, flag + 3));
     h->launches++;
-    int hv[3] = {0, 0, 0};
+    int hv[4] = {0, 0, 0, 0};
     LL_CK(cudaMemcpyAsync(hv, flag, sizeof hv, cudaMemcpyDeviceToHost, s));
     LL_CK(cudaStreamSynchronize(s));
     const int hf = hv[0];
     h->far_entries = hv[1];
     h->max_row = hv[2];
+    // the banded kernel takes matrices whose rows hold strictly increasing columns within
+    // BAND_H (= TMA_HALO) of the diagonal
+    h->band_ok = hv[1] == 0 && hv[3] == 0;
     if (hf) {
         char buf[160];
         snprintf(buf, sizeof buf, "invalid CSR:%s%s%s", (hf & 4) ? " rowptr[0]!=0 or rowptr[n]!=nnz;" : "",
@@ -341,11 +345,79 @@ struct StopState {
 // growing there; the dots of later steps are still written for the columns that run), and once
 // no column runs the remaining steps return at once. stop.stop_deg then holds each column's
 // final degree. The step kernel is the one chosen for the plain mode.
+// The pass on the banded kernel: the prepared values in DIA layout, then ceil(m / BAND_SMAX)
+// launches of up to BAND_SMAX steps each (W_j in and W_{j+s} out alternate between wa and wb).
+ll_status run_band_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int precision, int mode, int n, int b,
+                        const BandLaunch& BL, const void* win0, long long ldw, void* wa, void* wb, void* P,
+                        long long ldp, double* dots, const std::vector<double>& beta, const std::vector<double>& d,
+                        cudaStream_t s) {
+    static_assert(BAND_H == TMA_HALO, "the band test of the validation uses TMA_HALO");
+    const int m = (int)d.size() - 1;
+    const size_t raw = precision == LL_PREC_F32_MIXED ? 4 : 8;
+    WS(dia, void*, "band_dia", (size_t)n * (2 * BAND_H + 1) * raw);
+    LL_CK(launch_to_dia(precision, A->rowptr, A->colind, vals_prep, n, dia, s));
+    h->launches++;
+    BandParams bp{};
+    bp.dia = dia;
+    bp.ldw = ldw;
+    bp.ldp = ldp;
+    bp.n = n;
+    bp.b = b;
+    bp.tp = BL.tp;
+    bp.R = BL.R;
+    bp.num_tiles = BL.num_tiles;
+    bp.d0 = d[0];
+    bp.d0_df = df_split(d[0]);
+    if (mode == MODE_DOT) {
+        WS(partials, double*, "band_partials", (size_t)(BAND_SMAX + 1) * BL.grid * b * sizeof(double));
+        WS(ticket, unsigned int*, "dot_ticket", sizeof(unsigned int));
+        LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
+        bp.v = win0;
+        bp.partials = partials;
+        bp.ticket = ticket;
+        bp.dots = dots;
+    } else {
+        bp.p = P;
+    }
+    const void* cur = win0;
+    int flip = 0;
+    for (int j = 0; j < m;) {
+        const int sn = std::min(BAND_SMAX, m - j);
+        bp.j0 = j;
+        bp.s = sn;
+        for (int q = 0; q < sn; ++q) {
+            bp.beta[q] = beta[j + q];
+            bp.dn[q] = d[j + q + 1];
+            bp.beta_df[q] = df_split(beta[j + q]);
+            bp.dn_df[q] = df_split(d[j + q + 1]);
+        }
+        void* out = flip ? wb : wa;
+        bp.win = cur;
+        bp.wout = out;
+        LL_CK(launch_band(precision, mode, BL, bp, s));
+        h->launches++;
+        cur = out;
+        flip ^= 1;
+        j += sn;
+    }
+    h->last_kernel = LL_KERNEL_BAND;
+    h->last_threads = BAND_THREADS;
+    return LL_OK;
+}
+
 ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int precision, int mode, int n, int b,
                    const void* win0, long long ldw, void* wa, void* wb, void* P, long long ldp, double* dots,
                    const std::vector<double>& beta, const std::vector<double>& d, int kernel, int threads_target,
                    int rpt, cudaStream_t s, const StopState& stop = StopState{}) {
     const int m = (int)d.size() - 1;
+    // banded matrices: several steps per launch (the stopping rule runs on the one-step kernels)
+    if (stop.tol <= 0.0 && (mode == MODE_ACCUM || mode == MODE_DOT) && h->band_ok && m > 0 &&
+        (kernel == LL_KERNEL_AUTO || kernel == LL_KERNEL_BAND)) {
+        BandLaunch BL;
+        if (plan_band(precision, mode, n, b, h->sm_count, BL))
+            return run_band_pass(h, A, vals_prep, precision, mode, n, b, BL, win0, ldw, wa, wb, P, ldp, dots, beta, d, s);
+    }
+    if (kernel == LL_KERNEL_BAND) kernel = LL_KERNEL_AUTO;
     StepParams p{};
     p.rowptr = A->rowptr;
     p.colind = A->colind;
@@ -738,7 +810,7 @@ ll_status ll_debug_inject(ll_handle* h, int what) {
 }
 
 ll_status ll_set_step_config(ll_handle* h, int step_kernel, int threads_per_block, int rows_per_thread) {
-    if (!h || step_kernel < LL_KERNEL_AUTO || step_kernel > LL_KERNEL_TMA || threads_per_block < 0 || rows_per_thread < 0)
+    if (!h || step_kernel < LL_KERNEL_AUTO || step_kernel > LL_KERNEL_BAND || threads_per_block < 0 || rows_per_thread < 0)
         return LL_ERR_INVALID_ARG;
     h->cfg_kernel = step_kernel;
     h->cfg_threads = threads_per_block;

@@ -79,8 +79,9 @@ constexpr int TMA_HALO = 2;
 // flag[0]: error bits (1 rowptr decreasing, 2 column out of range, 4 rowptr[0] != 0 or rowptr[n] != nnz);
 // flag[1]: stored entries with |col - row| > TMA_HALO (int32; saturates nowhere below 2^31)
 // rowmax (optional): atomicMax of the longest row's entry count
+// unsorted (optional): rows whose column indices are not strictly increasing
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz,
-                                int* flag, cudaStream_t s, int* rowmax = nullptr);
+                                int* flag, cudaStream_t s, int* rowmax = nullptr, int* unsorted = nullptr);
 cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype,
                               int n, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
 // out[e] = convert(values[e] * scale) into the storage type of `precision`
@@ -114,6 +115,38 @@ cudaError_t launch_scaled_copy_f64(const double* in, long long ld_in, double* ou
 
 // out[i * ld + i] = 1 for i < n (type t); the rest of `out` is left as is
 cudaError_t launch_unit_diag(int t, void* out, long long ld, int n, cudaStream_t s);
+
+// Banded Léja steps (band.cu): matrices whose entries all lie within BAND_H of the diagonal,
+// stored as BAND_H * 2 + 1 diagonals (DIA layout of the prepared values), s <= BAND_SMAX steps
+// per launch over row tiles with halos, the intermediate W in shared memory.
+constexpr int BAND_H = 2;
+constexpr int BAND_SMAX = 4;
+constexpr int BAND_THREADS = 256;
+struct BandParams {
+    const void* dia;     // n x (2 BAND_H + 1) prepared values (the precision's raw value type)
+    const void* win;     // W_{j0} (W type, ldw columns)
+    void* wout;          // W_{j0+s}
+    const void* v;       // pass 2: V (W type, ldw)
+    void* p;             // pass 1: P (P type, ldp), read (j0 > 0) and written
+    double* partials;    // pass 2: (BAND_SMAX + 1) x grid x b doubles
+    unsigned int* ticket;   // pass 2: zero-initialised counter, reset by the last CTA
+    double* dots;        // pass 2: (m + 1) x b traces; writes rows j0 + 1 .. j0 + s (and 0 if j0 = 0)
+    long long ldw, ldp;
+    int n, b, tp, R, num_tiles, s, j0;
+    double beta[BAND_SMAX], dn[BAND_SMAX], d0;    // beta_{j0+q}, d_{j0+q+1}, d_0
+    float2 beta_df[BAND_SMAX], dn_df[BAND_SMAX], d0_df;
+};
+struct BandLaunch {
+    int R = 0, tp = 0, num_tiles = 0, grid = 0;
+    size_t smem = 0;
+};
+// launch shape for (precision, MODE_ACCUM or MODE_DOT, n, b); false when not applicable
+bool plan_band(int precision, int mode, int n, int b, int sm_count, BandLaunch& L);
+cudaError_t launch_band(int precision, int mode, const BandLaunch& L, const BandParams& p, cudaStream_t s);
+// dia[r * (2 BAND_H + 1) + (c - r + BAND_H)] = vals[e] for every entry e = (r, c) (rows with
+// strictly increasing columns within BAND_H of the diagonal), zero elsewhere
+cudaError_t launch_to_dia(int precision, const int32_t* rowptr, const int32_t* colind, const void* vals, int n, void* dia,
+                          cudaStream_t s);
 
 // Start of a pass under Algorithm 2's stopping rule: e_0 = |d_0| ||W_0 col||_2 for every column
 // c < b of the n x b block W0 (element type of `precision`'s W blocks, ld columns); live[c] =

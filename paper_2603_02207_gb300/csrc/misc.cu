@@ -35,30 +35,38 @@ cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, 
 
 // ----------------------------------------------------------------------------- CSR validation
 // flag[0] bits: 1 = rowptr decreasing, 2 = column index out of range, 4 = rowptr[0] != 0 or
-// rowptr[n] != nnz. flag[1]: largest forward offset col - row (rows with a valid range only).
-__global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, int* rowmax) {
+// rowptr[n] != nnz. flag[1]: entries farther than TMA_HALO from the diagonal. unsorted (optional):
+// rows whose columns are not strictly increasing.
+__global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, int* rowmax,
+                               int* unsorted) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (tid == 0 && (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) atomicOr(flag, 4);
-    int far = 0, longest = 0;
+    int far = 0, longest = 0, unsort = 0;
     for (int i = tid; i < n; i += stride) {
         const int a = rowptr[i], e = rowptr[i + 1];
         if (e < a) { atomicOr(flag, 1); continue; }
         longest = max(longest, e - a);
         if (a < 0 || (int64_t)e > nnz) { atomicOr(flag, 4); continue; }
+        int prev = -1;
+        bool inc = true;
         for (int k = a; k < e; ++k) {
             const int c = colind[k];
             if (c < 0 || c >= n) atomicOr(flag, 2);
             else far += (c - i > TMA_HALO || i - c > TMA_HALO) ? 1 : 0;
+            inc = inc && c > prev;
+            prev = c;
         }
+        unsort += inc ? 0 : 1;
     }
     if (far > 0) atomicAdd(flag + 1, far);
     if (rowmax && longest > 0) atomicMax(rowmax, longest);
+    if (unsorted && unsort > 0) atomicAdd(unsorted, unsort);
 }
 
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, cudaStream_t s,
-                                int* rowmax) {
-    k_validate_csr<<<152 * 4, 256, 0, s>>>(rowptr, colind, n, nnz, flag, rowmax);
+                                int* rowmax, int* unsorted) {
+    k_validate_csr<<<152 * 4, 256, 0, s>>>(rowptr, colind, n, nnz, flag, rowmax, unsorted);
     return cudaGetLastError();
 }
 
