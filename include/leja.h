@@ -145,7 +145,7 @@ typedef struct {
     int k;                           /* sketch columns used (min(m_vec/3, n))                     */
     int kernel_launches;             /* library kernels launched by the call                      */
     float ms_probes, ms_pass1, ms_qr, ms_pass2, ms_total;   /* device times (CUDA events)         */
-    int kernel_pass1, kernel_pass2;  /* LL_KERNEL_GATHER or LL_KERNEL_TMA used by each pass       */
+    int kernel_pass1, kernel_pass2;  /* LL_KERNEL_GATHER, _TMA or _BAND used by each pass          */
     int threads_pass1, threads_pass2;   /* CTA size used by each pass                             */
     int deg_max_pass1, deg_max_pass2;   /* largest final degree over the columns of each pass
                                            (the degree itself under a fixed degree)              */
