@@ -654,10 +654,11 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     void* S = kept_buf("fw_S");
     const double* Gb = static_cast<const double*>(kept_buf("fw_G"));
     const double* basis = static_cast<const double*>(kept_buf("fw_basis"));
-    if (prec == LL_PREC_DF64) {
-        // the DF64 forward keeps [Q | G'] only as double-float column pairs (V)
+    if (prec != LL_PREC_F64) {
+        // the DF64 forward keeps [Q | G'] as double-float column pairs in V, the FP32-mixed one in
+        // the basis block
         WS(b64, double*, "bw_basis64", (size_t)n * l2 * sizeof(double));
-        LL_CK(launch_block_to_f64(prec, V, l2, b64, l2, n, b2, s));
+        LL_CK(launch_block_to_f64(prec, prec == LL_PREC_DF64 ? V : static_cast<const void*>(basis), l2, b64, l2, n, b2, s));
         h->launches++;
         basis = b64;
     }
@@ -1123,7 +1124,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             // G' = (I - Q Q^T) G = 0; the estimate is the exact trace of p(A~)
             LL_CK(rec(h->ev[2], q));
             LL_CK(cudaMemsetAsync(basis, 0, (size_t)n * l2 * sizeof(double), q));
-            LL_CK(launch_unit_diag(T_F64, basis, l2, n, q));
+            // the basis block holds FP64 (F64, DF64) or double-float pairs (FP32-mixed)
+            LL_CK(launch_unit_diag(prec == LL_PREC_F32_MIXED ? T_DF64 : T_F64, basis, l2, n, q));
             h->launches++;
             if (wt != T_F64) {
                 LL_CK(cudaMemsetAsync(V, 0, (size_t)n * l2 * ew, q));
@@ -1140,27 +1142,35 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             t1 = h->last_threads;
             LL_CK(rec(h->ev[2], q));
 
-            // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']. In the DF64
-            // mode Q1 and Q stay double-float column pairs (Q in V itself): the products are
-            // double-float anyway, and FP64 intermediates would only add conversions on GB300's
-            // slow FP64 pipe. The other modes keep FP64 Q1 and Q (the basis block).
-            const bool dfq = prec == LL_PREC_DF64;
-            const int tq = dfq ? wt : T_F64;
+            // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']. Outside the
+            // F64 mode Q1 and Q stay double-float column pairs: the products are double-float
+            // anyway, and FP64 intermediates would only add conversions on GB300's slow FP64
+            // pipe. In the DF64 mode Q lives in V itself; in the FP32-mixed mode [Q | G'] is
+            // formed as pairs in the basis block and V (FP32) is written from it; the F64 mode
+            // keeps FP64 Q1 and Q (the basis block).
+            const bool dfq = prec != LL_PREC_F64;
+            const bool qv = prec == LL_PREC_DF64;
+            const int tq = dfq ? T_DF64 : T_F64;
             const long long ldq1 = dfq ? l1 : kq;
-            const void* Qb = dfq ? V : static_cast<const void*>(basis);
+            void* Qb = qv ? V : static_cast<void*>(basis);
             LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
             LL_CK(launch_chol_rinv(gram, kq, rinv1, qrstat, q));
-            if (dfq) LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, nullptr, 0, wt, q1, l1, q));
+            if (dfq) LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, nullptr, 0, T_DF64, q1, l1, q));
             else LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, q1, kq, T_F64, nullptr, 0, q));
             LL_CK(launch_gram(tq, q1, ldq1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
             LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
-            LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, dfq ? nullptr : basis, l2, wt, wt != T_F64 ? V : nullptr, l2, q));
+            if (dfq) LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, nullptr, l2, T_DF64, Qb, l2, q));
+            else LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, basis, l2, T_F64, nullptr, l2, q));
             LL_CK(launch_gram(tq, Qb, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, q));
             // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
-            // The typed block pointer of V is offset by kq elements: element index r * l2 + kq + c.
-            LL_CK(launch_project(tq, Qb, l2, kq, G, kg, kg, gram, n, dfq ? nullptr : basis + kq, l2, wt,
-                                 wt != T_F64 ? V : nullptr, l2, (b2 & 1), kq, q));
+            // The typed block pointer is offset by kq elements: element index r * l2 + kq + c.
+            LL_CK(launch_project(tq, Qb, l2, kq, G, kg, kg, gram, n, dfq ? nullptr : basis + kq, l2, T_DF64,
+                                 dfq ? Qb : nullptr, l2, (b2 & 1), kq, q));
             h->launches += 8;
+            if (dfq && !qv) {
+                LL_CK(launch_dfp_to_f32(basis, l2, static_cast<float*>(V), l2, n, b2, l2, q));
+                h->launches++;
+            }
             LL_CK(rec(h->ev[3], q));
         }
 
@@ -1967,9 +1977,10 @@ ll_status ll_kept_basis(const ll_handle* h, double* out, int64_t ld, int64_t* n_
     if (kg_out) *kg_out = h->kept_kg;
     if (!out) return LL_OK;
     if (ld < b2) return LL_ERR_INVALID_ARG;
-    if (h->kept_prec == LL_PREC_DF64) {
-        // the DF64 forward keeps [Q | G'] as double-float column pairs (V) only
-        auto iv = h->ws.find("fw_V");
+    if (h->kept_prec != LL_PREC_F64) {
+        // [Q | G'] is kept as double-float column pairs: in V (DF64) or in the basis block
+        // (FP32-mixed)
+        auto iv = h->ws.find(h->kept_prec == LL_PREC_DF64 ? "fw_V" : "fw_basis");
         if (iv == h->ws.end()) return LL_ERR_NO_FORWARD;
         cudaError_t e = launch_block_to_f64(h->kept_prec, iv->second.p, l2, out, ld, (int)h->kept_n, b2, (cudaStream_t)stream);
         return e == cudaSuccess ? LL_OK : LL_ERR_CUDA;

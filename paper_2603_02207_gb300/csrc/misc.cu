@@ -183,6 +183,29 @@ cudaError_t launch_block_to_f64(int precision, const void* in, long long ld_in, 
     return cudaGetLastError();
 }
 
+// out[r, c] = hi + lo (FP32) of a double-float column-pair block, columns [b, pad) zero
+__global__ void k_dfp_to_f32(const dfp* in, long long ld_in, float* out, long long ld_out, int n, int b, int pad) {
+    const long long total = (long long)n * pad;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / pad);
+        const int c = (int)(e - (long long)r * pad);
+        float v = 0.f;
+        if (c < b) {
+            const float* f = reinterpret_cast<const float*>(in) + dfp_hi((size_t)r * ld_in + c);
+            v = f[0] + f[2];
+        }
+        out[(size_t)r * ld_out + c] = v;
+    }
+}
+
+cudaError_t launch_dfp_to_f32(const void* in, long long ld_in, float* out, long long ld_out, int n, int b, int pad,
+                              cudaStream_t s) {
+    if (pad < b) pad = b;
+    if ((long long)n * pad <= 0) return cudaSuccess;
+    k_dfp_to_f32<<<152 * 8, 256, 0, s>>>(static_cast<const dfp*>(in), ld_in, out, ld_out, n, b, pad);
+    return cudaGetLastError();
+}
+
 __global__ void k_scaled_copy(const double* in, long long ld_in, double* out, long long ld_out, int n, int b, double alpha) {
     const long long total = (long long)n * b;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
