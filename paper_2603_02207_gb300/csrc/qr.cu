@@ -17,8 +17,8 @@ constexpr int QR_THREADS = 256;
 // latency (k = 10: 96 rows), between 32 and 256 in multiples of 16.
 __host__ __device__ inline int gram_tile_rows(int kxp, int kzp, bool sym) {
     const int cols = kxp + (sym ? 0 : kzp);
-    int tr = (1152 / cols) / 16 * 16;
-    return tr < 32 ? 32 : (tr > 256 ? 256 : tr);
+    int tr = (4608 / cols) / 16 * 16;
+    return tr < 32 ? 32 : (tr > 512 ? 512 : tr);
 }
 constexpr int QR_FLUSH = 8;     // tiles summed in double-float before they join the running sum
 
