@@ -1081,11 +1081,32 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     WS(tma_err, int*, "tma_error", sizeof(int));
     // column state of both passes under the stopping rule: live and final degree (b rounded up
     // to even), and the done flag
-    StopState stop1, stop2;
+    StopState stop1, stop2, stop2g;
+    // Under the rule, Hutch++'s trace pass runs as two passes, [Q] then [G']: the columns of Q
+    // (unit norm) stop long before those of G' (norm about sqrt n), and a pass costs its whole
+    // width until its last column stops
+    const bool split2 = adaptive && !hutch && kq > 0 && kq < n && kg > 0;
+    const int lg = block_ld(prec, kg);
     if (adaptive) {
-        WS(sst, int*, "fw_stop_state", (size_t)(2 * (kq + 2) + 2 * (b2 + 2) + 2) * sizeof(int));
-        stop1 = StopState{o.tol, sst, sst + (kq + 2), sst + 2 * (kq + 2) + 2 * (b2 + 2)};
-        stop2 = StopState{o.tol, sst + 2 * (kq + 2), sst + 2 * (kq + 2) + (b2 + 2), sst + 2 * (kq + 2) + 2 * (b2 + 2) + 1};
+        WS(sst, int*, "fw_stop_state", (size_t)(2 * (kq + 2) + 2 * (b2 + 2) + 2 * (kg + 2) + 3) * sizeof(int));
+        int* z = sst;
+        stop1 = StopState{o.tol, z, z + (kq + 2), nullptr};
+        z += 2 * (kq + 2);
+        stop2 = StopState{o.tol, z, z + (b2 + 2), nullptr};
+        z += 2 * (b2 + 2);
+        stop2g = StopState{o.tol, z, z + (kg + 2), nullptr};
+        z += 2 * (kg + 2);
+        stop1.done = z;
+        stop2.done = z + 1;
+        stop2g.done = z + 2;
+    }
+    void* Vq = nullptr;
+    void* Vg = nullptr;
+    if (split2) {
+        WS(vq_, void*, "fw_Vq", (size_t)n * l1 * ew);
+        WS(vg_, void*, "fw_Vg", (size_t)n * lg * ew);
+        Vq = vq_;
+        Vg = vg_;
     }
     int k1 = 0, t1 = 0;   // step kernel and CTA size of pass 1
 
@@ -1175,8 +1196,20 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         }
 
         // steps 5-6: traces t_j[col] = <V_col, W_j col> for j = 0..m
-        st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d, o.step_kernel,
-                      o.threads_per_block, o.rows_per_thread, q, stop2);
+        if (split2) {
+            // [Q] and [G'] as two blocks; their traces land in dots as (m+1) x kq, then (m+1) x kg
+            LL_CK(launch_copy_cols(wt, V, l2, 0, Vq, l1, n, kq, l1, q));
+            LL_CK(launch_copy_cols(wt, V, l2, kq, Vg, lg, n, kg, lg, q));
+            h->launches += 2;
+            st = run_pass(h, A, vprep, prec, MODE_DOT, n, kq, Vq, l1, wa, wb, nullptr, 0, dots, beta, d, o.step_kernel,
+                          o.threads_per_block, o.rows_per_thread, q, stop2);
+            if (st != LL_OK) return st;
+            st = run_pass(h, A, vprep, prec, MODE_DOT, n, kg, Vg, lg, wa, wb, nullptr, 0, dots + (size_t)(m + 1) * kq, beta,
+                          d, o.step_kernel, o.threads_per_block, o.rows_per_thread, q, stop2g);
+        } else {
+            st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d, o.step_kernel,
+                          o.threads_per_block, o.rows_per_thread, q, stop2);
+        }
         if (st != LL_OK) return st;
         LL_CK(rec(h->ev[4], q));
         return LL_OK;
@@ -1268,7 +1301,12 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if (adaptive) {
         if (kq > 0 && !hutch && kq < n)
             LL_CK(cudaMemcpyAsync(deg1.data(), stop1.stop_deg, kq * sizeof(int), cudaMemcpyDeviceToHost, s));
-        LL_CK(cudaMemcpyAsync(deg2.data(), stop2.stop_deg, b2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (split2) {
+            LL_CK(cudaMemcpyAsync(deg2.data(), stop2.stop_deg, kq * sizeof(int), cudaMemcpyDeviceToHost, s));
+            LL_CK(cudaMemcpyAsync(deg2.data() + kq, stop2g.stop_deg, kg * sizeof(int), cudaMemcpyDeviceToHost, s));
+        } else {
+            LL_CK(cudaMemcpyAsync(deg2.data(), stop2.stop_deg, b2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        }
     }
     LL_CK(cudaMemcpyAsync(&hstat, qrstat, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (h->tma_used) LL_CK(cudaMemcpyAsync(&herr, tma_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1277,6 +1315,14 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if (herr) return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out");
     if (hstat) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2: non-positive pivot (rank-deficient sketch)");
 
+    if (split2) {
+        // the two passes' traces, (m+1) x kq then (m+1) x kg, into the (m+1) x b2 layout
+        std::vector<double> two(hd);
+        for (int j = 0; j <= m; ++j) {
+            for (int col = 0; col < kq; ++col) hd[(size_t)j * b2 + col] = two[(size_t)j * kq + col];
+            for (int col = 0; col < kg; ++col) hd[(size_t)j * b2 + kq + col] = two[(size_t)(m + 1) * kq + (size_t)j * kg + col];
+        }
+    }
     // step 7 and output: n log sigma + tr(Q^T F Q) + (1/k) tr(G'^T F G'); under the stopping
     // rule, column col takes the terms j <= deg2[col] (the later dots are not its terms)
     double tq = 0.0, tr = 0.0;

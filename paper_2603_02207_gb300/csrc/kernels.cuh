@@ -109,6 +109,10 @@ cudaError_t launch_sddmm(int precision, const int32_t* rowidx, const int32_t* co
 cudaError_t launch_param_dot(const double* g, const double* dv, long long ldd, int64_t nnz, int np, double* partials,
                              unsigned int* ticket, double* out, int grid, cudaStream_t s);
 
+// out[r, c] = in[r, c0 + c], c < b, for blocks of W storage type t (the element's bits; both
+// parts of a double-float pair); columns [b, pad) of out set to zero
+cudaError_t launch_copy_cols(int t, const void* in, long long ld_in, int c0, void* out, long long ld_out, int n, int b,
+                             int pad, cudaStream_t s);
 // out (FP32, ld_out) <- hi + lo of a double-float column-pair block (ld_in), n x b; columns
 // [b, pad) of out are set to zero
 cudaError_t launch_dfp_to_f32(const void* in, long long ld_in, float* out, long long ld_out, int n, int b, int pad,

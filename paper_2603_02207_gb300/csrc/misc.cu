@@ -183,6 +183,47 @@ cudaError_t launch_block_to_f64(int precision, const void* in, long long ld_in, 
     return cudaGetLastError();
 }
 
+// out[r, c] = in[r, c0 + c] for c < b, raw (the element's bits, both parts of a double-float
+// pair); columns [b, pad) of out set to zero
+template <typename T>
+__global__ void k_copy_cols(const T* in, long long ld_in, int c0, T* out, long long ld_out, int n, int b, int pad) {
+    const long long total = (long long)n * pad;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / pad);
+        const int c = (int)(e - (long long)r * pad);
+        out[(size_t)r * ld_out + c] = c < b ? in[(size_t)r * ld_in + c0 + c] : T(0);
+    }
+}
+__global__ void k_copy_cols_dfp(const float* in, long long ld_in, int c0, float* out, long long ld_out, int n, int b, int pad) {
+    const long long total = (long long)n * pad;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / pad);
+        const int c = (int)(e - (long long)r * pad);
+        const size_t o = dfp_hi((size_t)r * ld_out + c);
+        if (c < b) {
+            const size_t i = dfp_hi((size_t)r * ld_in + c0 + c);
+            out[o] = in[i];
+            out[o + 2] = in[i + 2];
+        } else {
+            out[o] = 0.f;
+            out[o + 2] = 0.f;
+        }
+    }
+}
+
+cudaError_t launch_copy_cols(int t, const void* in, long long ld_in, int c0, void* out, long long ld_out, int n, int b,
+                             int pad, cudaStream_t s) {
+    if (pad < b) pad = b;
+    if ((long long)n * pad <= 0) return cudaSuccess;
+    const int grid = 152 * 8, threads = 256;
+    switch (t) {
+        case T_F64: k_copy_cols<double><<<grid, threads, 0, s>>>((const double*)in, ld_in, c0, (double*)out, ld_out, n, b, pad); break;
+        case T_F32: k_copy_cols<float><<<grid, threads, 0, s>>>((const float*)in, ld_in, c0, (float*)out, ld_out, n, b, pad); break;
+        default: k_copy_cols_dfp<<<grid, threads, 0, s>>>((const float*)in, ld_in, c0, (float*)out, ld_out, n, b, pad); break;
+    }
+    return cudaGetLastError();
+}
+
 // out[r, c] = hi + lo (FP32) of a double-float column-pair block, columns [b, pad) zero
 __global__ void k_dfp_to_f32(const dfp* in, long long ld_in, float* out, long long ld_out, int n, int b, int pad) {
     const long long total = (long long)n * pad;
