@@ -327,11 +327,12 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     // tiles above the mean by far are common
     const double slack = maxrow > 4.0 * avg + 16.0 ? 2.0 : 1.25;
     const size_t budget = (ctas_per_sm == 2 ? 112 : 224) * 1024 - 1024;
-    // Producer warps: two keep up with the consumers now that the per-step work is copies only.
-    // A producer waits for the release of tile i - nst only after the release of its previous
-    // wait target i - nprod - nst, so with nprod <= nst the stage's empty barrier is never more
-    // than one phase behind and the parity wait is unambiguous.
-    const int np_cap = TMA_MAX_PROD;
+    // Producer warps: two keep up with the double-float consumers; the FP32 consumers are fast
+    // enough that a third producer pays (Matérn 1024², FP32: forward 39.7 -> 35.3 ms; DF64 2%
+    // slower with three). A producer waits for the release of tile i - nst only after the release
+    // of its previous wait target i - nprod - nst, so with nprod <= nst the stage's empty barrier
+    // is never more than one phase behind and the parity wait is unambiguous.
+    const int np_cap = precision == LL_PREC_F32_MIXED ? TMA_MAX_PROD : 2;
     // layout for R rows per tile; returns the stage count that fits
     auto layout = [&](int Rt) {
         tma_stage_layout(q, Rt, avg, avgfar, slack);

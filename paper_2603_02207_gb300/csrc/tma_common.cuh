@@ -16,8 +16,8 @@
 namespace ll {
 
 constexpr int TMA_MAX_STAGES = 6;
-constexpr int TMA_MAX_THREADS = 576;   // up to 512 consumer threads and two producer warps
-constexpr int TMA_MAX_PROD = 2;
+constexpr int TMA_MAX_THREADS = 608;   // up to 512 consumer threads and three producer warps
+constexpr int TMA_MAX_PROD = 3;
 constexpr int TMA_GRING = 3;           // gather-column blocks staged up to two tiles ahead
 constexpr int TMA_MAX_WIN = 4;         // extra windows per tile (runs of far columns)
 
