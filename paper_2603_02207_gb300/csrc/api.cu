@@ -75,6 +75,7 @@ struct ll_handle {
     int kept_kq = 0, kept_kg = 0, kept_m = 0, kept_prec = 0, kept_ckpt = 0;
     bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
     bool kept_qr = false;     // the kept forward ran the sketch and its CholeskyQR2 (S, G, R1^-1, R2^-1 kept)
+    bool kept_band = false;   // the kept forward's matrix suits the banded kernel
     // final degree of every column of both passes of the last forward (Algorithm 2's rule)
     bool have_forward = false;
     std::vector<int> last_deg1, last_deg2;
@@ -671,6 +672,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
     WS(scratch, char*, "bw_tmp", 2 * blk);
     WS(FV, void*, "bw_FV", (size_t)n * l2 * ep);
+    h->band_ok = h->kept_band;   // the pass below runs on the kept forward's matrix (not revalidated)
     WS(FV64, double*, "bw_FV64", (size_t)n * b2 * sizeof(double));
     st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, b2, V, l2, scratch, scratch + blk, FV, l2, nullptr, beta, h->kept_d,
                   h->cfg_kernel, h->cfg_threads, h->cfg_rpt, s);
@@ -1379,6 +1381,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_kg = kg;
         h->kept_hutch = hutch;
         h->kept_qr = !hutch && kq < n;
+        h->kept_band = h->band_ok;
         h->kept_m = m;
         h->kept_prec = prec;
         h->kept_ckpt = o.ckpt_stride;

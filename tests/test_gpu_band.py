@@ -128,3 +128,22 @@ def test_band_not_taken_for_other_matrices(L, h):
     assert info["kernel_pass1"] != L.LL_KERNEL_BAND
     want = O.apply_poly(B, W, *O.gershgorin(B), 12)
     assert rel_err(got.cpu().numpy(), want) < 1e-10
+
+
+def test_backward_qr_uses_the_kept_matrix_band_choice(L, h):
+    """The through-QR adjoint's pass-1 sweep runs on the kept forward's matrix: a call on another
+    matrix in between (banded or not) must not change the kernel it takes."""
+    torch = need_gpu()
+    from synth import random_spd
+    for A, other in ((random_spd(600, seed=9), pentadiagonal(500, seed=1)), (pentadiagonal(700, seed=2), random_spd(400, seed=3))):
+        lo, hi = O.gershgorin(A)
+        lmin = max(lo, 0.05)
+        dA = L.DeviceCSR.from_host(A)
+        L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=15, probes=12, seed=4, keep_for_backward=True))
+        olo, ohi = O.gershgorin(other)
+        V = torch.as_tensor(np.random.default_rng(0).standard_normal((other.n, 3))).cuda()
+        L.ll_apply_poly(h, L.DeviceCSR.from_host(other), max(olo, 0.05), ohi, 5, V, "df64")
+        g = L.ll_logdet_backward(h, dA, 1.0, through_qr=True).cpu().numpy()
+        S, G = O.make_probes(A.n, 4, 4)
+        want = O.hutchpp_full_grad_values(A, lmin, hi, 15, S, G)
+        assert rel_err(g, want) < 1e-9
