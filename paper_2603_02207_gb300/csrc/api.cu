@@ -76,6 +76,8 @@ struct ll_handle {
     bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
     bool kept_qr = false;     // the kept forward ran the sketch and its CholeskyQR2 (S, G, R1^-1, R2^-1 kept)
     bool kept_band = false;   // the kept forward's matrix suits the banded kernel
+    int64_t kept_far = 0;     // its far-entry count and longest row (TMA plans of the adjoint)
+    int kept_max_row = 0;
     // final degree of every column of both passes of the last forward (Algorithm 2's rule)
     bool have_forward = false;
     std::vector<int> last_deg1, last_deg2;
@@ -636,6 +638,10 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     if (it_v == h->ws.end()) return fail(h, LL_ERR_NO_FORWARD, "kept basis missing");
     const void* V = it_v->second.p;
     const double sigma = h->kept_sigma, c = h->kept_c, gamma = h->kept_gamma;
+    // the step plans below describe the kept forward's matrix (it is not revalidated here)
+    h->band_ok = h->kept_band;
+    h->far_entries = h->kept_far;
+    h->max_row = h->kept_max_row;
     WS(vprep, void*, "bw_vals", (size_t)A->nnz * ew);
     LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
     h->launches++;
@@ -672,7 +678,6 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
     WS(scratch, char*, "bw_tmp", 2 * blk);
     WS(FV, void*, "bw_FV", (size_t)n * l2 * ep);
-    h->band_ok = h->kept_band;   // the pass below runs on the kept forward's matrix (not revalidated)
     WS(FV64, double*, "bw_FV64", (size_t)n * b2 * sizeof(double));
     st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, b2, V, l2, scratch, scratch + blk, FV, l2, nullptr, beta, h->kept_d,
                   h->cfg_kernel, h->cfg_threads, h->cfg_rpt, s);
@@ -1382,6 +1387,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_hutch = hutch;
         h->kept_qr = !hutch && kq < n;
         h->kept_band = h->band_ok;
+        h->kept_far = h->far_entries;
+        h->kept_max_row = h->max_row;
         h->kept_m = m;
         h->kept_prec = prec;
         h->kept_ckpt = o.ckpt_stride;
