@@ -6,14 +6,40 @@
 namespace ll {
 
 // ---------------------------------------------------------------------------- probes (Alg. 3)
+// A Rademacher value (+-1, or 0 in a pad column) stored without FP64 arithmetic: exact in every
+// storage type, the double-float pair being (+-1, 0). Gaussian values go through store_f64.
+__device__ __forceinline__ void store_sign(double* p, size_t i, float v) { p[i] = (double)v; }
+__device__ __forceinline__ void store_sign(float* p, size_t i, float v) { p[i] = v; }
+__device__ __forceinline__ void store_sign(dfp* p, size_t i, float v) {
+    float* f = reinterpret_cast<float*>(p) + dfp_hi(i);
+    f[0] = v;
+    f[2] = 0.f;
+}
+
+// Narrow blocks (pad <= blockDim): thread t owns column t % pad of rows t / pad + k * (blockDim /
+// pad) of the CTA's share. Wide blocks: a CTA takes one row at a time, its threads striding over
+// the columns. 32-bit index arithmetic per element.
 template <typename T>
 __global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols, int pad, T* out, long long ld) {
-    const long long total = (long long)n * pad;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int row = (int)(e / pad);
-        const int col = (int)(e - (long long)row * pad);
-        const double v = col < cols ? probe_value(kind, seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row) : 0.0;
-        store_f64<T>(out, (size_t)row * ld + col, v);
+    const int nt = (int)blockDim.x;
+    const bool narrow = pad <= nt;
+    const int rpb = narrow ? nt / pad : 1;                 // rows per CTA pass
+    const int roff = narrow ? (int)threadIdx.x / pad : 0;
+    const int col0 = (int)threadIdx.x - roff * (narrow ? pad : 0);
+    const int cstep = narrow ? pad : nt;
+    if (roff >= rpb) return;
+    for (int row = blockIdx.x * rpb + roff; row < n; row += gridDim.x * rpb) {
+        for (int col = col0; col < pad; col += cstep) {
+            const size_t idx = (size_t)row * ld + col;
+            if (kind == LL_PROBE_RADEMACHER) {
+                const float v = col < cols ? ((probe_bits(seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row) >> 63) ? -1.f : 1.f)
+                                           : 0.f;
+                store_sign(out, idx, v);
+            } else {
+                const double v = col < cols ? probe_value(kind, seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row) : 0.0;
+                store_f64<T>(out, idx, v);
+            }
+        }
     }
 }
 
@@ -23,7 +49,8 @@ cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, 
     const long long total = (long long)n * pad;
     if (total <= 0) return cudaSuccess;
     const int threads = 256;
-    long long blocks = (total + threads - 1) / threads;
+    const int rpb = pad <= threads ? threads / pad : 1;
+    long long blocks = ((long long)n + rpb - 1) / rpb;
     if (blocks > 152 * 16) blocks = 152 * 16;
     switch (out_type) {
         case T_F64: k_probes<double><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (double*)out, ld); break;
