@@ -250,14 +250,22 @@ def workload_config3(L, h, grid: int = 1024, degree: int = 80):
         ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), 2, 2)
         inf = h.info()
         ms_b, g = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 2, 1)
+        kept_w = inf["kept_w_steps"]
         th = L.ll_param_grad(h, g, dv)
         del g
         # the exact derivative of the estimate (through the sketch's QR)
         ms_bq, gq = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0, through_qr=True), 1, 1)
         thq = L.ll_param_grad(h, gq, dv)
         del gq
+        # the same backward with W_j recomputed from ceil(sqrt(m)) checkpoints instead of kept
+        ck = L.options(degree=degree, probes=60, seed=0, precision=prec, probe_kind="gaussian", keep_for_backward=True,
+                       ckpt_stride=int(np.ceil(np.sqrt(degree))))
+        L.ll_logdet_forward(h, dA, lmin, lmax, ck)
+        ms_bc, gc = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 2, 1)
+        del gc
         out[prec] = {"ms_forward": ms_f, "ms_backward": ms_b, "ms_forward_plus_gradient": ms_f + ms_b,
-                     "ms_backward_through_qr": ms_bq,
+                     "ms_backward_through_qr": ms_bq, "backward_kept_w_steps": kept_w,
+                     "ms_backward_checkpointed": ms_bc,
                      "estimate": est, "rel_err_vs_exact": abs(est - exact) / abs(exact),
                      "dlogdet_dkappa": th[0], "dlogdet_dtau": th[1],
                      "rel_err_dkappa": abs(th[0] - ex_k) / abs(ex_k), "rel_err_dtau": abs(th[1] - ex_t) / abs(ex_t),

@@ -120,7 +120,11 @@ typedef struct {
     int threads_per_block;     /* CTA size of the step kernel (0 = kernel default: 384 or 512
                                   for LL_KERNEL_GATHER, 512 for LL_KERNEL_TMA; a TMA CTA of at
                                   most 256 threads runs two per SM). Ignored by LL_KERNEL_AUTO.  */
-    int ckpt_stride;           /* backward: W_j checkpoint stride; 0 = ceil(sqrt(m))            */
+    int ckpt_stride;           /* backward: 0 (default) = the forward's trace pass keeps W_1 ..
+                                  W_{m-1} for the backward when they take at most half of the
+                                  free device memory, else checkpoints every ceil(sqrt(m))
+                                  steps; > 0 = checkpoints every ckpt_stride steps, the W_j
+                                  between them recomputed by the backward                       */
     int use_graph;             /* 1: capture the m-step passes in a CUDA graph (default 1)       */
     int64_t timeout_cycles;    /* batched launch: clock cycles a dependency wait may spin before
                                   the call fails with LL_ERR_TIMEOUT; 0 = about 2 s. Also bounds
@@ -150,6 +154,8 @@ typedef struct {
     int deg_max_pass1, deg_max_pass2;   /* largest final degree over the columns of each pass
                                            (the degree itself under a fixed degree)              */
     double deg_mean_pass2;              /* mean final degree over the trace pass's columns        */
+    int kept_w_steps;                   /* W_j blocks the trace pass kept for the backward (m - 1,
+                                           or 0 when the backward recomputes them)               */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */
@@ -286,7 +292,8 @@ ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* A_host, ll_bounds b
  *   grad_values[e] += grad_output * (1/gamma) sum_{j<m} Lambda_{j+1}[r_e, :] . W_j[c_e, :],
  *   Lambda_m = d_m U, Lambda_j = d_j U + (B - xi_j I)^T Lambda_{j+1}, U = [Q | G'/k].
  * A must be symmetric (B^T = B is used) and the same matrix (pattern and values) as in the
- * forward. W_j are checkpointed every ckpt_stride steps and recomputed.
+ * forward. The W_j come from the forward's trace pass when it kept them (ll_info.kept_w_steps),
+ * else from checkpoints every ckpt_stride steps, recomputed.
  * grad_values: device, nnz doubles, overwritten. Enqueue only. */
 ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream);
 

@@ -76,6 +76,7 @@ struct ll_handle {
     bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
     bool kept_qr = false;     // the kept forward ran the sketch and its CholeskyQR2 (S, G, R1^-1, R2^-1 kept)
     bool kept_band = false;   // the kept forward's matrix suits the banded kernel
+    bool kept_wall = false;   // the kept forward's trace pass left W_1 .. W_{m-1} in "bw_ckpt"
     int64_t kept_far = 0;     // its far-entry count and longest row (TMA plans of the adjoint)
     int kept_max_row = 0;
     // final degree of every column of both passes of the last forward (Algorithm 2's rule)
@@ -115,6 +116,15 @@ void* ws_get(ll_handle* h, const char* name, size_t bytes, cudaError_t* err) {
     }
     b.bytes = bytes;
     return b.p;
+}
+
+// Frees a workspace block (if any); the next ws_get of the name allocates afresh.
+void ws_release(ll_handle* h, const char* name) {
+    auto it = h->ws.find(name);
+    if (it == h->ws.end()) return;
+    if (it->second.p) cudaFree(it->second.p);
+    h->ws.erase(it);
+    h->ws_gen++;
 }
 
 #define WS(ptr, type, name, bytes)                                                               \
@@ -411,10 +421,15 @@ ll_status run_band_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, in
 ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int precision, int mode, int n, int b,
                    const void* win0, long long ldw, void* wa, void* wb, void* P, long long ldp, double* dots,
                    const std::vector<double>& beta, const std::vector<double>& d, int kernel, int threads_target,
-                   int rpt, cudaStream_t s, const StopState& stop = StopState{}) {
+                   int rpt, cudaStream_t s, const StopState& stop = StopState{}, void* store = nullptr) {
     const int m = (int)d.size() - 1;
-    // banded matrices: several steps per launch (the stopping rule runs on the one-step kernels)
-    if (stop.tol <= 0.0 && (mode == MODE_ACCUM || mode == MODE_DOT) && h->band_ok && m > 0 &&
+    // with store, W_1 .. W_{m-1} are written to consecutive n x ldw blocks there instead of the
+    // ping-pong pair (W_m, needed only for its trace, still goes to wa)
+    const size_t sblk = (size_t)n * ldw * elem_size(w_type_of(precision));
+    char* const sb = static_cast<char*>(store);
+    // banded matrices: several steps per launch (the stopping rule runs on the one-step kernels;
+    // a stored pass needs every W_j in memory)
+    if (stop.tol <= 0.0 && !store && (mode == MODE_ACCUM || mode == MODE_DOT) && h->band_ok && m > 0 &&
         (kernel == LL_KERNEL_AUTO || kernel == LL_KERNEL_BAND)) {
         BandLaunch BL;
         if (plan_band(precision, mode, n, b, h->sm_count, BL))
@@ -480,8 +495,13 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     h->last_kernel = E.kind;
     h->last_threads = E.cta();
     for (int j = 0; j < m; ++j) {
-        p.win = (j == 0) ? win0 : ((j & 1) ? wa : wb);
-        p.wout = (j & 1) ? wb : wa;
+        if (sb) {
+            p.win = (j == 0) ? win0 : (const void*)(sb + (size_t)(j - 1) * sblk);
+            p.wout = (j + 1 < m) ? (void*)(sb + (size_t)j * sblk) : wa;
+        } else {
+            p.win = (j == 0) ? win0 : ((j & 1) ? wa : wb);
+            p.wout = (j & 1) ? wb : wa;
+        }
         p.first = (j == 0);
         p.beta = beta[j];
         p.d0 = d[0];
@@ -502,12 +522,14 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
 // Adds grad_output * d/da_e sum_j d_j <U_w, W_j> to grad_values for the kept forward's coefficients,
 // with W_0 = W0 and U_w = coef(col) U (coef = cq for col < split, 1 / gdiv otherwise); W0 and U are
 // n x b blocks of the W storage type with leading dimension l. Reverse recurrence of the adjoint,
-// Lambda_m = d_m U_w, Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U_w (B symmetric), with the W_j
-// recomputed from sqrt(m)-spaced checkpoints; vprep holds the values prepared for B, rowidx the
-// row of every stored entry.
+// Lambda_m = d_m U_w, Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U_w (B symmetric); vprep holds the
+// values prepared for B, rowidx the row of every stored entry. The W_j come from the workspace
+// block ckpt_name: with stored, it already holds W_1 .. W_{m-1} (the forward's trace pass wrote
+// them) and no forward step runs here; otherwise they are recomputed from checkpoints kept there
+// every ckpt_stride (default ceil(sqrt(m))) steps.
 ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, const int32_t* rowidx, const void* W0,
                              const void* U, long long l, int b, int split, double cq, double gdiv, double grad_output,
-                             double* grad_values, cudaStream_t s) {
+                             double* grad_values, cudaStream_t s, const char* ckpt_name, bool stored) {
     const int n = (int)A->n;
     const int prec = h->kept_prec, m = h->kept_m;
     const int wt = w_type_of(prec);
@@ -517,12 +539,18 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
     std::vector<double> beta(m + 1);
     for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
     // checkpoints W_{k s} (k >= 1) and a segment buffer for W_{j0+1} .. W_{j1-1}
-    const int sck = h->kept_ckpt > 0 ? h->kept_ckpt : (int)std::ceil(std::sqrt((double)m));
+    const int sck = stored ? 1 : h->kept_ckpt > 0 ? h->kept_ckpt : (int)std::ceil(std::sqrt((double)m));
     const int nseg = (m + sck - 1) / sck;
-    WS(ckpt, char*, "bw_ckpt", blk * (size_t)(nseg > 1 ? nseg - 1 : 1));
-    WS(seg, char*, "bw_seg", blk * (size_t)(sck > 1 ? sck - 1 : 1));
+    WS(ckpt, char*, ckpt_name, blk * (size_t)(nseg > 1 ? nseg - 1 : 1));
     WS(lam, char*, "bw_lam", 2 * blk);
-    WS(tmp, char*, "bw_tmp", 2 * blk);
+    char* seg = nullptr;
+    char* tmp = nullptr;
+    if (!stored) {
+        WS(seg_, char*, "bw_seg", blk * (size_t)(sck > 1 ? sck - 1 : 1));
+        WS(tmp_, char*, "bw_tmp", 2 * blk);
+        seg = seg_;
+        tmp = tmp_;
+    }
 
     StepParams pp{};
     pp.rowptr = A->rowptr;
@@ -553,7 +581,8 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
     pa.adj_q_df = df_split(d[0] * cq);
     pa.adj_g_df = df_split(d[0] / gdiv);
     StepExec Ep, Ea;
-    ll_status cs = choose_exec(h, prec, MODE_PLAIN, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pp, Ep, s);
+    ll_status cs = LL_OK;
+    if (!stored) cs = choose_exec(h, prec, MODE_PLAIN, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pp, Ep, s);
     if (cs != LL_OK) return cs;
     cs = choose_exec(h, prec, MODE_ADJ, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pa, Ea, s);
     if (cs != LL_OK) return cs;
@@ -564,9 +593,9 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
         pp.beta_df = df_split(beta[j]);
         return exec_step(h, prec, MODE_PLAIN, Ep, pp, s);
     };
-    // phase A: W_1 .. W_{(nseg-1) sck}, keeping W_{k sck} in the checkpoint slots
+    // phase A: W_1 .. W_{(nseg-1) sck}, keeping W_{k sck} in the checkpoint slots (stored: there)
     const void* cur = W0;
-    for (int j = 0; j < (nseg - 1) * sck; ++j) {
+    for (int j = 0; !stored && j < (nseg - 1) * sck; ++j) {
         void* out = ((j + 1) % sck == 0) ? (void*)(ckpt + (size_t)((j + 1) / sck - 1) * blk)
                                          : (void*)(tmp + (cur == tmp ? blk : 0));
         LL_CK(plain_step(j, cur, out));
@@ -650,7 +679,8 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     LL_CK(launch_row_index(A->rowptr, n, rowidx, s));
     h->launches++;
     // frozen basis: W_0 = [Q | G'], U = [Q | G' / k]
-    st = adjoint_accumulate(h, A, vprep, rowidx, V, V, l2, b2, kq, 1.0, (double)kg, grad_output, grad_values, s);
+    st = adjoint_accumulate(h, A, vprep, rowidx, V, V, l2, b2, kq, 1.0, (double)kg, grad_output, grad_values, s,
+                            "bw_ckpt", h->kept_wall);
     if (st != LL_OK || !through_qr || !h->kept_qr) return st;
 
     // ---- through the QR: F [Q | G'] by the pass-1 arithmetic on the kept block
@@ -728,7 +758,9 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     LL_CK(cudaStreamSynchronize(s));   // the host copy of mt stays alive until the upload is done
 
     // ---- the QR term: W_0 = S, U = Gamma
-    return adjoint_accumulate(h, A, vprep, rowidx, S, gam, l1, kq, kq, 1.0, 1.0, grad_output, grad_values, s);
+    // the kept W_j of the trace pass stay for the next backward: these checkpoints go elsewhere
+    return adjoint_accumulate(h, A, vprep, rowidx, S, gam, l1, kq, kq, 1.0, 1.0, grad_output, grad_values, s,
+                              h->kept_wall ? "bw_ckpt_s" : "bw_ckpt", false);
 }
 
 
@@ -1115,6 +1147,31 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         Vq = vq_;
         Vg = vg_;
     }
+    // The backward needs W_0 .. W_{m-1} of the trace pass. With GB300's HBM they usually fit: the
+    // trace pass then writes W_1 .. W_{m-1} into the backward's checkpoint block, and the adjoint
+    // runs no forward steps. Taken when they need at most half of the free device memory
+    // (counting the backward blocks that this makes unnecessary), and not under an explicit
+    // checkpoint stride; the recompute buffers of an earlier backward are then released.
+    void* wall = nullptr;
+    if (o.keep_for_backward && o.ckpt_stride == 0 && m >= 2 && !split2) {
+        const size_t need = (size_t)(m - 1) * n * l2 * ew;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        size_t have = 0;
+        for (const char* nm : {"bw_ckpt", "bw_seg", "bw_tmp"}) {
+            auto it = h->ws.find(nm);
+            if (it != h->ws.end()) have += it->second.bytes;
+        }
+        if ((double)need <= 0.5 * (double)(fr + have)) {
+            ws_release(h, "bw_seg");
+            ws_release(h, "bw_tmp");
+            WS(wall_, void*, "bw_ckpt", need);
+            wall = wall_;
+        }
+    }
     int k1 = 0, t1 = 0;   // step kernel and CTA size of pass 1
 
     // the device work of the call (Algorithm 3 steps 2-6), enqueued on q; with capture, the
@@ -1215,7 +1272,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
                           d, o.step_kernel, o.threads_per_block, o.rows_per_thread, q, stop2g);
         } else {
             st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d, o.step_kernel,
-                          o.threads_per_block, o.rows_per_thread, q, stop2);
+                          o.threads_per_block, o.rows_per_thread, q, stop2, wall);
         }
         if (st != LL_OK) return st;
         LL_CK(rec(h->ev[4], q));
@@ -1238,7 +1295,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     key.n = A->n; key.nnz = A->nnz; key.dtype = A->dtype;
     key.lmin = bounds.lmin; key.lmax = bounds.lmax;
     key.o = o;
-    key.o.keep_for_backward = 0;
+    key.o.keep_for_backward = wall ? 1 : 0;   // the trace pass writes into the backward's block
     key.ws_gen = h->ws_gen;
     key.inject = h->inject;
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
@@ -1374,6 +1431,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         dsum += v;
     }
     I.deg_mean_pass2 = b2 > 0 ? dsum / b2 : 0.0;
+    I.kept_w_steps = wall ? m - 1 : 0;
     h->last_deg1 = deg1;
     h->last_deg2 = deg2;
     h->have_forward = true;
@@ -1387,6 +1445,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_hutch = hutch;
         h->kept_qr = !hutch && kq < n;
         h->kept_band = h->band_ok;
+        h->kept_wall = wall != nullptr;
         h->kept_far = h->far_entries;
         h->kept_max_row = h->max_row;
         h->kept_m = m;

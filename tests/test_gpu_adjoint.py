@@ -206,3 +206,49 @@ def test_autograd_through_qr(L, h):
     S, G = O.make_probes(A.n, 5, 2)
     want = O.hutchpp_full_grad_values(A, lmin, hi, 25, S, G)
     assert rel_err(vals.grad.cpu().numpy(), want) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+def test_backward_from_kept_w_equals_recomputed(L, h, prec):
+    """By default the trace pass keeps W_1 .. W_{m-1} for the backward (ll_info.kept_w_steps =
+    m - 1); under an explicit checkpoint stride the backward recomputes them. The W_j are the
+    same numbers either way, so the two gradients are identical, and a through-QR backward in
+    between (its own checkpoints) leaves the kept ones intact."""
+    A = random_spd(900, nnz_per_row=6, seed=11, empty_rows=2)
+    lo, hi = O.gershgorin(A)
+    lmin = max(lo, 0.05)
+    m = 17
+    dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+    grads = {}
+    for ckpt in (0, 4):
+        L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=m, probes=21, seed=5, precision=prec,
+                                                        keep_for_backward=True, ckpt_stride=ckpt))
+        assert h.info()["kept_w_steps"] == (m - 1 if ckpt == 0 else 0)
+        g = L.ll_logdet_backward(h, dA, 1.0)
+        gq = L.ll_logdet_backward(h, dA, 1.0, through_qr=True)
+        assert L.ll_logdet_backward(h, dA, 1.0).equal(g)
+        grads[ckpt] = (g, gq)
+    assert grads[0][0].equal(grads[4][0])
+    assert grads[0][1].equal(grads[4][1])
+    ref = O.logdet_leja(A, lmin, hi, m, 21, 5)
+    want = O.hutchpp_grad_values(A, lmin, hi, m, ref["Q"], ref["Gp"])
+    assert rel_err(grads[0][0].cpu().numpy(), want) < (1e-9 if prec != "f32" else 1e-4)
+
+
+def test_backward_from_kept_w_on_a_banded_matrix(L, h):
+    """A banded matrix: when its trace pass keeps the W_j it runs on the one-step kernels (the
+    multi-step kernel keeps only every fourth W_j in memory); pass 1 stays banded. Same gradient
+    as the checkpointed backward after a banded trace pass."""
+    from synth import pentadiagonal
+    A = pentadiagonal(1500, seed=3)
+    lo, hi = O.gershgorin(A)
+    dA = L.DeviceCSR.from_host(A)
+    out = {}
+    for ckpt in (0, 3):
+        L.ll_logdet_forward(h, dA, lo, hi, L.options(degree=11, probes=15, seed=2, keep_for_backward=True,
+                                                      ckpt_stride=ckpt))
+        info = h.info()
+        assert info["kernel_pass1"] == L.LL_KERNEL_BAND
+        assert (info["kernel_pass2"] == L.LL_KERNEL_BAND) == (ckpt != 0)
+        out[ckpt] = L.ll_logdet_backward(h, dA, 1.0)
+    assert out[0].equal(out[3])
