@@ -47,7 +47,7 @@ ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A,
 # Traffic grows in proportion to the rows of a stencil matrix, so the full-size value is this figure
 # times n. Only valid for the DF64 trace step of the kernel as captured.
 TRACE_STEP_DRAM_BYTES_PER_ROW = {("gather", "df64"): 1.477654528e9 / 884736,
-                                 ("tma", "df64"): (1.052302e9 + 0.441876736e9) / 884736}
+                                 ("tma", "df64"): (1.052284e9 + 0.443141376e9) / 884736}
 
 
 def step_bytes(n: int, nnz: int, b: int, prec: str, mode: str) -> int:
