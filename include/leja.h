@@ -74,6 +74,12 @@ enum { LL_EST_HUTCHPP = 0, LL_EST_HUTCHINSON = 1 };
 
 /* s_val of Algorithm 1: the Lemma 3.1 optimum c = (lmin+lmax)/2, or lmax/2. */
 enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
+/* How the Newton coefficients d_j are computed (ll_options.dd_scheme):
+ *   LL_DD_AUTO     Algorithm 1 (Section 3.1), or the FP64 divided-difference table in the xi
+ *                  variable (Eq. Léja7) when the series would need more than 1e6 terms;
+ *   LL_DD_TABLE_Q  the divided-difference table in the xi variable in binary128 arithmetic on the
+ *                  host (a second scheme for very large condition numbers), rounded to FP64. */
+enum { LL_DD_AUTO = 0, LL_DD_TABLE_Q = 1 };
 
 /* Step kernel of the m-step passes:
  *   LL_KERNEL_AUTO    banded matrices (every row's columns strictly increasing and within 2 of
@@ -136,6 +142,7 @@ typedef struct {
                                   with |d_m| ||w_m||_2 <= tol (w_m the Newton basis vector of
                                   the scaled operator), degree being the cap. Not with
                                   keep_for_backward nor ll_logdet_batched (LL_ERR_UNSUPPORTED).  */
+    int dd_scheme;             /* LL_DD_AUTO (default) or LL_DD_TABLE_Q                          */
 } ll_options;
 
 typedef struct ll_handle ll_handle;
@@ -204,6 +211,15 @@ ll_status ll_leja_points(int count, double* xi_out);
  * within 5e6 terms gives LL_ERR_DD_NOT_CONVERGED.
  * d_out: host, degree+1 doubles. terms_out: host, may be NULL. */
 ll_status ll_divided_differences(ll_bounds bounds, int degree, int sval_mode, double* d_out, int* terms_out);
+
+/* The same d_j (j = 0..degree) by the textbook divided-difference table of log(c + gamma xi)
+ * over the Léja points xi_j (Eq. Léja7) carried out in binary128 arithmetic on the host and
+ * rounded to FP64 (LL_DD_TABLE_Q). Every node and difference is exact or rounded at 113 bits, so
+ * the table's cancellation leaves the FP64 coefficients accurate at any degree <= 100000 and any
+ * condition number. c and gamma are the FP64 values (lmin+lmax)/2 and (lmax-lmin)/4.
+ * d_out: host, degree+1 doubles. Errors: LL_ERR_INVALID_ARG, LL_ERR_BAD_BOUNDS (lmin <= 0,
+ * lmin >= lmax, non-finite), LL_ERR_UNSUPPORTED (degree > 100000). */
+ll_status ll_divided_differences_q(ll_bounds bounds, int degree, double* d_out);
 
 /* ---- device kernels exposed for parity checks ---------------------------------------------- */
 

@@ -22,6 +22,7 @@ LL_F64, LL_F32 = 0, 1
 LL_PREC_F64, LL_PREC_DF64, LL_PREC_F32_MIXED = 0, 1, 2
 LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
+LL_DD_AUTO, LL_DD_TABLE_Q = 0, 1
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
 LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA, LL_KERNEL_BAND = 0, 1, 2, 3
 LL_EST_HUTCHPP, LL_EST_HUTCHINSON = 0, 1
@@ -44,7 +45,7 @@ class ll_options(ctypes.Structure):
                 ("keep_for_backward", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int), ("estimator", ctypes.c_int),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("dd_scheme", ctypes.c_int)]
 
 
 class ll_info(ctypes.Structure):
@@ -76,6 +77,7 @@ SIGNATURES = {
     "ll_debug_inject": (_I, [_P, _I]),
     "ll_leja_points": (_I, [_I, _PD]),
     "ll_divided_differences": (_I, [ll_bounds, _I, _I, _PD, ctypes.POINTER(_I)]),
+    "ll_divided_differences_q": (_I, [ll_bounds, _I, _PD]),
     "ll_gershgorin": (_I, [_P, ctypes.POINTER(ll_csr), ctypes.POINTER(ll_bounds), _P]),
     "ll_power_lmax": (_I, [_P, ctypes.POINTER(ll_csr), _I, _U64, _PD, _P]),
     "ll_power_lmax_noalloc": (_I, [ctypes.POINTER(ll_csr), _I, _U64, _PD, _P]),

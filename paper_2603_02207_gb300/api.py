@@ -121,11 +121,14 @@ def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
     return s, (rp, ci, va)
 
 
+DD_SCHEMES = {"auto": _ffi.LL_DD_AUTO, "table_q": _ffi.LL_DD_TABLE_Q}
+
+
 def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str = "rademacher",
             precision: str = "df64", sval_mode: int = LL_SVAL_CENTER, keep_for_backward: bool = False,
             rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
             use_graph: bool = True, timeout_cycles: int = 0, step_kernel: str = "auto",
-            estimator: str = "hutchpp", tol: float = 0.0) -> _ffi.ll_options:
+            estimator: str = "hutchpp", tol: float = 0.0, dd_scheme: str = "auto") -> _ffi.ll_options:
     o = _ffi.ll_options()
     _ffi.load().ll_default_options(ctypes.byref(o))
     o.degree = degree
@@ -143,6 +146,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
     o.step_kernel = STEP_KERNELS[step_kernel]
     o.estimator = ESTIMATORS[estimator]
     o.tol = tol
+    o.dd_scheme = DD_SCHEMES[dd_scheme]
     return o
 
 
@@ -164,6 +168,16 @@ def ll_divided_differences(lmin: float, lmax: float, degree: int, sval_mode: int
     if st != 0:
         raise LejaError(st, "ll_divided_differences")
     return out, terms.value
+
+
+def ll_divided_differences_q(lmin: float, lmax: float, degree: int) -> np.ndarray:
+    """The Newton coefficients by the divided-difference table in binary128 on the host."""
+    out = np.zeros(degree + 1, dtype=np.float64)
+    st = _ffi.load().ll_divided_differences_q(_ffi.ll_bounds(lmin, lmax), degree,
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != 0:
+        raise LejaError(st, "ll_divided_differences_q")
+    return out
 
 
 # ---------------------------------------------------------------------------- device pieces

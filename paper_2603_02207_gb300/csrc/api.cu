@@ -67,7 +67,7 @@ struct ll_handle {
     int max_row = 0;          // longest row of the last validated matrix
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
-    int dd_degree = -1, dd_sval = -1, dd_terms = 0;
+    int dd_degree = -1, dd_sval = -1, dd_scheme = -1, dd_terms = 0;
     std::vector<double> dd;
     // kept forward state (for the backward)
     bool kept = false;
@@ -177,17 +177,29 @@ ll_status validate_csr(ll_handle* h, const ll_csr* A, cudaStream_t s) {
 }
 
 // Léja points and Algorithm 1 coefficients for [lmin, lmax] (cached on the handle).
+// d[0..degree] on the scaled interval [lmin, lmax] by the chosen scheme; the Taylor terms used
+// (0 for either table), -1 if Algorithm 1 did not converge.
+int coefficients_by_scheme(double lmin, double lmax, int degree, int sval, int scheme, double* d) {
+    if (scheme == LL_DD_TABLE_Q) {
+        divided_differences_table_q(lmin, lmax, degree, d);
+        return 0;
+    }
+    return scaled_divided_differences(lmin, lmax, degree, sval, d);
+}
+
 ll_status setup_coefficients(ll_handle* h, double lmin, double lmax, int degree, int sval, std::vector<double>& xi,
-                             std::vector<double>& d) {
+                             std::vector<double>& d, int scheme = LL_DD_AUTO) {
     xi.resize(degree + 1);
     leja_points(degree + 1, xi.data());
-    if (!(h->dd_degree == degree && h->dd_sval == sval && h->dd_lmin == lmin && h->dd_lmax == lmax)) {
+    if (!(h->dd_degree == degree && h->dd_sval == sval && h->dd_scheme == scheme && h->dd_lmin == lmin &&
+          h->dd_lmax == lmax)) {
         std::vector<double> dn(degree + 1);
-        const int terms = scaled_divided_differences(lmin, lmax, degree, sval, dn.data());
+        const int terms = coefficients_by_scheme(lmin, lmax, degree, sval, scheme, dn.data());
         if (terms < 0) return fail(h, LL_ERR_DD_NOT_CONVERGED, "Algorithm 1 Taylor series did not converge within 5e6 terms");
         h->dd = dn;
         h->dd_degree = degree;
         h->dd_sval = sval;
+        h->dd_scheme = scheme;
         h->dd_lmin = lmin;
         h->dd_lmax = lmax;
         h->dd_terms = terms;
@@ -832,6 +844,7 @@ void ll_default_options(ll_options* o) {
     o->probe_kind = LL_PROBE_RADEMACHER;
     o->precision = LL_PREC_DF64;
     o->sval_mode = LL_SVAL_CENTER;
+    o->dd_scheme = LL_DD_AUTO;
     o->keep_for_backward = 0;
     o->rows_per_thread = 0;
     o->threads_per_block = 0;
@@ -872,6 +885,14 @@ ll_status ll_divided_differences(ll_bounds b, int degree, int sval_mode, double*
     const int terms = scaled_divided_differences(b.lmin, b.lmax, degree, sval_mode, d_out);
     if (terms < 0) return LL_ERR_DD_NOT_CONVERGED;
     if (terms_out) *terms_out = terms;
+    return LL_OK;
+}
+
+ll_status ll_divided_differences_q(ll_bounds b, int degree, double* d_out) {
+    if (degree < 0 || !d_out) return LL_ERR_INVALID_ARG;
+    if (degree > 100000) return LL_ERR_UNSUPPORTED;
+    if (!std::isfinite(b.lmin) || !std::isfinite(b.lmax) || !(b.lmin > 0.0) || !(b.lmin < b.lmax)) return LL_ERR_BAD_BOUNDS;
+    divided_differences_table_q(b.lmin, b.lmax, degree, d_out);
     return LL_OK;
 }
 
@@ -1059,6 +1080,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
     if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
     if (o.sval_mode != LL_SVAL_CENTER && o.sval_mode != LL_SVAL_HALF_LMAX) return fail(h, LL_ERR_INVALID_ARG, "unknown s_val mode");
+    if (o.dd_scheme != LL_DD_AUTO && o.dd_scheme != LL_DD_TABLE_Q) return fail(h, LL_ERR_INVALID_ARG, "unknown divided-difference scheme");
     if (!std::isfinite(o.tol) || o.tol < 0.0) return fail(h, LL_ERR_INVALID_ARG, "tol must be finite and >= 0");
     const bool adaptive = o.tol > 0.0;   // Algorithm 2's stopping rule in both passes
     if (adaptive && o.keep_for_backward)
@@ -1084,7 +1106,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     const double sigma = sigma_of(bounds.lmin);
     const double lt = bounds.lmin / sigma, ut = bounds.lmax / sigma;
     std::vector<double> xi, d;
-    if ((st = setup_coefficients(h, lt, ut, o.degree, o.sval_mode, xi, d)) != LL_OK) return st;
+    if ((st = setup_coefficients(h, lt, ut, o.degree, o.sval_mode, xi, d, o.dd_scheme)) != LL_OK) return st;
     const double c = (lt + ut) / 2.0, gamma = (ut - lt) / 4.0;
     const int m = o.degree;
     std::vector<double> beta(m + 1);
@@ -1546,6 +1568,7 @@ std::vector<unsigned char> batched_key(const ll_handle* h, const ll_csr* mats, c
     put(&oo.probe_kind, sizeof oo.probe_kind);
     put(&oo.precision, sizeof oo.precision);
     put(&oo.sval_mode, sizeof oo.sval_mode);
+    put(&oo.dd_scheme, sizeof oo.dd_scheme);
     put(&oo.timeout_cycles, sizeof oo.timeout_cycles);
     put(&oo.step_kernel, sizeof oo.step_kernel);
     put(&h->ws_gen, sizeof h->ws_gen);
@@ -1666,7 +1689,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         x.c = (lt + ut) / 2.0;
         x.gamma = (ut - lt) / 4.0;
         x.d.resize(x.m + 1);
-        if (scaled_divided_differences(lt, ut, x.m, o.sval_mode, x.d.data()) < 0)
+        if (coefficients_by_scheme(lt, ut, x.m, o.sval_mode, o.dd_scheme, x.d.data()) < 0)
             return fail(h, LL_ERR_DD_NOT_CONVERGED, "Algorithm 1 did not converge for batch entry " + std::to_string(i));
         std::vector<double> xi(x.m + 1);
         leja_points(x.m + 1, xi.data());

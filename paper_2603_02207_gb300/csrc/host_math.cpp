@@ -131,6 +131,34 @@ void divided_differences_table(double lmin, double lmax, int degree, double* d) 
     }
 }
 
+// Binary128 (113-bit significand) on both hosts: long double on aarch64, _Float128 on x86-64;
+// the logarithm is glibc's binary128 one in both cases.
+#if defined(__aarch64__)
+static_assert(__LDBL_MANT_DIG__ == 113, "long double is not binary128 on this aarch64 target");
+typedef long double quad;
+static inline quad quad_log(quad x) { return logl(x); }
+#else
+typedef _Float128 quad;
+static inline quad quad_log(quad x) { return logf128(x); }
+#endif
+
+void divided_differences_table_q(double lmin, double lmax, int degree, double* d) {
+    const int m1 = degree + 1;
+    std::vector<double> xi(m1);
+    leja_points(m1, xi.data());
+    // c and gamma as the step recurrence uses them (FP64); the nodes c + gamma xi_i are exact in
+    // binary128 (a 53 x 53-bit product and one addition)
+    const double c = (lmin + lmax) / 2.0;
+    const double gamma = (lmax - lmin) / 4.0;
+    std::vector<quad> col(m1);
+    for (int i = 0; i < m1; ++i) col[i] = quad_log((quad)c + (quad)gamma * (quad)xi[i]);
+    d[0] = (double)col[0];
+    for (int o = 1; o < m1; ++o) {
+        for (int i = 0; i + o < m1; ++i) col[i] = (col[i + 1] - col[i]) / ((quad)xi[i + o] - (quad)xi[i]);
+        d[o] = (double)col[0];
+    }
+}
+
 int scaled_divided_differences(double lmin, double lmax, int degree, int sval_mode, double* d) {
     const int m1 = degree + 1;
     std::vector<double> xi(m1);

@@ -17,6 +17,9 @@ void leja_points(int count, double* out);
 int divided_differences_alg1(double lmin, double lmax, int degree, int sval_mode, double* d, int max_terms);
 // The xi-variable divided-difference table of log(c + gamma xi) (Eq. Léja7): d[0..degree].
 void divided_differences_table(double lmin, double lmax, int degree, double* d);
+// The same table in binary128 arithmetic, rounded to FP64 at the end: the table's cancellation
+// costs no digit of the FP64 coefficients at the degrees and conditionings the library takes.
+void divided_differences_table_q(double lmin, double lmax, int degree, double* d);
 // Algorithm 1 when its series would converge within kTableThresholdTerms terms, else the table.
 // Returns the Taylor terms used (0 = table), -1 if Algorithm 1 did not converge.
 int scaled_divided_differences(double lmin, double lmax, int degree, int sval_mode, double* d);

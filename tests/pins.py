@@ -17,13 +17,17 @@ import numpy as np
 from scipy.interpolate import BarycentricInterpolator
 
 
-def hp_scaled_divided_differences(lmin: float, lmax: float, xi, prec: int = 120) -> np.ndarray:
+def hp_scaled_divided_differences(lmin: float, lmax: float, xi, prec: int = 120, c_g=None) -> np.ndarray:
     """gamma^j * log[z_0, ..., z_j] with z_i = c + gamma xi_i, c = (lmin+lmax)/2,
-    gamma = (lmax-lmin)/4, by the standard divided-difference table in `prec` digits."""
+    gamma = (lmax-lmin)/4, by the standard divided-difference table in `prec` digits. c_g = (c,
+    gamma) given as floats puts the nodes where an implementation that rounds c and gamma to
+    FP64 puts them."""
     getcontext().prec = prec
     lo, hi = Decimal(lmin), Decimal(lmax)
     c = (lo + hi) / 2
     g = (hi - lo) / 4
+    if c_g is not None:
+        c, g = Decimal(c_g[0]), Decimal(c_g[1])
     z = [c + g * Decimal(float(x)) for x in xi]
     m1 = len(z)
     col = [zi.ln() for zi in z]            # f[z_i]

@@ -74,3 +74,29 @@ def test_host_entry_points_reject_bad_arguments(libpath):
     # a condition number of 1e7 switches to the divided-difference table (0 Taylor terms)
     d, terms = L.ll_divided_differences(1.0, 1e7, 60)
     assert terms == 0 and np.all(np.isfinite(d))
+
+
+@pytest.mark.parametrize("lmin,lmax,m", [(1.0, 81.0, 39), (1.0, 8080.0, 80), (1.0, 2.5e6, 150), (1.0, 1e9, 250),
+                                          (0.01, 3e4, 150), (1.0, 1e12, 250), (0.37, 2.9, 7)])
+def test_host_binary128_table_is_the_rounded_exact_coefficients(libpath, lmin, lmax, m):
+    """LL_DD_TABLE_Q: every d_j is within rounding of the 120-digit table at the library's own
+    nodes c + gamma xi_i (c, gamma in FP64), at any conditioning; Algorithm 1's long series
+    (kappa = 8080: 117,022 terms) is 3.5e-14 off, the FP64 table up to 4e-12."""
+    from oracle.leja import fast_leja_points
+    import paper_2603_02207_gb300 as L
+    from tests import pins
+    d = L.ll_divided_differences_q(lmin, lmax, m)
+    ref = pins.hp_scaled_divided_differences(lmin, lmax, fast_leja_points(m + 1),
+                                             c_g=((lmin + lmax) / 2.0, (lmax - lmin) / 4.0))
+    assert np.max(np.abs(d - ref)) <= 2.5e-16 * np.max(np.abs(ref))
+
+
+def test_host_binary128_table_rejects_bad_arguments(libpath):
+    from paper_2603_02207_gb300 import _ffi
+    lib = _ffi.load()
+    out = np.zeros(4)
+    p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.ll_divided_differences_q(_ffi.ll_bounds(0.0, 1.0), 3, p) == 3
+    assert lib.ll_divided_differences_q(_ffi.ll_bounds(2.0, 1.0), 3, p) == 3
+    assert lib.ll_divided_differences_q(_ffi.ll_bounds(1.0, 2.0), -1, p) == 1
+    assert lib.ll_divided_differences_q(_ffi.ll_bounds(1.0, 2.0), 3, None) == 1
