@@ -250,7 +250,7 @@ def workload_config3(L, h, grid: int = 1024, degree: int = 80):
         ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), 2, 2)
         inf = h.info()
         ms_b, g = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 2, 1)
-        kept_w = inf["kept_w_steps"]
+        kept_w = (inf["kept_w_steps"], inf["kept_w_steps_pass1"])
         th = L.ll_param_grad(h, g, dv)
         del g
         # the exact derivative of the estimate (through the sketch's QR)

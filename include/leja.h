@@ -163,6 +163,8 @@ typedef struct {
     double deg_mean_pass2;              /* mean final degree over the trace pass's columns        */
     int kept_w_steps;                   /* W_j blocks the trace pass kept for the backward (m - 1,
                                            or 0 when the backward recomputes them)               */
+    int kept_w_steps_pass1;             /* the same for pass 1 (W_0 = S), used by the through-QR
+                                           adjoint; 0 for a banded matrix or when they do not fit */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */

@@ -56,7 +56,7 @@ class ll_info(ctypes.Structure):
                 ("ms_pass2", ctypes.c_float), ("ms_total", ctypes.c_float), ("kernel_pass1", ctypes.c_int),
                 ("kernel_pass2", ctypes.c_int), ("threads_pass1", ctypes.c_int), ("threads_pass2", ctypes.c_int),
                 ("deg_max_pass1", ctypes.c_int), ("deg_max_pass2", ctypes.c_int), ("deg_mean_pass2", ctypes.c_double),
-                ("kept_w_steps", ctypes.c_int)]
+                ("kept_w_steps", ctypes.c_int), ("kept_w_steps_pass1", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -77,6 +77,7 @@ struct ll_handle {
     bool kept_qr = false;     // the kept forward ran the sketch and its CholeskyQR2 (S, G, R1^-1, R2^-1 kept)
     bool kept_band = false;   // the kept forward's matrix suits the banded kernel
     bool kept_wall = false;   // the kept forward's trace pass left W_1 .. W_{m-1} in "bw_ckpt"
+    bool kept_wall_s = false; // and its pass 1 (W_0 = S) left them in "bw_ckpt_s"
     int64_t kept_far = 0;     // its far-entry count and longest row (TMA plans of the adjoint)
     int kept_max_row = 0;
     // final degree of every column of both passes of the last forward (Algorithm 2's rule)
@@ -770,9 +771,10 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     LL_CK(cudaStreamSynchronize(s));   // the host copy of mt stays alive until the upload is done
 
     // ---- the QR term: W_0 = S, U = Gamma
-    // the kept W_j of the trace pass stay for the next backward: these checkpoints go elsewhere
+    // pass 1's W_j as the forward kept them, or checkpoints in a block of their own, so that the
+    // trace pass's kept W_j stay valid for the next backward
     return adjoint_accumulate(h, A, vprep, rowidx, S, gam, l1, kq, kq, 1.0, 1.0, grad_output, grad_values, s,
-                              h->kept_wall ? "bw_ckpt_s" : "bw_ckpt", false);
+                              h->kept_wall ? "bw_ckpt_s" : "bw_ckpt", h->kept_wall_s);
 }
 
 
@@ -1174,16 +1176,21 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     // runs no forward steps. Taken when they need at most half of the free device memory
     // (counting the backward blocks that this makes unnecessary), and not under an explicit
     // checkpoint stride; the recompute buffers of an earlier backward are then released.
+    // Pass 1's W_j (W_0 = S), which the through-QR adjoint's second recurrence needs, are kept
+    // as well when both fit, except for a banded matrix, whose pass 1 keeps its multi-step kernel.
     void* wall = nullptr;
+    void* wall_s = nullptr;
     if (o.keep_for_backward && o.ckpt_stride == 0 && m >= 2 && !split2) {
         const size_t need = (size_t)(m - 1) * n * l2 * ew;
+        const bool sketch = !hutch && kq > 0 && kq < n && !h->band_ok;
+        const size_t need_s = sketch ? (size_t)(m - 1) * n * l1 * ew : 0;
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
             cudaGetLastError();
             fr = 0;
         }
         size_t have = 0;
-        for (const char* nm : {"bw_ckpt", "bw_seg", "bw_tmp"}) {
+        for (const char* nm : {"bw_ckpt", "bw_ckpt_s", "bw_seg", "bw_tmp"}) {
             auto it = h->ws.find(nm);
             if (it != h->ws.end()) have += it->second.bytes;
         }
@@ -1192,6 +1199,10 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             ws_release(h, "bw_tmp");
             WS(wall_, void*, "bw_ckpt", need);
             wall = wall_;
+            if (sketch && (double)(need + need_s) <= 0.5 * (double)(fr + have)) {
+                WS(wall_s_, void*, "bw_ckpt_s", need_s);
+                wall_s = wall_s_;
+            }
         }
     }
     int k1 = 0, t1 = 0;   // step kernel and CTA size of pass 1
@@ -1243,7 +1254,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         } else {
             // step 3: Y = p(A~) S
             st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, kq, S, l1, wa, wb, P, l1, nullptr, beta, d, o.step_kernel,
-                          o.threads_per_block, o.rows_per_thread, q, stop1);
+                          o.threads_per_block, o.rows_per_thread, q, stop1, wall_s);
             if (st != LL_OK) return st;
             k1 = h->last_kernel;
             t1 = h->last_threads;
@@ -1317,7 +1328,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     key.n = A->n; key.nnz = A->nnz; key.dtype = A->dtype;
     key.lmin = bounds.lmin; key.lmax = bounds.lmax;
     key.o = o;
-    key.o.keep_for_backward = wall ? 1 : 0;   // the trace pass writes into the backward's block
+    key.o.keep_for_backward = (wall ? 1 : 0) + (wall_s ? 2 : 0);   // the passes write into the backward's blocks
     key.ws_gen = h->ws_gen;
     key.inject = h->inject;
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
@@ -1454,6 +1465,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     }
     I.deg_mean_pass2 = b2 > 0 ? dsum / b2 : 0.0;
     I.kept_w_steps = wall ? m - 1 : 0;
+    I.kept_w_steps_pass1 = wall_s ? m - 1 : 0;
     h->last_deg1 = deg1;
     h->last_deg2 = deg2;
     h->have_forward = true;
@@ -1468,6 +1480,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_qr = !hutch && kq < n;
         h->kept_band = h->band_ok;
         h->kept_wall = wall != nullptr;
+        h->kept_wall_s = wall_s != nullptr;
         h->kept_far = h->far_entries;
         h->kept_max_row = h->max_row;
         h->kept_m = m;

@@ -210,8 +210,8 @@ def test_autograd_through_qr(L, h):
 
 @pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
 def test_backward_from_kept_w_equals_recomputed(L, h, prec):
-    """By default the trace pass keeps W_1 .. W_{m-1} for the backward (ll_info.kept_w_steps =
-    m - 1); under an explicit checkpoint stride the backward recomputes them. The W_j are the
+    """By default both passes keep W_1 .. W_{m-1} for the backward (ll_info.kept_w_steps and
+    kept_w_steps_pass1 = m - 1); under an explicit checkpoint stride the backward recomputes them. The W_j are the
     same numbers either way, so the two gradients are identical, and a through-QR backward in
     between (its own checkpoints) leaves the kept ones intact."""
     A = random_spd(900, nnz_per_row=6, seed=11, empty_rows=2)
@@ -223,7 +223,9 @@ def test_backward_from_kept_w_equals_recomputed(L, h, prec):
     for ckpt in (0, 4):
         L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=m, probes=21, seed=5, precision=prec,
                                                         keep_for_backward=True, ckpt_stride=ckpt))
-        assert h.info()["kept_w_steps"] == (m - 1 if ckpt == 0 else 0)
+        info = h.info()
+        assert info["kept_w_steps"] == (m - 1 if ckpt == 0 else 0)
+        assert info["kept_w_steps_pass1"] == (m - 1 if ckpt == 0 else 0)
         g = L.ll_logdet_backward(h, dA, 1.0)
         gq = L.ll_logdet_backward(h, dA, 1.0, through_qr=True)
         assert L.ll_logdet_backward(h, dA, 1.0).equal(g)
@@ -248,7 +250,7 @@ def test_backward_from_kept_w_on_a_banded_matrix(L, h):
         L.ll_logdet_forward(h, dA, lo, hi, L.options(degree=11, probes=15, seed=2, keep_for_backward=True,
                                                       ckpt_stride=ckpt))
         info = h.info()
-        assert info["kernel_pass1"] == L.LL_KERNEL_BAND
+        assert info["kernel_pass1"] == L.LL_KERNEL_BAND and info["kept_w_steps_pass1"] == 0
         assert (info["kernel_pass2"] == L.LL_KERNEL_BAND) == (ckpt != 0)
         out[ckpt] = L.ll_logdet_backward(h, dA, 1.0)
     assert out[0].equal(out[3])
