@@ -127,7 +127,7 @@ typedef struct {
                                   for LL_KERNEL_GATHER, 512 for LL_KERNEL_TMA; a TMA CTA of at
                                   most 256 threads runs two per SM). Ignored by LL_KERNEL_AUTO.  */
     int ckpt_stride;           /* backward: 0 (default) = the forward's trace pass keeps W_1 ..
-                                  W_{m-1} for the backward when they take at most half of the
+                                  W_m for the backward when they take at most half of the
                                   free device memory, else checkpoints every ceil(sqrt(m))
                                   steps; > 0 = checkpoints every ckpt_stride steps, the W_j
                                   between them recomputed by the backward                       */
@@ -161,8 +161,8 @@ typedef struct {
     int deg_max_pass1, deg_max_pass2;   /* largest final degree over the columns of each pass
                                            (the degree itself under a fixed degree)              */
     double deg_mean_pass2;              /* mean final degree over the trace pass's columns        */
-    int kept_w_steps;                   /* W_j blocks the trace pass kept for the backward (m - 1,
-                                           or 0 when the backward recomputes them)               */
+    int kept_w_steps;                   /* W_j blocks the trace pass kept for the backward (m:
+                                           W_1 .. W_m; 0 when the backward recomputes them)       */
     int kept_w_steps_pass1;             /* the same for pass 1 (W_0 = S), used by the through-QR
                                            adjoint; 0 for a banded matrix or when they do not fit */
 } ll_info;

@@ -4,6 +4,7 @@
 // chain to model parameters sum_e g_e da_e/dtheta_p.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "step_common.cuh"
 
 namespace ll {
 
@@ -114,6 +115,72 @@ cudaError_t launch_sddmm(int precision, const int32_t* rowidx, const int32_t* co
         case LL_PREC_F64: k_sddmm<LL_PREC_F64><<<(int)grid, threads, 0, s>>>(rowidx, colind, nnz, lam, w, ld, b, scale, g); break;
         case LL_PREC_DF64: k_sddmm<LL_PREC_DF64><<<(int)grid, threads, 0, s>>>(rowidx, colind, nnz, lam, w, ld, b, scale, g); break;
         default: k_sddmm<LL_PREC_F32_MIXED><<<(int)grid, threads, 0, s>>>(rowidx, colind, nnz, lam, w, ld, b, scale, g); break;
+    }
+    return cudaGetLastError();
+}
+
+// P = sum_{j=0..m} d_j W_j for the first npairs column pairs of W_0 (w0) and W_1 .. W_m
+// (consecutive n x ld blocks, blk bytes apart, from wk), by the P-axpy step epilogue's operations
+// in its order: d_0 W_0 and d_1 W_1 accumulated and renormalised, then one accumulation and one
+// renormalisation per further step. P therefore equals the P-axpy pass over the same W_j bit for
+// bit. d: FP64 coefficients, ddf: their double-float splits (device, m + 1 each).
+template <int PREC>
+__global__ void k_weighted_sum(const void* w0, const char* wk, size_t blk, long long ld, int n, int npairs, int m,
+                               const double* d, const float2* ddf, void* P, long long ldp) {
+    using WP = typename PairT<PREC>::W;
+    using PP = typename PairT<PREC>::P;
+    const long long ldq = ld >> 1, ldpq = ldp >> 1;
+    const long long total = (long long)n * npairs;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / npairs, q = e - r * npairs;
+        const size_t off = (size_t)r * ldq + q;
+        auto W = [&](int j) -> WP {
+            const WP* b = j == 0 ? static_cast<const WP*>(w0) : reinterpret_cast<const WP*>(wk + (size_t)(j - 1) * blk);
+            return b[off];
+        };
+        PP out;
+        if constexpr (PREC == LL_PREC_F64) {
+            const WP a = W(0), b = W(1);
+            double p0 = fma(d[1], b.x, d[0] * a.x), p1 = fma(d[1], b.y, d[0] * a.y);
+            for (int j = 2; j <= m; ++j) {
+                const WP w = W(j);
+                p0 = fma(d[j], w.x, p0);
+                p1 = fma(d[j], w.y, p1);
+            }
+            out = make_double2(p0, p1);
+        } else {
+            f2x ph = 0ull, pl = 0ull;
+            for (int j = 0; j <= m; ++j) {
+                const float2 c = ddf[j];
+                const f2x ch = f2_pack(c.x, c.x), cl = f2_pack(c.y, c.y), nch = f2_pack(-c.x, -c.x);
+                const WP w = W(j);
+                if constexpr (PREC == LL_PREC_DF64) df2_mac(ph, pl, ch, cl, nch, w.x, w.y);
+                else df2_mac_f(ph, pl, ch, cl, nch, w);
+                if (j >= 1) {   // the first step adds d_0 W_0 and d_1 W_1 before its renormalisation
+                    f2x oh, ol;
+                    df2_norm(ph, pl, oh, ol);
+                    ph = oh;
+                    pl = ol;
+                }
+            }
+            out = make_ulonglong2(ph, pl);
+        }
+        static_cast<PP*>(P)[(size_t)r * ldpq + q] = out;
+    }
+}
+
+cudaError_t launch_weighted_sum(int precision, const void* w0, const void* wk, size_t blk, long long ld, int n, int b,
+                                int m, const double* d, const float2* ddf, void* P, long long ldp, cudaStream_t s) {
+    if (n <= 0 || b <= 0 || m < 1) return cudaSuccess;
+    const int npairs = (b + 1) / 2;
+    const long long total = (long long)n * npairs;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 8) grid = 152 * 8;
+    const char* k = static_cast<const char*>(wk);
+    switch (precision) {
+        case LL_PREC_F64: k_weighted_sum<LL_PREC_F64><<<grid, 256, 0, s>>>(w0, k, blk, ld, n, npairs, m, d, ddf, P, ldp); break;
+        case LL_PREC_DF64: k_weighted_sum<LL_PREC_DF64><<<grid, 256, 0, s>>>(w0, k, blk, ld, n, npairs, m, d, ddf, P, ldp); break;
+        default: k_weighted_sum<LL_PREC_F32_MIXED><<<grid, 256, 0, s>>>(w0, k, blk, ld, n, npairs, m, d, ddf, P, ldp); break;
     }
     return cudaGetLastError();
 }

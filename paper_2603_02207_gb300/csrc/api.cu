@@ -76,7 +76,7 @@ struct ll_handle {
     bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
     bool kept_qr = false;     // the kept forward ran the sketch and its CholeskyQR2 (S, G, R1^-1, R2^-1 kept)
     bool kept_band = false;   // the kept forward's matrix suits the banded kernel
-    bool kept_wall = false;   // the kept forward's trace pass left W_1 .. W_{m-1} in "bw_ckpt"
+    bool kept_wall = false;   // the kept forward's trace pass left W_1 .. W_m in "bw_ckpt"
     bool kept_wall_s = false; // and its pass 1 (W_0 = S) left them in "bw_ckpt_s"
     int64_t kept_far = 0;     // its far-entry count and longest row (TMA plans of the adjoint)
     int kept_max_row = 0;
@@ -436,8 +436,8 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
                    const std::vector<double>& beta, const std::vector<double>& d, int kernel, int threads_target,
                    int rpt, cudaStream_t s, const StopState& stop = StopState{}, void* store = nullptr) {
     const int m = (int)d.size() - 1;
-    // with store, W_1 .. W_{m-1} are written to consecutive n x ldw blocks there instead of the
-    // ping-pong pair (W_m, needed only for its trace, still goes to wa)
+    // with store, W_1 .. W_m are written to m consecutive n x ldw blocks there instead of the
+    // ping-pong pair
     const size_t sblk = (size_t)n * ldw * elem_size(w_type_of(precision));
     char* const sb = static_cast<char*>(store);
     // banded matrices: several steps per launch (the stopping rule runs on the one-step kernels;
@@ -510,7 +510,7 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     for (int j = 0; j < m; ++j) {
         if (sb) {
             p.win = (j == 0) ? win0 : (const void*)(sb + (size_t)(j - 1) * sblk);
-            p.wout = (j + 1 < m) ? (void*)(sb + (size_t)j * sblk) : wa;
+            p.wout = sb + (size_t)j * sblk;
         } else {
             p.win = (j == 0) ? win0 : ((j & 1) ? wa : wb);
             p.wout = (j & 1) ? wb : wa;
@@ -537,7 +537,7 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
 // n x b blocks of the W storage type with leading dimension l. Reverse recurrence of the adjoint,
 // Lambda_m = d_m U_w, Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U_w (B symmetric); vprep holds the
 // values prepared for B, rowidx the row of every stored entry. The W_j come from the workspace
-// block ckpt_name: with stored, it already holds W_1 .. W_{m-1} (the forward's trace pass wrote
+// block ckpt_name: with stored, it already holds W_1 .. W_m (the forward's trace pass wrote
 // them) and no forward step runs here; otherwise they are recomputed from checkpoints kept there
 // every ckpt_stride (default ceil(sqrt(m))) steps.
 ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, const int32_t* rowidx, const void* W0,
@@ -719,12 +719,27 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     const size_t ep = elem_size(p_type_of(prec));
     std::vector<double> beta(m + 1);
     for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
-    WS(scratch, char*, "bw_tmp", 2 * blk);
     WS(FV, void*, "bw_FV", (size_t)n * l2 * ep);
     WS(FV64, double*, "bw_FV64", (size_t)n * b2 * sizeof(double));
-    st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, b2, V, l2, scratch, scratch + blk, FV, l2, nullptr, beta, h->kept_d,
-                  h->cfg_kernel, h->cfg_threads, h->cfg_rpt, s);
-    if (st != LL_OK) return st;
+    void* wk = h->kept_wall ? kept_buf("bw_ckpt") : nullptr;
+    if (wk) {
+        // the trace pass kept W_1 .. W_m of W_0 = [Q | G']: F [Q | G'] = sum_j d_j W_j, the same
+        // numbers as the P-axpy sweep below
+        std::vector<float2> ddf(m + 1);
+        for (int j = 0; j <= m; ++j) ddf[j] = df_split(h->kept_d[j]);
+        WS(dco, double*, "bw_dcoef", (size_t)(m + 1) * sizeof(double));
+        WS(dcf, float2*, "bw_dcoef_df", (size_t)(m + 1) * sizeof(float2));
+        LL_CK(cudaMemcpyAsync(dco, h->kept_d.data(), (size_t)(m + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+        LL_CK(cudaMemcpyAsync(dcf, ddf.data(), (size_t)(m + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
+        LL_CK(cudaStreamSynchronize(s));   // the host vectors go out of scope
+        LL_CK(launch_weighted_sum(prec, V, wk, blk, l2, n, b2, m, dco, dcf, FV, l2, s));
+        h->launches++;
+    } else {
+        WS(scratch, char*, "bw_tmp", 2 * blk);
+        st = run_pass(h, A, vprep, prec, MODE_ACCUM, n, b2, V, l2, scratch, scratch + blk, FV, l2, nullptr, beta, h->kept_d,
+                      h->cfg_kernel, h->cfg_threads, h->cfg_rpt, s);
+        if (st != LL_OK) return st;
+    }
     LL_CK(launch_block_to_f64(prec, FV, l2, FV64, b2, n, b2, s));
     h->launches++;
 
@@ -1171,8 +1186,9 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         Vq = vq_;
         Vg = vg_;
     }
-    // The backward needs W_0 .. W_{m-1} of the trace pass. With GB300's HBM they usually fit: the
-    // trace pass then writes W_1 .. W_{m-1} into the backward's checkpoint block, and the adjoint
+    // The backward needs W_0 .. W_{m-1} of the trace pass (and W_m for the through-QR term's
+    // F [Q | G']). With GB300's HBM they usually fit: the trace pass then writes W_1 .. W_m into
+    // the backward's checkpoint block, and the adjoint
     // runs no forward steps. Taken when they need at most half of the free device memory
     // (counting the backward blocks that this makes unnecessary), and not under an explicit
     // checkpoint stride; the recompute buffers of an earlier backward are then released.
@@ -1181,9 +1197,9 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     void* wall = nullptr;
     void* wall_s = nullptr;
     if (o.keep_for_backward && o.ckpt_stride == 0 && m >= 2 && !split2) {
-        const size_t need = (size_t)(m - 1) * n * l2 * ew;
+        const size_t need = (size_t)m * n * l2 * ew;
         const bool sketch = !hutch && kq > 0 && kq < n && !h->band_ok;
-        const size_t need_s = sketch ? (size_t)(m - 1) * n * l1 * ew : 0;
+        const size_t need_s = sketch ? (size_t)m * n * l1 * ew : 0;
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
             cudaGetLastError();
@@ -1464,8 +1480,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         dsum += v;
     }
     I.deg_mean_pass2 = b2 > 0 ? dsum / b2 : 0.0;
-    I.kept_w_steps = wall ? m - 1 : 0;
-    I.kept_w_steps_pass1 = wall_s ? m - 1 : 0;
+    I.kept_w_steps = wall ? m : 0;
+    I.kept_w_steps_pass1 = wall_s ? m : 0;
     h->last_deg1 = deg1;
     h->last_deg2 = deg2;
     h->have_forward = true;

@@ -101,6 +101,10 @@ cudaError_t launch_scale_cols(int precision, const void* V, long long ld, int n,
                               void* out, cudaStream_t s);
 // rowidx[e] = row of stored entry e
 cudaError_t launch_row_index(const int32_t* rowptr, int n, int32_t* rowidx, cudaStream_t s);
+// P = sum_{j<=m} d_j W_j over W_0 = w0 and the m blocks W_1 .. W_m at wk (blk bytes apart), with the
+// P-axpy step's arithmetic and order (same P as the pass); b columns, W and P leading dims ld, ldp
+cudaError_t launch_weighted_sum(int precision, const void* w0, const void* wk, size_t blk, long long ld, int n, int b,
+                                int m, const double* d, const float2* ddf, void* P, long long ldp, cudaStream_t s);
 // g[e] += scale * <Lam[r_e, :], W[c_e, :]> over b columns for every stored entry (W storage type of
 // `precision`, ld even; rowidx[e] = r_e from launch_row_index)
 cudaError_t launch_sddmm(int precision, const int32_t* rowidx, const int32_t* colind, int64_t nnz, const void* lam,

@@ -210,8 +210,10 @@ def test_autograd_through_qr(L, h):
 
 @pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
 def test_backward_from_kept_w_equals_recomputed(L, h, prec):
-    """By default both passes keep W_1 .. W_{m-1} for the backward (ll_info.kept_w_steps and
-    kept_w_steps_pass1 = m - 1); under an explicit checkpoint stride the backward recomputes them. The W_j are the
+    """By default both passes keep W_1 .. W_m for the backward (ll_info.kept_w_steps and
+    kept_w_steps_pass1 = m); under an explicit checkpoint stride the backward recomputes them.
+    The through-QR term's F [Q | G'] then comes from the kept W_j (a weighted sum) instead of a
+    P-axpy sweep, with the same numbers. The W_j are the
     same numbers either way, so the two gradients are identical, and a through-QR backward in
     between (its own checkpoints) leaves the kept ones intact."""
     A = random_spd(900, nnz_per_row=6, seed=11, empty_rows=2)
@@ -224,8 +226,8 @@ def test_backward_from_kept_w_equals_recomputed(L, h, prec):
         L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=m, probes=21, seed=5, precision=prec,
                                                         keep_for_backward=True, ckpt_stride=ckpt))
         info = h.info()
-        assert info["kept_w_steps"] == (m - 1 if ckpt == 0 else 0)
-        assert info["kept_w_steps_pass1"] == (m - 1 if ckpt == 0 else 0)
+        assert info["kept_w_steps"] == (m if ckpt == 0 else 0)
+        assert info["kept_w_steps_pass1"] == (m if ckpt == 0 else 0)
         g = L.ll_logdet_backward(h, dA, 1.0)
         gq = L.ll_logdet_backward(h, dA, 1.0, through_qr=True)
         assert L.ll_logdet_backward(h, dA, 1.0).equal(g)
