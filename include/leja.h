@@ -128,9 +128,9 @@ typedef struct {
                                   most 256 threads runs two per SM). Ignored by LL_KERNEL_AUTO.  */
     int ckpt_stride;           /* backward: 0 (default) = the forward's trace pass keeps W_1 ..
                                   W_m for the backward when they take at most half of the
-                                  free device memory, else checkpoints every ceil(sqrt(m))
-                                  steps; > 0 = checkpoints every ckpt_stride steps, the W_j
-                                  between them recomputed by the backward                       */
+                                  free device memory, else the trace pass writes checkpoints
+                                  at the smallest stride that fits (<= ceil(sqrt(m))); > 0 =
+                                  the backward checkpoints every ckpt_stride steps itself     */
     int use_graph;             /* 1: capture the m-step passes in a CUDA graph (default 1)       */
     int64_t timeout_cycles;    /* batched launch: clock cycles a dependency wait may spin before
                                   the call fails with LL_ERR_TIMEOUT; 0 = about 2 s. Also bounds
@@ -161,8 +161,9 @@ typedef struct {
     int deg_max_pass1, deg_max_pass2;   /* largest final degree over the columns of each pass
                                            (the degree itself under a fixed degree)              */
     double deg_mean_pass2;              /* mean final degree over the trace pass's columns        */
-    int kept_w_steps;                   /* W_j blocks the trace pass kept for the backward (m:
-                                           W_1 .. W_m; 0 when the backward recomputes them)       */
+    int kept_w_steps;                   /* W_j blocks the trace pass kept for the backward: m
+                                           (W_1 .. W_m), or the checkpoint count when only
+                                           W_s, W_2s, ... fit; 0: none                           */
     int kept_w_steps_pass1;             /* the same for pass 1 (W_0 = S), used by the through-QR
                                            adjoint; 0 for a banded matrix or when they do not fit */
 } ll_info;

@@ -76,7 +76,8 @@ struct ll_handle {
     bool kept_hutch = false;  // the kept forward used plain Hutchinson (V = G, no basis)
     bool kept_qr = false;     // the kept forward ran the sketch and its CholeskyQR2 (S, G, R1^-1, R2^-1 kept)
     bool kept_band = false;   // the kept forward's matrix suits the banded kernel
-    bool kept_wall = false;   // the kept forward's trace pass left W_1 .. W_m in "bw_ckpt"
+    int kept_stride = 0;      // the kept forward's trace pass left W_1 .. W_m (1) or the checkpoints
+                              // W_s, W_2s, ... (s > 1) in "bw_ckpt"; 0: none
     bool kept_wall_s = false; // and its pass 1 (W_0 = S) left them in "bw_ckpt_s"
     int64_t kept_far = 0;     // its far-entry count and longest row (TMA plans of the adjoint)
     int kept_max_row = 0;
@@ -434,10 +435,12 @@ ll_status run_band_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, in
 ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int precision, int mode, int n, int b,
                    const void* win0, long long ldw, void* wa, void* wb, void* P, long long ldp, double* dots,
                    const std::vector<double>& beta, const std::vector<double>& d, int kernel, int threads_target,
-                   int rpt, cudaStream_t s, const StopState& stop = StopState{}, void* store = nullptr) {
+                   int rpt, cudaStream_t s, const StopState& stop = StopState{}, void* store = nullptr,
+                   int store_stride = 1) {
     const int m = (int)d.size() - 1;
-    // with store, W_1 .. W_m are written to m consecutive n x ldw blocks there instead of the
-    // ping-pong pair
+    // with store and store_stride 1, W_1 .. W_m are written to m consecutive n x ldw blocks there
+    // instead of the ping-pong pair; with store_stride s > 1, W_s, W_2s, ..., W_{(ceil(m/s)-1)s}
+    // (the backward's checkpoints) go there and the others to the ping-pong pair
     const size_t sblk = (size_t)n * ldw * elem_size(w_type_of(precision));
     char* const sb = static_cast<char*>(store);
     // banded matrices: several steps per launch (the stopping rule runs on the one-step kernels;
@@ -507,10 +510,18 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     }
     h->last_kernel = E.kind;
     h->last_threads = E.cta();
+    const int nslot = store_stride > 1 ? (m + store_stride - 1) / store_stride - 1 : m;
+    const void* cur = win0;
     for (int j = 0; j < m; ++j) {
         if (sb) {
-            p.win = (j == 0) ? win0 : (const void*)(sb + (size_t)(j - 1) * sblk);
-            p.wout = sb + (size_t)j * sblk;
+            const int k = j + 1;   // this step writes W_k
+            void* out;
+            if (store_stride <= 1) out = sb + (size_t)j * sblk;
+            else if (k % store_stride == 0 && k / store_stride <= nslot) out = sb + (size_t)(k / store_stride - 1) * sblk;
+            else out = (cur == wa) ? wb : wa;
+            p.win = cur;
+            p.wout = out;
+            cur = out;
         } else {
             p.win = (j == 0) ? win0 : ((j & 1) ? wa : wb);
             p.wout = (j & 1) ? wb : wa;
@@ -542,7 +553,8 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
 // every ckpt_stride (default ceil(sqrt(m))) steps.
 ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, const int32_t* rowidx, const void* W0,
                              const void* U, long long l, int b, int split, double cq, double gdiv, double grad_output,
-                             double* grad_values, cudaStream_t s, const char* ckpt_name, bool stored) {
+                             double* grad_values, cudaStream_t s, const char* ckpt_name, int stored_stride) {
+    const bool stored = stored_stride > 0;   // the forward wrote the checkpoints at this stride
     const int n = (int)A->n;
     const int prec = h->kept_prec, m = h->kept_m;
     const int wt = w_type_of(prec);
@@ -552,16 +564,18 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
     std::vector<double> beta(m + 1);
     for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
     // checkpoints W_{k s} (k >= 1) and a segment buffer for W_{j0+1} .. W_{j1-1}
-    const int sck = stored ? 1 : h->kept_ckpt > 0 ? h->kept_ckpt : (int)std::ceil(std::sqrt((double)m));
+    const int sck = stored ? stored_stride : h->kept_ckpt > 0 ? h->kept_ckpt : (int)std::ceil(std::sqrt((double)m));
     const int nseg = (m + sck - 1) / sck;
     WS(ckpt, char*, ckpt_name, blk * (size_t)(nseg > 1 ? nseg - 1 : 1));
     WS(lam, char*, "bw_lam", 2 * blk);
     char* seg = nullptr;
     char* tmp = nullptr;
-    if (!stored) {
-        WS(seg_, char*, "bw_seg", blk * (size_t)(sck > 1 ? sck - 1 : 1));
-        WS(tmp_, char*, "bw_tmp", 2 * blk);
+    if (sck > 1) {
+        WS(seg_, char*, "bw_seg", blk * (size_t)(sck - 1));
         seg = seg_;
+    }
+    if (!stored) {
+        WS(tmp_, char*, "bw_tmp", 2 * blk);
         tmp = tmp_;
     }
 
@@ -595,7 +609,10 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
     pa.adj_g_df = df_split(d[0] / gdiv);
     StepExec Ep, Ea;
     ll_status cs = LL_OK;
-    if (!stored) cs = choose_exec(h, prec, MODE_PLAIN, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pp, Ep, s);
+    if (!stored || sck > 1) {
+        if (!tmp) pp.wout = seg;   // the autotuner's representative step (rewritten below)
+        cs = choose_exec(h, prec, MODE_PLAIN, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pp, Ep, s);
+    }
     if (cs != LL_OK) return cs;
     cs = choose_exec(h, prec, MODE_ADJ, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pa, Ea, s);
     if (cs != LL_OK) return cs;
@@ -693,7 +710,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     h->launches++;
     // frozen basis: W_0 = [Q | G'], U = [Q | G' / k]
     st = adjoint_accumulate(h, A, vprep, rowidx, V, V, l2, b2, kq, 1.0, (double)kg, grad_output, grad_values, s,
-                            "bw_ckpt", h->kept_wall);
+                            "bw_ckpt", h->kept_stride);
     if (st != LL_OK || !through_qr || !h->kept_qr) return st;
 
     // ---- through the QR: F [Q | G'] by the pass-1 arithmetic on the kept block
@@ -721,7 +738,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     for (int j = 0; j <= m; ++j) beta[j] = -(c / gamma + h->kept_xi[j]);
     WS(FV, void*, "bw_FV", (size_t)n * l2 * ep);
     WS(FV64, double*, "bw_FV64", (size_t)n * b2 * sizeof(double));
-    void* wk = h->kept_wall ? kept_buf("bw_ckpt") : nullptr;
+    void* wk = h->kept_stride == 1 ? kept_buf("bw_ckpt") : nullptr;
     if (wk) {
         // the trace pass kept W_1 .. W_m of W_0 = [Q | G']: F [Q | G'] = sum_j d_j W_j, the same
         // numbers as the P-axpy sweep below
@@ -789,7 +806,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     // pass 1's W_j as the forward kept them, or checkpoints in a block of their own, so that the
     // trace pass's kept W_j stay valid for the next backward
     return adjoint_accumulate(h, A, vprep, rowidx, S, gam, l1, kq, kq, 1.0, 1.0, grad_output, grad_values, s,
-                              h->kept_wall ? "bw_ckpt_s" : "bw_ckpt", h->kept_wall_s);
+                              h->kept_stride > 0 ? "bw_ckpt_s" : "bw_ckpt", h->kept_wall_s ? 1 : 0);
 }
 
 
@@ -1188,16 +1205,17 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     }
     // The backward needs W_0 .. W_{m-1} of the trace pass (and W_m for the through-QR term's
     // F [Q | G']). With GB300's HBM they usually fit: the trace pass then writes W_1 .. W_m into
-    // the backward's checkpoint block, and the adjoint
-    // runs no forward steps. Taken when they need at most half of the free device memory
-    // (counting the backward blocks that this makes unnecessary), and not under an explicit
-    // checkpoint stride; the recompute buffers of an earlier backward are then released.
+    // the backward's checkpoint block, and the adjoint runs no forward steps. Taken when they need
+    // at most half of the free device memory (counting the backward blocks this makes
+    // unnecessary); otherwise the trace pass writes the backward's checkpoints at the smallest
+    // stride that fits (at most ceil(sqrt(m))). Not under an explicit checkpoint stride.
     // Pass 1's W_j (W_0 = S), which the through-QR adjoint's second recurrence needs, are kept
     // as well when both fit, except for a banded matrix, whose pass 1 keeps its multi-step kernel.
     void* wall = nullptr;
     void* wall_s = nullptr;
+    int wstride = 0, wblocks = 0;
     if (o.keep_for_backward && o.ckpt_stride == 0 && m >= 2 && !split2) {
-        const size_t need = (size_t)m * n * l2 * ew;
+        const size_t blk2 = (size_t)n * l2 * ew;
         const bool sketch = !hutch && kq > 0 && kq < n && !h->band_ok;
         const size_t need_s = sketch ? (size_t)m * n * l1 * ew : 0;
         size_t fr = 0, tot = 0;
@@ -1210,15 +1228,34 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             auto it = h->ws.find(nm);
             if (it != h->ws.end()) have += it->second.bytes;
         }
-        if ((double)need <= 0.5 * (double)(fr + have)) {
-            ws_release(h, "bw_seg");
+        const double budget = 0.5 * (double)(fr + have);
+        // every W_j if they fit; else the checkpoints at the smallest stride that fits, at most the
+        // backward's own ceil(sqrt(m)): written here, they spare the backward its first sweep
+        const int smax = std::max(2, (int)std::ceil(std::sqrt((double)m)));
+        if ((double)m * (double)blk2 <= budget) {
+            wstride = 1;
+            wblocks = m;
+        } else {
+            for (int st_ = 2; st_ <= smax; ++st_) {
+                const int nb = (m + st_ - 1) / st_ - 1;
+                if ((double)nb * (double)blk2 <= budget || st_ == smax) {
+                    wstride = st_;
+                    wblocks = nb;
+                    break;
+                }
+            }
+        }
+        if (wstride > 0 && wblocks > 0) {
             ws_release(h, "bw_tmp");
-            WS(wall_, void*, "bw_ckpt", need);
+            if (wstride == 1) ws_release(h, "bw_seg");
+            WS(wall_, void*, "bw_ckpt", (size_t)wblocks * blk2);
             wall = wall_;
-            if (sketch && (double)(need + need_s) <= 0.5 * (double)(fr + have)) {
+            if (wstride == 1 && sketch && (double)(wblocks * blk2 + need_s) <= budget) {
                 WS(wall_s_, void*, "bw_ckpt_s", need_s);
                 wall_s = wall_s_;
             }
+        } else {
+            wstride = 0;
         }
     }
     int k1 = 0, t1 = 0;   // step kernel and CTA size of pass 1
@@ -1321,7 +1358,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
                           d, o.step_kernel, o.threads_per_block, o.rows_per_thread, q, stop2g);
         } else {
             st = run_pass(h, A, vprep, prec, MODE_DOT, n, b2, V, l2, wa, wb, nullptr, 0, dots, beta, d, o.step_kernel,
-                          o.threads_per_block, o.rows_per_thread, q, stop2, wall);
+                          o.threads_per_block, o.rows_per_thread, q, stop2, wall, wstride);
         }
         if (st != LL_OK) return st;
         LL_CK(rec(h->ev[4], q));
@@ -1344,7 +1381,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     key.n = A->n; key.nnz = A->nnz; key.dtype = A->dtype;
     key.lmin = bounds.lmin; key.lmax = bounds.lmax;
     key.o = o;
-    key.o.keep_for_backward = (wall ? 1 : 0) + (wall_s ? 2 : 0);   // the passes write into the backward's blocks
+    key.o.keep_for_backward = (wall ? 1 + wstride * 4 : 0) + (wall_s ? 2 : 0);   // the passes write into the backward's blocks
     key.ws_gen = h->ws_gen;
     key.inject = h->inject;
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
@@ -1480,7 +1517,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         dsum += v;
     }
     I.deg_mean_pass2 = b2 > 0 ? dsum / b2 : 0.0;
-    I.kept_w_steps = wall ? m : 0;
+    I.kept_w_steps = wall ? wblocks : 0;
     I.kept_w_steps_pass1 = wall_s ? m : 0;
     h->last_deg1 = deg1;
     h->last_deg2 = deg2;
@@ -1495,7 +1532,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_hutch = hutch;
         h->kept_qr = !hutch && kq < n;
         h->kept_band = h->band_ok;
-        h->kept_wall = wall != nullptr;
+        h->kept_stride = wall ? wstride : 0;
         h->kept_wall_s = wall_s != nullptr;
         h->kept_far = h->far_entries;
         h->kept_max_row = h->max_row;
