@@ -38,8 +38,9 @@ BOUNDS = (0.05, 12.05)
 PROBES = 99
 SEED = 1
 
-DTYPE_NAME = {"df64": "df64 (float-float on FP32 pipes, 8-byte storage)", "f64": "f64",
-              "f32": "f32 (double-float accumulation of P and traces)"}
+DTYPE_NAME = {"df64": "df64 = 48-bit float-float (FP32 pairs on the FP32 pipes, 8-byte storage; not IEEE f64)",
+              "f64": "f64 (IEEE binary64 on the FP64 pipe)",
+              "f32": "f32-mixed (FP32 values and W_j; P and the traces in double-float)"}
 ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A, s_W, s_P, s_V
 
 # DRAM bytes (read + write) of one pass-2 trace-step launch per matrix row, from one ncu capture of
@@ -141,31 +142,80 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(A, prec: str, budget_s: float = 12.0) -> dict:
-    """The FP64 CPU oracle as it stands (one column at a time, SciPy CSR mat-vec), timed on a
-    bounded sample: Algorithm 2 steps on single probe columns until ~budget_s of CPU time."""
-    import numpy as np
+CPU_SAMPLE_M = 8   # Léja steps per sampled probe column
 
+
+def _oracle_columns(A, budget_s: float, start_at: float = 0.0, col0: int = 0) -> tuple[int, float]:
+    """The FP64 oracle as it stands (Algorithm 2 one column at a time, SciPy CSR mat-vec) on
+    Rademacher probe columns of seeds SEED + col0, SEED + col0 + 1, ... until budget_s have passed:
+    (columns done, seconds). Waits until start_at (time.time()) first when given."""
     from oracle import logdet as O
     from oracle import rng as R
     sigma = O.sigma_of(BOUNDS[0])
     lt, ut = BOUNDS[0] / sigma, BOUNDS[1] / sigma
-    sample_m = 8
-    xi, c, g, d, _ = O.newton_leja_setup(lt, ut, sample_m)
+    xi, c, g, d, _ = O.newton_leja_setup(lt, ut, CPU_SAMPLE_M)
     M = O._scipy(A)
+    if start_at > 0.0:
+        while time.time() < start_at:
+            time.sleep(0.01)
     cols = 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        v = R.rademacher(SEED, 0, A.n, 1)
+        v = R.rademacher(SEED + col0 + cols, 0, A.n, 1)
         O.leja_apply_columns(M, v, xi, d, c, g, sigma)
         cols += 1
-    dt = time.perf_counter() - t0
+    return cols, time.perf_counter() - t0
+
+
+def _cpu_worker(args):
+    """One process of the all-core oracle sample (started by spawn: no CUDA state inherited)."""
+    grid, rank, budget_s, start_at = args
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from synth import laplacian_3d
+    A = laplacian_3d(grid, SHIFT)
+    return _oracle_columns(A, budget_s, start_at, col0=rank * 1000)
+
+
+def _host_cpu() -> dict:
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Architecture", "Model name", "Socket(s)", "Core(s) per socket", "Thread(s) per core"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
+def cpu_baseline(A, prec: str, budget_s: float = 12.0, all_cores: bool = True) -> dict:
+    """The FP64 CPU oracle as it stands (one column at a time, SciPy CSR mat-vec), timed on a
+    bounded sample of the headline workload: Algorithm 2 steps on single probe columns for about
+    budget_s, on one core; then the same on every host core at once (one spawned process per
+    core, each on its own columns: the oracle is single-threaded, so columns are its unit of
+    parallel work), reported beside it."""
     # per column-step bytes in the oracle's own FP64 layout: CSR + w read + w written + P read/written
     per = A.nnz * 12 + 4 * (A.n + 1) + A.n * (2 * 8 + 2 * 8)
-    gbs = cols * sample_m * per / dt / 1e9
-    return {"value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{cols} probe column(s) x {sample_m} Léja steps (Algorithm 2, FP64, SciPy CSR mat-vec) "
-                      f"on the {GRID_N}^3 Laplacian in {dt:.1f} s"}
+    cols, dt = _oracle_columns(A, budget_s)
+    gbs = cols * CPU_SAMPLE_M * per / dt / 1e9
+    host = _host_cpu()
+    out = {"value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host,
+           "sample": f"{cols} probe column(s) x {CPU_SAMPLE_M} Léja steps (Algorithm 2, FP64, SciPy CSR mat-vec) "
+                     f"on the {int(round(A.n ** (1 / 3)))}^3 Laplacian in {dt:.1f} s, one process"}
+    ncpu = os.cpu_count() or 1
+    if all_cores and ncpu > 1:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        start_at = time.time() + 10.0          # after every worker has built the matrix
+        with ctx.Pool(ncpu) as pool:
+            res = pool.map(_cpu_worker, [(int(round(A.n ** (1 / 3))), r, budget_s / 2, start_at) for r in range(ncpu)])
+        tot = sum(c for c, _ in res)
+        wall = max(t for _, t in res)
+        out["all_cores"] = {"value": tot * CPU_SAMPLE_M * per / wall / 1e9, "unit": UNIT, "cores": ncpu,
+                            "sample": f"{tot} probe columns x {CPU_SAMPLE_M} Léja steps over {ncpu} processes "
+                                      f"in {wall:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -175,11 +225,11 @@ def run_reference(args):
     from synth import laplacian_3d
     A = laplacian_3d(GRID_N, SHIFT)
     for _ in range(args.warmup):
-        cpu_baseline(A, args.precision, budget_s=2.0)
+        cpu_baseline(A, args.precision, budget_s=2.0, all_cores=False)
     vals = []
     cb = None
     for _ in range(args.steps):
-        cb = cpu_baseline(A, args.precision, budget_s=6.0)
+        cb = cpu_baseline(A, args.precision, budget_s=6.0, all_cores=False)
         vals.append(cb["value"])
     v = statistics.median(vals)
     cb["value"] = v
@@ -274,6 +324,55 @@ def workload_config3(L, h, grid: int = 1024, degree: int = 80):
                      "forward_phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
     return {"workload": f"Matern tau(kappa^2 I + L2D)^2 {grid}^2 (n={A.n}, nnz={A.nnz}), kappa={kappa}, tau={tau}, "
                         f"bounds [{lmin}, {lmax:.4f}], degree {degree}, 60 Gaussian probes, seed 0", **out}
+
+
+def workload_c3_time_to_tol(L, h, grid: int = 1024, tol: float = 1e-3, degrees=(80, 120, 160),
+                            probe_counts=(60, 120, 240)):
+    """Time of the log-determinant plus its gradient at `tol` relative error on the Matérn GMRF
+    of config 3 (tau (kappa^2 I + L_2D)^2 on grid^2, kappa = 0.3, tau = 1, Gaussian probes, seed 0).
+    A degree x probes sweep in FP32-mixed finds the cheapest setting (forward + frozen-basis
+    backward time) whose log-determinant and both theta-gradients (d/dkappa, d/dtau through
+    ll_param_grad) are within tol of the closed forms; that setting is then timed in IEEE FP64
+    (the plain FP64 form), DF64 and FP32-mixed on the same GPU."""
+    import numpy as np
+    import torch
+    from synth import matern_2d, matern_2d_derivatives
+    from tests.pins import dlogdet_matern_2d, logdet_matern_2d
+    kappa, tau = 0.3, 1.0
+    A = matern_2d(grid, kappa, tau)
+    dk, dt = matern_2d_derivatives(grid, kappa, tau)
+    dv = torch.as_tensor(np.stack([dk, dt])).cuda()
+    exact = logdet_matern_2d(grid, kappa, tau)
+    ex_k, ex_t = dlogdet_matern_2d(grid, kappa, tau)
+    dev = {"f64": L.DeviceCSR.from_host(A, "f64"), "f32": L.DeviceCSR.from_host(A, "f32")}
+    dev["df64"] = dev["f64"]
+    lmax = L.ll_gershgorin(h, dev["f64"])[1]
+    lmin = tau * kappa ** 4
+
+    def run(prec: str, degree: int, probes: int, warm: int = 2):
+        dA = dev[prec]
+        opts = L.options(degree=degree, probes=probes, seed=0, precision=prec, probe_kind="gaussian",
+                         keep_for_backward=True)
+        ms_f, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), 1, warm)
+        ms_b, g = time_calls(lambda: L.ll_logdet_backward(h, dA, 1.0), 1, 1)
+        th = L.ll_param_grad(h, g, dv)
+        del g
+        errs = {"logdet": abs(est - exact) / abs(exact), "dkappa": abs(th[0] - ex_k) / abs(ex_k),
+                "dtau": abs(th[1] - ex_t) / abs(ex_t)}
+        return {"degree": degree, "probes": probes, "ms_forward": ms_f, "ms_backward": ms_b,
+                "ms_logdet_plus_gradient": ms_f + ms_b, "rel_err": errs, "max_rel_err": max(errs.values()),
+                "kept_w_stride": h.info()["kept_w_stride"]}
+
+    sweep = [run("f32", d, p) for d in degrees for p in probe_counts]
+    ok = [x for x in sweep if x["max_rel_err"] <= tol]
+    pick = min(ok, key=lambda x: x["ms_logdet_plus_gradient"]) if ok else min(sweep, key=lambda x: x["max_rel_err"])
+    timed = {pr: run(pr, pick["degree"], pick["probes"]) for pr in ("f64", "df64", "f32")}
+    return {"workload": (f"Matern tau(kappa^2 I + L2D)^2 {grid}^2 (n={A.n}, nnz={A.nnz}), kappa={kappa}, tau={tau}, "
+                         f"Gaussian probes, seed 0; logdet + frozen-basis gradient chained to (kappa, tau)"),
+            "tol": tol, "reached": bool(ok), "setting": {"degree": pick["degree"], "probes": pick["probes"]},
+            "sweep_f32": sweep, "timed": timed,
+            "speedup_f32_vs_f64": timed["f64"]["ms_logdet_plus_gradient"] / timed["f32"]["ms_logdet_plus_gradient"],
+            "speedup_df64_vs_f64": timed["f64"]["ms_logdet_plus_gradient"] / timed["df64"]["ms_logdet_plus_gradient"]}
 
 
 def workload_config4(L, h, count: int = 64):
@@ -513,6 +612,23 @@ def workload_f4(L, h, N: int = 5000, thetas=(-0.24, -0.23, -0.22, -0.21, -0.20),
     return out
 
 
+def profile_case(name: str):
+    """Small single-call cases for ncu captures (see profiles/)."""
+    import torch
+
+    import paper_2603_02207_gb300 as L
+    from paper_2603_02207_gb300 import build as _b
+    _b.build()
+    h = L.Handle()
+    if name == "band":
+        from synth import pentadiagonal
+        A = pentadiagonal(2_000_000, seed=0)
+        dA = L.DeviceCSR.from_host(A)
+        lo, hi = L.ll_gershgorin(h, dA)
+        L.ll_logdet_forward(h, dA, lo, hi, L.options(degree=8, probes=30, seed=0, precision="df64", use_graph=False))
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,11 +646,17 @@ def main():
                     help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
                     help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
-    ap.add_argument("--workloads", default="c1,c3,c4,f1,f3,f4",
-                    help="extra workloads reported beside the headline (comma list of c1,c3,c4,c5,f1,f3,f4; '' for none)")
+    ap.add_argument("--workloads", default="c1,c3,c3t,c4,c5,f1,f3,f4",
+                    help="extra workloads reported beside the headline (comma list of c1,c3,c3t,c4,c5,f1,f3,f4; "
+                         "'' for none; c3t = the Matérn time to 1e-3 relative error)")
+    ap.add_argument("--profile-case", default="", choices=["", "band"],
+                    help="run one small case for a profiler capture and exit (no JSON line): band = one DF64 "
+                         "forward on the pentadiagonal family at n = 2e6, degree 8, 30 probes, graphs off")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args.profile_case)
 
     import numpy as np
     import torch
@@ -591,23 +713,29 @@ def main():
 
     # roofline of the dominant kernel (the pass-2 fused SpMM + trace step, width 2k)
     peaks, peak_src = load_peaks()
-    p2_launch_ms = statistics.median(r["p2"]) / m
-    p1_launch_ms = statistics.median(r["p1"]) / m
-    b_p2 = step_bytes(n, nnz, 2 * k, prec, "dot")
-    b_p1 = step_bytes(n, nnz, k, prec, "accum")
-    achieved = b_p2 / (p2_launch_ms / 1e3) / 1e9
-    kname = {L.LL_KERNEL_TMA: "tma", L.LL_KERNEL_GATHER: "gather"}.get(r["info"]["kernel_pass2"], "gather")
-    per_row = TRACE_STEP_DRAM_BYTES_PER_ROW.get((kname, prec))
-    kfun = "k_leja_tma" if kname == "tma" else "k_leja_step"
-    roof = {"kernel": f"{kfun}<{prec},DOT> (b={2 * k}, {r['info']['threads_pass2']} threads/CTA)", "bound": "hbm",
-            "achieved": achieved,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-            "traffic": per_row * n if per_row else None,
-            "traffic_source": f"ncu dram__bytes_read+write of one {kfun} launch at 96^3, scaled by rows" if per_row else None,
-            "peak_source": peak_src,
-            "per_launch_bytes": b_p2, "per_launch_ms": p2_launch_ms,
-            "pass1_kernel": {"achieved": b_p1 / (p1_launch_ms / 1e3) / 1e9, "per_launch_bytes": b_p1,
-                             "per_launch_ms": p1_launch_ms}}
+
+    def roofline_of(pr: str, rr: dict) -> dict:
+        p2_launch_ms = statistics.median(rr["p2"]) / m
+        p1_launch_ms = statistics.median(rr["p1"]) / m
+        b_p2 = step_bytes(n, nnz, 2 * k, pr, "dot")
+        b_p1 = step_bytes(n, nnz, k, pr, "accum")
+        achieved = b_p2 / (p2_launch_ms / 1e3) / 1e9
+        kname = {L.LL_KERNEL_TMA: "tma", L.LL_KERNEL_GATHER: "gather"}.get(rr["info"]["kernel_pass2"], "gather")
+        per_row = TRACE_STEP_DRAM_BYTES_PER_ROW.get((kname, pr))
+        kfun = "k_leja_tma" if kname == "tma" else "k_leja_step"
+        ach1 = b_p1 / (p1_launch_ms / 1e3) / 1e9
+        return {"kernel": f"{kfun}<{pr},DOT> (b={2 * k}, {rr['info']['threads_pass2']} threads/CTA)", "bound": "hbm",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": per_row * n if per_row else None,
+                "traffic_source": (f"ncu dram__bytes_read+write of one {kfun} launch on a smaller 3-D Laplacian, "
+                                   "scaled by rows") if per_row else None,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "per_launch_bytes": b_p2, "per_launch_ms": p2_launch_ms,
+                "pass1_kernel": {"kernel": f"{kfun}<{pr},ACCUM> (b={k}, {rr['info']['threads_pass1']} threads/CTA)",
+                                 "achieved": ach1, "frac": ach1 / peaks["hbm_gbs"], "per_launch_bytes": b_p1,
+                                 "per_launch_ms": p1_launch_ms}}
+
+    roof = roofline_of(prec, r)
 
     # end to end through the C ABI with host buffers (CSR copied host->device every call)
     e2e = None
@@ -631,17 +759,28 @@ def main():
         e2e = {"value": world * bytes_est * args.steps / wall / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": wall * 1e3 / args.steps}
 
-    variants = {}
+    # every precision side by side, each with the roofline of its own trace and P-axpy steps
+    from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only
+    exact = logdet_laplacian_3d(args.grid, SHIFT)
+
+    def precision_entry(pr: str, rr: dict, steps: int) -> dict:
+        bv = estimate_bytes(n, nnz, k, m, pr)
+        v = world * bv * steps / (rr["ms"] / 1e3) / 1e9
+        inf = rr["info"]
+        return {"dtype": DTYPE_NAME[pr], "value": v, "unit": UNIT, "hbm_frac_of_measured": v / peaks["hbm_gbs"],
+                "ms_per_step": rr["ms"] / steps, "estimate": rr["est"],
+                "rel_err_vs_exact": abs(rr["est"] - exact) / abs(exact),
+                "phase_ms": {"probes": inf["ms_probes"], "pass1": inf["ms_pass1"], "qr": inf["ms_qr"],
+                             "pass2": inf["ms_pass2"]},
+                "roofline": roofline_of(pr, rr)}
+
+    precisions = {prec: precision_entry(prec, r, args.steps)}
     if args.variants:
         for other in ("df64", "f64", "f32"):
             if other == prec:
                 continue
-            rv = time_precision(other, 2, 1)
-            bv = estimate_bytes(n, nnz, k, m, other)
-            variants[other] = {"value": bv * 2 / (rv["ms"] / 1e3) / 1e9, "ms_per_step": rv["ms"] / 2,
-                               "pass1_launch_ms": statistics.median(rv["p1"]) / m,
-                               "pass2_launch_ms": statistics.median(rv["p2"]) / m,
-                               "estimate": rv["est"]}
+            rv = time_precision(other, 3, 2)
+            precisions[other] = precision_entry(other, rv, 3)
 
     if rank != 0:
         if world > 1:
@@ -652,12 +791,11 @@ def main():
         if w == "f1":
             extra[w] = workload_f1(L, h, A, args.grid, m)
             continue
-        fn = {"c1": workload_config1, "c3": workload_config3, "c4": workload_config4, "c5": workload_config5,
-              "f3": workload_f3, "f4": workload_f4}[w]
+        fn = {"c1": workload_config1, "c3": workload_config3, "c3t": workload_c3_time_to_tol, "c4": workload_config4,
+              "c5": workload_config5, "f3": workload_f3, "f4": workload_f4}[w]
         extra[w] = fn(L, h, log2n=args.c5_log2n) if w == "c5" else fn(L, h)
+    c3t = extra.pop("c3t", None)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
-    from tests.pins import logdet_laplacian_3d  # closed form, for the reported error only
-    exact = logdet_laplacian_3d(args.grid, SHIFT)
     info = r["info"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -673,7 +811,8 @@ def main():
         "phase_ms": {"probes": info["ms_probes"], "pass1": info["ms_pass1"], "qr": info["ms_qr"],
                      "pass2": info["ms_pass2"], "total": info["ms_total"]},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": r["launches"], "clocks": r["clocks"], "variants": variants, "workloads": extra,
+        "c3_time_to_1e-3": c3t,
+        "gpu_launches": r["launches"], "clocks": r["clocks"], "precisions": precisions, "workloads": extra,
     }
     print(json.dumps(line))
     if world > 1:

@@ -128,9 +128,11 @@ typedef struct {
                                   most 256 threads runs two per SM). Ignored by LL_KERNEL_AUTO.  */
     int ckpt_stride;           /* backward: 0 (default) = the forward's trace pass keeps W_1 ..
                                   W_m for the backward when they take at most half of the
-                                  free device memory, else the trace pass writes checkpoints
-                                  at the smallest stride that fits (<= ceil(sqrt(m))); > 0 =
-                                  the backward checkpoints every ckpt_stride steps itself     */
+                                  free device memory (ll_set_keep_budget), else the trace pass
+                                  writes checkpoints at the smallest stride that fits
+                                  (<= ceil(sqrt(m))), else none are kept and the backward
+                                  checkpoints itself; > 0 = the backward checkpoints every
+                                  ckpt_stride steps itself                                     */
     int use_graph;             /* 1: capture the m-step passes in a CUDA graph (default 1)       */
     int64_t timeout_cycles;    /* batched launch: clock cycles a dependency wait may spin before
                                   the call fails with LL_ERR_TIMEOUT; 0 = about 2 s. Also bounds
@@ -166,6 +168,12 @@ typedef struct {
                                            W_s, W_2s, ... fit; 0: none                           */
     int kept_w_steps_pass1;             /* the same for pass 1 (W_0 = S), used by the through-QR
                                            adjoint; 0 for a banded matrix or when they do not fit */
+    int kept_w_stride;                  /* 1: the trace pass kept every W_j (kept_w_steps = m);
+                                           s > 1: it kept the checkpoints W_s, W_2s, ...
+                                           (kept_w_steps = ceil(m/s) - 1); 0: none kept        */
+    int64_t forward_id;                 /* 1 + the number of earlier successful forwards on the
+                                           handle: a caller that keeps it can tell whether the
+                                           handle's kept state is still that of its forward     */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */
@@ -184,6 +192,12 @@ void ll_default_options(ll_options* opts);
  * (LL_KERNEL_*, with threads_per_block and rows_per_thread as in ll_options; the default is
  * LL_KERNEL_AUTO). LL_ERR_INVALID_ARG for an unknown kernel or a negative shape. */
 ll_status ll_set_step_config(ll_handle* h, int step_kernel, int threads_per_block, int rows_per_thread);
+/* Device memory that ll_logdet_forward with keep_for_backward may spend on the trace pass's W_j
+ * for the backward (every W_j, else the checkpoints at the smallest stride <= ceil(sqrt(m)) that
+ * fits, else none). 0 (default): half of the free device memory at the call. Lets a caller
+ * leave memory to other work, and lets tests reach the checkpointed layout on small matrices.
+ * LL_ERR_INVALID_ARG for a negative value. */
+ll_status ll_set_keep_budget(ll_handle* h, int64_t bytes);
 
 /* Test hook for failure detection. LL_INJECT_STALL: from now on, the TMA step kernel launched by
  * this handle expects 16 bytes for its first tile that no copy delivers, so that tile's pipeline
@@ -240,14 +254,15 @@ ll_status ll_power_lmax(ll_handle* h, const ll_csr* A, int iters, uint64_t seed,
 /* Largest matrix order accepted by ll_power_lmax_noalloc. */
 #define LL_NOALLOC_MAX_ROWS (1 << 18)
 
-/* The same estimate as ll_power_lmax (identical kernels and reduction order, so identical
- * results), for callers that cannot allocate device memory: code running inside an application
+/* The same estimate as ll_power_lmax (identical kernels, grid and reduction order, so identical
+ * results on any part with at most 1024 SMs), for callers that cannot allocate device memory: code running inside an application
  * whose device memory belongs to another allocator (a framework's caching pool or a fixed arena
  * that forbids raw cudaMalloc), or latency-sensitive code that cannot accept the implicit device
  * synchronisation of cudaMalloc/cudaFree. No handle is needed and nothing is allocated: the
  * working vectors and reduction scratch live in one device array of about 4.2 MB that the library
  * reserves on every GPU that loads it, until the process exits. The paper has no counterpart.
- *   - A: device CSR with at most LL_NOALLOC_MAX_ROWS (262,144) rows; larger -> LL_ERR_UNSUPPORTED.
+ *   - A: device CSR with at most LL_NOALLOC_MAX_ROWS (262,144) rows; larger -> LL_ERR_UNSUPPORTED
+ *     (also on a part with more than 1024 SMs).
  *   - lmax_out: host; the call synchronises `stream`.
  *   - The first call on a device looks up the array's address with that device current; make
  *     that first call before any stream capture.
@@ -310,8 +325,10 @@ ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* A_host, ll_bounds b
  * QR and the bounds; not in the paper):
  *   grad_values[e] += grad_output * (1/gamma) sum_{j<m} Lambda_{j+1}[r_e, :] . W_j[c_e, :],
  *   Lambda_m = d_m U, Lambda_j = d_j U + (B - xi_j I)^T Lambda_{j+1}, U = [Q | G'/k].
- * A must be symmetric (B^T = B is used) and the same matrix (pattern and values) as in the
- * forward. The W_j come from the forward's trace pass when it kept them (ll_info.kept_w_steps),
+ * A must be symmetric (B^T = B is used; the call checks that every stored (r, c) has a stored
+ * (c, r) of the same value, else LL_ERR_INVALID_ARG) and the same matrix (pattern and values) as
+ * in the forward (only n and nnz are checked; ll_info.forward_id tells a caller whether another
+ * forward ran on the handle since its own). The W_j come from the forward's trace pass when it kept them (ll_info.kept_w_steps),
  * else from checkpoints every ckpt_stride steps, recomputed.
  * grad_values: device, nnz doubles, overwritten. Enqueue only. */
 ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream);

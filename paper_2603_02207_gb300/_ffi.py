@@ -56,7 +56,8 @@ class ll_info(ctypes.Structure):
                 ("ms_pass2", ctypes.c_float), ("ms_total", ctypes.c_float), ("kernel_pass1", ctypes.c_int),
                 ("kernel_pass2", ctypes.c_int), ("threads_pass1", ctypes.c_int), ("threads_pass2", ctypes.c_int),
                 ("deg_max_pass1", ctypes.c_int), ("deg_max_pass2", ctypes.c_int), ("deg_mean_pass2", ctypes.c_double),
-                ("kept_w_steps", ctypes.c_int), ("kept_w_steps_pass1", ctypes.c_int)]
+                ("kept_w_steps", ctypes.c_int), ("kept_w_steps_pass1", ctypes.c_int),
+                ("kept_w_stride", ctypes.c_int), ("forward_id", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -74,6 +75,7 @@ SIGNATURES = {
     "ll_last_error": (ctypes.c_char_p, [_P]),
     "ll_default_options": (None, [ctypes.POINTER(ll_options)]),
     "ll_set_step_config": (_I, [_P, _I, _I, _I]),
+    "ll_set_keep_budget": (_I, [_P, _I64]),
     "ll_debug_inject": (_I, [_P, _I]),
     "ll_leja_points": (_I, [_I, _PD]),
     "ll_divided_differences": (_I, [ll_bounds, _I, _I, _PD, ctypes.POINTER(_I)]),

@@ -70,6 +70,10 @@ class Handle:
         """Step kernel of ll_apply_poly and ll_logdet_backward on this handle."""
         self.check(self._lib.ll_set_step_config(self.ptr, STEP_KERNELS[kernel], threads_per_block, rows_per_thread))
 
+    def set_keep_budget(self, nbytes: int = 0):
+        """Device memory the forward may keep for the backward (0 = half the free memory)."""
+        self.check(self._lib.ll_set_keep_budget(self.ptr, int(nbytes)))
+
     def debug_inject(self, what: str = "none"):
         """Test hook: "stall" makes the TMA step kernel's first-tile waits run out (LL_ERR_TIMEOUT)."""
         self.check(self._lib.ll_debug_inject(self.ptr, {"none": _ffi.LL_INJECT_NONE, "stall": _ffi.LL_INJECT_STALL}[what]))

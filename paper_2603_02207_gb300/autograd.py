@@ -23,6 +23,7 @@ class LejaLogdet(torch.autograd.Function):
         opts = api.options(degree=degree, probes=probes, seed=seed, precision=precision, probe_kind=probe_kind,
                            keep_for_backward=True)
         est = api.ll_logdet_forward(handle, A, lmin, lmax, opts)
+        ctx.forward_id = handle.info()["forward_id"]
         ctx.handle = handle
         ctx.A = A
         ctx.through_qr = bool(through_qr)
@@ -30,6 +31,10 @@ class LejaLogdet(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_out):
+        # the handle keeps the state of its last forward only: refuse to differentiate an older one
+        if ctx.handle.info()["forward_id"] != ctx.forward_id:
+            raise api.LejaError(11, "another forward ran on this handle since this estimate's "
+                                    "(one handle per differentiable estimate)")
         g = api.ll_logdet_backward(ctx.handle, ctx.A, float(grad_out), through_qr=ctx.through_qr)
         return g.to(ctx.A.values.dtype), None, None, None, None, None, None, None, None, None, None, None, None
 

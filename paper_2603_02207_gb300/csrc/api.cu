@@ -65,6 +65,9 @@ struct ll_handle {
     int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
     bool band_ok = false;     // the last validated matrix suits the banded kernel
     int max_row = 0;          // longest row of the last validated matrix
+    bool sorted = false;      // every row of the last validated matrix has strictly increasing columns
+    int64_t keep_budget = 0;  // ll_set_keep_budget: bytes the forward may keep for the backward (0: half the free memory)
+    int64_t forward_id = 0;   // count of successful forwards on the handle (ll_info.forward_id)
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
     int dd_degree = -1, dd_sval = -1, dd_scheme = -1, dd_terms = 0;
@@ -81,6 +84,7 @@ struct ll_handle {
     bool kept_wall_s = false; // and its pass 1 (W_0 = S) left them in "bw_ckpt_s"
     int64_t kept_far = 0;     // its far-entry count and longest row (TMA plans of the adjoint)
     int kept_max_row = 0;
+    bool kept_sorted = false; // its rows have strictly increasing columns (the symmetry check)
     // final degree of every column of both passes of the last forward (Algorithm 2's rule)
     bool have_forward = false;
     std::vector<int> last_deg1, last_deg2;
@@ -169,6 +173,7 @@ ll_status validate_csr(ll_handle* h, const ll_csr* A, cudaStream_t s) {
     // the banded kernel takes matrices whose rows hold strictly increasing columns within
     // BAND_H (= TMA_HALO) of the diagonal
     h->band_ok = hv[1] == 0 && hv[3] == 0;
+    h->sorted = hv[3] == 0;
     if (hf) {
         char buf[160];
         snprintf(buf, sizeof buf, "invalid CSR:%s%s%s", (hf & 4) ? " rowptr[0]!=0 or rowptr[n]!=nnz;" : "",
@@ -691,8 +696,22 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     const int b2 = kq + kg, l2 = block_ld(prec, b2);
     const int wt = w_type_of(prec);
     const size_t ew = elem_size(wt), blk = (size_t)n * l2 * ew;
-    if (A->nnz > 0) LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
-    if (n == 0 || A->nnz == 0) return LL_OK;
+    if (n == 0 || A->nnz == 0) {
+        if (A->nnz > 0) LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
+        return LL_OK;
+    }
+    {
+        // the reverse recurrence uses B^T = B: refuse a matrix that is not symmetric
+        WS(sflag, int*, "bw_sym_flag", sizeof(int));
+        LL_CK(cudaMemsetAsync(sflag, 0, sizeof(int), s));
+        LL_CK(launch_check_symmetric(A->rowptr, A->colind, A->values, A->dtype, n, h->kept_sorted ? 1 : 0, sflag, s));
+        h->launches++;
+        int hs = 0;
+        LL_CK(cudaMemcpyAsync(&hs, sflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LL_CK(cudaStreamSynchronize(s));
+        if (hs) return fail(h, LL_ERR_INVALID_ARG, "A is not symmetric (the adjoint uses A^T = A)");
+    }
+    LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
     auto it_v = h->ws.find(wt == T_F64 ? "fw_basis" : "fw_V");
     if (it_v == h->ws.end()) return fail(h, LL_ERR_NO_FORWARD, "kept basis missing");
     const void* V = it_v->second.p;
@@ -893,6 +912,13 @@ void ll_default_options(ll_options* o) {
 ll_status ll_debug_inject(ll_handle* h, int what) {
     if (!h || what < LL_INJECT_NONE || what > LL_INJECT_STALL) return LL_ERR_INVALID_ARG;
     h->inject = what;
+    return LL_OK;
+}
+
+ll_status ll_set_keep_budget(ll_handle* h, int64_t bytes) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    if (bytes < 0) return fail(h, LL_ERR_INVALID_ARG, "negative keep budget");
+    h->keep_budget = bytes;
     return LL_OK;
 }
 
@@ -1228,9 +1254,10 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             auto it = h->ws.find(nm);
             if (it != h->ws.end()) have += it->second.bytes;
         }
-        const double budget = 0.5 * (double)(fr + have);
+        const double budget = h->keep_budget > 0 ? (double)h->keep_budget : 0.5 * (double)(fr + have);
         // every W_j if they fit; else the checkpoints at the smallest stride that fits, at most the
         // backward's own ceil(sqrt(m)): written here, they spare the backward its first sweep
+        // (when not even that fits, the forward keeps none and the backward checkpoints itself)
         const int smax = std::max(2, (int)std::ceil(std::sqrt((double)m)));
         if ((double)m * (double)blk2 <= budget) {
             wstride = 1;
@@ -1238,7 +1265,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         } else {
             for (int st_ = 2; st_ <= smax; ++st_) {
                 const int nb = (m + st_ - 1) / st_ - 1;
-                if ((double)nb * (double)blk2 <= budget || st_ == smax) {
+                if ((double)nb * (double)blk2 <= budget) {
                     wstride = st_;
                     wblocks = nb;
                     break;
@@ -1519,6 +1546,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     I.deg_mean_pass2 = b2 > 0 ? dsum / b2 : 0.0;
     I.kept_w_steps = wall ? wblocks : 0;
     I.kept_w_steps_pass1 = wall_s ? m : 0;
+    I.kept_w_stride = wall ? wstride : 0;
+    I.forward_id = ++h->forward_id;
     h->last_deg1 = deg1;
     h->last_deg2 = deg2;
     h->have_forward = true;
@@ -1536,6 +1565,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_wall_s = wall_s != nullptr;
         h->kept_far = h->far_entries;
         h->kept_max_row = h->max_row;
+        h->kept_sorted = h->sorted;
         h->kept_m = m;
         h->kept_prec = prec;
         h->kept_ckpt = o.ckpt_stride;

@@ -82,6 +82,10 @@ constexpr int TMA_HALO = 2;
 // unsorted (optional): rows whose column indices are not strictly increasing
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz,
                                 int* flag, cudaStream_t s, int* rowmax = nullptr, int* unsorted = nullptr);
+// flag[0] |= 1 when some stored entry (r, c) has no stored (c, r) of the same value; sorted: every
+// row's columns strictly increase (the search is then binary)
+cudaError_t launch_check_symmetric(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype, int n,
+                                   int sorted, int* flag, cudaStream_t s);
 cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype,
                               int n, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
 // out[e] = convert(values[e] * scale) into the storage type of `precision`

@@ -97,6 +97,46 @@ cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, in
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------- symmetry of a CSR matrix
+// flag[0] = 1 when some stored entry (r, c, v) has no stored partner (c, r) with the same value
+// (bit for bit). sorted: every row's columns strictly increase (binary search), else a scan.
+template <typename T>
+__global__ void k_check_symmetric(const int32_t* rowptr, const int32_t* colind, const T* vals, int n, int sorted,
+                                  int* flag) {
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += gridDim.x * (blockDim.x >> 5)) {
+        const int k0 = rowptr[r], k1 = rowptr[r + 1];
+        bool bad = false;
+        for (int k = k0 + (threadIdx.x & 31); k < k1; k += 32) {
+            const int c = colind[k];
+            const T v = vals[k];
+            int lo = rowptr[c], hi = rowptr[c + 1];
+            bool found = false;
+            if (sorted) {
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int cm = colind[mid];
+                    if (cm == r) { found = vals[mid] == v; break; }
+                    if (cm < r) lo = mid + 1; else hi = mid;
+                }
+            } else {
+                for (int t = lo; t < hi && !found; ++t) found = colind[t] == r && vals[t] == v;
+            }
+            bad = bad || !found;
+        }
+        if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+    }
+}
+
+cudaError_t launch_check_symmetric(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype, int n,
+                                   int sorted, int* flag, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (dtype == LL_F64)
+        k_check_symmetric<double><<<152 * 8, 256, 0, s>>>(rowptr, colind, static_cast<const double*>(vals), n, sorted, flag);
+    else
+        k_check_symmetric<float><<<152 * 8, 256, 0, s>>>(rowptr, colind, static_cast<const float*>(vals), n, sorted, flag);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------------- Gershgorin (Section 3)
 template <typename T>
 __global__ void k_gershgorin(const int32_t* rowptr, const int32_t* colind, const T* vals, int n,

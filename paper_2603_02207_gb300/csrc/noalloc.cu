@@ -9,8 +9,9 @@
 //
 // Contract:
 //   * at most LL_NOALLOC_MAX_ROWS rows (the array holds two FP64 vectors of that length plus the
-//     reduction scratch: 2 * 262,144 * 8 B + ~5 KB, about 4.2 MB, held on every GPU that loads the
-//     library until the process exits); larger matrices are rejected with LL_ERR_UNSUPPORTED;
+//     reduction scratch: 2 * 262,144 * 8 B + 32 KB, about 4.2 MB, held on every GPU that loads the
+//     library until the process exits); larger matrices are rejected with LL_ERR_UNSUPPORTED, and
+//     so are parts with more than 1024 SMs;
 //   * the first call on a device looks up the array's device address (cudaGetSymbolAddress) with
 //     that device current; make that first call before any stream capture;
 //   * every call reuses the same array and leaves its last contents there; the ticket and the
@@ -26,7 +27,10 @@
 namespace ll {
 namespace {
 
-constexpr int kNoAllocGrid = 608;     // CTAs of the reduction kernels (4 per SM on GB300)
+// The reduction kernels run 4 CTAs per SM, the grid of ll_power_lmax, so both entry points sum
+// their partials in the same order on any part; the partials slot is sized for up to 1024 SMs.
+constexpr int kNoAllocMaxSms = 1024;
+constexpr int kNoAllocGrid = 4 * kNoAllocMaxSms;
 // layout in doubles: x[MAX_ROWS] | y[MAX_ROWS] | partials[kNoAllocGrid] | nrm | ticket+flags
 constexpr size_t kNoAllocDoubles = 2 * (size_t)LL_NOALLOC_MAX_ROWS + kNoAllocGrid + 8;
 
@@ -72,10 +76,14 @@ extern "C" ll_status ll_power_lmax_noalloc(const ll_csr* A, int iters, uint64_t 
     double* nrm = partials + kNoAllocGrid;
     unsigned int* ticket = reinterpret_cast<unsigned int*>(nrm + 2);
     int* flag = reinterpret_cast<int*>(nrm + 4);
-    int sms = 152;
+    int sms = 0;
     int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (4 * sms < kNoAllocGrid) ? 4 * sms : kNoAllocGrid;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LL_ERR_CUDA;
+    }
+    if (sms < 1 || sms > kNoAllocMaxSms) return LL_ERR_UNSUPPORTED;
+    const int grid = 4 * sms;   // as ll_power_lmax
 
 #define NA_CK(expr) do { if ((expr) != cudaSuccess) { cudaGetLastError(); return LL_ERR_CUDA; } } while (0)
     // start-of-call state: ticket and validation flags at zero

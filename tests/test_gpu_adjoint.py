@@ -256,3 +256,80 @@ def test_backward_from_kept_w_on_a_banded_matrix(L, h):
         assert (info["kernel_pass2"] == L.LL_KERNEL_BAND) == (ckpt != 0)
         out[ckpt] = L.ll_logdet_backward(h, dA, 1.0)
     assert out[0].equal(out[3])
+
+
+@pytest.mark.parametrize("prec", ["df64", "f32"])
+def test_backward_from_forward_written_checkpoints(L, h, prec):
+    """A keep budget too small for every W_j but large enough for the checkpoints at stride 3
+    (5.5 blocks: stride 2 needs 8, stride 3 needs ceil(17/3) - 1 = 5): the trace pass writes W_3,
+    W_6, ..., W_15 for the backward, which then recomputes only inside segments. Both gradients
+    are bit-identical to an explicit ckpt_stride = 3 (the backward checkpoints itself), and the
+    kept checkpoints survive a first backward. Under a budget below the largest stride's 3
+    blocks nothing is kept and the result is the same."""
+    A = random_spd(900, nnz_per_row=6, seed=11, empty_rows=2)
+    lo, hi = O.gershgorin(A)
+    lmin = max(lo, 0.05)
+    m, probes = 17, 21
+    dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+    l2 = 16 if prec == "f32" else 14                      # [Q | G'] block: 14 columns
+    blk = A.n * l2 * (4 if prec == "f32" else 8)
+    out = {}
+    try:
+        for name, budget, ckpt in (("fwd", int(5.5 * blk), 0), ("bwd", 0, 3), ("none", int(2.5 * blk), 0)):
+            h.set_keep_budget(budget)
+            L.ll_logdet_forward(h, dA, lmin, hi, L.options(degree=m, probes=probes, seed=5, precision=prec,
+                                                            keep_for_backward=True, ckpt_stride=ckpt))
+            info = h.info()
+            want_stride, want_steps = {"fwd": (3, 5), "bwd": (0, 0), "none": (0, 0)}[name]
+            assert (info["kept_w_stride"], info["kept_w_steps"]) == (want_stride, want_steps)
+            g1 = L.ll_logdet_backward(h, dA, 1.0)
+            gq = L.ll_logdet_backward(h, dA, 1.0, through_qr=True)
+            g2 = L.ll_logdet_backward(h, dA, 1.0)
+            assert g1.equal(g2)
+            out[name] = (g1, gq)
+    finally:
+        h.set_keep_budget(0)
+    for name in ("bwd", "none"):
+        assert out["fwd"][0].equal(out[name][0])
+        assert out["fwd"][1].equal(out[name][1])
+    ref = O.logdet_leja(A, lmin, hi, m, probes, 5)
+    want = O.hutchpp_grad_values(A, lmin, hi, m, ref["Q"], ref["Gp"])
+    assert rel_err(out["fwd"][0].cpu().numpy(), want) < (1e-9 if prec != "f32" else 1e-4)
+
+
+def test_backward_rejects_a_nonsymmetric_matrix(L, h):
+    """The reverse recurrence uses B^T = B: a stored (r, c) whose (c, r) partner differs fails."""
+    A = random_spd(400, seed=3)
+    lo, hi = O.gershgorin(A)
+    vals = np.array(A.values, dtype=np.float64)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    e = int(np.nonzero(np.asarray(A.colind) != rows)[0][0])
+    dA = L.DeviceCSR.from_host(A)
+    L.ll_logdet_forward(h, dA, max(lo, 0.05), hi, L.options(degree=10, probes=6, seed=1, keep_for_backward=True))
+    assert L.ll_logdet_backward(h, dA, 1.0).shape[0] == A.nnz
+    vals[e] *= 1.5
+    dA.values.copy_(need_gpu().as_tensor(vals))
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_logdet_backward(h, dA, 1.0)
+    assert ei.value.name == "LL_ERR_INVALID_ARG"
+
+
+def test_autograd_refuses_a_stale_forward(L):
+    """The handle keeps only its last forward: differentiating an earlier estimate on the same
+    handle is refused, not answered with the later forward's gradient."""
+    torch = need_gpu()
+    h2 = L.Handle()
+    A, B = laplacian_2d(20, 0.1), laplacian_2d(20, 0.2)
+    dA, dB = L.DeviceCSR.from_host(A), L.DeviceCSR.from_host(B)
+    va = dA.values.clone().requires_grad_(True)
+    vb = dB.values.clone().requires_grad_(True)
+    ea = L.logdet(va, dA.rowptr, dA.colind, A.n, (0.1, 8.1), 20, 6, 1, handle=h2)
+    eb = L.logdet(vb, dB.rowptr, dB.colind, B.n, (0.2, 8.2), 20, 6, 1, handle=h2)
+    eb.backward()
+    assert vb.grad is not None
+    with pytest.raises(L.LejaError) as ei:
+        ea.backward()
+    assert ei.value.name == "LL_ERR_NO_FORWARD"
+    with pytest.raises(L.LejaError):
+        h2.set_keep_budget(-1)
+    del torch

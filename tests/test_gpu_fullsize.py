@@ -128,3 +128,37 @@ def test_config5_powerlaw_reduced_size(L, h, prec):
     want = O.logdet_leja(A, lmin, lmax, 150, 120, 3)["estimate"]
     assert abs(got - want) / abs(want) < TOL[prec]
     assert math.isfinite(got)
+
+
+@pytest.fixture(scope="module")
+def lap3d_80():
+    return laplacian_3d(80, 0.05)
+
+
+@pytest.fixture(scope="module")
+def oracle_80(lap3d_80):
+    cache = {}
+
+    def get(f32: bool):
+        if f32 not in cache:
+            cache[f32] = O.logdet_leja(lap3d_80, 0.05, 12.05, 20, 99, 4, f32=f32)
+        return cache[f32]
+    return get
+
+
+@pytest.mark.parametrize("prec", ["df64", "f64", "f32"])
+def test_hutchpp_multi_tile_gram_matches_oracle(L, h, lap3d_80, oracle_80, prec):
+    """80^3 Laplacian + 0.05 I (n = 512,000), Hutch++ with k = 33, degree 20: large enough that
+    every CTA of the CholeskyQR2 Gram launches sums more than QR_FLUSH = 8 row tiles (13 tiles of
+    128 rows per CTA for Y^T Y, 26 of 64 rows for Q^T G) before the running double-float sum and
+    the fixed-order reduction of 304 CTA partials. The estimate and G' = (I - Q Q^T) G (unique for
+    the span, so compared element by element) against the oracle's Householder path."""
+    A = lap3d_80
+    dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
+    opts = L.options(degree=20, probes=99, seed=4, precision=prec, keep_for_backward=True)
+    got = L.ll_logdet_forward(h, dA, 0.05, 12.05, opts)
+    ref = oracle_80(prec == "f32")
+    assert abs(got - ref["estimate"]) < TOL[prec] * abs(ref["estimate"])
+    Q, Gp = (t.cpu().numpy() for t in L.ll_kept_basis(h))
+    assert rel_err(Gp, ref["Gp"]) < TOL[prec]
+    assert np.max(np.abs(Q.T @ Q - np.eye(33))) < (1e-12 if prec != "f32" else 1e-6)

@@ -137,7 +137,7 @@ def test_divided_differences_nonconvergence_is_an_error():
         divdiff.divided_differences(xi, 5.0, 2.4, s=5.0, max_terms=50)
 
 
-def test_taylor_term_counts_match_survey_checks():
+def test_taylor_term_counts_grow_with_condition_number():
     # s = c gives |z/s - 1| <= (k-1)/(k+1); the term counts grow with the condition number
     _, _, _, _, p1 = logdet.newton_leja_setup(1.0, 81.0, 39)
     _, _, _, _, p3 = logdet.newton_leja_setup(1.0, 8080.0, 80)
@@ -260,6 +260,45 @@ def test_power_iteration_bounds_lmax():
     lp = logdet.power_iteration_lmax(A, iters=20, seed=3)
     assert lp <= lam[-1] * (1 + 1e-12)
     assert lp >= 0.8 * lam[-1]
+
+
+def _power_closed_form(a: np.ndarray, c: np.ndarray, k: int) -> float:
+    # A = U diag(a) U^T and c = U^T r for the start vector r: after k normalised steps
+    # v_k = A^k r / ||A^k r||, so v_k^T A v_k = sum a_i^(2k+1) c_i^2 / sum a_i^(2k) c_i^2
+    w = c * c
+    return float(np.sum(a ** (2 * k + 1) * w) / np.sum(a ** (2 * k) * w))
+
+
+@pytest.mark.parametrize("k", [0, 1, 3, 20])
+def test_power_iteration_closed_form_diagonal(k):
+    # diagonal A: U = I, and the Rademacher start vector has r_i^2 = 1, so the Rayleigh quotient
+    # after k steps is sum a^(2k+1) / sum a^(2k) -- not ||A v_k||, and a different k gives a
+    # different value (the spread of a keeps the iteration far from converged)
+    a = np.linspace(1.0, 2.0, 50)
+    got = logdet.power_iteration_lmax(diagonal(a), iters=k, seed=5)
+    assert got == pytest.approx(_power_closed_form(a, np.ones_like(a), k), rel=1e-13)
+    if k > 0:
+        assert abs(got - _power_closed_form(a, np.ones_like(a), k - 1)) > 1e-6
+        assert abs(got - _power_closed_form(a, np.ones_like(a), k + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 4, 20])
+def test_power_iteration_closed_form_reflected(k):
+    # A = H diag(a) H with the Householder reflector H = I - 2 u u^T / u^T u (H = H^T = H^-1):
+    # c = H r depends on the signs of the start vector, so the value pins the generator stream
+    # (LL_STREAM_POWER = 2) and the seed as well as the iteration
+    n = 40
+    a = np.linspace(0.5, 3.0, n)
+    u = np.cos(np.arange(n) * 0.7) + 0.3
+    H = np.eye(n) - 2.0 * np.outer(u, u) / (u @ u)
+    A = csr_from_dense(H @ np.diag(a) @ H)
+    seed = 11
+    r = rng.rademacher(seed, rng.STREAM_POWER, n, 1)[:, 0]
+    got = logdet.power_iteration_lmax(A, iters=k, seed=seed)
+    assert got == pytest.approx(_power_closed_form(a, H @ r, k), rel=1e-12)
+    for stream in (rng.STREAM_S, rng.STREAM_G):
+        r_other = rng.rademacher(seed, stream, n, 1)[:, 0]
+        assert abs(got - _power_closed_form(a, H @ r_other, k)) > 1e-8
 
 
 def test_sigma_rule():

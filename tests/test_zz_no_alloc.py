@@ -2,8 +2,10 @@
 
 ll_power_lmax_noalloc exists for callers that cannot allocate device memory: code whose device
 memory belongs to another allocator, or code that cannot afford the implicit synchronisation of
-cudaMalloc/cudaFree. It must return what the allocating entry point returns, call after call,
-although every call reuses the same library-owned scratch array.
+cudaMalloc/cudaFree. It runs the kernels of the allocating entry point with the same grid and
+reduction order, so it must return exactly what that entry point returns, call after call,
+although every call reuses the same library-owned scratch array; and it must not take device
+memory.
 """
 from __future__ import annotations
 
@@ -24,7 +26,23 @@ def test_noalloc_power_iteration_matches_allocating_entry_point():
         want = L.ll_power_lmax(h, dA, iters=iters, seed=seed)
         for _ in range(2):                       # two calls in a row reuse the same scratch
             got = L.ll_power_lmax_noalloc(dA, iters=iters, seed=seed)
-            assert got == pytest.approx(want, rel=1e-12)
+            assert got == want                   # same kernels, grid and summation order
+
+
+def test_noalloc_power_iteration_takes_no_device_memory():
+    import torch
+    L = lib()
+    A = laplacian_2d(400, 0.1)
+    dA = L.DeviceCSR.from_host(A)
+    L.ll_power_lmax_noalloc(dA, iters=5, seed=0)    # first call: the scratch address is looked up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    vals = [L.ll_power_lmax_noalloc(dA, iters=20, seed=s) for s in range(10)]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    # any workspace allocation takes at least one 2 MiB page of device memory
+    assert free0 - free1 < (1 << 20), (free0, free1)
+    assert all(v > 0 for v in vals)
 
 
 def test_noalloc_power_iteration_rejects_too_many_rows():
