@@ -122,7 +122,8 @@ typedef struct {
     int precision;             /* LL_PREC_*                                                      */
     int sval_mode;             /* LL_SVAL_*                                                      */
     int keep_for_backward;     /* 1: keep [Q | G'] and the coefficients for ll_logdet_backward   */
-    int rows_per_thread;       /* LL_KERNEL_GATHER: rows each thread handles per tile (0 = 8)    */
+    int rows_per_thread;       /* LL_KERNEL_GATHER: rows each thread handles per tile (0 = 8);
+                                  LL_KERNEL_TMA: 2 = two column pairs per thread (FP32-mixed)   */
     int threads_per_block;     /* CTA size of the step kernel (0 = kernel default: 384 or 512
                                   for LL_KERNEL_GATHER, 512 for LL_KERNEL_TMA; a TMA CTA of at
                                   most 256 threads runs two per SM). Ignored by LL_KERNEL_AUTO.  */
@@ -174,6 +175,8 @@ typedef struct {
     int64_t forward_id;                 /* 1 + the number of earlier successful forwards on the
                                            handle: a caller that keeps it can tell whether the
                                            handle's kept state is still that of its forward     */
+    int pairs_pass1, pairs_pass2;       /* column pairs per thread of each pass's step kernel (2:
+                                           the FP32-mixed TMA kernel with 16-byte row accesses)  */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */

@@ -41,13 +41,14 @@ struct ll_handle {
     int inject = LL_INJECT_NONE;            // ll_debug_inject
     bool tma_used = false;                  // a TMA step ran since the last error-flag check
     int last_kernel = 0, last_threads = 0;  // choice of the last run_pass
+    int last_np = 1;                        // and its column pairs per thread
     // CUDA graph of the last forward's device work (replayed when the next call is identical)
     uint64_t ws_gen = 0;                    // bumped whenever a workspace buffer moves
     cudaStream_t cap_stream = nullptr;      // capture stream (the caller's may be the legacy stream)
     struct Graph {
         std::vector<unsigned char> key;
         cudaGraphExec_t exec = nullptr;
-        int launches = 0, k1 = 0, t1 = 0, k2 = 0, t2 = 0;
+        int launches = 0, k1 = 0, t1 = 0, k2 = 0, t2 = 0, np1 = 1, np2 = 1;
         bool tma = false;
     } gfwd;
     // CUDA graph of the last batched call's device work, with what the host combine needs
@@ -234,8 +235,10 @@ bool plan_exec(ll_handle* h, int kind, int precision, int mode, int n, int64_t n
     E.threads = threads;
     E.rpt = rpt;
     if (kind == LL_KERNEL_TMA) {
+        // rpt = 2 selects two column pairs per consumer thread (FP32-mixed blocks)
         const int ctas = (threads > 0 && threads <= 256) ? 2 : 1;
-        if (!plan_step_tma(precision, mode, n, nnz, h->far_entries, h->max_row, b, threads, ctas, p, E.tl, h->sm_count))
+        if (!plan_step_tma(precision, mode, n, nnz, h->far_entries, h->max_row, b, threads, ctas, p, E.tl, h->sm_count,
+                           rpt == 2 ? 2 : 1))
             return false;
         E.tl.q.spin_budget = h->spin_budget;
         E.tl.q.inject = h->inject;
@@ -310,7 +313,7 @@ ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz,
     ll_status st;
     if (kernel == LL_KERNEL_TMA) {
         StepParams q = p;
-        if (plan_exec(h, LL_KERNEL_TMA, precision, mode, n, nnz, b, threads, 0, q, E)) {
+        if (plan_exec(h, LL_KERNEL_TMA, precision, mode, n, nnz, b, threads, rpt, q, E)) {
             p = q;
             return bind_exec(h, precision, mode, b, E, p, s);
         }
@@ -330,8 +333,10 @@ ll_status choose_exec(ll_handle* h, int precision, int mode, int n, int64_t nnz,
         return bind_exec(h, precision, mode, b, E, p, s);
     }
     struct Cand { int kind, threads, rpt; };
-    const Cand cands[] = {{LL_KERNEL_TMA, 512, 0}, {LL_KERNEL_TMA, 256, 0}, {LL_KERNEL_GATHER, 0, 8},
-                          {LL_KERNEL_GATHER, 0, 4}, {LL_KERNEL_GATHER, 0, 2}, {LL_KERNEL_GATHER, 256, 2}};
+    // (TMA candidates with rpt = 2 take two column pairs per thread; FP32-mixed only)
+    const Cand cands[] = {{LL_KERNEL_TMA, 512, 0}, {LL_KERNEL_TMA, 256, 0}, {LL_KERNEL_TMA, 512, 2},
+                          {LL_KERNEL_TMA, 256, 2}, {LL_KERNEL_GATHER, 0, 8}, {LL_KERNEL_GATHER, 0, 4},
+                          {LL_KERNEL_GATHER, 0, 2}, {LL_KERNEL_GATHER, 256, 2}};
     float best_ms = 0.f;
     Cand best{LL_KERNEL_GATHER, 0, 8};
     bool have = false;
@@ -434,6 +439,7 @@ ll_status run_band_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, in
     }
     h->last_kernel = LL_KERNEL_BAND;
     h->last_threads = BAND_THREADS;
+    h->last_np = 1;
     return LL_OK;
 }
 
@@ -515,6 +521,7 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     }
     h->last_kernel = E.kind;
     h->last_threads = E.cta();
+    h->last_np = E.kind == LL_KERNEL_TMA ? E.tl.np : 1;
     const int nslot = store_stride > 1 ? (m + store_stride - 1) / store_stride - 1 : m;
     const void* cur = win0;
     for (int j = 0; j < m; ++j) {
@@ -1285,7 +1292,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             wstride = 0;
         }
     }
-    int k1 = 0, t1 = 0;   // step kernel and CTA size of pass 1
+    int k1 = 0, t1 = 0, np1 = 1;   // step kernel, CTA size and column pairs per thread of pass 1
 
     // the device work of the call (Algorithm 3 steps 2-6), enqueued on q; with capture, the
     // phase events become event-record nodes of the graph
@@ -1338,6 +1345,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             if (st != LL_OK) return st;
             k1 = h->last_kernel;
             t1 = h->last_threads;
+            np1 = h->last_np;
             LL_CK(rec(h->ev[2], q));
 
             // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']. Outside the
@@ -1419,8 +1427,10 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->launches += gr.launches;
         k1 = gr.k1;
         t1 = gr.t1;
+        np1 = gr.np1;
         h->last_kernel = gr.k2;
         h->last_threads = gr.t2;
+        h->last_np = gr.np2;
         h->tma_used = gr.tma;
     } else {
         const int before = h->launches;
@@ -1440,7 +1450,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             cudaGraph_t graph = nullptr;
             LL_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
             capturing = true;
-            const int kk1 = k1, tt1 = t1, kk2 = h->last_kernel, tt2 = h->last_threads;
+            const int kk1 = k1, tt1 = t1, kk2 = h->last_kernel, tt2 = h->last_threads, nn1 = np1, nn2 = h->last_np;
             const int cap0 = h->launches;
             ll_status cst = enqueue(h->cap_stream);
             const int in_graph = h->launches - cap0;   // without the autotuner's launches of the eager run
@@ -1454,6 +1464,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
                 gr.t1 = tt1;
                 gr.k2 = kk2;
                 gr.t2 = tt2;
+                gr.np1 = nn1;
+                gr.np2 = nn2;
                 gr.tma = tma;
             } else {
                 gr.exec = nullptr;
@@ -1466,6 +1478,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             t1 = tt1;
             h->last_kernel = kk2;
             h->last_threads = tt2;
+            np1 = nn1;
+            h->last_np = nn2;
             h->tma_used = tma;
         }
     }
@@ -1535,6 +1549,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     I.threads_pass1 = t1;
     I.kernel_pass2 = h->last_kernel;
     I.threads_pass2 = h->last_threads;
+    I.pairs_pass1 = np1;
+    I.pairs_pass2 = h->last_np;
     I.deg_max_pass1 = 0;
     for (int v : deg1) I.deg_max_pass1 = v > I.deg_max_pass1 ? v : I.deg_max_pass1;
     I.deg_max_pass2 = 0;

@@ -299,6 +299,7 @@ struct TmaParams {
 };
 struct TmaLaunch {
     TmaParams q;
+    int np = 1;       // column pairs per consumer thread (2: FP32-mixed, 16-byte row accesses)
     int threads, grid;
     size_t smem;
     size_t desc_bytes, gcol_bytes, meta_bytes;   // global descriptor arrays of the pass
@@ -309,7 +310,7 @@ struct TmaLaunch {
 // nfar: entries with |col - row| > TMA_HALO; maxrow: the longest row (both size the per-tile record
 // and gather capacities; hints, not bounds)
 bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int maxrow, int b, int threads_target,
-                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count);
+                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count, int np = 1);
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s);
 // builds the tile descriptors of a plan (L.q.desc_w, gcol_w, meta_w) from the CSR and the prepared
 // values in p; once per pass, before its steps

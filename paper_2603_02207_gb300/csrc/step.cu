@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(step_max_threads<PREC>(), 2) k_leja_step(const
 
     if constexpr (MB == MODE_DOT || stop_mode(MODE)) {
         __shared__ bool s_last;
-        trace_reduce<PREC, MODE>(p, T, reinterpret_cast<double*>(smem), tp, p.rl, &s_last);
+        trace_reduce<PREC, MODE>(p, &T, reinterpret_cast<double*>(smem), tp, p.rl, &s_last);
     }
 }
 

@@ -169,45 +169,54 @@ __device__ __forceinline__ void row_epilogue(const StepParams& p, const StepScal
 // per-CTA partials in CTA order (both orders fixed: the result is deterministic). Quantities:
 // 0 = V . W_{j+1} and 1 = V . W_0 (first step) in the DOT modes, 2 = ||W_{j+1}||^2 in the STOP
 // modes, where the last CTA then applies Algorithm 2's test |d_{j+1}| ||W_{j+1}|| > tol to every
-// live column. `red` must hold 2 * blockDim.x doubles; every thread of the CTA calls this.
-template <int PREC, int MODE>
-__device__ __forceinline__ void trace_reduce(const StepParams& p, TracePart& T, double* red, int tp, int rows,
+// live column. A thread holds NP consecutive column pairs (T[0..NP-1]): thread (row lane l,
+// column group g) of `tp` groups per row owns columns 2 NP g .. 2 NP g + 2 NP - 1. `red` must hold
+// 2 NP * blockDim.x doubles; every thread of the CTA calls this.
+template <int PREC, int MODE, int NP = 1>
+__device__ __forceinline__ void trace_reduce(const StepParams& p, TracePart* T, double* red, int tp, int rows,
                                              bool* s_last) {
     constexpr int MB = base_mode(MODE);
     constexpr bool STOP = stop_mode(MODE);
+    constexpr int CW = 2 * NP;   // columns per thread
     const int tid = threadIdx.x;
     if constexpr (PREC != LL_PREC_F64) {
-        float h0, h1, l0, l1;
-        if constexpr (MB == MODE_DOT) {
-            f2_unpack(T.th2, h0, h1);
-            f2_unpack(T.tl2, l0, l1);
-            T.td[0] = (double)h0 + (double)l0;
-            T.td[1] = (double)h1 + (double)l1;
-            f2_unpack(T.t0h2, h0, h1);
-            f2_unpack(T.t0l2, l0, l1);
-            T.t0d[0] = (double)h0 + (double)l0;
-            T.t0d[1] = (double)h1 + (double)l1;
-        }
-        if constexpr (STOP) {
-            f2_unpack(T.nh2, h0, h1);
-            f2_unpack(T.nl2, l0, l1);
-            T.nd[0] = (double)h0 + (double)l0;
-            T.nd[1] = (double)h1 + (double)l1;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float h0, h1, l0, l1;
+            if constexpr (MB == MODE_DOT) {
+                f2_unpack(T[q].th2, h0, h1);
+                f2_unpack(T[q].tl2, l0, l1);
+                T[q].td[0] = (double)h0 + (double)l0;
+                T[q].td[1] = (double)h1 + (double)l1;
+                f2_unpack(T[q].t0h2, h0, h1);
+                f2_unpack(T[q].t0l2, l0, l1);
+                T[q].t0d[0] = (double)h0 + (double)l0;
+                T[q].t0d[1] = (double)h1 + (double)l1;
+            }
+            if constexpr (STOP) {
+                f2_unpack(T[q].nh2, h0, h1);
+                f2_unpack(T[q].nl2, l0, l1);
+                T[q].nd[0] = (double)h0 + (double)l0;
+                T[q].nd[1] = (double)h1 + (double)l1;
+            }
         }
     }
     const int b = p.b;
-    for (int q = 0; q < 3; ++q) {
-        if (q < 2 && MB != MODE_DOT) continue;
-        if (q == 1 && !p.first) continue;
-        if (q == 2 && !STOP) continue;
-        red[2 * tid] = q == 0 ? T.td[0] : (q == 1 ? T.t0d[0] : T.nd[0]);
-        red[2 * tid + 1] = q == 0 ? T.td[1] : (q == 1 ? T.t0d[1] : T.nd[1]);
+    for (int qn = 0; qn < 3; ++qn) {
+        if (qn < 2 && MB != MODE_DOT) continue;
+        if (qn == 1 && !p.first) continue;
+        if (qn == 2 && !STOP) continue;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            red[CW * tid + 2 * q] = qn == 0 ? T[q].td[0] : (qn == 1 ? T[q].t0d[0] : T[q].nd[0]);
+            red[CW * tid + 2 * q + 1] = qn == 0 ? T[q].td[1] : (qn == 1 ? T[q].t0d[1] : T[q].nd[1]);
+        }
         __syncthreads();
         for (int c = tid; c < b; c += blockDim.x) {
-            const int pc = c >> 1, lane = c & 1;
+            const int pc = c / CW, e = c - pc * CW;
             double s = 0.0;
-            for (int l = 0; l < rows; ++l) s += red[2 * (l * tp + pc) + lane];
-            p.partials[((size_t)q * gridDim.x + blockIdx.x) * b + c] = s;
+            for (int l = 0; l < rows; ++l) s += red[CW * (l * tp + pc) + e];
+            p.partials[((size_t)qn * gridDim.x + blockIdx.x) * b + c] = s;
         }
         __syncthreads();
     }

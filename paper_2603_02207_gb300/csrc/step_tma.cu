@@ -26,7 +26,32 @@
 
 namespace ll {
 
-template <int PREC, int MODE>
+// NP consecutive column pairs of W to or from a 16-byte aligned address (one 16-byte access for two
+// FP32 pairs)
+template <int NP, typename WP>
+__device__ __forceinline__ void ld_pairs(WP (&x)[NP], const void* a) {
+    if constexpr (NP == 2 && sizeof(WP) == 8) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(a);
+        x[0] = v.x;
+        x[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) x[q] = reinterpret_cast<const WP*>(a)[q];
+    }
+}
+template <int NP, typename WP>
+__device__ __forceinline__ void st_pairs(WP* a, const WP (&x)[NP]) {
+    if constexpr (NP == 2 && sizeof(WP) == 8) {
+        *reinterpret_cast<ulonglong2*>(a) = make_ulonglong2(x[0], x[1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) a[q] = x[q];
+    }
+}
+
+// NP: column pairs per consumer thread (1; or 2 in the FP32-mixed mode, whose rows are whole
+// 16-byte units: one 16-byte load feeds both pairs, and a tile holds twice the rows)
+template <int PREC, int MODE, int NP>
 __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     k_leja_tma(const __grid_constant__ CUtensorMap tm_gather, const __grid_constant__ CUtensorMap tm_win,
                const __grid_constant__ CUtensorMap tm_aux, const StepParams p, const TmaParams q) {
@@ -73,7 +98,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     const int my = (int)blockIdx.x < nt ? (nt - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int rstep = (int)gridDim.x * R;   // rows between this CTA's consecutive tiles
     bool dead = false;
-    TracePart T;
+    TracePart T[NP];
 
     if (tid >= cthreads) {
         // ------------------------------------------------------------------ producer warps
@@ -193,15 +218,17 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
         const Raw* __restrict__ vals = static_cast<const Raw*>(p.vals);
         PP* __restrict__ pblk = static_cast<PP*>(p.p);
         const int* __restrict__ colind = p.colind;
-        const StepScalars<PREC> S(p, cp, stop_mode(MODE) && MB == MODE_ACCUM);
-        const unsigned cpoff = (unsigned)(cp * sizeof(WP));
+        const int cp0 = cp * NP;   // the thread's first column pair
+        const StepScalars<PREC> S0(p, cp0, stop_mode(MODE) && MB == MODE_ACCUM);
+        const StepScalars<PREC> S1(p, cp0 + NP - 1, stop_mode(MODE) && MB == MODE_ACCUM);
+        const unsigned cpoff = (unsigned)(cp0 * sizeof(WP));
         const unsigned own_off = (unsigned)(rlane + TMA_HALO) * (unsigned)q.rowbytes + cpoff;
         const unsigned aux_off = (unsigned)q.off_aux + (unsigned)rlane * (unsigned)q.auxbytes +
-                                 (unsigned)(cp * (MB == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
+                                 (unsigned)(cp0 * (MB == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
         int s = 0, ph = 0;
         int r = (int)blockIdx.x * R + rlane;
-        WP* wo = wout + (size_t)r * ldq + cp;   // this thread's W_{j+1} and P pairs, advanced per tile
-        PP* po_ptr = pblk + (size_t)r * ldpq + cp;
+        WP* wo = wout + (size_t)r * ldq + cp0;   // this thread's W_{j+1} and P pairs, advanced per tile
+        PP* po_ptr = pblk + (size_t)r * ldpq + cp0;
         const size_t wstep = (size_t)rstep * ldq, pstep = (size_t)rstep * ldpq;
         for (int i = 0; i < my; ++i) {
             // every lane waits (acquiring the stage's copies); the warp gives up together
@@ -217,38 +244,64 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_desc + q.hdr_bytes);
                 const int k0 = srp[rlane], k1 = srp[rlane + 1];
                 const int g = srp[R + 2];
-                const WP wr = *reinterpret_cast<const WP*>(st + own_off);
-                WP vr{};
-                PP po{};
-                if constexpr (MB == MODE_DOT || MB == MODE_ADJ) vr = *reinterpret_cast<const WP*>(st + aux_off);
+                WP wr[NP], vr[NP] = {};
+                PP po[NP] = {};
+                ld_pairs<NP>(wr, st + own_off);
+                if constexpr (MB == MODE_DOT || MB == MODE_ADJ) ld_pairs<NP>(vr, st + aux_off);
                 if constexpr (MB == MODE_ACCUM) {
-                    if (!p.first) po = *reinterpret_cast<const PP*>(st + aux_off);
+                    if (!p.first) {
+#pragma unroll
+                        for (int qq = 0; qq < NP; ++qq) po[qq] = reinterpret_cast<const PP*>(st + aux_off)[qq];
+                    }
                 }
-                RowAcc A;
+                RowAcc A[NP];
                 const int kend = min(k1, g);
                 const unsigned char* stc = st + cpoff;
 #pragma unroll 4
                 for (int k = k0; k < kend; ++k) {
                     const RecT rk = rec[k];
-                    row_mac<PREC>(A, expand(rk.a), *reinterpret_cast<const WP*>(stc + rk.off));
+                    const auto ex = expand(rk.a);
+                    WP x[NP];
+                    ld_pairs<NP>(x, stc + rk.off);
+#pragma unroll
+                    for (int qq = 0; qq < NP; ++qq) row_mac<PREC>(A[qq], ex, x[qq]);
                 }
                 if (k1 > g) {   // beyond the records: direct loads, eight in flight, added in entry order
                     const int z0 = srp[R + 1];
                     int k = max(k0, g);
                     for (; k + 8 <= k1; k += 8) {
-                        WP x[8];
+                        WP x[8][NP];
                         Raw v[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             v[u] = vals[z0 + k + u];
-                            x[u] = win[(size_t)colind[z0 + k + u] * ldq + cp];
+                            ld_pairs<NP>(x[u], win + (size_t)colind[z0 + k + u] * ldq + cp0);
                         }
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) row_mac<PREC>(A, expand(v[u]), x[u]);
+                        for (int u = 0; u < 8; ++u) {
+                            const auto ex = expand(v[u]);
+#pragma unroll
+                            for (int qq = 0; qq < NP; ++qq) row_mac<PREC>(A[qq], ex, x[u][qq]);
+                        }
                     }
-                    for (; k < k1; ++k) row_mac<PREC>(A, expand(vals[z0 + k]), win[(size_t)colind[z0 + k] * ldq + cp]);
+                    for (; k < k1; ++k) {
+                        WP x[NP];
+                        ld_pairs<NP>(x, win + (size_t)colind[z0 + k] * ldq + cp0);
+                        const auto ex = expand(vals[z0 + k]);
+#pragma unroll
+                        for (int qq = 0; qq < NP; ++qq) row_mac<PREC>(A[qq], ex, x[qq]);
+                    }
                 }
-                row_epilogue<PREC, MODE>(p, S, A, wr, vr, po, wo, po_ptr, T);
+                WP wn[NP];
+                PP pn[NP];
+#pragma unroll
+                for (int qq = 0; qq < NP; ++qq)
+                    row_epilogue<PREC, MODE>(p, qq == 0 ? S0 : S1, A[qq], wr[qq], vr[qq], po[qq], &wn[qq], &pn[qq], T[qq]);
+                st_pairs<NP>(wo, wn);
+                if constexpr (MB == MODE_ACCUM) {
+#pragma unroll
+                    for (int qq = 0; qq < NP; ++qq) po_ptr[qq] = pn[qq];
+                }
             }
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[s]));
@@ -263,7 +316,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
     }
     const int any_dead = __syncthreads_or(dead ? 1 : 0);
     if constexpr (MB == MODE_DOT || stop_mode(MODE)) {
-        if (!any_dead) trace_reduce<PREC, MODE>(p, T, reinterpret_cast<double*>(smem), tp, R, &s_last);
+        if (!any_dead) trace_reduce<PREC, MODE, NP>(p, T, reinterpret_cast<double*>(smem), tp, R, &s_last);
     }
 }
 
@@ -271,32 +324,37 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
 
 namespace {
 
-template <int PREC, int MODE>
+template <int PREC, int MODE, int NP>
 int occupancy_tma(int threads, size_t smem) {
-    cudaFuncSetAttribute(k_leja_tma<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_leja_tma<PREC, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leja_tma<PREC, MODE>, threads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leja_tma<PREC, MODE, NP>, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return per_sm;
 }
 
-template <int PREC, int MODE>
+template <int PREC, int MODE, int NP>
 cudaError_t launch_tma_typed(const TmaLaunch& L, const CUtensorMap& g, const CUtensorMap& o, const CUtensorMap& a,
                              const StepParams& p, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_leja_tma<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    cudaError_t e = cudaFuncSetAttribute(k_leja_tma<PREC, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
-    k_leja_tma<PREC, MODE><<<L.grid, L.threads, L.smem, s>>>(g, o, a, p, L.q);
+    k_leja_tma<PREC, MODE, NP><<<L.grid, L.threads, L.smem, s>>>(g, o, a, p, L.q);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int maxrow, int b, int threads_target,
-                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count) {
+                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count, int np) {
     L = TmaLaunch{};
     if (n <= 0 || b <= 0 || !encode_fn()) return false;
+    // two column pairs per thread: FP32-mixed only, with rows of whole 16-byte units (the P rows
+    // of pass 1 are 16 bytes per pair, so any width qualifies there)
+    if (np != 1 && np != 2) return false;
+    if (np == 2 && (precision != LL_PREC_F32_MIXED || p.ldw % 4 != 0)) return false;
+    L.np = np;
     if (ctas_per_sm < 1 || ctas_per_sm > 2) ctas_per_sm = 1;
     const int ew = (int)elem_size(w_type_of(precision));
     const long long ld = p.ldw;
@@ -310,7 +368,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
         auxbytes = (int)(p.ldp * 8);
     }
     if (threads_target <= 0 || threads_target > 512) threads_target = 512 / ctas_per_sm;
-    const int tp = (b + 1) / 2;
+    const int tp = (b + 2 * np - 1) / (2 * np);
     int R = threads_target / tp;
     if (R < 1) R = 1;
     if (R > 256 - 2 * TMA_HALO) R = 256 - 2 * TMA_HALO;   // window box rows <= 256
@@ -357,7 +415,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     q.ring_base = q.nst * q.stage_bytes;
     L.smem = (size_t)q.ring_base + (size_t)nprod * TMA_GRING * q.gcol_stride;
     L.threads = ((R * tp + 31) / 32) * 32 + 32 * nprod;   // consumer warps and the producer warps
-    if (L.smem < (size_t)L.threads * 2 * sizeof(double)) L.smem = (size_t)L.threads * 2 * sizeof(double);
+    if (L.smem < (size_t)L.threads * 2 * np * sizeof(double)) L.smem = (size_t)L.threads * 2 * np * sizeof(double);
     L.smem += 128;
     p.tp = tp;
     p.rl = R;
@@ -369,11 +427,11 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     L.gcol_bytes = (size_t)p.num_tiles * q.gcol_stride;
     L.meta_bytes = (size_t)p.num_tiles * sizeof(int4);
     int per_sm = 0;
-    switch (precision * NUM_MODES + mode) {
-#define OCC(P_, M_) case P_ * NUM_MODES + M_: per_sm = occupancy_tma<P_, M_>(L.threads, L.smem); break;
-#define OCC4(P_) OCC(P_, MODE_PLAIN) OCC(P_, MODE_ACCUM) OCC(P_, MODE_DOT) OCC(P_, MODE_ADJ) \
-    OCC(P_, MODE_ACCUM_STOP) OCC(P_, MODE_DOT_STOP)
-        OCC4(LL_PREC_F64) OCC4(LL_PREC_DF64) OCC4(LL_PREC_F32_MIXED)
+    switch ((np - 1) * 3 * NUM_MODES + precision * NUM_MODES + mode) {
+#define OCC(N_, P_, M_) case (N_ - 1) * 3 * NUM_MODES + P_ * NUM_MODES + M_: per_sm = occupancy_tma<P_, M_, N_>(L.threads, L.smem); break;
+#define OCC4(N_, P_) OCC(N_, P_, MODE_PLAIN) OCC(N_, P_, MODE_ACCUM) OCC(N_, P_, MODE_DOT) OCC(N_, P_, MODE_ADJ) \
+    OCC(N_, P_, MODE_ACCUM_STOP) OCC(N_, P_, MODE_DOT_STOP)
+        OCC4(1, LL_PREC_F64) OCC4(1, LL_PREC_DF64) OCC4(1, LL_PREC_F32_MIXED) OCC4(2, LL_PREC_F32_MIXED)
 #undef OCC4
 #undef OCC
         default: break;
@@ -419,11 +477,11 @@ cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const S
     else if (base_mode(mode) == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, p.n, L.q.R);
     else a = w;
     if (!aux_ok) return cudaErrorInvalidValue;
-    switch (precision * NUM_MODES + mode) {
-#define LCH(P_, M_) case P_ * NUM_MODES + M_: return launch_tma_typed<P_, M_>(L, g, w, a, p, s);
-#define LCH4(P_) LCH(P_, MODE_PLAIN) LCH(P_, MODE_ACCUM) LCH(P_, MODE_DOT) LCH(P_, MODE_ADJ) \
-    LCH(P_, MODE_ACCUM_STOP) LCH(P_, MODE_DOT_STOP)
-        LCH4(LL_PREC_F64) LCH4(LL_PREC_DF64) LCH4(LL_PREC_F32_MIXED)
+    switch ((L.np - 1) * 3 * NUM_MODES + precision * NUM_MODES + mode) {
+#define LCH(N_, P_, M_) case (N_ - 1) * 3 * NUM_MODES + P_ * NUM_MODES + M_: return launch_tma_typed<P_, M_, N_>(L, g, w, a, p, s);
+#define LCH4(N_, P_) LCH(N_, P_, MODE_PLAIN) LCH(N_, P_, MODE_ACCUM) LCH(N_, P_, MODE_DOT) LCH(N_, P_, MODE_ADJ) \
+    LCH(N_, P_, MODE_ACCUM_STOP) LCH(N_, P_, MODE_DOT_STOP)
+        LCH4(1, LL_PREC_F64) LCH4(1, LL_PREC_DF64) LCH4(1, LL_PREC_F32_MIXED) LCH4(2, LL_PREC_F32_MIXED)
 #undef LCH4
 #undef LCH
         default: return cudaErrorInvalidValue;

@@ -27,10 +27,10 @@ def L():
     return lib()
 
 
-def _apply(L, A, lo, hi, m, V, prec, kernel, threads=0):
+def _apply(L, A, lo, hi, m, V, prec, kernel, threads=0, rpt=0):
     torch = need_gpu()
     h = L.Handle()
-    h.set_step_config(kernel, threads, 0)
+    h.set_step_config(kernel, threads, rpt)
     dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
     out = L.ll_apply_poly(h, dA, lo, hi, m, torch.as_tensor(V).cuda(), prec).cpu().numpy()
     return out, h.info()
@@ -195,3 +195,43 @@ def test_graph_replay_matches_eager(L):
     e5 = L.ll_logdet_forward(h, dA, 2 * lo, 2 * hi, o3)
     e5g = L.ll_logdet_forward(h2, dA, 2 * lo, 2 * hi, L.options(degree=15, probes=30, seed=3, use_graph=False, step_kernel="tma"))
     assert e5 == e5g
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("b", [1, 2, 7, 33, 66])
+@pytest.mark.parametrize("threads", [512, 256])
+def test_tma_two_pairs_per_thread_matches_gather_bitwise(L, name, b, threads):
+    """FP32-mixed, two column pairs per consumer thread (one 16-byte access per operand row and
+    twice the rows per tile): the same per-column arithmetic in the same entry order, so p(A)V
+    equals the register kernel's bit for bit, including the pad columns of widths that are not
+    multiples of four and the ragged last tile."""
+    A, lo, hi = _mat(name)
+    V = R.rademacher(7, R.STREAM_S, A.n, b)
+    g, _ = _apply(L, A, lo, hi, 12, V, "f32", "gather")
+    t, it = _apply(L, A, lo, hi, 12, V, "f32", "tma", threads=threads, rpt=2)
+    assert it["kernel_pass1"] == L.LL_KERNEL_TMA and it["pairs_pass1"] == 2
+    assert np.array_equal(g, t)
+
+
+def test_tma_two_pairs_per_thread_forward_and_backward(L):
+    """The trace pass (DOT), the adjoint's recompute (PLAIN) and reverse (ADJ) steps with two
+    column pairs per thread: the estimate equals the one-pair kernel's to rounding (the traces
+    are summed over another row grouping), and the value gradients are bit-identical (the SDDMM
+    reads the same W_j and Lambda_j)."""
+    need_gpu()
+    A, lo, hi = _mat("matern_60")
+    dA = L.DeviceCSR.from_host(A, "f32")
+    res = {}
+    for rpt in (0, 2):
+        h = L.Handle()
+        h.set_step_config("tma", 0, rpt)
+        est = L.ll_logdet_forward(h, dA, lo, hi, L.options(degree=20, probes=30, seed=4, precision="f32",
+                                                              keep_for_backward=True, step_kernel="tma",
+                                                              rows_per_thread=rpt))
+        info = h.info()
+        assert info["pairs_pass1"] == info["pairs_pass2"] == (2 if rpt == 2 else 1)
+        res[rpt] = (est, L.ll_logdet_backward(h, dA, 1.0).cpu().numpy())
+    assert abs(res[2][0] - res[0][0]) <= 1e-12 * abs(res[0][0])
+    assert np.array_equal(res[2][1], res[0][1])
+    want = O.logdet_leja(A, lo, hi, 20, 30, 4, f32=True)["estimate"]
+    assert abs(res[2][0] - want) / abs(want) < TOL["f32"]
