@@ -1079,6 +1079,7 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
     h->info = ll_info{};
     h->info.kernel_pass1 = h->last_kernel;
     h->info.threads_pass1 = h->last_threads;
+    h->info.pairs_pass1 = h->last_np;
     LL_CK(launch_block_to_f64(precision, pp, lb, PV, ldp, n, b, s));
     h->launches++;
     return check_tma_flag(h, s);
@@ -1125,6 +1126,7 @@ ll_status ll_apply_poly_tol(ll_handle* h, const ll_csr* A, ll_bounds bounds, int
     h->info = ll_info{};
     h->info.kernel_pass1 = h->last_kernel;
     h->info.threads_pass1 = h->last_threads;
+    h->info.pairs_pass1 = h->last_np;
     LL_CK(launch_block_to_f64(precision, pp, lb, PV, ldp, n, b, s));
     h->launches++;
     LL_CK(cudaMemcpyAsync(degrees_out, stop.stop_deg, (size_t)b * sizeof(int), cudaMemcpyDeviceToHost, s));
