@@ -646,6 +646,9 @@ def main():
                     help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
                     help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
+    ap.add_argument("--rpt", type=int, default=0,
+                    help="with --step-kernel: rows per thread (gather) or column pairs per thread (tma, 2 = FP32 "
+                         "16-byte rows); for profiler captures")
     ap.add_argument("--workloads", default="c1,c3,c3t,c4,c5,f1,f3,f4",
                     help="extra workloads reported beside the headline (comma list of c1,c3,c3t,c4,c5,f1,f3,f4; "
                          "'' for none; c3t = the Matérn time to 1e-3 relative error)")
@@ -683,7 +686,8 @@ def main():
 
     def time_precision(prec: str, steps: int, warmup: int, sampler=None):
         dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
-        opts = L.options(degree=m, probes=PROBES, seed=SEED + rank, precision=prec, step_kernel=args.step_kernel)
+        opts = L.options(degree=m, probes=PROBES, seed=SEED + rank, precision=prec, step_kernel=args.step_kernel,
+                         rows_per_thread=args.rpt)
         for _ in range(warmup):
             L.ll_logdet_forward(h, dA, *BOUNDS, opts)
         barrier()
@@ -724,14 +728,17 @@ def main():
         per_row = TRACE_STEP_DRAM_BYTES_PER_ROW.get((kname, pr))
         kfun = "k_leja_tma" if kname == "tma" else "k_leja_step"
         ach1 = b_p1 / (p1_launch_ms / 1e3) / 1e9
-        return {"kernel": f"{kfun}<{pr},DOT> (b={2 * k}, {rr['info']['threads_pass2']} threads/CTA)", "bound": "hbm",
+        inf = rr["info"]
+        return {"kernel": (f"{kfun}<{pr},DOT> (b={2 * k}, {inf['threads_pass2']} threads/CTA, "
+                           f"{2 * inf['pairs_pass2']} columns/thread)"), "bound": "hbm",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "traffic": per_row * n if per_row else None,
                 "traffic_source": (f"ncu dram__bytes_read+write of one {kfun} launch on a smaller 3-D Laplacian, "
                                    "scaled by rows") if per_row else None,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
                 "per_launch_bytes": b_p2, "per_launch_ms": p2_launch_ms,
-                "pass1_kernel": {"kernel": f"{kfun}<{pr},ACCUM> (b={k}, {rr['info']['threads_pass1']} threads/CTA)",
+                "pass1_kernel": {"kernel": (f"{kfun}<{pr},ACCUM> (b={k}, {inf['threads_pass1']} threads/CTA, "
+                                            f"{2 * inf['pairs_pass1']} columns/thread)"),
                                  "achieved": ach1, "frac": ach1 / peaks["hbm_gbs"], "per_launch_bytes": b_p1,
                                  "per_launch_ms": p1_launch_ms}}
 
