@@ -80,6 +80,15 @@ enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
  *   LL_DD_TABLE_Q  the divided-difference table in the xi variable in binary128 arithmetic on the
  *                  host (a second scheme for very large condition numbers), rounded to FP64. */
 enum { LL_DD_AUTO = 0, LL_DD_TABLE_Q = 1 };
+/* Kernel of CholeskyQR2's Gram products Y^T Y, Q1^T Q1 and Q^T G (ll_options.qr_gram, ll_gram):
+ *   LL_GRAM_AUTO    the tensor-core kernel when both widths are at most 40 (else LL_GRAM_DFLOAT);
+ *   LL_GRAM_TENSOR  tcgen05 MMAs on BF16 digit slices: each column is written in fixed point per
+ *                   batch of 512 rows as six 8-bit digits below its scale 2^E (max |x| < 2^(E-1)),
+ *                   every slice product is exact in the FP32 accumulators, and the products are
+ *                   scaled and summed in double-float (Ozaki, Ogita & Oishi 2012): about 47 bits
+ *                   below each column's batch maximum; widths up to 40;
+ *   LL_GRAM_DFLOAT  double-float products on the FP32 pipes (any width up to 96).            */
+enum { LL_GRAM_AUTO = 0, LL_GRAM_TENSOR = 1, LL_GRAM_DFLOAT = 2 };
 
 /* Step kernel of the m-step passes:
  *   LL_KERNEL_AUTO    banded matrices (every row's columns strictly increasing and within 2 of
@@ -146,6 +155,9 @@ typedef struct {
                                   the scaled operator), degree being the cap. Not with
                                   keep_for_backward nor ll_logdet_batched (LL_ERR_UNSUPPORTED).  */
     int dd_scheme;             /* LL_DD_AUTO (default) or LL_DD_TABLE_Q                          */
+    int qr_gram;               /* LL_GRAM_AUTO (default), LL_GRAM_TENSOR or LL_GRAM_DFLOAT: the
+                                  Gram kernel of the CholeskyQR2 of Algorithm 3 step 4 and of
+                                  Q^T G in step 6 (the backward uses the kept forward's)        */
 } ll_options;
 
 typedef struct ll_handle ll_handle;
@@ -364,6 +376,16 @@ ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* d
  * seed + i. estimates: host, count doubles; synchronises `stream`. */
 ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b, int count,
                             const ll_options* opts, const int* degrees, double* estimates, void* stream);
+
+/* The Gram product X^T Z as CholeskyQR2 forms it (Algorithm 3 step 4: G = Y^T Y; step 6: C = Q^T G):
+ * a parity hook for the Gram kernels. X: device, n x kx, row-major with leading dimension ldx, in
+ * `layout` LL_PREC_F64 (FP64 elements) or LL_PREC_DF64 (the library's double-float blocks: the 16
+ * bytes of columns (2q, 2q+1) of a row hold (hi_2q, hi_2q+1, lo_2q, lo_2q+1); ldx even). Z: device
+ * FP64 n x kz (ldz), or NULL for X^T X. method: LL_GRAM_*. out: device kx x kz FP64 row-major.
+ * 1 <= kx, kz <= 96; LL_GRAM_TENSOR with a width above 40 gives LL_ERR_UNSUPPORTED. Synchronises
+ * `stream` (the kernel's bounded waits are checked: LL_ERR_TIMEOUT). */
+ll_status ll_gram(ll_handle* h, int layout, const void* X, int64_t ldx, int kx, const double* Z, int64_t ldz, int kz,
+                  int64_t n, int method, double* out, void* stream);
 
 /* Diagnostics of the last ll_logdet_forward on this handle. */
 ll_status ll_get_info(const ll_handle* h, ll_info* out);

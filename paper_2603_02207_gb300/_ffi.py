@@ -23,6 +23,7 @@ LL_PREC_F64, LL_PREC_DF64, LL_PREC_F32_MIXED = 0, 1, 2
 LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
 LL_DD_AUTO, LL_DD_TABLE_Q = 0, 1
+LL_GRAM_AUTO, LL_GRAM_TENSOR, LL_GRAM_DFLOAT = 0, 1, 2
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
 LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA, LL_KERNEL_BAND = 0, 1, 2, 3
 LL_EST_HUTCHPP, LL_EST_HUTCHINSON = 0, 1
@@ -45,7 +46,7 @@ class ll_options(ctypes.Structure):
                 ("keep_for_backward", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int), ("estimator", ctypes.c_int),
-                ("tol", ctypes.c_double), ("dd_scheme", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("dd_scheme", ctypes.c_int), ("qr_gram", ctypes.c_int)]
 
 
 class ll_info(ctypes.Structure):
@@ -95,6 +96,7 @@ SIGNATURES = {
     "ll_param_grad": (_I, [_P, _P, _P, _I64, _I64, _I, _PD, _P]),
     "ll_logdet_batched": (_I, [_P, ctypes.POINTER(ll_csr), ctypes.POINTER(ll_bounds), _I,
                                ctypes.POINTER(ll_options), ctypes.POINTER(_I), _PD, _P]),
+    "ll_gram": (_I, [_P, _I, _P, _I64, _I, _P, _I64, _I, _I64, _I, _P, _P]),
     "ll_get_info": (_I, [_P, ctypes.POINTER(ll_info)]),
     "ll_stop_degrees": (_I, [_P, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]),
     "ll_kept_basis": (_I, [_P, _P, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),

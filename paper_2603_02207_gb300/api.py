@@ -126,13 +126,15 @@ def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
 
 
 DD_SCHEMES = {"auto": _ffi.LL_DD_AUTO, "table_q": _ffi.LL_DD_TABLE_Q}
+GRAM_METHODS = {"auto": _ffi.LL_GRAM_AUTO, "tensor": _ffi.LL_GRAM_TENSOR, "dfloat": _ffi.LL_GRAM_DFLOAT}
 
 
 def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str = "rademacher",
             precision: str = "df64", sval_mode: int = LL_SVAL_CENTER, keep_for_backward: bool = False,
             rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
             use_graph: bool = True, timeout_cycles: int = 0, step_kernel: str = "auto",
-            estimator: str = "hutchpp", tol: float = 0.0, dd_scheme: str = "auto") -> _ffi.ll_options:
+            estimator: str = "hutchpp", tol: float = 0.0, dd_scheme: str = "auto",
+            qr_gram: str = "auto") -> _ffi.ll_options:
     o = _ffi.ll_options()
     _ffi.load().ll_default_options(ctypes.byref(o))
     o.degree = degree
@@ -151,6 +153,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
     o.estimator = ESTIMATORS[estimator]
     o.tol = tol
     o.dd_scheme = DD_SCHEMES[dd_scheme]
+    o.qr_gram = GRAM_METHODS[qr_gram]
     return o
 
 
@@ -333,3 +336,39 @@ def logdet_leja(A: DeviceCSR, bounds: tuple[float, float], degree: int, probes: 
     h = handle or Handle()
     return ll_logdet_forward(h, A, bounds[0], bounds[1],
                              options(degree=degree, probes=probes, seed=seed, precision=precision, probe_kind=probe_kind))
+
+
+def ll_gram(h: Handle, X, Z=None, method: str = "auto", kx: int | None = None, stream=None):
+    """X^T Z (X^T X when Z is None) by CholeskyQR2's Gram kernels (method "auto", "tensor" or
+    "dfloat"). X is a CUDA float64 tensor n x kx, or a float32 tensor n x 2 ld holding a
+    double-float block in the library's column-pair layout (then kx gives its width). Z: a CUDA
+    float64 tensor n x kz or None. Returns a kx x kz (kx x kx) float64 tensor."""
+    torch = _torch()
+    n = X.shape[0]
+    if X.dtype == torch.float64:
+        kx, ldx, lay = X.shape[1], X.stride(0), LL_PREC_F64
+    else:
+        ldx, lay = X.shape[1] // 2, LL_PREC_DF64
+    kz, ldz = (0, 0) if Z is None else (Z.shape[1], Z.stride(0))
+    out = torch.empty((kx, kx if Z is None else kz), dtype=torch.float64, device="cuda")
+    h.check(h._lib.ll_gram(h.ptr, lay, X.data_ptr(), ldx, kx, 0 if Z is None else Z.data_ptr(), ldz, kz, n,
+                           GRAM_METHODS[method], out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def df64_block(x, ld: int | None = None):
+    """The library's double-float column-pair layout of a float64 array x (n x k, host): a float32
+    array n x 2 ld (ld even, >= k) whose 16 bytes of columns (2q, 2q+1) per row are
+    (hi_2q, hi_2q+1, lo_2q, lo_2q+1), hi = float32(x), lo = float32(x - hi); pad columns zero."""
+    x = np.asarray(x, dtype=np.float64)
+    n, k = x.shape
+    ld = ld or (k + (k & 1))
+    hi = x.astype(np.float32)
+    lo = (x - hi.astype(np.float64)).astype(np.float32)
+    out = np.zeros((n, ld // 2, 4), dtype=np.float32)
+    hp = np.zeros((n, ld), dtype=np.float32)
+    lp = np.zeros((n, ld), dtype=np.float32)
+    hp[:, :k], lp[:, :k] = hi, lo
+    out[:, :, 0], out[:, :, 1] = hp[:, 0::2], hp[:, 1::2]
+    out[:, :, 2], out[:, :, 3] = lp[:, 0::2], lp[:, 1::2]
+    return out.reshape(n, 2 * ld)

@@ -69,6 +69,8 @@ struct ll_handle {
     bool sorted = false;      // every row of the last validated matrix has strictly increasing columns
     int64_t keep_budget = 0;  // ll_set_keep_budget: bytes the forward may keep for the backward (0: half the free memory)
     int64_t forward_id = 0;   // count of successful forwards on the handle (ll_info.forward_id)
+    int gram_method = LL_GRAM_AUTO;   // CholeskyQR2 Gram kernel of the running call (ll_options.qr_gram)
+    int kept_gram = LL_GRAM_AUTO;     // and of the kept forward (its backward uses the same)
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
     int dd_degree = -1, dd_sval = -1, dd_scheme = -1, dd_terms = 0;
@@ -303,6 +305,29 @@ ll_status check_tma_flag(ll_handle* h, cudaStream_t s) {
         return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out");
     }
     return LL_OK;
+}
+
+// X^T Z (Z = X when sym) for CholeskyQR2 and the through-QR adjoint: on the tensor cores (k_gram_tc)
+// when h->gram_method allows and the widths and element type fit, else in double-float on the FP32
+// pipes (k_gram). The tensor-core kernel's bounded waits report through the pipeline error flag.
+ll_status run_gram(ll_handle* h, int tx, const void* X, long long ldx, int kx, const double* Z, long long ldz, int kz,
+                   int n, bool sym, double* partials, unsigned int* ticket, double* out, int ggrid, cudaStream_t s) {
+    const bool tc = h->gram_method != LL_GRAM_DFLOAT && gram_tc_supported(tx, kx, kz, sym) && (tx != T_DF64 || ldx % 2 == 0);
+    if (h->gram_method == LL_GRAM_TENSOR && !tc)
+        return fail(h, LL_ERR_UNSUPPORTED, "tensor-core Gram: widths up to 40 and FP64 or double-float operands");
+    if (tc) {
+        WS(err, int*, "tma_error", sizeof(int));
+        h->tma_used = true;
+        LL_CK(launch_gram_tc(tx, X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, err, h->spin_budget, h->sm_count, s));
+    } else {
+        LL_CK(launch_gram(tx, X, ldx, kx, T_F64, sym ? nullptr : Z, ldz, kz, n, sym, partials, ticket, out, ggrid, s));
+    }
+    return LL_OK;
+}
+
+// doubles of Gram partials for either kernel (kx x kz, grid ggrid for k_gram)
+size_t gram_partials_any(const ll_handle* h, int kx, int kz, bool sym, int ggrid) {
+    return std::max(gram_partials_doubles(kx, kz, sym, ggrid), gram_tc_partials_doubles(kx, kz, h->sm_count));
 }
 
 // Chooses the step launch for (precision, mode, n, nnz, b). kernel = LL_KERNEL_AUTO times the
@@ -788,7 +813,8 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
 
     // ---- Gamma = 2 (I - Pi) Z Q R^-T (tall-skinny FP64 products)
     const int ggrid = h->sm_count * 2;
-    const size_t gpn = gram_partials_doubles(kg > kq ? kg : kq, kq, false, ggrid);
+    const size_t gpn = gram_partials_any(h, kg > kq ? kg : kq, kq, false, ggrid);
+    h->gram_method = h->kept_gram;
     WS(gpart, double*, "bw_gram_partials", gpn * sizeof(double));
     WS(gticket, unsigned int*, "bw_gram_ticket", sizeof(unsigned int));
     WS(small, double*, "bw_small", (size_t)5 * (kg > kq ? kg : kq) * kq * sizeof(double));
@@ -801,12 +827,12 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     double* ZQ = zq + (size_t)n * kq;
     double* Xb = zq + (size_t)2 * n * kq;
     LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), s));
-    LL_CK(launch_gram(T_F64, basis + kq, l2, kg, T_F64, FV64, b2, kq, n, false, gpart, gticket, C1, ggrid, s));
-    LL_CK(launch_gram(T_F64, Gb, kg, kg, T_F64, basis, l2, kq, n, false, gpart, gticket, C2, ggrid, s));
+    if ((st = run_gram(h, T_F64, basis + kq, l2, kg, FV64, b2, kq, n, false, gpart, gticket, C1, ggrid, s)) != LL_OK) return st;
+    if ((st = run_gram(h, T_F64, Gb, kg, kg, basis, l2, kq, n, false, gpart, gticket, C2, ggrid, s)) != LL_OK) return st;
     LL_CK(launch_scaled_copy_f64(C1, kq, C1, kq, 2 * kg, kq, 1.0 / kg, s));
     LL_CK(launch_project(T_F64, Gb, kg, kg, FV64, b2, kq, C1, n, ZQa, kq, T_F64, nullptr, 0, 0, 0, s));
     LL_CK(launch_project(T_F64, FV64 + kq, b2, kg, ZQa, kq, kq, C2, n, ZQ, kq, T_F64, nullptr, 0, 0, 0, s));
-    LL_CK(launch_gram(T_F64, basis, l2, kq, T_F64, ZQ, kq, kq, n, false, gpart, gticket, C3, ggrid, s));
+    if ((st = run_gram(h, T_F64, basis, l2, kq, ZQ, kq, kq, n, false, gpart, gticket, C3, ggrid, s)) != LL_OK) return st;
     LL_CK(launch_project(T_F64, basis, l2, kq, ZQ, kq, kq, C3, n, Xb, kq, T_F64, nullptr, 0, 0, 0, s));
     h->launches += 8;
     // R^-1 = R1^-1 R2^-1 (Y R1^-1 = Q1, Q1 R2^-1 = Q), and M = 2 R^-T, on the host (kq x kq)
@@ -914,6 +940,7 @@ void ll_default_options(ll_options* o) {
     o->step_kernel = LL_KERNEL_AUTO;
     o->estimator = LL_EST_HUTCHPP;
     o->tol = 0.0;
+    o->qr_gram = LL_GRAM_AUTO;
 }
 
 ll_status ll_debug_inject(ll_handle* h, int what) {
@@ -1151,6 +1178,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if (o.sval_mode != LL_SVAL_CENTER && o.sval_mode != LL_SVAL_HALF_LMAX) return fail(h, LL_ERR_INVALID_ARG, "unknown s_val mode");
     if (o.dd_scheme != LL_DD_AUTO && o.dd_scheme != LL_DD_TABLE_Q) return fail(h, LL_ERR_INVALID_ARG, "unknown divided-difference scheme");
     if (!std::isfinite(o.tol) || o.tol < 0.0) return fail(h, LL_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (o.qr_gram < LL_GRAM_AUTO || o.qr_gram > LL_GRAM_DFLOAT) return fail(h, LL_ERR_INVALID_ARG, "unknown Gram method");
+    h->gram_method = o.qr_gram;
     const bool adaptive = o.tol > 0.0;   // Algorithm 2's stopping rule in both passes
     if (adaptive && o.keep_for_backward)
         return fail(h, LL_ERR_UNSUPPORTED, "the backward needs a fixed degree (tol = 0)");
@@ -1200,7 +1229,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         V = vv;
     }
     const int ggrid = h->sm_count * 2;
-    const size_t gp1 = gram_partials_doubles(kq, kq, true, ggrid), gp2 = gram_partials_doubles(kq, kg, false, ggrid);
+    const size_t gp1 = gram_partials_any(h, kq, kq, true, ggrid), gp2 = gram_partials_any(h, kq, kg, false, ggrid);
     WS(gpart, double*, "fw_gram_partials", (gp1 > gp2 ? gp1 : gp2) * sizeof(double));
     WS(gticket, unsigned int*, "fw_gram_ticket", sizeof(unsigned int));
     WS(gram, double*, "fw_gram", (size_t)kq * (kq > kg ? kq : kg) * sizeof(double));
@@ -1361,15 +1390,15 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             const int tq = dfq ? T_DF64 : T_F64;
             const long long ldq1 = dfq ? l1 : kq;
             void* Qb = qv ? V : static_cast<void*>(basis);
-            LL_CK(launch_gram(pt, P, l1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
+            if ((st = run_gram(h, pt, P, l1, kq, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q)) != LL_OK) return st;
             LL_CK(launch_chol_rinv(gram, kq, rinv1, qrstat, q));
             if (dfq) LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, nullptr, 0, T_DF64, q1, l1, q));
             else LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, q1, kq, T_F64, nullptr, 0, q));
-            LL_CK(launch_gram(tq, q1, ldq1, kq, T_F64, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q));
+            if ((st = run_gram(h, tq, q1, ldq1, kq, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q)) != LL_OK) return st;
             LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
             if (dfq) LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, nullptr, l2, T_DF64, Qb, l2, q));
             else LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, basis, l2, T_F64, nullptr, l2, q));
-            LL_CK(launch_gram(tq, Qb, l2, kq, T_F64, G, kg, kg, n, false, gpart, gticket, gram, ggrid, q));
+            if ((st = run_gram(h, tq, Qb, l2, kq, G, kg, kg, n, false, gpart, gticket, gram, ggrid, q)) != LL_OK) return st;
             // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
             // The typed block pointer is offset by kq elements: element index r * l2 + kq + c.
             LL_CK(launch_project(tq, Qb, l2, kq, G, kg, kg, gram, n, dfq ? nullptr : basis + kq, l2, T_DF64,
@@ -1587,6 +1616,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         h->kept_m = m;
         h->kept_prec = prec;
         h->kept_ckpt = o.ckpt_stride;
+        h->kept_gram = o.qr_gram;
         h->kept_sigma = sigma;
         h->kept_c = c;
         h->kept_gamma = gamma;
@@ -2198,6 +2228,39 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         h->launches = before + launched;
     }
     return batched_finish(h, mats, count, estimates, s);
+}
+
+ll_status ll_gram(ll_handle* h, int layout, const void* X, int64_t ldx, int kx, const double* Z, int64_t ldz, int kz,
+                  int64_t n, int method, double* out, void* stream) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    if (layout != LL_PREC_F64 && layout != LL_PREC_DF64) return fail(h, LL_ERR_INVALID_ARG, "layout must be LL_PREC_F64 or LL_PREC_DF64");
+    if (method < LL_GRAM_AUTO || method > LL_GRAM_DFLOAT) return fail(h, LL_ERR_INVALID_ARG, "unknown Gram method");
+    const bool sym = Z == nullptr;
+    if (sym) kz = kx, ldz = 0;
+    if (n < 0 || kx < 1 || kz < 1 || kx > 96 || kz > 96 || ldx < kx || (!sym && ldz < kz)) return fail(h, LL_ERR_INVALID_ARG, "bad Gram shape");
+    if (layout == LL_PREC_DF64 && (ldx & 1)) return fail(h, LL_ERR_INVALID_ARG, "double-float column pairs need an even ldx");
+    if (n >= ((int64_t)1 << 31)) return fail(h, LL_ERR_UNSUPPORTED, "n must be < 2^31");
+    if (!out || (n > 0 && !X)) return fail(h, LL_ERR_INVALID_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        LL_CK(cudaMemsetAsync(out, 0, (size_t)kx * kz * sizeof(double), s));
+        return LL_OK;
+    }
+    const int tx = layout == LL_PREC_F64 ? T_F64 : T_DF64;
+    const int ggrid = h->sm_count * 2;
+    WS(part, double*, "gram_partials", gram_partials_any(h, kx, kz, sym, ggrid) * sizeof(double));
+    WS(tick, unsigned int*, "gram_ticket", sizeof(unsigned int));
+    WS(err, int*, "tma_error", sizeof(int));
+    LL_CK(cudaMemsetAsync(tick, 0, sizeof(unsigned int), s));
+    LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    h->gram_method = method;
+    h->launches = 0;
+    ll_status st = run_gram(h, tx, X, ldx, kx, Z, ldz, kz, (int)n, sym, part, tick, out, ggrid, s);
+    h->gram_method = LL_GRAM_AUTO;
+    if (st != LL_OK) return st;
+    h->launches++;
+    h->tma_used = true;
+    return check_tma_flag(h, s);
 }
 
 ll_status ll_get_info(const ll_handle* h, ll_info* out) {

@@ -66,6 +66,28 @@ __host__ __device__ __forceinline__ float2 df_split(double x) {
 
 __device__ __forceinline__ double df_to_double(float2 v) { return (double)v.x + (double)v.y; }
 
+// A double as an unevaluated float pair hi + lo, from its bit fields with integer operations and
+// one integer-to-float conversion (GB300 runs FP64 instructions, conversions from double among
+// them, at a small fraction of the FP32 rate): hi takes the sign, the exponent and the leading 23
+// stored mantissa bits (truncated), lo the remaining 29 bits rounded to 24, scaled by
+// 2^(e - 52). |x - hi - lo| <= 2^-47 |x|. Values outside the float pair's exponent range (zero,
+// subnormals, |x| >= 2^128, inf, nan) take the plain conversion and lo = 0.
+__device__ __forceinline__ void split_bits(double x, float& h, float& l) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hw = (unsigned int)(u >> 32);
+    const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+    if (e < -126 || e > 127) {
+        h = (e < -126) ? __uint_as_float(hw & 0x80000000u) : __double2float_rn(x);
+        l = 0.f;
+        return;
+    }
+    const unsigned int sign = hw & 0x80000000u;
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    h = __uint_as_float(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29));
+    const float lf = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull));
+    l = ldexpf(sign ? -lf : lf, e - 52);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Packed FP32 pairs (Blackwell f32x2 instructions): two floats in one 64-bit register, the first
 // in the low word. One instruction performs the operation on both lanes with IEEE RN rounding.
