@@ -81,12 +81,13 @@ enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
  *                  host (a second scheme for very large condition numbers), rounded to FP64. */
 enum { LL_DD_AUTO = 0, LL_DD_TABLE_Q = 1 };
 /* Kernel of CholeskyQR2's Gram products Y^T Y, Q1^T Q1 and Q^T G (ll_options.qr_gram, ll_gram):
- *   LL_GRAM_AUTO    the tensor-core kernel when both widths are at most 40 (else LL_GRAM_DFLOAT);
- *   LL_GRAM_TENSOR  tcgen05 MMAs on BF16 digit slices: each column is written in fixed point per
- *                   batch of 512 rows as six 8-bit digits below its scale 2^E (max |x| < 2^(E-1)),
- *                   every slice product is exact in the FP32 accumulators, and the products are
- *                   scaled and summed in double-float (Ozaki, Ogita & Oishi 2012): about 47 bits
- *                   below each column's batch maximum; widths up to 40;
+ *   LL_GRAM_AUTO    the tensor-core kernel when both widths are at most 42 (else LL_GRAM_DFLOAT);
+ *   LL_GRAM_TENSOR  tcgen05 MMAs on BF16 digit slices: each column is written in fixed point as
+ *                   seven 7-bit digits (six for widths above 36) below its scale 2^E (max |x| <
+ *                   2^(E-1), from a maximum pre-pass), every slice product summed over up to 4096
+ *                   rows is exact in the FP32 accumulators, and the products are scaled and summed
+ *                   in double-float (Ozaki, Ogita & Oishi 2012): 49 (42) bits below each column's
+ *                   maximum; widths up to 42;
  *   LL_GRAM_DFLOAT  double-float products on the FP32 pipes (any width up to 96).            */
 enum { LL_GRAM_AUTO = 0, LL_GRAM_TENSOR = 1, LL_GRAM_DFLOAT = 2 };
 
@@ -382,7 +383,7 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
  * `layout` LL_PREC_F64 (FP64 elements) or LL_PREC_DF64 (the library's double-float blocks: the 16
  * bytes of columns (2q, 2q+1) of a row hold (hi_2q, hi_2q+1, lo_2q, lo_2q+1); ldx even). Z: device
  * FP64 n x kz (ldz), or NULL for X^T X. method: LL_GRAM_*. out: device kx x kz FP64 row-major.
- * 1 <= kx, kz <= 96; LL_GRAM_TENSOR with a width above 40 gives LL_ERR_UNSUPPORTED. Synchronises
+ * 1 <= kx, kz <= 96; LL_GRAM_TENSOR with a width above 42 gives LL_ERR_UNSUPPORTED. Synchronises
  * `stream` (the kernel's bounded waits are checked: LL_ERR_TIMEOUT). */
 ll_status ll_gram(ll_handle* h, int layout, const void* X, int64_t ldx, int kx, const double* Z, int64_t ldz, int kz,
                   int64_t n, int method, double* out, void* stream);

@@ -314,11 +314,14 @@ ll_status run_gram(ll_handle* h, int tx, const void* X, long long ldx, int kx, c
                    int n, bool sym, double* partials, unsigned int* ticket, double* out, int ggrid, cudaStream_t s) {
     const bool tc = h->gram_method != LL_GRAM_DFLOAT && gram_tc_supported(tx, kx, kz, sym) && (tx != T_DF64 || ldx % 2 == 0);
     if (h->gram_method == LL_GRAM_TENSOR && !tc)
-        return fail(h, LL_ERR_UNSUPPORTED, "tensor-core Gram: widths up to 40 and FP64 or double-float operands");
+        return fail(h, LL_ERR_UNSUPPORTED, "tensor-core Gram: widths up to 42 and FP64 or double-float operands");
     if (tc) {
         WS(err, int*, "tma_error", sizeof(int));
+        WS(work, void*, "gram_tc_work", gram_tc_workspace_bytes(kx, sym ? kx : kz, h->sm_count));
         h->tma_used = true;
-        LL_CK(launch_gram_tc(tx, X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, err, h->spin_budget, h->sm_count, s));
+        LL_CK(launch_gram_tc(tx, X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, work, err, h->spin_budget,
+                             h->sm_count, s));
+        h->launches += sym ? 2 : 3;
     } else {
         LL_CK(launch_gram(tx, X, ldx, kx, T_F64, sym ? nullptr : Z, ldz, kz, n, sym, partials, ticket, out, ggrid, s));
     }

@@ -3,25 +3,32 @@
 //
 // tcgen05 multiplies BF16 operands into FP32 accumulators in tensor memory (TMEM). An FP64-class
 // product is made of exact pieces by the error-free splitting of Ozaki, Ogita & Oishi (2012):
-//   * rows are processed in batches of GT_BATCH_ROWS; within a batch, column j of X is scaled by
-//     2^-E_j with max_i |x_ij| < 2^(E_j - 1) and written in fixed point as
-//     x_ij = 2^E_j sum_{s < S} t_s[i, j] 2^(-8 (s + 1)), with integer digits |t_s| <= 128
-//     (exact in BF16) and S = 6 (about 47 bits below the column's scale); Z likewise (F_l);
-//   * then X^T Z = sum_{s, u} 2^(E_j + F_l - 8 (s + u + 2)) T_s^T U_u, and every T_s^T U_u over a
-//     batch is a sum of at most 512 * 128^2 = 2^23 integer products: exact in FP32;
-//   * one MMA computes all slice pairs at once: A holds [T_0; ...; T_5] (6 kx rows, K = the
-//     batch's rows), B holds [U_0; ...; U_5] (6 kz rows), D = A B^T (6 kx x 6 kz) in TMEM;
-//   * after each batch every thread reads its D row (s, j) from TMEM, scales each entry exactly by
-//     powers of two and adds it into double-float sums per (s, j, l) in shared memory; at the end
-//     the sums over s give the CTA's partial X^T Z, and the last CTA adds the partials in CTA order.
-// The products carry no rounding; the only roundings are the digit truncation (below 2^-47 of a
-// column's batch maximum) and the double-float sums (about 2^-48 relative).
+//   * a pre-pass takes each column's maximum; column j of X is scaled by 2^-E_j with
+//     max_i |x_ij| < 2^(E_j - 1) and written in fixed point as
+//     x_ij = 2^E_j sum_{s < S} t_s[i, j] 2^(-7 (s + 1)), integer digits |t_s| <= 64 (exact in
+//     BF16); S = 7 digits for widths up to 36 (49 bits below the column's scale), 6 up to 42;
+//     Z likewise (exponents F_l);
+//   * then X^T Z = sum_{s, u} 2^(E_j + F_l - 7 (s + u + 2)) T_s^T U_u, and T_s^T U_u summed over
+//     up to 4096 rows is a sum of integer products of at most 64^2 = 2^12 each: below 2^24, so
+//     exact in FP32 whatever the order of the additions;
+//   * one MMA computes all slice pairs at once: A holds [T_0; ...; T_{S-1}] (S kx rows, K = rows),
+//     B holds [U_0; ...; U_{S-1}] (S kz rows), D = A B^T (S kx x S kz) in TMEM;
+//   * every 4096 rows (and at the end of the CTA's rows) each thread reads its D row (s, j) from
+//     TMEM, scales the entries exactly by powers of two and adds them into double-float sums per
+//     (s, j, l) in global memory (the CTA's own slice of the workspace; an L2-resident region);
+//     at the end the sums over s give the CTA's partial X^T Z, and the last CTA adds the
+//     partials in CTA order.
+// The products carry no rounding; the only roundings are the digit truncation (below 2^-49, or
+// 2^-42, of each column's maximum) and the double-float sums (about 2^-48 relative).
 //
-// Operands go to shared memory in the canonical K-major layout without swizzle: 8 x 8 BF16 core
-// matrices (8 rows of 16 bytes), K-adjacent core matrices GT_LBO bytes apart (128 + 16: the padding
-// keeps the 16-byte digit stores free of bank conflicts), 8-row groups GT_SBO bytes apart. One
-// thread issues the MMAs and commits them to an mbarrier; every wait is bounded, and a wait that
-// runs out sets the error flag, waits (bounded) for the MMAs in flight, frees the TMEM and returns.
+// Pipeline of a CTA over its contiguous rows, in chunks of GT_CH rows: the raw rows of chunk c + 1
+// are copied to shared memory (cp.async) while chunk c is split into digits, and the digits of
+// chunk c go to one of two operand buffers while the MMAs of chunk c - 1 read the other. Operands
+// use the canonical K-major layout without swizzle: 8 x 8 BF16 core matrices (8 rows of 16 bytes),
+// K-adjacent core matrices 128 bytes apart, 8-row groups GT_SBO = 1040 bytes apart (16 bytes of
+// padding spread the digit stores over the banks). One thread issues the MMAs and commits each
+// chunk to its buffer's mbarrier. Every wait is bounded: one that runs out sets the error flag,
+// waits (bounded) for the MMAs in flight, frees the TMEM and returns.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tma_common.cuh"
@@ -29,13 +36,12 @@
 namespace ll {
 namespace {
 
-constexpr int GT_S = 6;                        // digits per value
-constexpr int GT_CH = 128;                     // rows per staged chunk (MMA K: 8 steps of 16)
-constexpr int GT_BATCH = 4;                    // chunks per exact accumulation batch
-constexpr int GT_BATCH_ROWS = GT_CH * GT_BATCH;
-constexpr int GT_LBO = 144;                    // bytes between K-adjacent core matrices
-constexpr int GT_SBO = (GT_CH / 8) * GT_LBO;   // bytes between 8-row groups (2304)
+constexpr int GT_CH = 64;                      // rows per chunk (MMA K: 4 steps of 16)
+constexpr int GT_BATCH_CHUNKS = 64;            // chunks summed exactly in TMEM (4096 rows)
+constexpr int GT_LBO = 128;                    // bytes between K-adjacent core matrices
+constexpr int GT_SBO = (GT_CH / 8) * GT_LBO + 16;   // bytes between 8-row groups (1040)
 constexpr int GT_THREADS = 256;
+constexpr int GT_SMAX = 7;
 
 // ---- tcgen05 / TMEM wrappers (inline PTX) ----------------------------------------------------
 __device__ __forceinline__ void tc_alloc(uint32_t dst_smem, uint32_t ncols) {
@@ -85,90 +91,99 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// ---- operands ----------------------------------------------------------------------------------
-// columns (2 cp, 2 cp + 1) of row `row` as double-float pairs: hi = (h0, h1), lo = (l0, l1); columns
-// at or past k read as zero
-__device__ __forceinline__ void ld_cols(const dfp* X, long long ld, int k, long long row, int cp, f2x& hi, f2x& lo) {
-    const float4 v = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + ((row * ld + 2 * cp) >> 1) * 4);
-    hi = f2_pack(v.x, 2 * cp + 1 < k ? v.y : 0.f);
-    lo = f2_pack(v.z, 2 * cp + 1 < k ? v.w : 0.f);
-}
-__device__ __forceinline__ void ld_cols(const double* X, long long ld, int k, long long row, int cp, f2x& hi, f2x& lo) {
-    float h0, l0, h1 = 0.f, l1 = 0.f;
-    split_bits(X[row * ld + 2 * cp], h0, l0);
-    if (2 * cp + 1 < k) split_bits(X[row * ld + 2 * cp + 1], h1, l1);
-    hi = f2_pack(h0, h1);
-    lo = f2_pack(l0, l1);
-}
-
 // 2^e as a float, e clamped to the normal range [-126, 127]
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(max(-126, min(127, e)) + 127) << 23); }
-// x 2^e for e in [-252, 254] by two exact multiplications (exact unless the result leaves the
-// float range)
+// x 2^e for e in [-252, 254] by two exact multiplications (exact unless the result leaves the float range)
 __device__ __forceinline__ float scale2(float x, int e) {
     const int e1 = max(-126, min(127, e));
     return (x * pow2f(e1)) * pow2f(e - e1);
 }
 
-struct GtShape {
-    int k;        // columns of the operand
-    int kp2;      // column pairs
-    int rows;     // slice rows: 6 k
-    int base;     // shared-memory offset of the operand
+// ---- operand element access ------------------------------------------------------------------
+// Raw staging of an operand's chunk in shared memory: DF64 blocks by 16-byte column pairs, FP64
+// blocks by 8-byte elements (their rows need not be 16-byte aligned); row stride `rs` bytes.
+template <typename T> struct Raw;
+template <> struct Raw<dfp> {
+    static constexpr int unit = 16;
+    __device__ static int units(int k) { return (k + 1) / 2; }
+    __device__ static const void* src(const dfp* X, long long ld, long long row, int u) {
+        return reinterpret_cast<const float*>(X) + ((row * ld + 2 * u) >> 1) * 4;
+    }
+    // columns (2 cp, 2 cp + 1) of a staged row as (hi pair, lo pair); a column at or past k is zero
+    __device__ static void pair(const unsigned char* row, int cp, int k, f2x& hi, f2x& lo) {
+        const float4 v = *reinterpret_cast<const float4*>(row + 16 * cp);
+        hi = f2_pack(v.x, 2 * cp + 1 < k ? v.y : 0.f);
+        lo = f2_pack(v.z, 2 * cp + 1 < k ? v.w : 0.f);
+    }
+};
+template <> struct Raw<double> {
+    static constexpr int unit = 8;
+    __device__ static int units(int k) { return k; }
+    __device__ static const void* src(const double* X, long long ld, long long row, int u) { return X + row * ld + u; }
+    __device__ static void pair(const unsigned char* row, int cp, int k, f2x& hi, f2x& lo) {
+        const double* r = reinterpret_cast<const double*>(row);
+        float h0, l0, h1 = 0.f, l1 = 0.f;
+        split_bits(r[2 * cp], h0, l0);
+        if (2 * cp + 1 < k) split_bits(r[2 * cp + 1], h1, l1);
+        hi = f2_pack(h0, h1);
+        lo = f2_pack(l0, l1);
+    }
 };
 
-// Maxima of |x_ij| over rows [r0, r0 + nr) into smax[j] (float bits, atomicMax), coalesced: thread t
-// takes column pair t % kp2 of rows t / kp2, t / kp2 + rstride, ...
+template <int CP>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc),
+                 "n"(CP), "r"(valid ? CP : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// rows [c0, c0 + GT_CH) of X into the raw stage (rows at or past `end` zero-filled)
 template <typename T>
-__device__ __forceinline__ void batch_max(const T* X, long long ld, const GtShape& S, long long r0, int nr,
-                                          unsigned int* smax) {
-    const int rstride = GT_THREADS / S.kp2;
-    const int cp = threadIdx.x % S.kp2, rg = threadIdx.x / S.kp2;
-    if (rg >= rstride) return;
-    float m0 = 0.f, m1 = 0.f;
-    for (int i = rg; i < nr; i += rstride) {
-        f2x hi, lo;
-        ld_cols(X, ld, S.k, r0 + i, cp, hi, lo);
-        float h0, h1;
-        f2_unpack(hi, h0, h1);
-        m0 = fmaxf(m0, fabsf(h0));
-        m1 = fmaxf(m1, fabsf(h1));
+__device__ __forceinline__ void stage_raw(unsigned char* st, int rs, const T* X, long long ld, int k, long long c0, long long end) {
+    const int U = Raw<T>::units(k);
+    for (int e = threadIdx.x; e < GT_CH * U; e += GT_THREADS) {
+        const int r = e / U, u = e - r * U;
+        const long long row = c0 + r;
+        const bool ok = row < end;
+        cp_async<Raw<T>::unit>(st + r * rs + u * Raw<T>::unit, ok ? Raw<T>::src(X, ld, row, u) : (const void*)X, ok);
     }
-    atomicMax(&smax[2 * cp], __float_as_uint(m0));
-    if (2 * cp + 1 < S.k) atomicMax(&smax[2 * cp + 1], __float_as_uint(m1));
 }
 
-// Digits of rows [c0, c0 + GT_CH) of X (rows at or past n are zero) into the operand's slice rows
-// s k + j, K index = row - c0, scaled by sc[j] = 2^-E_j. One item = 8 rows x one column pair; per
-// digit and column the 8 rows' BF16 digits form one 16-byte store (a core-matrix row).
+// The staged chunk's digits into the operand buffer `op`: slice row m = s k + j, K index = the row
+// within the chunk. One item = 4 rows x one column pair; per digit and column the 4 rows' BF16
+// digits make one 8-byte store (half a core-matrix row). ex[j]: the column exponents E_j.
 template <typename T>
-__device__ __forceinline__ void slice_chunk(const T* X, long long ld, const GtShape& S, long long c0, long long n,
-                                            const int* ex, unsigned char* smem) {
-    const f2x k256 = f2_pack(256.f, 256.f);
+__device__ __forceinline__ void slice_chunk(const unsigned char* st, int rs, int k, int S, const int* ex, unsigned char* op) {
+    const f2x k128 = f2_pack(128.f, 128.f);
     const f2x magic = f2_pack(12582912.f, 12582912.f);   // 1.5 * 2^23: adding and subtracting it rounds to an integer
-    for (int it = threadIdx.x; it < 16 * S.kp2; it += GT_THREADS) {
-        const int g = it & 15, cp = it >> 4;
+    const int kp2 = (k + 1) / 2;
+    for (int it = threadIdx.x; it < (GT_CH / 4) * kp2; it += GT_THREADS) {
+        const int cp = it % kp2, g4 = it / kp2;   // lanes vary the column pair first
         const int j0 = 2 * cp;
         // 2^-E_j as the product of two floats (E_j may leave the normal range of one)
-        const int e0 = ex[j0], e1 = j0 + 1 < S.k ? ex[j0 + 1] : 0;
+        const int e0 = ex[j0], e1 = j0 + 1 < k ? ex[j0 + 1] : 0;
         const int a0 = max(-126, min(127, -e0)), a1 = max(-126, min(127, -e1));
         const f2x sa = f2_pack(pow2f(a0), pow2f(a1)), sb = f2_pack(pow2f(-e0 - a0), pow2f(-e1 - a1));
-        f2x vh[8], vl[8];
+        f2x vh[4], vl[4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const long long row = c0 + 8 * g + r;
-            f2x hi = 0ull, lo = 0ull;
-            if (row < n) ld_cols(X, ld, S.k, row, cp, hi, lo);
+        for (int r = 0; r < 4; ++r) {
+            f2x hi, lo;
+            Raw<T>::pair(st + (4 * g4 + r) * rs, cp, k, hi, lo);
             vh[r] = f2_mul(f2_mul(hi, sa), sb);
             vl[r] = f2_mul(f2_mul(lo, sa), sb);
         }
+        // K index 4 g4 .. 4 g4 + 3: core matrix g4 / 2 along K, bytes 8 (g4 & 1) .. + 7 of its row
+        const int koff = (g4 >> 1) * GT_LBO + (g4 & 1) * 8;
 #pragma unroll
-        for (int s = 0; s < GT_S; ++s) {
-            uint32_t w0[4], w1[4];   // 8 rows of BF16 digits for columns j0 and j0 + 1
+        for (int s = 0; s < GT_SMAX; ++s) {
+            if (s >= S) break;
+            uint32_t w0[2], w1[2];   // 4 rows of BF16 digits for columns j0 and j0 + 1
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const f2x h = f2_mul(vh[r], k256);
-                const f2x l = f2_mul(vl[r], k256);
+            for (int r = 0; r < 4; ++r) {
+                const f2x h = f2_mul(vh[r], k128);
+                const f2x l = f2_mul(vl[r], k128);
                 const f2x t = f2_sub(f2_add(h, magic), magic);
                 const f2x d = f2_sub(h, t);   // exact remainder in [-1/2, 1/2]
                 // TwoSum(d, l): the remainder as a normalised double-float pair again
@@ -178,7 +193,7 @@ __device__ __forceinline__ void slice_chunk(const T* X, long long ld, const GtSh
                 vh[r] = sm;
                 float t0, t1;
                 f2_unpack(t, t0, t1);
-                // |t| <= 128: a BF16 holds it exactly in the float's upper 16 bits
+                // |t| <= 64: a BF16 holds it exactly in the float's upper 16 bits
                 if (r & 1) {   // (row r - 1, row r) as the low and high halves of one word
                     asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w0[r >> 1]) : "r"(w0[r >> 1]), "r"(__float_as_uint(t0)));
                     asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w1[r >> 1]) : "r"(w1[r >> 1]), "r"(__float_as_uint(t1)));
@@ -187,14 +202,11 @@ __device__ __forceinline__ void slice_chunk(const T* X, long long ld, const GtSh
                     w1[r >> 1] = __float_as_uint(t1);
                 }
             }
-            // slice row m = s k + j, K offset 8 g: core matrix (m / 8, g), row m % 8
-            const int m0 = s * S.k + j0;
-            *reinterpret_cast<uint4*>(smem + S.base + (m0 >> 3) * GT_SBO + g * GT_LBO + (m0 & 7) * 16) =
-                make_uint4(w0[0], w0[1], w0[2], w0[3]);
-            if (j0 + 1 < S.k) {
+            const int m0 = s * k + j0;
+            *reinterpret_cast<uint2*>(op + (m0 >> 3) * GT_SBO + koff + (m0 & 7) * 16) = make_uint2(w0[0], w0[1]);
+            if (j0 + 1 < k) {
                 const int m1 = m0 + 1;
-                *reinterpret_cast<uint4*>(smem + S.base + (m1 >> 3) * GT_SBO + g * GT_LBO + (m1 & 7) * 16) =
-                    make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                *reinterpret_cast<uint2*>(op + (m1 >> 3) * GT_SBO + koff + (m1 & 7) * 16) = make_uint2(w1[0], w1[1]);
             }
         }
     }
@@ -204,46 +216,52 @@ struct GramTcArgs {
     const void* X;
     long long ldx;
     int kx;
-    const double* Z;   // null: Z = X (symmetric)
+    const double* Z;     // null: Z = X (symmetric)
     long long ldz;
     int kz;
     long long n;
-    double* partials;  // grid x kx x kz
+    long long rows_per_cta;   // a multiple of GT_CH
+    const unsigned int* mx;   // column maxima (float bits): kx of X, then kz of Z
+    float2* acc;         // per CTA: S kx x kz double-float sums
+    double* partials;    // grid x kx x kz
     unsigned int* ticket;
-    double* out;       // kx x kz
+    double* out;         // kx x kz
     int* err;
     long long spin_budget;
-    int mt, nb;        // M tiles (1 or 2) of A, N of B (a multiple of 16)
-    int off_b, off_acc, off_sc, acc_stride, acc_copies, zero_bytes;
+    int S, mt, nb;       // digits, M tiles (1 or 2) of A, N of B (a multiple of 16)
+    int off_a, off_b, off_rx, off_rz, rsx, rsz, opbytes_a, opbytes_b;
     uint32_t tmem_cols;
 };
 
 template <typename TX>
 __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t s_tmem;
     __shared__ bool s_last;
-    __shared__ int s_dead;
+    __shared__ int s_ex[128];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const bool sym = a.Z == nullptr;
     const TX* X = static_cast<const TX*>(a.X);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const GtShape SA{a.kx, (a.kx + 1) / 2, GT_S * a.kx, 0};
-    const GtShape SB{a.kz, (a.kz + 1) / 2, GT_S * a.kz, sym ? 0 : a.off_b};
-    // per-column exponents E of the batch (|x| < 2^(E - 1)), and the maxima they come from
-    int* exx = reinterpret_cast<int*>(smem + a.off_sc);
-    int* exz = exx + 64;
-    unsigned int* mxx = reinterpret_cast<unsigned int*>(exz + 64);
-    unsigned int* mxz = mxx + 64;
-    float2* acc = reinterpret_cast<float2*>(smem + a.off_acc);
+    const int S = a.S;
+    const int kz = sym ? a.kx : a.kz;
+    int* exx = s_ex;
+    int* exz = sym ? s_ex : s_ex + 64;
+    float2* accg = a.acc + (size_t)blockIdx.x * S * a.kx * kz;
 
-    // zero the operands (slice rows past 6 k stay zero) and the sums
-    for (uint32_t i = tid * 16u; i < (uint32_t)a.zero_bytes; i += GT_THREADS * 16u) *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
+    // column exponents: max |x| < 2^(E - 1); all-zero columns take E = 0 (their digits are zero)
+    for (int j = tid; j < a.kx + (sym ? 0 : a.kz); j += GT_THREADS) {
+        const float m = __uint_as_float(a.mx[j]);
+        s_ex[j < a.kx ? j : 64 + (j - a.kx)] = m > 0.f ? ilogbf(m) + 2 : 0;
+    }
+    // zero both operand buffers (slice rows past S k stay zero) and this CTA's sums
+    for (int i = tid * 16; i < a.off_rx; i += GT_THREADS * 16) *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < S * a.kx * kz; i += GT_THREADS) accg[i] = make_float2(0.f, 0.f);
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar), 1);
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        s_dead = 0;
     }
     if (warp == 0) {
         tc_alloc(smem_u32(&s_tmem), a.tmem_cols);
@@ -254,129 +272,148 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = tc_idesc(128, a.nb);
-    const uint32_t sbase = smem_u32(smem);
-    uint32_t phase = 0;
-    int pending = 0;   // MMA commits not yet waited for (0 or 1)
+    const long long r0 = (long long)blockIdx.x * a.rows_per_cta;
+    const long long r1 = min(a.n, r0 + a.rows_per_cta);
+    const int nch = r0 < r1 ? (int)((r1 - r0 + GT_CH - 1) / GT_CH) : 0;
+    uint32_t phase[2] = {0u, 0u};
+    int pend[2] = {0, 0};   // a commit of the buffer not yet waited for
     bool dead = false;
-    const long long nbat = (a.n + GT_BATCH_ROWS - 1) / GT_BATCH_ROWS;
 
-    for (long long bt = blockIdx.x; bt < nbat && !dead; bt += gridDim.x) {
-        const long long r0 = bt * GT_BATCH_ROWS;
-        const int nr = (int)min((long long)GT_BATCH_ROWS, a.n - r0);
-        // ---- column scales of the batch
-        for (int j = tid; j < 64; j += GT_THREADS) { mxx[j] = 0u; mxz[j] = 0u; }
-        __syncthreads();
-        batch_max<TX>(X, a.ldx, SA, r0, nr, mxx);
-        if (!sym) batch_max<double>(a.Z, a.ldz, SB, r0, nr, mxz);
-        __syncthreads();
-        for (int j = tid; j < 128; j += GT_THREADS) {
-            const bool isx = j < 64;
-            const int jj = isx ? j : j - 64;
-            if (jj >= (isx ? a.kx : a.kz)) continue;
-            const float mx = __uint_as_float(isx ? mxx[jj] : mxz[jj]);
-            // E with mx < 2^(E - 1); all-zero columns take E = 0 (their digits are zero)
-            (isx ? exx : exz)[jj] = mx > 0.f ? ilogbf(mx) + 2 : 0;
-        }
-        __syncthreads();
-        // ---- the batch's chunks: digits into shared memory, then the MMAs of the chunk
-        for (int c = 0; c < GT_BATCH; ++c) {
-            const long long c0 = r0 + (long long)c * GT_CH;
-            if (c0 >= a.n) break;
-            if (pending) {   // the previous chunk's MMAs have read the operands
-                const bool ok = mbar_wait_bounded(smem_u32(&mbar), phase, a.spin_budget);
-                if (__syncthreads_or(ok ? 0 : 1)) { dead = true; break; }
-                phase ^= 1u;
-                pending = 0;
-            }
-            slice_chunk<TX>(X, a.ldx, SA, c0, a.n, exx, smem);
-            if (!sym) slice_chunk<double>(a.Z, a.ldz, SB, c0, a.n, exz, smem);
-            fence_proxy_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-#pragma unroll 1
-                for (int t = 0; t < GT_CH / 16; ++t) {
-                    // K step t: the core matrices 2t and 2t + 1 of every 8-row group
-                    const uint64_t bd = tc_desc(sbase + (uint32_t)SB.base + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
-                    for (int mt = 0; mt < a.mt; ++mt) {
-                        const uint64_t ad = tc_desc(sbase + (uint32_t)SA.base + (uint32_t)(16 * mt) * GT_SBO + (uint32_t)(2 * t) * GT_LBO,
-                                                    GT_LBO, GT_SBO);
-                        tc_mma(tmem + (uint32_t)(256 * mt), ad, bd, idesc, (c > 0 || t > 0) ? 1u : 0u);
-                    }
-                }
-                tc_commit(smem_u32(&mbar));
-            }
-            pending = 1;
-        }
-        if (dead) break;
-        // ---- the batch's products: scaled into the double-float sums
-        {
-            const bool ok = mbar_wait_bounded(smem_u32(&mbar), phase, a.spin_budget);
-            if (__syncthreads_or(ok ? 0 : 1)) { dead = true; break; }
-            phase ^= 1u;
-            pending = 0;
-        }
+    // waits for buffer b's last commit (every thread; false when the wait ran out anywhere)
+    auto wait_buf = [&](int b) -> bool {
+        if (!pend[b]) return true;
+        const bool ok = mbar_wait_bounded(smem_u32(&mbar[b]), phase[b], a.spin_budget);
+        if (__syncthreads_or(ok ? 0 : 1)) return false;
+        phase[b] ^= 1u;
+        pend[b] = 0;
+        return true;
+    };
+    // the D rows of this thread's TMEM lane, scaled exactly, into the (s, j, l) sums
+    auto drain = [&]() {
         tc_fence_after();
-        const int grp = warp >> 2;                        // two groups of four warps
+        const int grp = warp >> 2;   // two groups of four warps: both M tiles, or the two halves of one
         const int tile = a.mt == 2 ? grp : 0;
-        const int m = tile * 128 + 32 * (warp & 3) + lane;   // slice row of A (this thread's TMEM lane)
+        const int m = tile * 128 + 32 * (warp & 3) + lane;
         const int nblk = a.nb / 16;
         const int b0 = a.mt == 2 ? 0 : (grp == 0 ? 0 : (nblk + 1) / 2);
         const int b1 = a.mt == 2 ? nblk : (grp == 0 ? (nblk + 1) / 2 : nblk);
-        const bool rowok = m < SA.rows;
+        const bool rowok = m < S * a.kx;
         const int s = rowok ? m / a.kx : 0, j = rowok ? m - s * a.kx : 0;
-        float2* accr = acc + ((size_t)(a.mt == 2 ? 0 : grp) * SA.rows + (rowok ? m : 0)) * a.acc_stride;
-        const int* ez = sym ? exx : exz;
-        const int ebase = rowok ? exx[j] - 16 - 8 * s : 0;
+        float2* accr = accg + (size_t)(rowok ? m : 0) * kz;
+        const int ebase = rowok ? exx[j] - 14 - 7 * s : 0;
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * tile);
         for (int blk = b0; blk < b1; ++blk) {
             float v[16];
             tc_ld16(taddr + (uint32_t)(16 * blk), v);   // every lane of the warp takes part
             if (!rowok) continue;
+            // the block's entries in segments of at most kz consecutive columns (distinct l): the
+            // segment's sums are read together, updated, and written back together
+            const int seg = kz < 16 ? kz : 16;
+            for (int q0 = 0; q0 < 16; q0 += seg) {
+                float2 r[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int col = 16 * blk + q;
-                if (col >= SB.rows) continue;
-                const int u = col / a.kz, l = col - u * a.kz;
-                // the exact product D 2^(E_j + F_l - 8 (s + u + 2)) added into the (s, j, l) sum
-                const float x = scale2(v[q], ebase + ez[l] - 8 * u);
-                float2 r = accr[l];
-                const float sm = r.x + x;
-                const float bb = sm - r.x;
-                r.y += (r.x - (sm - bb)) + (x - bb);
-                r.x = sm;
-                accr[l] = r;
+                for (int q = 0; q < 16; ++q) {
+                    const int col = 16 * blk + q;
+                    if (q >= q0 && q < q0 + seg && col < S * kz) r[q] = accr[col % kz];
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = 16 * blk + q;
+                    if (q < q0 || q >= q0 + seg || col >= S * kz) continue;
+                    const int u = col / kz, l = col - u * kz;
+                    // the exact product D 2^(E_j + F_l - 7 (s + u + 2)) added into the (s, j, l) sum
+                    const float x = scale2(v[q], ebase + exz[l] - 7 * u);
+                    const float sm = r[q].x + x;
+                    const float bb = sm - r[q].x;
+                    r[q].y += (r[q].x - (sm - bb)) + (x - bb);
+                    r[q].x = sm;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = 16 * blk + q;
+                    if (q >= q0 && q < q0 + seg && col < S * kz) accr[col % kz] = r[q];
+                }
             }
         }
         tc_fence_before();
-        __syncthreads();   // TMEM read before the next batch's first MMA overwrites it
+        __syncthreads();   // TMEM read (and sums written) before the next MMAs overwrite it
+    };
+
+    if (nch > 0) {
+        stage_raw<TX>(smem + a.off_rx, a.rsx, X, a.ldx, a.kx, r0, r1);
+        if (!sym) stage_raw<double>(smem + a.off_rz, a.rsz, a.Z, a.ldz, a.kz, r0, r1);
+        cp_async_commit();
+    }
+    int inbatch = 0;   // chunks accumulated in TMEM since the last drain
+    for (int c = 0; c < nch && !dead; ++c) {
+        const int b = c & 1;
+        const long long c0 = r0 + (long long)c * GT_CH;
+        // next chunk's raw rows in flight while this one is split
+        if (c + 1 < nch) {
+            stage_raw<TX>(smem + a.off_rx + (b ^ 1) * GT_CH * a.rsx, a.rsx, X, a.ldx, a.kx, c0 + GT_CH, r1);
+            if (!sym) stage_raw<double>(smem + a.off_rz + (b ^ 1) * GT_CH * a.rsz, a.rsz, a.Z, a.ldz, a.kz, c0 + GT_CH, r1);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        // the MMAs of chunk c - 2 have read operand buffer b
+        if (!wait_buf(b)) { dead = true; break; }
+        unsigned char* opa = smem + a.off_a + b * a.opbytes_a;
+        unsigned char* opb = sym ? opa : smem + a.off_b + b * a.opbytes_b;
+        slice_chunk<TX>(smem + a.off_rx + b * GT_CH * a.rsx, a.rsx, a.kx, S, exx, opa);
+        if (!sym) slice_chunk<double>(smem + a.off_rz + b * GT_CH * a.rsz, a.rsz, a.kz, S, exz, opb);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int t = 0; t < GT_CH / 16; ++t) {
+                // K step t: the core matrices 2t and 2t + 1 of every 8-row group
+                const uint64_t bd = tc_desc(smem_u32(opb) + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
+                for (int mt = 0; mt < a.mt; ++mt) {
+                    const uint64_t ad = tc_desc(smem_u32(opa) + (uint32_t)(16 * mt) * GT_SBO + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
+                    tc_mma(tmem + (uint32_t)(256 * mt), ad, bd, idesc, (inbatch > 0 || t > 0) ? 1u : 0u);
+                }
+            }
+            tc_commit(smem_u32(&mbar[b]));
+        }
+        pend[b] = 1;
+        ++inbatch;
+        if (inbatch == GT_BATCH_CHUNKS || c + 1 == nch) {
+            // every MMA of the batch done: the other buffer's commit came first
+            if (!wait_buf(b ^ 1) || !wait_buf(b)) { dead = true; break; }
+            drain();
+            inbatch = 0;
+        }
     }
     // ---- after a failed wait: the MMAs in flight finish before the TMEM is freed
     if (dead && tid == 0) {
         *((volatile int*)a.err) = 1;
-        if (pending) mbar_wait_bounded(smem_u32(&mbar), phase, a.spin_budget > TMA_DRAIN_MIN ? a.spin_budget : TMA_DRAIN_MIN);
+        const long long drain_budget = a.spin_budget > TMA_DRAIN_MIN ? a.spin_budget : TMA_DRAIN_MIN;
+        for (int b = 0; b < 2; ++b)
+            if (pend[b]) mbar_wait_bounded(smem_u32(&mbar[b]), phase[b], drain_budget);
     }
+    cp_async_wait<0>();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tc_dealloc(tmem, a.tmem_cols);
     }
-    // ---- the CTA's partial X^T Z: the (s, j, l) sums added over s (and over the two column halves)
-    const int ncop = a.acc_copies;
-    for (int o = tid; o < a.kx * a.kz; o += GT_THREADS) {
-        const int j = o / a.kz, l = o - j * a.kz;
+    // ---- the CTA's partial X^T Z: the (s, j, l) sums added over s
+    __threadfence_block();
+    for (int o = tid; o < a.kx * kz; o += GT_THREADS) {
+        const int j = o / kz, l = o - j * kz;
         float h = 0.f, lo = 0.f;
-        for (int cpy = 0; cpy < ncop; ++cpy)
-            for (int s = 0; s < GT_S; ++s) {
-                const float2 r = acc[((size_t)cpy * SA.rows + s * a.kx + j) * a.acc_stride + l];
-                // double-float add of (r.x, r.y) into (h, lo)
-                const float sm = h + r.x;
-                const float bb = sm - h;
-                lo += ((h - (sm - bb)) + (r.x - bb)) + r.y;
-                h = sm;
-            }
-        a.partials[(size_t)blockIdx.x * a.kx * a.kz + o] = (double)h + (double)lo;
+        for (int s = 0; s < S; ++s) {
+            const float2 r = accg[(size_t)(s * a.kx + j) * kz + l];
+            // double-float add of (r.x, r.y) into (h, lo)
+            const float sm = h + r.x;
+            const float bb = sm - h;
+            lo += ((h - (sm - bb)) + (r.x - bb)) + r.y;
+            h = sm;
+        }
+        a.partials[(size_t)blockIdx.x * a.kx * kz + o] = (double)h + (double)lo;
     }
     __threadfence();
     __syncthreads();
@@ -384,38 +421,80 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     __syncthreads();
     if (s_last) {
         __threadfence();
-        for (int o = tid; o < a.kx * a.kz; o += GT_THREADS) {
-            const int j = o / a.kz, l = o - j * a.kz;
+        for (int o = tid; o < a.kx * kz; o += GT_THREADS) {
+            const int j = o / kz, l = o - j * kz;
             if (sym && l < j) continue;
             double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             int bx = 0;
             for (; bx + 8 <= (int)gridDim.x; bx += 8) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) s8[u] += __ldcg(&a.partials[(size_t)(bx + u) * a.kx * a.kz + o]);
+                for (int u = 0; u < 8; ++u) s8[u] += __ldcg(&a.partials[(size_t)(bx + u) * a.kx * kz + o]);
             }
-            for (int u = 0; bx < (int)gridDim.x; ++bx, ++u) s8[u] += __ldcg(&a.partials[(size_t)bx * a.kx * a.kz + o]);
-            const double v = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+            double tail = 0.0;
+            for (; bx < (int)gridDim.x; ++bx) tail += __ldcg(&a.partials[(size_t)bx * a.kx * kz + o]);
+            const double v = (((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]))) + tail;
             a.out[o] = v;
-            if (sym) a.out[(size_t)l * a.kz + j] = v;
+            if (sym) a.out[(size_t)l * kz + j] = v;
         }
         if (tid == 0) *a.ticket = 0u;
     }
 }
 
+// Column maxima of |x| (hi parts) into mx[0..k) as float bits (atomicMax; mx zeroed before).
+template <typename T>
+__global__ void __launch_bounds__(256) k_colmax(const T* X, long long ld, int k, long long n, unsigned int* mx) {
+    __shared__ unsigned int smx[64];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) smx[j] = 0u;
+    __syncthreads();
+    const int kp2 = (k + 1) / 2;
+    const int rpb = blockDim.x / kp2;   // rows per pass of the block
+    const int cp = threadIdx.x % kp2, rg = threadIdx.x / kp2;
+    if (rg < rpb) {
+        float m0 = 0.f, m1 = 0.f;
+        for (long long i = (long long)blockIdx.x * rpb + rg; i < n; i += (long long)gridDim.x * rpb) {
+            float h0, h1 = 0.f, l;
+            if constexpr (sizeof(T) == 4) {   // dfp: the hi parts of the column pair
+                const float2 v = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(X) + ((i * ld + 2 * cp) >> 1) * 4);
+                h0 = v.x;
+                h1 = 2 * cp + 1 < k ? v.y : 0.f;
+            } else {
+                split_bits(reinterpret_cast<const double*>(X)[i * ld + 2 * cp], h0, l);
+                if (2 * cp + 1 < k) split_bits(reinterpret_cast<const double*>(X)[i * ld + 2 * cp + 1], h1, l);
+            }
+            m0 = fmaxf(m0, fabsf(h0));
+            m1 = fmaxf(m1, fabsf(h1));
+        }
+        atomicMax(&smx[2 * cp], __float_as_uint(m0));
+        if (2 * cp + 1 < k) atomicMax(&smx[2 * cp + 1], __float_as_uint(m1));
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) atomicMax(&mx[j], smx[j]);
+}
+
 }  // namespace
+
+int gram_tc_digits(int kx, int kz) {
+    const int k = kx > kz ? kx : kz;
+    return k <= 36 ? 7 : (k <= 42 ? 6 : 0);
+}
 
 size_t gram_tc_partials_doubles(int kx, int kz, int grid) { return (size_t)grid * kx * kz; }
 
+size_t gram_tc_workspace_bytes(int kx, int kz, int grid) {
+    return (size_t)grid * GT_SMAX * kx * kz * sizeof(float2) + 128 * sizeof(unsigned int);
+}
+
 bool gram_tc_supported(int tx, int kx, int kz, bool sym) {
-    if (kx < 1 || kz < 1 || kx > GRAM_TC_KMAX || kz > GRAM_TC_KMAX) return false;
+    if (kx < 1 || kz < 1 || gram_tc_digits(kx, kz) == 0) return false;
     if (sym && kx != kz) return false;
     return tx == T_F64 || tx == T_DF64;
 }
 
 cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const double* Z, long long ldz, int kz, long long n,
-                           bool sym, double* partials, unsigned int* ticket, double* out, int* err, long long spin_budget,
-                           int sm_count, cudaStream_t s) {
-    if (!gram_tc_supported(tx, kx, kz, sym) || n < 1) return cudaErrorInvalidValue;
+                           bool sym, double* partials, unsigned int* ticket, double* out, void* work, int* err,
+                           long long spin_budget, int sm_count, cudaStream_t s) {
+    if (sym) kz = kx;
+    if (!gram_tc_supported(tx, kx, kz, sym) || n < 1 || !work) return cudaErrorInvalidValue;
     if (tx == T_DF64 && (ldx & 1)) return cudaErrorInvalidValue;   // column pairs need an even leading dimension
     GramTcArgs a{};
     a.X = X;
@@ -423,34 +502,49 @@ cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const d
     a.kx = kx;
     a.Z = sym ? nullptr : Z;
     a.ldz = ldz;
-    a.kz = sym ? kx : kz;
+    a.kz = kz;
     a.n = n;
-    a.partials = partials;
-    a.ticket = ticket;
-    a.out = out;
-    a.err = err;
-    a.spin_budget = spin_budget;
-    const int ma = GT_S * a.kx, mb = GT_S * a.kz;
+    a.S = gram_tc_digits(kx, kz);
+    const int ma = a.S * kx, mb = a.S * kz;
     a.mt = ma > 128 ? 2 : 1;
     a.nb = (mb + 15) / 16 * 16;
-    const size_t bytes_a = (size_t)a.mt * 16 * GT_SBO;
-    const size_t bytes_b = sym ? 0 : (size_t)(a.nb / 8) * GT_SBO;
-    a.off_b = (int)bytes_a;
-    a.off_sc = (int)(bytes_a + bytes_b);
-    a.off_acc = a.off_sc + 4 * 64 * 4;
-    a.acc_stride = a.kz | 1;   // odd: the per-thread rows of the sums spread over the banks
-    a.acc_copies = a.mt == 2 ? 1 : 2;
-    a.zero_bytes = (int)(((size_t)a.off_acc + (size_t)a.acc_copies * ma * a.acc_stride * sizeof(float2) + 15) & ~(size_t)15);
-    size_t smem = (size_t)a.zero_bytes + 128;
-    // at least 116 KB: one CTA per SM, so that no second CTA waits for the TMEM it holds
+    if (a.nb > 256) return cudaErrorInvalidValue;
+    // shared memory: operand buffers (two each), then the raw stages (two each)
+    a.opbytes_a = a.mt * 16 * GT_SBO;
+    a.opbytes_b = sym ? 0 : (a.nb / 8) * GT_SBO;
+    a.off_a = 0;
+    a.off_b = 2 * a.opbytes_a;
+    a.off_rx = a.off_b + 2 * a.opbytes_b;
+    a.rsx = tx == T_DF64 ? ((kx + 1) / 2) * 16 : ((kx * 8 + 15) / 16) * 16;
+    a.rsz = sym ? 0 : ((kz * 8 + 15) / 16) * 16;
+    a.off_rz = a.off_rx + 2 * GT_CH * a.rsx;
+    size_t smem = (size_t)a.off_rz + (size_t)2 * GT_CH * a.rsz + 128;
+    // at least 116 KB: one CTA per SM, so that no second CTA waits for the TMEM one holds
     if (smem < 116 * 1024) smem = 116 * 1024;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     uint32_t cols = a.mt == 2 ? 512u : 32u;
     while (cols < (uint32_t)a.nb) cols <<= 1;
     a.tmem_cols = cols;
-    const long long nbat = (n + GT_BATCH_ROWS - 1) / GT_BATCH_ROWS;
-    const int grid = (int)std::min<long long>(nbat, (long long)sm_count);
-    cudaError_t e;
+    // contiguous rows per CTA, whole chunks
+    const long long nchunks = (n + GT_CH - 1) / GT_CH;
+    int grid = (int)std::min<long long>(nchunks, (long long)sm_count);
+    a.rows_per_cta = ((nchunks + grid - 1) / grid) * GT_CH;
+    grid = (int)((n + a.rows_per_cta - 1) / a.rows_per_cta);
+    unsigned int* mx = static_cast<unsigned int*>(work);
+    a.mx = mx;
+    a.acc = reinterpret_cast<float2*>(static_cast<unsigned char*>(work) + 128 * sizeof(unsigned int));
+    a.partials = partials;
+    a.ticket = ticket;
+    a.out = out;
+    a.err = err;
+    a.spin_budget = spin_budget;
+    cudaError_t e = cudaMemsetAsync(mx, 0, 128 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    const int cgrid = sm_count * 2;
+    if (tx == T_DF64) k_colmax<dfp><<<cgrid, 256, 0, s>>>(static_cast<const dfp*>(X), ldx, kx, n, mx);
+    else k_colmax<double><<<cgrid, 256, 0, s>>>(static_cast<const double*>(X), ldx, kx, n, mx);
+    if (!sym) k_colmax<double><<<cgrid, 256, 0, s>>>(Z, ldz, kz, n, mx + kx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (tx == T_DF64) {
         e = cudaFuncSetAttribute(k_gram_tc<dfp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

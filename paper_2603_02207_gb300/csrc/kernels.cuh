@@ -221,17 +221,20 @@ cudaError_t launch_mul_small(const double* X, long long ldx, int n, int kx, int 
                              long long ld64, int t2, void* out2, long long ld2, cudaStream_t s);
 // doubles of Gram partials needed for a launch with `grid` CTAs
 size_t gram_partials_doubles(int kx, int kz, bool sym, int grid);
-// The same Gram X^T Z on the tensor cores (gram_tc.cu): BF16 digit slices of both operands in
-// fixed point per column and row batch, exact FP32 products in TMEM, double-float sums. X of type
-// T_F64 or T_DF64 (column pairs, even ldx), Z FP64 (ignored when sym), kx, kz <= GRAM_TC_KMAX;
-// partials: gram_tc_partials_doubles(kx, kz, sm_count) doubles; ticket zero-initialised (reset by the
-// last CTA); err set to 1 when a bounded wait runs out. One CTA per SM.
-constexpr int GRAM_TC_KMAX = 40;
+// The same Gram X^T Z on the tensor cores (gram_tc.cu): BF16 fixed-point digit slices of both
+// operands (per-column scales from a maximum pre-pass), exact FP32 products in TMEM, double-float
+// sums. X of type T_F64 or T_DF64 (column pairs, even ldx), Z FP64 (ignored when sym); widths up to
+// 42 (gram_tc_digits: 7 digits up to 36, 6 up to 42, 0 = unsupported); partials:
+// gram_tc_partials_doubles(kx, kz, sm_count) doubles; work: gram_tc_workspace_bytes(kx, kz,
+// sm_count) bytes; ticket zero-initialised (reset by the last CTA); err set to 1 when a bounded wait
+// runs out. One CTA per SM.
+int gram_tc_digits(int kx, int kz);
 bool gram_tc_supported(int tx, int kx, int kz, bool sym);
 size_t gram_tc_partials_doubles(int kx, int kz, int grid);
+size_t gram_tc_workspace_bytes(int kx, int kz, int grid);
 cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const double* Z, long long ldz, int kz, long long n,
-                           bool sym, double* partials, unsigned int* ticket, double* out, int* err, long long spin_budget,
-                           int sm_count, cudaStream_t s);
+                           bool sym, double* partials, unsigned int* ticket, double* out, void* work, int* err,
+                           long long spin_budget, int sm_count, cudaStream_t s);
 
 // out (kx x kz, row-major) = X^T Z, X: n x kx (type tx), Z: n x kz (type tz); sym: X == Z
 cudaError_t launch_gram(int tx, const void* X, long long ldx, int kx, int tz, const void* Z, long long ldz, int kz,

@@ -127,3 +127,26 @@ def test_forward_with_either_gram_kernel(L, h, prec):
     assert abs(est["tensor"] - est["dfloat"]) <= 1e-12 * abs(est["dfloat"])
     want = O.logdet_leja(A, 0.05, 12.05, 20, 99, 4, f32=(prec == "f32"))["estimate"]
     assert abs(est["tensor"] - want) <= TOL[prec] * abs(want)
+
+
+@pytest.mark.parametrize("layout", ["df64", "f64"])
+def test_gram_many_exact_batches_per_cta(L, h, layout):
+    """More than 4096 rows per CTA (the exact FP32 sums are drained into the double-float sums
+    several times), with a ragged last chunk."""
+    torch = need_gpu()
+    n, k = 152 * 4096 * 2 + 4097, 33
+    X = _cols(n, k, seed=21)
+    if layout == "df64":
+        B = L.df64_block(X)
+        hi = B.reshape(n, -1, 4)
+        xr = np.zeros((n, B.shape[1] // 2))
+        xr[:, 0::2] = hi[:, :, 0].astype(np.float64) + hi[:, :, 2].astype(np.float64)
+        xr[:, 1::2] = hi[:, :, 1].astype(np.float64) + hi[:, :, 3].astype(np.float64)
+        X, dX = xr[:, :k], torch.as_tensor(B).cuda()
+    else:
+        dX = torch.as_tensor(X).cuda()
+    got = L.ll_gram(h, dX, None, method="tensor", kx=k).cpu().numpy()
+    assert np.all(np.abs(got - X.T @ X) <= 1e-13 * _bound(X, X))
+    Z = np.sign(_cols(n, 20, seed=22))
+    got = L.ll_gram(h, torch.as_tensor(X).cuda(), torch.as_tensor(Z).cuda(), method="tensor").cpu().numpy()
+    assert np.all(np.abs(got - X.T @ Z) <= 1e-13 * _bound(X, Z))
