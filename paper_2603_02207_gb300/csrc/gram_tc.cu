@@ -15,7 +15,8 @@
 //     B holds [U_0; ...; U_{S-1}] (S kz rows), D = A B^T (S kx x S kz) in TMEM;
 //   * every 4096 rows (and at the end of the CTA's rows) each thread reads its D row (s, j) from
 //     TMEM, scales the entries exactly by powers of two and adds them into double-float sums per
-//     (s, j, l) in global memory (the CTA's own slice of the workspace; an L2-resident region);
+//     (s, j, l) in global memory (the CTA's own slice of the workspace, an L2-resident region; two
+//     sets when the two groups of drain warps split the columns of one M tile);
 //     at the end the sums over s give the CTA's partial X^T Z, and the last CTA adds the
 //     partials in CTA order.
 // The products carry no rounding; the only roundings are the digit truncation (below 2^-49, or
@@ -248,7 +249,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     const int kz = sym ? a.kx : a.kz;
     int* exx = s_ex;
     int* exz = sym ? s_ex : s_ex + 64;
-    float2* accg = a.acc + (size_t)blockIdx.x * S * a.kx * kz;
+    // the CTA's sums: one set per group of four drain warps when both groups read one M tile
+    const int ncopy = a.mt == 2 ? 1 : 2;
+    const size_t cset = (size_t)S * a.kx * kz;
+    float2* accg = a.acc + (size_t)blockIdx.x * 2 * cset;
 
     // column exponents: max |x| < 2^(E - 1); all-zero columns take E = 0 (their digits are zero)
     for (int j = tid; j < a.kx + (sym ? 0 : a.kz); j += GT_THREADS) {
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     }
     // zero both operand buffers (slice rows past S k stay zero) and this CTA's sums
     for (int i = tid * 16; i < a.off_rx; i += GT_THREADS * 16) *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < S * a.kx * kz; i += GT_THREADS) accg[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < (int)(ncopy * cset); i += GT_THREADS) accg[i] = make_float2(0.f, 0.f);
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
         const int b1 = a.mt == 2 ? nblk : (grp == 0 ? (nblk + 1) / 2 : nblk);
         const bool rowok = m < S * a.kx;
         const int s = rowok ? m / a.kx : 0, j = rowok ? m - s * a.kx : 0;
-        float2* accr = accg + (size_t)(rowok ? m : 0) * kz;
+        float2* accr = accg + (size_t)(a.mt == 2 ? 0 : grp) * cset + (size_t)(rowok ? m : 0) * kz;
         const int ebase = rowok ? exx[j] - 14 - 7 * s : 0;
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * tile);
         for (int blk = b0; blk < b1; ++blk) {
@@ -405,8 +409,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     for (int o = tid; o < a.kx * kz; o += GT_THREADS) {
         const int j = o / kz, l = o - j * kz;
         float h = 0.f, lo = 0.f;
-        for (int s = 0; s < S; ++s) {
-            const float2 r = accg[(size_t)(s * a.kx + j) * kz + l];
+        for (int q = 0; q < ncopy * S; ++q) {
+            const int cpy = q / S, s = q - cpy * S;
+            const float2 r = accg[cpy * cset + (size_t)(s * a.kx + j) * kz + l];
             // double-float add of (r.x, r.y) into (h, lo)
             const float sm = h + r.x;
             const float bb = sm - h;
@@ -481,7 +486,7 @@ int gram_tc_digits(int kx, int kz) {
 size_t gram_tc_partials_doubles(int kx, int kz, int grid) { return (size_t)grid * kx * kz; }
 
 size_t gram_tc_workspace_bytes(int kx, int kz, int grid) {
-    return (size_t)grid * GT_SMAX * kx * kz * sizeof(float2) + 128 * sizeof(unsigned int);
+    return (size_t)grid * 2 * GT_SMAX * kx * kz * sizeof(float2) + 128 * sizeof(unsigned int);
 }
 
 bool gram_tc_supported(int tx, int kx, int kz, bool sym) {
