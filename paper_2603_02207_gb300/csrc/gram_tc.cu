@@ -15,16 +15,16 @@
 //     B holds [U_0; ...; U_{S-1}] (S kz rows), D = A B^T (S kx x S kz) in TMEM;
 //   * every 4096 rows (and at the end of the CTA's rows) each thread reads its D row (s, j) from
 //     TMEM, scales the entries exactly by powers of two and adds them into double-float sums per
-//     (s, j, l) in global memory (the CTA's own slice of the workspace, an L2-resident region; two
-//     sets when the two groups of drain warps split the columns of one M tile);
+//     (s, j, l) in global memory (the CTA's own slice of the workspace, an L2-resident region);
 //     at the end the sums over s give the CTA's partial X^T Z, and the last CTA adds the
 //     partials in CTA order.
 // The products carry no rounding; the only roundings are the digit truncation (below 2^-49, or
 // 2^-42, of each column's maximum) and the double-float sums (about 2^-48 relative).
 //
 // Pipeline of a CTA over its contiguous rows, in chunks of GT_CH rows: the raw rows of chunk c + 1
-// are copied to shared memory (cp.async) while chunk c is split into digits, and the digits of
-// chunk c go to one of two operand buffers while the MMAs of chunk c - 1 read the other. Operands
+// are copied to shared memory (cp.async) while chunk c is split into digits (one thread per item
+// of 4 rows x one column pair), and the digits of chunk c go to one of two operand buffers while
+// the MMAs of chunk c - 1 read the other. Operands
 // use the canonical K-major layout without swizzle: 8 x 8 BF16 core matrices (8 rows of 16 bytes),
 // K-adjacent core matrices 128 bytes apart, 8-row groups GT_SBO = 1040 bytes apart (16 bytes of
 // padding spread the digit stores over the banks). One thread issues the MMAs and commits each
@@ -41,7 +41,7 @@ constexpr int GT_CH = 64;                      // rows per chunk (MMA K: 4 steps
 constexpr int GT_BATCH_CHUNKS = 64;            // chunks summed exactly in TMEM (4096 rows)
 constexpr int GT_LBO = 128;                    // bytes between K-adjacent core matrices
 constexpr int GT_SBO = (GT_CH / 8) * GT_LBO + 16;   // bytes between 8-row groups (1040)
-constexpr int GT_THREADS = 256;
+constexpr int GT_MAX_THREADS = 576;           // one thread per digit item of a chunk (at least 256)
 constexpr int GT_SMAX = 7;
 
 // ---- tcgen05 / TMEM wrappers (inline PTX) ----------------------------------------------------
@@ -144,7 +144,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 template <typename T>
 __device__ __forceinline__ void stage_raw(unsigned char* st, int rs, const T* X, long long ld, int k, long long c0, long long end) {
     const int U = Raw<T>::units(k);
-    for (int e = threadIdx.x; e < GT_CH * U; e += GT_THREADS) {
+    for (int e = threadIdx.x; e < GT_CH * U; e += blockDim.x) {
         const int r = e / U, u = e - r * U;
         const long long row = c0 + r;
         const bool ok = row < end;
@@ -152,63 +152,61 @@ __device__ __forceinline__ void stage_raw(unsigned char* st, int rs, const T* X,
     }
 }
 
-// The staged chunk's digits into the operand buffer `op`: slice row m = s k + j, K index = the row
-// within the chunk. One item = 4 rows x one column pair; per digit and column the 4 rows' BF16
-// digits make one 8-byte store (half a core-matrix row). ex[j]: the column exponents E_j.
+// One item of the staged chunk's digits into the operand buffer `op`: rows 4 g4 .. 4 g4 + 3 of the
+// chunk, columns 2 cp and 2 cp + 1; slice row m = s k + j, K index = the row within the chunk. Per
+// digit and column the 4 rows' BF16 digits make one 8-byte store (half a core-matrix row).
+// ex[j]: the column exponents E_j.
 template <typename T>
-__device__ __forceinline__ void slice_chunk(const unsigned char* st, int rs, int k, int S, const int* ex, unsigned char* op) {
+__device__ __forceinline__ void slice_item(const unsigned char* st, int rs, int k, int S, const int* ex, unsigned char* op,
+                                           int cp, int g4) {
     const f2x k128 = f2_pack(128.f, 128.f);
     const f2x magic = f2_pack(12582912.f, 12582912.f);   // 1.5 * 2^23: adding and subtracting it rounds to an integer
-    const int kp2 = (k + 1) / 2;
-    for (int it = threadIdx.x; it < (GT_CH / 4) * kp2; it += GT_THREADS) {
-        const int cp = it % kp2, g4 = it / kp2;   // lanes vary the column pair first
-        const int j0 = 2 * cp;
-        // 2^-E_j as the product of two floats (E_j may leave the normal range of one)
-        const int e0 = ex[j0], e1 = j0 + 1 < k ? ex[j0 + 1] : 0;
-        const int a0 = max(-126, min(127, -e0)), a1 = max(-126, min(127, -e1));
-        const f2x sa = f2_pack(pow2f(a0), pow2f(a1)), sb = f2_pack(pow2f(-e0 - a0), pow2f(-e1 - a1));
-        f2x vh[4], vl[4];
+    const int j0 = 2 * cp;
+    // 2^-E_j as the product of two floats (E_j may leave the normal range of one)
+    const int e0 = ex[j0], e1 = j0 + 1 < k ? ex[j0 + 1] : 0;
+    const int a0 = max(-126, min(127, -e0)), a1 = max(-126, min(127, -e1));
+    const f2x sa = f2_pack(pow2f(a0), pow2f(a1)), sb = f2_pack(pow2f(-e0 - a0), pow2f(-e1 - a1));
+    f2x vh[4], vl[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        f2x hi, lo;
+        Raw<T>::pair(st + (4 * g4 + r) * rs, cp, k, hi, lo);
+        vh[r] = f2_mul(f2_mul(hi, sa), sb);
+        vl[r] = f2_mul(f2_mul(lo, sa), sb);
+    }
+    // K index 4 g4 .. 4 g4 + 3: core matrix g4 / 2 along K, bytes 8 (g4 & 1) .. + 7 of its row
+    unsigned char* o0 = op + (g4 >> 1) * GT_LBO + (g4 & 1) * 8;
+#pragma unroll
+    for (int s = 0; s < GT_SMAX; ++s) {
+        if (s >= S) break;
+        uint32_t w0[2], w1[2];   // 4 rows of BF16 digits for columns j0 and j0 + 1
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            f2x hi, lo;
-            Raw<T>::pair(st + (4 * g4 + r) * rs, cp, k, hi, lo);
-            vh[r] = f2_mul(f2_mul(hi, sa), sb);
-            vl[r] = f2_mul(f2_mul(lo, sa), sb);
+            const f2x h = f2_mul(vh[r], k128);
+            const f2x l = f2_mul(vl[r], k128);
+            const f2x t = f2_sub(f2_add(h, magic), magic);
+            const f2x d = f2_sub(h, t);   // exact remainder in [-1/2, 1/2]
+            // TwoSum(d, l): the remainder as a normalised double-float pair again
+            const f2x sm = f2_add(d, l);
+            const f2x bb = f2_sub(sm, d);
+            vl[r] = f2_add(f2_sub(d, f2_sub(sm, bb)), f2_sub(l, bb));
+            vh[r] = sm;
+            float t0, t1;
+            f2_unpack(t, t0, t1);
+            // |t| <= 64: a BF16 holds it exactly in the float's upper 16 bits
+            if (r & 1) {   // (row r - 1, row r) as the low and high halves of one word
+                asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w0[r >> 1]) : "r"(w0[r >> 1]), "r"(__float_as_uint(t0)));
+                asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w1[r >> 1]) : "r"(w1[r >> 1]), "r"(__float_as_uint(t1)));
+            } else {
+                w0[r >> 1] = __float_as_uint(t0);
+                w1[r >> 1] = __float_as_uint(t1);
+            }
         }
-        // K index 4 g4 .. 4 g4 + 3: core matrix g4 / 2 along K, bytes 8 (g4 & 1) .. + 7 of its row
-        const int koff = (g4 >> 1) * GT_LBO + (g4 & 1) * 8;
-#pragma unroll
-        for (int s = 0; s < GT_SMAX; ++s) {
-            if (s >= S) break;
-            uint32_t w0[2], w1[2];   // 4 rows of BF16 digits for columns j0 and j0 + 1
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const f2x h = f2_mul(vh[r], k128);
-                const f2x l = f2_mul(vl[r], k128);
-                const f2x t = f2_sub(f2_add(h, magic), magic);
-                const f2x d = f2_sub(h, t);   // exact remainder in [-1/2, 1/2]
-                // TwoSum(d, l): the remainder as a normalised double-float pair again
-                const f2x sm = f2_add(d, l);
-                const f2x bb = f2_sub(sm, d);
-                vl[r] = f2_add(f2_sub(d, f2_sub(sm, bb)), f2_sub(l, bb));
-                vh[r] = sm;
-                float t0, t1;
-                f2_unpack(t, t0, t1);
-                // |t| <= 64: a BF16 holds it exactly in the float's upper 16 bits
-                if (r & 1) {   // (row r - 1, row r) as the low and high halves of one word
-                    asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w0[r >> 1]) : "r"(w0[r >> 1]), "r"(__float_as_uint(t0)));
-                    asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(w1[r >> 1]) : "r"(w1[r >> 1]), "r"(__float_as_uint(t1)));
-                } else {
-                    w0[r >> 1] = __float_as_uint(t0);
-                    w1[r >> 1] = __float_as_uint(t1);
-                }
-            }
-            const int m0 = s * k + j0;
-            *reinterpret_cast<uint2*>(op + (m0 >> 3) * GT_SBO + koff + (m0 & 7) * 16) = make_uint2(w0[0], w0[1]);
-            if (j0 + 1 < k) {
-                const int m1 = m0 + 1;
-                *reinterpret_cast<uint2*>(op + (m1 >> 3) * GT_SBO + koff + (m1 & 7) * 16) = make_uint2(w1[0], w1[1]);
-            }
+        const int m0 = s * k + j0;
+        *reinterpret_cast<uint2*>(o0 + (m0 >> 3) * GT_SBO + (m0 & 7) * 16) = make_uint2(w0[0], w0[1]);
+        if (j0 + 1 < k) {
+            const int m1 = m0 + 1;
+            *reinterpret_cast<uint2*>(o0 + (m1 >> 3) * GT_SBO + (m1 & 7) * 16) = make_uint2(w1[0], w1[1]);
         }
     }
 }
@@ -235,7 +233,7 @@ struct GramTcArgs {
 };
 
 template <typename TX>
-__global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
+__global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t s_tmem;
@@ -249,19 +247,26 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     const int kz = sym ? a.kx : a.kz;
     int* exx = s_ex;
     int* exz = sym ? s_ex : s_ex + 64;
-    // the CTA's sums: one set per group of four drain warps when both groups read one M tile
-    const int ncopy = a.mt == 2 ? 1 : 2;
+    // the CTA's (s, j, l) sums
     const size_t cset = (size_t)S * a.kx * kz;
-    float2* accg = a.acc + (size_t)blockIdx.x * 2 * cset;
+    float2* accg = a.acc + (size_t)blockIdx.x * cset;
+    // this thread's digit item of every chunk: 4 rows x one column pair of X (or of Z)
+    const int kp2x = (a.kx + 1) / 2, kp2z = (kz + 1) / 2;
+    const int itx = (GT_CH / 4) * kp2x, itz = sym ? 0 : (GT_CH / 4) * kp2z;
+    const bool on_x = tid < itx, on_z = !on_x && tid < itx + itz;
+    const int iz = tid - itx;
+    const int my_cp = on_x ? tid % kp2x : (on_z ? iz % kp2z : 0);
+    const int my_g4 = on_x ? tid / kp2x : (on_z ? iz / kp2z : 0);
 
     // column exponents: max |x| < 2^(E - 1); all-zero columns take E = 0 (their digits are zero)
-    for (int j = tid; j < a.kx + (sym ? 0 : a.kz); j += GT_THREADS) {
+    const int nt = blockDim.x;
+    for (int j = tid; j < a.kx + (sym ? 0 : a.kz); j += nt) {
         const float m = __uint_as_float(a.mx[j]);
         s_ex[j < a.kx ? j : 64 + (j - a.kx)] = m > 0.f ? ilogbf(m) + 2 : 0;
     }
     // zero both operand buffers (slice rows past S k stay zero) and this CTA's sums
-    for (int i = tid * 16; i < a.off_rx; i += GT_THREADS * 16) *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < (int)(ncopy * cset); i += GT_THREADS) accg[i] = make_float2(0.f, 0.f);
+    for (int i = tid * 16; i < a.off_rx; i += nt * 16) *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < (int)cset; i += nt) accg[i] = make_float2(0.f, 0.f);
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
@@ -295,18 +300,16 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     // the D rows of this thread's TMEM lane, scaled exactly, into the (s, j, l) sums
     auto drain = [&]() {
         tc_fence_after();
-        const int grp = warp >> 2;   // two groups of four warps: both M tiles, or the two halves of one
-        const int tile = a.mt == 2 ? grp : 0;
+        // warps 4 t .. 4 t + 3 read M tile t (warp w reaches TMEM lanes 32 (w % 4) .. + 31)
+        const int tile = warp >> 2;
         const int m = tile * 128 + 32 * (warp & 3) + lane;
-        const int nblk = a.nb / 16;
-        const int b0 = a.mt == 2 ? 0 : (grp == 0 ? 0 : (nblk + 1) / 2);
-        const int b1 = a.mt == 2 ? nblk : (grp == 0 ? (nblk + 1) / 2 : nblk);
-        const bool rowok = m < S * a.kx;
+        const int nblk = tile < a.mt ? a.nb / 16 : 0;
+        const bool rowok = tile < a.mt && m < S * a.kx;
         const int s = rowok ? m / a.kx : 0, j = rowok ? m - s * a.kx : 0;
-        float2* accr = accg + (size_t)(a.mt == 2 ? 0 : grp) * cset + (size_t)(rowok ? m : 0) * kz;
+        float2* accr = accg + (size_t)(rowok ? m : 0) * kz;
         const int ebase = rowok ? exx[j] - 14 - 7 * s : 0;
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * tile);
-        for (int blk = b0; blk < b1; ++blk) {
+        for (int blk = 0; blk < nblk; ++blk) {
             float v[16];
             tc_ld16(taddr + (uint32_t)(16 * blk), v);   // every lane of the warp takes part
             if (!rowok) continue;
@@ -364,8 +367,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
         if (!wait_buf(b)) { dead = true; break; }
         unsigned char* opa = smem + a.off_a + b * a.opbytes_a;
         unsigned char* opb = sym ? opa : smem + a.off_b + b * a.opbytes_b;
-        slice_chunk<TX>(smem + a.off_rx + b * GT_CH * a.rsx, a.rsx, a.kx, S, exx, opa);
-        if (!sym) slice_chunk<double>(smem + a.off_rz + b * GT_CH * a.rsz, a.rsz, a.kz, S, exz, opb);
+        if (on_x) slice_item<TX>(smem + a.off_rx + b * GT_CH * a.rsx, a.rsx, a.kx, S, exx, opa, my_cp, my_g4);
+        if (on_z) slice_item<double>(smem + a.off_rz + b * GT_CH * a.rsz, a.rsz, a.kz, S, exz, opb, my_cp, my_g4);
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -406,12 +409,11 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     }
     // ---- the CTA's partial X^T Z: the (s, j, l) sums added over s
     __threadfence_block();
-    for (int o = tid; o < a.kx * kz; o += GT_THREADS) {
+    for (int o = tid; o < a.kx * kz; o += nt) {
         const int j = o / kz, l = o - j * kz;
         float h = 0.f, lo = 0.f;
-        for (int q = 0; q < ncopy * S; ++q) {
-            const int cpy = q / S, s = q - cpy * S;
-            const float2 r = accg[cpy * cset + (size_t)(s * a.kx + j) * kz + l];
+        for (int s = 0; s < S; ++s) {
+            const float2 r = accg[(size_t)(s * a.kx + j) * kz + l];
             // double-float add of (r.x, r.y) into (h, lo)
             const float sm = h + r.x;
             const float bb = sm - h;
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     __syncthreads();
     if (s_last) {
         __threadfence();
-        for (int o = tid; o < a.kx * kz; o += GT_THREADS) {
+        for (int o = tid; o < a.kx * kz; o += nt) {
             const int j = o / kz, l = o - j * kz;
             if (sym && l < j) continue;
             double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -456,18 +458,24 @@ __global__ void __launch_bounds__(256) k_colmax(const T* X, long long ld, int k,
     const int cp = threadIdx.x % kp2, rg = threadIdx.x / kp2;
     if (rg < rpb) {
         float m0 = 0.f, m1 = 0.f;
-        for (long long i = (long long)blockIdx.x * rpb + rg; i < n; i += (long long)gridDim.x * rpb) {
-            float h0, h1 = 0.f, l;
-            if constexpr (sizeof(T) == 4) {   // dfp: the hi parts of the column pair
+        if constexpr (sizeof(T) == 4) {   // dfp: the hi parts of the column pair
+            for (long long i = (long long)blockIdx.x * rpb + rg; i < n; i += (long long)gridDim.x * rpb) {
                 const float2 v = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(X) + ((i * ld + 2 * cp) >> 1) * 4);
-                h0 = v.x;
-                h1 = 2 * cp + 1 < k ? v.y : 0.f;
-            } else {
-                split_bits(reinterpret_cast<const double*>(X)[i * ld + 2 * cp], h0, l);
-                if (2 * cp + 1 < k) split_bits(reinterpret_cast<const double*>(X)[i * ld + 2 * cp + 1], h1, l);
+                m0 = fmaxf(m0, fabsf(v.x));
+                m1 = fmaxf(m1, fabsf(2 * cp + 1 < k ? v.y : 0.f));
             }
-            m0 = fmaxf(m0, fabsf(h0));
-            m1 = fmaxf(m1, fabsf(h1));
+        } else {
+            // FP64: the largest magnitude by its bits (an order-preserving integer compare, no FP64
+            // instructions), then the hi float of that value
+            const unsigned long long* B = reinterpret_cast<const unsigned long long*>(X);
+            unsigned long long b0 = 0ull, b1 = 0ull;
+            for (long long i = (long long)blockIdx.x * rpb + rg; i < n; i += (long long)gridDim.x * rpb) {
+                b0 = max(b0, B[i * ld + 2 * cp] & 0x7FFFFFFFFFFFFFFFull);
+                if (2 * cp + 1 < k) b1 = max(b1, B[i * ld + 2 * cp + 1] & 0x7FFFFFFFFFFFFFFFull);
+            }
+            float l;
+            split_bits(__longlong_as_double((long long)b0), m0, l);
+            split_bits(__longlong_as_double((long long)b1), m1, l);
         }
         atomicMax(&smx[2 * cp], __float_as_uint(m0));
         if (2 * cp + 1 < k) atomicMax(&smx[2 * cp + 1], __float_as_uint(m1));
@@ -486,7 +494,7 @@ int gram_tc_digits(int kx, int kz) {
 size_t gram_tc_partials_doubles(int kx, int kz, int grid) { return (size_t)grid * kx * kz; }
 
 size_t gram_tc_workspace_bytes(int kx, int kz, int grid) {
-    return (size_t)grid * 2 * GT_SMAX * kx * kz * sizeof(float2) + 128 * sizeof(unsigned int);
+    return (size_t)grid * GT_SMAX * kx * kz * sizeof(float2) + 128 * sizeof(unsigned int);
 }
 
 bool gram_tc_supported(int tx, int kx, int kz, bool sym) {
@@ -543,6 +551,11 @@ cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const d
     a.out = out;
     a.err = err;
     a.spin_budget = spin_budget;
+    // one thread per digit item of a chunk (4 rows x one column pair of X, then of Z), at least the
+    // eight warps of the drain
+    const int items = (GT_CH / 4) * ((kx + 1) / 2 + (sym ? 0 : (kz + 1) / 2));
+    const int threads = std::max(256, (items + 31) / 32 * 32);
+    if (threads > GT_MAX_THREADS) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(mx, 0, 128 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     const int cgrid = sm_count * 2;
@@ -553,11 +566,11 @@ cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const d
     if (tx == T_DF64) {
         e = cudaFuncSetAttribute(k_gram_tc<dfp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_gram_tc<dfp><<<grid, GT_THREADS, smem, s>>>(a);
+        k_gram_tc<dfp><<<grid, threads, smem, s>>>(a);
     } else {
         e = cudaFuncSetAttribute(k_gram_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_gram_tc<double><<<grid, GT_THREADS, smem, s>>>(a);
+        k_gram_tc<double><<<grid, threads, smem, s>>>(a);
     }
     return cudaGetLastError();
 }
