@@ -41,7 +41,7 @@ constexpr int GT_CH = 64;                      // rows per chunk (MMA K: 4 steps
 constexpr int GT_BATCH_CHUNKS = 64;            // chunks summed exactly in TMEM (4096 rows)
 constexpr int GT_LBO = 128;                    // bytes between K-adjacent core matrices
 constexpr int GT_SBO = (GT_CH / 8) * GT_LBO + 16;   // bytes between 8-row groups (1040)
-constexpr int GT_MAX_THREADS = 576;           // one thread per digit item of a chunk (at least 256)
+constexpr int GT_MAX_THREADS = 672;           // one thread per digit item of a chunk (at least 256; 672 for two widths of 42)
 constexpr int GT_SMAX = 7;
 
 // ---- tcgen05 / TMEM wrappers (inline PTX) ----------------------------------------------------
