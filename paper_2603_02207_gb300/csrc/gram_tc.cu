@@ -41,7 +41,7 @@ constexpr int GT_CH = 64;                      // rows per chunk (MMA K: 4 steps
 constexpr int GT_BATCH_CHUNKS = 64;            // chunks summed exactly in TMEM (4096 rows)
 constexpr int GT_LBO = 128;                    // bytes between K-adjacent core matrices
 constexpr int GT_SBO = (GT_CH / 8) * GT_LBO + 16;   // bytes between 8-row groups (1040)
-constexpr int GT_MAX_THREADS = 672;           // one thread per digit item of a chunk (at least 256; 672 for two widths of 42)
+constexpr int GT_MAX_THREADS = 512;           // threads of a CTA: one per digit item of a chunk (at least 256)
 constexpr int GT_SMAX = 7;
 
 // ---- tcgen05 / TMEM wrappers (inline PTX) ----------------------------------------------------
@@ -227,7 +227,7 @@ struct GramTcArgs {
     double* out;         // kx x kz
     int* err;
     long long spin_budget;
-    int S, mt, nb;       // digits, M tiles (1 or 2) of A, N of B (a multiple of 16)
+    int S, mt, nb, nb1;  // digits, M tiles (1 or 2) of A, N of B (a multiple of 16), and N for M tile 1
     int off_a, off_b, off_rx, off_rz, rsx, rsz, opbytes_a, opbytes_b;
     uint32_t tmem_cols;
 };
@@ -250,13 +250,10 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
     // the CTA's (s, j, l) sums
     const size_t cset = (size_t)S * a.kx * kz;
     float2* accg = a.acc + (size_t)blockIdx.x * cset;
-    // this thread's digit item of every chunk: 4 rows x one column pair of X (or of Z)
+    // digit items of every chunk: 4 rows x one column pair of X, then of Z; thread t takes items
+    // t, t + blockDim, ...
     const int kp2x = (a.kx + 1) / 2, kp2z = (kz + 1) / 2;
     const int itx = (GT_CH / 4) * kp2x, itz = sym ? 0 : (GT_CH / 4) * kp2z;
-    const bool on_x = tid < itx, on_z = !on_x && tid < itx + itz;
-    const int iz = tid - itx;
-    const int my_cp = on_x ? tid % kp2x : (on_z ? iz % kp2z : 0);
-    const int my_g4 = on_x ? tid / kp2x : (on_z ? iz / kp2z : 0);
 
     // column exponents: max |x| < 2^(E - 1); all-zero columns take E = 0 (their digits are zero)
     const int nt = blockDim.x;
@@ -281,6 +278,7 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = tc_idesc(128, a.nb);
+    const uint32_t idesc1 = tc_idesc(128, a.nb1);   // M tile 1: only the columns u < S - s_min of its rows
     const long long r0 = (long long)blockIdx.x * a.rows_per_cta;
     const long long r1 = min(a.n, r0 + a.rows_per_cta);
     const int nch = r0 < r1 ? (int)((r1 - r0 + GT_CH - 1) / GT_CH) : 0;
@@ -303,42 +301,46 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
         // warps 4 t .. 4 t + 3 read M tile t (warp w reaches TMEM lanes 32 (w % 4) .. + 31)
         const int tile = warp >> 2;
         const int m = tile * 128 + 32 * (warp & 3) + lane;
-        const int nblk = tile < a.mt ? a.nb / 16 : 0;
+        const int nblk = tile < a.mt ? (tile == 0 ? a.nb : a.nb1) / 16 : 0;
+        const int ncols = tile == 0 ? S * kz : min(S * kz, a.nb1);
         const bool rowok = tile < a.mt && m < S * a.kx;
         const int s = rowok ? m / a.kx : 0, j = rowok ? m - s * a.kx : 0;
-        float2* accr = accg + (size_t)(rowok ? m : 0) * kz;
+        // sums stored l-major (lanes = consecutive slice rows m: coalesced accesses)
+        float2* accr = accg + (rowok ? m : 0);
+        const int ms = S * a.kx;
         const int ebase = rowok ? exx[j] - 14 - 7 * s : 0;
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * tile);
         for (int blk = 0; blk < nblk; ++blk) {
             float v[16];
             tc_ld16(taddr + (uint32_t)(16 * blk), v);   // every lane of the warp takes part
             if (!rowok) continue;
-            // the block's entries in segments of at most kz consecutive columns (distinct l): the
-            // segment's sums are read together, updated, and written back together
-            const int seg = kz < 16 ? kz : 16;
+            // the block's entries in segments of at most min(kz, 8) consecutive columns (distinct l):
+            // the segment's sums are read together, updated, and written back
+            const int seg = kz < 8 ? kz : 8;
+            const int cb = 16 * blk;
+            int u0 = cb / kz, l0 = cb - u0 * kz;
             for (int q0 = 0; q0 < 16; q0 += seg) {
                 float2 r[16];
+                int u = u0, l = l0;   // (u, l) of column cb + q, advanced with q
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const int col = 16 * blk + q;
-                    if (q >= q0 && q < q0 + seg && col < S * kz) r[q] = accr[col % kz];
+                    if (q >= q0 && q < q0 + seg && cb + q < ncols) r[q] = accr[(size_t)l * ms];
+                    if (++l == kz) { l = 0; ++u; }
                 }
+                u = u0;
+                l = l0;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const int col = 16 * blk + q;
-                    if (q < q0 || q >= q0 + seg || col >= S * kz) continue;
-                    const int u = col / kz, l = col - u * kz;
-                    // the exact product D 2^(E_j + F_l - 7 (s + u + 2)) added into the (s, j, l) sum
-                    const float x = scale2(v[q], ebase + exz[l] - 7 * u);
-                    const float sm = r[q].x + x;
-                    const float bb = sm - r[q].x;
-                    r[q].y += (r[q].x - (sm - bb)) + (x - bb);
-                    r[q].x = sm;
-                }
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int col = 16 * blk + q;
-                    if (q >= q0 && q < q0 + seg && col < S * kz) accr[col % kz] = r[q];
+                    if (q >= q0 && q < q0 + seg && cb + q < ncols) {
+                        // the exact product D 2^(E_j + F_l - 7 (s + u + 2)) added into the (s, j, l) sum
+                        const float x = scale2(v[q], ebase + exz[l] - 7 * u);
+                        const float sm = r[q].x + x;
+                        const float bb = sm - r[q].x;
+                        r[q].y += (r[q].x - (sm - bb)) + (x - bb);
+                        r[q].x = sm;
+                        accr[(size_t)l * ms] = r[q];
+                    }
+                    if (++l == kz) { l = 0; ++u; }
                 }
             }
         }
@@ -367,8 +369,10 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
         if (!wait_buf(b)) { dead = true; break; }
         unsigned char* opa = smem + a.off_a + b * a.opbytes_a;
         unsigned char* opb = sym ? opa : smem + a.off_b + b * a.opbytes_b;
-        if (on_x) slice_item<TX>(smem + a.off_rx + b * GT_CH * a.rsx, a.rsx, a.kx, S, exx, opa, my_cp, my_g4);
-        if (on_z) slice_item<double>(smem + a.off_rz + b * GT_CH * a.rsz, a.rsz, a.kz, S, exz, opb, my_cp, my_g4);
+        for (int it = tid; it < itx + itz; it += nt) {
+            if (it < itx) slice_item<TX>(smem + a.off_rx + b * GT_CH * a.rsx, a.rsx, a.kx, S, exx, opa, it % kp2x, it / kp2x);
+            else slice_item<double>(smem + a.off_rz + b * GT_CH * a.rsz, a.rsz, a.kz, S, exz, opb, (it - itx) % kp2z, (it - itx) / kp2z);
+        }
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
                 const uint64_t bd = tc_desc(smem_u32(opb) + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
                 for (int mt = 0; mt < a.mt; ++mt) {
                     const uint64_t ad = tc_desc(smem_u32(opa) + (uint32_t)(16 * mt) * GT_SBO + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
-                    tc_mma(tmem + (uint32_t)(256 * mt), ad, bd, idesc, (inbatch > 0 || t > 0) ? 1u : 0u);
+                    tc_mma(tmem + (uint32_t)(256 * mt), ad, bd, mt == 0 ? idesc : idesc1, (inbatch > 0 || t > 0) ? 1u : 0u);
                 }
             }
             tc_commit(smem_u32(&mbar[b]));
@@ -413,7 +417,7 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
         const int j = o / kz, l = o - j * kz;
         float h = 0.f, lo = 0.f;
         for (int s = 0; s < S; ++s) {
-            const float2 r = accg[(size_t)(s * a.kx + j) * kz + l];
+            const float2 r = accg[(size_t)l * S * a.kx + s * a.kx + j];
             // double-float add of (r.x, r.y) into (h, lo)
             const float sm = h + r.x;
             const float bb = sm - h;
@@ -522,6 +526,9 @@ cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const d
     a.mt = ma > 128 ? 2 : 1;
     a.nb = (mb + 15) / 16 * 16;
     if (a.nb > 256) return cudaErrorInvalidValue;
+    // M tile 1 holds the slice rows s >= s1 = 128 / kx: pairs with s + u >= S lie below the digits'
+    // resolution and are left out, so its MMAs take N = (S - s1) kz columns
+    a.nb1 = std::min(a.nb, ((a.S - 128 / kx) * kz + 15) / 16 * 16);
     // shared memory: operand buffers (two each), then the raw stages (two each)
     a.opbytes_a = a.mt * 16 * GT_SBO;
     a.opbytes_b = sym ? 0 : (a.nb / 8) * GT_SBO;
@@ -554,8 +561,7 @@ cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const d
     // one thread per digit item of a chunk (4 rows x one column pair of X, then of Z), at least the
     // eight warps of the drain
     const int items = (GT_CH / 4) * ((kx + 1) / 2 + (sym ? 0 : (kz + 1) / 2));
-    const int threads = std::max(256, (items + 31) / 32 * 32);
-    if (threads > GT_MAX_THREADS) return cudaErrorInvalidValue;
+    const int threads = std::min(GT_MAX_THREADS, std::max(256, (items + 31) / 32 * 32));
     cudaError_t e = cudaMemsetAsync(mx, 0, 128 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     const int cgrid = sm_count * 2;
