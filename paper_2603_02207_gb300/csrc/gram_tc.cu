@@ -526,9 +526,10 @@ cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const d
     a.mt = ma > 128 ? 2 : 1;
     a.nb = (mb + 15) / 16 * 16;
     if (a.nb > 256) return cudaErrorInvalidValue;
-    // M tile 1 holds the slice rows s >= s1 = 128 / kx: pairs with s + u >= S lie below the digits'
-    // resolution and are left out, so its MMAs take N = (S - s1) kz columns
-    a.nb1 = std::min(a.nb, ((a.S - 128 / kx) * kz + 15) / 16 * 16);
+    // M tile 1 holds the slice rows s >= s1 = 128 / kx: pairs with s + u > S lie below the digits'
+    // resolution (2^-7 of the truncation of the last digit) and are left out, so its MMAs take
+    // N = (S - s1 + 1) kz columns
+    a.nb1 = std::min(a.nb, ((a.S - 128 / kx + 1) * kz + 15) / 16 * 16);
     // shared memory: operand buffers (two each), then the raw stages (two each)
     a.opbytes_a = a.mt * 16 * GT_SBO;
     a.opbytes_b = sym ? 0 : (a.nb / 8) * GT_SBO;
