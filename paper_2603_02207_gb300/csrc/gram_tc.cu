@@ -142,9 +142,10 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 
 // rows [c0, c0 + GT_CH) of X into the raw stage (rows at or past `end` zero-filled)
 template <typename T>
-__device__ __forceinline__ void stage_raw(unsigned char* st, int rs, const T* X, long long ld, int k, long long c0, long long end) {
+__device__ __forceinline__ void stage_raw(unsigned char* st, int rs, const T* X, long long ld, int k, long long c0, long long end,
+                                          int t, int nthreads) {
     const int U = Raw<T>::units(k);
-    for (int e = threadIdx.x; e < GT_CH * U; e += blockDim.x) {
+    for (int e = t; e < GT_CH * U; e += nthreads) {
         const int r = e / U, u = e - r * U;
         const long long row = c0 + r;
         const bool ok = row < end;
@@ -235,8 +236,11 @@ struct GramTcArgs {
 template <typename TX>
 __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long full[2];    // slicer warps: buffer b holds a chunk's digits
+    __shared__ __align__(8) unsigned long long empty[2];   // tcgen05.commit: the MMAs reading buffer b are done
+    __shared__ __align__(8) unsigned long long fin;        // tcgen05.commit: every MMA issued is done
     __shared__ uint32_t s_tmem;
+    __shared__ int s_dead;
     __shared__ bool s_last;
     __shared__ int s_ex[128];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -264,9 +268,16 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
     // zero both operand buffers (slice rows past S k stay zero) and this CTA's sums
     for (int i = tid * 16; i < a.off_rx; i += nt * 16) *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < (int)cset; i += nt) accg[i] = make_float2(0.f, 0.f);
+    // the last warp issues the MMAs; the others (slicers) stage, split and drain
+    const int nsl = nt - 32;
+    const bool issuer = tid >= nsl;
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
+        mbar_init(smem_u32(&full[0]), nsl / 32);
+        mbar_init(smem_u32(&full[1]), nsl / 32);
+        mbar_init(smem_u32(&empty[0]), 1);
+        mbar_init(smem_u32(&empty[1]), 1);
+        mbar_init(smem_u32(&fin), 1);
+        s_dead = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -282,19 +293,8 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
     const long long r0 = (long long)blockIdx.x * a.rows_per_cta;
     const long long r1 = min(a.n, r0 + a.rows_per_cta);
     const int nch = r0 < r1 ? (int)((r1 - r0 + GT_CH - 1) / GT_CH) : 0;
-    uint32_t phase[2] = {0u, 0u};
-    int pend[2] = {0, 0};   // a commit of the buffer not yet waited for
-    bool dead = false;
-
-    // waits for buffer b's last commit (every thread; false when the wait ran out anywhere)
-    auto wait_buf = [&](int b) -> bool {
-        if (!pend[b]) return true;
-        const bool ok = mbar_wait_bounded(smem_u32(&mbar[b]), phase[b], a.spin_budget);
-        if (__syncthreads_or(ok ? 0 : 1)) return false;
-        phase[b] ^= 1u;
-        pend[b] = 0;
-        return true;
-    };
+    // named barrier of the slicer warps (the issuer warp does not take part)
+    auto sl_sync = [&]() { asm volatile("bar.sync 1, %0;\n" ::"r"(nsl) : "memory"); };
     // the D rows of this thread's TMEM lane, scaled exactly, into the (s, j, l) sums
     auto drain = [&]() {
         tc_fence_after();
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
             // the segment's sums are read together, updated, and written back
             const int seg = kz < 8 ? kz : 8;
             const int cb = 16 * blk;
-            int u0 = cb / kz, l0 = cb - u0 * kz;
+            const int u0 = cb / kz, l0 = cb - u0 * kz;
             for (int q0 = 0; q0 < 16; q0 += seg) {
                 float2 r[16];
                 int u = u0, l = l0;   // (u, l) of column cb + q, advanced with q
@@ -345,64 +345,102 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
             }
         }
         tc_fence_before();
-        __syncthreads();   // TMEM read (and sums written) before the next MMAs overwrite it
     };
 
-    if (nch > 0) {
-        stage_raw<TX>(smem + a.off_rx, a.rsx, X, a.ldx, a.kx, r0, r1);
-        if (!sym) stage_raw<double>(smem + a.off_rz, a.rsz, a.Z, a.ldz, a.kz, r0, r1);
-        cp_async_commit();
-    }
-    int inbatch = 0;   // chunks accumulated in TMEM since the last drain
-    for (int c = 0; c < nch && !dead; ++c) {
-        const int b = c & 1;
-        const long long c0 = r0 + (long long)c * GT_CH;
-        // next chunk's raw rows in flight while this one is split
-        if (c + 1 < nch) {
-            stage_raw<TX>(smem + a.off_rx + (b ^ 1) * GT_CH * a.rsx, a.rsx, X, a.ldx, a.kx, c0 + GT_CH, r1);
-            if (!sym) stage_raw<double>(smem + a.off_rz + (b ^ 1) * GT_CH * a.rsz, a.rsz, a.Z, a.ldz, a.kz, c0 + GT_CH, r1);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        // the MMAs of chunk c - 2 have read operand buffer b
-        if (!wait_buf(b)) { dead = true; break; }
-        unsigned char* opa = smem + a.off_a + b * a.opbytes_a;
-        unsigned char* opb = sym ? opa : smem + a.off_b + b * a.opbytes_b;
-        for (int it = tid; it < itx + itz; it += nt) {
-            if (it < itx) slice_item<TX>(smem + a.off_rx + b * GT_CH * a.rsx, a.rsx, a.kx, S, exx, opa, it % kp2x, it / kp2x);
-            else slice_item<double>(smem + a.off_rz + b * GT_CH * a.rsz, a.rsz, a.kz, S, exz, opb, (it - itx) % kp2z, (it - itx) / kp2z);
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll 1
-            for (int t = 0; t < GT_CH / 16; ++t) {
-                // K step t: the core matrices 2t and 2t + 1 of every 8-row group
-                const uint64_t bd = tc_desc(smem_u32(opb) + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
-                for (int mt = 0; mt < a.mt; ++mt) {
-                    const uint64_t ad = tc_desc(smem_u32(opa) + (uint32_t)(16 * mt) * GT_SBO + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
-                    tc_mma(tmem + (uint32_t)(256 * mt), ad, bd, mt == 0 ? idesc : idesc1, (inbatch > 0 || t > 0) ? 1u : 0u);
-                }
+    if (issuer) {
+        // ---------------------------------------------------------------- the MMA issuer warp
+        uint32_t pf[2] = {0u, 0u};
+        int inbatch = 0;   // chunks accumulated in TMEM since the last drain
+        for (int c = 0; c < nch; ++c) {
+            const int b = c & 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(smem_u32(&full[b]), pf[b], a.spin_budget);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok || *((volatile int*)&s_dead)) {
+                if (lane == 0) { s_dead = 1; *((volatile int*)a.err) = 1; }
+                break;
             }
-            tc_commit(smem_u32(&mbar[b]));
+            pf[b] ^= 1u;
+            if (lane == 0) {
+                tc_fence_after();
+                const unsigned char* opa = smem + a.off_a + b * a.opbytes_a;
+                const unsigned char* opb = sym ? opa : smem + a.off_b + b * a.opbytes_b;
+#pragma unroll 1
+                for (int t = 0; t < GT_CH / 16; ++t) {
+                    // K step t: the core matrices 2t and 2t + 1 of every 8-row group
+                    const uint64_t bd = tc_desc(smem_u32(opb) + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
+                    for (int mt = 0; mt < a.mt; ++mt) {
+                        const uint64_t ad = tc_desc(smem_u32(opa) + (uint32_t)(16 * mt) * GT_SBO + (uint32_t)(2 * t) * GT_LBO, GT_LBO, GT_SBO);
+                        tc_mma(tmem + (uint32_t)(256 * mt), ad, bd, mt == 0 ? idesc : idesc1, (inbatch > 0 || t > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(smem_u32(&empty[b]));
+            }
+            __syncwarp();
+            if (++inbatch == GT_BATCH_CHUNKS) inbatch = 0;
         }
-        pend[b] = 1;
-        ++inbatch;
-        if (inbatch == GT_BATCH_CHUNKS || c + 1 == nch) {
-            // every MMA of the batch done: the other buffer's commit came first
-            if (!wait_buf(b ^ 1) || !wait_buf(b)) { dead = true; break; }
-            drain();
-            inbatch = 0;
+        // every MMA issued has completed before the TMEM is freed (bounded: on a timeout elsewhere)
+        if (lane == 0) {
+            tc_commit(smem_u32(&fin));
+            const long long bud = a.spin_budget > TMA_DRAIN_MIN ? a.spin_budget : TMA_DRAIN_MIN;
+            if (!mbar_wait_bounded(smem_u32(&fin), 0u, bud)) *((volatile int*)a.err) = 1;
         }
-    }
-    // ---- after a failed wait: the MMAs in flight finish before the TMEM is freed
-    if (dead && tid == 0) {
-        *((volatile int*)a.err) = 1;
-        const long long drain_budget = a.spin_budget > TMA_DRAIN_MIN ? a.spin_budget : TMA_DRAIN_MIN;
-        for (int b = 0; b < 2; ++b)
-            if (pend[b]) mbar_wait_bounded(smem_u32(&mbar[b]), phase[b], drain_budget);
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- slicer warps
+        uint32_t pe[2] = {0u, 0u};
+        int waited[2] = {-1, -1};   // the last chunk on buffer b whose MMAs were waited for
+        auto wait_empty = [&](int b, int c) {   // the MMAs of chunk c (on buffer b) are done
+            if (waited[b] >= c) return;
+            if (!mbar_wait_bounded(smem_u32(&empty[b]), pe[b], a.spin_budget)) {
+                s_dead = 1;
+                *((volatile int*)a.err) = 1;
+                return;
+            }
+            pe[b] ^= 1u;
+            waited[b] = c;
+        };
+        if (nch > 0) {
+            stage_raw<TX>(smem + a.off_rx, a.rsx, X, a.ldx, a.kx, r0, r1, tid, nsl);
+            if (!sym) stage_raw<double>(smem + a.off_rz, a.rsz, a.Z, a.ldz, a.kz, r0, r1, tid, nsl);
+            cp_async_commit();
+        }
+        int inbatch = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int b = c & 1;
+            const long long c0 = r0 + (long long)c * GT_CH;
+            // next chunk's raw rows in flight while this one is split
+            if (c + 1 < nch) {
+                stage_raw<TX>(smem + a.off_rx + (b ^ 1) * GT_CH * a.rsx, a.rsx, X, a.ldx, a.kx, c0 + GT_CH, r1, tid, nsl);
+                if (!sym)
+                    stage_raw<double>(smem + a.off_rz + (b ^ 1) * GT_CH * a.rsz, a.rsz, a.Z, a.ldz, a.kz, c0 + GT_CH, r1, tid, nsl);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();
+            // the MMAs of chunk c - 2 have read operand buffer b
+            if (c >= 2) wait_empty(b, c - 2);
+            sl_sync();
+            if (*((volatile int*)&s_dead)) break;
+            unsigned char* opa = smem + a.off_a + b * a.opbytes_a;
+            unsigned char* opb = sym ? opa : smem + a.off_b + b * a.opbytes_b;
+            for (int it = tid; it < itx + itz; it += nsl) {
+                if (it < itx) slice_item<TX>(smem + a.off_rx + b * GT_CH * a.rsx, a.rsx, a.kx, S, exx, opa, it % kp2x, it / kp2x);
+                else slice_item<double>(smem + a.off_rz + b * GT_CH * a.rsz, a.rsz, a.kz, S, exz, opb, (it - itx) % kp2z, (it - itx) / kp2z);
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&full[b]));
+            if (++inbatch == GT_BATCH_CHUNKS || c + 1 == nch) {
+                // the batch's MMAs done (chunk c's commit covers every earlier one): drain the sums
+                inbatch = 0;
+                wait_empty(b, c);
+                sl_sync();
+                if (*((volatile int*)&s_dead)) break;
+                drain();
+                // each warp arrives on full[] for the next chunk after its drain: the issuer's next
+                // MMAs (which overwrite the accumulators) wait for every warp's arrival
+            }
+        }
     }
     cp_async_wait<0>();
     tc_fence_before();
@@ -562,7 +600,7 @@ cudaError_t launch_gram_tc(int tx, const void* X, long long ldx, int kx, const d
     // one thread per digit item of a chunk (4 rows x one column pair of X, then of Z), at least the
     // eight warps of the drain
     const int items = (GT_CH / 4) * ((kx + 1) / 2 + (sym ? 0 : (kz + 1) / 2));
-    const int threads = std::min(GT_MAX_THREADS, std::max(256, (items + 31) / 32 * 32));
+    const int threads = 32 + std::min(GT_MAX_THREADS - 32, std::max(256, (items + 31) / 32 * 32));
     cudaError_t e = cudaMemsetAsync(mx, 0, 128 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     const int cgrid = sm_count * 2;
