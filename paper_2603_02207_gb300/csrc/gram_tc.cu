@@ -430,6 +430,8 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&full[b]));
+            // every slicer is done with raw stage b before the next iteration copies chunk c + 2 there
+            sl_sync();
             if (++inbatch == GT_BATCH_CHUNKS || c + 1 == nch) {
                 // the batch's MMAs done (chunk c's commit covers every earlier one): drain the sums
                 inbatch = 0;
