@@ -314,24 +314,23 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
             float v[16];
             tc_ld16(taddr + (uint32_t)(16 * blk), v);   // every lane of the warp takes part
             if (!rowok) continue;
-            // the block's entries in segments of at most min(kz, 8) consecutive columns (distinct l):
-            // the segment's sums are read together, updated, and written back
-            const int seg = kz < 8 ? kz : 8;
             const int cb = 16 * blk;
             const int u0 = cb / kz, l0 = cb - u0 * kz;
-            for (int q0 = 0; q0 < 16; q0 += seg) {
+            if (kz >= 16) {
+                // the block's 16 columns have distinct l: their sums are read together, updated and
+                // written back together
                 float2 r[16];
                 int u = u0, l = l0;   // (u, l) of column cb + q, advanced with q
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    if (q >= q0 && q < q0 + seg && cb + q < ncols) r[q] = accr[(size_t)l * ms];
+                    if (cb + q < ncols) r[q] = accr[(size_t)l * ms];
                     if (++l == kz) { l = 0; ++u; }
                 }
                 u = u0;
                 l = l0;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    if (q >= q0 && q < q0 + seg && cb + q < ncols) {
+                    if (cb + q < ncols) {
                         // the exact product D 2^(E_j + F_l - 7 (s + u + 2)) added into the (s, j, l) sum
                         const float x = scale2(v[q], ebase + exz[l] - 7 * u);
                         const float sm = r[q].x + x;
@@ -339,6 +338,22 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
                         r[q].y += (r[q].x - (sm - bb)) + (x - bb);
                         r[q].x = sm;
                         accr[(size_t)l * ms] = r[q];
+                    }
+                    if (++l == kz) { l = 0; ++u; }
+                }
+            } else {
+                // narrow Z: one column after the other (columns of one block may share l)
+                int u = u0, l = l0;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    if (cb + q < ncols) {
+                        const float x = scale2(v[q], ebase + exz[l] - 7 * u);
+                        float2 r = accr[(size_t)l * ms];
+                        const float sm = r.x + x;
+                        const float bb = sm - r.x;
+                        r.y += (r.x - (sm - bb)) + (x - bb);
+                        r.x = sm;
+                        accr[(size_t)l * ms] = r;
                     }
                     if (++l == kz) { l = 0; ++u; }
                 }
