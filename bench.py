@@ -419,6 +419,8 @@ def workload_config4(L, h, count: int = 64):
         errs = [abs(e - x) / abs(x) for e, x in zip(est, exact)]
         out[prec] = {"ms_batched": ms_b, "ms_one_call_per_matrix": ms_s, "speedup": ms_s / ms_b,
                      "step_kernel": {v: k for k, v in L.STEP_KERNELS.items()}.get(inf["kernel_pass1"], "?"),
+                     "autotuned_shape": {"tuned": inf["batch_tuned"], "threads": [inf["threads_pass1"], inf["threads_pass2"]],
+                                         "rows_per_tile": [inf["rows_pass1"], inf["rows_pass2"]]},
                      "pass_gbs": {"pass1": b1 / (inf["ms_pass1"] * 1e-3) / 1e9, "pass2": b2 / (inf["ms_pass2"] * 1e-3) / 1e9},
                      "ms_batched_register_kernel": ms_r,
                      "register_kernel_phase_ms": {"pass1": inf_r["ms_pass1"], "qr": inf_r["ms_qr"], "pass2": inf_r["ms_pass2"]},

@@ -190,6 +190,9 @@ typedef struct {
                                            handle's kept state is still that of its forward     */
     int pairs_pass1, pairs_pass2;       /* column pairs per thread of each pass's step kernel (2:
                                            the FP32-mixed TMA kernel with 16-byte row accesses)  */
+    int rows_pass1, rows_pass2;         /* rows per tile of each pass's step kernel               */
+    int batch_tuned;                    /* ll_logdet_batched: 1 when the autotuner chose the launch
+                                           shape (step kernel, threads and rows per pass)        */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */
@@ -374,7 +377,12 @@ ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* d
  * mats[0..count-1] (device CSR each), bounds b[i], per-matrix degree degrees[i] (NULL = from the
  * bound ratio: m = clamp(ceil(ln 1e6 / ln rho), 10, 250), rho = (sqrt(kappa)+1)/(sqrt(kappa)-1),
  * Proposition 3.1). opts->probes, seed, kind and precision apply to every matrix; matrix i uses
- * seed + i. estimates: host, count doubles; synchronises `stream`. */
+ * seed + i. estimates: host, count doubles; synchronises `stream`.
+ * With opts->step_kernel = LL_KERNEL_AUTO the first call for a batch shape (precision, count, k,
+ * total rows and entries, largest degree) times the candidate launch shapes on the real operands
+ * (the TMA kernel with 512, 384 and 256 consumer threads per pass, i.e. rows per tile, and the
+ * register kernel), keeps the fastest shape of each pass on the handle, and runs with it;
+ * ll_info reports the shape (threads_pass1/2, rows_pass1/2, batch_tuned). */
 ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b, int count,
                             const ll_options* opts, const int* degrees, double* estimates, void* stream);
 

@@ -59,7 +59,8 @@ class ll_info(ctypes.Structure):
                 ("deg_max_pass1", ctypes.c_int), ("deg_max_pass2", ctypes.c_int), ("deg_mean_pass2", ctypes.c_double),
                 ("kept_w_steps", ctypes.c_int), ("kept_w_steps_pass1", ctypes.c_int),
                 ("kept_w_stride", ctypes.c_int), ("forward_id", ctypes.c_int64),
-                ("pairs_pass1", ctypes.c_int), ("pairs_pass2", ctypes.c_int)]
+                ("pairs_pass1", ctypes.c_int), ("pairs_pass2", ctypes.c_int),
+                ("rows_pass1", ctypes.c_int), ("rows_pass2", ctypes.c_int), ("batch_tuned", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -42,13 +42,14 @@ struct ll_handle {
     bool tma_used = false;                  // a TMA step ran since the last error-flag check
     int last_kernel = 0, last_threads = 0;  // choice of the last run_pass
     int last_np = 1;                        // and its column pairs per thread
+    int last_rows = 0;                      // and its rows per tile
     // CUDA graph of the last forward's device work (replayed when the next call is identical)
     uint64_t ws_gen = 0;                    // bumped whenever a workspace buffer moves
     cudaStream_t cap_stream = nullptr;      // capture stream (the caller's may be the legacy stream)
     struct Graph {
         std::vector<unsigned char> key;
         cudaGraphExec_t exec = nullptr;
-        int launches = 0, k1 = 0, t1 = 0, k2 = 0, t2 = 0, np1 = 1, np2 = 1;
+        int launches = 0, k1 = 0, t1 = 0, k2 = 0, t2 = 0, np1 = 1, np2 = 1, r1 = 0, r2 = 0;
         bool tma = false;
     } gfwd;
     // CUDA graph of the last batched call's device work, with what the host combine needs
@@ -62,7 +63,11 @@ struct ll_handle {
         unsigned long long* ctr = nullptr;    // counters (error flag at 2 count + 2)
         int* qrstat = nullptr;
         int kernel = 0, threads1 = 0, threads2 = 0;   // step kernel of both passes, CTA sizes
+        int rows1 = 0, rows2 = 0;                     // rows per tile of both passes
     } gbat;
+    // autotuned batched launch shapes: (precision, count, k, total rows, total entries, largest degree)
+    // -> (kernel, consumer-thread targets of both passes)
+    std::map<std::tuple<int, int, int, int64_t, int64_t, int>, std::tuple<int, int, int>> tuned_batch;
     int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
     bool band_ok = false;     // the last validated matrix suits the banded kernel
     int max_row = 0;          // longest row of the last validated matrix
@@ -468,6 +473,7 @@ ll_status run_band_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, in
     h->last_kernel = LL_KERNEL_BAND;
     h->last_threads = BAND_THREADS;
     h->last_np = 1;
+    h->last_rows = BL.R;
     return LL_OK;
 }
 
@@ -550,6 +556,7 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     h->last_kernel = E.kind;
     h->last_threads = E.cta();
     h->last_np = E.kind == LL_KERNEL_TMA ? E.tl.np : 1;
+    h->last_rows = E.kind == LL_KERNEL_TMA ? E.tl.q.R : p.rl * p.rpt;
     const int nslot = store_stride > 1 ? (m + store_stride - 1) / store_stride - 1 : m;
     const void* cur = win0;
     for (int j = 0; j < m; ++j) {
@@ -1110,6 +1117,7 @@ ll_status ll_apply_poly(ll_handle* h, const ll_csr* A, ll_bounds bounds, int deg
     h->info.kernel_pass1 = h->last_kernel;
     h->info.threads_pass1 = h->last_threads;
     h->info.pairs_pass1 = h->last_np;
+    h->info.rows_pass1 = h->last_rows;
     LL_CK(launch_block_to_f64(precision, pp, lb, PV, ldp, n, b, s));
     h->launches++;
     return check_tma_flag(h, s);
@@ -1157,6 +1165,7 @@ ll_status ll_apply_poly_tol(ll_handle* h, const ll_csr* A, ll_bounds bounds, int
     h->info.kernel_pass1 = h->last_kernel;
     h->info.threads_pass1 = h->last_threads;
     h->info.pairs_pass1 = h->last_np;
+    h->info.rows_pass1 = h->last_rows;
     LL_CK(launch_block_to_f64(precision, pp, lb, PV, ldp, n, b, s));
     h->launches++;
     LL_CK(cudaMemcpyAsync(degrees_out, stop.stop_deg, (size_t)b * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1326,7 +1335,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             wstride = 0;
         }
     }
-    int k1 = 0, t1 = 0, np1 = 1;   // step kernel, CTA size and column pairs per thread of pass 1
+    int k1 = 0, t1 = 0, np1 = 1, rw1 = 0;   // step kernel, CTA size, column pairs per thread, rows per tile of pass 1
 
     // the device work of the call (Algorithm 3 steps 2-6), enqueued on q; with capture, the
     // phase events become event-record nodes of the graph
@@ -1380,6 +1389,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             k1 = h->last_kernel;
             t1 = h->last_threads;
             np1 = h->last_np;
+            rw1 = h->last_rows;
             LL_CK(rec(h->ev[2], q));
 
             // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']. Outside the
@@ -1462,9 +1472,11 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         k1 = gr.k1;
         t1 = gr.t1;
         np1 = gr.np1;
+        rw1 = gr.r1;
         h->last_kernel = gr.k2;
         h->last_threads = gr.t2;
         h->last_np = gr.np2;
+        h->last_rows = gr.r2;
         h->tma_used = gr.tma;
     } else {
         const int before = h->launches;
@@ -1485,6 +1497,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             LL_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
             capturing = true;
             const int kk1 = k1, tt1 = t1, kk2 = h->last_kernel, tt2 = h->last_threads, nn1 = np1, nn2 = h->last_np;
+            const int rr1 = rw1, rr2 = h->last_rows;
             const int cap0 = h->launches;
             ll_status cst = enqueue(h->cap_stream);
             const int in_graph = h->launches - cap0;   // without the autotuner's launches of the eager run
@@ -1500,6 +1513,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
                 gr.t2 = tt2;
                 gr.np1 = nn1;
                 gr.np2 = nn2;
+                gr.r1 = rr1;
+                gr.r2 = rr2;
                 gr.tma = tma;
             } else {
                 gr.exec = nullptr;
@@ -1514,6 +1529,8 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             h->last_threads = tt2;
             np1 = nn1;
             h->last_np = nn2;
+            rw1 = rr1;
+            h->last_rows = rr2;
             h->tma_used = tma;
         }
     }
@@ -1585,6 +1602,9 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     I.threads_pass2 = h->last_threads;
     I.pairs_pass1 = np1;
     I.pairs_pass2 = h->last_np;
+    I.rows_pass1 = rw1;
+    I.rows_pass2 = h->last_rows;
+    I.batch_tuned = 0;
     I.deg_max_pass1 = 0;
     for (int v : deg1) I.deg_max_pass1 = v > I.deg_max_pass1 ? v : I.deg_max_pass1;
     I.deg_max_pass2 = 0;
@@ -1764,6 +1784,9 @@ ll_status batched_finish(ll_handle* h, const ll_csr* mats, int count, double* es
     I.kernel_pass2 = G.kernel;
     I.threads_pass1 = G.threads1;
     I.threads_pass2 = G.threads2;
+    I.rows_pass1 = G.rows1;
+    I.rows_pass2 = G.rows2;
+    I.pairs_pass1 = I.pairs_pass2 = 1;
     cudaEventElapsedTime(&I.ms_probes, h->ev[0], h->ev[1]);
     cudaEventElapsedTime(&I.ms_pass1, h->ev[1], h->ev[2]);
     cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
@@ -1772,12 +1795,17 @@ ll_status batched_finish(ll_handle* h, const ll_csr* mats, int count, double* es
     return LL_OK;
 }
 
-}  // namespace
+// Launch shape of a batched call: the step kernel of both passes (LL_KERNEL_TMA or LL_KERNEL_GATHER)
+// and, for the TMA kernel, the consumer-thread target of each pass (rows per tile = target / column
+// pairs); graph: capture / replay the device work.
+struct BatchCfg {
+    int kernel = LL_KERNEL_TMA;
+    int threads1 = 512, threads2 = 512;
+    bool graph = true;
+};
 
-extern "C" {
-
-ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* bnd, int count, const ll_options* opts,
-                            const int* degrees, double* estimates, void* stream) {
+ll_status batched_run(ll_handle* h, const ll_csr* mats, const ll_bounds* bnd, int count, const ll_options* opts,
+                      const int* degrees, double* estimates, void* stream, const BatchCfg& cfg) {
     if (!h || !opts || count < 0 || (count > 0 && (!mats || !bnd || !estimates))) return LL_ERR_INVALID_ARG;
     if (count == 0) return LL_OK;
     const ll_options& o = *opts;
@@ -1819,7 +1847,8 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     }
     // an identical call replays the captured device work (the descriptors, tables and
     // coefficients it reads are still on the device)
-    if (o.use_graph && h->gbat.exec && h->gbat.key == batched_key(h, mats, bnd, count, o, degrees)) {
+    const bool use_graph = o.use_graph && cfg.graph;
+    if (use_graph && h->gbat.exec && h->gbat.key == batched_key(h, mats, bnd, count, o, degrees)) {
         LL_CK(cudaGraphLaunch(h->gbat.exec, s));
         h->launches += h->gbat.launches;
         return batched_finish(h, mats, count, estimates, s);
@@ -1859,15 +1888,17 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     // TMA-fed persistent passes, unless the register-gather kernel is asked for or no layout fits
     BatchTmaLaunch tl1, tl2;
     bool use_tma = false;
-    if (o.step_kernel != LL_KERNEL_GATHER) {
+    if (cfg.kernel != LL_KERNEL_GATHER) {
         int n_min = INT32_MAX;
         double far = 0.0;
         for (int i = 0; i < count; ++i) {
             n_min = std::min(n_min, (int)mats[i].n);
             far += (double)hfar[i];
         }
-        use_tma = plan_batched_tma(prec, MODE_ACCUM, n_min, avg, far / tot_n, b1, l1, l1, max_m, count, h->sm_count, tl1) &&
-                  plan_batched_tma(prec, MODE_DOT, n_min, avg, far / tot_n, b2, l2, l2, max_m, count, h->sm_count, tl2);
+        use_tma = plan_batched_tma(prec, MODE_ACCUM, n_min, avg, far / tot_n, b1, l1, l1, max_m, count, h->sm_count, tl1,
+                                   cfg.threads1) &&
+                  plan_batched_tma(prec, MODE_DOT, n_min, avg, far / tot_n, b2, l2, l2, max_m, count, h->sm_count, tl2,
+                                   cfg.threads2);
     }
     const int R1 = use_tma ? tl1.q.R : bp1.R, R2 = use_tma ? tl2.q.R : bp2.R;
     const int tstride = bt_table_ints(max_m, count);   // per pass: step offsets, active counts, tile prefix, coef offsets
@@ -2209,12 +2240,14 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
     G.kernel = use_tma ? LL_KERNEL_TMA : LL_KERNEL_GATHER;
     G.threads1 = use_tma ? tl1.threads : BATCH_THREADS;
     G.threads2 = use_tma ? tl2.threads : BATCH_THREADS;
+    G.rows1 = R1;
+    G.rows2 = R2;
     if (G.exec) {
         cudaGraphExecDestroy(G.exec);
         G.exec = nullptr;
     }
     G.key.clear();
-    if (o.use_graph) {
+    if (use_graph) {
         if (!h->cap_stream) LL_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         LL_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -2231,6 +2264,69 @@ ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b
         h->launches = before + launched;
     }
     return batched_finish(h, mats, count, estimates, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* bnd, int count, const ll_options* opts,
+                            const int* degrees, double* estimates, void* stream) {
+    if (!h || !opts || count < 0 || (count > 0 && (!mats || !bnd || !estimates))) return LL_ERR_INVALID_ARG;
+    if (count == 0) return LL_OK;
+    const ll_options& o = *opts;
+    BatchCfg cfg;
+    if (o.step_kernel == LL_KERNEL_GATHER) cfg.kernel = LL_KERNEL_GATHER;
+    if (o.step_kernel != LL_KERNEL_AUTO) {
+        const ll_status st = batched_run(h, mats, bnd, count, opts, degrees, estimates, stream, cfg);
+        h->info.batch_tuned = 0;
+        return st;
+    }
+    // LL_KERNEL_AUTO: the first call for a batch shape times the candidate launch shapes (the TMA
+    // kernel with 512, 384 and 256 consumer threads per pass, and the register kernel) on the real
+    // operands, picks the fastest pass 1 and pass 2 shapes, and caches them on the handle
+    int64_t ntot = 0, nnztot = 0;
+    int maxdeg = 0;
+    for (int i = 0; i < count; ++i) {
+        ntot += mats[i].n;
+        nnztot += mats[i].nnz;
+        if (degrees) maxdeg = std::max(maxdeg, degrees[i]);
+    }
+    const auto key = std::make_tuple(o.precision, count, o.probes / 3, ntot, nnztot, maxdeg);
+    auto it = h->tuned_batch.find(key);
+    if (it == h->tuned_batch.end()) {
+        const int cand[3] = {512, 384, 256};
+        float best1 = 0.f, best2 = 0.f, best_tma = 0.f;
+        int t1 = 512, t2 = 512;
+        bool have = false;
+        for (int c : cand) {
+            BatchCfg x;
+            x.threads1 = x.threads2 = c;
+            x.graph = false;
+            ll_status st = batched_run(h, mats, bnd, count, opts, degrees, estimates, stream, x);
+            if (st != LL_OK) return st;
+            if (h->gbat.kernel != LL_KERNEL_TMA) break;   // no TMA layout fits: the register kernel ran
+            const float p1 = h->info.ms_pass1, p2 = h->info.ms_pass2;
+            if (!have || p1 < best1) { best1 = p1; t1 = c; }
+            if (!have || p2 < best2) { best2 = p2; t2 = c; }
+            have = true;
+        }
+        best_tma = best1 + best2;
+        BatchCfg g;
+        g.kernel = LL_KERNEL_GATHER;
+        g.graph = false;
+        ll_status st = batched_run(h, mats, bnd, count, opts, degrees, estimates, stream, g);
+        if (st != LL_OK) return st;
+        const float pg = h->info.ms_pass1 + h->info.ms_pass2;
+        const int kern = (have && best_tma <= pg) ? LL_KERNEL_TMA : LL_KERNEL_GATHER;
+        it = h->tuned_batch.emplace(key, std::make_tuple(kern, t1, t2)).first;
+    }
+    cfg.kernel = std::get<0>(it->second);
+    cfg.threads1 = std::get<1>(it->second);
+    cfg.threads2 = std::get<2>(it->second);
+    const ll_status st = batched_run(h, mats, bnd, count, opts, degrees, estimates, stream, cfg);
+    h->info.batch_tuned = 1;
+    return st;
 }
 
 ll_status ll_gram(ll_handle* h, int layout, const void* X, int64_t ldx, int kx, const double* Z, int64_t ldz, int kz,

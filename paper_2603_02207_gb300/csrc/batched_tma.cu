@@ -690,7 +690,7 @@ int occupancy_bt(int threads, size_t smem) {
 }  // namespace
 
 bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double avg_far, int b, long long ldw,
-                      long long ldp, int max_m, int count, int sm_count, BatchTmaLaunch& L) {
+                      long long ldp, int max_m, int count, int sm_count, BatchTmaLaunch& L, int threads_target) {
     L = BatchTmaLaunch{};
     if (n_min <= 0 || b <= 0 || max_m < 1 || count < 1 || !encode_fn()) return false;
     if (mode != MODE_ACCUM && mode != MODE_DOT) return false;
@@ -707,7 +707,9 @@ bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double
     q.slot = (int)a128((size_t)4 * q.rowbytes);
     q.recbytes = (int)rec_size(precision);
     const int tp = (b + 1) / 2;
-    int R = 512 / tp;
+    if (threads_target < 32 || threads_target > 512) threads_target = 512;
+    int R = threads_target / tp;
+    if (R < 1) R = 1;
     if (R > 256 - 2 * TMA_HALO) R = 256 - 2 * TMA_HALO;   // window box rows <= 256
     if (R + 2 * TMA_HALO > n_min) R = n_min - 2 * TMA_HALO;  // a box no taller than the smallest matrix
     if (R < 1) return false;

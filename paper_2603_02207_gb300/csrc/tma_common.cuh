@@ -354,10 +354,11 @@ struct BatchTmaLaunch {
     size_t off_red = 0, off_tab = 0;   // shared-memory offsets of the trace reduction area and the tables
 };
 
-// Plans one batched pass: rows per tile and stages for b columns, the shared-memory layout, the
-// launch shape (one CTA per SM). False when no layout fits (the register kernel is used then).
+// Plans one batched pass: rows per tile (about threads_target / ((b + 1) / 2) rows, fewer when three
+// stages do not fit) and stages for b columns, the shared-memory layout, the launch shape (one CTA
+// per SM). False when no layout fits (the register kernel is used then).
 bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double avg_far, int b, long long ldw,
-                      long long ldp, int max_m, int count, int sm_count, BatchTmaLaunch& L);
+                      long long ldp, int max_m, int count, int sm_count, BatchTmaLaunch& L, int threads_target = 512);
 cudaError_t launch_batched_tma(int precision, int mode, const BatchTmaParams& bp, const BatchTmaLaunch& L, cudaStream_t s);
 cudaError_t launch_batched_dots(int precision, const BatchTmaMat* mats, int count, int b, int max_span, cudaStream_t s);
 
