@@ -583,6 +583,34 @@ def workload_f4(L, h, N: int = 5000, thetas=(-0.24, -0.23, -0.22, -0.21, -0.20),
     offd = (dA.colind != rows).to(torch.float64)          # d a_e / d theta
     del rows
     out = {"n": n, "nnz": nnz, "generate_s": t_gen, "thetas": list(thetas), "rows": []}
+    # the bounds and degrees of the grid (Gershgorin of Q(theta): [1 - 4|theta|, 1 + 4|theta|])
+    grid = []
+    for theta in thetas:
+        dA.values = torch.where(offd > 0, torch.full_like(offd, theta), torch.ones_like(offd))
+        lo, hi = L.ll_gershgorin(h, dA)
+        kap = hi / lo
+        rho = (_m.sqrt(kap) + 1) / (_m.sqrt(kap) - 1)
+        grid.append((lo, hi, max(10, min(250, _m.ceil(_m.log(1e6) / _m.log(rho))))))
+    # the whole grid in one sweep (ll_logdet_sweep: O = Adj, D = 1, one pass pair over all thetas,
+    # the same probes for each), on a handle of its own that is closed before the per-theta runs
+    hs = L.Handle()
+    dO = L.DeviceCSR(n=n, rowptr=dA.rowptr, colind=dA.colind, values=offd)
+    dD = torch.ones(n, dtype=torch.float64, device="cuda")
+    sweep = {}
+    for prec in ("df64", "f32"):
+        so = L.options(degree=10, probes=probes, seed=0, precision=prec)
+        ms_s, est_s = time_calls(lambda: L.ll_logdet_sweep(hs, dO, dD, list(thetas), [g[:2] for g in grid], so,
+                                                           degrees=[g[2] for g in grid]), 2, 1)
+        inf = hs.info()
+        sweep[prec] = {"ms_sweep": ms_s, "estimates": [float(x) for x in est_s],
+                       "phase_ms": {"probes": inf["ms_probes"], "pass1": inf["ms_pass1"], "qr": inf["ms_qr"],
+                                    "pass2": inf["ms_pass2"]},
+                       "shape_pass2": {"threads": inf["threads_pass2"], "pairs_per_thread": inf["pairs_pass2"],
+                                       "rows_per_tile": inf["rows_pass2"]},
+                       "launches": inf["kernel_launches"]}
+    hs.close()
+    del hs, dD
+    torch.cuda.empty_cache()
     for theta in thetas:
         dA.values = torch.where(offd > 0, torch.full_like(offd, theta), torch.ones_like(offd))
         lo, hi = L.ll_gershgorin(h, dA)
@@ -609,8 +637,18 @@ def workload_f4(L, h, N: int = 5000, thetas=(-0.24, -0.23, -0.22, -0.21, -0.20),
                           "rel_err_dtheta": abs(th - dexact) / abs(dexact)})
             row[prec] = r
         out["rows"].append(row)
+    for prec, sw in sweep.items():
+        seq = sum(r[prec]["ms_forward"] for r in out["rows"])
+        sw["ms_sequential_forwards"] = seq
+        sw["speedup_vs_sequential"] = seq / sw["ms_sweep"]
+        sw["max_rel_diff_vs_forward"] = max(abs(e - r[prec]["estimate"]) / abs(r[prec]["estimate"])
+                                            for e, r in zip(sw["estimates"], out["rows"]))
+        sw["max_rel_err_vs_exact"] = max(abs(e - r["exact_logdet"]) / abs(r["exact_logdet"])
+                                         for e, r in zip(sw["estimates"], out["rows"]))
+    out["sweep"] = sweep
     out["workload"] = (f"GMRF Q(theta) = I + theta Adj on {N}^2 (n={n}, nnz={nnz}), theta in {list(thetas)}, "
-                       f"Gershgorin bounds, degree from the bounds, Hutch++ {probes} Rademacher probes, seed 0")
+                       f"Gershgorin bounds, degree from the bounds, Hutch++ {probes} Rademacher probes, seed 0; "
+                       f"the grid once per theta (forward, backward) and as one sweep (forward)")
     return out
 
 

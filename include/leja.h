@@ -386,6 +386,29 @@ ll_status ll_param_grad(ll_handle* h, const double* grad_values, const double* d
 ll_status ll_logdet_batched(ll_handle* h, const ll_csr* mats, const ll_bounds* b, int count,
                             const ll_options* opts, const int* degrees, double* estimates, void* stream);
 
+/* Log-determinants along a matrix pencil (Section 5's GMRF likelihood over a theta grid, where
+ * Q(theta) = I + theta Adj): estimates[g] ~ log det A_g for A_g = diag(D) + thetas[g] O, g < t,
+ * every A_g symmetric positive definite with spectrum inside bounds[g] (the Léja interval of its
+ * own scaling, Section 4) and run at degrees[g] (NULL: opts->degree for every theta). O: device
+ * CSR (FP32 or FP64 values; its diagonal entries, if stored, are part of O); D: device, n FP64
+ * values; thetas, bounds, degrees, estimates: host arrays of t entries.
+ * All t estimates come from one pass pair over a block of t column groups, one per theta: each
+ * step reads the shared sparsity structure once for every theta (a multi-value SpMM: one operand
+ * offset per stored entry, then the t matrices' prepared values A_g / (sigma_g gamma_g), each
+ * group with its own step scalars), and the block shrinks to the groups still running once a
+ * theta's degree is reached (the groups are ordered by degree). Every theta takes the same probes
+ * (opts->seed): estimates[g] equals ll_logdet_forward on A_g assembled in FP64 with the same
+ * options, up to rounding. Where D_r != 0, O must store exactly one diagonal entry of row r
+ * (LL_ERR_INVALID_ARG otherwise, after the passes).
+ * opts as for ll_logdet_forward, with tol = 0 and keep_for_backward = 0 (LL_ERR_UNSUPPORTED
+ * otherwise); TMA step kernel only (step_kernel AUTO or TMA); t x (probe columns of one theta,
+ * rounded up to 16 bytes of a row) <= 1024, t n < 2^31 and k < n, else LL_ERR_UNSUPPORTED. ll_info reports the
+ * phases (ms_*), the launch shapes and deg_max_pass2 = the largest degree. Synchronises
+ * `stream`. */
+ll_status ll_logdet_sweep(ll_handle* h, const ll_csr* O, const double* D, int t, const double* thetas,
+                          const ll_bounds* bounds, const int* degrees, const ll_options* opts, double* estimates,
+                          void* stream);
+
 /* The Gram product X^T Z as CholeskyQR2 forms it (Algorithm 3 step 4: G = Y^T Y; step 6: C = Q^T G):
  * a parity hook for the Gram kernels. X: device, n x kx, row-major with leading dimension ldx, in
  * `layout` LL_PREC_F64 (FP64 elements) or LL_PREC_DF64 (the library's double-float blocks: the 16

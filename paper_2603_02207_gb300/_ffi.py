@@ -97,6 +97,8 @@ SIGNATURES = {
     "ll_param_grad": (_I, [_P, _P, _P, _I64, _I64, _I, _PD, _P]),
     "ll_logdet_batched": (_I, [_P, ctypes.POINTER(ll_csr), ctypes.POINTER(ll_bounds), _I,
                                ctypes.POINTER(ll_options), ctypes.POINTER(_I), _PD, _P]),
+    "ll_logdet_sweep": (_I, [_P, ctypes.POINTER(ll_csr), _P, _I, _PD, ctypes.POINTER(ll_bounds),
+                             ctypes.POINTER(_I), ctypes.POINTER(ll_options), _PD, _P]),
     "ll_gram": (_I, [_P, _I, _P, _I64, _I, _P, _I64, _I, _I64, _I, _P, _P]),
     "ll_get_info": (_I, [_P, ctypes.POINTER(ll_info)]),
     "ll_stop_degrees": (_I, [_P, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]),

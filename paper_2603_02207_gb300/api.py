@@ -330,6 +330,31 @@ def ll_logdet_batched(h: Handle, mats: list, bounds: list, opts: _ffi.ll_options
     return out
 
 
+def ll_logdet_sweep(h: Handle, O: DeviceCSR, D, thetas, bounds: list, opts: _ffi.ll_options, degrees=None,
+                    stream=None):
+    """log det(diag(D) + theta O) for every theta of `thetas` (one block pass pair over all of them,
+    the same probes for each). O: device CSR; D: CUDA FP64 tensor of n values; bounds: (lmin, lmax)
+    of each theta's matrix; degrees: one per theta, or None for opts.degree."""
+    torch = _torch()
+    t = len(thetas)
+    if not (isinstance(D, torch.Tensor) and D.is_cuda and D.dtype == torch.float64 and D.is_contiguous()
+            and D.numel() == O.n):
+        raise ValueError("D must be a contiguous CUDA float64 tensor of n values")
+    if len(bounds) != t or (degrees is not None and len(degrees) != t):
+        raise ValueError("one bound pair (and degree) per theta")
+    th = np.ascontiguousarray(thetas, dtype=np.float64)
+    barr = (_ffi.ll_bounds * t)(*[_ffi.ll_bounds(lo, hi) for lo, hi in bounds])
+    deg = None
+    if degrees is not None:
+        deg = (ctypes.c_int * t)(*[int(x) for x in degrees])
+    out = np.zeros(t, dtype=np.float64)
+    h.check(h._lib.ll_logdet_sweep(h.ptr, ctypes.byref(O.c()), D.data_ptr(), t,
+                                   th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), barr, deg,
+                                   ctypes.byref(opts), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   _stream_ptr(stream)))
+    return out
+
+
 def logdet_leja(A: DeviceCSR, bounds: tuple[float, float], degree: int, probes: int, seed: int,
                 precision: str = "df64", probe_kind: str = "rademacher", handle: Handle | None = None) -> float:
     """logdet_leja(csr, bounds, degree, probes, seed) -> estimate (Algorithm 3)."""

@@ -276,15 +276,13 @@ ll_status bind_exec(ll_handle* h, int precision, int mode, int b, StepExec& E, S
     if (E.kind == LL_KERNEL_TMA) {
         WS(err, int*, "tma_error", sizeof(int));
         E.tl.q.error = err;
-        static const char* dn[NUM_MODES] = {"tma_desc_plain", "tma_desc_accum", "tma_desc_dot", "tma_desc_adj",
-                                            "tma_desc_4", "tma_desc_accum_stop", "tma_desc_dot_stop", "tma_desc_7"};
-        static const char* gn[NUM_MODES] = {"tma_gcol_plain", "tma_gcol_accum", "tma_gcol_dot", "tma_gcol_adj",
-                                            "tma_gcol_4", "tma_gcol_accum_stop", "tma_gcol_dot_stop", "tma_gcol_7"};
-        static const char* mn[NUM_MODES] = {"tma_meta_plain", "tma_meta_accum", "tma_meta_dot", "tma_meta_adj",
-                                            "tma_meta_4", "tma_meta_accum_stop", "tma_meta_dot_stop", "tma_meta_7"};
-        WS(desc, unsigned char*, dn[mode], E.tl.desc_bytes);
-        WS(gcol, int*, gn[mode], E.tl.gcol_bytes);
-        WS(meta, int4*, mn[mode], E.tl.meta_bytes);
+        // one descriptor set per mode (a pass's steps and the adjoint's reverse steps interleave)
+        static const char* mname[NUM_MODES] = {"plain", "accum", "dot", "adj", "4", "accum_stop", "dot_stop", "7",
+                                               "8", "accum_sweep", "dot_sweep", "11", "12", "13", "14", "15"};
+        const std::string mnm = mname[mode];
+        WS(desc, unsigned char*, ("tma_desc_" + mnm).c_str(), E.tl.desc_bytes);
+        WS(gcol, int*, ("tma_gcol_" + mnm).c_str(), E.tl.gcol_bytes);
+        WS(meta, int4*, ("tma_meta_" + mnm).c_str(), E.tl.meta_bytes);
         E.tl.q.desc = desc;
         E.tl.q.gcol = gcol;
         E.tl.q.meta = meta;
@@ -336,6 +334,65 @@ ll_status run_gram(ll_handle* h, int tx, const void* X, long long ldx, int kx, c
 // doubles of Gram partials for either kernel (kx x kz, grid ggrid for k_gram)
 size_t gram_partials_any(const ll_handle* h, int kx, int kz, bool sym, int ggrid) {
     return std::max(gram_partials_doubles(kx, kz, sym, ggrid), gram_tc_partials_doubles(kx, kz, h->sm_count));
+}
+
+// The blocks of Algorithm 3 steps 4 and 6 for one sketch (leading dimensions in columns; typed
+// pointers already offset to the sketch's columns where several share a block)
+struct QrBlocks {
+    const void* P;       // Y: n x kq, P storage type of the precision
+    long long lp;
+    void* q1;            // Q1 of the first CholeskyQR (FP64; double-float pairs outside the F64 mode)
+    long long lq1;
+    const double* G;     // the residual probes, n x kg FP64 (ld kg)
+    void* V;             // the trace block [Q | G'] (W storage type)
+    double* basis;       // [Q | G'] in FP64 (F64 mode) or as double-float pairs (FP32-mixed); unused in DF64
+    long long lv;        // leading dimension of V and basis
+    int vpad;            // columns of V written (from column 0): b2 and zeros up to vpad
+    double* gpart;
+    unsigned int* gticket;
+    double* gram;
+    double* rinv1;
+    double* rinv;
+    int* qrstat;
+    int ggrid;
+};
+
+// Algorithm 3 step 4, Q = CholeskyQR2(Y), and step 6, G' = G - Q (Q^T G), forming V = [Q | G'].
+// Outside the F64 mode Q1 and Q stay double-float column pairs: the products are double-float
+// anyway, and FP64 intermediates would only add conversions on GB300's slow FP64 pipe. In the DF64
+// mode Q lives in V itself; in the FP32-mixed mode [Q | G'] is formed as pairs in the basis block
+// and V (FP32) is written from it; the F64 mode keeps FP64 Q1 and Q (the basis block, which is V).
+ll_status qr_project(ll_handle* h, int prec, int n, int kq, int kg, const QrBlocks& B, cudaStream_t q) {
+    ll_status st;
+    const int b2 = kq + kg;
+    const int pt = p_type_of(prec);
+    const bool dfq = prec != LL_PREC_F64;
+    const bool qv = prec == LL_PREC_DF64;
+    const int tq = dfq ? T_DF64 : T_F64;
+    void* Qb = qv ? B.V : static_cast<void*>(B.basis);
+    const long long l2 = B.lv;
+    if ((st = run_gram(h, pt, B.P, B.lp, kq, nullptr, 0, kq, n, true, B.gpart, B.gticket, B.gram, B.ggrid, q)) != LL_OK)
+        return st;
+    LL_CK(launch_chol_rinv(B.gram, kq, B.rinv1, B.qrstat, q));
+    if (dfq) LL_CK(launch_apply_rinv(pt, B.P, B.lp, n, kq, B.rinv1, nullptr, 0, T_DF64, B.q1, B.lq1, q));
+    else LL_CK(launch_apply_rinv(pt, B.P, B.lp, n, kq, B.rinv1, static_cast<double*>(B.q1), B.lq1, T_F64, nullptr, 0, q));
+    if ((st = run_gram(h, tq, B.q1, B.lq1, kq, nullptr, 0, kq, n, true, B.gpart, B.gticket, B.gram, B.ggrid, q)) != LL_OK)
+        return st;
+    LL_CK(launch_chol_rinv(B.gram, kq, B.rinv, B.qrstat, q));
+    if (dfq) LL_CK(launch_apply_rinv(tq, B.q1, B.lq1, n, kq, B.rinv, nullptr, l2, T_DF64, Qb, l2, q));
+    else LL_CK(launch_apply_rinv(tq, B.q1, B.lq1, n, kq, B.rinv, B.basis, l2, T_F64, nullptr, l2, q));
+    if ((st = run_gram(h, tq, Qb, l2, kq, B.G, kg, kg, n, false, B.gpart, B.gticket, B.gram, B.ggrid, q)) != LL_OK)
+        return st;
+    // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
+    // The typed block pointer is offset by kq elements: element index r * l2 + kq + c.
+    LL_CK(launch_project(tq, Qb, l2, kq, B.G, kg, kg, B.gram, n, dfq ? nullptr : B.basis + kq, l2, T_DF64,
+                         dfq ? Qb : nullptr, l2, (b2 & 1), kq, q));
+    h->launches += 8;
+    if (dfq && !qv) {
+        LL_CK(launch_dfp_to_f32(B.basis, l2, static_cast<float*>(B.V), l2, n, b2, B.vpad, q));
+        h->launches++;
+    }
+    return LL_OK;
 }
 
 // Chooses the step launch for (precision, mode, n, nnz, b). kernel = LL_KERNEL_AUTO times the
@@ -1392,35 +1449,10 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
             rw1 = h->last_rows;
             LL_CK(rec(h->ev[2], q));
 
-            // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']. Outside the
-            // F64 mode Q1 and Q stay double-float column pairs: the products are double-float
-            // anyway, and FP64 intermediates would only add conversions on GB300's slow FP64
-            // pipe. In the DF64 mode Q lives in V itself; in the FP32-mixed mode [Q | G'] is
-            // formed as pairs in the basis block and V (FP32) is written from it; the F64 mode
-            // keeps FP64 Q1 and Q (the basis block).
-            const bool dfq = prec != LL_PREC_F64;
-            const bool qv = prec == LL_PREC_DF64;
-            const int tq = dfq ? T_DF64 : T_F64;
-            const long long ldq1 = dfq ? l1 : kq;
-            void* Qb = qv ? V : static_cast<void*>(basis);
-            if ((st = run_gram(h, pt, P, l1, kq, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q)) != LL_OK) return st;
-            LL_CK(launch_chol_rinv(gram, kq, rinv1, qrstat, q));
-            if (dfq) LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, nullptr, 0, T_DF64, q1, l1, q));
-            else LL_CK(launch_apply_rinv(pt, P, l1, n, kq, rinv1, q1, kq, T_F64, nullptr, 0, q));
-            if ((st = run_gram(h, tq, q1, ldq1, kq, nullptr, 0, kq, n, true, gpart, gticket, gram, ggrid, q)) != LL_OK) return st;
-            LL_CK(launch_chol_rinv(gram, kq, rinv, qrstat, q));
-            if (dfq) LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, nullptr, l2, T_DF64, Qb, l2, q));
-            else LL_CK(launch_apply_rinv(tq, q1, ldq1, n, kq, rinv, basis, l2, T_F64, nullptr, l2, q));
-            if ((st = run_gram(h, tq, Qb, l2, kq, G, kg, kg, n, false, gpart, gticket, gram, ggrid, q)) != LL_OK) return st;
-            // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
-            // The typed block pointer is offset by kq elements: element index r * l2 + kq + c.
-            LL_CK(launch_project(tq, Qb, l2, kq, G, kg, kg, gram, n, dfq ? nullptr : basis + kq, l2, T_DF64,
-                                 dfq ? Qb : nullptr, l2, (b2 & 1), kq, q));
-            h->launches += 8;
-            if (dfq && !qv) {
-                LL_CK(launch_dfp_to_f32(basis, l2, static_cast<float*>(V), l2, n, b2, l2, q));
-                h->launches++;
-            }
+            // step 4: Q = CholeskyQR2(Y); step 6: G' = G - Q (Q^T G); V = [Q | G']
+            const QrBlocks qb{P,     l1,      q1,   prec != LL_PREC_F64 ? l1 : kq, G,    V,      basis, l2, l2,
+                              gpart, gticket, gram, rinv1, rinv, qrstat, ggrid};
+            if ((st = qr_project(h, prec, n, kq, kg, qb, q)) != LL_OK) return st;
             LL_CK(rec(h->ev[3], q));
         }
 
@@ -2360,6 +2392,386 @@ ll_status ll_gram(ll_handle* h, int layout, const void* X, int64_t ldx, int kx, 
     h->launches++;
     h->tma_used = true;
     return check_tma_flag(h, s);
+}
+
+}  // extern "C"
+
+// One pass of a sweep (MODE_ACCUM_SWEEP or MODE_DOT_SWEEP) over t groups of gw columns, sorted by
+// degree (deg[0] >= deg[1] >= ...). Every block stacks the groups' n x gw blocks (group g's rows at
+// g n, leading dimension gw: W_0 = win0, the ping-pong pair wa / wb, P); step j runs on the groups
+// with deg[g] > j, the first ones of the stack, through a TMA plan for that many groups
+// (re-planned, with its tile descriptors, where the count drops). vals: the t matrices' prepared
+// values, group g's at g * O->nnz; dots: (deg[0] + 1) x (t gw) traces, column g gw + c for group
+// g; tab / tab_df: SWEEP_SCALARS per group for every step (device, t * SWEEP_SCALARS per step).
+// The launch shape (CTA size, column pairs per thread) is timed on all t groups once per
+// (precision, mode, n, nnz, t gw) and cached on the handle.
+ll_status run_sweep_pass(ll_handle* h, const ll_csr* O, const void* vals, int prec, int mode, int n, int t, int gw,
+                         const std::vector<int>& deg, const void* win0, void* wa, void* wb, void* P, double* dots,
+                         const double* tab, const float2* tab_df, int threads, int rpt, cudaStream_t s) {
+    const int mmax = deg[0];
+    const long long dld = (long long)t * gw;   // columns of a row of dots
+    StepParams p{};
+    p.rowptr = O->rowptr;
+    p.colind = O->colind;
+    p.vals = vals;
+    p.ldw = gw;
+    p.ldv = gw;
+    p.ldp = gw;
+    p.p = P;
+    p.sw_gpairs = gw / 2;
+    p.sw_vstride = O->nnz;
+    if (base_mode(mode) == MODE_DOT) {
+        WS(ticket, unsigned int*, "dot_ticket", sizeof(unsigned int));
+        LL_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
+        p.ticket = ticket;
+        p.v = win0;
+    }
+    {
+        WS(err, int*, "tma_error", sizeof(int));
+        LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    }
+    ll_status st;
+    const int bfull = t * gw;
+    if (threads <= 0 && rpt <= 0) {
+        const auto key = std::make_tuple(prec, mode, n, O->nnz, bfull, (long long)gw);
+        auto it = h->tuned.find(key);
+        if (it != h->tuned.end()) {
+            threads = std::get<1>(it->second);
+            rpt = std::get<2>(it->second);
+        } else {
+            // a representative non-first step on all groups (its outputs are overwritten by the pass)
+            const int jt = mmax > 1 ? 1 : 0;
+            p.win = win0;
+            p.wout = wa;
+            p.first = 0;
+            p.sw_scal = tab + (size_t)jt * t * SWEEP_SCALARS;
+            p.sw_scal_df = tab_df + (size_t)jt * t * SWEEP_SCALARS;
+            if (base_mode(mode) == MODE_DOT) {
+                p.dots_next = dots + (size_t)(jt + 1) * dld;
+                p.dots_first = dots;
+            }
+            const int cands[4][2] = {{512, 0}, {256, 0}, {512, 2}, {256, 2}};
+            float best_ms = 0.f;
+            bool have = false;
+            for (const auto& c : cands) {
+                StepParams q = p;
+                StepExec C;
+                if (!plan_exec(h, LL_KERNEL_TMA, prec, mode, n, O->nnz, bfull, c[0], c[1], q, C)) continue;
+                if ((st = bind_exec(h, prec, mode, bfull, C, q, s)) != LL_OK) return st;
+                LL_CK(exec_step(h, prec, mode, C, q, s));
+                LL_CK(cudaEventRecord(h->ev[6], s));
+                LL_CK(exec_step(h, prec, mode, C, q, s));
+                LL_CK(exec_step(h, prec, mode, C, q, s));
+                LL_CK(cudaEventRecord(h->ev[7], s));
+                LL_CK(cudaEventSynchronize(h->ev[7]));
+                if ((st = check_tma_flag(h, s)) != LL_OK) return st;
+                float ms = 0.f;
+                LL_CK(cudaEventElapsedTime(&ms, h->ev[6], h->ev[7]));
+                if (!have || ms < best_ms) {
+                    best_ms = ms;
+                    threads = c[0];
+                    rpt = c[1];
+                    have = true;
+                }
+            }
+            if (!have) return fail(h, LL_ERR_UNSUPPORTED, "sweep: no TMA step plan fits the block");
+            h->tuned[key] = std::make_tuple((int)LL_KERNEL_TMA, threads, rpt);
+        }
+    }
+    StepExec E;
+    int act = -1;
+    for (int j = 0; j < mmax; ++j) {
+        int a = 0;
+        while (a < t && deg[a] > j) ++a;
+        if (a != act) {
+            StepParams q = p;
+            // two pairs per thread need an even number of pairs per group: otherwise one pair
+            if (!plan_exec(h, LL_KERNEL_TMA, prec, mode, n, O->nnz, a * gw, threads, rpt, q, E)) {
+                q = p;
+                if (!plan_exec(h, LL_KERNEL_TMA, prec, mode, n, O->nnz, a * gw, threads, 0, q, E))
+                    return fail(h, LL_ERR_UNSUPPORTED, "sweep: no TMA step plan fits the block");
+            }
+            p = q;
+            if ((st = bind_exec(h, prec, mode, a * gw, E, p, s)) != LL_OK) return st;
+            if (act < 0) {
+                h->last_kernel = E.kind;
+                h->last_threads = E.cta();
+                h->last_np = E.tl.np;
+                h->last_rows = E.tl.q.R;
+            }
+            act = a;
+        }
+        p.win = j == 0 ? win0 : ((j & 1) ? wa : wb);
+        p.wout = (j & 1) ? wb : wa;
+        p.first = j == 0;
+        p.sw_scal = tab + (size_t)j * t * SWEEP_SCALARS;
+        p.sw_scal_df = tab_df + (size_t)j * t * SWEEP_SCALARS;
+        if (base_mode(mode) == MODE_DOT) {
+            p.dots_next = dots + (size_t)(j + 1) * dld;
+            p.dots_first = dots;
+        }
+        p.jnext = j + 1;
+        LL_CK(exec_step(h, prec, mode, E, p, s));
+    }
+    return LL_OK;
+}
+
+extern "C" {
+
+ll_status ll_logdet_sweep(ll_handle* h, const ll_csr* O, const double* D, int t, const double* thetas,
+                          const ll_bounds* bounds, const int* degrees, const ll_options* opts, double* estimates,
+                          void* stream) {
+    if (!h || !opts || !estimates || !thetas || !bounds || t < 1) return LL_ERR_INVALID_ARG;
+    ll_status st = check_csr_args(h, O);
+    if (st != LL_OK) return st;
+    const ll_options& o = *opts;
+    if (o.estimator != LL_EST_HUTCHPP && o.estimator != LL_EST_HUTCHINSON) return fail(h, LL_ERR_INVALID_ARG, "unknown estimator");
+    const bool hutch = o.estimator == LL_EST_HUTCHINSON;
+    if (hutch ? o.probes <= 0 : (o.probes <= 0 || o.probes % 3 != 0))
+        return fail(h, LL_ERR_INVALID_ARG, hutch ? "probes must be positive" : "probes must be a positive multiple of 3");
+    if (o.probe_kind != LL_PROBE_RADEMACHER && o.probe_kind != LL_PROBE_GAUSSIAN) return fail(h, LL_ERR_INVALID_ARG, "unknown probe kind");
+    if (o.precision < LL_PREC_F64 || o.precision > LL_PREC_F32_MIXED) return fail(h, LL_ERR_INVALID_ARG, "unknown precision");
+    if (o.sval_mode != LL_SVAL_CENTER && o.sval_mode != LL_SVAL_HALF_LMAX) return fail(h, LL_ERR_INVALID_ARG, "unknown s_val mode");
+    if (o.dd_scheme != LL_DD_AUTO && o.dd_scheme != LL_DD_TABLE_Q) return fail(h, LL_ERR_INVALID_ARG, "unknown divided-difference scheme");
+    if (o.qr_gram < LL_GRAM_AUTO || o.qr_gram > LL_GRAM_DFLOAT) return fail(h, LL_ERR_INVALID_ARG, "unknown Gram method");
+    if (o.tol != 0.0 || o.keep_for_backward)
+        return fail(h, LL_ERR_UNSUPPORTED, "a sweep runs fixed degrees (tol = 0) and keeps nothing for a backward");
+    if (o.step_kernel != LL_KERNEL_AUTO && o.step_kernel != LL_KERNEL_TMA)
+        return fail(h, LL_ERR_UNSUPPORTED, "a sweep runs on the TMA step kernel");
+    for (int g = 0; g < t; ++g) {
+        if (!std::isfinite(thetas[g])) return fail(h, LL_ERR_INVALID_ARG, "non-finite theta");
+        if ((st = check_bounds(h, bounds[g])) != LL_OK) return st;
+        const int m = degrees ? degrees[g] : o.degree;
+        if (m < 1) return fail(h, LL_ERR_INVALID_ARG, "degree must be >= 1");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    h->launches = 0;
+    h->kept = false;
+    h->have_forward = false;
+    h->gram_method = o.qr_gram;
+    h->spin_budget = o.timeout_cycles > 0 ? o.timeout_cycles : 4000000000LL;
+    const int n = (int)O->n;
+    if (n == 0) {
+        for (int g = 0; g < t; ++g) estimates[g] = 0.0;
+        return LL_OK;
+    }
+    if (!D) return fail(h, LL_ERR_INVALID_ARG, "null diagonal");
+    const int kg = hutch ? o.probes : o.probes / 3;
+    const int kq = hutch ? 0 : kg;
+    const int b2 = kq + kg;
+    if (!hutch && kq >= n) return fail(h, LL_ERR_UNSUPPORTED, "a sweep needs k < n");
+    const int prec = o.precision;
+    // group widths: whole 16-byte units of a W row (4 FP32 columns, 2 otherwise); every block stacks
+    // the t groups' n x wg blocks (group g's rows from g n)
+    const int al = prec == LL_PREC_F32_MIXED ? 4 : 2;
+    const int wg1 = (kq + al - 1) / al * al, wg2 = (b2 + al - 1) / al * al;
+    const long long L2 = (long long)t * wg2;   // columns of a row of the traces
+    if (L2 > 1024 || kq > 96)
+        return fail(h, LL_ERR_UNSUPPORTED, "a sweep takes at most 1024 trace columns (theta count x probe columns)");
+    if ((long long)t * n >= (1LL << 31)) return fail(h, LL_ERR_UNSUPPORTED, "theta count x n must be < 2^31");
+    if ((st = validate_csr(h, O, s)) != LL_OK) return st;
+
+    // per theta: sigma, the scaled interval, Léja points, coefficients; groups by degree, descending
+    struct Grp { int idx, m; double sigma, c, gamma; std::vector<double> xi, d; };
+    std::vector<Grp> gs(t);
+    for (int g = 0; g < t; ++g) {
+        Grp& x = gs[g];
+        x.idx = g;
+        x.m = degrees ? degrees[g] : o.degree;
+        x.sigma = sigma_of(bounds[g].lmin);
+        const double lt = bounds[g].lmin / x.sigma, ut = bounds[g].lmax / x.sigma;
+        if ((st = setup_coefficients(h, lt, ut, x.m, o.sval_mode, x.xi, x.d, o.dd_scheme)) != LL_OK) return st;
+        x.c = (lt + ut) / 2.0;
+        x.gamma = (ut - lt) / 4.0;
+    }
+    std::stable_sort(gs.begin(), gs.end(), [](const Grp& a, const Grp& b) { return a.m > b.m; });
+    std::vector<int> deg(t);
+    for (int g = 0; g < t; ++g) deg[g] = gs[g].m;
+    const int mmax = deg[0];
+    // step scalars of group g at step j: beta_{g,j} = -(c_g / gamma_g + xi_j), d_{g,j+1}, d_{g,0}
+    // (B_g = (A_g / sigma_g - c_g I) / gamma_g, its values A_g / (sigma_g gamma_g) prepared below)
+    std::vector<double> tab((size_t)mmax * t * SWEEP_SCALARS, 0.0);
+    for (int j = 0; j < mmax; ++j)
+        for (int g = 0; g < t; ++g) {
+            const Grp& x = gs[g];
+            if (j >= x.m) continue;
+            double* e = &tab[((size_t)j * t + g) * SWEEP_SCALARS];
+            e[0] = -(x.c / x.gamma + x.xi[j]);
+            e[1] = x.d[j + 1];
+            e[2] = x.d[0];
+        }
+    std::vector<float2> tab_df(tab.size());
+    for (size_t x = 0; x < tab.size(); ++x) tab_df[x] = df_split(tab[x]);
+
+    const int wt = w_type_of(prec), pt = p_type_of(prec);
+    const size_t ew = elem_size(wt), ep = elem_size(pt);
+    WS(vals, void*, "sw_vals", (size_t)t * O->nnz * ew);
+    WS(vflag, int*, "sw_value_flag", sizeof(int));
+    WS(dtab, double*, "sw_tab", tab.size() * sizeof(double));
+    WS(dtab_df, float2*, "sw_tab_df", tab_df.size() * sizeof(float2));
+    WS(G, double*, "sw_G", (size_t)n * kg * sizeof(double));
+    const size_t blk1 = (size_t)n * wg1, blk2 = (size_t)n * wg2;   // elements of one group's block
+    WS(wa, void*, "sw_wa", (size_t)t * blk2 * ew);
+    WS(wb, void*, "sw_wb", (size_t)t * blk2 * ew);
+    WS(V, void*, "sw_V", (size_t)t * blk2 * ew);
+    WS(dots, double*, "sw_dots", (size_t)(mmax + 1) * L2 * sizeof(double));
+    WS(qrstat, int*, "sw_qr_status", sizeof(int));
+    WS(tma_err, int*, "tma_error", sizeof(int));
+    void* S = nullptr;
+    void* P = nullptr;
+    void* q1 = nullptr;
+    double* basis = nullptr;
+    double* gpart = nullptr;
+    unsigned int* gticket = nullptr;
+    double* gram = nullptr;
+    double* rinv1 = nullptr;
+    double* rinv = nullptr;
+    const int ggrid = h->sm_count * 2;
+    if (!hutch) {
+        WS(S_, void*, "sw_S", (size_t)t * blk1 * ew);
+        WS(P_, void*, "sw_P", (size_t)t * blk1 * ep);
+        WS(q1_, void*, "sw_q1", blk1 * sizeof(double));
+        S = S_;
+        P = P_;
+        q1 = q1_;
+        if (prec != LL_PREC_DF64) {
+            WS(basis_, double*, "sw_basis", (size_t)t * blk2 * sizeof(double));
+            basis = basis_;
+        }
+        const size_t gp1 = gram_partials_any(h, kq, kq, true, ggrid), gp2 = gram_partials_any(h, kq, kg, false, ggrid);
+        WS(gpart_, double*, "sw_gram_partials", (gp1 > gp2 ? gp1 : gp2) * sizeof(double));
+        WS(gticket_, unsigned int*, "sw_gram_ticket", sizeof(unsigned int));
+        WS(gram_, double*, "sw_gram", (size_t)kq * kg * sizeof(double));
+        WS(rinv1_, double*, "sw_rinv1", (size_t)kq * kq * sizeof(double));
+        WS(rinv_, double*, "sw_rinv", (size_t)kq * kq * sizeof(double));
+        gpart = gpart_;
+        gticket = gticket_;
+        gram = gram_;
+        rinv1 = rinv1_;
+        rinv = rinv_;
+    }
+    // the F64 mode's trace block is the FP64 basis itself
+    if (prec == LL_PREC_F64 && !hutch) V = basis;
+
+    LL_CK(cudaEventRecord(h->ev[0], s));
+    LL_CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    LL_CK(cudaMemcpyAsync(dtab_df, tab_df.data(), tab_df.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    LL_CK(cudaMemsetAsync(qrstat, 0, sizeof(int), s));
+    if (gticket) LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), s));
+    // every group's matrix A_g = diag(D) + theta_g O, prepared as A_g / (sigma_g gamma_g)
+    LL_CK(cudaMemsetAsync(vflag, 0, sizeof(int), s));
+    for (int g = 0; g < t; ++g) {
+        const Grp& x = gs[g];
+        LL_CK(launch_prepare_pencil(O->rowptr, O->colind, O->values, O->dtype, D, n, thetas[x.idx],
+                                    1.0 / (x.sigma * x.gamma), prec, static_cast<char*>(vals) + (size_t)g * O->nnz * ew,
+                                    vflag, s));
+        h->launches++;
+    }
+    // the same probes for every theta (common random numbers across the sweep): each group's
+    // columns get the block ll_logdet_forward draws with this seed
+    for (int g = 0; g < t; ++g) {
+        if (hutch) {
+            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_G, n, kg, wg2, static_cast<char*>(V) + g * blk2 * ew, wg2, s));
+        } else {
+            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, wg1, static_cast<char*>(S) + g * blk1 * ew, wg1, s));
+        }
+        h->launches++;
+    }
+    if (!hutch) {
+        LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, s));
+        h->launches++;
+    }
+    LL_CK(cudaEventRecord(h->ev[1], s));
+    int k1 = 0, t1 = 0, np1 = 1, rw1 = 0;
+    if (!hutch) {
+        // step 3 for every theta: Y_g = p_g(A_g~) S, then steps 4 and 6 per group
+        st = run_sweep_pass(h, O, vals, prec, MODE_ACCUM_SWEEP, n, t, wg1, deg, S, wa, wb, P, nullptr, dtab, dtab_df,
+                            o.threads_per_block, o.rows_per_thread, s);
+        if (st != LL_OK) return st;
+        k1 = h->last_kernel;
+        t1 = h->last_threads;
+        np1 = h->last_np;
+        rw1 = h->last_rows;
+        LL_CK(cudaEventRecord(h->ev[2], s));
+        for (int g = 0; g < t; ++g) {
+            const QrBlocks qb{static_cast<char*>(P) + g * blk1 * ep,
+                              wg1,
+                              q1,
+                              wg1,
+                              G,
+                              static_cast<char*>(V) + g * blk2 * ew,
+                              basis ? basis + g * blk2 : nullptr,
+                              wg2,
+                              wg2,
+                              gpart,
+                              gticket,
+                              gram,
+                              rinv1,
+                              rinv,
+                              qrstat,
+                              ggrid};
+            if ((st = qr_project(h, prec, n, kq, kg, qb, s)) != LL_OK) return st;
+        }
+    } else {
+        LL_CK(cudaEventRecord(h->ev[2], s));
+    }
+    LL_CK(cudaEventRecord(h->ev[3], s));
+    // steps 5-6 for every theta: traces t_j[col] = <V_col, W_j col>
+    st = run_sweep_pass(h, O, vals, prec, MODE_DOT_SWEEP, n, t, wg2, deg, V, wa, wb, nullptr, dots, dtab, dtab_df,
+                        o.threads_per_block, o.rows_per_thread, s);
+    if (st != LL_OK) return st;
+    LL_CK(cudaEventRecord(h->ev[4], s));
+
+    std::vector<double> hd((size_t)(mmax + 1) * L2);
+    int hstat = 0, herr = 0, hflag = 0;
+    LL_CK(cudaMemcpyAsync(hd.data(), dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaMemcpyAsync(&hflag, vflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaMemcpyAsync(&hstat, qrstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaMemcpyAsync(&herr, tma_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    h->tma_used = false;
+    if (hflag) return fail(h, LL_ERR_INVALID_ARG, "O must store one diagonal entry in every row where D is non-zero");
+    if (herr) return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out");
+    if (hstat) return fail(h, LL_ERR_QR_BREAKDOWN, "CholeskyQR2: non-positive pivot (rank-deficient sketch)");
+    // step 7 per theta: n log sigma_g + tr(Q_g^T F_g Q_g) + (1/k) tr(G_g'^T F_g G_g')
+    for (int g = 0; g < t; ++g) {
+        const Grp& x = gs[g];
+        const size_t c0 = (size_t)g * wg2;
+        double tq = 0.0, tr = 0.0;
+        for (int j = 0; j <= x.m; ++j) {
+            double sq = 0.0, sr = 0.0;
+            for (int col = 0; col < kq; ++col) sq += hd[(size_t)j * L2 + c0 + col];
+            for (int col = kq; col < b2; ++col) sr += hd[(size_t)j * L2 + c0 + col];
+            tq += x.d[j] * sq;
+            tr += x.d[j] * sr;
+        }
+        tr /= (double)kg;
+        if (!std::isfinite(tq) || !std::isfinite(tr)) return fail(h, LL_ERR_NONFINITE, "non-finite trace");
+        estimates[x.idx] = (double)n * std::log(x.sigma) + tq + tr;
+    }
+    ll_info& I = h->info;
+    I = ll_info{};
+    I.k = kq;
+    I.kernel_launches = h->launches;
+    cudaEventElapsedTime(&I.ms_probes, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&I.ms_pass1, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&I.ms_qr, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&I.ms_pass2, h->ev[3], h->ev[4]);
+    cudaEventElapsedTime(&I.ms_total, h->ev[0], h->ev[4]);
+    I.kernel_pass1 = k1;
+    I.threads_pass1 = t1;
+    I.pairs_pass1 = np1;
+    I.rows_pass1 = rw1;
+    I.kernel_pass2 = h->last_kernel;
+    I.threads_pass2 = h->last_threads;
+    I.pairs_pass2 = h->last_np;
+    I.rows_pass2 = h->last_rows;
+    I.deg_max_pass1 = hutch ? 0 : mmax;
+    I.deg_max_pass2 = mmax;
+    double dsum = 0.0;
+    for (int g = 0; g < t; ++g) dsum += deg[g];
+    I.deg_mean_pass2 = dsum / t;
+    return LL_OK;
 }
 
 ll_status ll_get_info(const ll_handle* h, ll_info* out) {

@@ -16,9 +16,21 @@ enum StepMode { MODE_PLAIN = 0, MODE_ACCUM = 1, MODE_DOT = 2, MODE_ADJ = 3 };
 constexpr int MODE_STOP = 4;
 constexpr int MODE_ACCUM_STOP = MODE_ACCUM | MODE_STOP;
 constexpr int MODE_DOT_STOP = MODE_DOT | MODE_STOP;
-constexpr int NUM_MODES = 8;
+// A sweep over t matrices A_g that share one sparsity pattern (a theta grid of a parametric
+// matrix), on top of ACCUM or DOT, on the TMA step kernel: the blocks stack one n x (2 sw_gpairs)
+// block per group (ldw = 2 sw_gpairs; group g's row r is row g n + r; b = the columns of all
+// groups), group g for A_g, with its own prepared values (each tile record holds one operand
+// offset and the values of every group) and its own step scalars (beta_{g,j}, d_{g,j+1},
+// d_{g,0}). A tile loads its operand rows once per group.
+constexpr int MODE_SWEEP = 8;
+constexpr int MODE_ACCUM_SWEEP = MODE_ACCUM | MODE_SWEEP;
+constexpr int MODE_DOT_SWEEP = MODE_DOT | MODE_SWEEP;
+constexpr int NUM_MODES = 16;
 __host__ __device__ constexpr int base_mode(int mode) { return mode & 3; }
 __host__ __device__ constexpr bool stop_mode(int mode) { return (mode & MODE_STOP) != 0; }
+__host__ __device__ constexpr bool sweep_mode(int mode) { return (mode & MODE_SWEEP) != 0; }
+// per group and step of a sweep: beta_{g,j}, d_{g,j+1}, d_{g,0}
+constexpr int SWEEP_SCALARS = 3;
 
 // One Léja step over an n x b block, all columns at once (Algorithm 2 loop body):
 //   Wout = B Win - xi_j Win   with B = (A - c I)/gamma folded into prepared values a_e / gamma
@@ -55,6 +67,13 @@ struct StepParams {
     int* done;                   // 1 once no column runs: the step returns at once
     double tol;                  // Algorithm 2's tolerance
     int jnext;                   // j + 1: the index of the W this step writes
+    // SWEEP modes: the step's SWEEP_SCALARS scalars of every group (FP64 and double-float), the
+    // column pairs of one group, and the elements between the groups' value arrays (vals holds
+    // group g's prepared values at g * sw_vstride)
+    const double* sw_scal;
+    const float2* sw_scal_df;
+    int sw_gpairs;
+    long long sw_vstride;
 };
 
 struct StepLaunch {
@@ -91,6 +110,12 @@ cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, cons
 // out[e] = convert(values[e] * scale) into the storage type of `precision`
 cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, double scale, int precision,
                                   void* out, cudaStream_t s);
+// out[e] = convert((theta * o_e + [c_e == r_e] D_{r_e}) * scale) into the storage type of `precision`
+// (one matrix of a pencil sweep diag(D) + theta O, prepared as launch_prepare_values would prepare
+// it assembled in FP64); flag[0] |= 1 where D_r != 0 and row r stores no single diagonal entry
+cudaError_t launch_prepare_pencil(const int32_t* rowptr, const int32_t* colind, const void* o, int dtype, const double* D,
+                                  int n, double theta, double scale, int precision, void* out, int* flag,
+                                  cudaStream_t s);
 // out (type of `precision` W storage, ld_out) <- in (FP64, ld_in), n x b; columns [b, pad) of out
 // are set to zero
 cudaError_t launch_convert_block(const double* in, long long ld_in, int precision, void* out,
@@ -301,6 +326,9 @@ struct TmaParams {
     int gcol_stride;   // bytes per tile of the gather-column array (4 window rows, then fcap columns)
     int stage_bytes;   // bytes per stage: window, aux rows, gathered rows, descriptor
     int off_aux, off_gat, off_desc;   // the window is at offset 0
+    int ngrp, gsz;     // a sweep's groups per tile and bytes of one group's part of a stage (its
+                       // window, V or P rows and gathered rows at offsets off_aux, off_gat from
+                       // g gsz; the shared descriptor at off_desc); 1, 0 otherwise
     int ring_base;     // gather-column rings of the producer warps, after the stages
     const unsigned char* desc;   // per-tile descriptors (built once per pass)
     const int* gcol;             // per-tile gather columns

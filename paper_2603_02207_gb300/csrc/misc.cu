@@ -1,5 +1,7 @@
 // Probe generation, CSR validation, Gershgorin bounds, value preparation, block conversions and
 // the FP64 pieces of the power iteration.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -211,6 +213,49 @@ cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, doub
         else if (t == T_F32) k_prepare<float, float><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float*)out);
         else k_prepare<float, float2><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float2*)out);
     }
+    return cudaGetLastError();
+}
+
+// Values of one matrix of a pencil sweep, A = diag(D) + theta O, prepared like k_prepare: out[e] =
+// convert((theta * o_e + [c_e == r] D_r) * scale), the product and the sum rounded separately (no
+// FMA), as the same matrix assembled in FP64 and prepared on its own. One thread per row; flag[0]
+// |= 1 where D_r != 0 and row r stores no diagonal entry or more than one.
+template <typename TI, typename TO>
+__global__ void k_prepare_pencil(const int32_t* rowptr, const int32_t* colind, const TI* o, const double* D, int n,
+                                 double theta, double scale, TO* out, int* flag) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const double dr = D[r];
+        int nd = 0;
+        for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+            double v = __dmul_rn(theta, (double)o[e]);
+            if (colind[e] == r) {
+                v = __dadd_rn(v, dr);
+                ++nd;
+            }
+            store_f64<TO>(out, (size_t)e, __dmul_rn(v, scale));
+        }
+        if (nd != 1 && dr != 0.0) atomicOr(flag, 1);
+    }
+}
+
+cudaError_t launch_prepare_pencil(const int32_t* rowptr, const int32_t* colind, const void* o, int dtype, const double* D,
+                                  int n, double theta, double scale, int precision, void* out, int* flag,
+                                  cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int grid = (int)std::min<int64_t>(((int64_t)n + threads - 1) / threads, 152 * 16);
+    const int t = w_type_of(precision);
+#define PP_(TI, TO) k_prepare_pencil<TI, TO><<<grid, threads, 0, s>>>(rowptr, colind, (const TI*)o, D, n, theta, scale, (TO*)out, flag)
+    if (dtype == LL_F64) {
+        if (t == T_F64) PP_(double, double);
+        else if (t == T_F32) PP_(double, float);
+        else PP_(double, float2);
+    } else {
+        if (t == T_F64) PP_(float, double);
+        else if (t == T_F32) PP_(float, float);
+        else PP_(float, float2);
+    }
+#undef PP_
     return cudaGetLastError();
 }
 

@@ -63,8 +63,34 @@ struct StepScalars {
     double cadj0, cadj1;
     f2x ch2, cl2, nch2, cf2;
     double dn0, dn1;   // d_{j+1} per column (zero in retired columns under the stopping rule)
+    double betad, d0d;   // beta_j and d_0 (FP64)
+    __device__ __forceinline__ StepScalars() {}
+    // the scalars of column group g of a sweep (beta_{g,j}, d_{g,j+1}, d_{g,0}; no stopping rule)
+    __device__ __forceinline__ static StepScalars group(const StepParams& p, int g) {
+        StepScalars S;
+        const float2* q = p.sw_scal_df + g * SWEEP_SCALARS;
+        const double* qd = p.sw_scal + g * SWEEP_SCALARS;
+        S.betad = qd[0];
+        S.dn0 = S.dn1 = qd[1];
+        S.d0d = qd[2];
+        S.bh2 = f2_pack(q[0].x, q[0].x);
+        S.bl2 = f2_pack(q[0].y, q[0].y);
+        S.nbh2 = f2_pack(-q[0].x, -q[0].x);
+        S.beta2 = S.bh2;
+        S.dnh2 = f2_pack(q[1].x, q[1].x);
+        S.dnl2 = f2_pack(q[1].y, q[1].y);
+        S.ndnh2 = f2_pack(-q[1].x, -q[1].x);
+        S.d0h2 = f2_pack(q[2].x, q[2].x);
+        S.d0l2 = f2_pack(q[2].y, q[2].y);
+        S.nd0h2 = f2_pack(-q[2].x, -q[2].x);
+        S.cadj0 = S.cadj1 = 0.0;
+        S.ch2 = S.cl2 = S.nch2 = S.cf2 = 0ull;
+        return S;
+    }
     // masked = true: d_{j+1} applies only to the columns with live[col] set
     __device__ __forceinline__ StepScalars(const StepParams& p, int cp, bool masked = false) {
+        betad = p.beta;
+        d0d = p.d0;
         bh2 = f2_pack(p.beta_df.x, p.beta_df.x);
         bl2 = f2_pack(p.beta_df.y, p.beta_df.y);
         nbh2 = f2_pack(-p.beta_df.x, -p.beta_df.x);
@@ -101,16 +127,15 @@ __device__ __forceinline__ void row_epilogue(const StepParams& p, const StepScal
     constexpr int MB = base_mode(MODE);
     constexpr bool STOP = stop_mode(MODE);
     if constexpr (PREC == LL_PREC_F64) {
-        double w0 = fma(p.beta, wr.x, A.a0), w1 = fma(p.beta, wr.y, A.a1);
+        double w0 = fma(S.betad, wr.x, A.a0), w1 = fma(S.betad, wr.y, A.a1);
         if constexpr (MB == MODE_ADJ) {
             w0 = fma(S.cadj0, vr.x, w0);
             w1 = fma(S.cadj1, vr.y, w1);
         }
         *wout = make_double2(w0, w1);
         if constexpr (MB == MODE_ACCUM) {
-            const double b0 = p.first ? p.d0 * wr.x : po.x, b1 = p.first ? p.d0 * wr.y : po.y;
-            if constexpr (STOP) *pout = make_double2(fma(S.dn0, w0, b0), fma(S.dn1, w1, b1));
-            else *pout = make_double2(fma(p.dn, w0, b0), fma(p.dn, w1, b1));
+            const double b0 = p.first ? S.d0d * wr.x : po.x, b1 = p.first ? S.d0d * wr.y : po.y;
+            *pout = make_double2(fma(S.dn0, w0, b0), fma(S.dn1, w1, b1));
         }
         if constexpr (MB == MODE_DOT) {
             T.td[0] = fma(vr.x, w0, T.td[0]);

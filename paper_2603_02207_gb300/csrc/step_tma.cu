@@ -164,27 +164,52 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
             const int nw = mt.z;
             unsigned char* st = smem + s * q.stage_bytes;
             const uint32_t bar = smem_u32(&full[s]);
+            // a sweep loads every operand region once per active group: group g's rows are rows
+            // g n + r of the stacked blocks, its part of the stage starts at g gsz
+            const int ngrp = sweep_mode(MODE) ? q.ngrp : 1;
             if (lane == 0) {
                 // (the test hook adds 16 bytes to tile 0 that no copy delivers: its waits run out)
                 const uint32_t dbytes = (uint32_t)q.hdr_bytes + (uint32_t)mt.x * (uint32_t)q.recbytes;
                 const uint32_t dbytes16 = (dbytes + 15u) & ~15u;
-                const uint32_t bytes = dbytes16 + (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
-                                       (uint32_t)(1 + nw) * (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
-                                       (has_aux ? (uint32_t)R * (uint32_t)q.auxbytes : 0u) +
-                                       ((q.inject && i == 0) ? 16u : 0u);
+                const uint32_t per_grp = (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
+                                         (uint32_t)(1 + nw) * (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
+                                         (has_aux ? (uint32_t)R * (uint32_t)q.auxbytes : 0u);
+                const uint32_t bytes = dbytes16 + (uint32_t)ngrp * per_grp + ((q.inject && i == 0) ? 16u : 0u);
                 mbar_arrive_expect_tx(bar, bytes);
                 bulk_copy(smem_u32(st + q.off_desc), q.desc + (size_t)tile * q.desc_stride, dbytes16, bar);
-                // the window may start above row 0 or end below row n: those rows are zero-filled
-                tma_load_rows(smem_u32(st), &tm_win, r0 - TMA_HALO, bar);
-                if (has_aux) tma_load_rows(smem_u32(st + q.off_aux), &tm_aux, r0, bar);
+                if constexpr (!sweep_mode(MODE)) {
+                    // the window may start above row 0 or end below row n: those rows are zero-filled
+                    tma_load_rows(smem_u32(st), &tm_win, r0 - TMA_HALO, bar);
+                    if (has_aux) tma_load_rows(smem_u32(st + q.off_aux), &tm_aux, r0, bar);
+                }
             }
             const int* gcs = reinterpret_cast<const int*>(ring + gslot * q.gcol_stride);
-            // extra windows (runs of far columns) in the first gather slots, then the gathers
-            if (lane < nw) tma_load_rows(smem_u32(st + q.off_gat + lane * q.wslots * q.slot), &tm_win, gcs[lane], bar);
             const int gs0 = nw * q.wslots;
-            for (int gi = lane; gi < ngr; gi += 32) {
-                const int4 c4 = *reinterpret_cast<const int4*>(gcs + TMA_MAX_WIN + 4 * gi);
-                tma_gather4(smem_u32(st + q.off_gat + (gs0 + gi) * q.slot), &tm_gather, c4.x, c4.y, c4.z, c4.w, bar);
+            if constexpr (sweep_mode(MODE)) {
+                // (a window's halo rows past a group's ends hold the neighbouring group's rows, or
+                // zeros past the stack: no record refers to them)
+                for (int gi = lane; gi < ngrp; gi += 32) {
+                    tma_load_rows(smem_u32(st + gi * q.gsz), &tm_win, gi * n + r0 - TMA_HALO, bar);
+                    if (has_aux) tma_load_rows(smem_u32(st + gi * q.gsz + q.off_aux), &tm_aux, gi * n + r0, bar);
+                }
+                for (int x = lane; x < nw * ngrp; x += 32) {
+                    const int gi = x / nw, w = x - gi * nw;
+                    tma_load_rows(smem_u32(st + gi * q.gsz + q.off_gat + w * q.wslots * q.slot), &tm_win, gi * n + gcs[w], bar);
+                }
+                for (int x = lane; x < ngr * ngrp; x += 32) {
+                    const int gi = x / ngr, q4 = x - gi * ngr;
+                    const int4 c4 = *reinterpret_cast<const int4*>(gcs + TMA_MAX_WIN + 4 * q4);
+                    const int o = gi * n;
+                    tma_gather4(smem_u32(st + gi * q.gsz + q.off_gat + (gs0 + q4) * q.slot), &tm_gather, o + c4.x, o + c4.y,
+                                o + c4.z, o + c4.w, bar);
+                }
+            } else {
+                // extra windows (runs of far columns) in the first gather slots, then the gathers
+                if (lane < nw) tma_load_rows(smem_u32(st + q.off_gat + lane * q.wslots * q.slot), &tm_win, gcs[lane], bar);
+                for (int gi = lane; gi < ngr; gi += 32) {
+                    const int4 c4 = *reinterpret_cast<const int4*>(gcs + TMA_MAX_WIN + 4 * gi);
+                    tma_gather4(smem_u32(st + q.off_gat + (gs0 + gi) * q.slot), &tm_gather, c4.x, c4.y, c4.z, c4.w, bar);
+                }
             }
             __syncwarp();   // the ring slot is read before the next copy into it
             ++issued;
@@ -219,16 +244,24 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
         PP* __restrict__ pblk = static_cast<PP*>(p.p);
         const int* __restrict__ colind = p.colind;
         const int cp0 = cp * NP;   // the thread's first column pair
-        const StepScalars<PREC> S0(p, cp0, stop_mode(MODE) && MB == MODE_ACCUM);
-        const StepScalars<PREC> S1(p, cp0 + NP - 1, stop_mode(MODE) && MB == MODE_ACCUM);
-        const unsigned cpoff = (unsigned)(cp0 * sizeof(WP));
+        // a sweep takes the scalars and the record values of the thread's column group (the NP
+        // pairs of a thread lie in one group)
+        const int grp = sweep_mode(MODE) ? cp0 / p.sw_gpairs : 0;
+        const int cpg = cp0 - grp * (sweep_mode(MODE) ? p.sw_gpairs : 0);   // first pair within the group
+        const size_t grow = (size_t)grp * (size_t)n;                        // the group's first row in the stacks
+        const StepScalars<PREC> S0 = sweep_mode(MODE) ? StepScalars<PREC>::group(p, grp)
+                                                      : StepScalars<PREC>(p, cp0, stop_mode(MODE) && MB == MODE_ACCUM);
+        const StepScalars<PREC> S1 = sweep_mode(MODE) ? S0 : StepScalars<PREC>(p, cp0 + NP - 1, stop_mode(MODE) && MB == MODE_ACCUM);
+        const Raw* __restrict__ gvals = vals + (sweep_mode(MODE) ? (size_t)grp * (size_t)p.sw_vstride : 0);
+        const unsigned goff = sweep_mode(MODE) ? (unsigned)grp * (unsigned)q.gsz : 0u;   // the group's part of a stage
+        const unsigned cpoff = (unsigned)(cpg * sizeof(WP)) + goff;
         const unsigned own_off = (unsigned)(rlane + TMA_HALO) * (unsigned)q.rowbytes + cpoff;
         const unsigned aux_off = (unsigned)q.off_aux + (unsigned)rlane * (unsigned)q.auxbytes +
-                                 (unsigned)(cp0 * (MB == MODE_ACCUM ? sizeof(PP) : sizeof(WP)));
+                                 (unsigned)(cpg * (MB == MODE_ACCUM ? sizeof(PP) : sizeof(WP))) + goff;
         int s = 0, ph = 0;
         int r = (int)blockIdx.x * R + rlane;
-        WP* wo = wout + (size_t)r * ldq + cp0;   // this thread's W_{j+1} and P pairs, advanced per tile
-        PP* po_ptr = pblk + (size_t)r * ldpq + cp0;
+        WP* wo = wout + (grow + (size_t)r) * ldq + cpg;   // this thread's W_{j+1} and P pairs, advanced per tile
+        PP* po_ptr = pblk + (grow + (size_t)r) * ldpq + cpg;
         const size_t wstep = (size_t)rstep * ldq, pstep = (size_t)rstep * ldpq;
         for (int i = 0; i < my; ++i) {
             // every lane waits (acquiring the stage's copies); the warp gives up together
@@ -241,7 +274,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
             const unsigned char* st = smem + s * q.stage_bytes;
             if (active && r < n) {
                 const int* srp = reinterpret_cast<const int*>(st + q.off_desc);
-                const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_desc + q.hdr_bytes);
+                const unsigned char* recb = st + q.off_desc + q.hdr_bytes;
+                const RecT* rec = reinterpret_cast<const RecT*>(recb);
                 const int k0 = srp[rlane], k1 = srp[rlane + 1];
                 const int g = srp[R + 2];
                 WP wr[NP], vr[NP] = {};
@@ -257,14 +291,28 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 RowAcc A[NP];
                 const int kend = min(k1, g);
                 const unsigned char* stc = st + cpoff;
+                if constexpr (sweep_mode(MODE)) {
+                    // multi-value records: the operand offset, then one value per active group
+                    const unsigned char* rv = recb + sweep_rec_head(PREC) + grp * (int)sizeof(Raw);
 #pragma unroll 4
-                for (int k = k0; k < kend; ++k) {
-                    const RecT rk = rec[k];
-                    const auto ex = expand(rk.a);
-                    WP x[NP];
-                    ld_pairs<NP>(x, stc + rk.off);
+                    for (int k = k0; k < kend; ++k) {
+                        const int off = *reinterpret_cast<const int*>(recb + k * q.recbytes);
+                        const auto ex = expand(*reinterpret_cast<const Raw*>(rv + k * q.recbytes));
+                        WP x[NP];
+                        ld_pairs<NP>(x, stc + off);
 #pragma unroll
-                    for (int qq = 0; qq < NP; ++qq) row_mac<PREC>(A[qq], ex, x[qq]);
+                        for (int qq = 0; qq < NP; ++qq) row_mac<PREC>(A[qq], ex, x[qq]);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = k0; k < kend; ++k) {
+                        const RecT rk = rec[k];
+                        const auto ex = expand(rk.a);
+                        WP x[NP];
+                        ld_pairs<NP>(x, stc + rk.off);
+#pragma unroll
+                        for (int qq = 0; qq < NP; ++qq) row_mac<PREC>(A[qq], ex, x[qq]);
+                    }
                 }
                 if (k1 > g) {   // beyond the records: direct loads, eight in flight, added in entry order
                     const int z0 = srp[R + 1];
@@ -274,8 +322,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                         Raw v[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
-                            v[u] = vals[z0 + k + u];
-                            ld_pairs<NP>(x[u], win + (size_t)colind[z0 + k + u] * ldq + cp0);
+                            v[u] = gvals[z0 + k + u];
+                            ld_pairs<NP>(x[u], win + (grow + (size_t)colind[z0 + k + u]) * ldq + cpg);
                         }
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
@@ -286,8 +334,8 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                     }
                     for (; k < k1; ++k) {
                         WP x[NP];
-                        ld_pairs<NP>(x, win + (size_t)colind[z0 + k] * ldq + cp0);
-                        const auto ex = expand(vals[z0 + k]);
+                        ld_pairs<NP>(x, win + (grow + (size_t)colind[z0 + k]) * ldq + cpg);
+                        const auto ex = expand(gvals[z0 + k]);
 #pragma unroll
                         for (int qq = 0; qq < NP; ++qq) row_mac<PREC>(A[qq], ex, x[qq]);
                     }
@@ -353,7 +401,16 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     // two column pairs per thread: FP32-mixed only, with rows of whole 16-byte units (the P rows
     // of pass 1 are 16 bytes per pair, so any width qualifies there)
     if (np != 1 && np != 2) return false;
-    if (np == 2 && (precision != LL_PREC_F32_MIXED || p.ldw % 4 != 0)) return false;
+    // (the sweep modes also in DF64 and F64, whose blocks of several groups would leave few rows
+    // per tile)
+    if (np == 2 && precision == LL_PREC_F32_MIXED && p.ldw % 4 != 0) return false;
+    if (np == 2 && precision != LL_PREC_F32_MIXED && !sweep_mode(mode)) return false;
+    // a sweep's blocks are stacks of ngrp groups of n rows of one group width (ldw = 2 sw_gpairs),
+    // b the columns of the groups together
+    const int ngrp = sweep_mode(mode) ? (p.sw_gpairs > 0 ? (b / 2) / p.sw_gpairs : 0) : 1;
+    if (sweep_mode(mode) && (p.sw_gpairs < 1 || b % 2 != 0 || (b / 2) % p.sw_gpairs != 0 || p.sw_gpairs % np != 0 ||
+                             p.ldw != 2 * p.sw_gpairs || (long long)ngrp * n >= (1LL << 31)))
+        return false;
     L.np = np;
     if (ctas_per_sm < 1 || ctas_per_sm > 2) ctas_per_sm = 1;
     const int ew = (int)elem_size(w_type_of(precision));
@@ -361,10 +418,10 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     if (ld > 256 || (ld * ew) % 16 != 0) return false;
     int auxbytes = 0;
     if (base_mode(mode) == MODE_DOT || mode == MODE_ADJ) {
-        if (p.ldv != ld) return false;
+        if (p.ldv != p.ldw) return false;
         auxbytes = (int)(ld * ew);
     } else if (base_mode(mode) == MODE_ACCUM) {
-        if (p.ldp > 256 || (p.ldp * 8) % 16 != 0) return false;
+        if (p.ldp > 256 || (p.ldp * 8) % 16 != 0 || (sweep_mode(mode) && p.ldp != p.ldw)) return false;
         auxbytes = (int)(p.ldp * 8);
     }
     if (threads_target <= 0 || threads_target > 512) threads_target = 512 / ctas_per_sm;
@@ -378,7 +435,10 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     q.rowbytes = (int)(ld * ew);
     q.auxbytes = auxbytes;
     q.slot = (int)a128((size_t)4 * q.rowbytes);
-    q.recbytes = (int)rec_size(precision);
+    // sweep records: the offset (padded to the value size), then the values of the b / (2 sw_gpairs)
+    // groups
+    q.recbytes = sweep_mode(mode) ? sweep_rec_head(precision) + ((b / 2) / p.sw_gpairs) * raw_size(precision)
+                                  : (int)rec_size(precision);
     const double avg = (double)nnz / (double)n;
     const double avgfar = nfar >= 0 && nfar <= nnz ? (double)nfar / (double)n : avg;
     // tile capacity slack over the mean: more for irregular row lengths (power-law graphs), where
@@ -394,6 +454,15 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     // layout for R rows per tile; returns the stage count that fits
     auto layout = [&](int Rt) {
         tma_stage_layout(q, Rt, avg, avgfar, slack);
+        // a sweep's stage: one group part (window, V or P rows, gathered rows) per group, then the
+        // shared descriptor
+        q.ngrp = ngrp;
+        q.gsz = 0;
+        if (sweep_mode(mode)) {
+            q.gsz = (int)a128((size_t)q.off_desc);
+            q.off_desc = ngrp * q.gsz;
+            q.stage_bytes = (int)a128((size_t)q.off_desc + (size_t)q.desc_stride);
+        }
         const size_t ring_total = (size_t)np_cap * TMA_GRING * q.gcol_stride;
         const int nst = budget > ring_total ? (int)((budget - ring_total) / q.stage_bytes) : 0;
         q.nst = nst > TMA_MAX_STAGES ? TMA_MAX_STAGES : nst;
@@ -430,8 +499,11 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     switch ((np - 1) * 3 * NUM_MODES + precision * NUM_MODES + mode) {
 #define OCC(N_, P_, M_) case (N_ - 1) * 3 * NUM_MODES + P_ * NUM_MODES + M_: per_sm = occupancy_tma<P_, M_, N_>(L.threads, L.smem); break;
 #define OCC4(N_, P_) OCC(N_, P_, MODE_PLAIN) OCC(N_, P_, MODE_ACCUM) OCC(N_, P_, MODE_DOT) OCC(N_, P_, MODE_ADJ) \
-    OCC(N_, P_, MODE_ACCUM_STOP) OCC(N_, P_, MODE_DOT_STOP)
+    OCC(N_, P_, MODE_ACCUM_STOP) OCC(N_, P_, MODE_DOT_STOP) OCC(N_, P_, MODE_ACCUM_SWEEP) OCC(N_, P_, MODE_DOT_SWEEP)
+#define OCCSW(N_, P_) OCC(N_, P_, MODE_ACCUM_SWEEP) OCC(N_, P_, MODE_DOT_SWEEP)
         OCC4(1, LL_PREC_F64) OCC4(1, LL_PREC_DF64) OCC4(1, LL_PREC_F32_MIXED) OCC4(2, LL_PREC_F32_MIXED)
+        OCCSW(2, LL_PREC_F64) OCCSW(2, LL_PREC_DF64)
+#undef OCCSW
 #undef OCC4
 #undef OCC
         default: break;
@@ -449,18 +521,23 @@ cudaError_t launch_tma_describe(int precision, const TmaLaunch& L, const StepPar
     int grid = (p.num_tiles + warps_per_cta - 1) / warps_per_cta;
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) return cudaSuccess;
+    // a sweep's records carry the values of its b / (2 sw_gpairs) groups
+    const int ngv = p.sw_gpairs > 0 ? (p.b / 2) / p.sw_gpairs : 0;
     switch (precision) {
         case LL_PREC_F64:
             k_tma_describe<LL_PREC_F64><<<grid, 32 * warps_per_cta, 0, s>>>(p.rowptr, p.colind, static_cast<const double*>(p.vals),
-                                                                        p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w);
+                                                                        p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w,
+                                                                        ngv, p.sw_vstride);
             break;
         case LL_PREC_DF64:
             k_tma_describe<LL_PREC_DF64><<<grid, 32 * warps_per_cta, 0, s>>>(p.rowptr, p.colind, static_cast<const float2*>(p.vals),
-                                                                         p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w);
+                                                                         p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w,
+                                                                         ngv, p.sw_vstride);
             break;
         default:
             k_tma_describe<LL_PREC_F32_MIXED><<<grid, 32 * warps_per_cta, 0, s>>>(p.rowptr, p.colind, static_cast<const float*>(p.vals),
-                                                                              p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w);
+                                                                              p.n, p.num_tiles, L.q, L.q.desc_w, L.q.gcol_w, L.q.meta_w,
+                                                                              ngv, p.sw_vstride);
             break;
     }
     return cudaGetLastError();
@@ -469,19 +546,24 @@ cudaError_t launch_tma_describe(int precision, const TmaLaunch& L, const StepPar
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s) {
     if (p.num_tiles <= 0) return cudaSuccess;
     const int ew = (int)elem_size(w_type_of(precision));
+    // rows of the maps: a sweep's blocks stack its groups (group g's row r is row g n + r)
+    const int rows = (sweep_mode(mode) ? L.q.ngrp : 1) * p.n;
     CUtensorMap g{}, w{}, a{};
-    if (!encode_rows(&g, p.win, ew, p.ldw, p.n, 1) || !encode_rows(&w, p.win, ew, p.ldw, p.n, L.q.R + 2 * TMA_HALO))
+    if (!encode_rows(&g, p.win, ew, p.ldw, rows, 1) || !encode_rows(&w, p.win, ew, p.ldw, rows, L.q.R + 2 * TMA_HALO))
         return cudaErrorInvalidValue;
     bool aux_ok = true;
-    if (base_mode(mode) == MODE_DOT || mode == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, p.n, L.q.R);
-    else if (base_mode(mode) == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, p.n, L.q.R);
+    if (base_mode(mode) == MODE_DOT || mode == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, rows, L.q.R);
+    else if (base_mode(mode) == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, rows, L.q.R);
     else a = w;
     if (!aux_ok) return cudaErrorInvalidValue;
     switch ((L.np - 1) * 3 * NUM_MODES + precision * NUM_MODES + mode) {
 #define LCH(N_, P_, M_) case (N_ - 1) * 3 * NUM_MODES + P_ * NUM_MODES + M_: return launch_tma_typed<P_, M_, N_>(L, g, w, a, p, s);
 #define LCH4(N_, P_) LCH(N_, P_, MODE_PLAIN) LCH(N_, P_, MODE_ACCUM) LCH(N_, P_, MODE_DOT) LCH(N_, P_, MODE_ADJ) \
-    LCH(N_, P_, MODE_ACCUM_STOP) LCH(N_, P_, MODE_DOT_STOP)
+    LCH(N_, P_, MODE_ACCUM_STOP) LCH(N_, P_, MODE_DOT_STOP) LCH(N_, P_, MODE_ACCUM_SWEEP) LCH(N_, P_, MODE_DOT_SWEEP)
+#define LCHSW(N_, P_) LCH(N_, P_, MODE_ACCUM_SWEEP) LCH(N_, P_, MODE_DOT_SWEEP)
         LCH4(1, LL_PREC_F64) LCH4(1, LL_PREC_DF64) LCH4(1, LL_PREC_F32_MIXED) LCH4(2, LL_PREC_F32_MIXED)
+        LCHSW(2, LL_PREC_F64) LCHSW(2, LL_PREC_DF64)
+#undef LCHSW
 #undef LCH4
 #undef LCH
         default: return cudaErrorInvalidValue;

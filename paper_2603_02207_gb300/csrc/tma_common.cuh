@@ -107,9 +107,14 @@ template <> struct __align__(8) Rec<LL_PREC_F32_MIXED> { float a; int off; };
 // windows occupy the first wslots gather slots each; the other far columns take the next gather
 // slot in entry order. When the gather slots run out (or after ecap entries) the records stop, and
 // that entry and every later entry of the tile load directly.
+// ngv > 0 (a sweep over ngv matrices of one pattern): a record is the operand offset (padded to
+// the value size, sweep_rec_head bytes), then the values of the ngv matrices, vals[v * vstride + e]
+// for v < ngv (q.recbytes bytes per record).
 template <int PREC>
 __global__ void k_tma_describe(const int32_t* rowptr, const int32_t* colind, const typename PairT<PREC>::Raw* vals, int n,
-                               int num_tiles, const TmaParams q, unsigned char* desc, int* gcol, int4* meta) {
+                               int num_tiles, const TmaParams q, unsigned char* desc, int* gcol, int4* meta, int ngv = 0,
+                               long long vstride = 0) {
+    using Raw = typename PairT<PREC>::Raw;
     using RecT = Rec<PREC>;
     constexpr int NCAND = 8;
     const int lane = threadIdx.x & 31;
@@ -195,17 +200,26 @@ __global__ void k_tma_describe(const int32_t* rowptr, const int32_t* colind, con
             const unsigned over = __ballot_sync(0xffffffffu, gath && fs >= gcap);
             if (over) gcut = e0 + __ffs(over) - 1;   // first entry without a gather slot
             if (valid && e < gcut) {
-                RecT rr;
-                rr.a = vals[z0 + e];
+                int off;
                 if (near) {
-                    rr.off = (c - wlo) * q.rowbytes;
+                    off = (c - wlo) * q.rowbytes;
                 } else if (woff >= 0) {
-                    rr.off = woff;
+                    off = woff;
                 } else {
-                    rr.off = gbase + (fs >> 2) * q.slot + (fs & 3) * q.rowbytes;
+                    off = gbase + (fs >> 2) * q.slot + (fs & 3) * q.rowbytes;
                     gc[TMA_MAX_WIN + fs] = c;
                 }
-                rec[e] = rr;
+                if (ngv == 0) {
+                    RecT rr;
+                    rr.a = vals[z0 + e];
+                    rr.off = off;
+                    rec[e] = rr;
+                } else {
+                    unsigned char* rb = reinterpret_cast<unsigned char*>(rec) + (size_t)e * q.recbytes;
+                    *reinterpret_cast<int*>(rb) = off;
+                    Raw* rv = reinterpret_cast<Raw*>(rb + sizeof(Raw));
+                    for (int v = 0; v < ngv; ++v) rv[v] = vals[(size_t)v * (size_t)vstride + z0 + e];
+                }
             }
             nfar += __popc(farm);
         }
@@ -244,13 +258,16 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D map over the rows of an n x ld block of `elem` bytes per element; a box is `box_rows` whole rows
-inline bool encode_rows(CUtensorMap* m, const void* base, int elem, long long ld, int n, int box_rows) {
+// 2-D map over the rows of an n x ld block of `elem` bytes per element; a box is `box_rows` rows of
+// the first box_cols columns (0: whole rows)
+inline bool encode_rows(CUtensorMap* m, const void* base, int elem, long long ld, int n, int box_rows, long long box_cols = 0) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn || !base || ((uintptr_t)base & 15) != 0) return false;
+    if (box_cols <= 0) box_cols = ld;
+    if (box_cols > ld || (box_cols * elem) % 16 != 0) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)elem};
-    const cuuint32_t box[2] = {(cuuint32_t)ld, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     const cuuint32_t es[2] = {1, 1};
     return fn(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dims,
               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -259,6 +276,11 @@ inline bool encode_rows(CUtensorMap* m, const void* base, int elem, long long ld
 
 inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 inline size_t a128(size_t x) { return (x + 127) & ~(size_t)127; }
+
+// bytes of one prepared matrix value
+__host__ __device__ constexpr int raw_size(int precision) { return precision == LL_PREC_F32_MIXED ? 4 : 8; }
+// bytes of a sweep record's head (the operand offset, padded to the alignment of the values)
+__host__ __device__ constexpr int sweep_rec_head(int precision) { return raw_size(precision); }
 
 inline size_t rec_size(int precision) {
     return precision == LL_PREC_F64 ? sizeof(Rec<LL_PREC_F64>) : (precision == LL_PREC_DF64 ? sizeof(Rec<LL_PREC_DF64>) : sizeof(Rec<LL_PREC_F32_MIXED>));
