@@ -383,10 +383,11 @@ ll_status qr_project(ll_handle* h, int prec, int n, int kq, int kg, const QrBloc
     else LL_CK(launch_apply_rinv(tq, B.q1, B.lq1, n, kq, B.rinv, B.basis, l2, T_F64, nullptr, l2, q));
     if ((st = run_gram(h, tq, Qb, l2, kq, B.G, kg, kg, n, false, B.gpart, B.gticket, B.gram, B.ggrid, q)) != LL_OK)
         return st;
-    // G' into columns [kq, kq + kg); the pad column of an odd width is zeroed by the same kernel.
+    // G' into columns [kq, kq + kg); the pad columns up to the leading dimension are zeroed by the
+    // same kernel.
     // The typed block pointer is offset by kq elements: element index r * l2 + kq + c.
     LL_CK(launch_project(tq, Qb, l2, kq, B.G, kg, kg, B.gram, n, dfq ? nullptr : B.basis + kq, l2, T_DF64,
-                         dfq ? Qb : nullptr, l2, (b2 & 1), kq, q));
+                         dfq ? Qb : nullptr, l2, (int)(l2 - b2), kq, q));
     h->launches += 8;
     if (dfq && !qv) {
         LL_CK(launch_dfp_to_f32(B.basis, l2, static_cast<float*>(B.V), l2, n, b2, B.vpad, q));
@@ -2231,7 +2232,7 @@ ll_status batched_run(ll_handle* h, const ll_csr* mats, const ll_bounds* bnd, in
             LL_CK(launch_chol_jobs(kq, c0, cjobs, count, q));
             LL_CK(launch_apply_rinv_jobs(T_F64, kq, kq, l2, wt, l2, r0, rjobs + count, count, n_max, q));
             LL_CK(launch_gram_jobs(T_F64, l2, kq, T_F64, kg, kg, false, g0, gjobs + 2 * count, count, gxc_max, q));
-            LL_CK(launch_project_jobs(l2, kq, kg, kg, l2, wt, l2, (b2 & 1), kq, r0, rjobs + 2 * count, count, n_max, q));
+            LL_CK(launch_project_jobs(l2, kq, kg, kg, l2, wt, l2, l2 - b2, kq, r0, rjobs + 2 * count, count, n_max, q));
             h->launches += 8;
         }
         LL_CK(rec(h->ev[3], q));

@@ -272,8 +272,8 @@ cudaError_t launch_apply_rinv(int tx, const void* X, long long ldx, int n, int k
                               double* out64, long long ld64, int t2, void* out2, long long ld2, cudaStream_t s);
 // G' = G - Q C in double-float arithmetic, G: FP64 (ldg), Q: type tq (T_F64 or T_DF64 column
 // pairs, ldq), C k x kg; writes FP64 (out64, columns [0, kg); may be null) and optionally out2
-// (type t2, columns [col2, col2 + kg)); zero_pad: also write 0 to the column after the last one
-// (the pad column of a pair layout)
+// (type t2, columns [col2, col2 + kg)); zero_pad: also write 0 to the zero_pad columns after the
+// last one (the pad columns of a pair layout)
 cudaError_t launch_project(int tq, const void* Q, long long ldq, int k, const double* G, long long ldg, int kg,
                            const double* C, int n, double* out64, long long ld64, int t2, void* out2,
                            long long ld2, int zero_pad, int col2, cudaStream_t s);
@@ -367,7 +367,10 @@ enum ElemType { T_F64 = 0, T_F32 = 1, T_DF64 = 2 };
 // even leading dimension of a block of b columns
 inline int even_ld(int b) { return b + (b & 1); }
 // leading dimension of an n x b block in the W storage of `precision`: column pairs (even), and
-// for FP32 a multiple of 4 so that a row is a whole number of 16-byte units (the TMA row stride)
+// for FP32 a multiple of 4 so that a row is a whole number of 16-byte units (the TMA row stride).
+// (Padding DF64 blocks to 4 columns as well, so that every width could take two column pairs per
+// thread, cost 6% more bytes in pass 1 and the autotuner kept one pair: measured on the 128^3
+// Laplacian, pass 1 30.7 -> 32.4 ms.)
 inline int block_ld(int precision, int b) { return precision == LL_PREC_F32_MIXED ? (b + 3) & ~3 : b + (b & 1); }
 inline int w_type_of(int precision) {
     return precision == LL_PREC_F64 ? T_F64 : (precision == LL_PREC_DF64 ? T_DF64 : T_F32);

@@ -453,21 +453,28 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
         __syncthreads();
         const int row = tile * RG + rr;
         if (!act || row >= n) continue;
-        if (zero_pad && cg == 0) {
-            if (out64) out64[(size_t)row * ld64 + kc] = 0.0;
-            if (out2) store_f64<T2>(out2, (size_t)row * ld2 + col2 + kc, 0.0);
+        if (zero_pad > 0 && cg == 0) {
+            for (int z = 0; z < zero_pad; ++z) {
+                if (out64) out64[(size_t)row * ld64 + kc + z] = 0.0;
+                if (out2) store_f64<T2>(out2, (size_t)row * ld2 + col2 + kc + z, 0.0);
+            }
         }
-        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        // the four columns as two f32x2 pairs: df2_mac runs df_mac's operations on both lanes
+        f2x h01 = 0ull, l01 = 0ull, h23 = 0ull, l23 = 0ull;
         const int amax = (MODE == 0) ? min(kx, cg * 4 + 4) : kx;
         for (int a = 0; a < amax; ++a) {
             const float x_h = xh[rr * kxp + a], x_l = xl[rr * kxp + a];
-            const float4 m4h = *reinterpret_cast<const float4*>(&mh[(size_t)a * kcp + cg * 4]);
-            const float4 m4l = *reinterpret_cast<const float4*>(&ml[(size_t)a * kcp + cg * 4]);
-            df_mac(h[0], l[0], x_h, x_l, m4h.x, m4l.x);
-            df_mac(h[1], l[1], x_h, x_l, m4h.y, m4l.y);
-            df_mac(h[2], l[2], x_h, x_l, m4h.z, m4l.z);
-            df_mac(h[3], l[3], x_h, x_l, m4h.w, m4l.w);
+            const f2x ah2 = f2_pack(x_h, x_h), al2 = f2_pack(x_l, x_l), nah2 = f2_pack(-x_h, -x_h);
+            const ulonglong2 m4h = *reinterpret_cast<const ulonglong2*>(&mh[(size_t)a * kcp + cg * 4]);
+            const ulonglong2 m4l = *reinterpret_cast<const ulonglong2*>(&ml[(size_t)a * kcp + cg * 4]);
+            df2_mac(h01, l01, ah2, al2, nah2, m4h.x, m4l.x);
+            df2_mac(h23, l23, ah2, al2, nah2, m4h.y, m4l.y);
         }
+        float h[4], l[4];
+        f2_unpack(h01, h[0], h[1]);
+        f2_unpack(h23, h[2], h[3]);
+        f2_unpack(l01, l[0], l[1]);
+        f2_unpack(l23, l[2], l[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = cg * 4 + j;

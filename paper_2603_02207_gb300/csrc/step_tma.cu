@@ -398,13 +398,15 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
                    int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count, int np) {
     L = TmaLaunch{};
     if (n <= 0 || b <= 0 || !encode_fn()) return false;
-    // two column pairs per thread: FP32-mixed only, with rows of whole 16-byte units (the P rows
-    // of pass 1 are 16 bytes per pair, so any width qualifies there)
+    // two column pairs per thread: the block's pairs must come in twos (ldw a multiple of 4), since a
+    // thread reads and writes both of its pairs (the last thread's second pair would otherwise lie
+    // past the row: in the last row, past the block). FP32-mixed (one 16-byte access for both
+    // pairs) and DF64 (two pairs share each entry record and give two independent double-float
+    // chains); F64 only in the sweep modes, whose blocks of several groups would leave few rows per
+    // tile.
     if (np != 1 && np != 2) return false;
-    // (the sweep modes also in DF64 and F64, whose blocks of several groups would leave few rows
-    // per tile)
-    if (np == 2 && precision == LL_PREC_F32_MIXED && p.ldw % 4 != 0) return false;
-    if (np == 2 && precision != LL_PREC_F32_MIXED && !sweep_mode(mode)) return false;
+    if (np == 2 && (p.ldw % 4 != 0 || (base_mode(mode) == MODE_ACCUM && p.ldp % 4 != 0))) return false;
+    if (np == 2 && precision == LL_PREC_F64 && !sweep_mode(mode)) return false;
     // a sweep's blocks are stacks of ngrp groups of n rows of one group width (ldw = 2 sw_gpairs),
     // b the columns of the groups together
     const int ngrp = sweep_mode(mode) ? (p.sw_gpairs > 0 ? (b / 2) / p.sw_gpairs : 0) : 1;
@@ -502,7 +504,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     OCC(N_, P_, MODE_ACCUM_STOP) OCC(N_, P_, MODE_DOT_STOP) OCC(N_, P_, MODE_ACCUM_SWEEP) OCC(N_, P_, MODE_DOT_SWEEP)
 #define OCCSW(N_, P_) OCC(N_, P_, MODE_ACCUM_SWEEP) OCC(N_, P_, MODE_DOT_SWEEP)
         OCC4(1, LL_PREC_F64) OCC4(1, LL_PREC_DF64) OCC4(1, LL_PREC_F32_MIXED) OCC4(2, LL_PREC_F32_MIXED)
-        OCCSW(2, LL_PREC_F64) OCCSW(2, LL_PREC_DF64)
+        OCC4(2, LL_PREC_DF64) OCCSW(2, LL_PREC_F64)
 #undef OCCSW
 #undef OCC4
 #undef OCC
@@ -562,7 +564,7 @@ cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const S
     LCH(N_, P_, MODE_ACCUM_STOP) LCH(N_, P_, MODE_DOT_STOP) LCH(N_, P_, MODE_ACCUM_SWEEP) LCH(N_, P_, MODE_DOT_SWEEP)
 #define LCHSW(N_, P_) LCH(N_, P_, MODE_ACCUM_SWEEP) LCH(N_, P_, MODE_DOT_SWEEP)
         LCH4(1, LL_PREC_F64) LCH4(1, LL_PREC_DF64) LCH4(1, LL_PREC_F32_MIXED) LCH4(2, LL_PREC_F32_MIXED)
-        LCHSW(2, LL_PREC_F64) LCHSW(2, LL_PREC_DF64)
+        LCH4(2, LL_PREC_DF64) LCHSW(2, LL_PREC_F64)
 #undef LCHSW
 #undef LCH4
 #undef LCH

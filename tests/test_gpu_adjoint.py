@@ -271,7 +271,7 @@ def test_backward_from_forward_written_checkpoints(L, h, prec):
     lmin = max(lo, 0.05)
     m, probes = 17, 21
     dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
-    l2 = 16 if prec == "f32" else 14                      # [Q | G'] block: 14 columns
+    l2 = 16 if prec == "f32" else 14                      # [Q | G'] block: 14 columns (FP32: 16)
     blk = A.n * l2 * (4 if prec == "f32" else 8)
     out = {}
     try:
