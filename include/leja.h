@@ -81,7 +81,10 @@ enum { LL_SVAL_CENTER = 0, LL_SVAL_HALF_LMAX = 1 };
  *                  host (a second scheme for very large condition numbers), rounded to FP64. */
 enum { LL_DD_AUTO = 0, LL_DD_TABLE_Q = 1 };
 /* Kernel of CholeskyQR2's Gram products Y^T Y, Q1^T Q1 and Q^T G (ll_options.qr_gram, ll_gram):
- *   LL_GRAM_AUTO    the tensor-core kernel when both widths are at most 42 (else LL_GRAM_DFLOAT);
+ *   LL_GRAM_AUTO    the faster of the two for the shape (element type, widths, symmetry, rows):
+ *                   both are timed on the first product of a shape on the handle and the choice
+ *                   is cached (the chosen kernel runs last, so every call of the shape gives the
+ *                   same result); LL_GRAM_DFLOAT above width 42;
  *   LL_GRAM_TENSOR  tcgen05 MMAs on BF16 digit slices: each column is written in fixed point as
  *                   seven 7-bit digits (six for widths above 36) below its scale 2^E (max |x| <
  *                   2^(E-1), from a maximum pre-pass), every slice product summed over up to 4096

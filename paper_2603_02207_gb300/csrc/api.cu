@@ -75,6 +75,8 @@ struct ll_handle {
     int64_t keep_budget = 0;  // ll_set_keep_budget: bytes the forward may keep for the backward (0: half the free memory)
     int64_t forward_id = 0;   // count of successful forwards on the handle (ll_info.forward_id)
     int gram_method = LL_GRAM_AUTO;   // CholeskyQR2 Gram kernel of the running call (ll_options.qr_gram)
+    // LL_GRAM_AUTO: the faster Gram kernel per (element type, kx, kz, sym, n), timed on first use
+    std::map<std::tuple<int, int, int, int, int>, int> gram_choice;
     int kept_gram = LL_GRAM_AUTO;     // and of the kept forward (its backward uses the same)
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
@@ -315,20 +317,50 @@ ll_status check_tma_flag(ll_handle* h, cudaStream_t s) {
 // pipes (k_gram). The tensor-core kernel's bounded waits report through the pipeline error flag.
 ll_status run_gram(ll_handle* h, int tx, const void* X, long long ldx, int kx, const double* Z, long long ldz, int kz,
                    int n, bool sym, double* partials, unsigned int* ticket, double* out, int ggrid, cudaStream_t s) {
-    const bool tc = h->gram_method != LL_GRAM_DFLOAT && gram_tc_supported(tx, kx, kz, sym) && (tx != T_DF64 || ldx % 2 == 0);
+    bool tc = h->gram_method != LL_GRAM_DFLOAT && gram_tc_supported(tx, kx, kz, sym) && (tx != T_DF64 || ldx % 2 == 0);
     if (h->gram_method == LL_GRAM_TENSOR && !tc)
         return fail(h, LL_ERR_UNSUPPORTED, "tensor-core Gram: widths up to 42 and FP64 or double-float operands");
-    if (tc) {
-        WS(err, int*, "tma_error", sizeof(int));
-        WS(work, void*, "gram_tc_work", gram_tc_workspace_bytes(kx, sym ? kx : kz, h->sm_count));
-        h->tma_used = true;
-        LL_CK(launch_gram_tc(tx, X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, work, err, h->spin_budget,
-                             h->sm_count, s));
-        h->launches += sym ? 2 : 3;
-    } else {
-        LL_CK(launch_gram(tx, X, ldx, kx, T_F64, sym ? nullptr : Z, ldz, kz, n, sym, partials, ticket, out, ggrid, s));
+    auto launch = [&](bool on_tc) -> ll_status {
+        if (on_tc) {
+            WS(err, int*, "tma_error", sizeof(int));
+            WS(work, void*, "gram_tc_work", gram_tc_workspace_bytes(kx, sym ? kx : kz, h->sm_count));
+            h->tma_used = true;
+            LL_CK(launch_gram_tc(tx, X, ldx, kx, Z, ldz, kz, n, sym, partials, ticket, out, work, err, h->spin_budget,
+                                 h->sm_count, s));
+            h->launches += sym ? 2 : 3;
+        } else {
+            LL_CK(launch_gram(tx, X, ldx, kx, T_F64, sym ? nullptr : Z, ldz, kz, n, sym, partials, ticket, out, ggrid, s));
+            h->launches++;
+        }
+        return LL_OK;
+    };
+    if (tc && h->gram_method == LL_GRAM_AUTO) {
+        // both kernels timed once per shape (not inside a stream capture, where the tensor-core
+        // kernel is taken), the faster cached; the chosen one runs last, so its result is the one
+        // every later call of the shape reproduces
+        const auto key = std::make_tuple(tx, kx, sym ? kx : kz, (int)sym, n);
+        auto it = h->gram_choice.find(key);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        LL_CK(cudaStreamIsCapturing(s, &cs));
+        if (it != h->gram_choice.end()) {
+            tc = it->second == LL_GRAM_TENSOR;
+        } else if (cs == cudaStreamCaptureStatusNone) {
+            float ms[2] = {0.f, 0.f};
+            const int counted = h->launches;   // the timing runs are not the call's launches
+            for (int v = 0; v < 2; ++v) {
+                LL_CK(cudaEventRecord(h->ev[6], s));
+                ll_status st = launch(v == 0);
+                if (st != LL_OK) return st;
+                LL_CK(cudaEventRecord(h->ev[7], s));
+                LL_CK(cudaEventSynchronize(h->ev[7]));
+                LL_CK(cudaEventElapsedTime(&ms[v], h->ev[6], h->ev[7]));
+            }
+            h->launches = counted;
+            tc = ms[0] <= ms[1];
+            h->gram_choice[key] = tc ? LL_GRAM_TENSOR : LL_GRAM_DFLOAT;
+        }
     }
-    return LL_OK;
+    return launch(tc);
 }
 
 // doubles of Gram partials for either kernel (kx x kz, grid ggrid for k_gram)
@@ -388,7 +420,7 @@ ll_status qr_project(ll_handle* h, int prec, int n, int kq, int kg, const QrBloc
     // The typed block pointer is offset by kq elements: element index r * l2 + kq + c.
     LL_CK(launch_project(tq, Qb, l2, kq, B.G, kg, kg, B.gram, n, dfq ? nullptr : B.basis + kq, l2, T_DF64,
                          dfq ? Qb : nullptr, l2, (int)(l2 - b2), kq, q));
-    h->launches += 8;
+    h->launches += 5;   // (run_gram counts its own)
     if (dfq && !qv) {
         LL_CK(launch_dfp_to_f32(B.basis, l2, static_cast<float*>(B.V), l2, n, b2, B.vpad, q));
         h->launches++;
@@ -902,7 +934,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     LL_CK(launch_project(T_F64, FV64 + kq, b2, kg, ZQa, kq, kq, C2, n, ZQ, kq, T_F64, nullptr, 0, 0, 0, s));
     if ((st = run_gram(h, T_F64, basis, l2, kq, ZQ, kq, kq, n, false, gpart, gticket, C3, ggrid, s)) != LL_OK) return st;
     LL_CK(launch_project(T_F64, basis, l2, kq, ZQ, kq, kq, C3, n, Xb, kq, T_F64, nullptr, 0, 0, 0, s));
-    h->launches += 8;
+    h->launches += 4;   // (run_gram counts its own)
     // R^-1 = R1^-1 R2^-1 (Y R1^-1 = Q1, Q1 R2^-1 = Q), and M = 2 R^-T, on the host (kq x kq)
     std::vector<double> r1((size_t)kq * kq), r2((size_t)kq * kq), mt((size_t)kq * kq, 0.0);
     LL_CK(cudaMemcpyAsync(r1.data(), rinv1, r1.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -2390,7 +2422,6 @@ ll_status ll_gram(ll_handle* h, int layout, const void* X, int64_t ldx, int kx, 
     ll_status st = run_gram(h, tx, X, ldx, kx, Z, ldz, kz, (int)n, sym, part, tick, out, ggrid, s);
     h->gram_method = LL_GRAM_AUTO;
     if (st != LL_OK) return st;
-    h->launches++;
     h->tma_used = true;
     return check_tma_flag(h, s);
 }

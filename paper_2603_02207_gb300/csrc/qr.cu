@@ -70,16 +70,19 @@ __device__ __forceinline__ void stage_tile(unsigned char* stage, const T* X, lon
         cp_async_unit<CP>(stage + (size_t)u * CP, valid ? unit_src(X, ld, row, a) : (const void*)X, valid);
     }
 }
-// Splits a staged tile into float pairs: h[r * kp + a], l[r * kp + a] (columns >= k are zero)
+// Splits a staged tile into float pairs: h[r * ks + a], l[r * ks + a] for a < kp (columns >= k
+// are zero; ks >= kp is the row stride, kp when 0)
 template <typename T>
-__device__ __forceinline__ void split_tile(const unsigned char* stage, int k, int kp, float* h, float* l, int TR) {
+__device__ __forceinline__ void split_tile(const unsigned char* stage, int k, int kp, float* h, float* l, int TR,
+                                           int ks = 0) {
     constexpr int CP = Stg<T>::cp, PER = Stg<T>::per;
+    if (ks <= 0) ks = kp;
     for (int i = threadIdx.x; i < TR * kp; i += blockDim.x) {
         const int r = i / kp, a = i - r * kp;
         float hh = 0.f, ll = 0.f;
         if (a < k) unit_split(reinterpret_cast<const T*>(stage + ((size_t)r * (kp / PER) + a / PER) * CP), a % PER, hh, ll);
-        h[i] = hh;
-        l[i] = ll;
+        h[(size_t)r * ks + a] = hh;
+        l[(size_t)r * ks + a] = ll;
     }
 }
 __device__ __forceinline__ void ld_split(const float2* p, size_t i, float& h, float& l) {
@@ -407,8 +410,20 @@ __device__ __forceinline__ void st_out2(dfp* p, size_t i, float h, float l) {
     f[2] = v.y;
 }
 
+// Thread layout: warp w takes the four columns 4 (w mod CG) .. + 3 of the 32 rows 32 (w / CG) ..
+// + 31 of each tile of TR = 32 RB rows (CG = kcp / 4 column groups, RB row blocks, 32 CG RB
+// threads): a warp's lanes share their column group, so the triangular loop of mode 0 runs
+// without divergence. The split rows have an odd stride (kxs = kxp + 1): the lanes' loads of their
+// rows' element a fall in distinct banks.
+__host__ __device__ inline int rowprod_row_blocks(int CG) { return CG >= 8 ? 1 : (8 + CG - 1) / CG; }
+constexpr int ROWPROD_MAX_THREADS = 1024;
+// bytes of the split M and row arrays (16-byte multiple: the staging buffers follow)
+__host__ __device__ inline size_t rowprod_split_bytes(int kx, int kcp, int RG, int kxs) {
+    return (((size_t)2 * kx * kcp + (size_t)2 * RG * kxs) * sizeof(float) + 15) & ~(size_t)15;
+}
+
 template <typename TX, typename T2, int MODE>
-__global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, int kc, long long ldg, long long ld64,
+__global__ void __launch_bounds__(ROWPROD_MAX_THREADS) k_rowprod(long long ldx, int kx, int kc, long long ldg, long long ld64,
                                                         long long ld2, int col2, int zero_pad, RowJob one,
                                                         const RowJob* jobs) {
     extern __shared__ __align__(16) float srp[];
@@ -419,13 +434,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
     const int n = J.n;
     double* out64 = J.out64;
     T2* out2 = static_cast<T2*>(J.out2);
-    const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
+    const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3, kxs = kxp + 1;
     const int CG = kcp / 4;
-    const int RG = QR_THREADS / CG;
+    const int RG = 32 * rowprod_row_blocks(CG);   // rows per tile
     float* mh = srp;                    // kx x kcp
     float* ml = mh + (size_t)kx * kcp;
-    float* xh = ml + (size_t)kx * kcp;  // RG x kxp
-    float* xl = xh + (size_t)RG * kxp;
+    float* xh = ml + (size_t)kx * kcp;  // RG x kxs
+    float* xl = xh + (size_t)RG * kxs;
     for (int i = threadIdx.x; i < kx * kcp; i += blockDim.x) {
         const int a = i / kcp, c = i - a * kcp;
         float hh = 0.f, ll = 0.f;
@@ -433,12 +448,14 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
         mh[i] = hh;
         ml[i] = ll;
     }
-    const int cg = threadIdx.x % CG;
-    const int rr = threadIdx.x / CG;
+    const int warp = threadIdx.x >> 5;
+    const int cg = warp % CG;
+    const int rr = (warp / CG) * 32 + (threadIdx.x & 31);
     const bool act = rr < RG;
     const int ntiles = (n + RG - 1) / RG;
-    // raw row tiles staged asynchronously one tile ahead (two buffers after the split arrays)
-    unsigned char* stg = reinterpret_cast<unsigned char*>(xl + (size_t)RG * kxp);
+    // raw row tiles staged asynchronously one tile ahead (two buffers after the split arrays,
+    // 16-byte aligned)
+    unsigned char* stg = reinterpret_cast<unsigned char*>(srp) + rowprod_split_bytes(kx, kcp, RG, kxs);
     const size_t sxb = stage_bytes<TX>(RG, kxp);
     int buf = 0;
     if ((int)blockIdx.x < ntiles) stage_tile<TX>(stg, X, ldx, kx, kxp, n, blockIdx.x, RG);
@@ -448,7 +465,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
         cp_async_commit();
         cp_async_wait<1>();   // this thread's copies of `tile`
         __syncthreads();      // ... everyone's, and every thread is done with the previous tile
-        split_tile<TX>(stg + (size_t)buf * sxb, kx, kxp, xh, xl, RG);
+        split_tile<TX>(stg + (size_t)buf * sxb, kx, kxp, xh, xl, RG, kxs);
         buf ^= 1;
         __syncthreads();
         const int row = tile * RG + rr;
@@ -463,7 +480,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
         f2x h01 = 0ull, l01 = 0ull, h23 = 0ull, l23 = 0ull;
         const int amax = (MODE == 0) ? min(kx, cg * 4 + 4) : kx;
         for (int a = 0; a < amax; ++a) {
-            const float x_h = xh[rr * kxp + a], x_l = xl[rr * kxp + a];
+            const float x_h = xh[rr * kxs + a], x_l = xl[rr * kxs + a];
             const f2x ah2 = f2_pack(x_h, x_h), al2 = f2_pack(x_l, x_l), nah2 = f2_pack(-x_h, -x_h);
             const ulonglong2 m4h = *reinterpret_cast<const ulonglong2*>(&mh[(size_t)a * kcp + cg * 4]);
             const ulonglong2 m4l = *reinterpret_cast<const ulonglong2*>(&ml[(size_t)a * kcp + cg * 4]);
@@ -501,14 +518,15 @@ __global__ void __launch_bounds__(QR_THREADS) k_rowprod(long long ldx, int kx, i
 
 template <typename TX, typename T2, int MODE>
 static cudaError_t rowprod_launch(long long ldx, int kx, int kc, long long ldg, long long ld64, long long ld2, int col2,
-                                  int zero_pad, const RowJob& one, const RowJob* jobs, dim3 gd, size_t smem, cudaStream_t s) {
+                                  int zero_pad, const RowJob& one, const RowJob* jobs, dim3 gd, int threads, size_t smem,
+                                  cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_rowprod<TX, T2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_rowprod<TX, T2, MODE><<<gd, QR_THREADS, smem, s>>>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs);
+    k_rowprod<TX, T2, MODE><<<gd, threads, smem, s>>>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs);
     return cudaGetLastError();
 }
 
@@ -517,20 +535,25 @@ template <typename TX, int MODE>
 static cudaError_t rowprod_dispatch(int t2, long long ldx, int kx, int kc, long long ldg, long long ld64, long long ld2,
                                     int col2, int zero_pad, const RowJob& one, const RowJob* jobs, int count, int n_max,
                                     cudaStream_t s) {
-    const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3;
+    const int kxp = (kx + 3) & ~3, kcp = (kc + 3) & ~3, kxs = kxp + 1;
     const int CG = kcp / 4;
-    const int RG = QR_THREADS / CG;
-    if (RG < 1 || count < 1) return cudaErrorInvalidValue;
+    const int RB = rowprod_row_blocks(CG);
+    const int RG = 32 * RB;
+    const int threads = 32 * CG * RB;
+    if (CG < 1 || threads > ROWPROD_MAX_THREADS || count < 1) return cudaErrorInvalidValue;
     int blocks = (n_max + RG - 1) / RG;
-    const int cap = 152 * 4;   // per matrix: the largest matrix of a batch sets the time; CTAs past a matrix's tiles leave
+    const int cap = 152 * 8;   // per matrix: the largest matrix of a batch sets the time; CTAs past a matrix's tiles leave
     if (blocks > cap) blocks = cap;
     if (blocks < 1) return cudaSuccess;
-    const size_t smem = ((size_t)2 * kx * kcp + (size_t)2 * RG * kxp) * sizeof(float) + 2 * stage_bytes<TX>(RG, kxp);
+    const size_t smem = rowprod_split_bytes(kx, kcp, RG, kxs) + 2 * stage_bytes<TX>(RG, kxp);
     const dim3 gd(blocks, 1, count);
     switch (t2) {
-        case T_F32: return rowprod_launch<TX, float, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, smem, s);
-        case T_DF64: return rowprod_launch<TX, dfp, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, smem, s);
-        default: return rowprod_launch<TX, double, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, smem, s);
+        case T_F32:
+            return rowprod_launch<TX, float, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, threads, smem, s);
+        case T_DF64:
+            return rowprod_launch<TX, dfp, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, threads, smem, s);
+        default:
+            return rowprod_launch<TX, double, MODE>(ldx, kx, kc, ldg, ld64, ld2, col2, zero_pad, one, jobs, gd, threads, smem, s);
     }
 }
 

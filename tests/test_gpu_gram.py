@@ -156,3 +156,18 @@ def test_gram_many_exact_batches_per_cta(L, h, layout):
     Z = np.sign(_cols(n, 20, seed=22))
     got = L.ll_gram(h, torch.as_tensor(X).cuda(), torch.as_tensor(Z).cuda(), method="tensor").cpu().numpy()
     assert np.all(np.abs(got - X.T @ Z) <= 1e-13 * _bound(X, Z))
+
+
+@pytest.mark.parametrize("k", [10, 33])
+def test_auto_gram_is_one_of_the_kernels_and_repeats(L, k):
+    """LL_GRAM_AUTO times both kernels on the first product of a shape and keeps the faster: the
+    first and later results are bit-identical, and equal to one of the two kernels' results."""
+    torch = need_gpu()
+    h2 = L.Handle()
+    X = torch.as_tensor(_cols(200_003, k, seed=k)).cuda()
+    first = L.ll_gram(h2, X, None, method="auto").cpu().numpy()
+    again = L.ll_gram(h2, X, None, method="auto").cpu().numpy()
+    assert np.array_equal(first, again)
+    tc = L.ll_gram(h2, X, None, method="tensor").cpu().numpy()
+    df = L.ll_gram(h2, X, None, method="dfloat").cpu().numpy()
+    assert np.array_equal(first, tc) or np.array_equal(first, df)
