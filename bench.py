@@ -44,11 +44,13 @@ DTYPE_NAME = {"df64": "df64 = 48-bit float-float (FP32 pairs on the FP32 pipes, 
 ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A, s_W, s_P, s_V
 
 # DRAM bytes (read + write) of one pass-2 trace-step launch per matrix row, from one ncu capture of
-# each kernel on the 96^3 Laplacian (n = 884,736): register gathers 1.4777 GB, TMA 1.5066 GB.
-# Traffic grows in proportion to the rows of a stencil matrix, so the full-size value is this figure
-# times n. Only valid for the DF64 trace step of the kernel as captured.
+# each kernel on the 96^3 Laplacian (n = 884,736): DF64 register gathers 1.4777 GB, DF64 TMA
+# 1.4960 GB, FP32-mixed TMA with two column pairs per thread 0.7577 GB. Traffic grows in proportion
+# to the rows of a stencil matrix, so the full-size value is this figure times n. Only valid for the
+# trace steps of the kernels as captured (profiles/k_leja_tma_*_96cubed.md).
 TRACE_STEP_DRAM_BYTES_PER_ROW = {("gather", "df64"): 1.477654528e9 / 884736,
-                                 ("tma", "df64"): (1.052284e9 + 0.443141376e9) / 884736}
+                                 ("tma", "df64"): (1.052321e9 + 0.4436736e9) / 884736,
+                                 ("tma", "f32"): (0.542242816e9 + 0.21548032e9) / 884736}
 
 
 def step_bytes(n: int, nnz: int, b: int, prec: str, mode: str) -> int:
@@ -686,6 +688,9 @@ def main():
                     help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
                     help="step kernel of the headline passes (auto = autotuned; the others are for profiler captures)")
+    ap.add_argument("--qr-gram", default="auto", choices=["auto", "tensor", "dfloat"],
+                    help="CholeskyQR2 Gram kernel of the headline estimate (auto = timed per shape; the others "
+                         "for profiler captures, under which the timed choice is distorted)")
     ap.add_argument("--rpt", type=int, default=0,
                     help="with --step-kernel: rows per thread (gather) or column pairs per thread (tma, 2 = FP32 "
                          "16-byte rows); for profiler captures")
@@ -727,7 +732,7 @@ def main():
     def time_precision(prec: str, steps: int, warmup: int, sampler=None):
         dA = L.DeviceCSR.from_host(A, "f32" if prec == "f32" else "f64")
         opts = L.options(degree=m, probes=PROBES, seed=SEED + rank, precision=prec, step_kernel=args.step_kernel,
-                         rows_per_thread=args.rpt)
+                         rows_per_thread=args.rpt, qr_gram=args.qr_gram)
         for _ in range(warmup):
             L.ll_logdet_forward(h, dA, *BOUNDS, opts)
         barrier()
