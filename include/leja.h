@@ -93,6 +93,20 @@ enum { LL_DD_AUTO = 0, LL_DD_TABLE_Q = 1 };
  *                   maximum; widths up to 42;
  *   LL_GRAM_DFLOAT  double-float products on the FP32 pipes (any width up to 96).            */
 enum { LL_GRAM_AUTO = 0, LL_GRAM_TENSOR = 1, LL_GRAM_DFLOAT = 2 };
+/* Row order of the forward (ll_options.reorder):
+ *   LL_REORDER_AUTO    the degree order below for irregular matrices (the longest row above four
+ *                      times the mean plus 16, most entries outside the tile windows, not banded)
+ *                      in a forward that keeps nothing for a backward; else the matrix's order;
+ *   LL_REORDER_NONE    the matrix's order;
+ *   LL_REORDER_DEGREE  the passes run on P A P^T with the rows ordered by entry count, descending
+ *                      (ties by row index): a power-law graph's hubs come first and the rows most
+ *                      entries gather stay together in L2. The probe rows keep the probe values
+ *                      of their original rows, so the estimate equals the unpermuted one up to the
+ *                      order of its sums. The permuted structure is built on the device once per
+ *                      structure (a checksum of rowptr and colind tells a changed one) and cached
+ *                      on the handle; the values are gathered through it at every call. Not with
+ *                      keep_for_backward (LL_ERR_UNSUPPORTED). */
+enum { LL_REORDER_AUTO = 0, LL_REORDER_NONE = 1, LL_REORDER_DEGREE = 2 };
 
 /* Step kernel of the m-step passes:
  *   LL_KERNEL_AUTO    banded matrices (every row's columns strictly increasing and within 2 of
@@ -162,6 +176,7 @@ typedef struct {
     int qr_gram;               /* LL_GRAM_AUTO (default), LL_GRAM_TENSOR or LL_GRAM_DFLOAT: the
                                   Gram kernel of the CholeskyQR2 of Algorithm 3 step 4 and of
                                   Q^T G in step 6 (the backward uses the kept forward's)        */
+    int reorder;               /* LL_REORDER_AUTO (default), LL_REORDER_NONE or LL_REORDER_DEGREE */
 } ll_options;
 
 typedef struct ll_handle ll_handle;
@@ -196,6 +211,7 @@ typedef struct {
     int rows_pass1, rows_pass2;         /* rows per tile of each pass's step kernel               */
     int batch_tuned;                    /* ll_logdet_batched: 1 when the autotuner chose the launch
                                            shape (step kernel, threads and rows per pass)        */
+    int reordered;                      /* 1 when the passes ran on the degree-ordered matrix    */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */

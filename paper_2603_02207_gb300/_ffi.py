@@ -24,6 +24,7 @@ LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
 LL_DD_AUTO, LL_DD_TABLE_Q = 0, 1
 LL_GRAM_AUTO, LL_GRAM_TENSOR, LL_GRAM_DFLOAT = 0, 1, 2
+LL_REORDER_AUTO, LL_REORDER_NONE, LL_REORDER_DEGREE = 0, 1, 2
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
 LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA, LL_KERNEL_BAND = 0, 1, 2, 3
 LL_EST_HUTCHPP, LL_EST_HUTCHINSON = 0, 1
@@ -46,7 +47,8 @@ class ll_options(ctypes.Structure):
                 ("keep_for_backward", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_int64), ("step_kernel", ctypes.c_int), ("estimator", ctypes.c_int),
-                ("tol", ctypes.c_double), ("dd_scheme", ctypes.c_int), ("qr_gram", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("dd_scheme", ctypes.c_int), ("qr_gram", ctypes.c_int),
+                ("reorder", ctypes.c_int)]
 
 
 class ll_info(ctypes.Structure):
@@ -60,7 +62,8 @@ class ll_info(ctypes.Structure):
                 ("kept_w_steps", ctypes.c_int), ("kept_w_steps_pass1", ctypes.c_int),
                 ("kept_w_stride", ctypes.c_int), ("forward_id", ctypes.c_int64),
                 ("pairs_pass1", ctypes.c_int), ("pairs_pass2", ctypes.c_int),
-                ("rows_pass1", ctypes.c_int), ("rows_pass2", ctypes.c_int), ("batch_tuned", ctypes.c_int)]
+                ("rows_pass1", ctypes.c_int), ("rows_pass2", ctypes.c_int), ("batch_tuned", ctypes.c_int),
+                ("reordered", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -127,6 +127,7 @@ def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
 
 DD_SCHEMES = {"auto": _ffi.LL_DD_AUTO, "table_q": _ffi.LL_DD_TABLE_Q}
 GRAM_METHODS = {"auto": _ffi.LL_GRAM_AUTO, "tensor": _ffi.LL_GRAM_TENSOR, "dfloat": _ffi.LL_GRAM_DFLOAT}
+REORDERS = {"auto": _ffi.LL_REORDER_AUTO, "none": _ffi.LL_REORDER_NONE, "degree": _ffi.LL_REORDER_DEGREE}
 
 
 def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str = "rademacher",
@@ -134,7 +135,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
             rows_per_thread: int = 0, threads_per_block: int = 0, ckpt_stride: int = 0,
             use_graph: bool = True, timeout_cycles: int = 0, step_kernel: str = "auto",
             estimator: str = "hutchpp", tol: float = 0.0, dd_scheme: str = "auto",
-            qr_gram: str = "auto") -> _ffi.ll_options:
+            qr_gram: str = "auto", reorder: str = "auto") -> _ffi.ll_options:
     o = _ffi.ll_options()
     _ffi.load().ll_default_options(ctypes.byref(o))
     o.degree = degree
@@ -154,6 +155,7 @@ def options(degree: int = 40, probes: int = 30, seed: int = 0, probe_kind: str =
     o.tol = tol
     o.dd_scheme = DD_SCHEMES[dd_scheme]
     o.qr_gram = GRAM_METHODS[qr_gram]
+    o.reorder = REORDERS[reorder]
     return o
 
 

@@ -21,6 +21,7 @@ namespace {
 struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
+    uint64_t gen = 0;   // the handle's ws_gen when the block was allocated
 };
 
 }  // namespace
@@ -75,6 +76,15 @@ struct ll_handle {
     int64_t keep_budget = 0;  // ll_set_keep_budget: bytes the forward may keep for the backward (0: half the free memory)
     int64_t forward_id = 0;   // count of successful forwards on the handle (ll_info.forward_id)
     int gram_method = LL_GRAM_AUTO;   // CholeskyQR2 Gram kernel of the running call (ll_options.qr_gram)
+    // the structure last reordered (LL_REORDER_DEGREE) and the allocation generations of the
+    // workspace blocks that hold its permuted copy
+    struct Reorder {
+        const void* rp = nullptr;
+        const void* ci = nullptr;
+        int64_t n = -1, nnz = -1;
+        unsigned long long hash = 0;
+        uint64_t gens = 0;
+    } ro;
     // LL_GRAM_AUTO: the faster Gram kernel per (element type, kx, kz, sym, n), timed on first use
     std::map<std::tuple<int, int, int, int, int>, int> gram_choice;
     int kept_gram = LL_GRAM_AUTO;     // and of the kept forward (its backward uses the same)
@@ -124,7 +134,7 @@ void* ws_get(ll_handle* h, const char* name, size_t bytes, cudaError_t* err) {
     b.p = nullptr;
     b.bytes = 0;
     cudaError_t e = cudaMalloc(&b.p, bytes);
-    h->ws_gen++;
+    b.gen = ++h->ws_gen;
     if (e != cudaSuccess) {
         cudaGetLastError();
         *err = e;
@@ -366,6 +376,47 @@ ll_status run_gram(ll_handle* h, int tx, const void* X, long long ldx, int kx, c
 // doubles of Gram partials for either kernel (kx x kz, grid ggrid for k_gram)
 size_t gram_partials_any(const ll_handle* h, int kx, int kz, bool sym, int ggrid) {
     return std::max(gram_partials_doubles(kx, kz, sym, ggrid), gram_tc_partials_doubles(kx, kz, h->sm_count));
+}
+
+// The degree-ordered copy P A P^T of A for the passes (LL_REORDER_DEGREE): built on the device
+// when A's structure differs from the cached one (pointers, sizes and a checksum of rowptr and
+// colind) or a block holding it was reallocated; Aw then describes it (A's values, gathered
+// through *src by the value preparation), *perm maps its rows to A's (the probes' row map), and
+// the handle's matrix statistics are the permuted matrix's.
+ll_status prepare_reorder(ll_handle* h, const ll_csr* A, ll_csr& Aw, const int32_t** perm_out, const int32_t** src_out,
+                          cudaStream_t s) {
+    const int n = (int)A->n;
+    WS(perm, int32_t*, "ro_perm", (size_t)n * sizeof(int32_t));
+    WS(inv, int32_t*, "ro_inv", (size_t)n * sizeof(int32_t));
+    WS(rp2, int32_t*, "ro_rowptr", (size_t)(n + 1) * sizeof(int32_t));
+    WS(ci2, int32_t*, "ro_colind", (size_t)A->nnz * sizeof(int32_t));
+    WS(src, int32_t*, "ro_src", (size_t)A->nnz * sizeof(int32_t));
+    WS(work, void*, "ro_work", reorder_work_bytes(n));
+    WS(hash, unsigned long long*, "ro_hash", sizeof(unsigned long long));
+    uint64_t gens = 0;
+    for (const char* nm : {"ro_perm", "ro_inv", "ro_rowptr", "ro_colind", "ro_src"}) gens = gens * 1000003u + h->ws[nm].gen;
+    LL_CK(launch_structure_hash(A->rowptr, A->colind, n, A->nnz, hash, s));
+    h->launches++;
+    unsigned long long hv = 0;
+    LL_CK(cudaMemcpyAsync(&hv, hash, sizeof hv, cudaMemcpyDeviceToHost, s));
+    LL_CK(cudaStreamSynchronize(s));
+    ll_handle::Reorder& R = h->ro;
+    if (!(R.rp == A->rowptr && R.ci == A->colind && R.n == A->n && R.nnz == A->nnz && R.hash == hv && R.gens == gens)) {
+        LL_CK(launch_reorder(A->rowptr, A->colind, n, perm, inv, rp2, ci2, src, work, s));
+        h->launches += 8;
+        R.rp = A->rowptr;
+        R.ci = A->colind;
+        R.n = A->n;
+        R.nnz = A->nnz;
+        R.hash = hv;
+        R.gens = gens;
+    }
+    Aw = *A;
+    Aw.rowptr = rp2;
+    Aw.colind = ci2;
+    *perm_out = perm;
+    *src_out = src;
+    return validate_csr(h, &Aw, s);
 }
 
 // The blocks of Algorithm 3 steps 4 and 6 for one sketch (leading dimensions in columns; typed
@@ -1263,10 +1314,11 @@ ll_status ll_apply_poly_tol(ll_handle* h, const ll_csr* A, ll_bounds bounds, int
     return check_tma_flag(h, s);
 }
 
-ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, const ll_options* opts, double* estimate,
+ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A0, ll_bounds bounds, const ll_options* opts, double* estimate,
                             void* stream) {
+    const ll_csr* A = A0;   // the matrix the passes run on: A0, or its degree-ordered copy
     if (!h || !opts || !estimate) return LL_ERR_INVALID_ARG;
-    ll_status st = check_csr_args(h, A);
+    ll_status st = check_csr_args(h, A0);
     if (st != LL_OK) return st;
     if ((st = check_bounds(h, bounds)) != LL_OK) return st;
     const ll_options& o = *opts;
@@ -1281,6 +1333,9 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     if (o.dd_scheme != LL_DD_AUTO && o.dd_scheme != LL_DD_TABLE_Q) return fail(h, LL_ERR_INVALID_ARG, "unknown divided-difference scheme");
     if (!std::isfinite(o.tol) || o.tol < 0.0) return fail(h, LL_ERR_INVALID_ARG, "tol must be finite and >= 0");
     if (o.qr_gram < LL_GRAM_AUTO || o.qr_gram > LL_GRAM_DFLOAT) return fail(h, LL_ERR_INVALID_ARG, "unknown Gram method");
+    if (o.reorder < LL_REORDER_AUTO || o.reorder > LL_REORDER_DEGREE) return fail(h, LL_ERR_INVALID_ARG, "unknown row order");
+    if (o.reorder == LL_REORDER_DEGREE && o.keep_for_backward)
+        return fail(h, LL_ERR_UNSUPPORTED, "the degree order is for forwards that keep nothing for a backward");
     h->gram_method = o.qr_gram;
     const bool adaptive = o.tol > 0.0;   // Algorithm 2's stopping rule in both passes
     if (adaptive && o.keep_for_backward)
@@ -1300,7 +1355,20 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     const int b2 = kq + kg;
     if (hutch && kg > 192) return fail(h, LL_ERR_UNSUPPORTED, "more than 192 Hutchinson probes are not supported");
     if (b2 > 512 || kq > 96) return fail(h, LL_ERR_UNSUPPORTED, "m_vec / 3 above 96 is not supported");
-    if ((st = validate_csr(h, A, s)) != LL_OK) return st;
+    if ((st = validate_csr(h, A0, s)) != LL_OK) return st;
+    // the degree order for irregular matrices (power-law graphs: hubs first, their rows together in L2)
+    ll_csr Aw{};
+    const int32_t* rowmap = nullptr;   // probe row map of the permuted passes
+    const int32_t* vsrc = nullptr;     // value gather map of the permuted passes
+    {
+        const double avg = (double)A0->nnz / (double)n;
+        const bool irregular = !h->band_ok && (double)h->max_row > 4.0 * avg + 16.0 && 2 * h->far_entries > A0->nnz;
+        const bool reorder = o.reorder == LL_REORDER_DEGREE || (o.reorder == LL_REORDER_AUTO && !o.keep_for_backward && irregular);
+        if (reorder) {
+            if ((st = prepare_reorder(h, A0, Aw, &rowmap, &vsrc, s)) != LL_OK) return st;
+            A = &Aw;
+        }
+    }
 
     // host set-up: sigma, the scaled interval, Léja points, Algorithm 1 coefficients
     const double sigma = sigma_of(bounds.lmin);
@@ -1438,19 +1506,19 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         LL_CK(cudaMemsetAsync(gticket, 0, sizeof(unsigned int), q));
         LL_CK(cudaMemsetAsync(qrstat, 0, sizeof(int), q));
         // matrix values scaled by 1 / (sigma gamma): B = (A/sigma - c I)/gamma = prepared - (c/gamma) I
-        LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, q));
+        LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, q, vsrc));
         if (hutch) {
             // plain Hutchinson (Eq. Léja8): G straight into the trace pass's block (the pad
             // column zeroed); no pass 1 and no QR
-            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_G, n, kg, l2, V, l2, q));
+            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_G, n, kg, l2, V, l2, q, rowmap));
             h->launches += 2;
             LL_CK(rec(h->ev[1], q));
             LL_CK(rec(h->ev[2], q));
             LL_CK(rec(h->ev[3], q));
         } else {
             // Algorithm 3 step 2 (S) and step 6 (G)
-            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, l1, S, l1, q));
-            LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, q));
+            LL_CK(launch_probes(wt, o.probe_kind, o.seed, LL_STREAM_S, n, kq, l1, S, l1, q, rowmap));
+            LL_CK(launch_probes(T_F64, o.probe_kind, o.seed, LL_STREAM_G, n, kg, kg, G, kg, q, rowmap));
             h->launches += 3;
             LL_CK(rec(h->ev[1], q));
         }
@@ -1518,16 +1586,18 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
         ll_options o;
         uint64_t ws_gen;
         int inject;
+        int reordered;
     };
     Key key;
     memset(&key, 0, sizeof key);
-    key.rp = A->rowptr; key.ci = A->colind; key.va = A->values;
+    key.rp = A0->rowptr; key.ci = A0->colind; key.va = A0->values;
     key.n = A->n; key.nnz = A->nnz; key.dtype = A->dtype;
     key.lmin = bounds.lmin; key.lmax = bounds.lmax;
     key.o = o;
     key.o.keep_for_backward = (wall ? 1 + wstride * 4 : 0) + (wall_s ? 2 : 0);   // the passes write into the backward's blocks
     key.ws_gen = h->ws_gen;
     key.inject = h->inject;
+    key.reordered = A != A0;
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
     ll_handle::Graph& gr = h->gfwd;
     const bool hit = o.use_graph && gr.exec && gr.key.size() == sizeof key && memcmp(gr.key.data(), kb, sizeof key) == 0;
@@ -1670,6 +1740,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A, ll_bounds bounds, con
     I.rows_pass1 = rw1;
     I.rows_pass2 = h->last_rows;
     I.batch_tuned = 0;
+    I.reordered = A != A0;
     I.deg_max_pass1 = 0;
     for (int v : deg1) I.deg_max_pass1 = v > I.deg_max_pass1 ? v : I.deg_max_pass1;
     I.deg_max_pass2 = 0;

@@ -89,9 +89,21 @@ StepLaunch plan_step(int precision, int mode, int n, int64_t nnz, int b, int thr
 cudaError_t launch_step(int precision, int mode, const StepLaunch& L, const StepParams& p, cudaStream_t s);
 
 // probes into columns [0, cols) of an n x ld block of element type out_type; columns
-// [cols, pad) are set to zero (pad = cols for none)
+// [cols, pad) are set to zero (pad = cols for none). rowmap (optional, device, n entries): row i of
+// the block holds the probe values of row rowmap[i] (a reordered matrix keeps its rows' probes)
 cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols, int pad,
-                          void* out, long long ld, cudaStream_t s);
+                          void* out, long long ld, cudaStream_t s, const int32_t* rowmap = nullptr);
+
+// Locality reordering (reorder.cu): perm[i] = the old row of new row i, rows by entry count,
+// descending (ties by row index; counts from 1023 on share one bucket), inv its inverse; the
+// matrix P A P^T as rowptr_new (n + 1), colind_new (nnz; columns relabelled by inv, in the old
+// row's order) and src (nnz; the old entry of each new entry). work: reorder_work_bytes(n).
+size_t reorder_work_bytes(int n);
+cudaError_t launch_reorder(const int32_t* rowptr, const int32_t* colind, int n, int32_t* perm, int32_t* inv,
+                           int32_t* rowptr_new, int32_t* colind_new, int32_t* src, void* work, cudaStream_t s);
+// *out = an order-independent 64-bit checksum of (rowptr, colind)
+cudaError_t launch_structure_hash(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz,
+                                  unsigned long long* out, cudaStream_t s);
 // rows of halo on each side of a TMA step tile's window (entries with |col - row| <= TMA_HALO are
 // always served from the window)
 constexpr int TMA_HALO = 2;
@@ -107,9 +119,9 @@ cudaError_t launch_check_symmetric(const int32_t* rowptr, const int32_t* colind,
                                    int sorted, int* flag, cudaStream_t s);
 cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype,
                               int n, double* partials, unsigned int* ticket, double* out, int grid, cudaStream_t s);
-// out[e] = convert(values[e] * scale) into the storage type of `precision`
+// out[e] = convert(values[src ? src[e] : e] * scale) into the storage type of `precision`
 cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, double scale, int precision,
-                                  void* out, cudaStream_t s);
+                                  void* out, cudaStream_t s, const int32_t* src = nullptr);
 // out[e] = convert((theta * o_e + [c_e == r_e] D_{r_e}) * scale) into the storage type of `precision`
 // (one matrix of a pencil sweep diag(D) + theta O, prepared as launch_prepare_values would prepare
 // it assembled in FP64); flag[0] |= 1 where D_r != 0 and row r stores no single diagonal entry

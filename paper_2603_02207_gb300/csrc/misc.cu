@@ -22,7 +22,8 @@ __device__ __forceinline__ void store_sign(dfp* p, size_t i, float v) {
 // pad) of the CTA's share. Wide blocks: a CTA takes one row at a time, its threads striding over
 // the columns. 32-bit index arithmetic per element.
 template <typename T>
-__global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols, int pad, T* out, long long ld) {
+__global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols, int pad, T* out, long long ld,
+                         const int32_t* rowmap) {
     const int nt = (int)blockDim.x;
     const bool narrow = pad <= nt;
     const int rpb = narrow ? nt / pad : 1;                 // rows per CTA pass
@@ -31,14 +32,15 @@ __global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols
     const int cstep = narrow ? pad : nt;
     if (roff >= rpb) return;
     for (int row = blockIdx.x * rpb + roff; row < n; row += gridDim.x * rpb) {
+        const uint32_t prow = (uint32_t)(rowmap ? rowmap[row] : row);   // the row whose probe values these are
         for (int col = col0; col < pad; col += cstep) {
             const size_t idx = (size_t)row * ld + col;
             if (kind == LL_PROBE_RADEMACHER) {
-                const float v = col < cols ? ((probe_bits(seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row) >> 63) ? -1.f : 1.f)
+                const float v = col < cols ? ((probe_bits(seed, (uint32_t)stream_id, (uint32_t)col, prow) >> 63) ? -1.f : 1.f)
                                            : 0.f;
                 store_sign(out, idx, v);
             } else {
-                const double v = col < cols ? probe_value(kind, seed, (uint32_t)stream_id, (uint32_t)col, (uint32_t)row) : 0.0;
+                const double v = col < cols ? probe_value(kind, seed, (uint32_t)stream_id, (uint32_t)col, prow) : 0.0;
                 store_f64<T>(out, idx, v);
             }
         }
@@ -46,7 +48,7 @@ __global__ void k_probes(int kind, uint64_t seed, int stream_id, int n, int cols
 }
 
 cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, int n, int cols, int pad,
-                          void* out, long long ld, cudaStream_t s) {
+                          void* out, long long ld, cudaStream_t s, const int32_t* rowmap) {
     if (pad < cols) pad = cols;
     const long long total = (long long)n * pad;
     if (total <= 0) return cudaSuccess;
@@ -55,9 +57,9 @@ cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, 
     long long blocks = ((long long)n + rpb - 1) / rpb;
     if (blocks > 152 * 16) blocks = 152 * 16;
     switch (out_type) {
-        case T_F64: k_probes<double><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (double*)out, ld); break;
-        case T_F32: k_probes<float><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (float*)out, ld); break;
-        default: k_probes<dfp><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (dfp*)out, ld); break;
+        case T_F64: k_probes<double><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (double*)out, ld, rowmap); break;
+        case T_F32: k_probes<float><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (float*)out, ld, rowmap); break;
+        default: k_probes<dfp><<<(int)blocks, threads, 0, s>>>(kind, seed, stream_id, n, cols, pad, (dfp*)out, ld, rowmap); break;
     }
     return cudaGetLastError();
 }
@@ -194,24 +196,24 @@ cudaError_t launch_gershgorin(const int32_t* rowptr, const int32_t* colind, cons
 
 // ------------------------------------------------------------------------ value preparation
 template <typename TI, typename TO>
-__global__ void k_prepare(const TI* in, int64_t nnz, double scale, TO* out) {
+__global__ void k_prepare(const TI* in, int64_t nnz, double scale, TO* out, const int32_t* src) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
-        store_f64<TO>(out, (size_t)e, (double)in[e] * scale);
+        store_f64<TO>(out, (size_t)e, (double)in[src ? (int64_t)src[e] : e] * scale);
 }
 
 cudaError_t launch_prepare_values(const void* vals, int dtype, int64_t nnz, double scale, int precision,
-                                  void* out, cudaStream_t s) {
+                                  void* out, cudaStream_t s, const int32_t* src) {
     if (nnz <= 0) return cudaSuccess;
     const int grid = 152 * 8, threads = 256;
     const int t = w_type_of(precision);
     if (dtype == LL_F64) {
-        if (t == T_F64) k_prepare<double, double><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (double*)out);
-        else if (t == T_F32) k_prepare<double, float><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (float*)out);
-        else k_prepare<double, float2><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (float2*)out);
+        if (t == T_F64) k_prepare<double, double><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (double*)out, src);
+        else if (t == T_F32) k_prepare<double, float><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (float*)out, src);
+        else k_prepare<double, float2><<<grid, threads, 0, s>>>((const double*)vals, nnz, scale, (float2*)out, src);
     } else {
-        if (t == T_F64) k_prepare<float, double><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (double*)out);
-        else if (t == T_F32) k_prepare<float, float><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float*)out);
-        else k_prepare<float, float2><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float2*)out);
+        if (t == T_F64) k_prepare<float, double><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (double*)out, src);
+        else if (t == T_F32) k_prepare<float, float><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float*)out, src);
+        else k_prepare<float, float2><<<grid, threads, 0, s>>>((const float*)vals, nnz, scale, (float2*)out, src);
     }
     return cudaGetLastError();
 }
