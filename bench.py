@@ -432,7 +432,7 @@ def workload_config4(L, h, count: int = 64):
     return {"workload": f"{count} x (L2D + tau_i I), sides log-uniform [64,512], tau U[0.01,1], seed 2, 30 probes", **out}
 
 
-def workload_config5(L, h, log2n: int = 22, degree: int = 150, probes: int = 120):
+def workload_config5(L, h, log2n: int = 22, degree: int = 150, probes: int = 120, reorder: str = "auto"):
     """Weighted graph Laplacian + 1e-2 I of a power-law (Chung-Lu) graph, n = 2^22, mean degree 16,
     exponent 2.3, weights U[0.5, 1.5], seed 3. Bounds from Gershgorin plus 20 power iterations
     (lmax = min(Gershgorin, 1.05 x Rayleigh quotient), lmin = 0.01); degree 150, Hutch++ 120
@@ -452,7 +452,7 @@ def workload_config5(L, h, log2n: int = 22, degree: int = 150, probes: int = 120
     out = {"n": n, "nnz": nnz, "max_row_nnz": int((A.rowptr[1:] - A.rowptr[:-1]).max()), "generate_s": t_gen,
            "gershgorin": [glo, ghi], "lambda_power": lp, "bounds": [lmin, lmax]}
     for prec, dA, reps in (("f32", d32, 2), ("f64", d64, 1)):
-        opts = L.options(degree=degree, probes=probes, seed=3, precision=prec)
+        opts = L.options(degree=degree, probes=probes, seed=3, precision=prec, reorder=reorder)
         ms, est = time_calls(lambda: L.ll_logdet_forward(h, dA, lmin, lmax, opts), reps, 1)
         inf = h.info()
         b2 = step_bytes(n, nnz, 2 * k, prec, "dot")
@@ -460,7 +460,7 @@ def workload_config5(L, h, log2n: int = 22, degree: int = 150, probes: int = 120
         out[prec] = {"ms_per_estimate": ms, "estimate": est, "GBps_estimate": estimate_bytes(n, nnz, k, degree, prec) / (ms / 1e3) / 1e9,
                      "pass1_launch_GBps": b1 / (inf["ms_pass1"] / degree / 1e3) / 1e9,
                      "pass2_launch_GBps": b2 / (inf["ms_pass2"] / degree / 1e3) / 1e9,
-                     "kernels": [inf["kernel_pass1"], inf["kernel_pass2"]],
+                     "kernels": [inf["kernel_pass1"], inf["kernel_pass2"]], "reordered": inf["reordered"],
                      "phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
     out["rel_diff_f32_vs_f64"] = abs(out["f32"]["estimate"] - out["f64"]["estimate"]) / abs(out["f64"]["estimate"])
     out["workload"] = (f"power-law Laplacian + 1e-2 I, n=2^{log2n} ({n}), nnz={nnz}, mean degree 16, exponent 2.3, "
@@ -684,6 +684,8 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID_N, help="side of the 3-D grid (128 = the benchmark workload; "
                     "smaller sides are for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--c5-reorder", default="auto", choices=["auto", "none", "degree"],
+                    help="row order of the config-5 forwards (auto = degree order for this power-law graph)")
     ap.add_argument("--c5-log2n", type=int, default=22,
                     help="log2 of the config-5 graph size (22 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "gather", "tma"],
@@ -845,7 +847,7 @@ def main():
             continue
         fn = {"c1": workload_config1, "c3": workload_config3, "c3t": workload_c3_time_to_tol, "c4": workload_config4,
               "c5": workload_config5, "f3": workload_f3, "f4": workload_f4}[w]
-        extra[w] = fn(L, h, log2n=args.c5_log2n) if w == "c5" else fn(L, h)
+        extra[w] = fn(L, h, log2n=args.c5_log2n, reorder=args.c5_reorder) if w == "c5" else fn(L, h)
     c3t = extra.pop("c3t", None)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(A, prec)
     info = r["info"]
