@@ -463,6 +463,12 @@ def workload_config5(L, h, log2n: int = 22, degree: int = 150, probes: int = 120
                      "kernels": [inf["kernel_pass1"], inf["kernel_pass2"]], "reordered": inf["reordered"],
                      "phase_ms": {"pass1": inf["ms_pass1"], "qr": inf["ms_qr"], "pass2": inf["ms_pass2"]}}
     out["rel_diff_f32_vs_f64"] = abs(out["f32"]["estimate"] - out["f64"]["estimate"]) / abs(out["f64"]["estimate"])
+    if log2n == 22:
+        # DRAM bytes of one FP32 trace-step launch (k_leja_tma<f32,DOT>, width 80) from ncu at this
+        # size (profiles/k_leja_tma_f32_powerlaw_config5.md), beside the algorithmic bytes
+        out["trace_step_dram_bytes"] = {"algorithmic": step_bytes(n, nnz, 2 * k, "f32", "dot"),
+                                        "ncu_degree_order": 23.8397e9 + 1.3285e9,
+                                        "ncu_matrix_order": 27.0815e9 + 1.3390e9}
     out["workload"] = (f"power-law Laplacian + 1e-2 I, n=2^{log2n} ({n}), nnz={nnz}, mean degree 16, exponent 2.3, "
                        f"seed 3, degree {degree}, {probes} probes")
     return out
