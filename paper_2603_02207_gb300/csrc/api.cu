@@ -85,6 +85,9 @@ struct ll_handle {
         unsigned long long hash = 0;
         uint64_t gens = 0;
     } ro;
+    // L2 bytes for the hub rows of a degree-ordered matrix's passes (set by the forward that runs
+    // on one; 0 otherwise)
+    long long hub_bytes = 0;
     // LL_GRAM_AUTO: the faster Gram kernel per (element type, kx, kz, sym, n), timed on first use
     std::map<std::tuple<int, int, int, int, int>, int> gram_choice;
     int kept_gram = LL_GRAM_AUTO;     // and of the kept forward (its backward uses the same)
@@ -646,6 +649,7 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
     p.ldv = ldw;
     p.ldp = ldp;
     p.p = P;
+    p.hub_bytes = h->hub_bytes;
     const bool adaptive = stop.tol > 0.0;
     if (mode == MODE_DOT || adaptive) {
         WS(ticket, unsigned int*, "dot_ticket", sizeof(unsigned int));
@@ -1369,6 +1373,12 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A0, ll_bounds bounds, co
             A = &Aw;
         }
     }
+    // the gathered hub rows of the degree order kept in L2 (about half of it), for this call's passes
+    struct HubScope {
+        ll_handle* h;
+        ~HubScope() { h->hub_bytes = 0; }
+    } hub_scope{h};
+    h->hub_bytes = A != A0 ? (long long)64 << 20 : 0;
 
     // host set-up: sigma, the scaled interval, Léja points, Algorithm 1 coefficients
     const double sigma = sigma_of(bounds.lmin);

@@ -74,6 +74,8 @@ struct StepParams {
     const float2* sw_scal_df;
     int sw_gpairs;
     long long sw_vstride;
+    long long hub_bytes;         // TMA step: L2 bytes for the rows of the first (hub) rows of W_j
+                                 // gathered with an evict-last policy (0: none)
 };
 
 struct StepLaunch {
@@ -338,6 +340,8 @@ struct TmaParams {
     int gcol_stride;   // bytes per tile of the gather-column array (4 window rows, then fcap columns)
     int stage_bytes;   // bytes per stage: window, aux rows, gathered rows, descriptor
     int off_aux, off_gat, off_desc;   // the window is at offset 0
+    int hub_rows;      // gathered rows below this index (a degree-ordered matrix's hubs) are kept in
+                       // L2 in preference to the others (0: no cache policy)
     int ngrp, gsz;     // a sweep's groups per tile and bytes of one group's part of a stage (its
                        // window, V or P rows and gathered rows at offsets off_aux, off_gat from
                        // g gsz; the shared descriptor at off_desc); 1, 0 otherwise

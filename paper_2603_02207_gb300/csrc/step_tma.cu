@@ -19,6 +19,8 @@
 // are read directly from global memory. Every wait on an mbarrier is bounded (clock64 budget);
 // when one runs out the kernel records the error, stops issuing copies, waits (bounded) for the
 // copies it issued and returns.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "step_common.cuh"
@@ -116,6 +118,10 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
         int zb = 0;
         int4 mcur = meta_of(lane), mnext = meta_of(32 + lane);
         int cslot = 0;   // ring slot of the next gather-column block to stage
+        // L2 policies of the gathered rows: a degree-ordered matrix's hub rows (the first
+        // hub_rows) kept, the others given up first
+        const uint64_t pol_hub = q.hub_rows > 0 ? l2_policy_evict_last() : 0ull;
+        const uint64_t pol_rest = q.hub_rows > 0 ? l2_policy_evict_first() : 0ull;
         // stage the gather columns of this producer's tile t (t increasing by one per call)
         auto stage_gcol = [&](int t) {
             if (t >= zb + 32) {
@@ -208,7 +214,13 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 if (lane < nw) tma_load_rows(smem_u32(st + q.off_gat + lane * q.wslots * q.slot), &tm_win, gcs[lane], bar);
                 for (int gi = lane; gi < ngr; gi += 32) {
                     const int4 c4 = *reinterpret_cast<const int4*>(gcs + TMA_MAX_WIN + 4 * gi);
-                    tma_gather4(smem_u32(st + q.off_gat + (gs0 + gi) * q.slot), &tm_gather, c4.x, c4.y, c4.z, c4.w, bar);
+                    const uint32_t dst = smem_u32(st + q.off_gat + (gs0 + gi) * q.slot);
+                    if (q.hub_rows > 0) {
+                        const int cmin = min(min(c4.x, c4.y), min(c4.z, c4.w));
+                        tma_gather4_hint(dst, &tm_gather, c4.x, c4.y, c4.z, c4.w, bar, cmin < q.hub_rows ? pol_hub : pol_rest);
+                    } else {
+                        tma_gather4(dst, &tm_gather, c4.x, c4.y, c4.z, c4.w, bar);
+                    }
                 }
             }
             __syncwarp();   // the ring slot is read before the next copy into it
@@ -436,6 +448,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     TmaParams& q = L.q;
     q.rowbytes = (int)(ld * ew);
     q.auxbytes = auxbytes;
+    q.hub_rows = p.hub_bytes > 0 && !sweep_mode(mode) ? (int)std::min<long long>(n, p.hub_bytes / q.rowbytes) : 0;
     q.slot = (int)a128((size_t)4 * q.rowbytes);
     // sweep records: the offset (padded to the value size), then the values of the b / (2 sw_gpairs)
     // groups
