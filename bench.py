@@ -580,6 +580,9 @@ def workload_f4(L, h, N: int = 5000, thetas=(-0.24, -0.23, -0.22, -0.21, -0.20),
     import torch
     from synth import gmrf_theta
     from tests.pins import dlogdet_gmrf_theta, logdet_gmrf_theta
+    # the earlier workloads' blocks (kept W_j above all) leave the GMRF's blocks too little memory
+    h.trim()
+    torch.cuda.empty_cache()
     t0 = _t.perf_counter()
     A = gmrf_theta(N, 1.0)
     t_gen = _t.perf_counter() - t0

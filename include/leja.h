@@ -236,6 +236,12 @@ ll_status ll_set_step_config(ll_handle* h, int step_kernel, int threads_per_bloc
  * leave memory to other work, and lets tests reach the checkpointed layout on small matrices.
  * LL_ERR_INVALID_ARG for a negative value. */
 ll_status ll_set_keep_budget(ll_handle* h, int64_t bytes);
+/* Free the handle's device workspace: every block the calls allocated (probe and W blocks, the
+ * kept W_j, tile descriptors, the cached degree order) and the captured CUDA graphs, so that other
+ * work can use the memory. The kept forward state is dropped (ll_logdet_backward then returns
+ * LL_ERR_NO_FORWARD); the autotuners' choices stay. The next call allocates afresh. Synchronises
+ * the device. */
+ll_status ll_trim_workspace(ll_handle* h);
 
 /* Test hook for failure detection. LL_INJECT_STALL: from now on, the TMA step kernel launched by
  * this handle expects 16 bytes for its first tile that no copy delivers, so that tile's pipeline

@@ -82,6 +82,7 @@ SIGNATURES = {
     "ll_default_options": (None, [ctypes.POINTER(ll_options)]),
     "ll_set_step_config": (_I, [_P, _I, _I, _I]),
     "ll_set_keep_budget": (_I, [_P, _I64]),
+    "ll_trim_workspace": (_I, [_P]),
     "ll_debug_inject": (_I, [_P, _I]),
     "ll_leja_points": (_I, [_I, _PD]),
     "ll_divided_differences": (_I, [ll_bounds, _I, _I, _PD, ctypes.POINTER(_I)]),

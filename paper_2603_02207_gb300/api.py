@@ -74,6 +74,10 @@ class Handle:
         """Device memory the forward may keep for the backward (0 = half the free memory)."""
         self.check(self._lib.ll_set_keep_budget(self.ptr, int(nbytes)))
 
+    def trim(self):
+        """Free the handle's device workspace (the kept forward state with it)."""
+        self.check(self._lib.ll_trim_workspace(self.ptr))
+
     def debug_inject(self, what: str = "none"):
         """Test hook: "stall" makes the TMA step kernel's first-tile waits run out (LL_ERR_TIMEOUT)."""
         self.check(self._lib.ll_debug_inject(self.ptr, {"none": _ffi.LL_INJECT_NONE, "stall": _ffi.LL_INJECT_STALL}[what]))

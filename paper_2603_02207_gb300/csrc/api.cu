@@ -1111,6 +1111,26 @@ ll_status ll_set_keep_budget(ll_handle* h, int64_t bytes) {
     return LL_OK;
 }
 
+ll_status ll_trim_workspace(ll_handle* h) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(h, LL_ERR_CUDA, std::string("cudaDeviceSynchronize: ") + cudaGetErrorString(e));
+    for (auto& kv : h->ws)
+        if (kv.second.p) cudaFree(kv.second.p);
+    h->ws.clear();
+    h->ws_gen++;
+    if (h->gfwd.exec) cudaGraphExecDestroy(h->gfwd.exec);
+    h->gfwd.exec = nullptr;
+    h->gfwd.key.clear();
+    if (h->gbat.exec) cudaGraphExecDestroy(h->gbat.exec);
+    h->gbat.exec = nullptr;
+    h->gbat.key.clear();
+    h->ro = ll_handle::Reorder{};
+    h->kept = false;
+    h->have_forward = false;
+    return LL_OK;
+}
+
 ll_status ll_set_step_config(ll_handle* h, int step_kernel, int threads_per_block, int rows_per_thread) {
     if (!h || step_kernel < LL_KERNEL_AUTO || step_kernel > LL_KERNEL_BAND || threads_per_block < 0 || rows_per_thread < 0)
         return LL_ERR_INVALID_ARG;

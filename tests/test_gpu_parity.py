@@ -299,3 +299,25 @@ def test_forward_host_path_matches_device_path(L, h):
     e_dev = L.ll_logdet_forward(h, L.DeviceCSR.from_host(A), 0.1, 8.1, opts)
     e_host = L.ll_logdet_forward_host(h, A, 0.1, 8.1, opts)
     assert e_dev == e_host
+
+
+def test_trim_workspace_frees_memory_and_the_next_call_reallocates(L):
+    """ll_trim_workspace frees the handle's blocks (the device's free memory grows back), drops the
+    kept forward (the backward refuses), and the next forward gives the same estimate."""
+    torch = need_gpu()
+    from synth import laplacian_3d
+    A = laplacian_3d(64, 0.05)
+    dA = L.DeviceCSR.from_host(A)
+    h = L.Handle()
+    o = L.options(degree=20, probes=30, seed=3, keep_for_backward=True, step_kernel="tma", qr_gram="dfloat")
+    e1 = L.ll_logdet_forward(h, dA, 0.05, 12.05, o)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    h.trim()
+    free_after = torch.cuda.mem_get_info()[0]
+    assert free_after > free_before + (64 << 20)
+    with pytest.raises(L.LejaError) as ei:
+        L.ll_logdet_backward(h, dA, 1.0)
+    assert ei.value.name == "LL_ERR_NO_FORWARD"
+    e2 = L.ll_logdet_forward(h, dA, 0.05, 12.05, o)
+    assert e1 == e2
