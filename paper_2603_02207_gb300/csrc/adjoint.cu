@@ -13,6 +13,45 @@ __global__ void k_row_index(const int32_t* rowptr, int n, int32_t* rowidx) {
         for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) rowidx[e] = i;
 }
 
+// tmap[e] = the index of entry (c, r) for every stored entry e = (r, c) of a pattern whose rows hold
+// strictly increasing columns (binary search in row c); flag[0] |= 1 where (c, r) is not stored
+__global__ void k_transpose_map(const int32_t* rowptr, const int32_t* colind, int n, int32_t* tmap, int* flag) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+            const int c = colind[e];
+            int lo = rowptr[c], hi = rowptr[c + 1];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (colind[mid] < r) lo = mid + 1; else hi = mid;
+            }
+            if (lo < rowptr[c + 1] && colind[lo] == r) {
+                tmap[e] = lo;
+            } else {
+                tmap[e] = e;
+                atomicOr(flag, 1);
+            }
+        }
+    }
+}
+
+cudaError_t launch_transpose_map(const int32_t* rowptr, const int32_t* colind, int n, int32_t* tmap, int* flag,
+                                 cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_transpose_map<<<152 * 8, 256, 0, s>>>(rowptr, colind, n, tmap, flag);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_add(const int32_t* map, const double* src, int64_t nnz, double* dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] += src[map[e]];
+}
+
+cudaError_t launch_gather_add(const int32_t* map, const double* src, int64_t nnz, double* dst, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    k_gather_add<<<152 * 8, 256, 0, s>>>(map, src, nnz, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_row_index(const int32_t* rowptr, int n, int32_t* rowidx, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_row_index<<<152 * 4, 256, 0, s>>>(rowptr, n, rowidx);

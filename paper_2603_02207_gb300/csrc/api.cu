@@ -70,6 +70,7 @@ struct ll_handle {
     // -> (kernel, consumer-thread targets of both passes)
     std::map<std::tuple<int, int, int, int64_t, int64_t, int>, std::tuple<int, int, int>> tuned_batch;
     int64_t far_entries = 0;  // entries with |col - row| > TMA_HALO of the last validated matrix
+    int64_t far_runs = 0;     // those of them on a diagonal run (a stencil's far diagonals)
     bool band_ok = false;     // the last validated matrix suits the banded kernel
     int max_row = 0;          // longest row of the last validated matrix
     bool sorted = false;      // every row of the last validated matrix has strictly increasing columns
@@ -106,6 +107,7 @@ struct ll_handle {
                               // W_s, W_2s, ... (s > 1) in "bw_ckpt"; 0: none
     bool kept_wall_s = false; // and its pass 1 (W_0 = S) left them in "bw_ckpt_s"
     int64_t kept_far = 0;     // its far-entry count and longest row (TMA plans of the adjoint)
+    int64_t kept_runs = 0;
     int kept_max_row = 0;
     bool kept_sorted = false; // its rows have strictly increasing columns (the symmetry check)
     // final degree of every column of both passes of the last forward (Algorithm 2's rule)
@@ -183,15 +185,16 @@ ll_status check_bounds(ll_handle* h, ll_bounds b) {
 // Validates the device CSR (synchronises the stream).
 ll_status validate_csr(ll_handle* h, const ll_csr* A, cudaStream_t s) {
     if (A->n == 0) return LL_OK;
-    WS(flag, int*, "csr_flag", 4 * sizeof(int));
-    LL_CK(cudaMemsetAsync(flag, 0, 4 * sizeof(int), s));
-    LL_CK(launch_validate_csr(A->rowptr, A->colind, (int)A->n, A->nnz, flag, s, flag + 2, flag + 3));
+    WS(flag, int*, "csr_flag", 5 * sizeof(int));
+    LL_CK(cudaMemsetAsync(flag, 0, 5 * sizeof(int), s));
+    LL_CK(launch_validate_csr(A->rowptr, A->colind, (int)A->n, A->nnz, flag, s, flag + 2, flag + 3, flag + 4));
     h->launches++;
-    int hv[4] = {0, 0, 0, 0};
+    int hv[5] = {0, 0, 0, 0, 0};
     LL_CK(cudaMemcpyAsync(hv, flag, sizeof hv, cudaMemcpyDeviceToHost, s));
     LL_CK(cudaStreamSynchronize(s));
     const int hf = hv[0];
     h->far_entries = hv[1];
+    h->far_runs = hv[4];
     h->max_row = hv[2];
     // the banded kernel takes matrices whose rows hold strictly increasing columns within
     // BAND_H (= TMA_HALO) of the diagonal
@@ -259,7 +262,7 @@ bool plan_exec(ll_handle* h, int kind, int precision, int mode, int n, int64_t n
     if (kind == LL_KERNEL_TMA) {
         // rpt = 2 selects two column pairs per consumer thread (FP32-mixed blocks)
         const int ctas = (threads > 0 && threads <= 256) ? 2 : 1;
-        if (!plan_step_tma(precision, mode, n, nnz, h->far_entries, h->max_row, b, threads, ctas, p, E.tl, h->sm_count,
+        if (!plan_step_tma(precision, mode, n, nnz, h->far_entries, h->far_runs, h->max_row, b, threads, ctas, p, E.tl, h->sm_count,
                            rpt == 2 ? 2 : 1))
             return false;
         E.tl.q.spin_budget = h->spin_budget;
@@ -292,9 +295,10 @@ ll_status bind_exec(ll_handle* h, int precision, int mode, int b, StepExec& E, S
         WS(err, int*, "tma_error", sizeof(int));
         E.tl.q.error = err;
         // one descriptor set per mode (a pass's steps and the adjoint's reverse steps interleave)
-        static const char* mname[NUM_MODES] = {"plain", "accum", "dot", "adj", "4", "accum_stop", "dot_stop", "7",
-                                               "8", "accum_sweep", "dot_sweep", "11", "12", "13", "14", "15"};
-        const std::string mnm = mname[mode];
+        static const char* mname[] = {"plain", "accum", "dot", "adj", "4", "accum_stop", "dot_stop", "7",
+                                      "8", "accum_sweep", "dot_sweep", "11", "12", "13", "14", "15",
+                                      "16", "17", "18", "adj_grad"};
+        const std::string mnm = mode < (int)(sizeof mname / sizeof mname[0]) ? mname[mode] : std::to_string(mode);
         WS(desc, unsigned char*, ("tma_desc_" + mnm).c_str(), E.tl.desc_bytes);
         WS(gcol, int*, ("tma_gcol_" + mnm).c_str(), E.tl.gcol_bytes);
         WS(meta, int4*, ("tma_meta_" + mnm).c_str(), E.tl.meta_bytes);
@@ -320,7 +324,7 @@ ll_status check_tma_flag(ll_handle* h, cudaStream_t s) {
     LL_CK(cudaStreamSynchronize(s));
     if (v) {
         LL_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
-        return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out");
+        return fail(h, LL_ERR_TIMEOUT, "step kernel: a bounded pipeline wait ran out (code " + std::to_string(v) + ")");
     }
     return LL_OK;
 }
@@ -743,9 +747,10 @@ ll_status run_pass(ll_handle* h, const ll_csr* A, const void* vals_prep, int pre
 // block ckpt_name: with stored, it already holds W_1 .. W_m (the forward's trace pass wrote
 // them) and no forward step runs here; otherwise they are recomputed from checkpoints kept there
 // every ckpt_stride (default ceil(sqrt(m))) steps.
-ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, const int32_t* rowidx, const void* W0,
-                             const void* U, long long l, int b, int split, double cq, double gdiv, double grad_output,
-                             double* grad_values, cudaStream_t s, const char* ckpt_name, int stored_stride) {
+ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, const int32_t* rowidx, const int32_t* tmap,
+                             const void* W0, const void* U, long long l, int b, int split, double cq, double gdiv,
+                             double grad_output, double* grad_values, cudaStream_t s, const char* ckpt_name,
+                             int stored_stride) {
     const bool stored = stored_stride > 0;   // the forward wrote the checkpoints at this stride
     const int n = (int)A->n;
     const int prec = h->kept_prec, m = h->kept_m;
@@ -808,6 +813,27 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
     if (cs != LL_OK) return cs;
     cs = choose_exec(h, prec, MODE_ADJ, n, A->nnz, b, h->cfg_kernel, h->cfg_threads, h->cfg_rpt, pa, Ea, s);
     if (cs != LL_OK) return cs;
+    const double scale = grad_output / (sigma * gamma);
+    // the reverse step fused with the gradient contraction (TMA kernel, one column pair per
+    // thread, the shape the autotuner chose for the plain reverse step): no separate SDDMM. The
+    // step accumulates each entry's term in transposed order (gt[e] holds the term of entry
+    // tmap[e]), mapped into grad_values after the last step.
+    StepParams pg = pa;
+    StepExec Eg;
+    bool fused = false;
+    double* gt = nullptr;
+    if (tmap && Ea.kind == LL_KERNEL_TMA && Ea.tl.np == 1) {
+        WS(gtw, double*, "bw_gt", (size_t)A->nnz * sizeof(double));
+        gt = gtw;
+        pg.wj = W0;
+        pg.grad = gt;
+        pg.gscale = scale;
+        if (plan_exec(h, LL_KERNEL_TMA, prec, MODE_ADJ_GRAD, n, A->nnz, b, Ea.threads, 0, pg, Eg)) {
+            if ((cs = bind_exec(h, prec, MODE_ADJ_GRAD, b, Eg, pg, s)) != LL_OK) return cs;
+            LL_CK(cudaMemsetAsync(gt, 0, (size_t)A->nnz * sizeof(double), s));
+            fused = true;
+        }
+    }
     auto plain_step = [&](int j, const void* win, void* wout) -> cudaError_t {
         pp.win = win;
         pp.wout = wout;
@@ -824,7 +850,6 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
         cur = out;
     }
     // phase B: Lambda_m = d_m U, then segments in reverse
-    const double scale = grad_output / (sigma * gamma);
     char* lam_cur = lam;
     LL_CK(launch_scale_cols(prec, U, l, n, b, split, d[m] * cq, d[m] / gdiv, lam_cur, s));
     h->launches++;
@@ -839,6 +864,23 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
         }
         for (int j = j1 - 1; j >= j0; --j) {
             const void* wj = (j == j0) ? wj0 : (const void*)(seg + (size_t)(j - j0 - 1) * blk);
+            if (fused) {
+                // Lambda_j and g_e += (1 / (sigma gamma)) <Lambda_{j+1}[r, :], W_j[c, :]> in one step
+                // (Lambda_0, written at j = 0, is not used)
+                char* lam_next = (lam_cur == lam) ? lam + blk : lam;
+                pg.win = lam_cur;
+                pg.wout = lam_next;
+                pg.wj = wj;
+                pg.beta = beta[j];
+                pg.beta_df = df_split(beta[j]);
+                pg.adj_q = d[j] * cq;
+                pg.adj_g = d[j] / gdiv;
+                pg.adj_q_df = df_split(d[j] * cq);
+                pg.adj_g_df = df_split(d[j] / gdiv);
+                LL_CK(exec_step(h, prec, MODE_ADJ_GRAD, Eg, pg, s));
+                lam_cur = lam_next;
+                continue;
+            }
             // g_e += (1 / (sigma gamma)) <Lambda_{j+1}[r, :], W_j[c, :]>
             LL_CK(launch_sddmm(prec, rowidx, A->colind, A->nnz, lam_cur, wj, l, b, scale, grad_values, s));
             h->launches++;
@@ -856,6 +898,10 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
             LL_CK(exec_step(h, prec, MODE_ADJ, Ea, pa, s));
             lam_cur = lam_next;
         }
+    }
+    if (fused) {
+        LL_CK(launch_gather_add(tmap, gt, A->nnz, grad_values, s));
+        h->launches++;
     }
     LL_CK(cudaGetLastError());
     return check_tma_flag(h, s);
@@ -898,6 +944,19 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
         LL_CK(cudaStreamSynchronize(s));
         if (hs) return fail(h, LL_ERR_INVALID_ARG, "A is not symmetric (the adjoint uses A^T = A)");
     }
+    // the transposed-entry map of the fused adjoint step (rows with strictly increasing columns)
+    const int32_t* tmap = nullptr;
+    if (h->kept_sorted && A->nnz > 0) {
+        WS(tm, int32_t*, "bw_tmap", (size_t)A->nnz * sizeof(int32_t));
+        WS(tflag, int*, "bw_tmap_flag", sizeof(int));
+        LL_CK(cudaMemsetAsync(tflag, 0, sizeof(int), s));
+        LL_CK(launch_transpose_map(A->rowptr, A->colind, n, tm, tflag, s));
+        h->launches++;
+        int ht = 0;
+        LL_CK(cudaMemcpyAsync(&ht, tflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LL_CK(cudaStreamSynchronize(s));
+        if (!ht) tmap = tm;
+    }
     LL_CK(cudaMemsetAsync(grad_values, 0, (size_t)A->nnz * sizeof(double), s));
     auto it_v = h->ws.find(wt == T_F64 ? "fw_basis" : "fw_V");
     if (it_v == h->ws.end()) return fail(h, LL_ERR_NO_FORWARD, "kept basis missing");
@@ -906,6 +965,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     // the step plans below describe the kept forward's matrix (it is not revalidated here)
     h->band_ok = h->kept_band;
     h->far_entries = h->kept_far;
+    h->far_runs = h->kept_runs;
     h->max_row = h->kept_max_row;
     WS(vprep, void*, "bw_vals", (size_t)A->nnz * ew);
     LL_CK(launch_prepare_values(A->values, A->dtype, A->nnz, 1.0 / (sigma * gamma), prec, vprep, s));
@@ -915,7 +975,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     LL_CK(launch_row_index(A->rowptr, n, rowidx, s));
     h->launches++;
     // frozen basis: W_0 = [Q | G'], U = [Q | G' / k]
-    st = adjoint_accumulate(h, A, vprep, rowidx, V, V, l2, b2, kq, 1.0, (double)kg, grad_output, grad_values, s,
+    st = adjoint_accumulate(h, A, vprep, rowidx, tmap, V, V, l2, b2, kq, 1.0, (double)kg, grad_output, grad_values, s,
                             "bw_ckpt", h->kept_stride);
     if (st != LL_OK || !through_qr || !h->kept_qr) return st;
 
@@ -1012,7 +1072,7 @@ ll_status backward_impl(ll_handle* h, const ll_csr* A, double grad_output, doubl
     // ---- the QR term: W_0 = S, U = Gamma
     // pass 1's W_j as the forward kept them, or checkpoints in a block of their own, so that the
     // trace pass's kept W_j stay valid for the next backward
-    return adjoint_accumulate(h, A, vprep, rowidx, S, gam, l1, kq, kq, 1.0, 1.0, grad_output, grad_values, s,
+    return adjoint_accumulate(h, A, vprep, rowidx, tmap, S, gam, l1, kq, kq, 1.0, 1.0, grad_output, grad_values, s,
                               h->kept_stride > 0 ? "bw_ckpt_s" : "bw_ckpt", h->kept_wall_s ? 1 : 0);
 }
 
@@ -1391,6 +1451,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A0, ll_bounds bounds, co
         if (reorder) {
             if ((st = prepare_reorder(h, A0, Aw, &rowmap, &vsrc, s)) != LL_OK) return st;
             A = &Aw;
+            h->far_runs = 0;   // (the order breaks the diagonal runs: gather capacity for every far entry)
         }
     }
     // the gathered hub rows of the degree order kept in L2 (about half of it), for this call's passes
@@ -1800,6 +1861,7 @@ ll_status ll_logdet_forward(ll_handle* h, const ll_csr* A0, ll_bounds bounds, co
         h->kept_stride = wall ? wstride : 0;
         h->kept_wall_s = wall_s != nullptr;
         h->kept_far = h->far_entries;
+        h->kept_runs = h->far_runs;
         h->kept_max_row = h->max_row;
         h->kept_sorted = h->sorted;
         h->kept_m = m;

@@ -704,6 +704,8 @@ bool plan_batched_tma(int precision, int mode, int n_min, double avg_nnz, double
     } else {
         q.auxbytes = q.rowbytes;
     }
+    q.wjbytes = 0;
+    q.gsp = 1;
     q.slot = (int)a128((size_t)4 * q.rowbytes);
     q.recbytes = (int)rec_size(precision);
     const int tp = (b + 1) / 2;

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
             if (lane == 0) ok = mbar_wait_bounded(smem_u32(&full[b]), pf[b], a.spin_budget);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok || *((volatile int*)&s_dead)) {
-                if (lane == 0) { s_dead = 1; *((volatile int*)a.err) = 1; }
+                if (lane == 0) { s_dead = 1; atomicCAS(a.err, 0, TMA_ERR_GRAM); }
                 break;
             }
             pf[b] ^= 1u;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
         if (lane == 0) {
             tc_commit(smem_u32(&fin));
             const long long bud = a.spin_budget > TMA_DRAIN_MIN ? a.spin_budget : TMA_DRAIN_MIN;
-            if (!mbar_wait_bounded(smem_u32(&fin), 0u, bud)) *((volatile int*)a.err) = 1;
+            if (!mbar_wait_bounded(smem_u32(&fin), 0u, bud)) atomicCAS(a.err, 0, TMA_ERR_GRAM);
         }
         __syncwarp();
     } else {
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(GT_MAX_THREADS, 1) k_gram_tc(const GramTcArgs 
             if (waited[b] >= c) return;
             if (!mbar_wait_bounded(smem_u32(&empty[b]), pe[b], a.spin_budget)) {
                 s_dead = 1;
-                *((volatile int*)a.err) = 1;
+                atomicCAS(a.err, 0, TMA_ERR_GRAM);
                 return;
             }
             pe[b] ^= 1u;

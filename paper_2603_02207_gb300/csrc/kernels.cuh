@@ -25,8 +25,17 @@ constexpr int MODE_DOT_STOP = MODE_DOT | MODE_STOP;
 constexpr int MODE_SWEEP = 8;
 constexpr int MODE_ACCUM_SWEEP = MODE_ACCUM | MODE_SWEEP;
 constexpr int MODE_DOT_SWEEP = MODE_DOT | MODE_SWEEP;
-constexpr int NUM_MODES = 16;
+// The adjoint step fused with the gradient contraction (TMA step kernel, on top of ADJ): besides
+// Lambda_j = (B - xi_j I) Lambda_{j+1} + d_j U, a tile also adds, for every stored entry e = (r, c)
+// of its rows, gscale <Lambda_{j+1}[c, :], W_j[r, :]> to grad[e]: the term of the transposed entry
+// (c, r) (B symmetric), from the staged neighbour rows of Lambda_{j+1} and the tile's own W_j rows
+// (staged beside them). grad is therefore in transposed order; the caller maps it back once, after
+// the last step (launch_gather_add through the transposed-entry map).
+constexpr int MODE_GRAD = 16;
+constexpr int MODE_ADJ_GRAD = MODE_ADJ | MODE_GRAD;
+constexpr int NUM_MODES = 32;
 __host__ __device__ constexpr int base_mode(int mode) { return mode & 3; }
+__host__ __device__ constexpr bool grad_mode(int mode) { return (mode & MODE_GRAD) != 0; }
 __host__ __device__ constexpr bool stop_mode(int mode) { return (mode & MODE_STOP) != 0; }
 __host__ __device__ constexpr bool sweep_mode(int mode) { return (mode & MODE_SWEEP) != 0; }
 // per group and step of a sweep: beta_{g,j}, d_{g,j+1}, d_{g,0}
@@ -76,6 +85,10 @@ struct StepParams {
     long long sw_vstride;
     long long hub_bytes;         // TMA step: L2 bytes for the rows of the first (hub) rows of W_j
                                  // gathered with an evict-last policy (0: none)
+    // ADJ_GRAD: W_j (W type, ldw), the gradient in transposed-entry order and its scale
+    const void* wj;
+    double* grad;
+    double gscale;
 };
 
 struct StepLaunch {
@@ -113,8 +126,11 @@ constexpr int TMA_HALO = 2;
 // flag[1]: stored entries with |col - row| > TMA_HALO (int32; saturates nowhere below 2^31)
 // rowmax (optional): atomicMax of the longest row's entry count
 // unsorted (optional): rows whose column indices are not strictly increasing
+// runs (optional): entries of flag[1] on a diagonal run ((i - 1, c - 1) or (i + 1, c + 1) stored,
+// found by binary search: exact for rows with increasing columns, a hint otherwise)
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz,
-                                int* flag, cudaStream_t s, int* rowmax = nullptr, int* unsorted = nullptr);
+                                int* flag, cudaStream_t s, int* rowmax = nullptr, int* unsorted = nullptr,
+                                int* runs = nullptr);
 // flag[0] |= 1 when some stored entry (r, c) has no stored (c, r) of the same value; sorted: every
 // row's columns strictly increase (the search is then binary)
 cudaError_t launch_check_symmetric(const int32_t* rowptr, const int32_t* colind, const void* vals, int dtype, int n,
@@ -144,6 +160,12 @@ cudaError_t launch_scale_cols(int precision, const void* V, long long ld, int n,
                               void* out, cudaStream_t s);
 // rowidx[e] = row of stored entry e
 cudaError_t launch_row_index(const int32_t* rowptr, int n, int32_t* rowidx, cudaStream_t s);
+// tmap[e] = the index of entry (c, r) for every entry e = (r, c) (rows with strictly increasing
+// columns); flag[0] |= 1 where the transposed entry is not stored
+cudaError_t launch_transpose_map(const int32_t* rowptr, const int32_t* colind, int n, int32_t* tmap, int* flag,
+                                 cudaStream_t s);
+// dst[e] += src[map[e]] for e < nnz
+cudaError_t launch_gather_add(const int32_t* map, const double* src, int64_t nnz, double* dst, cudaStream_t s);
 // P = sum_{j<=m} d_j W_j over W_0 = w0 and the m blocks W_1 .. W_m at wk (blk bytes apart), with the
 // P-axpy step's arithmetic and order (same P as the pass); b columns, W and P leading dims ld, ldp
 cudaError_t launch_weighted_sum(int precision, const void* w0, const void* wk, size_t blk, long long ld, int n, int b,
@@ -334,12 +356,14 @@ struct TmaParams {
     int wslots;        // gather slots taken by one extra window (R + 2 HALO rows)
     int rowbytes;      // bytes of one W row (ld * element size)
     int auxbytes;      // bytes of one V (pass 2, adjoint) or P (pass 1) row; 0 without
+    int wjbytes;       // bytes of one staged W_j row (the reverse step with the gradient contraction); 0 without
+    int gsp;           // lanes per entry of the gradient contraction (1, 2 or 4)
     int recbytes;      // bytes of one entry record (prepared value, operand offset)
     int hdr_bytes;     // descriptor header: R + 1 row offsets, z0, record count (16-byte padded)
     int desc_stride;   // bytes per tile of the descriptor array (header and ecap records)
     int gcol_stride;   // bytes per tile of the gather-column array (4 window rows, then fcap columns)
     int stage_bytes;   // bytes per stage: window, aux rows, gathered rows, descriptor
-    int off_aux, off_gat, off_desc;   // the window is at offset 0
+    int off_aux, off_wj, off_gat, off_desc;   // the window is at offset 0
     int hub_rows;      // gathered rows below this index (a degree-ordered matrix's hubs) are kept in
                        // L2 in preference to the others (0: no cache policy)
     int ngrp, gsz;     // a sweep's groups per tile and bytes of one group's part of a stage (its
@@ -352,7 +376,7 @@ struct TmaParams {
     unsigned char* desc_w;       // the same arrays, writable (for the describe kernel)
     int* gcol_w;
     int4* meta_w;
-    int* error;                                  // set to 1 when a bounded wait runs out
+    int* error;                                  // TMA_ERR_* where a bounded wait ran out (the first)
     long long spin_budget;                       // clock64 cycles a wait may spin
     int inject;                                  // test hook: tile 0 expects bytes no copy delivers
 };
@@ -366,10 +390,11 @@ struct TmaLaunch {
 // Shape of a TMA-fed step launch; false when the block layout does not allow TMA (a row wider than
 // 256 elements or not a multiple of 16 bytes) or the pipeline does not fit in shared memory.
 // ctas_per_sm: 1 (one 512-thread CTA with ~223 KB of stages) or 2 (two of half the size).
-// nfar: entries with |col - row| > TMA_HALO; maxrow: the longest row (both size the per-tile record
-// and gather capacities; hints, not bounds)
-bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int maxrow, int b, int threads_target,
-                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count, int np = 1);
+// nfar: entries with |col - row| > TMA_HALO, nrun: those of them on a diagonal run (the extra
+// windows take them); maxrow: the longest row (all three size the per-tile record and gather
+// capacities; hints, not bounds)
+bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int64_t nrun, int maxrow, int b,
+                   int threads_target, int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count, int np = 1);
 cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const StepParams& p, cudaStream_t s);
 // builds the tile descriptors of a plan (L.q.desc_w, gcol_w, meta_w) from the CSR and the prepared
 // values in p; once per pass, before its steps

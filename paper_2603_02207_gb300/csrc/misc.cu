@@ -68,12 +68,24 @@ cudaError_t launch_probes(int out_type, int kind, uint64_t seed, int stream_id, 
 // flag[0] bits: 1 = rowptr decreasing, 2 = column index out of range, 4 = rowptr[0] != 0 or
 // rowptr[n] != nnz. flag[1]: entries farther than TMA_HALO from the diagonal. unsorted (optional):
 // rows whose columns are not strictly increasing.
+// (i, c) is stored in row i (a row of increasing columns; false for a row whose offsets are not in
+// [0, nnz] or decrease)
+__device__ __forceinline__ bool csr_has(const int32_t* rowptr, const int32_t* colind, int64_t nnz, int i, int c) {
+    int lo = rowptr[i], hi = rowptr[i + 1];
+    if (lo < 0 || hi < lo || (int64_t)hi > nnz) return false;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (colind[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return lo < rowptr[i + 1] && colind[lo] == c;
+}
+
 __global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, int* rowmax,
-                               int* unsorted) {
+                               int* unsorted, int* runs) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (tid == 0 && (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) atomicOr(flag, 4);
-    int far = 0, longest = 0, unsort = 0;
+    int far = 0, longest = 0, unsort = 0, run = 0;
     for (int i = tid; i < n; i += stride) {
         const int a = rowptr[i], e = rowptr[i + 1];
         if (e < a) { atomicOr(flag, 1); continue; }
@@ -83,8 +95,14 @@ __global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int
         bool inc = true;
         for (int k = a; k < e; ++k) {
             const int c = colind[k];
-            if (c < 0 || c >= n) atomicOr(flag, 2);
-            else far += (c - i > TMA_HALO || i - c > TMA_HALO) ? 1 : 0;
+            if (c < 0 || c >= n) {
+                atomicOr(flag, 2);
+            } else if (c - i > TMA_HALO || i - c > TMA_HALO) {
+                ++far;
+                if (runs && ((i > 0 && c > 0 && csr_has(rowptr, colind, nnz, i - 1, c - 1)) ||
+                             (i + 1 < n && c + 1 < n && csr_has(rowptr, colind, nnz, i + 1, c + 1))))
+                    ++run;
+            }
             inc = inc && c > prev;
             prev = c;
         }
@@ -93,11 +111,12 @@ __global__ void k_validate_csr(const int32_t* rowptr, const int32_t* colind, int
     if (far > 0) atomicAdd(flag + 1, far);
     if (rowmax && longest > 0) atomicMax(rowmax, longest);
     if (unsorted && unsort > 0) atomicAdd(unsorted, unsort);
+    if (runs && run > 0) atomicAdd(runs, run);
 }
 
 cudaError_t launch_validate_csr(const int32_t* rowptr, const int32_t* colind, int n, int64_t nnz, int* flag, cudaStream_t s,
-                                int* rowmax, int* unsorted) {
-    k_validate_csr<<<152 * 4, 256, 0, s>>>(rowptr, colind, n, nnz, flag, rowmax, unsorted);
+                                int* rowmax, int* unsorted, int* runs) {
+    k_validate_csr<<<152 * 4, 256, 0, s>>>(rowptr, colind, n, nnz, flag, rowmax, unsorted, runs);
     return cudaGetLastError();
 }
 

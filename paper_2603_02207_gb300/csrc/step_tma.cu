@@ -159,10 +159,14 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
             // this tile's gather columns, and a free stage (every consumer warp released the
             // stage's previous tile)
             bool ok = mbar_wait_bounded(smem_u32(&gb[gslot]), (uint32_t)gph, q.spin_budget);
-            if (ok && i >= NST && lane == 0) ok = mbar_wait_bounded(smem_u32(&empty[s]), (uint32_t)(ph ^ 1), q.spin_budget);
+            int where = ok ? 0 : TMA_ERR_GCOL;
+            if (ok && i >= NST && lane == 0) {
+                ok = mbar_wait_bounded(smem_u32(&empty[s]), (uint32_t)(ph ^ 1), q.spin_budget);
+                if (!ok) where = TMA_ERR_EMPTY;
+            }
             if (!__all_sync(0xffffffffu, ok)) {
                 dead = true;
-                if (lane == 0) *((volatile int*)q.error) = 1;
+                if (!ok) atomicCAS(q.error, 0, where);
                 break;
             }
             const int4 mt = gm[gslot];
@@ -180,7 +184,9 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 const uint32_t per_grp = (uint32_t)ngr * 4u * (uint32_t)q.rowbytes +
                                          (uint32_t)(1 + nw) * (uint32_t)(R + 2 * TMA_HALO) * (uint32_t)q.rowbytes +
                                          (has_aux ? (uint32_t)R * (uint32_t)q.auxbytes : 0u);
-                const uint32_t bytes = dbytes16 + (uint32_t)ngrp * per_grp + ((q.inject && i == 0) ? 16u : 0u);
+                // (the gradient contraction's W_j rows: the tile's rows of a contiguous block, one copy)
+                const uint32_t wjb = grad_mode(MODE) ? (uint32_t)min(R, n - r0) * (uint32_t)q.rowbytes : 0u;
+                const uint32_t bytes = dbytes16 + (uint32_t)ngrp * per_grp + wjb + ((q.inject && i == 0) ? 16u : 0u);
                 mbar_arrive_expect_tx(bar, bytes);
                 bulk_copy(smem_u32(st + q.off_desc), q.desc + (size_t)tile * q.desc_stride, dbytes16, bar);
                 if constexpr (!sweep_mode(MODE)) {
@@ -188,6 +194,9 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                     tma_load_rows(smem_u32(st), &tm_win, r0 - TMA_HALO, bar);
                     if (has_aux) tma_load_rows(smem_u32(st + q.off_aux), &tm_aux, r0, bar);
                 }
+                if constexpr (grad_mode(MODE))
+                    bulk_copy(smem_u32(st + q.off_wj), static_cast<const unsigned char*>(p.wj) + (size_t)r0 * q.rowbytes, wjb,
+                              bar);
             }
             const int* gcs = reinterpret_cast<const int*>(ring + gslot * q.gcol_stride);
             const int gs0 = nw * q.wslots;
@@ -271,6 +280,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
         const unsigned aux_off = (unsigned)q.off_aux + (unsigned)rlane * (unsigned)q.auxbytes +
                                  (unsigned)(cpg * (MB == MODE_ACCUM ? sizeof(PP) : sizeof(WP))) + goff;
         int s = 0, ph = 0;
+        int gbase = 0;   // (the gradient contraction: the lane group that takes the tile's first entry)
         int r = (int)blockIdx.x * R + rlane;
         WP* wo = wout + (grow + (size_t)r) * ldq + cpg;   // this thread's W_{j+1} and P pairs, advanced per tile
         PP* po_ptr = pblk + (grow + (size_t)r) * ldpq + cpg;
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
             const bool ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)ph, q.spin_budget);
             if (!__all_sync(0xffffffffu, ok)) {
                 dead = true;
-                if ((tid & 31) == 0) *((volatile int*)q.error) = 1;
+                if ((tid & 31) == 0) atomicCAS(q.error, 0, TMA_ERR_FULL);
                 break;
             }
             const unsigned char* st = smem + s * q.stage_bytes;
@@ -363,6 +373,97 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                     for (int qq = 0; qq < NP; ++qq) po_ptr[qq] = pn[qq];
                 }
             }
+            if constexpr (grad_mode(MODE)) {
+                // the gradient contraction of the tile's entries: entry e = (rw, c) adds
+                // gscale <Lambda_{j+1}[c], W_j[rw]> to grad[e] (the transposed entry's term, in the
+                // tile's entry order: neighbouring entries update neighbouring words, and the old
+                // value is loaded before the dot product), Lambda_{j+1}[c] from its record's operand
+                // row (past the records: global memory), W_j[rw] from the staged rows. An entry takes gsp adjacent lanes (lane u of the group: the column pairs
+                // congruent to u mod gsp, from a start that differs between neighbouring entries, so
+                // that they meet other bank groups), and the entries go round the CTA's lane groups
+                // from where the previous tile's left off, so that every warp takes its share.
+                const int* srp = reinterpret_cast<const int*>(st + q.off_desc);
+                const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_desc + q.hdr_bytes);
+                const int r0t = (int)(blockIdx.x + (long long)i * gridDim.x) * R;
+                const int nr = min(R, n - r0t);
+                const int z0 = srp[R + 1], gcap = srp[R + 2];
+                int ktot = srp[nr];
+                if (ktot < 0 || (long long)ktot > (long long)nr * n || gcap < 0 || gcap > q.ecap) {   // (a header that cannot be)
+                    if (tid == 0) atomicCAS(q.error, 0, TMA_ERR_DESC);
+                    ktot = 0;
+                }
+                const int sp = q.gsp;
+                const int nslot = cthreads / sp;
+                const int sub = tid & (sp - 1);
+                const unsigned gmask = ((1u << sp) - 1u) << ((tid & 31) & ~(sp - 1));
+                const int npairs = (p.b + 1) / 2;
+                int k = tid / sp - gbase;
+                if (k < 0) k += nslot;
+                for (; k < ktot; k += nslot) {
+                    int lo = 0;   // the entry's row: srp[lo] <= k < srp[lo + 1] (16-byte records carry it)
+                    if (PREC != LL_PREC_F32_MIXED && k < gcap) {
+                        lo = rec_row(rec[k]);
+                    } else {
+                        int hi = nr;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (srp[mid] <= k) lo = mid; else hi = mid;
+                        }
+                    }
+                    const WP* wrow = reinterpret_cast<const WP*>(st + q.off_wj + lo * q.rowbytes);
+                    const WP* lrow = k < gcap ? reinterpret_cast<const WP*>(st + rec[k].off)
+                                              : win + (size_t)colind[z0 + k] * ldq;
+                    const int rot = (k * sp) % npairs;
+                    const double gold = sub == 0 ? p.grad[z0 + k] : 0.0;
+                    // two independent accumulators (alternate pairs of the lane's share)
+                    f2x sh[2] = {0ull, 0ull}, sl[2] = {0ull, 0ull};
+                    double a[4] = {0.0, 0.0, 0.0, 0.0};
+                    auto mac = [&](int u, int qr) {
+                        int qq = qr + rot;
+                        if (qq >= npairs) qq -= npairs;
+                        const WP lv = lrow[qq];
+                        const WP wv = wrow[qq];
+                        if constexpr (PREC == LL_PREC_F64) {
+                            a[2 * u] = fma(lv.x, wv.x, a[2 * u]);
+                            a[2 * u + 1] = fma(lv.y, wv.y, a[2 * u + 1]);
+                        } else if constexpr (PREC == LL_PREC_DF64) {
+                            df2_mac_pp(sh[u], sl[u], lv.x, lv.y, f2_sub(0ull, lv.x), wv.x, wv.y);
+                        } else {
+                            df2_mac_f(sh[u], sl[u], lv, 0ull, f2_sub(0ull, lv), wv);   // exact FP32 products
+                        }
+                    };
+                    int qr = sub;
+#pragma unroll 2
+                    for (; qr + sp < npairs; qr += 2 * sp) {
+                        mac(0, qr);
+                        mac(1, qr + sp);
+                    }
+                    if (qr < npairs) mac(0, qr);
+                    double dot;
+                    if constexpr (PREC == LL_PREC_F64) {
+                        dot = (a[0] + a[1]) + (a[2] + a[3]);
+                        for (int o = 1; o < sp; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
+                    } else {
+                        float h = 0.f, lo2 = 0.f;
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            float h0, h1, l0, l1;
+                            f2_unpack(sh[u], h0, h1);
+                            f2_unpack(sl[u], l0, l1);
+                            df_mac(h, lo2, h0, l0, 1.f, 0.f);
+                            df_mac(h, lo2, h1, l1, 1.f, 0.f);
+                        }
+                        for (int o = 1; o < sp; o <<= 1) {
+                            const float ph = __shfl_xor_sync(gmask, h, o), pl = __shfl_xor_sync(gmask, lo2, o);
+                            df_mac(h, lo2, ph, pl, 1.f, 0.f);
+                        }
+                        dot = (double)h + (double)lo2;
+                    }
+                    if (sub == 0) p.grad[z0 + k] = gold + p.gscale * dot;
+                }
+                gbase += ktot % nslot;
+                if (gbase >= nslot) gbase -= nslot;
+            }
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[s]));
             r += rstep;
@@ -406,8 +507,8 @@ cudaError_t launch_tma_typed(const TmaLaunch& L, const CUtensorMap& g, const CUt
 
 }  // namespace
 
-bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int maxrow, int b, int threads_target,
-                   int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count, int np) {
+bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, int64_t nrun, int maxrow, int b,
+                   int threads_target, int ctas_per_sm, StepParams& p, TmaLaunch& L, int sm_count, int np) {
     L = TmaLaunch{};
     if (n <= 0 || b <= 0 || !encode_fn()) return false;
     // two column pairs per thread: the block's pairs must come in twos (ldw a multiple of 4), since a
@@ -419,6 +520,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     if (np != 1 && np != 2) return false;
     if (np == 2 && (p.ldw % 4 != 0 || (base_mode(mode) == MODE_ACCUM && p.ldp % 4 != 0))) return false;
     if (np == 2 && precision == LL_PREC_F64 && !sweep_mode(mode)) return false;
+    if (grad_mode(mode) && (np != 1 || base_mode(mode) != MODE_ADJ || !p.wj || !p.grad)) return false;
     // a sweep's blocks are stacks of ngrp groups of n rows of one group width (ldw = 2 sw_gpairs),
     // b the columns of the groups together
     const int ngrp = sweep_mode(mode) ? (p.sw_gpairs > 0 ? (b / 2) / p.sw_gpairs : 0) : 1;
@@ -431,7 +533,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     const long long ld = p.ldw;
     if (ld > 256 || (ld * ew) % 16 != 0) return false;
     int auxbytes = 0;
-    if (base_mode(mode) == MODE_DOT || mode == MODE_ADJ) {
+    if (base_mode(mode) == MODE_DOT || base_mode(mode) == MODE_ADJ) {
         if (p.ldv != p.ldw) return false;
         auxbytes = (int)(ld * ew);
     } else if (base_mode(mode) == MODE_ACCUM) {
@@ -449,6 +551,15 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     q.rowbytes = (int)(ld * ew);
     q.auxbytes = auxbytes;
     q.hub_rows = p.hub_bytes > 0 && !sweep_mode(mode) ? (int)std::min<long long>(n, p.hub_bytes / q.rowbytes) : 0;
+    // the gradient contraction: the tile's W_j rows staged beside the operand rows; the entries'
+    // dot products split over gsp lanes, about as many lanes per tile as the tile has threads
+    q.wjbytes = grad_mode(mode) ? q.rowbytes : 0;
+    q.gsp = 1;
+    if (grad_mode(mode)) {
+        if ((reinterpret_cast<uintptr_t>(p.wj) & 15) != 0) return false;
+        const double lanes = (double)tp * (double)n / (double)(nnz > 0 ? nnz : 1);
+        q.gsp = lanes >= 4.0 ? 4 : (lanes >= 2.0 ? 2 : 1);
+    }
     q.slot = (int)a128((size_t)4 * q.rowbytes);
     // sweep records: the offset (padded to the value size), then the values of the b / (2 sw_gpairs)
     // groups
@@ -456,6 +567,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
                                   : (int)rec_size(precision);
     const double avg = (double)nnz / (double)n;
     const double avgfar = nfar >= 0 && nfar <= nnz ? (double)nfar / (double)n : avg;
+    const double avgrun = nrun > 0 && nrun <= nfar && nfar <= nnz ? (double)nrun / (double)n : 0.0;
     // tile capacity slack over the mean: more for irregular row lengths (power-law graphs), where
     // tiles above the mean by far are common
     const double slack = maxrow > 4.0 * avg + 16.0 ? 2.0 : 1.25;
@@ -468,7 +580,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     const int np_cap = precision == LL_PREC_F32_MIXED ? TMA_MAX_PROD : 2;
     // layout for R rows per tile; returns the stage count that fits
     auto layout = [&](int Rt) {
-        tma_stage_layout(q, Rt, avg, avgfar, slack);
+        tma_stage_layout(q, Rt, avg, avgfar, slack, avgrun);
         // a sweep's stage: one group part (window, V or P rows, gathered rows) per group, then the
         // shared descriptor
         q.ngrp = ngrp;
@@ -517,6 +629,7 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
     OCC(N_, P_, MODE_ACCUM_STOP) OCC(N_, P_, MODE_DOT_STOP) OCC(N_, P_, MODE_ACCUM_SWEEP) OCC(N_, P_, MODE_DOT_SWEEP)
 #define OCCSW(N_, P_) OCC(N_, P_, MODE_ACCUM_SWEEP) OCC(N_, P_, MODE_DOT_SWEEP)
         OCC4(1, LL_PREC_F64) OCC4(1, LL_PREC_DF64) OCC4(1, LL_PREC_F32_MIXED) OCC4(2, LL_PREC_F32_MIXED)
+        OCC(1, LL_PREC_F64, MODE_ADJ_GRAD) OCC(1, LL_PREC_DF64, MODE_ADJ_GRAD) OCC(1, LL_PREC_F32_MIXED, MODE_ADJ_GRAD)
         OCC4(2, LL_PREC_DF64) OCCSW(2, LL_PREC_F64)
 #undef OCCSW
 #undef OCC4
@@ -567,7 +680,7 @@ cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const S
     if (!encode_rows(&g, p.win, ew, p.ldw, rows, 1) || !encode_rows(&w, p.win, ew, p.ldw, rows, L.q.R + 2 * TMA_HALO))
         return cudaErrorInvalidValue;
     bool aux_ok = true;
-    if (base_mode(mode) == MODE_DOT || mode == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, rows, L.q.R);
+    if (base_mode(mode) == MODE_DOT || base_mode(mode) == MODE_ADJ) aux_ok = encode_rows(&a, p.v, ew, p.ldv, rows, L.q.R);
     else if (base_mode(mode) == MODE_ACCUM && !p.first) aux_ok = encode_rows(&a, p.p, 8, p.ldp, rows, L.q.R);
     else a = w;
     if (!aux_ok) return cudaErrorInvalidValue;
@@ -577,6 +690,7 @@ cudaError_t launch_step_tma(int precision, int mode, const TmaLaunch& L, const S
     LCH(N_, P_, MODE_ACCUM_STOP) LCH(N_, P_, MODE_DOT_STOP) LCH(N_, P_, MODE_ACCUM_SWEEP) LCH(N_, P_, MODE_DOT_SWEEP)
 #define LCHSW(N_, P_) LCH(N_, P_, MODE_ACCUM_SWEEP) LCH(N_, P_, MODE_DOT_SWEEP)
         LCH4(1, LL_PREC_F64) LCH4(1, LL_PREC_DF64) LCH4(1, LL_PREC_F32_MIXED) LCH4(2, LL_PREC_F32_MIXED)
+        LCH(1, LL_PREC_F64, MODE_ADJ_GRAD) LCH(1, LL_PREC_DF64, MODE_ADJ_GRAD) LCH(1, LL_PREC_F32_MIXED, MODE_ADJ_GRAD)
         LCH4(2, LL_PREC_DF64) LCHSW(2, LL_PREC_F64)
 #undef LCHSW
 #undef LCH4

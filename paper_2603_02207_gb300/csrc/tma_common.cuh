@@ -7,6 +7,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <mutex>
 
 #include "common.cuh"
@@ -20,6 +21,10 @@ constexpr int TMA_MAX_THREADS = 608;   // up to 512 consumer threads and three p
 constexpr int TMA_MAX_PROD = 3;
 constexpr int TMA_GRING = 3;           // gather-column blocks staged up to two tiles ahead
 constexpr int TMA_MAX_WIN = 4;         // extra windows per tile (runs of far columns)
+// error flag values of the TMA step kernel (the first failure is kept): a bounded wait that ran out
+// on the gather-column ring, on a stage's release, on a stage's copies; a tile header out of range
+constexpr int TMA_ERR_GCOL = 1, TMA_ERR_EMPTY = 2, TMA_ERR_FULL = 3, TMA_ERR_DESC = 4;
+constexpr int TMA_ERR_GRAM = 8;   // a bounded wait of the tensor-core Gram
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -106,9 +111,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // the byte offset of its operand row W_j[c, :] in the stage (window or gather slot). One
 // broadcast shared-memory load per entry in the consumer loop.
 template <int PREC> struct Rec;
-template <> struct __align__(16) Rec<LL_PREC_F64> { double a; int off, pad; };
-template <> struct __align__(16) Rec<LL_PREC_DF64> { float2 a; int off, pad; };   // (hi, lo)
+template <> struct __align__(16) Rec<LL_PREC_F64> { double a; int off, pad; };     // pad: the entry's row in the tile
+template <> struct __align__(16) Rec<LL_PREC_DF64> { float2 a; int off, pad; };    // (hi, lo); pad as above
 template <> struct __align__(8) Rec<LL_PREC_F32_MIXED> { float a; int off; };
+__device__ __forceinline__ int rec_row(const Rec<LL_PREC_F64>& r) { return r.pad; }
+__device__ __forceinline__ int rec_row(const Rec<LL_PREC_DF64>& r) { return r.pad; }
+__device__ __forceinline__ int rec_row(const Rec<LL_PREC_F32_MIXED>&) { return 0; }   // (not carried)
 
 // Tile descriptors, built once per pass (the matrix and the tile geometry do not change between
 // the m steps). One warp per tile of R rows:
@@ -152,7 +160,11 @@ __global__ void k_tma_describe(const int32_t* rowptr, const int32_t* colind, con
         int* gc = gcol + (size_t)t * gstride;
         for (int e = lane; e <= nr; e += 32) hdr[e] = rowptr[r0 + e] - z0;
         const int wlo = r0 - TMA_HALO, whi = r0 + R + TMA_HALO;
-        // candidate windows (warp-uniform): the first four far columns of the first and last rows
+        // candidate windows (warp-uniform), from the far columns of the first and last rows in
+        // increasing order: a window started HALO before a far column's diagonal d covers the
+        // diagonals d .. d + 2 HALO of every row of the tile, so a column whose diagonal lies
+        // within that reach of the previous candidate's starts none (a stencil's cluster of
+        // neighbouring far diagonals takes one window)
         int cand[NCAND] = {0, 0, 0, 0, 0, 0, 0, 0};
         int nc = 0;
 #pragma unroll
@@ -161,12 +173,15 @@ __global__ void k_tma_describe(const int32_t* rowptr, const int32_t* colind, con
             const int k0 = rowptr[rr], k1 = rowptr[rr + 1];
             const int c = (k0 + lane < k1) ? colind[k0 + lane] : wlo;   // rows longer than 32: the first 32
             unsigned farm = __ballot_sync(0xffffffffu, c < wlo || c >= whi);
-#pragma unroll
-            for (int x = 0; x < NCAND / 2; ++x) {
-                if (!farm) break;
+            long long reach = LLONG_MIN;   // the last diagonal the previous candidate covers
+            while (farm && nc < NCAND) {
                 const int src = __ffs(farm) - 1;
                 farm &= farm - 1;
-                const int wsv = __shfl_sync(0xffffffffu, c, src) - (rr - r0) - TMA_HALO;
+                const int cs = __shfl_sync(0xffffffffu, c, src);
+                const long long dg = (long long)cs - rr;
+                if (dg <= reach) continue;
+                reach = dg + 2 * TMA_HALO;
+                const int wsv = cs - (rr - r0) - TMA_HALO;
                 bool dup = false;
 #pragma unroll
                 for (int y = 0; y < NCAND; ++y) dup = dup || (y < nc && cand[y] == wsv);
@@ -232,6 +247,16 @@ __global__ void k_tma_describe(const int32_t* rowptr, const int32_t* colind, con
                     RecT rr;
                     rr.a = vals[z0 + e];
                     rr.off = off;
+                    if constexpr (PREC != LL_PREC_F32_MIXED) {
+                        // (16-byte records: the entry's row in the tile, for the reverse step's
+                        // gradient contraction)
+                        int lo = 0, hi = nr;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (rowptr[r0 + mid] - z0 <= e) lo = mid; else hi = mid;
+                        }
+                        rr.pad = lo;
+                    }
                     rec[e] = rr;
                 } else {
                     unsigned char* rb = reinterpret_cast<unsigned char*>(rec) + (size_t)e * q.recbytes;
@@ -307,13 +332,20 @@ inline size_t rec_size(int precision) {
 
 
 // Per-stage layout of a tile of Rt rows (entry records, gather slots, operand window, V/P rows):
-// sets ecap, fcap, hdr_bytes, desc_stride, gcol_stride, off_aux, off_gat, off_desc, stage_bytes
-// from rowbytes, auxbytes, slot and recbytes. `avg` / `avgfar` are the mean entries / far entries
-// (outside the window) per row; `slack` the capacity margin over those means.
-inline void tma_stage_layout(TmaParams& q, int Rt, double avg, double avgfar, double slack) {
+// sets ecap, fcap, hdr_bytes, desc_stride, gcol_stride, off_aux, off_wj, off_gat, off_desc,
+// stage_bytes from rowbytes, auxbytes, wjbytes, slot and recbytes. `avg` / `avgfar` are the mean
+// entries / far entries (outside the window) per row; `slack` the capacity margin over those means.
+// `avgrun`: far entries per row on diagonal runs (a stencil's), which the extra windows take: the
+// gather rows then cover TMA_MAX_WIN windows and the other far entries, where that is fewer.
+inline void tma_stage_layout(TmaParams& q, int Rt, double avg, double avgfar, double slack, double avgrun = 0.0) {
     int ecap = (((int)(avg * Rt * slack) + 8) + 3) & ~3;
     if (ecap > 4096) ecap = 4096;
+    q.wslots = (int)(((size_t)(Rt + 2 * TMA_HALO) * q.rowbytes + q.slot - 1) / q.slot);
     int fcap = (((int)(avgfar * Rt * slack) + 8) + 3) & ~3;
+    if (avgrun > 0.0 && avgrun <= avgfar) {
+        const int frun = TMA_MAX_WIN * q.wslots * 4 + ((((int)((avgfar - avgrun) * Rt * slack) + 8) + 3) & ~3);
+        if (frun < fcap) fcap = frun;
+    }
     if (fcap > ecap) fcap = ecap;
     q.R = Rt;
     q.ecap = ecap;
@@ -321,9 +353,9 @@ inline void tma_stage_layout(TmaParams& q, int Rt, double avg, double avgfar, do
     q.hdr_bytes = (int)a16((size_t)(Rt + 3) * 4);
     q.desc_stride = (int)a16((size_t)q.hdr_bytes + (size_t)ecap * q.recbytes);
     q.gcol_stride = (int)a16((size_t)(TMA_MAX_WIN + fcap) * 4);
-    q.wslots = (int)(((size_t)(Rt + 2 * TMA_HALO) * q.rowbytes + q.slot - 1) / q.slot);
     q.off_aux = (int)a128((size_t)(Rt + 2 * TMA_HALO) * q.rowbytes);
-    q.off_gat = q.off_aux + (int)a128((size_t)Rt * q.auxbytes);
+    q.off_wj = q.off_aux + (int)a128((size_t)Rt * q.auxbytes);
+    q.off_gat = q.off_wj + (int)a128((size_t)Rt * q.wjbytes);
     q.off_desc = q.off_gat + (fcap / 4) * q.slot;
     q.stage_bytes = (int)a128((size_t)q.off_desc + (size_t)q.desc_stride);
 }

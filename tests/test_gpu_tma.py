@@ -125,7 +125,10 @@ def test_tma_forward_and_backward(L, prec):
     assert res["tma"][2]["kernel_pass1"] == L.LL_KERNEL_TMA and res["tma"][2]["kernel_pass2"] == L.LL_KERNEL_TMA
     assert res["gather"][2]["kernel_pass2"] == L.LL_KERNEL_GATHER
     assert abs(res["tma"][0] - res["gather"][0]) <= 1e-12 * abs(res["gather"][0])
-    assert np.array_equal(res["tma"][1], res["gather"][1])
+    # the TMA reverse step takes the gradient contraction into its tiles, where each entry's column
+    # pairs are summed in another order than the separate contraction's: equal up to rounding
+    gt, gg = res["tma"][1], res["gather"][1]
+    assert np.max(np.abs(gt - gg)) <= 1e-12 * np.max(np.abs(gg))
     want = O.logdet_leja(A, lo, hi, 20, 30, 4, f32=(prec == "f32"))["estimate"]
     assert abs(res["tma"][0] - want) / abs(want) < TOL[prec]
     del torch
@@ -216,8 +219,9 @@ def test_tma_two_pairs_per_thread_matches_gather_bitwise(L, name, b, threads):
 def test_tma_two_pairs_per_thread_forward_and_backward(L):
     """The trace pass (DOT), the adjoint's recompute (PLAIN) and reverse (ADJ) steps with two
     column pairs per thread: the estimate equals the one-pair kernel's to rounding (the traces
-    are summed over another row grouping), and the value gradients are bit-identical (the SDDMM
-    reads the same W_j and Lambda_j)."""
+    are summed over another row grouping), and so do the value gradients (the one-pair reverse
+    step takes the gradient contraction into its tiles and sums each entry's column pairs in
+    another order than the separate contraction that follows the two-pair step)."""
     need_gpu()
     A, lo, hi = _mat("matern_60")
     dA = L.DeviceCSR.from_host(A, "f32")
@@ -232,6 +236,6 @@ def test_tma_two_pairs_per_thread_forward_and_backward(L):
         assert info["pairs_pass1"] == info["pairs_pass2"] == (2 if rpt == 2 else 1)
         res[rpt] = (est, L.ll_logdet_backward(h, dA, 1.0).cpu().numpy())
     assert abs(res[2][0] - res[0][0]) <= 1e-12 * abs(res[0][0])
-    assert np.array_equal(res[2][1], res[0][1])
+    assert np.max(np.abs(res[2][1] - res[0][1])) <= 1e-12 * np.max(np.abs(res[0][1]))
     want = O.logdet_leja(A, lo, hi, 20, 30, 4, f32=True)["estimate"]
     assert abs(res[2][0] - want) / abs(want) < TOL["f32"]
