@@ -91,6 +91,9 @@ struct ll_handle {
     long long hub_bytes = 0;
     // LL_GRAM_AUTO: the faster Gram kernel per (element type, kx, kz, sym, n), timed on first use
     std::map<std::tuple<int, int, int, int, int>, int> gram_choice;
+    // the adjoint's reverse step with the gradient contraction fused in (1) or followed by the
+    // separate contraction (0), per (precision, n, nnz, width, ld): timed on first use
+    std::map<std::tuple<int, int, long long, int, long long>, int> adj_fuse_choice;
     int kept_gram = LL_GRAM_AUTO;     // and of the kept forward (its backward uses the same)
     // cached coefficients of the last set-up
     double dd_lmin = 0, dd_lmax = 0;
@@ -830,8 +833,37 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
         pg.gscale = scale;
         if (plan_exec(h, LL_KERNEL_TMA, prec, MODE_ADJ_GRAD, n, A->nnz, b, Ea.threads, 0, pg, Eg)) {
             if ((cs = bind_exec(h, prec, MODE_ADJ_GRAD, b, Eg, pg, s)) != LL_OK) return cs;
-            LL_CK(cudaMemsetAsync(gt, 0, (size_t)A->nnz * sizeof(double), s));
             fused = true;
+            // the fused step against the reverse step followed by the separate contraction, both
+            // timed once per shape on the representative operands (Lambda buffers rewritten below,
+            // gt cleared after) and the faster cached: fusing gains where rows are long (13-point
+            // stencil) and can lose where they are short and the step is cheap
+            const auto key = std::make_tuple(prec, n, (long long)A->nnz, b, l);
+            auto it = h->adj_fuse_choice.find(key);
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            LL_CK(cudaStreamIsCapturing(s, &cap));
+            if (it != h->adj_fuse_choice.end()) {
+                fused = it->second != 0;
+            } else if (cap == cudaStreamCaptureStatusNone) {
+                float ms[2] = {0.f, 0.f};
+                const int counted = h->launches;   // the timing runs are not the call's launches
+                for (int v = 0; v < 2; ++v) {
+                    LL_CK(cudaEventRecord(h->ev[6], s));
+                    if (v == 0) {
+                        LL_CK(exec_step(h, prec, MODE_ADJ_GRAD, Eg, pg, s));
+                    } else {
+                        LL_CK(exec_step(h, prec, MODE_ADJ, Ea, pa, s));
+                        LL_CK(launch_sddmm(prec, rowidx, A->colind, A->nnz, lam, W0, l, b, scale, gt, s));
+                    }
+                    LL_CK(cudaEventRecord(h->ev[7], s));
+                    LL_CK(cudaEventSynchronize(h->ev[7]));
+                    LL_CK(cudaEventElapsedTime(&ms[v], h->ev[6], h->ev[7]));
+                }
+                h->launches = counted;
+                fused = ms[0] < ms[1];
+                h->adj_fuse_choice[key] = fused ? 1 : 0;
+            }
+            if (fused) LL_CK(cudaMemsetAsync(gt, 0, (size_t)A->nnz * sizeof(double), s));
         }
     }
     auto plain_step = [&](int j, const void* win, void* wout) -> cudaError_t {
