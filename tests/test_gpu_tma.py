@@ -107,6 +107,51 @@ def test_tma_long_rows_beyond_gather_capacity(L):
         assert rel_err(t[:, :2], want) < TOL[prec]
 
 
+def _six_band_matrix(n: int = 4096, seed: int = 8):
+    """Symmetric, diagonally dominant: the ±1 neighbours, six far bands (offsets ±64, ±128, ±192,
+    every far entry on a diagonal run) and a few isolated far pairs. Validation counts the runs,
+    so a tile's gather rows cover four extra windows; the other two bands' entries and the isolated
+    ones then go past the gather capacity and are read directly."""
+    import scipy.sparse as sp
+    from synth import CSR
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for off in (1, 64, 128, 192):
+        i = np.arange(n - off)
+        rows += [i, i + off]
+        cols += [i + off, i]
+    iso_r = rng.integers(0, n, 40)
+    iso_c = (iso_r + rng.integers(600, n - 600, 40)) % n
+    keep = np.abs(iso_r - iso_c) > 200
+    rows += [iso_r[keep], iso_c[keep]]
+    cols += [iso_c[keep], iso_r[keep]]
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    v = -rng.uniform(0.2, 1.0, r.size)
+    M = sp.coo_matrix((v, (r, c)), shape=(n, n)).tocsr()
+    M.sum_duplicates()
+    M = (M + M.T) * 0.5
+    d = -np.asarray(M.sum(axis=1)).ravel() + 0.05
+    M = (M + sp.diags(d)).tocsr()
+    M.sort_indices()
+    return CSR.from_scipy(M)
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("b", [7, 66])
+def test_tma_windows_and_gathers_past_the_run_capacity(L, prec, b):
+    """Far entries on runs size the gather rows for four extra windows: the bands beyond them and
+    the isolated far entries overflow into direct loads, bit for bit as the register kernel."""
+    A = _six_band_matrix()
+    lo, hi = 0.05, O.gershgorin(A)[1]
+    V = R.rademacher(11, R.STREAM_S, A.n, b)
+    g, _ = _apply(L, A, lo, hi, 8, V, prec, "gather")
+    t, it = _apply(L, A, lo, hi, 8, V, prec, "tma")
+    assert it["kernel_pass1"] == L.LL_KERNEL_TMA
+    assert np.array_equal(g, t)
+    want = O.apply_poly(A, V[:, :3], lo, hi, 8, f32=(prec == "f32"))
+    assert rel_err(t[:, :3], want) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
 def test_tma_forward_and_backward(L, prec):
     """Forward (pass 1 and the trace pass) and the adjoint (recompute and reverse steps)."""
