@@ -93,6 +93,8 @@ enum { LL_DD_AUTO = 0, LL_DD_TABLE_Q = 1 };
  *                   maximum; widths up to 42;
  *   LL_GRAM_DFLOAT  double-float products on the FP32 pipes (any width up to 96).            */
 enum { LL_GRAM_AUTO = 0, LL_GRAM_TENSOR = 1, LL_GRAM_DFLOAT = 2 };
+/* ll_set_adjoint_fusion modes */
+enum { LL_FUSE_AUTO = 0, LL_FUSE_ON = 1, LL_FUSE_OFF = 2 };
 /* Row order of the forward (ll_options.reorder):
  *   LL_REORDER_AUTO    the degree order below for irregular matrices (the longest row above four
  *                      times the mean plus 16, most entries outside the tile windows, not banded)
@@ -212,6 +214,9 @@ typedef struct {
     int batch_tuned;                    /* ll_logdet_batched: 1 when the autotuner chose the launch
                                            shape (step kernel, threads and rows per pass)        */
     int reordered;                      /* 1 when the passes ran on the degree-ordered matrix    */
+    int adjoint_fused;                  /* ll_logdet_backward(_qr): 1 when the reverse steps of its
+                                           last adjoint recurrence ran with the gradient
+                                           contraction fused in, 0 with it separate              */
 } ll_info;
 
 /* ---- handle -------------------------------------------------------------------------------- */
@@ -236,6 +241,18 @@ ll_status ll_set_step_config(ll_handle* h, int step_kernel, int threads_per_bloc
  * leave memory to other work, and lets tests reach the checkpointed layout on small matrices.
  * LL_ERR_INVALID_ARG for a negative value. */
 ll_status ll_set_keep_budget(ll_handle* h, int64_t bytes);
+/* The gradient contraction of ll_logdet_backward(_qr) (the sum over j of
+ * Lambda_{j+1}[r_e, :] . W_j[c_e, :] for every stored entry e) fused into the reverse step of the
+ * adjoint recurrence: the TMA step kernel with one column pair per thread, on a matrix whose
+ * rows hold strictly increasing columns, adds each tile's entries from the rows it stages.
+ *   LL_FUSE_AUTO (default): the first backward of a shape (precision, n, nnz, width) times the
+ *                           fused step against the reverse step plus the separate contraction
+ *                           and keeps the faster on the handle;
+ *   LL_FUSE_ON:  fused wherever it applies;
+ *   LL_FUSE_OFF: always the separate contraction.
+ * Both forms give the same gradient up to the order of each entry's sum. ll_info.adjoint_fused
+ * reports the form the last backward took. LL_ERR_INVALID_ARG for another mode. */
+ll_status ll_set_adjoint_fusion(ll_handle* h, int mode);
 /* Free the handle's device workspace: every block the calls allocated (probe and W blocks, the
  * kept W_j, tile descriptors, the cached degree order) and the captured CUDA graphs, so that other
  * work can use the memory. The kept forward state is dropped (ll_logdet_backward then returns

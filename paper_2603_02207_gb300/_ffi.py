@@ -24,6 +24,7 @@ LL_PROBE_RADEMACHER, LL_PROBE_GAUSSIAN = 0, 1
 LL_SVAL_CENTER, LL_SVAL_HALF_LMAX = 0, 1
 LL_DD_AUTO, LL_DD_TABLE_Q = 0, 1
 LL_GRAM_AUTO, LL_GRAM_TENSOR, LL_GRAM_DFLOAT = 0, 1, 2
+LL_FUSE_AUTO, LL_FUSE_ON, LL_FUSE_OFF = 0, 1, 2
 LL_REORDER_AUTO, LL_REORDER_NONE, LL_REORDER_DEGREE = 0, 1, 2
 LL_STREAM_S, LL_STREAM_G, LL_STREAM_POWER = 0, 1, 2
 LL_KERNEL_AUTO, LL_KERNEL_GATHER, LL_KERNEL_TMA, LL_KERNEL_BAND = 0, 1, 2, 3
@@ -63,7 +64,7 @@ class ll_info(ctypes.Structure):
                 ("kept_w_stride", ctypes.c_int), ("forward_id", ctypes.c_int64),
                 ("pairs_pass1", ctypes.c_int), ("pairs_pass2", ctypes.c_int),
                 ("rows_pass1", ctypes.c_int), ("rows_pass2", ctypes.c_int), ("batch_tuned", ctypes.c_int),
-                ("reordered", ctypes.c_int)]
+                ("reordered", ctypes.c_int), ("adjoint_fused", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -82,6 +83,7 @@ SIGNATURES = {
     "ll_default_options": (None, [ctypes.POINTER(ll_options)]),
     "ll_set_step_config": (_I, [_P, _I, _I, _I]),
     "ll_set_keep_budget": (_I, [_P, _I64]),
+    "ll_set_adjoint_fusion": (_I, [_P, _I]),
     "ll_trim_workspace": (_I, [_P]),
     "ll_debug_inject": (_I, [_P, _I]),
     "ll_leja_points": (_I, [_I, _PD]),

@@ -70,6 +70,11 @@ class Handle:
         """Step kernel of ll_apply_poly and ll_logdet_backward on this handle."""
         self.check(self._lib.ll_set_step_config(self.ptr, STEP_KERNELS[kernel], threads_per_block, rows_per_thread))
 
+    def set_adjoint_fusion(self, mode: str = "auto"):
+        """The backward's gradient contraction fused into its reverse steps: "auto" (timed per
+        shape), "on" or "off" (ll_set_adjoint_fusion)."""
+        self.check(self._lib.ll_set_adjoint_fusion(self.ptr, FUSE_MODES[mode]))
+
     def set_keep_budget(self, nbytes: int = 0):
         """Device memory the forward may keep for the backward (0 = half the free memory)."""
         self.check(self._lib.ll_set_keep_budget(self.ptr, int(nbytes)))
@@ -131,6 +136,7 @@ def host_csr_struct(csr) -> tuple[_ffi.ll_csr, tuple]:
 
 DD_SCHEMES = {"auto": _ffi.LL_DD_AUTO, "table_q": _ffi.LL_DD_TABLE_Q}
 GRAM_METHODS = {"auto": _ffi.LL_GRAM_AUTO, "tensor": _ffi.LL_GRAM_TENSOR, "dfloat": _ffi.LL_GRAM_DFLOAT}
+FUSE_MODES = {"auto": _ffi.LL_FUSE_AUTO, "on": _ffi.LL_FUSE_ON, "off": _ffi.LL_FUSE_OFF}
 REORDERS = {"auto": _ffi.LL_REORDER_AUTO, "none": _ffi.LL_REORDER_NONE, "degree": _ffi.LL_REORDER_DEGREE}
 
 

@@ -75,6 +75,7 @@ struct ll_handle {
     int max_row = 0;          // longest row of the last validated matrix
     bool sorted = false;      // every row of the last validated matrix has strictly increasing columns
     int64_t keep_budget = 0;  // ll_set_keep_budget: bytes the forward may keep for the backward (0: half the free memory)
+    int fuse_mode = LL_FUSE_AUTO;   // ll_set_adjoint_fusion
     int64_t forward_id = 0;   // count of successful forwards on the handle (ll_info.forward_id)
     int gram_method = LL_GRAM_AUTO;   // CholeskyQR2 Gram kernel of the running call (ll_options.qr_gram)
     // the structure last reordered (LL_REORDER_DEGREE) and the allocation generations of the
@@ -825,7 +826,7 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
     StepExec Eg;
     bool fused = false;
     double* gt = nullptr;
-    if (tmap && Ea.kind == LL_KERNEL_TMA && Ea.tl.np == 1) {
+    if (h->fuse_mode != LL_FUSE_OFF && tmap && Ea.kind == LL_KERNEL_TMA && Ea.tl.np == 1) {
         WS(gtw, double*, "bw_gt", (size_t)A->nnz * sizeof(double));
         gt = gtw;
         pg.wj = W0;
@@ -842,7 +843,9 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
             auto it = h->adj_fuse_choice.find(key);
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
             LL_CK(cudaStreamIsCapturing(s, &cap));
-            if (it != h->adj_fuse_choice.end()) {
+            if (h->fuse_mode == LL_FUSE_ON) {
+                fused = true;
+            } else if (it != h->adj_fuse_choice.end()) {
                 fused = it->second != 0;
             } else if (cap == cudaStreamCaptureStatusNone) {
                 float ms[2] = {0.f, 0.f};
@@ -935,6 +938,7 @@ ll_status adjoint_accumulate(ll_handle* h, const ll_csr* A, const void* vprep, c
         LL_CK(launch_gather_add(tmap, gt, A->nnz, grad_values, s));
         h->launches++;
     }
+    h->info.adjoint_fused = fused ? 1 : 0;
     LL_CK(cudaGetLastError());
     return check_tma_flag(h, s);
 }
@@ -1193,6 +1197,14 @@ void ll_default_options(ll_options* o) {
 ll_status ll_debug_inject(ll_handle* h, int what) {
     if (!h || what < LL_INJECT_NONE || what > LL_INJECT_STALL) return LL_ERR_INVALID_ARG;
     h->inject = what;
+    return LL_OK;
+}
+
+ll_status ll_set_adjoint_fusion(ll_handle* h, int mode) {
+    if (!h) return LL_ERR_INVALID_ARG;
+    if (mode != LL_FUSE_AUTO && mode != LL_FUSE_ON && mode != LL_FUSE_OFF)
+        return fail(h, LL_ERR_INVALID_ARG, "unknown adjoint fusion mode");
+    h->fuse_mode = mode;
     return LL_OK;
 }
 

@@ -71,6 +71,9 @@ def test_host_entry_points_reject_bad_arguments(libpath):
     assert lib.ll_divided_differences(_ffi.ll_bounds(2.0, 1.0), 3, 0, p, None) == 3
     assert lib.ll_divided_differences(_ffi.ll_bounds(1.0, 2.0), 3, 7, p, None) == 1
     assert lib.ll_status_string(5) == b"LL_ERR_QR_BREAKDOWN"
+    # handle setters refuse a null handle before touching the device
+    assert lib.ll_set_adjoint_fusion(None, _ffi.LL_FUSE_ON) == 1
+    assert lib.ll_set_keep_budget(None, 0) == 1
     # a condition number of 1e7 switches to the divided-difference table (0 Taylor terms)
     d, terms = L.ll_divided_differences(1.0, 1e7, 60)
     assert terms == 0 and np.all(np.isfinite(d))

@@ -333,3 +333,39 @@ def test_autograd_refuses_a_stale_forward(L):
     with pytest.raises(L.LejaError):
         h2.set_keep_budget(-1)
     del torch
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("mat", ["matern", "irregular"])
+def test_fused_and_separate_contraction_agree_with_the_oracle(L, prec, mat):
+    """The reverse step with the gradient contraction fused in (ll_set_adjoint_fusion "on") and
+    the reverse step followed by the separate contraction ("off"), both on the TMA step kernel
+    with one column pair per thread: each against the oracle's frozen-basis gradient, and the two
+    against each other to rounding (each entry's column pairs are summed in another order)."""
+    if mat == "matern":
+        A = matern_2d(40, 0.3, 1.0)
+        lmin = 0.0081
+    else:
+        A = random_spd(900, nnz_per_row=9, seed=7, empty_rows=4)
+        lmin = max(O.gershgorin(A)[0], 0.05)
+    hi = O.gershgorin(A)[1]
+    m, probes, seed = 20, 30, 3
+    got = {}
+    for mode in ("on", "off"):
+        hh = L.Handle()
+        hh.set_step_config("tma", 0, 1)
+        hh.set_adjoint_fusion(mode)
+        _, got[mode], _ = _gpu_grad(L, hh, A, lmin, hi, m, probes, seed, prec)
+        assert hh.info()["adjoint_fused"] == (1 if mode == "on" else 0)
+    ref = O.logdet_leja(A, lmin, hi, m, probes, seed)
+    want = O.hutchpp_grad_values(A, lmin, hi, m, ref["Q"], ref["Gp"])
+    for mode in ("on", "off"):
+        assert rel_err(got[mode], want) < (1e-9 if prec != "f32" else 1e-4)
+    assert np.max(np.abs(got["on"] - got["off"])) <= 1e-12 * np.max(np.abs(got["off"]))
+
+
+def test_adjoint_fusion_mode_is_checked(L):
+    hh = L.Handle()
+    with pytest.raises(L.LejaError) as ei:
+        hh.check(hh._lib.ll_set_adjoint_fusion(hh.ptr, 7))
+    assert ei.value.name == "LL_ERR_INVALID_ARG"
