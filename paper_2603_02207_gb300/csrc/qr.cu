@@ -123,9 +123,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
     const int kxp = (kx + 3) & ~3;
     const int kzp = sym ? kxp : ((kz + 3) & ~3);
     const int trows = gram_tile_rows(kxp, kzp, sym != 0);
+    // double-float X is read straight from its staged column pairs (hi, hi, lo, lo): no split
+    // arrays for it (and none at all when Z = X)
+    constexpr bool XRAW = std::is_same<TX, dfp>::value;
+    const int xrows = XRAW ? 0 : trows;
     float* xh = sgf;
-    float* xl = xh + trows * kxp;
-    float* zh = sym ? xh : xl + trows * kxp;
+    float* xl = xh + xrows * kxp;
+    float* zh = sym ? xh : xl + xrows * kxp;
     float* zl = sym ? xl : zh + trows * kzp;
     const int ta = kxp / 4, tc = kzp / 4;
     const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
     const int ntiles = (n + trows - 1) / trows;
     // raw tiles staged asynchronously one tile ahead (two buffers after the split arrays), so that
     // the next tile's loads are in flight while this one is computed
-    unsigned char* stg = reinterpret_cast<unsigned char*>(zl + trows * kzp);
+    unsigned char* stg = reinterpret_cast<unsigned char*>(sym ? xl + xrows * kxp : zl + trows * kzp);
     const size_t sxb = stage_bytes<TX>(trows, kxp), szb = sym ? 0 : stage_bytes<TZ>(trows, kzp);
     auto stage = [&](int tile, int b) {
         unsigned char* sb = stg + (size_t)b * (sxb + szb);
@@ -170,16 +174,39 @@ __global__ void __launch_bounds__(QR_THREADS) k_gram(long long ldx, int kx, long
         cp_async_wait<1>();   // this thread's copies of `tile`
         __syncthreads();
         const unsigned char* sb = stg + (size_t)buf * (sxb + szb);
-        split_tile<TX>(sb, kx, kxp, xh, xl, trows);
+        if (!XRAW) split_tile<TX>(sb, kx, kxp, xh, xl, trows);
         if (!sym) split_tile<TZ>(sb + sxb, kz, kzp, zh, zl, trows);
         buf ^= 1;
-        __syncthreads();
+        if (!XRAW || !sym) __syncthreads();   // the split arrays are complete
+        // four columns 4 q .. 4 q + 3 of staged row rr of X as hi and lo parts (columns at or past
+        // kx are zero: the pad column of a staged pair may hold anything)
+        auto raw4 = [&](int rr, int q, float4& h4, float4& l4) {
+            const float4* u = reinterpret_cast<const float4*>(sb + ((size_t)rr * (kxp / 2) + 2 * q) * 16);
+            const float4 v0 = u[0], v1 = u[1];
+            h4 = make_float4(v0.x, v0.y, v1.x, v1.y);
+            l4 = make_float4(v0.z, v0.w, v1.z, v1.w);
+            if (4 * q + 4 > kx) {
+                const int c = kx - 4 * q;   // valid columns of the group (1 .. 3)
+                if (c < 4) { h4.w = 0.f; l4.w = 0.f; }
+                if (c < 3) { h4.z = 0.f; l4.z = 0.f; }
+                if (c < 2) { h4.y = 0.f; l4.y = 0.f; }
+            }
+        };
         if (act) {
             for (int rr = g; rr < trows; rr += G) {
-                const float4 a4h = *reinterpret_cast<const float4*>(&xh[rr * kxp + ia * 4]);
-                const float4 a4l = *reinterpret_cast<const float4*>(&xl[rr * kxp + ia * 4]);
-                const float4 c4h = *reinterpret_cast<const float4*>(&zh[rr * kzp + ic * 4]);
-                const float4 c4l = *reinterpret_cast<const float4*>(&zl[rr * kzp + ic * 4]);
+                float4 a4h, a4l, c4h, c4l;
+                if constexpr (XRAW) {
+                    raw4(rr, ia, a4h, a4l);
+                } else {
+                    a4h = *reinterpret_cast<const float4*>(&xh[rr * kxp + ia * 4]);
+                    a4l = *reinterpret_cast<const float4*>(&xl[rr * kxp + ia * 4]);
+                }
+                if (XRAW && sym) {
+                    raw4(rr, ic, c4h, c4l);
+                } else {
+                    c4h = *reinterpret_cast<const float4*>(&zh[rr * kzp + ic * 4]);
+                    c4l = *reinterpret_cast<const float4*>(&zl[rr * kzp + ic * 4]);
+                }
                 const float ah[4] = {a4h.x, a4h.y, a4h.z, a4h.w}, al[4] = {a4l.x, a4l.y, a4l.z, a4l.w};
                 const f2x c0h = f2_pack(c4h.x, c4h.y), c1h = f2_pack(c4h.z, c4h.w);
                 const f2x c0l = f2_pack(c4l.x, c4l.y), c1l = f2_pack(c4l.z, c4l.w);
@@ -277,7 +304,8 @@ static cudaError_t gram_typed(long long ldx, int kx, long long ldz, int kz, bool
     const int OT = sym ? ta * (ta + 1) / 2 : ta * tc;
     const int chunks = (OT + QR_THREADS - 1) / QR_THREADS;
     const int trows = gram_tile_rows(kxp, kzp, sym);
-    size_t smem = (size_t)trows * (kxp + (sym ? 0 : kzp)) * 2 * sizeof(float) +
+    const int xrows = std::is_same<TX, dfp>::value ? 0 : trows;   // (double-float X: no split arrays)
+    size_t smem = ((size_t)xrows * kxp + (sym ? 0 : (size_t)trows * kzp)) * 2 * sizeof(float) +
                   2 * (stage_bytes<TX>(trows, kxp) + (sym ? 0 : stage_bytes<TZ>(trows, kzp)));
     const size_t red = (size_t)QR_THREADS * 16 * sizeof(double);
     if (smem < red) smem = red;
