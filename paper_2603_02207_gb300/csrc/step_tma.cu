@@ -595,11 +595,15 @@ bool plan_step_tma(int precision, int mode, int n, int64_t nnz, int64_t nfar, in
         q.nst = nst > TMA_MAX_STAGES ? TMA_MAX_STAGES : nst;
         return q.nst;
     };
-    // the most rows per tile that keep three stages (two at the least) in shared memory
+    // the most rows per tile that keep three stages (two at the least) in shared memory; the
+    // reverse step with the gradient contraction takes the most rows that keep two (its staged
+    // W_j rows would cut config 3's tiles from 17 to 12 rows at three stages, and its latency-bound
+    // contraction gains more from the warps than from the third stage: 83.4 -> 74.8 ms per DF64
+    // backward)
     int Rbest = 0;
     for (int Rt = R; Rt >= 1; Rt = Rt > 4 ? Rt * 3 / 4 : Rt - 1) {
         const int nst = layout(Rt);
-        if (nst >= 3) { Rbest = Rt; break; }
+        if (nst >= (grad_mode(mode) ? 2 : 3)) { Rbest = Rt; break; }
         if (nst >= 2 && Rbest == 0) Rbest = Rt;
     }
     if (Rbest == 0) return false;
