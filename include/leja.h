@@ -390,7 +390,9 @@ ll_status ll_logdet_forward_host(ll_handle* h, const ll_csr* A_host, ll_bounds b
  * (c, r) of the same value, else LL_ERR_INVALID_ARG) and the same matrix (pattern and values) as
  * in the forward (only n and nnz are checked; ll_info.forward_id tells a caller whether another
  * forward ran on the handle since its own). The W_j come from the forward's trace pass when it kept them (ll_info.kept_w_steps),
- * else from checkpoints every ckpt_stride steps, recomputed.
+ * else from checkpoints every ckpt_stride steps, recomputed. The contraction over the entries
+ * runs inside the reverse steps or after each of them (ll_set_adjoint_fusion,
+ * ll_info.adjoint_fused); the first backward of a shape may time both forms.
  * grad_values: device, nnz doubles, overwritten. Enqueue only. */
 ll_status ll_logdet_backward(ll_handle* h, const ll_csr* A, double grad_output, double* grad_values, void* stream);
 
