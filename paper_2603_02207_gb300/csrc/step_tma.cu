@@ -377,11 +377,13 @@ __global__ void __launch_bounds__(TMA_MAX_THREADS, 1)
                 // the gradient contraction of the tile's entries: entry e = (rw, c) adds
                 // gscale <Lambda_{j+1}[c], W_j[rw]> to grad[e] (the transposed entry's term, in the
                 // tile's entry order: neighbouring entries update neighbouring words, and the old
-                // value is loaded before the dot product), Lambda_{j+1}[c] from its record's operand
-                // row (past the records: global memory), W_j[rw] from the staged rows. An entry takes gsp adjacent lanes (lane u of the group: the column pairs
-                // congruent to u mod gsp, from a start that differs between neighbouring entries, so
-                // that they meet other bank groups), and the entries go round the CTA's lane groups
-                // from where the previous tile's left off, so that every warp takes its share.
+                // value is loaded before the dot product), Lambda_{j+1}[c] from its record's
+                // operand row (past the records: global memory), W_j[rw] from the staged rows.
+                // An entry takes gsp adjacent lanes (lane u of the group: the column pairs
+                // congruent to u mod gsp, from a start that differs between neighbouring entries,
+                // so that they meet other bank groups), and the entries go round the CTA's lane
+                // groups from where the previous tile's left off, so that every warp takes its
+                // share.
                 const int* srp = reinterpret_cast<const int*>(st + q.off_desc);
                 const RecT* rec = reinterpret_cast<const RecT*>(st + q.off_desc + q.hdr_bytes);
                 const int r0t = (int)(blockIdx.x + (long long)i * gridDim.x) * R;
