@@ -103,3 +103,27 @@ def test_host_binary128_table_rejects_bad_arguments(libpath):
     assert lib.ll_divided_differences_q(_ffi.ll_bounds(2.0, 1.0), 3, p) == 3
     assert lib.ll_divided_differences_q(_ffi.ll_bounds(1.0, 2.0), -1, p) == 1
     assert lib.ll_divided_differences_q(_ffi.ll_bounds(1.0, 2.0), 3, None) == 1
+
+
+def _header_constants() -> dict[str, int]:
+    """LL_ constants of include/leja.h: enumerators with explicit values and #define'd integers."""
+    text = open(os.path.join(ROOT, "include", "leja.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for name, val in re.findall(r"\b(LL_[A-Z0-9_]+)\s*=\s*([0-9]+)\s*[,}]", text):
+        out[name] = int(val)
+    for name, expr in re.findall(r"#define\s+(LL_[A-Z0-9_]+)\s+\(?([0-9 <]+)\)?", text):
+        out[name] = int(eval(expr, {"__builtins__": {}}))   # digits and shifts only
+    return out
+
+
+def test_binding_constants_equal_the_header():
+    """Every LL_ integer the ctypes binding defines is declared in the header with that value."""
+    from paper_2603_02207_gb300 import _ffi
+    hdr = _header_constants()
+    ours = {k: v for k, v in vars(_ffi).items() if k.startswith("LL_") and isinstance(v, int)}
+    assert ours, "no constants in the binding"
+    missing = sorted(k for k in ours if k not in hdr)
+    assert not missing, missing
+    wrong = sorted(k for k, v in ours.items() if hdr[k] != v)
+    assert not wrong, {k: (ours[k], hdr[k]) for k in wrong}
