@@ -45,12 +45,12 @@ ELEM = {"df64": (8, 8, 8, 8), "f64": (8, 8, 8, 8), "f32": (4, 4, 8, 4)}   # s_A,
 
 # DRAM bytes (read + write) of one pass-2 trace-step launch per matrix row, from one ncu capture of
 # each kernel on the 96^3 Laplacian (n = 884,736): DF64 register gathers 1.4777 GB, DF64 TMA
-# 1.4960 GB, FP32-mixed TMA with two column pairs per thread 0.7577 GB. Traffic grows in proportion
+# 1.4945 GB, FP32-mixed TMA with two column pairs per thread 0.7570 GB. Traffic grows in proportion
 # to the rows of a stencil matrix, so the full-size value is this figure times n. Only valid for the
 # trace steps of the kernels as captured (profiles/k_leja_tma_*_96cubed.md).
 TRACE_STEP_DRAM_BYTES_PER_ROW = {("gather", "df64"): 1.477654528e9 / 884736,
-                                 ("tma", "df64"): (1.052321e9 + 0.4436736e9) / 884736,
-                                 ("tma", "f32"): (0.542242816e9 + 0.21548032e9) / 884736}
+                                 ("tma", "df64"): (1.052240128e9 + 0.442266112e9) / 884736,
+                                 ("tma", "f32"): (0.542213632e9 + 0.214823424e9) / 884736}
 
 
 def step_bytes(n: int, nnz: int, b: int, prec: str, mode: str) -> int:
